@@ -1,0 +1,262 @@
+"""Plain FP64 CPU oracle of the QMCUR hot path (arXiv 2402.19147).
+
+TEST INFRASTRUCTURE ONLY (see oracle/quat.py).  Nothing here is fast and
+nothing here is shared with the CUDA library; both sides only share the seeded
+input generators, which hold none of this arithmetic.
+
+Steps, in the order of Algorithm 1 (Sec. 3.1):
+
+* ``probabilities``   - p_j = ||X(:,j)||^2 / ||X||_F^2, q_i = ||X(i,:)||^2 / ||X||_F^2
+                        (QMCUR_length) or p_j = 1/n, q_i = 1/m (QMCUR_uniform), Sec. 3.1.
+* ``sample``          - draw J subset [n] from {p_j} and I subset [m] from {q_i}
+                        (Algorithm 1 steps 1-2).  The paper names no mechanism; the
+                        reading used here is listed in ``sample``'s docstring.
+* ``gather``          - C = X(:,J), R = X(I,:) (Sec. 3.1) and the intersection
+                        W = X(I,J).
+* ``pinv_truncated``  - U = W^+ through the QSVD (Sec. 2.2) of W, computed as the
+                        SVD of its complex adjoint, truncated at rcond and rank_cap.
+* ``reconstruct``     - Z = C (U R) (Eq. 1, Algorithm 1 output).
+* ``residual``        - ||X - Z||_F / ||X||_F (Example 4.2's relative error).
+* ``core_paper``      - the paper's own core C^+ X R^+ (Algorithm 1 step 3), used to
+                        check that it equals W^+ when rank(W) = rank(X).
+
+Parity status: every function is pinned by tests/test_oracle_*.py (Hamilton
+table, complex-adjoint homomorphism, Penrose conditions, reduction to
+numpy.linalg.pinv in the real and complex cases, exact recovery on exactly
+low-rank inputs, Lemma 1, Philox known-answer vectors, brute-force inverse CDF,
+chi-square frequencies of the sampler).
+"""
+import numpy as np
+
+from .quat import (as_q, qmatmul, conj_transpose, complex_adjoint,
+                   from_complex_adjoint, fro2)
+from .philox import philox4x32_10
+
+SAMPLER_UNIFORM = 0
+SAMPLER_NORM = 1
+
+PREFIX_BLOCKS = 256     # number of contiguous blocks of the fixed-order prefix sum
+
+
+# ----------------------------------------------------------------- Sec. 3.1 -
+def squared_norms(A):
+    """Column and row squared norms and ||A||_F^2 (Sec. 3.1, Sec. 2.2).
+
+    col2[j] = sum_i |a_ij|^2, row2[i] = sum_j |a_ij|^2, F = sum_j col2[j].
+    """
+    A = as_q(A)
+    sq = np.sum(A * A, axis=0)              # |a_ij|^2, shape (m, n)
+    col2 = sq.sum(axis=0)
+    row2 = sq.sum(axis=1)
+    F = float(col2.sum())
+    return col2, row2, F
+
+
+def probabilities(A, sampler=SAMPLER_NORM):
+    """Sampling probabilities (p over columns, q over rows) and ||A||_F^2 (Sec. 3.1).
+
+    QMCUR_length: p_j = ||A(:,j)||^2/||A||_F^2, q_i = ||A(i,:)||^2/||A||_F^2.
+    QMCUR_uniform: p_j = 1/n, q_i = 1/m.
+    """
+    A = as_q(A)
+    m, n = A.shape[1], A.shape[2]
+    col2, row2, F = squared_norms(A)
+    if sampler == SAMPLER_UNIFORM:
+        return np.full(n, 1.0 / n), np.full(m, 1.0 / m), F
+    if not np.isfinite(F):
+        raise FloatingPointError("non-finite entry in A")
+    if F == 0.0:
+        raise ZeroDivisionError("||A||_F = 0")
+    return col2 / F, row2 / F, F
+
+
+# -------------------------------------------------------- Algorithm 1, 1-2 -
+def blocked_prefix(p):
+    """Inclusive prefix sums of p in a fixed association order.
+
+    The n entries are cut into PREFIX_BLOCKS contiguous blocks of length
+    L = ceil(n / PREFIX_BLOCKS).  Inside block b the sums run left to right;
+    the block totals are chained left to right into offsets O_b; the prefix
+    at entry k of block b is O_b + s_k.  Every operation is one IEEE double
+    addition rounded to nearest, so any implementation that follows this
+    order gets the same bits.  Returns (P, S) with S the grand total.
+    """
+    p = np.asarray(p, dtype=np.float64)
+    n = p.shape[0]
+    L = -(-n // PREFIX_BLOCKS)
+    P = np.empty(n)
+    offset = 0.0
+    for b in range(PREFIX_BLOCKS):
+        lo = b * L
+        hi = min(n, lo + L)
+        s = 0.0
+        for k in range(lo, hi):
+            s = float(p[k]) if k == lo else s + float(p[k])
+            P[k] = offset + s
+        offset = offset + s
+    return P, offset
+
+
+def _draw_word(seed, stream_id, which, t):
+    key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    ctr = (t & 0xFFFFFFFF, (t >> 32) & 0xFFFFFFFF, stream_id & 0xFFFFFFFF, which)
+    return philox4x32_10(ctr, key)
+
+
+def uniform53(x0, x1):
+    """u = ((x0 << 32 | x1) >> 11) * 2^-53, an exact double in [0, 1)."""
+    return float(((x0 << 32) | x1) >> 11) * (2.0 ** -53)
+
+
+def sample(p, count, seed, stream_id, which, sampler, max_attempts=0):
+    """Draw `count` distinct indices of [len(p)] from the distribution p.
+
+    Reading of Algorithm 1 steps 1-2 (the paper fixes no mechanism):
+    * J and I are *sets*, so the draw is without replacement: a draw that
+      repeats an accepted index is rejected and the next counter is used;
+      the accepted set is returned sorted ascending.
+    * Draw t uses Philox4x32-10 with key = (seed_lo, seed_hi) and counter =
+      (t_lo, t_hi, stream_id, which), which = 0 for columns, 1 for rows.
+    * QMCUR_length (norm): u = uniform53(x0, x1), target = u * S (one rounded
+      multiply), index = first k with P[k] > target, P and S from
+      ``blocked_prefix``.  If no such k exists (target rounded up to S) the
+      last index with p > 0 is taken.
+    * QMCUR_uniform: index = (x0 * n) >> 32 (integer multiply-shift).
+    * At most max_attempts draws (0 selects 64*count + 1024); running out
+      raises RuntimeError (the library reports QMCUR_ERR_SAMPLE_LIMIT).
+    """
+    p = np.asarray(p, dtype=np.float64)
+    n = p.shape[0]
+    if count < 1 or count > n:
+        raise ValueError("count must be in [1, n]")
+    if max_attempts <= 0:
+        max_attempts = 64 * count + 1024
+    if sampler == SAMPLER_NORM:
+        support = int(np.count_nonzero(p > 0))
+        if support < count:
+            raise ValueError("fewer positive probabilities than requested indices")
+        P, S = blocked_prefix(p)
+        last_pos = int(np.nonzero(p > 0)[0][-1])
+    chosen = []
+    taken = np.zeros(n, dtype=bool)
+    t = 0
+    while len(chosen) < count:
+        if t >= max_attempts:
+            raise RuntimeError("sample attempt limit reached")
+        x0, x1, _, _ = _draw_word(seed, stream_id, which, t)
+        t += 1
+        if sampler == SAMPLER_NORM:
+            target = uniform53(x0, x1) * S
+            k = int(np.searchsorted(P, target, side="right"))
+            if k >= n:
+                k = last_pos
+        else:
+            k = (x0 * n) >> 32
+        if not taken[k]:
+            taken[k] = True
+            chosen.append(k)
+    return np.array(sorted(chosen), dtype=np.int64), t
+
+
+# ----------------------------------------------------------------- Sec. 3.1 -
+def gather(A, I, J):
+    """C = A(:,J), R = A(I,:), W = A(I,J) (Sec. 3.1; W is the intersection)."""
+    A = as_q(A)
+    I = np.asarray(I)
+    J = np.asarray(J)
+    C = A[:, :, J].copy()
+    R = A[:, I, :].copy()
+    W = A[:, I][:, :, J].copy()
+    return C, R, W
+
+
+# ------------------------------------------------------------ Sec. 2.2, 3.1 -
+def qsvd_values(W):
+    """Quaternion singular values of W (descending), from its complex adjoint.
+
+    chi(W) has every quaternion singular value twice; one of each pair is kept.
+    """
+    s = np.linalg.svd(complex_adjoint(W), compute_uv=False)
+    return s[0::2].copy()
+
+
+def pinv_truncated(W, rcond=1e-10, rank_cap=0):
+    """Truncated Moore-Penrose inverse of a quaternion matrix (Sec. 2.2, Alg. 1).
+
+    The QSVD W = P Sigma V^H is taken as the SVD of chi(W) (LAPACK, FP64).
+    Kept: sigma_i > rcond * sigma_1, and at most rank_cap of them when
+    rank_cap > 0.  U = V_k Sigma_k^{-1} P_k^H, mapped back from the adjoint.
+    Returns (U, rank, sigma) with sigma the quaternion singular values.
+    """
+    W = as_q(W)
+    X = complex_adjoint(W)
+    Pc, s, Vh = np.linalg.svd(X, full_matrices=False)
+    sq = s[0::2]
+    if sq.size == 0 or sq[0] == 0.0:
+        k = 0
+    else:
+        k = int(np.count_nonzero(sq > rcond * sq[0]))
+    if rank_cap > 0:
+        k = min(k, rank_cap)
+    kk = 2 * k
+    Xp = (Vh[:kk].conj().T / s[:kk]) @ Pc[:, :kk].conj().T
+    return from_complex_adjoint(Xp), k, sq.copy()
+
+
+def pinv_plain(W):
+    """Untruncated-by-cap pseudo-inverse with a tiny relative cut (for C^+, R^+)."""
+    return pinv_truncated(W, rcond=1e-13, rank_cap=0)[0]
+
+
+# ----------------------------------------------------------------- Eq. (1) -
+def reconstruct(C, U, R):
+    """Z = C (U R) (Eq. 1), right product first as the library does."""
+    return qmatmul(C, qmatmul(U, R))
+
+
+def residual(A, Z, mask=None):
+    """Relative Frobenius residual ||A - Z||_F / ||A||_F (Example 4.2).
+
+    With a mask (m x n, nonzero = observed, the set Omega of Example 4.4) both
+    norms run over the observed entries only.  Returns (rel, num2, den2).
+    """
+    A = as_q(A)
+    Z = as_q(Z)
+    D = A - Z
+    if mask is not None:
+        w = (np.asarray(mask) != 0).astype(np.float64)
+        D = D * w
+        A = A * w
+    num2 = fro2(D)
+    den2 = fro2(A)
+    return float(np.sqrt(num2 / den2)) if den2 > 0 else float("nan"), num2, den2
+
+
+def core_paper(A, C, R):
+    """The paper's core U = C^+ X R^+ (Algorithm 1 step 3, Eq. 2)."""
+    return qmatmul(qmatmul(pinv_plain(C), as_q(A)), pinv_plain(R))
+
+
+# -------------------------------------------------------------- Algorithm 1 -
+def qmcur(A, c, r, sampler=SAMPLER_NORM, seed=0, stream_id=0, rcond=1e-10,
+          rank_cap=0, col_p=None, row_p=None):
+    """One QMCUR decomposition of A, Algorithm 1 with U = W^+.
+
+    col_p / row_p may be given to sample from externally computed
+    probabilities (the tests pass the library's so that index sets can be
+    compared bit for bit).
+    """
+    A = as_q(A)
+    p, q, F = probabilities(A, sampler)
+    if col_p is not None:
+        p = np.asarray(col_p, dtype=np.float64)
+    if row_p is not None:
+        q = np.asarray(row_p, dtype=np.float64)
+    J, _ = sample(p, c, seed, stream_id, 0, sampler)
+    I, _ = sample(q, r, seed, stream_id, 1, sampler)
+    C, R, W = gather(A, I, J)
+    U, rank, sigma = pinv_truncated(W, rcond, rank_cap)
+    Z = reconstruct(C, U, R)
+    rel, num2, den2 = residual(A, Z)
+    return dict(p=p, q=q, F=F, J=J, I=I, C=C, R=R, W=W, U=U, rank=rank,
+                sigma=sigma, Z=Z, rel=rel, num2=num2, den2=den2)
