@@ -1,0 +1,216 @@
+/*
+ * qmcur.h - C ABI of libqmcur.so, the GB300 (sm_103a) hot path of quaternion
+ * CUR low-rank approximation (QMCUR, arXiv 2402.19147).
+ *
+ * The calls follow the paper's statement of the problem (Algorithm 1,
+ * Sec. 3.1): given a quaternion matrix X in H^{m x n}, column and row counts
+ * |J| = c, |I| = r and sampling probabilities {p_j}, {q_i}, produce
+ * C = X(:,J), R = X(I,:) and a core U such that X ~ C U R.  The core is the
+ * Moore-Penrose inverse of the intersection W = X(I,J); it equals the paper's
+ * C^+ X R^+ whenever rank(W) = rank(X) (Lemma 1 and the Penrose conditions).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Storage.  A quaternion matrix A = A0 + A1 i + A2 j + A3 k (Sec. 2.2) is held
+ *   *split*: four real planes of the same shape, each row-major with the same
+ *   row stride `ld` (elements).  All plane pointers are DEVICE pointers owned
+ *   by the caller; the library never allocates or frees them.
+ * Streams.  Every call enqueues its kernels on the caller's stream and returns
+ *   without synchronising.  No call copies between host and device, and no
+ *   call allocates device memory: scratch space comes from the caller through
+ *   (workspace, ws_bytes), sized by qmcur_workspace_size().  The workspace of
+ *   one call may be reused by the next call on the same stream.
+ * Errors.  Argument and shape errors are returned synchronously (nothing is
+ *   enqueued).  Errors that depend on the data (non-finite input, zero norm,
+ *   too few columns with positive probability, sampling attempt limit, Jacobi
+ *   sweep limit, a device-side wait that ran out) are written by the kernels
+ *   to the caller's device word *dev_status (first error wins, 0 = OK); the
+ *   caller reads it after synchronising.  Kernels never trap or abort.
+ *   dev_status may be NULL, in which case such errors are not reported.
+ * Indices are 0-based int32; index sets are returned sorted ascending.
+ */
+#ifndef QMCUR_H
+#define QMCUR_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { QMCUR_F32 = 0, QMCUR_F64 = 1 } qmcur_dtype;
+
+/* A device quaternion matrix: plane[t] points to the rows x cols real plane t
+ * (t = 0 real, 1 i, 2 j, 3 k), row-major, row stride ld >= cols elements. */
+typedef struct {
+  void*   plane[4];
+  int64_t rows;
+  int64_t cols;
+  int64_t ld;
+  int32_t dtype; /* qmcur_dtype */
+  int32_t reserved;
+} qmcur_qmat;
+
+/* Sampling strategy of Sec. 3.1: QMCUR_uniform (p_j = 1/n, q_i = 1/m) or
+ * QMCUR_length (p_j = ||X(:,j)||^2 / ||X||_F^2, q_i = ||X(i,:)||^2 / ||X||_F^2). */
+typedef enum { QMCUR_SAMPLER_UNIFORM = 0, QMCUR_SAMPLER_NORM = 1 } qmcur_sampler;
+
+/* Arithmetic of the reconstruction GEMMs C (U R). */
+typedef enum {
+  QMCUR_PREC_FP64   = 0, /* FP64 CUDA-core FMA; all operands FP64             */
+  QMCUR_PREC_FP32   = 1, /* plain FP32 CUDA-core FMA                           */
+  QMCUR_PREC_TF32X3 = 2, /* tensor cores (tcgen05 kind::tf32): each operand
+                            split into big + small TF32 parts, products
+                            big*big + big*small + small*big, FP32 accumulate  */
+  QMCUR_PREC_BF16X3 = 3, /* tensor cores (tcgen05 kind::f16, BF16): hi + lo
+                            parts, products hi*hi + hi*lo + lo*hi              */
+  QMCUR_PREC_BF16X6 = 4  /* tensor cores, BF16 hi + mid + lo parts, the six
+                            products of order <= 2, FP32 accumulate            */
+} qmcur_prec;
+
+typedef enum {
+  QMCUR_OK = 0,
+  QMCUR_ERR_INVALID_ARG = 1,          /* bad pointer, shape, stride, dtype, size */
+  QMCUR_ERR_NONFINITE = 2,            /* NaN or Inf in the input                  */
+  QMCUR_ERR_ZERO_NORM = 3,            /* ||X||_F = 0 with the norm sampler        */
+  QMCUR_ERR_INSUFFICIENT_SUPPORT = 4, /* fewer positive probabilities than c or r */
+  QMCUR_ERR_SAMPLE_LIMIT = 5,         /* max_attempts draws did not give c (r)
+                                         distinct indices                         */
+  QMCUR_ERR_NO_CONVERGENCE = 6,       /* Jacobi sweep limit reached               */
+  QMCUR_ERR_UNSUPPORTED = 7,          /* valid request this build cannot serve    */
+  QMCUR_ERR_CUDA = 8,                 /* a CUDA runtime call failed               */
+  QMCUR_ERR_TIMEOUT = 9               /* a bounded device-side wait ran out       */
+} qmcur_status;
+
+/* Human-readable name of a status code (static string). */
+const char* qmcur_status_str(int32_t status);
+
+/* Bytes of workspace that suffice for every call below on an m x n input with
+ * c sampled columns and r sampled rows at precision `prec`. */
+size_t qmcur_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec);
+
+/*
+ * qmcur_probs - sampling probabilities (Sec. 3.1).
+ *   A        m x n input (F32 or F64).
+ *   sampler  QMCUR_SAMPLER_NORM: col_p[j] = ||A(:,j)||^2 / ||A||_F^2,
+ *            row_p[i] = ||A(i,:)||^2 / ||A||_F^2; the sums run over the four
+ *            planes in FP32 (F32 input) or FP64 (F64 input) in short runs that
+ *            are accumulated in FP64 in a fixed order (bit-reproducible).
+ *            QMCUR_SAMPLER_UNIFORM: col_p[j] = 1/n, row_p[i] = 1/m; A is read
+ *            only when fro2 != NULL.
+ *   col_p    device double[n]; row_p device double[m] (outputs).
+ *   fro2     device double scalar ||A||_F^2 or NULL.
+ *   Device errors: NONFINITE, ZERO_NORM (norm sampler only).
+ */
+qmcur_status qmcur_probs(const qmcur_qmat* A, int32_t sampler, double* col_p, double* row_p,
+                         double* fro2, void* workspace, size_t ws_bytes, int32_t* dev_status,
+                         cudaStream_t stream);
+
+/*
+ * qmcur_sample - Algorithm 1 steps 1-2: draw J subset [n] (|J| = c) from col_p
+ * and I subset [m] (|I| = r) from row_p, then gather C = A(:,J) (m x c),
+ * R = A(I,:) (r x n) and the intersection W = A(I,J) (r x c).
+ *   Draws are without replacement: a draw repeating an accepted index is
+ *   rejected.  Draw t uses Philox4x32-10 (Salmon et al., SC'11) with key
+ *   (seed_lo, seed_hi) and counter (t_lo, t_hi, stream_id, which), which = 0
+ *   for J, 1 for I.  Norm sampler: u = ((x0<<32|x1)>>11) 2^-53, target = u*S,
+ *   index = first k with P[k] > target, P the prefix sums of the probabilities
+ *   taken in 256 contiguous blocks (within-block left to right, block totals
+ *   chained left to right, every addition IEEE double round-to-nearest).
+ *   Uniform sampler: index = (x0 * n) >> 32, col_p / row_p may be NULL.
+ *   max_attempts <= 0 selects 64*count + 1024 draws per set.
+ *   J (device int32[c]) and I (device int32[r]) are written sorted ascending.
+ *   C, R, W may each be NULL; C and R take A's dtype or the other one (F32/F64
+ *   conversion on the fly); W may be F32 or F64.
+ *   Requires 1 <= c <= n, 1 <= r <= m.
+ *   Device errors: INSUFFICIENT_SUPPORT, SAMPLE_LIMIT.
+ */
+qmcur_status qmcur_sample(const qmcur_qmat* A, int32_t sampler, const double* col_p,
+                          const double* row_p, int64_t c, int64_t r, uint64_t seed,
+                          uint32_t stream_id, int32_t max_attempts, int32_t* J, int32_t* I,
+                          qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W, void* workspace,
+                          size_t ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * qmcur_pinv_core - U = W^+ (Sec. 2.2 Moore-Penrose inverse through the QSVD;
+ * Algorithm 1's core), truncated: singular values sigma_i > rcond * sigma_1
+ * are kept, at most rank_cap of them when rank_cap > 0.
+ *   W        r x c, F64 (F32 is widened).
+ *   U        c x r output, F64 or F32.
+ *   rank_out device int32 scalar (number of kept singular values) or NULL.
+ *   sigma_out device double[min(r,c)] quaternion singular values, descending,
+ *            or NULL.
+ *   max_sweeps <= 0 selects 40.  The QSVD is computed in FP64 by one-sided
+ *   (Hestenes) Jacobi rotations in quaternion arithmetic.
+ *   Device errors: NO_CONVERGENCE, NONFINITE, TIMEOUT.
+ */
+qmcur_status qmcur_pinv_core(const qmcur_qmat* W, double rcond, int32_t rank_cap,
+                             int32_t max_sweeps, qmcur_qmat* U, int32_t* rank_out,
+                             double* sigma_out, void* workspace, size_t ws_bytes,
+                             int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * qmcur_reconstruct - Z = C (U R) (Eq. 1 / Algorithm 1 output), computed as
+ * T = U R (c x n) then Z = C T (m x n) with the Hamilton product (Sec. 2.2).
+ *   C m x c, U c x r, R r x n, Z m x n.  prec selects the arithmetic
+ *   (qmcur_prec); QMCUR_PREC_FP64 needs F64 operands and output, the other
+ *   precisions take F32 (U may be F64) and write F32.
+ *   Device errors: TIMEOUT.
+ */
+qmcur_status qmcur_reconstruct(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
+                               int32_t prec, qmcur_qmat* Z, void* workspace, size_t ws_bytes,
+                               int32_t* dev_status, cudaStream_t stream);
+
+/*
+ * qmcur_residual - relative Frobenius residual ||A - Z||_F / ||A||_F
+ * (Example 4.2's error measure).
+ *   If Z != NULL it is read (standalone pass over A and Z).  If Z == NULL the
+ *   reconstruction C (U R) is formed at precision prec inside the GEMM and
+ *   never written (C, U, R required).
+ *   mask     NULL or device uint8 m x n (row stride n): only entries with a
+ *            nonzero byte (the observed set Omega, Example 4.4) enter both
+ *            norms.
+ *   out3     device double[3]: {rel, sum |a - z|^2, sum |a|^2}.  Sums are
+ *            reduced in a fixed order (bit-reproducible).
+ *   Device errors: TIMEOUT.
+ */
+qmcur_status qmcur_residual(const qmcur_qmat* A, const qmcur_qmat* C, const qmcur_qmat* U,
+                            const qmcur_qmat* R, int32_t prec, const uint8_t* mask,
+                            const qmcur_qmat* Z, double* out3, void* workspace,
+                            size_t ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
+/* Options of qmcur_decompose. */
+typedef struct {
+  int32_t  sampler;      /* qmcur_sampler */
+  int32_t  prec;         /* qmcur_prec of the reconstruction GEMMs */
+  uint64_t seed;         /* Philox key */
+  uint32_t stream_id;    /* Philox counter word 2 */
+  int32_t  max_attempts; /* <= 0: default */
+  double   rcond;        /* relative singular value cut of W^+ */
+  int32_t  rank_cap;     /* <= 0: no cap */
+  int32_t  max_sweeps;   /* <= 0: default */
+} qmcur_opts;
+
+/*
+ * qmcur_decompose - one whole QMCUR decomposition (Algorithm 1 with U = W^+)
+ * on the stream: qmcur_probs, qmcur_sample, qmcur_pinv_core, then
+ * qmcur_residual with the reconstruction fused (Z never written).
+ *   Outputs (device, caller-owned): J[c], I[r], C (m x c), R (r x n),
+ *   W (r x c, F64), U (c x r, F64), rank_out, sigma_out[min(r,c)] (may be
+ *   NULL), out3[3] as in qmcur_residual.  col_p[n], row_p[m] (device) receive
+ *   the probabilities.
+ */
+qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qmcur_opts* opts,
+                             double* col_p, double* row_p, int32_t* J, int32_t* I,
+                             qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W, qmcur_qmat* U,
+                             int32_t* rank_out, double* sigma_out, double* out3,
+                             void* workspace, size_t ws_bytes, int32_t* dev_status,
+                             cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QMCUR_H */

@@ -1,0 +1,168 @@
+// C ABI of libqmcur (declared and documented in include/qmcur.h): argument
+// checks, workspace sizing and the composition of the stages.
+#include "common.cuh"
+
+namespace qmcur {
+
+size_t simt_partials(int64_t m, int64_t n);
+size_t residual_partials(int64_t m, int64_t n);
+qmcur_status launch_qgemm_simt(const QView& X, const QView& Y, const QView* Z, const QView* A,
+                               const uint8_t* mask, double* partial, bool fp64, cudaStream_t st);
+__global__ void k_residual_fold(const double* partial, int64_t count, double* out3);
+
+// Tensor-core path (qgemm_tc.cu).
+size_t tc_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec);
+qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
+                                   int32_t prec, qmcur_qmat* Z, const qmcur_qmat* A,
+                                   const uint8_t* mask, double* out3, void* ws, size_t ws_bytes,
+                                   int32_t* dev_status, cudaStream_t st);
+
+size_t gemm_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec) {
+  if (prec == QMCUR_PREC_FP64 || prec == QMCUR_PREC_FP32) {
+    Carve cv(nullptr, 0);
+    cv.take<double>((size_t)(4 * c * n));   // T = U R (FP64 worst case)
+    const size_t p1 = simt_partials(m, n), p2 = residual_partials(m, n);
+    cv.take<double>(2 * (p1 > p2 ? p1 : p2));
+    return cv.off;
+  }
+  return tc_ws_bytes(m, n, c, r, prec);
+}
+
+qmcur_status launch_reconstruct(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
+                                int32_t prec, qmcur_qmat* Z, const qmcur_qmat* A,
+                                const uint8_t* mask, double* out3, void* ws, size_t ws_bytes,
+                                int32_t* dev_status, cudaStream_t st) {
+  if (!valid_qmat(C) || !valid_qmat(U) || !valid_qmat(R)) return QMCUR_ERR_INVALID_ARG;
+  const int64_t m = C->rows, c = C->cols, r = R->rows, n = R->cols;
+  if (U->rows != c || U->cols != r || m < 1 || n < 1 || c < 1 || r < 1) return QMCUR_ERR_INVALID_ARG;
+  if (Z != nullptr && (!valid_qmat(Z) || Z->rows != m || Z->cols != n)) return QMCUR_ERR_INVALID_ARG;
+  if (Z == nullptr && (A == nullptr || out3 == nullptr)) return QMCUR_ERR_INVALID_ARG;
+  if (A != nullptr && (!valid_qmat(A) || A->rows != m || A->cols != n)) return QMCUR_ERR_INVALID_ARG;
+  if (prec == QMCUR_PREC_FP64 || prec == QMCUR_PREC_FP32) {
+    const bool fp64 = prec == QMCUR_PREC_FP64;
+    if (fp64 && (C->dtype != QMCUR_F64 || U->dtype != QMCUR_F64 || R->dtype != QMCUR_F64))
+      return QMCUR_ERR_INVALID_ARG;
+    if (!fp64 && (C->dtype != QMCUR_F32 || R->dtype != QMCUR_F32)) return QMCUR_ERR_INVALID_ARG;
+    if (Z != nullptr && fp64 && Z->dtype != QMCUR_F64) return QMCUR_ERR_INVALID_ARG;
+    Carve cv(ws, ws_bytes);
+    const size_t es = fp64 ? 8 : 4;
+    char* tbuf = cv.take<char>((size_t)(4 * c * n) * es);
+    const size_t p1 = simt_partials(m, n), p2 = residual_partials(m, n);
+    double* partial = cv.take<double>(2 * (p1 > p2 ? p1 : p2));
+    if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
+    QView T;
+    for (int t = 0; t < 4; ++t) T.p[t] = tbuf + (size_t)t * c * n * es;
+    T.rows = c; T.cols = n; T.ld = n; T.dtype = fp64 ? QMCUR_F64 : QMCUR_F32;
+    QView vU = view(U), vR = view(R), vC = view(C);
+    qmcur_status s = launch_qgemm_simt(vU, vR, &T, nullptr, nullptr, nullptr, fp64, st);
+    if (s != QMCUR_OK) return s;
+    if (Z != nullptr) {
+      QView vZ = view(Z);
+      return launch_qgemm_simt(vC, T, &vZ, nullptr, nullptr, nullptr, fp64, st);
+    }
+    QView vA = view(A);
+    s = launch_qgemm_simt(vC, T, nullptr, &vA, mask, partial, fp64, st);
+    if (s != QMCUR_OK) return s;
+    k_residual_fold<<<1, 1024, 0, st>>>(partial, (int64_t)p1, out3);
+    return cuda_ok(cudaGetLastError());
+  }
+  if (prec == QMCUR_PREC_TF32X3 || prec == QMCUR_PREC_BF16X3 || prec == QMCUR_PREC_BF16X6)
+    return launch_reconstruct_tc(C, U, R, prec, Z, A, mask, out3, ws, ws_bytes, dev_status, st);
+  return QMCUR_ERR_INVALID_ARG;
+}
+
+}  // namespace qmcur
+
+using namespace qmcur;
+
+extern "C" {
+
+const char* qmcur_status_str(int32_t s) {
+  switch (s) {
+    case QMCUR_OK: return "QMCUR_OK";
+    case QMCUR_ERR_INVALID_ARG: return "QMCUR_ERR_INVALID_ARG";
+    case QMCUR_ERR_NONFINITE: return "QMCUR_ERR_NONFINITE";
+    case QMCUR_ERR_ZERO_NORM: return "QMCUR_ERR_ZERO_NORM";
+    case QMCUR_ERR_INSUFFICIENT_SUPPORT: return "QMCUR_ERR_INSUFFICIENT_SUPPORT";
+    case QMCUR_ERR_SAMPLE_LIMIT: return "QMCUR_ERR_SAMPLE_LIMIT";
+    case QMCUR_ERR_NO_CONVERGENCE: return "QMCUR_ERR_NO_CONVERGENCE";
+    case QMCUR_ERR_UNSUPPORTED: return "QMCUR_ERR_UNSUPPORTED";
+    case QMCUR_ERR_CUDA: return "QMCUR_ERR_CUDA";
+    case QMCUR_ERR_TIMEOUT: return "QMCUR_ERR_TIMEOUT";
+    default: return "QMCUR_ERR_UNKNOWN";
+  }
+}
+
+size_t qmcur_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec) {
+  if (m < 1 || n < 1 || c < 1 || r < 1) return 0;
+  size_t s = probs_ws_bytes(m, n);
+  const size_t s2 = sample_ws_bytes(m, n), s3 = pinv_ws_bytes(r, c), s4 = gemm_ws_bytes(m, n, c, r, prec);
+  if (s2 > s) s = s2;
+  if (s3 > s) s = s3;
+  if (s4 > s) s = s4;
+  return s + 256;
+}
+
+qmcur_status qmcur_probs(const qmcur_qmat* A, int32_t sampler, double* col_p, double* row_p,
+                         double* fro2, void* workspace, size_t ws_bytes, int32_t* dev_status,
+                         cudaStream_t stream) {
+  return launch_probs(A, sampler, col_p, row_p, fro2, workspace, ws_bytes, dev_status, stream);
+}
+
+qmcur_status qmcur_sample(const qmcur_qmat* A, int32_t sampler, const double* col_p,
+                          const double* row_p, int64_t c, int64_t r, uint64_t seed,
+                          uint32_t stream_id, int32_t max_attempts, int32_t* J, int32_t* I,
+                          qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W, void* workspace,
+                          size_t ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  return launch_sample(A, sampler, col_p, row_p, c, r, seed, stream_id, max_attempts, J, I, C, R, W,
+                       workspace, ws_bytes, dev_status, stream);
+}
+
+qmcur_status qmcur_pinv_core(const qmcur_qmat* W, double rcond, int32_t rank_cap,
+                             int32_t max_sweeps, qmcur_qmat* U, int32_t* rank_out,
+                             double* sigma_out, void* workspace, size_t ws_bytes,
+                             int32_t* dev_status, cudaStream_t stream) {
+  return launch_pinv(W, rcond, rank_cap, max_sweeps, U, rank_out, sigma_out, workspace, ws_bytes,
+                     dev_status, stream);
+}
+
+qmcur_status qmcur_reconstruct(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
+                               int32_t prec, qmcur_qmat* Z, void* workspace, size_t ws_bytes,
+                               int32_t* dev_status, cudaStream_t stream) {
+  if (Z == nullptr) return QMCUR_ERR_INVALID_ARG;
+  return launch_reconstruct(C, U, R, prec, Z, nullptr, nullptr, nullptr, workspace, ws_bytes,
+                            dev_status, stream);
+}
+
+qmcur_status qmcur_residual(const qmcur_qmat* A, const qmcur_qmat* C, const qmcur_qmat* U,
+                            const qmcur_qmat* R, int32_t prec, const uint8_t* mask,
+                            const qmcur_qmat* Z, double* out3, void* workspace,
+                            size_t ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  if (A == nullptr || out3 == nullptr) return QMCUR_ERR_INVALID_ARG;
+  if (Z != nullptr)
+    return launch_residual_standalone(A, Z, mask, out3, workspace, ws_bytes, dev_status, stream);
+  return launch_reconstruct(C, U, R, prec, nullptr, A, mask, out3, workspace, ws_bytes, dev_status,
+                            stream);
+}
+
+qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qmcur_opts* o,
+                             double* col_p, double* row_p, int32_t* J, int32_t* I,
+                             qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W, qmcur_qmat* U,
+                             int32_t* rank_out, double* sigma_out, double* out3,
+                             void* workspace, size_t ws_bytes, int32_t* dev_status,
+                             cudaStream_t stream) {
+  if (A == nullptr || o == nullptr || C == nullptr || R == nullptr || W == nullptr || U == nullptr)
+    return QMCUR_ERR_INVALID_ARG;
+  qmcur_status s = launch_probs(A, o->sampler, col_p, row_p, nullptr, workspace, ws_bytes, dev_status, stream);
+  if (s != QMCUR_OK) return s;
+  s = launch_sample(A, o->sampler, col_p, row_p, c, r, o->seed, o->stream_id, o->max_attempts, J, I,
+                    C, R, W, workspace, ws_bytes, dev_status, stream);
+  if (s != QMCUR_OK) return s;
+  s = launch_pinv(W, o->rcond, o->rank_cap, o->max_sweeps, U, rank_out, sigma_out, workspace,
+                  ws_bytes, dev_status, stream);
+  if (s != QMCUR_OK) return s;
+  return launch_reconstruct(C, U, R, o->prec, nullptr, A, nullptr, out3, workspace, ws_bytes,
+                            dev_status, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Sampling probabilities of QMCUR (Sec. 3.1):
+//   QMCUR_length  p_j = ||X(:,j)||^2 / ||X||_F^2,  q_i = ||X(i,:)||^2 / ||X||_F^2
+//   QMCUR_uniform p_j = 1/n, q_i = 1/m.
+// One streaming pass over the four planes (HBM bound): a CTA owns a tile of
+// kRows rows x kCols columns; each thread owns 4 adjacent columns, so a warp
+// reads 512 contiguous bytes of a row per plane (float4).  Squares are summed
+// in FP32 over short runs (16 terms for a row piece, 32 for a column piece)
+// and carried in FP64 from there on.  Every reduction has a fixed order, so
+// the result is bit-reproducible and no atomics touch values.
+#include "common.cuh"
+
+namespace qmcur {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRows = 32;              // rows per CTA tile
+constexpr int kFlush = 8;              // FP32 column run length (rows)
+constexpr int kCols = kThreads * 4;    // columns per CTA tile
+
+template <typename T>
+struct Acc { using type = float; };
+template <>
+struct Acc<double> { using type = double; };
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* row, int64_t j0, int64_t n, bool vec, T out[4]) {
+  if (vec && j0 + 3 < n) {
+    if constexpr (sizeof(T) == 4) {
+      float4 v = __ldcs(reinterpret_cast<const float4*>(row + j0));
+      out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+    } else {
+      double2 a = __ldcs(reinterpret_cast<const double2*>(row + j0));
+      double2 b = __ldcs(reinterpret_cast<const double2*>(row + j0 + 2));
+      out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) out[u] = (j0 + u < n) ? row[j0 + u] : T(0);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_norm_partial(QView A, bool vec, double* __restrict__ col_part, double* __restrict__ row_part) {
+  using acc_t = typename Acc<T>::type;
+  const int64_t m = A.rows, n = A.cols;
+  const int ctile = blockIdx.x, rtile = blockIdx.y;
+  const int64_t j0 = (int64_t)ctile * kCols + threadIdx.x * 4;
+  const int64_t i0 = (int64_t)rtile * kRows;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ acc_t row_warp[kRows][kThreads / 32];
+
+  double col64[4] = {0.0, 0.0, 0.0, 0.0};
+  acc_t col32[4] = {0, 0, 0, 0};
+  const T* P0 = plane<T>(A, 0);
+  const T* P1 = plane<T>(A, 1);
+  const T* P2 = plane<T>(A, 2);
+  const T* P3 = plane<T>(A, 3);
+  for (int rr = 0; rr < kRows; ++rr) {
+    const int64_t i = i0 + rr;
+    acc_t rs = 0;
+    if (i < m) {
+      T x[4][4];
+      load4<T>(P0 + i * A.ld, j0, n, vec, x[0]);
+      load4<T>(P1 + i * A.ld, j0, n, vec, x[1]);
+      load4<T>(P2 + i * A.ld, j0, n, vec, x[2]);
+      load4<T>(P3 + i * A.ld, j0, n, vec, x[3]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc_t s = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) s = fma((acc_t)x[t][u], (acc_t)x[t][u], s);
+        col32[u] += s;
+        rs += s;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+    if (lane == 0) row_warp[rr][warp] = rs;
+    if ((rr + 1) % kFlush == 0) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { col64[u] += (double)col32[u]; col32[u] = 0; }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (j0 + u < n) col_part[(int64_t)rtile * n + j0 + u] = col64[u];
+  __syncthreads();
+  if (threadIdx.x < kRows) {
+    const int64_t i = i0 + threadIdx.x;
+    if (i < m) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < kThreads / 32; ++w) s += (double)row_warp[threadIdx.x][w];
+      row_part[(int64_t)ctile * m + i] = s;
+    }
+  }
+}
+
+// col2[j] = sum over row tiles (fixed order), row2[i] = sum over column tiles.
+__global__ void k_norm_fold(const double* __restrict__ col_part, const double* __restrict__ row_part,
+                            int64_t m, int64_t n, int rtiles, int ctiles, double* __restrict__ col2,
+                            double* __restrict__ row2) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) {
+    double s = 0.0;
+    for (int t = 0; t < rtiles; ++t) s += col_part[(int64_t)t * n + g];
+    col2[g] = s;
+  } else if (g < n + m) {
+    int64_t i = g - n;
+    double s = 0.0;
+    for (int t = 0; t < ctiles; ++t) s += row_part[(int64_t)t * m + i];
+    row2[i] = s;
+  }
+}
+
+// F = sum_j col2[j] by one CTA in a fixed order; reports NONFINITE / ZERO_NORM.
+__global__ void __launch_bounds__(1024)
+k_norm_total(const double* __restrict__ col2, int64_t n, double* __restrict__ F_out,
+             double* __restrict__ fro2, int check_zero, int32_t* status) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += 1024) s += col2[j];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double F = red[0];
+    *F_out = F;
+    if (fro2 != nullptr) *fro2 = F;
+    if (!isfinite(F)) set_status(status, QMCUR_ERR_NONFINITE);
+    else if (check_zero && F == 0.0) set_status(status, QMCUR_ERR_ZERO_NORM);
+  }
+}
+
+__global__ void k_norm_scale(double* __restrict__ col_p, double* __restrict__ row_p, int64_t m,
+                             int64_t n, const double* __restrict__ F_in) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double F = *F_in;
+  if (g < n) col_p[g] = col_p[g] / F;
+  else if (g < n + m) row_p[g - n] = row_p[g - n] / F;
+}
+
+__global__ void k_uniform(double* __restrict__ col_p, double* __restrict__ row_p, int64_t m, int64_t n) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) col_p[g] = 1.0 / (double)n;
+  else if (g < n + m) row_p[g - n] = 1.0 / (double)m;
+}
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+size_t probs_ws_bytes(int64_t m, int64_t n) {
+  Carve c(nullptr, 0);
+  const int64_t rt = cdiv(m, kRows), ct = cdiv(n, kCols);
+  c.take<double>((size_t)(rt * n));
+  c.take<double>((size_t)(ct * m));
+  c.take<double>((size_t)(n + m));
+  c.take<double>(4);
+  return c.off;
+}
+
+qmcur_status launch_probs(const qmcur_qmat* A, int32_t sampler, double* col_p, double* row_p,
+                          double* fro2, void* ws, size_t ws_bytes, int32_t* dev_status,
+                          cudaStream_t st) {
+  if (!valid_qmat(A) || col_p == nullptr || row_p == nullptr) return QMCUR_ERR_INVALID_ARG;
+  if (sampler != QMCUR_SAMPLER_UNIFORM && sampler != QMCUR_SAMPLER_NORM) return QMCUR_ERR_INVALID_ARG;
+  const int64_t m = A->rows, n = A->cols;
+  if (m < 1 || n < 1) return QMCUR_ERR_INVALID_ARG;
+  const int64_t total = m + n;
+  const int fold_blocks = (int)cdiv(total, 256);
+  if (sampler == QMCUR_SAMPLER_UNIFORM) {
+    k_uniform<<<fold_blocks, 256, 0, st>>>(col_p, row_p, m, n);
+    if (fro2 == nullptr) return cuda_ok(cudaGetLastError());
+  }
+  const int64_t rt = cdiv(m, kRows), ct = cdiv(n, kCols);
+  if (rt > 65535) return QMCUR_ERR_UNSUPPORTED;
+  Carve cv(ws, ws_bytes);
+  double* col_part = cv.take<double>((size_t)(rt * n));
+  double* row_part = cv.take<double>((size_t)(ct * m));
+  double* sums = cv.take<double>((size_t)(n + m));
+  double* F = cv.take<double>(4);
+  if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
+  // Norm mode folds the sums straight into the outputs; uniform mode (which
+  // only wants ||A||_F^2) folds them into scratch, the outputs hold 1/n, 1/m.
+  double* col2 = col_p;
+  double* row2 = row_p;
+  if (sampler == QMCUR_SAMPLER_UNIFORM) { col2 = sums; row2 = sums + n; }
+  QView v = view(A);
+  const size_t es = esize(A->dtype);
+  bool vec = (A->ld * es) % 16 == 0;
+  for (int t = 0; t < 4; ++t) vec = vec && (reinterpret_cast<uintptr_t>(A->plane[t]) % 16 == 0);
+  dim3 grid((unsigned)ct, (unsigned)rt);
+  if (A->dtype == QMCUR_F32) k_norm_partial<float><<<grid, kThreads, 0, st>>>(v, vec, col_part, row_part);
+  else k_norm_partial<double><<<grid, kThreads, 0, st>>>(v, vec, col_part, row_part);
+  k_norm_fold<<<fold_blocks, 256, 0, st>>>(col_part, row_part, m, n, (int)rt, (int)ct, col2, row2);
+  k_norm_total<<<1, 1024, 0, st>>>(col2, n, F, fro2, sampler == QMCUR_SAMPLER_NORM, dev_status);
+  if (sampler == QMCUR_SAMPLER_NORM) k_norm_scale<<<fold_blocks, 256, 0, st>>>(col_p, row_p, m, n, F);
+  return cuda_ok(cudaGetLastError());
+}
+
+}  // namespace qmcur

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of libqmcur.so (C ABI in include/qmcur.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams.  If the library has
+not been built, ``lib()`` raises (there is no CPU fallback).
+
+A quaternion matrix is a torch tensor of shape (4, rows, cols) (planes real,
+i, j, k), float32 or float64, on a CUDA device, with unit stride along the
+last axis; ``qmat()`` turns it into the C descriptor.
+"""
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqmcur.so")
+
+F32, F64 = 0, 1
+SAMPLER_UNIFORM, SAMPLER_NORM = 0, 1
+PREC_FP64, PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3, 4
+PREC_NAMES = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32x3": PREC_TF32X3,
+              "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6}
+STATUS = {0: "QMCUR_OK", 1: "QMCUR_ERR_INVALID_ARG", 2: "QMCUR_ERR_NONFINITE",
+          3: "QMCUR_ERR_ZERO_NORM", 4: "QMCUR_ERR_INSUFFICIENT_SUPPORT",
+          5: "QMCUR_ERR_SAMPLE_LIMIT", 6: "QMCUR_ERR_NO_CONVERGENCE",
+          7: "QMCUR_ERR_UNSUPPORTED", 8: "QMCUR_ERR_CUDA", 9: "QMCUR_ERR_TIMEOUT"}
+
+
+class QmcurError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s" % (where, STATUS.get(code, code)))
+
+
+class QMat(ctypes.Structure):
+    _fields_ = [("plane", ctypes.c_void_p * 4), ("rows", ctypes.c_int64),
+                ("cols", ctypes.c_int64), ("ld", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("sampler", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32),
+                ("max_attempts", ctypes.c_int32), ("rcond", ctypes.c_double),
+                ("rank_cap", ctypes.c_int32), ("max_sweeps", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_QP = ctypes.POINTER(QMat)
+_I64, _I32, _U32, _U64, _D, _SZ = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
+                                   ctypes.c_uint64, ctypes.c_double, ctypes.c_size_t)
+
+# name -> (restype, argtypes); the exported symbols of include/qmcur.h
+SIGNATURES = {
+    "qmcur_status_str": (ctypes.c_char_p, [_I32]),
+    "qmcur_workspace_size": (_SZ, [_I64, _I64, _I64, _I64, _I32]),
+    "qmcur_probs": (_I32, [_QP, _I32, _P, _P, _P, _P, _SZ, _P, _P]),
+    "qmcur_sample": (_I32, [_QP, _I32, _P, _P, _I64, _I64, _U64, _U32, _I32, _P, _P,
+                            _QP, _QP, _QP, _P, _SZ, _P, _P]),
+    "qmcur_pinv_core": (_I32, [_QP, _D, _I32, _I32, _QP, _P, _P, _P, _SZ, _P, _P]),
+    "qmcur_reconstruct": (_I32, [_QP, _QP, _QP, _I32, _QP, _P, _SZ, _P, _P]),
+    "qmcur_residual": (_I32, [_QP, _QP, _QP, _QP, _I32, _P, _QP, _P, _P, _SZ, _P, _P]),
+    "qmcur_decompose": (_I32, [_QP, _I64, _I64, ctypes.POINTER(Opts), _P, _P, _P, _P,
+                               _QP, _QP, _QP, _QP, _P, _P, _P, _P, _SZ, _P, _P]),
+}
+
+
+def lib():
+    """Load libqmcur.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libqmcur.so is not built (run __graft_entry__.build()); "
+                               "the library has no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def qmat(t):
+    """C descriptor of a (4, rows, cols) CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if t.dim() != 3 or t.shape[0] != 4 or t.stride(2) != 1:
+        raise ValueError("quaternion matrix must be (4, rows, cols) with unit column stride")
+    if t.dtype not in (torch.float32, torch.float64):
+        raise ValueError("quaternion planes must be float32 or float64")
+    es = t.element_size()
+    q = QMat()
+    base = t.data_ptr()
+    for k in range(4):
+        q.plane[k] = base + k * t.stride(0) * es
+    q.rows, q.cols = t.shape[1], t.shape[2]
+    q.ld = max(t.stride(1), t.shape[2], 1)
+    q.dtype = F64 if t.dtype == torch.float64 else F32
+    return q
+
+
+def _ref(q):
+    return None if q is None else ctypes.byref(q)
+
+
+def _check(code, where):
+    if code != 0:
+        raise QmcurError(code, where)
+
+
+def workspace_size(m, n, c, r, prec):
+    return int(lib().qmcur_workspace_size(m, n, c, r, prec))
+
+
+def workspace(m, n, c, r, prec, device="cuda"):
+    return torch.empty(workspace_size(m, n, c, r, prec), dtype=torch.uint8, device=device)
+
+
+def status_tensor(device="cuda"):
+    return torch.zeros(1, dtype=torch.int32, device=device)
+
+
+def probs(A, sampler, col_p, row_p, fro2=None, ws=None, status=None, stream=None):
+    _check(lib().qmcur_probs(_ref(qmat(A)), sampler, _ptr(col_p), _ptr(row_p), _ptr(fro2),
+                             _ptr(ws), 0 if ws is None else ws.numel(), _ptr(status),
+                             _stream(stream)), "qmcur_probs")
+
+
+def sample(A, sampler, col_p, row_p, c, r, seed, stream_id, J, I, C=None, R=None, W=None,
+           max_attempts=0, ws=None, status=None, stream=None):
+    qC, qR, qW = qmat(C), qmat(R), qmat(W)
+    _check(lib().qmcur_sample(_ref(qmat(A)), sampler, _ptr(col_p), _ptr(row_p), c, r,
+                              seed, stream_id, max_attempts, _ptr(J), _ptr(I), _ref(qC),
+                              _ref(qR), _ref(qW), _ptr(ws), 0 if ws is None else ws.numel(),
+                              _ptr(status), _stream(stream)), "qmcur_sample")
+
+
+def pinv_core(W, U, rcond=1e-10, rank_cap=0, max_sweeps=0, rank_out=None, sigma_out=None,
+              ws=None, status=None, stream=None):
+    _check(lib().qmcur_pinv_core(_ref(qmat(W)), rcond, rank_cap, max_sweeps, _ref(qmat(U)),
+                                 _ptr(rank_out), _ptr(sigma_out), _ptr(ws),
+                                 0 if ws is None else ws.numel(), _ptr(status),
+                                 _stream(stream)), "qmcur_pinv_core")
+
+
+def reconstruct(C, U, R, prec, Z, ws=None, status=None, stream=None):
+    _check(lib().qmcur_reconstruct(_ref(qmat(C)), _ref(qmat(U)), _ref(qmat(R)), prec,
+                                   _ref(qmat(Z)), _ptr(ws), 0 if ws is None else ws.numel(),
+                                   _ptr(status), _stream(stream)), "qmcur_reconstruct")
+
+
+def residual(A, out3, C=None, U=None, R=None, prec=PREC_FP32, mask=None, Z=None, ws=None,
+             status=None, stream=None):
+    _check(lib().qmcur_residual(_ref(qmat(A)), _ref(qmat(C)), _ref(qmat(U)), _ref(qmat(R)),
+                                prec, _ptr(mask), _ref(qmat(Z)), _ptr(out3), _ptr(ws),
+                                0 if ws is None else ws.numel(), _ptr(status),
+                                _stream(stream)), "qmcur_residual")
+
+
+class Decomposition:
+    """Device buffers of one QMCUR decomposition of an m x n input."""
+
+    def __init__(self, m, n, c, r, prec, dtype=torch.float32, device="cuda"):
+        self.m, self.n, self.c, self.r, self.prec = m, n, c, r, prec
+        f = dict(device=device)
+        self.col_p = torch.empty(n, dtype=torch.float64, **f)
+        self.row_p = torch.empty(m, dtype=torch.float64, **f)
+        self.J = torch.empty(c, dtype=torch.int32, **f)
+        self.I = torch.empty(r, dtype=torch.int32, **f)
+        self.C = torch.empty(4, m, c, dtype=dtype, **f)
+        self.R = torch.empty(4, r, n, dtype=dtype, **f)
+        self.W = torch.empty(4, r, c, dtype=torch.float64, **f)
+        self.U = torch.empty(4, c, r, dtype=torch.float64, **f)
+        self.rank = torch.zeros(1, dtype=torch.int32, **f)
+        self.sigma = torch.empty(min(r, c), dtype=torch.float64, **f)
+        self.out3 = torch.empty(3, dtype=torch.float64, **f)
+        self.status = torch.zeros(1, dtype=torch.int32, **f)
+        self.ws = workspace(m, n, c, r, prec, device)
+
+
+def decompose(A, D, sampler=SAMPLER_NORM, seed=0, stream_id=0, rcond=1e-10, rank_cap=0,
+              max_sweeps=0, max_attempts=0, stream=None):
+    """One whole QMCUR decomposition of A into the buffers of D (qmcur_decompose)."""
+    o = Opts(sampler, D.prec, seed, stream_id, max_attempts, rcond, rank_cap, max_sweeps)
+    qs = [qmat(D.C), qmat(D.R), qmat(D.W), qmat(D.U)]
+    _check(lib().qmcur_decompose(_ref(qmat(A)), D.c, D.r, ctypes.byref(o), _ptr(D.col_p),
+                                 _ptr(D.row_p), _ptr(D.J), _ptr(D.I), *[_ref(q) for q in qs],
+                                 _ptr(D.rank), _ptr(D.sigma), _ptr(D.out3), _ptr(D.ws),
+                                 D.ws.numel(), _ptr(D.status), _stream(stream)),
+           "qmcur_decompose")
+
+
+def check_status(status, where="device"):
+    code = int(status.item())
+    if code != 0:
+        raise QmcurError(code, where)

@@ -1,0 +1,241 @@
+"""Parity of every step of the CUDA hot path with the FP64 oracle, through the
+C ABI, on seeded synthetic inputs (several tiles and ragged tails), plus the
+status-code paths.
+
+Tolerances (derived from the arithmetic, u32 = 2^-24, u64 = 2^-53):
+* probabilities of FP32 input: each squared norm is an FP32 sum of at most 20
+  rounding steps before FP64 takes over (16 terms per thread piece, a 5-level
+  warp tree) -> elementwise relative error <= 24 u32; FP64 input: 1e-12.
+* index sets and gathers: bit-exact (integer work; the norm sampler is fed the
+  library's own probabilities on both sides).
+* pseudo-inverse (FP64 Jacobi vs LAPACK SVD of the complex adjoint): relative
+  Frobenius 1e-12 on the FP64 workload, scaled by kappa(W_k) elsewhere.
+* reconstruction: FP64 1e-12, FP32 and split paths 1e-5 relative Frobenius
+  (both sides given the same U rounded to FP32).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import qmcur as O
+from paper_2402_19147_gb300 import qmcur as Q
+from paper_2402_19147_gb300 import synth
+from gpu_util import U32, dev, host, probs, rel_fro, run_status
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    Q.lib()
+
+
+# ----------------------------------------------------------- probabilities -
+@pytest.mark.parametrize("m,n", [(300, 700), (1, 5), (64, 1025), (257, 33)])
+def test_probs_norm_fp32(m, n):
+    A = synth.lowrank_gaussian(m, n, 3, seed=m + n, noise_rel=0.1)[0]
+    col_p, row_p, fro2, st = probs(dev(A), Q.SAMPLER_NORM)
+    assert st == 0
+    p, q, F = O.probabilities(A.astype(np.float64), O.SAMPLER_NORM)
+    assert np.allclose(host(col_p), p, rtol=24 * U32, atol=0)
+    assert np.allclose(host(row_p), q, rtol=24 * U32, atol=0)
+    assert abs(host(fro2)[0] - F) <= 24 * U32 * F
+
+
+def test_probs_norm_fp64_and_uniform():
+    A = synth.make("gauss256_rank10_fp64")
+    col_p, row_p, fro2, st = probs(dev(A), Q.SAMPLER_NORM)
+    assert st == 0
+    p, q, F = O.probabilities(A, O.SAMPLER_NORM)
+    assert rel_fro(host(col_p), p) < 1e-12 and rel_fro(host(row_p), q) < 1e-12
+    col_u, row_u, fro2u, st = probs(dev(A), Q.SAMPLER_UNIFORM)
+    assert st == 0
+    assert np.all(host(col_u) == 1.0 / 256) and np.all(host(row_u) == 1.0 / 256)
+    assert abs(host(fro2u)[0] - F) < 1e-12 * F
+
+
+def test_probs_status_codes():
+    Z = np.zeros((4, 20, 30), dtype=np.float32)
+    _, _, _, st = probs(dev(Z), Q.SAMPLER_NORM)
+    assert st == 3                                  # ZERO_NORM
+    Z[2, 5, 7] = np.nan
+    _, _, _, st = probs(dev(Z), Q.SAMPLER_NORM)
+    assert st == 2                                  # NONFINITE
+    with pytest.raises(Q.QmcurError) as e:          # too small a workspace
+        Q.probs(dev(Z), 1, torch.empty(30, dtype=torch.float64, device="cuda"),
+                torch.empty(20, dtype=torch.float64, device="cuda"), None,
+                torch.empty(8, dtype=torch.uint8, device="cuda"))
+    assert e.value.code == 1
+
+
+# ------------------------------------------------------------ sample/gather -
+def _sample(A_t, sampler, col_p, row_p, c, r, seed, stream_id, max_attempts=0, gather=True,
+            Wdtype=torch.float64):
+    m, n = A_t.shape[1], A_t.shape[2]
+    J = torch.full((c,), -1, dtype=torch.int32, device="cuda")
+    I = torch.full((r,), -1, dtype=torch.int32, device="cuda")
+    C = R = W = None
+    if gather:
+        C = torch.empty(4, m, c, dtype=A_t.dtype, device="cuda")
+        R = torch.empty(4, r, n, dtype=A_t.dtype, device="cuda")
+        W = torch.empty(4, r, c, dtype=Wdtype, device="cuda")
+    ws = Q.workspace(m, n, c, r, Q.PREC_FP32)
+    st = Q.status_tensor()
+    Q.sample(A_t, sampler, col_p, row_p, c, r, seed, stream_id, J, I, C, R, W,
+             max_attempts=max_attempts, ws=ws, status=st)
+    return J, I, C, R, W, run_status(st)
+
+
+@pytest.mark.parametrize("sampler", [Q.SAMPLER_NORM, Q.SAMPLER_UNIFORM])
+@pytest.mark.parametrize("m,n,c,r,seed", [(300, 700, 40, 25, 7), (1000, 257, 257, 3, 1),
+                                          (5, 4096, 100, 5, 2**40 + 3)])
+def test_sample_bit_exact_and_gather(sampler, m, n, c, r, seed):
+    A = synth.lowrank_gaussian(m, n, 4, seed=m, noise_rel=0.05)[0]
+    A_t = dev(A)
+    col_p, row_p, _, st = probs(A_t, sampler)
+    assert st == 0
+    J, I, C, R, W, st = _sample(A_t, sampler, col_p, row_p, c, r, seed, 9)
+    assert st == 0
+    Jo, _ = O.sample(host(col_p), c, seed, 9, 0, sampler)
+    Io, _ = O.sample(host(row_p), r, seed, 9, 1, sampler)
+    assert np.array_equal(host(J), Jo) and np.array_equal(host(I), Io)
+    Co, Ro, Wo = O.gather(A.astype(np.float64), Io, Jo)
+    assert np.array_equal(host(C), Co.astype(np.float32))
+    assert np.array_equal(host(R), Ro.astype(np.float32))
+    assert np.array_equal(host(W), Wo)
+
+
+def test_sample_status_codes():
+    A = np.zeros((4, 50, 60), dtype=np.float32)
+    A[0, :, 3] = 1.0
+    A[0, :, 9] = 1.0
+    A_t = dev(A)
+    col_p, row_p, _, st = probs(A_t, Q.SAMPLER_NORM)
+    assert st == 0
+    *_, st = _sample(A_t, Q.SAMPLER_NORM, col_p, row_p, 3, 4, 0, 0, gather=False)
+    assert st == 4                                  # INSUFFICIENT_SUPPORT
+    A[0, 0, 20] = 1e-7
+    A_t = dev(A)
+    col_p, row_p, _, st = probs(A_t, Q.SAMPLER_NORM)
+    *_, st = _sample(A_t, Q.SAMPLER_NORM, col_p, row_p, 3, 4, 0, 0, max_attempts=64,
+                     gather=False)
+    assert st == 5                                  # SAMPLE_LIMIT
+    with pytest.raises(Q.QmcurError):
+        _sample(A_t, Q.SAMPLER_UNIFORM, None, None, 61, 4, 0, 0)   # c > n
+
+
+# ----------------------------------------------------------- pseudo-inverse -
+def _pinv(W, rcond=1e-10, rank_cap=0, Udtype=torch.float64):
+    r, c = W.shape[1], W.shape[2]
+    U = torch.empty(4, c, r, dtype=Udtype, device="cuda")
+    rank = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sig = torch.empty(min(r, c), dtype=torch.float64, device="cuda")
+    ws = Q.workspace(r, c, c, r, Q.PREC_FP64)
+    st = Q.status_tensor()
+    Q.pinv_core(dev(W), U, rcond, rank_cap, 0, rank, sig, ws, st)
+    return U, int(host(rank)[0]), host(sig), run_status(st)
+
+
+def _kappa_k(sig, k):
+    return sig[0] / sig[k - 1] if k > 0 else 1.0
+
+
+@pytest.mark.parametrize("r,c", [(30, 20), (20, 30), (17, 17), (1, 5), (6, 1)])
+def test_pinv_full_rank(r, c):
+    W = np.random.default_rng(r * c).standard_normal((4, r, c))
+    U, k, sig, st = _pinv(W)
+    assert st == 0
+    Uo, ko, so = O.pinv_truncated(W)
+    assert k == ko == min(r, c)
+    assert rel_fro(sig, so[:min(r, c)]) < 1e-13
+    assert rel_fro(host(U), Uo) < 1e-13 * _kappa_k(so, ko) * 10
+
+
+def test_pinv_gauss256_intersection():
+    # the FP64 workload's 40 x 40 intersection of exact rank 10
+    A = synth.make("gauss256_rank10_fp64")
+    out = O.qmcur(A, 40, 40, sampler=O.SAMPLER_UNIFORM, seed=0)
+    U, k, sig, st = _pinv(out["W"], rcond=1e-10)
+    assert st == 0 and k == out["rank"] == 10
+    assert rel_fro(host(U), out["U"]) < 1e-12
+
+
+def test_pinv_rank_cap_noisy():
+    W, _ = synth.lowrank_gaussian(60, 50, 8, seed=21, noise_rel=1e-3, dtype=np.float64)
+    U, k, sig, st = _pinv(W, rcond=1e-10, rank_cap=8)
+    assert st == 0 and k == 8
+    Uo, ko, so = O.pinv_truncated(W, 1e-10, 8)
+    assert rel_fro(sig, so) < 1e-13
+    assert rel_fro(host(U), Uo) < 1e-13 * _kappa_k(so, 8) ** 2 * (so[0] / (so[7] - so[8]))
+
+
+def test_pinv_zero_and_f32_output():
+    W = np.zeros((4, 5, 7))
+    U, k, sig, st = _pinv(W)
+    assert st == 0 and k == 0 and np.all(host(U) == 0)
+    W = np.random.default_rng(3).standard_normal((4, 9, 6))
+    U, k, _, st = _pinv(W, Udtype=torch.float32)
+    assert st == 0 and rel_fro(host(U), O.pinv_truncated(W)[0]) < 1e-6
+
+
+# ----------------------------------------------------------- reconstruction -
+@pytest.mark.parametrize("m,n,c,r", [(200, 300, 40, 30), (129, 65, 7, 9), (1, 1, 1, 1)])
+def test_reconstruct_fp64_and_fp32(m, n, c, r):
+    rng = np.random.default_rng(m + n)
+    C = rng.standard_normal((4, m, c))
+    U = rng.standard_normal((4, c, r))
+    R = rng.standard_normal((4, r, n))
+    Zo = O.reconstruct(C, U, R)
+    Z = torch.empty(4, m, n, dtype=torch.float64, device="cuda")
+    ws = Q.workspace(m, n, c, r, Q.PREC_FP64)
+    st = Q.status_tensor()
+    Q.reconstruct(dev(C), dev(U), dev(R), Q.PREC_FP64, Z, ws, st)
+    assert run_status(st) == 0
+    assert rel_fro(host(Z), Zo) < 1e-12
+    C32, U32_, R32 = (x.astype(np.float32) for x in (C, U, R))
+    Zo32 = O.reconstruct(C32.astype(np.float64), U32_.astype(np.float64), R32.astype(np.float64))
+    Z32 = torch.empty(4, m, n, dtype=torch.float32, device="cuda")
+    ws = Q.workspace(m, n, c, r, Q.PREC_FP32)
+    Q.reconstruct(dev(C32), dev(U32_), dev(R32), Q.PREC_FP32, Z32, ws, st)
+    assert run_status(st) == 0
+    assert rel_fro(host(Z32), Zo32) < 1e-5
+
+
+def test_residual_fused_and_standalone():
+    m, n, c, r = 333, 515, 24, 20
+    A, _ = synth.lowrank_gaussian(m, n, 6, seed=5, noise_rel=1e-2)
+    out = O.qmcur(A.astype(np.float64), c, r, sampler=O.SAMPLER_UNIFORM, seed=4, rank_cap=6)
+    U32_ = out["U"].astype(np.float32).astype(np.float64)
+    Zo = O.reconstruct(out["C"], U32_, out["R"])
+    mask = synth.bernoulli_mask(m, n, seed=6)
+    for msk in (None, mask):
+        rel_o, num_o, den_o = O.residual(A.astype(np.float64), Zo, msk)
+        out3 = torch.empty(3, dtype=torch.float64, device="cuda")
+        ws = Q.workspace(m, n, c, r, Q.PREC_FP32)
+        st = Q.status_tensor()
+        mk = None if msk is None else dev(msk)
+        Q.residual(dev(A), out3, dev(out["C"].astype(np.float32)), dev(U32_.astype(np.float32)),
+                   dev(out["R"].astype(np.float32)), Q.PREC_FP32, mk, None, ws, st)
+        assert run_status(st) == 0
+        o = host(out3)
+        assert abs(o[0] - rel_o) < 1e-5 and abs(o[2] - den_o) < 24 * U32 * den_o
+        Q.residual(dev(A), out3, mask=mk, Z=dev(Zo.astype(np.float32)), ws=ws, status=st)
+        assert run_status(st) == 0
+        o2 = host(out3)
+        assert abs(o2[0] - rel_o) < 1e-5 and abs(o2[2] - den_o) < 1e-12 * den_o
+
+
+# ---------------------------------------------------------------- whole path -
+def test_decompose_gauss256_fp64():
+    w = synth.WORKLOADS["gauss256_rank10_fp64"]
+    A = synth.make("gauss256_rank10_fp64")
+    D = Q.Decomposition(256, 256, 40, 40, Q.PREC_FP64, dtype=torch.float64)
+    Q.decompose(dev(A), D, sampler=Q.SAMPLER_UNIFORM, seed=0, rcond=w["rcond"])
+    assert run_status(D.status) == 0
+    out = O.qmcur(A, 40, 40, sampler=O.SAMPLER_UNIFORM, seed=0, rcond=w["rcond"])
+    assert np.array_equal(host(D.J), out["J"]) and np.array_equal(host(D.I), out["I"])
+    assert int(host(D.rank)[0]) == 10
+    assert rel_fro(host(D.U), out["U"]) < 1e-12
+    o = host(D.out3)
+    assert o[0] < 1e-12 and out["rel"] < 1e-12
