@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""QMCUR decompositions/s on GB300 (one JSON line on stdout, rank 0).
+
+A step is one whole QMCUR decomposition (probabilities, index draws and
+gathers, the core pseudo-inverse, the two reconstruction GEMMs with the fused
+relative residual) of a 2048 x 2048 quaternion matrix of rank 50 plus Gaussian
+noise (sigma = 1e-3 ||A||_F / 2048), norm sampling, c = r = 200, rank cap 50,
+inputs resident in HBM.  Between timed steps L2 is flushed (a 256 MiB write,
+outside the timed windows).  With N GPUs every rank decomposes its own matrix
+(replicas only: the path has no data-path exchange), and value = N K / (max
+over ranks of the summed step times).
+
+``--impl reference`` times the FP64 CPU oracle on the same workload on the
+host cores (the reference arm; no GPU work).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = ("QMCUR decompositions/sec and quaternion GEMM TFLOP/s vs plain FP32 at "
+          "≤1e-5 rel err")
+WORKLOAD = "gauss2048_rank50_noisy"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32x3", "bf16x3", "bf16x6"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_config():
+    from paper_2402_19147_gb300 import synth
+    w = dict(synth.WORKLOADS[WORKLOAD])
+    return w
+
+
+# --------------------------------------------------------------- CPU oracle -
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return int(max(i.get("num_threads", 1) for i in info))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def oracle_rate(A, w, seconds):
+    """Whole oracle decompositions on the host cores, bounded by `seconds`."""
+    from oracle import qmcur as O
+    sampler = O.SAMPLER_NORM if w["sampler"] == "norm" else O.SAMPLER_UNIFORM
+    A64 = A.astype(np.float64)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        O.qmcur(A64, w["c"], w["r"], sampler=sampler, seed=done, rcond=w["rcond"],
+                rank_cap=w["rank_cap"])
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or done >= 50:
+            break
+    return done / el, done, el
+
+
+# -------------------------------------------------------------------- clocks -
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- reference -
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2402_19147_gb300 import synth
+    w = workload_config()
+    A = synth.make(WORKLOAD)
+    rate, done, el = oracle_rate(A, w, args.cpu_seconds)
+    cores = cpu_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "decompositions/s",
+        "n_gpus": args.gpus, "steps": done, "warmup": 0, "ms_per_step": 1e3 * el / done,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "m": w["m"], "n": w["n"],
+                                        "c": w["c"], "r": w["r"], "rank_cap": w["rank_cap"],
+                                        "sampler": w["sampler"]},
+        "cpu_baseline": {"value": rate, "unit": "decompositions/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": "%d whole FP64 oracle decompositions (%.1f s)" % (done, el)},
+        "e2e": {"value": rate, "unit": "decompositions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- ours -
+def stage_work(w, prec, sweeps):
+    """Algorithmic work per decomposition of each stage (bytes or flops)."""
+    m, n, c, r = w["m"], w["n"], w["c"], w["r"]
+    es = 4
+    nr, nc = max(r, c), min(r, c)
+    N = nc + (nc % 2)
+    pairs = (N // 2) * (N - 1)
+    # per pair: alpha, beta (8 flops per entry each), gamma (32), then the
+    # rotation of both columns of G and V (q*w 32 flops, two combinations 16).
+    jac = sweeps * pairs * (nr * 48 + (nr + nc) * 48)
+    return {
+        "probs": ("hbm", 4 * m * n * es + 8 * (m + n), "GB/s"),
+        "sample": ("hbm", 4 * es * 2 * (m * c + r * n) + 4 * r * c * (es + 8), "GB/s"),
+        "pinv": ("alu", jac, "TFLOP/s"),
+        "gemm": ("alu" if prec == "fp32" else "tensor", 32.0 * (c * r * n + m * c * n),
+                 "TFLOP/s"),
+    }
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def alu_peak_tflops(kind):
+    # 152 SMs at the 2070 MHz maximum clock: FP32 128 FMA lanes per SM;
+    # FP64 at the nominal 1.25 TFLOP/s of the part.
+    if kind == "fp64":
+        return 1.25
+    return 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def run_ours(args):
+    import torch
+    from paper_2402_19147_gb300 import qmcur as Q
+    from paper_2402_19147_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = workload_config()
+    m, n, c, r = w["m"], w["n"], w["c"], w["r"]
+    prec = Q.PREC_NAMES[args.prec]
+    sampler = Q.SAMPLER_NORM if w["sampler"] == "norm" else Q.SAMPLER_UNIFORM
+    A_np = synth.make(WORKLOAD)
+    A = torch.from_numpy(A_np).to(dev)
+    D = Q.Decomposition(m, n, c, r, prec, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stages = ["probs", "sample", "pinv", "gemm"]
+
+    def step(seed, ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        Q.probs(A, sampler, D.col_p, D.row_p, None, D.ws, D.status, stream)
+        mark(1)
+        Q.sample(A, sampler, D.col_p, D.row_p, c, r, seed, rank, D.J, D.I, D.C, D.R, D.W,
+                 ws=D.ws, status=D.status, stream=stream)
+        mark(2)
+        Q.pinv_core(D.W, D.U, w["rcond"], w["rank_cap"], 0, D.rank, D.sigma, D.ws, D.status,
+                    stream)
+        mark(3)
+        Q.residual(A, D.out3, D.C, D.U, D.R, prec, None, None, D.ws, D.status, stream)
+        mark(4)
+
+    for s in range(args.warmup):
+        step(1000 + s)
+    torch.cuda.synchronize()
+    Q.check_status(D.status, "warm-up")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    clocks = Clocks(torch.cuda.current_device())
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for s in range(args.steps):
+        flush.fill_(s & 0xff)
+        step(s, evs[s])
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    Q.check_status(D.status, "timed steps")
+    stage_ms = {k: 0.0 for k in stages}
+    total_ms = 0.0
+    for e in evs:
+        for i, k in enumerate(stages):
+            stage_ms[k] += e[i].elapsed_time(e[i + 1])
+        total_ms += e[0].elapsed_time(e[4])
+    sweeps = int(D.rank[1].item())
+    rel = float(D.out3[0].item())
+    t_max = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / (t_max / 1e3)
+
+    # end to end through the C ABI with host buffers (pinned), one copy each way
+    A_host = torch.from_numpy(A_np).pin_memory()
+    outs = [torch.empty_like(x, device="cpu").pin_memory() for x in (D.J, D.I, D.U, D.out3)]
+    h2d = A_host.numel() * A_host.element_size()
+    d2h = sum(o.numel() * o.element_size() for o in outs)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for s in range(args.steps):
+        flush.fill_(s & 0xff)
+        e0.record(stream)
+        A.copy_(A_host, non_blocking=True)
+        Q.decompose(A, D, sampler=sampler, seed=s, stream_id=rank, rcond=w["rcond"],
+                    rank_cap=w["rank_cap"], stream=stream)
+        for o, x in zip(outs, (D.J, D.I, D.U, D.out3)):
+            o.copy_(x, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    Q.check_status(D.status, "e2e steps")
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    work = stage_work(w, args.prec, sweeps)
+    dom = max(stages, key=lambda k: stage_ms[k])
+    bound, amount, unit = work[dom]
+    per_launch_s = stage_ms[dom] / args.steps / 1e3
+    pk, pk_kind = peaks()
+    if unit == "GB/s":
+        achieved = amount / per_launch_s / 1e9
+        peak = pk["hbm_gbs"]
+    else:
+        achieved = amount / per_launch_s / 1e12
+        if dom == "pinv":
+            peak = alu_peak_tflops("fp64")
+            pk_kind = "nominal FP64 1.25 TFLOP/s"
+        elif bound == "alu":
+            peak = alu_peak_tflops("fp32")
+            pk_kind = "FP32 CUDA-core 152 SMs x 128 lanes x 2 x 2.07 GHz"
+        else:
+            peak = pk["bf16_tflops"]
+    gemm_tflops = work["gemm"][1] / (stage_ms["gemm"] / args.steps / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "decompositions/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": m, "n": n, "c": c, "r": r,
+                   "rank_cap": w["rank_cap"], "sampler": w["sampler"], "gemm_prec": args.prec,
+                   "pinv": "fp64-jacobi", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "stage_ms": {k: v / args.steps for k, v in stage_ms.items()},
+        "gemm_tflops": gemm_tflops, "rel_residual": rel, "jacobi_sweeps": sweeps,
+        "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
+                     "unit": unit, "frac": achieved / peak, "traffic": None,
+                     "peak_source": pk_kind},
+        "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "decompositions/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 13 * args.steps,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        rate, done, el = oracle_rate(A_np, w, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "decompositions/s",
+                                "cores": cpu_threads(), "kind": "oracle",
+                                "sample": "%d whole FP64 oracle decompositions (%.1f s)"
+                                          % (done, el)}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

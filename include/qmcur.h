@@ -139,7 +139,8 @@ qmcur_status qmcur_sample(const qmcur_qmat* A, int32_t sampler, const double* co
  * are kept, at most rank_cap of them when rank_cap > 0.
  *   W        r x c, F64 (F32 is widened).
  *   U        c x r output, F64 or F32.
- *   rank_out device int32 scalar (number of kept singular values) or NULL.
+ *   rank_out device int32[2] or NULL: {number of kept singular values,
+ *            Jacobi sweeps executed}.
  *   sigma_out device double[min(r,c)] quaternion singular values, descending,
  *            or NULL.
  *   max_sweeps <= 0 selects 40.  The QSVD is computed in FP64 by one-sided
@@ -198,7 +199,7 @@ typedef struct {
  * on the stream: qmcur_probs, qmcur_sample, qmcur_pinv_core, then
  * qmcur_residual with the reconstruction fused (Z never written).
  *   Outputs (device, caller-owned): J[c], I[r], C (m x c), R (r x n),
- *   W (r x c, F64), U (c x r, F64), rank_out, sigma_out[min(r,c)] (may be
+ *   W (r x c, F64), U (c x r, F64), rank_out[2], sigma_out[min(r,c)] (may be
  *   NULL), out3[3] as in qmcur_residual.  col_p[n], row_p[m] (device) receive
  *   the probabilities.
  */

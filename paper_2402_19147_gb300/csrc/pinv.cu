@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kPinvThreads) k_pinv_jacobi(PinvArgs a) {
 __global__ void __launch_bounds__(1024)
 k_pinv_select(const double* G, int64_t nr, int64_t nc, double rcond, int rank_cap,
               double* sig, int* order_pos, int* kidx, double* kw, int* k_out, int32_t* rank_out,
-              double* sigma_out, int32_t* status) {
+              double* sigma_out, const int* sweeps, int32_t* status) {
   __shared__ double smax_sh;
   __shared__ int nonfinite_sh;
   __shared__ int keep_sh;
@@ -271,7 +271,7 @@ k_pinv_select(const double* G, int64_t nr, int64_t nc, double rcond, int rank_ca
   }
   if (threadIdx.x == 0) {
     *k_out = k;
-    if (rank_out != nullptr) *rank_out = k;
+    if (rank_out != nullptr) { rank_out[0] = k; rank_out[1] = *sweeps; }
   }
 }
 
@@ -379,7 +379,7 @@ qmcur_status launch_pinv(const qmcur_qmat* W, double rcond, int32_t rank_cap, in
                                               dim3(kPinvThreads), args, 0, st);
   if (e != cudaSuccess) return QMCUR_ERR_CUDA;
   k_pinv_select<<<1, 1024, 0, st>>>(w.G, a.nr, a.nc, rcond, rank_cap, w.sig, w.pos, w.kidx, w.kw,
-                                     w.k, rank_out, sigma_out, dev_status);
+                                     w.k, rank_out, sigma_out, w.sweeps, dev_status);
   {
     const double* X = a.transposed ? w.G : w.V;
     const int64_t ldx = a.transposed ? a.nr : a.nc;

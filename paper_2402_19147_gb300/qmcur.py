@@ -184,7 +184,7 @@ class Decomposition:
         self.R = torch.empty(4, r, n, dtype=dtype, **f)
         self.W = torch.empty(4, r, c, dtype=torch.float64, **f)
         self.U = torch.empty(4, c, r, dtype=torch.float64, **f)
-        self.rank = torch.zeros(1, dtype=torch.int32, **f)
+        self.rank = torch.zeros(2, dtype=torch.int32, **f)   # {rank, sweeps}
         self.sigma = torch.empty(min(r, c), dtype=torch.float64, **f)
         self.out3 = torch.empty(3, dtype=torch.float64, **f)
         self.status = torch.zeros(1, dtype=torch.int32, **f)

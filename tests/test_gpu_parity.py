@@ -129,7 +129,7 @@ def test_sample_status_codes():
 def _pinv(W, rcond=1e-10, rank_cap=0, Udtype=torch.float64):
     r, c = W.shape[1], W.shape[2]
     U = torch.empty(4, c, r, dtype=Udtype, device="cuda")
-    rank = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rank = torch.zeros(2, dtype=torch.int32, device="cuda")
     sig = torch.empty(min(r, c), dtype=torch.float64, device="cuda")
     ws = Q.workspace(r, c, c, r, Q.PREC_FP64)
     st = Q.status_tensor()
