@@ -109,6 +109,27 @@ qmcur_status qmcur_probs(const qmcur_qmat* A, int32_t sampler, double* col_p, do
                          cudaStream_t stream);
 
 /*
+ * qmcur_probs_noalloc - the same computation and outputs as qmcur_probs, for
+ * callers that cannot allocate device memory or pass a workspace (a host
+ * framework that owns every device allocation, or a latency-bound loop where
+ * cudaMalloc, which may synchronise the device, is not allowed).  The paper
+ * has no counterpart: this is a memory-management variant of the call above.
+ *   Allocates nothing.  Its scratch is a static 8 MiB device array inside the
+ *   library, held on every GPU that loads the library until the process
+ *   exits.  Inputs needing more (ceil(m/32) n + ceil(n/1024) m + n + m + 4
+ *   doubles, padded to 256 bytes per part, above 8 MiB; about m n <= 3e7)
+ *   are rejected with QMCUR_ERR_UNSUPPORTED before anything is enqueued.
+ *   The first call on a device looks up the array's device address (a CUDA
+ *   runtime query, no allocation); make that first call before any stream
+ *   capture on that device.  All calls on a device share the array and it
+ *   keeps the last call's contents (every entry read is rewritten first, so
+ *   results do not depend on it); calls that overlap on the GPU race on it.
+ */
+qmcur_status qmcur_probs_noalloc(const qmcur_qmat* A, int32_t sampler, double* col_p,
+                                 double* row_p, double* fro2, int32_t* dev_status,
+                                 cudaStream_t stream);
+
+/*
  * qmcur_sample - Algorithm 1 steps 1-2: draw J subset [n] (|J| = c) from col_p
  * and I subset [m] (|I| = r) from row_p, then gather C = A(:,J) (m x c),
  * R = A(I,:) (r x n) and the intersection W = A(I,J) (r x c).

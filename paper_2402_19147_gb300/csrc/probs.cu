@@ -7,6 +7,8 @@
 // in FP32 over short runs (16 terms for a row piece, 32 for a column piece)
 // and carried in FP64 from there on.  Every reduction has a fixed order, so
 // the result is bit-reproducible and no atomics touch values.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace qmcur {
@@ -203,4 +205,53 @@ qmcur_status launch_probs(const qmcur_qmat* A, int32_t sampler, double* col_p, d
   return cuda_ok(cudaGetLastError());
 }
 
+// ------------------------------------------------------------------------
+// Allocation-free variant of qmcur_probs.
+//
+// For callers that cannot call cudaMalloc or hand the library a workspace:
+// code inside a host framework whose allocator owns all device memory, or a
+// latency-bound loop where an allocation (which can synchronise the device)
+// is not acceptable, and whose interface has no place to thread a scratch
+// buffer through.  Its scratch is this file-scope array: every GPU that loads
+// the library holds it until the process exits, all calls on a device share
+// it and it keeps the last call's contents.  Every scratch entry the kernels
+// read is written earlier in the same call, so nothing needs clearing; calls
+// that overlap on the GPU (e.g. on two streams at once) race on it.
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;   // 8 MiB per device
+static __device__ __align__(256) unsigned char g_probs_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_scratch_mu;
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_probs_scratch on the current device, looked up once per
+// device (in host code the array's name is only a host-side stand-in).
+qmcur_status scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return QMCUR_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (g_scratch_addr[dev] == nullptr) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_probs_scratch) != cudaSuccess || p == nullptr) return QMCUR_ERR_CUDA;
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return QMCUR_OK;
+}
+}  // namespace
+
 }  // namespace qmcur
+
+extern "C" qmcur_status qmcur_probs_noalloc(const qmcur_qmat* A, int32_t sampler, double* col_p,
+                                            double* row_p, double* fro2, int32_t* dev_status,
+                                            cudaStream_t stream) {
+  using namespace qmcur;
+  if (!valid_qmat(A)) return QMCUR_ERR_INVALID_ARG;
+  if (probs_ws_bytes(A->rows, A->cols) > kNoAllocScratchBytes) return QMCUR_ERR_UNSUPPORTED;
+  void* scratch = nullptr;
+  const qmcur_status s = scratch_address(&scratch);
+  if (s != QMCUR_OK) return s;
+  return launch_probs(A, sampler, col_p, row_p, fro2, scratch, kNoAllocScratchBytes, dev_status,
+                      stream);
+}

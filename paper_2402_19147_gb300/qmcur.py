@@ -57,6 +57,7 @@ SIGNATURES = {
     "qmcur_status_str": (ctypes.c_char_p, [_I32]),
     "qmcur_workspace_size": (_SZ, [_I64, _I64, _I64, _I64, _I32]),
     "qmcur_probs": (_I32, [_QP, _I32, _P, _P, _P, _P, _SZ, _P, _P]),
+    "qmcur_probs_noalloc": (_I32, [_QP, _I32, _P, _P, _P, _P, _P]),
     "qmcur_sample": (_I32, [_QP, _I32, _P, _P, _I64, _I64, _U64, _U32, _I32, _P, _P,
                             _QP, _QP, _QP, _P, _SZ, _P, _P]),
     "qmcur_pinv_core": (_I32, [_QP, _D, _I32, _I32, _QP, _P, _P, _P, _SZ, _P, _P]),
@@ -137,6 +138,13 @@ def probs(A, sampler, col_p, row_p, fro2=None, ws=None, status=None, stream=None
     _check(lib().qmcur_probs(_ref(qmat(A)), sampler, _ptr(col_p), _ptr(row_p), _ptr(fro2),
                              _ptr(ws), 0 if ws is None else ws.numel(), _ptr(status),
                              _stream(stream)), "qmcur_probs")
+
+
+def probs_noalloc(A, sampler, col_p, row_p, fro2=None, status=None, stream=None):
+    """qmcur_probs without a workspace: scratch is the library's static array."""
+    _check(lib().qmcur_probs_noalloc(_ref(qmat(A)), sampler, _ptr(col_p), _ptr(row_p),
+                                     _ptr(fro2), _ptr(status), _stream(stream)),
+           "qmcur_probs_noalloc")
 
 
 def sample(A, sampler, col_p, row_p, c, r, seed, stream_id, J, I, C=None, R=None, W=None,
