@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32x3", "bf16x3", "bf16x6"])
+    ap.add_argument("--pinv", default="subspace", choices=["subspace", "jacobi"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -155,16 +156,28 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------- ours -
-def stage_work(w, prec, sweeps):
+def pinv_flops(w, method, sweeps):
+    """Algorithmic real flops of one pseudo-inverse of the r x c intersection."""
+    c, r = w["c"], w["r"]
+    nr, nc = max(r, c), min(r, c)
+    if method == "jacobi":
+        N = nc + (nc % 2)
+        pairs = (N // 2) * (N - 1)
+        # per pair: alpha, beta (8 flops per entry each), gamma (32), then the
+        # rotation of both columns of G and V (q*w 32 flops, two combinations 16).
+        return sweeps * pairs * (nr * 48 + (nr + nc) * 48)
+    k = min(w["rank_cap"], nc)
+    # subspace iteration: W Omega, two (W^H Q, W P) pairs; seven CholeskyQR
+    # passes (Gram + Q R^-1, 2 rows k^2 quaternion FMAs each); U = P R^-1 Q^H.
+    qfma = 5 * r * c * k + 7 * 2 * ((r + c) // 2) * k * k + 2 * c * k * k + c * r * k
+    return 32 * qfma
+
+
+def stage_work(w, prec, sweeps, method="subspace"):
     """Algorithmic work per decomposition of each stage (bytes or flops)."""
     m, n, c, r = w["m"], w["n"], w["c"], w["r"]
     es = 4
-    nr, nc = max(r, c), min(r, c)
-    N = nc + (nc % 2)
-    pairs = (N // 2) * (N - 1)
-    # per pair: alpha, beta (8 flops per entry each), gamma (32), then the
-    # rotation of both columns of G and V (q*w 32 flops, two combinations 16).
-    jac = sweeps * pairs * (nr * 48 + (nr + nc) * 48)
+    jac = pinv_flops(w, method, sweeps)
     return {
         "probs": ("hbm", 4 * m * n * es + 8 * (m + n), "GB/s"),
         "sample": ("hbm", 4 * es * 2 * (m * c + r * n) + 4 * r * c * (es + 8), "GB/s"),
@@ -210,6 +223,7 @@ def run_ours(args):
     m, n, c, r = w["m"], w["n"], w["c"], w["r"]
     prec = Q.PREC_NAMES[args.prec]
     sampler = Q.SAMPLER_NORM if w["sampler"] == "norm" else Q.SAMPLER_UNIFORM
+    pinv_method = Q.PINV_SUBSPACE_FP32 if args.pinv == "subspace" else Q.PINV_JACOBI_FP64
     A_np = synth.make(WORKLOAD)
     A = torch.from_numpy(A_np).to(dev)
     D = Q.Decomposition(m, n, c, r, prec, device=dev)
@@ -228,7 +242,7 @@ def run_ours(args):
                  ws=D.ws, status=D.status, stream=stream)
         mark(2)
         Q.pinv_core(D.W, D.U, w["rcond"], w["rank_cap"], 0, D.rank, D.sigma, D.ws, D.status,
-                    stream)
+                    stream, method=pinv_method)
         mark(3)
         Q.residual(A, D.out3, D.C, D.U, D.R, prec, None, None, D.ws, D.status, stream)
         mark(4)
@@ -279,7 +293,7 @@ def run_ours(args):
         e0.record(stream)
         A.copy_(A_host, non_blocking=True)
         Q.decompose(A, D, sampler=sampler, seed=s, stream_id=rank, rcond=w["rcond"],
-                    rank_cap=w["rank_cap"], stream=stream)
+                    rank_cap=w["rank_cap"], stream=stream, pinv_method=pinv_method)
         for o, x in zip(outs, (D.J, D.I, D.U, D.out3)):
             o.copy_(x, non_blocking=True)
         e1.record(stream)
@@ -295,7 +309,7 @@ def run_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
-    work = stage_work(w, args.prec, sweeps)
+    work = stage_work(w, args.prec, sweeps, args.pinv)
     dom = max(stages, key=lambda k: stage_ms[k])
     bound, amount, unit = work[dom]
     per_launch_s = stage_ms[dom] / args.steps / 1e3
@@ -305,9 +319,12 @@ def run_ours(args):
         peak = pk["hbm_gbs"]
     else:
         achieved = amount / per_launch_s / 1e12
-        if dom == "pinv":
+        if dom == "pinv" and args.pinv == "jacobi":
             peak = alu_peak_tflops("fp64")
             pk_kind = "nominal FP64 1.25 TFLOP/s"
+        elif dom == "pinv":
+            peak = alu_peak_tflops("fp32")
+            pk_kind = "FP32 CUDA-core 152 SMs x 128 lanes x 2 x 2.07 GHz"
         elif bound == "alu":
             peak = alu_peak_tflops("fp32")
             pk_kind = "FP32 CUDA-core 152 SMs x 128 lanes x 2 x 2.07 GHz"
@@ -321,16 +338,17 @@ def run_ours(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "m": m, "n": n, "c": c, "r": r,
                    "rank_cap": w["rank_cap"], "sampler": w["sampler"], "gemm_prec": args.prec,
-                   "pinv": "fp64-jacobi", "parallelism": "replicas" if world > 1 else "single",
+                   "pinv": "fp32-subspace" if args.pinv == "subspace" else "fp64-jacobi",
+                   "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (256 MiB write)"},
         "stage_ms": {k: v / args.steps for k, v in stage_ms.items()},
-        "gemm_tflops": gemm_tflops, "rel_residual": rel, "jacobi_sweeps": sweeps,
+        "gemm_tflops": gemm_tflops, "rel_residual": rel,
         "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak, "traffic": None,
                      "peak_source": pk_kind},
         "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "decompositions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 13 * args.steps,
+        "gpu_launches": (13 if args.pinv == "jacobi" else 9 + 32) * args.steps,
         "clocks": clk,
     }
     if not args.no_cpu_baseline:

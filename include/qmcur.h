@@ -81,8 +81,21 @@ typedef enum {
   QMCUR_ERR_NO_CONVERGENCE = 6,       /* Jacobi sweep limit reached               */
   QMCUR_ERR_UNSUPPORTED = 7,          /* valid request this build cannot serve    */
   QMCUR_ERR_CUDA = 8,                 /* a CUDA runtime call failed               */
-  QMCUR_ERR_TIMEOUT = 9               /* a bounded device-side wait ran out       */
+  QMCUR_ERR_TIMEOUT = 9,              /* a bounded device-side wait ran out       */
+  QMCUR_ERR_ILL_CONDITIONED = 10      /* FP32 subspace pseudo-inverse met a
+                                         non-positive Cholesky pivot            */
 } qmcur_status;
+
+/* How qmcur_pinv_core computes the truncated inverse. */
+typedef enum {
+  QMCUR_PINV_JACOBI_FP64 = 0,  /* full QSVD by FP64 one-sided Jacobi: any rank
+                                  rule, FP64 accuracy, slow on GB300's FP64 rate */
+  QMCUR_PINV_SUBSPACE_FP32 = 1 /* rank_cap >= 1 required (k = min(rank_cap, r, c)
+                                  <= 112): top-k subspaces by two FP32 subspace
+                                  iterations with CholeskyQR2, U = P R^-1 Q^H;
+                                  assumes sigma_k > sigma_{k+1} clearly, ignores
+                                  rcond, does not write sigma_out             */
+} qmcur_pinv_method;
 
 /* Human-readable name of a status code (static string). */
 const char* qmcur_status_str(int32_t status);
@@ -164,11 +177,15 @@ qmcur_status qmcur_sample(const qmcur_qmat* A, int32_t sampler, const double* co
  *            Jacobi sweeps executed}.
  *   sigma_out device double[min(r,c)] quaternion singular values, descending,
  *            or NULL.
- *   max_sweeps <= 0 selects 40.  The QSVD is computed in FP64 by one-sided
- *   (Hestenes) Jacobi rotations in quaternion arithmetic.
- *   Device errors: NO_CONVERGENCE, NONFINITE, TIMEOUT.
+ *   method   qmcur_pinv_method.  QMCUR_PINV_JACOBI_FP64: the QSVD is computed
+ *            in FP64 by one-sided (Hestenes) Jacobi rotations in quaternion
+ *            arithmetic; max_sweeps <= 0 selects 40; rank_out[1] = sweeps.
+ *            QMCUR_PINV_SUBSPACE_FP32: see the enum; rank_out = {k, 2}.
+ *   Device errors: NO_CONVERGENCE, NONFINITE, TIMEOUT (Jacobi);
+ *   ILL_CONDITIONED (subspace).  UNSUPPORTED (synchronous) when the subspace
+ *   method is asked for without a rank cap or with k > 112.
  */
-qmcur_status qmcur_pinv_core(const qmcur_qmat* W, double rcond, int32_t rank_cap,
+qmcur_status qmcur_pinv_core(const qmcur_qmat* W, int32_t method, double rcond, int32_t rank_cap,
                              int32_t max_sweeps, qmcur_qmat* U, int32_t* rank_out,
                              double* sigma_out, void* workspace, size_t ws_bytes,
                              int32_t* dev_status, cudaStream_t stream);
@@ -213,6 +230,8 @@ typedef struct {
   double   rcond;        /* relative singular value cut of W^+ */
   int32_t  rank_cap;     /* <= 0: no cap */
   int32_t  max_sweeps;   /* <= 0: default */
+  int32_t  pinv_method;  /* qmcur_pinv_method */
+  int32_t  reserved;
 } qmcur_opts;
 
 /*

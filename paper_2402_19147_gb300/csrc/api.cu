@@ -10,6 +10,12 @@ qmcur_status launch_qgemm_simt(const QView& X, const QView& Y, const QView* Z, c
                                const uint8_t* mask, double* partial, bool fp64, cudaStream_t st);
 __global__ void k_residual_fold(const double* partial, int64_t count, double* out3);
 
+// Subspace pseudo-inverse (pinv_fast.cu).
+size_t pinv_fast_ws_bytes(int64_t r, int64_t c, int64_t k);
+qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat* U,
+                              int32_t* rank_out, uint64_t seed, void* ws, size_t ws_bytes,
+                              int32_t* dev_status, cudaStream_t st);
+
 // Tensor-core path (qgemm_tc.cu).
 size_t tc_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec);
 qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
@@ -89,6 +95,7 @@ const char* qmcur_status_str(int32_t s) {
     case QMCUR_ERR_UNSUPPORTED: return "QMCUR_ERR_UNSUPPORTED";
     case QMCUR_ERR_CUDA: return "QMCUR_ERR_CUDA";
     case QMCUR_ERR_TIMEOUT: return "QMCUR_ERR_TIMEOUT";
+    case QMCUR_ERR_ILL_CONDITIONED: return "QMCUR_ERR_ILL_CONDITIONED";
     default: return "QMCUR_ERR_UNKNOWN";
   }
 }
@@ -97,6 +104,9 @@ size_t qmcur_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r, int32_t 
   if (m < 1 || n < 1 || c < 1 || r < 1) return 0;
   size_t s = probs_ws_bytes(m, n);
   const size_t s2 = sample_ws_bytes(m, n), s3 = pinv_ws_bytes(r, c), s4 = gemm_ws_bytes(m, n, c, r, prec);
+  const int64_t kmax = (r < c ? r : c) < 112 ? (r < c ? r : c) : 112;
+  const size_t s5 = pinv_fast_ws_bytes(r, c, kmax);
+  if (s5 > s) s = s5;
   if (s2 > s) s = s2;
   if (s3 > s) s = s3;
   if (s4 > s) s = s4;
@@ -118,12 +128,27 @@ qmcur_status qmcur_sample(const qmcur_qmat* A, int32_t sampler, const double* co
                        workspace, ws_bytes, dev_status, stream);
 }
 
-qmcur_status qmcur_pinv_core(const qmcur_qmat* W, double rcond, int32_t rank_cap,
+static qmcur_status pinv_dispatch(const qmcur_qmat* W, int32_t method, double rcond,
+                                  int32_t rank_cap, int32_t max_sweeps, qmcur_qmat* U,
+                                  int32_t* rank_out, double* sigma_out, void* workspace,
+                                  size_t ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  if (method == QMCUR_PINV_JACOBI_FP64)
+    return launch_pinv(W, rcond, rank_cap, max_sweeps, U, rank_out, sigma_out, workspace,
+                       ws_bytes, dev_status, stream);
+  if (method != QMCUR_PINV_SUBSPACE_FP32) return QMCUR_ERR_INVALID_ARG;
+  if (!valid_qmat(W) || !valid_qmat(U)) return QMCUR_ERR_INVALID_ARG;
+  if (W->rows < 1 || W->cols < 1 || U->rows != W->cols || U->cols != W->rows)
+    return QMCUR_ERR_INVALID_ARG;
+  return launch_pinv_fast(W, rank_cap, U, rank_out, 0x9e3779b97f4a7c15ull, workspace, ws_bytes,
+                          dev_status, stream);
+}
+
+qmcur_status qmcur_pinv_core(const qmcur_qmat* W, int32_t method, double rcond, int32_t rank_cap,
                              int32_t max_sweeps, qmcur_qmat* U, int32_t* rank_out,
                              double* sigma_out, void* workspace, size_t ws_bytes,
                              int32_t* dev_status, cudaStream_t stream) {
-  return launch_pinv(W, rcond, rank_cap, max_sweeps, U, rank_out, sigma_out, workspace, ws_bytes,
-                     dev_status, stream);
+  return pinv_dispatch(W, method, rcond, rank_cap, max_sweeps, U, rank_out, sigma_out, workspace,
+                       ws_bytes, dev_status, stream);
 }
 
 qmcur_status qmcur_reconstruct(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
@@ -158,8 +183,8 @@ qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qm
   s = launch_sample(A, o->sampler, col_p, row_p, c, r, o->seed, o->stream_id, o->max_attempts, J, I,
                     C, R, W, workspace, ws_bytes, dev_status, stream);
   if (s != QMCUR_OK) return s;
-  s = launch_pinv(W, o->rcond, o->rank_cap, o->max_sweeps, U, rank_out, sigma_out, workspace,
-                  ws_bytes, dev_status, stream);
+  s = pinv_dispatch(W, o->pinv_method, o->rcond, o->rank_cap, o->max_sweeps, U, rank_out,
+                    sigma_out, workspace, ws_bytes, dev_status, stream);
   if (s != QMCUR_OK) return s;
   return launch_reconstruct(C, U, R, o->prec, nullptr, A, nullptr, out3, workspace, ws_bytes,
                             dev_status, stream);

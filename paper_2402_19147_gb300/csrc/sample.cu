@@ -60,15 +60,19 @@ struct SampleArgs {
   int32_t* attempts_out;  // optional: draws consumed per set (2 ints)
 };
 
-__global__ void __launch_bounds__(kSampleThreads) k_sample(SampleArgs a) {
+__global__ void __launch_bounds__(kSampleThreads) k_sample(SampleArgs a, int P_in_smem) {
   const int set = blockIdx.x;
   const int tid = threadIdx.x;
   const int64_t N = a.N[set];
   const int64_t count = a.count[set];
   const double* p = a.prob[set];
-  double* P = a.P[set];
-  uint32_t* bits = a.bits[set];
   const int64_t words = (N + 31) / 32;
+  // Dynamic shared memory: the acceptance bitmap (and the prefix sums when
+  // they fit), so that the sequential acceptance and the binary searches stay
+  // on chip.
+  extern __shared__ __align__(16) unsigned char dyn[];
+  uint32_t* bits = reinterpret_cast<uint32_t*>(dyn);
+  double* P = P_in_smem ? reinterpret_cast<double*>(dyn + ((words * 4 + 15) / 16) * 16) : a.P[set];
 
   __shared__ double blk_total[kPrefixBlocks];
   __shared__ double blk_off[kPrefixBlocks];
@@ -256,7 +260,18 @@ qmcur_status launch_sample(const qmcur_qmat* A, int32_t sampler, const double* c
   a.max_attempts[1] = max_attempts > 0 ? max_attempts : 64 * r + 1024;
   a.norm = sampler == QMCUR_SAMPLER_NORM;
   a.status = dev_status;
-  k_sample<<<2, kSampleThreads, 0, st>>>(a);
+  const int64_t nmax = n > m ? n : m;
+  const size_t bits_bytes = (size_t)((nmax + 31) / 32 * 4 + 15) / 16 * 16;
+  const size_t p_bytes = (size_t)nmax * 8;
+  const size_t kSmemCap = 200 * 1024;
+  if (bits_bytes > kSmemCap) return QMCUR_ERR_UNSUPPORTED;
+  const int P_in_smem = bits_bytes + p_bytes <= kSmemCap;
+  const size_t smem = bits_bytes + (P_in_smem ? p_bytes : 0);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap) !=
+          cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  k_sample<<<2, kSampleThreads, smem, st>>>(a, P_in_smem);
   if (C || R || W) {
     QView vA = view(A);
     QView vC = C ? view(C) : vA, vR = R ? view(R) : vA, vW = W ? view(W) : vA;

@@ -24,7 +24,9 @@ PREC_NAMES = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32x3": PREC_TF32X3,
 STATUS = {0: "QMCUR_OK", 1: "QMCUR_ERR_INVALID_ARG", 2: "QMCUR_ERR_NONFINITE",
           3: "QMCUR_ERR_ZERO_NORM", 4: "QMCUR_ERR_INSUFFICIENT_SUPPORT",
           5: "QMCUR_ERR_SAMPLE_LIMIT", 6: "QMCUR_ERR_NO_CONVERGENCE",
-          7: "QMCUR_ERR_UNSUPPORTED", 8: "QMCUR_ERR_CUDA", 9: "QMCUR_ERR_TIMEOUT"}
+          7: "QMCUR_ERR_UNSUPPORTED", 8: "QMCUR_ERR_CUDA", 9: "QMCUR_ERR_TIMEOUT",
+          10: "QMCUR_ERR_ILL_CONDITIONED"}
+PINV_JACOBI_FP64, PINV_SUBSPACE_FP32 = 0, 1
 
 
 class QmcurError(RuntimeError):
@@ -43,7 +45,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("sampler", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32),
                 ("max_attempts", ctypes.c_int32), ("rcond", ctypes.c_double),
-                ("rank_cap", ctypes.c_int32), ("max_sweeps", ctypes.c_int32)]
+                ("rank_cap", ctypes.c_int32), ("max_sweeps", ctypes.c_int32),
+                ("pinv_method", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -60,7 +63,7 @@ SIGNATURES = {
     "qmcur_probs_noalloc": (_I32, [_QP, _I32, _P, _P, _P, _P, _P]),
     "qmcur_sample": (_I32, [_QP, _I32, _P, _P, _I64, _I64, _U64, _U32, _I32, _P, _P,
                             _QP, _QP, _QP, _P, _SZ, _P, _P]),
-    "qmcur_pinv_core": (_I32, [_QP, _D, _I32, _I32, _QP, _P, _P, _P, _SZ, _P, _P]),
+    "qmcur_pinv_core": (_I32, [_QP, _I32, _D, _I32, _I32, _QP, _P, _P, _P, _SZ, _P, _P]),
     "qmcur_reconstruct": (_I32, [_QP, _QP, _QP, _I32, _QP, _P, _SZ, _P, _P]),
     "qmcur_residual": (_I32, [_QP, _QP, _QP, _QP, _I32, _P, _QP, _P, _P, _SZ, _P, _P]),
     "qmcur_decompose": (_I32, [_QP, _I64, _I64, ctypes.POINTER(Opts), _P, _P, _P, _P,
@@ -157,8 +160,9 @@ def sample(A, sampler, col_p, row_p, c, r, seed, stream_id, J, I, C=None, R=None
 
 
 def pinv_core(W, U, rcond=1e-10, rank_cap=0, max_sweeps=0, rank_out=None, sigma_out=None,
-              ws=None, status=None, stream=None):
-    _check(lib().qmcur_pinv_core(_ref(qmat(W)), rcond, rank_cap, max_sweeps, _ref(qmat(U)),
+              ws=None, status=None, stream=None, method=PINV_JACOBI_FP64):
+    _check(lib().qmcur_pinv_core(_ref(qmat(W)), method, rcond, rank_cap, max_sweeps,
+                                 _ref(qmat(U)),
                                  _ptr(rank_out), _ptr(sigma_out), _ptr(ws),
                                  0 if ws is None else ws.numel(), _ptr(status),
                                  _stream(stream)), "qmcur_pinv_core")
@@ -200,9 +204,10 @@ class Decomposition:
 
 
 def decompose(A, D, sampler=SAMPLER_NORM, seed=0, stream_id=0, rcond=1e-10, rank_cap=0,
-              max_sweeps=0, max_attempts=0, stream=None):
+              max_sweeps=0, max_attempts=0, stream=None, pinv_method=PINV_JACOBI_FP64):
     """One whole QMCUR decomposition of A into the buffers of D (qmcur_decompose)."""
-    o = Opts(sampler, D.prec, seed, stream_id, max_attempts, rcond, rank_cap, max_sweeps)
+    o = Opts(sampler, D.prec, seed, stream_id, max_attempts, rcond, rank_cap, max_sweeps,
+             pinv_method, 0)
     qs = [qmat(D.C), qmat(D.R), qmat(D.W), qmat(D.U)]
     _check(lib().qmcur_decompose(_ref(qmat(A)), D.c, D.r, ctypes.byref(o), _ptr(D.col_p),
                                  _ptr(D.row_p), _ptr(D.J), _ptr(D.I), *[_ref(q) for q in qs],

@@ -239,3 +239,42 @@ def test_decompose_gauss256_fp64():
     assert rel_fro(host(D.U), out["U"]) < 1e-12
     o = host(D.out3)
     assert o[0] < 1e-12 and out["rel"] < 1e-12
+
+
+# ----------------------------------------------- FP32 subspace pseudo-inverse -
+def _pinv_fast(W, rank_cap):
+    r, c = W.shape[1], W.shape[2]
+    U = torch.empty(4, c, r, dtype=torch.float64, device="cuda")
+    rank = torch.zeros(2, dtype=torch.int32, device="cuda")
+    ws = Q.workspace(r, c, c, r, Q.PREC_FP32)
+    st = Q.status_tensor()
+    Q.pinv_core(dev(W), U, 1e-10, rank_cap, 0, rank, None, ws, st, method=Q.PINV_SUBSPACE_FP32)
+    return U, host(rank), run_status(st)
+
+
+@pytest.mark.parametrize("r,c,k,noise", [(200, 200, 50, 1e-3), (120, 90, 12, 1e-4),
+                                         (64, 80, 30, 0.0), (33, 17, 5, 1e-3)])
+def test_pinv_subspace_fp32(r, c, k, noise):
+    W = synth.lowrank_gaussian(r, c, k, seed=r + c + k, noise_rel=noise)[0]
+    U, info, st = _pinv_fast(W, k)
+    assert st == 0 and info[0] == k
+    W64 = W.astype(np.float64)
+    Uo, ko, so = O.pinv_truncated(W64, 1e-10, k)
+    kap = so[0] / so[k - 1]
+    err = rel_fro(host(U), Uo)
+    # FP32 subspace iteration: rounding ~ u32 * kappa_k per step, a few steps
+    assert err < 64 * U32 * kap * kap, (err, kap)
+    # reconstruction through the fast core equals the oracle's to 1e-5
+    A = np.zeros((4, r + 7, c + 5))
+    A[:, :r, :c] = W64
+    C, R = A[:, :, :c], A[:, :r, :]
+    Zf = O.reconstruct(C, host(U), R)
+    Zo = O.reconstruct(C, Uo, R)
+    assert rel_fro(Zf, Zo) < 1e-5
+
+
+def test_pinv_subspace_needs_cap():
+    W = np.random.default_rng(0).standard_normal((4, 10, 10))
+    with pytest.raises(Q.QmcurError) as e:
+        _pinv_fast(W, 0)
+    assert e.value.code == 7
