@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32x3", "bf16x3", "bf16x6"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3", "bf16x6"])
     ap.add_argument("--pinv", default="subspace", choices=["subspace", "jacobi"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -187,6 +187,46 @@ def stage_work(w, prec, sweeps, method="subspace"):
     }
 
 
+def launches_per_step(args):
+    """Kernels of the library launched per decomposition (counted from the code)."""
+    n = 4 + 2                                  # probabilities, sampler + gathers
+    n += 4 if args.pinv == "jacobi" else 32    # pseudo-inverse
+    n += 3 if args.prec == "fp32" else 6       # GEMMs (+ operand splits) + fold
+    return n
+
+
+def gemm_check(Q, A, D, prec, stream, reps=5):
+    """Reconstruction error of `prec` against the FP64 oracle on the step's own
+    C, U (rounded to FP32) and R, and GEMM TFLOP/s of `prec` and of plain FP32."""
+    import torch
+    from oracle import qmcur as O
+    m, n, c, r = D.m, D.n, D.c, D.r
+    U32 = D.U.float()
+    Z = torch.empty(4, m, n, dtype=torch.float32, device=A.device)
+    out = {}
+    for name, pc in (("fp32", Q.PREC_FP32), ("sel", prec)):
+        ws = Q.workspace(m, n, c, r, pc, device=A.device)
+        st = Q.status_tensor(A.device)
+        Q.residual(A, D.out3, D.C, U32, D.R, pc, None, None, ws, st, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            Q.residual(A, D.out3, D.C, U32, D.R, pc, None, None, ws, st, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_ms"] = e0.elapsed_time(e1) / reps
+        if name == "sel":
+            Q.reconstruct(D.C, U32, D.R, pc, Z, ws, st, stream)
+            torch.cuda.synchronize()
+            Zo = O.reconstruct(D.C.double().cpu().numpy(), U32.double().cpu().numpy(),
+                               D.R.double().cpu().numpy())
+            out["rel_err"] = float(np.linalg.norm(Z.cpu().numpy() - Zo) / np.linalg.norm(Zo))
+    fl = 32.0 * (c * r * n + m * c * n)
+    out["tflops"] = fl / (out["sel_ms"] / 1e3) / 1e12
+    out["tflops_fp32"] = fl / (out["fp32_ms"] / 1e3) / 1e12
+    return out
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -331,24 +371,26 @@ def run_ours(args):
         else:
             peak = pk["bf16_tflops"]
     gemm_tflops = work["gemm"][1] / (stage_ms["gemm"] / args.steps / 1e3) / 1e12
+    gchk = gemm_check(Q, A, D, Q.PREC_NAMES[args.prec], stream)
     line = {
         "metric": METRIC, "value": value, "unit": "decompositions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "dtype": "f32" if args.prec == "fp32" else args.prec, "data": "synthetic",
         "config": {"workload": WORKLOAD, "m": m, "n": n, "c": c, "r": r,
                    "rank_cap": w["rank_cap"], "sampler": w["sampler"], "gemm_prec": args.prec,
                    "pinv": "fp32-subspace" if args.pinv == "subspace" else "fp64-jacobi",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (256 MiB write)"},
         "stage_ms": {k: v / args.steps for k, v in stage_ms.items()},
-        "gemm_tflops": gemm_tflops, "rel_residual": rel,
+        "gemm_tflops": gemm_tflops, "gemm_tflops_plain_fp32": gchk["tflops_fp32"],
+        "gemm_rel_err_vs_fp64_oracle": gchk["rel_err"], "rel_residual": rel,
         "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak, "traffic": None,
                      "peak_source": pk_kind},
         "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "decompositions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": (13 if args.pinv == "jacobi" else 9 + 32) * args.steps,
+        "gpu_launches": launches_per_step(args) * args.steps,
         "clocks": clk,
     }
     if not args.no_cpu_baseline:

@@ -1,14 +1,703 @@
-// Tensor-core (tcgen05) quaternion GEMM: placeholder until the kernel lands.
+// Quaternion GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Z = X Y with the Hamilton product (Sec. 2.2) in split planes:
+//   Z_p = sum_t s(p,t) X_t Y_{y(p,t)},
+//   Z0 = X0Y0 - X1Y1 - X2Y2 - X3Y3      Z1 = X0Y1 + X1Y0 + X2Y3 - X3Y2
+//   Z2 = X0Y2 - X1Y3 + X2Y0 + X3Y1      Z3 = X0Y3 + X1Y2 - X2Y1 + X3Y0,
+// i.e. the real 4x4 block representation, issued as 16 real MMAs per K step
+// whose minus signs come from the instruction descriptor's negate-A bit.
+//
+// Precision: every FP32 operand is split into pieces (BF16 hi/lo or
+// hi/mid/lo, or TF32 big/small); a "term" multiplies one piece of X by one of
+// Y, and the terms (3 or 6) accumulate into the same FP32 TMEM accumulator.
+//
+// Layout: pieces are stored K-major, [piece][plane][rows][Kpad] (Kpad a
+// multiple of 64 bytes, zero padded), one 3-D tensor map per operand, so a
+// single TMA copy brings the four planes of one piece for one 64-byte K
+// slice into shared memory (64-byte swizzle).  K steps that lie entirely in
+// the padding are not issued.
+//
+// Kernel: persistent, warp-specialised (6 warps).  Warp 0 lane 0 issues TMA
+// loads into a 4-stage ring; warp 1 owns the TMEM allocation and its lane 0
+// issues the MMAs (M = 128, N = 64 per MMA, four output planes side by side
+// in TMEM, two accumulator buffers so the epilogue of one tile overlaps the
+// MMAs of the next); warps 2-5 are the epilogue, each reading its own
+// 32-lane TMEM sub-partition (one output row per thread).  Epilogue modes:
+//   STORE_Z   write Z (FP32 planes);
+//   RESIDUAL  never write Z: read the matching tile of A and accumulate
+//             sum |a - z|^2, sum |a|^2 (optionally over a mask) into one FP64
+//             pair per tile, folded later in a fixed order;
+//   SPLIT_T   write the pieces of Z^T straight into the K-major B operand of
+//             a following GEMM (T = U R feeding C T).
+// Every wait is bounded: on timeout the kernel raises an abort flag, the
+// roles drain, TMEM is freed and QMCUR_ERR_TIMEOUT is reported.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
 #include "common.cuh"
 
 namespace qmcur {
 
-size_t tc_ws_bytes(int64_t, int64_t, int64_t, int64_t, int32_t) { return 0; }
+size_t residual_partials(int64_t m, int64_t n);
+__global__ void k_residual_fold(const double* partial, int64_t count, double* out3);
 
-qmcur_status launch_reconstruct_tc(const qmcur_qmat*, const qmcur_qmat*, const qmcur_qmat*, int32_t,
-                                   qmcur_qmat*, const qmcur_qmat*, const uint8_t*, double*, void*,
-                                   size_t, int32_t*, cudaStream_t) {
-  return QMCUR_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int BM = 128, BN = 64;
+constexpr int ROWB = 64;                      // bytes of K per shared row (one swizzle row)
+constexpr int STAGES = 4;
+constexpr int A_PLANE = BM * ROWB;            // 8 KiB
+constexpr int B_PLANE = BN * ROWB;            // 4 KiB
+constexpr int A_STAGE = 4 * A_PLANE;
+constexpr int B_STAGE = 4 * B_PLANE;
+constexpr int STAGE = A_STAGE + B_STAGE;      // 48 KiB
+constexpr int ACC_COLS = 4 * BN;              // FP32 TMEM columns per accumulator
+constexpr int TMEM_COLS = 2 * ACC_COLS;       // 512: two accumulators
+constexpr int kTcThreads = 192;
+constexpr int kTcSmem = STAGES * STAGE + 1024 + 256;
+constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+
+enum { MODE_STORE_Z = 0, MODE_RESIDUAL = 1, MODE_SPLIT_T = 2 };
+
+struct TcParams {
+  int M, N;
+  int K;                  // true inner dimension (the rest of Kpad is zero)
+  int kblocks;            // Kpad / (elements per 64 bytes)
+  int nterms;
+  int ta[6], tb[6];       // piece of X and of Y of each term
+  int mode;
+  // MODE_STORE_Z
+  float* z[4];
+  int64_t ldz;
+  // MODE_RESIDUAL
+  const float* a[4];
+  int64_t lda;
+  int a_vec;              // planes 16-byte aligned and lda % 4 == 0
+  const uint8_t* mask;
+  double* partial;
+  // MODE_SPLIT_T: pieces of Z^T into [piece][plane][bt_rows][bt_kpad]
+  void* bt;
+  int bt_npieces;
+  int64_t bt_rows, bt_kpad;
+  int32_t* status;
+};
+
+// ------------------------------------------------------------- PTX helpers -
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of parity `parity`; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 63u) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
+// 512 bytes apart (SBO), descriptor version 1 (bits 46-47), swizzle mode 4
+// (bits 61-63).  The leading-byte offset is unused for this layout.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((8 * ROWB) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16 (BF16 operands) or kind::tf32: FP32
+// accumulator (bits 4-5 = 1), A/B formats (bits 7-9, 10-12), negate A (bit 13),
+// both operands K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc(bool bf16, bool neg_a) {
+  return (1u << 4) | ((bf16 ? 1u : 2u) << 7) | ((bf16 ? 1u : 2u) << 10) |
+         ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <bool BF16>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                     uint32_t accumulate) {
+  if constexpr (BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   saddr(bar))
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Pieces of one value: BF16 (npieces 2 or 3) or TF32 (npieces 2).
+template <bool BF16, typename T>
+__device__ __forceinline__ void split_value(T x, int npieces, float out[3]) {
+  if constexpr (BF16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+    const T r1 = x - (T)__bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn((float)r1);
+    const T r2 = r1 - (T)__bfloat162float(m);
+    out[0] = __bfloat162float(h);
+    out[1] = __bfloat162float(m);
+    out[2] = npieces > 2 ? __bfloat162float(__float2bfloat16_rn((float)r2)) : 0.f;
+  } else {
+    const float b = tf32_rna((float)x);
+    out[0] = b;
+    out[1] = (float)(x - (T)b);
+    out[2] = 0.f;
+  }
+}
+
+// ------------------------------------------------------------------ kernel -
+template <bool BF16>
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+           TcParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  double* red = reinterpret_cast<double*>(tmem_slot + 2);   // [2][4]
+
+  constexpr int kY[4][4] = {{0, 1, 2, 3}, {1, 0, 3, 2}, {2, 3, 0, 1}, {3, 2, 1, 0}};
+  constexpr int kNeg[4][4] = {{0, 1, 1, 1}, {0, 0, 0, 1}, {0, 1, 0, 0}, {0, 0, 1, 0}};
+  constexpr uint32_t kIdPos = make_idesc(BF16, false), kIdNeg = make_idesc(BF16, true);
+  constexpr int kElemsPerRow = ROWB / (BF16 ? 2 : 4);
+  constexpr int kStepElems = 32 / (BF16 ? 2 : 4);          // K of one MMA (32 bytes)
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int mtiles = (p.M + BM - 1) / BM, ntiles = (p.N + BN - 1) / BN;
+  const int tiles = mtiles * ntiles;
+  const int kiters = p.nterms * p.kblocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], 4); }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------------------------------------------- TMA producer --
+    uint32_t it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+      const int mt = tile % mtiles, nt = tile / mtiles;
+      for (int term = 0; term < p.nterms && ok; ++term)
+        for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) { ok = false; break; }
+          mbar_expect_tx(&full[s], STAGE);
+          const uint32_t sa = saddr(smem + s * STAGE);
+          tma_load_3d(sa, &mapA, &full[s], kb * kElemsPerRow, mt * BM, p.ta[term] * 4);
+          tma_load_3d(sa + A_STAGE, &mapB, &full[s], kb * kElemsPerRow, nt * BN, p.tb[term] * 4);
+        }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------------ MMA issuer --
+    uint32_t it = 0;
+    int local = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++local) {
+      const int a = local & 1;
+      const uint32_t aph = (local >> 1) & 1;
+      if (!mbar_wait(&tempty[a], aph ^ 1u, abort_flag)) break;
+      tc_fence_after();
+      const uint32_t dbase = tmem_base + (uint32_t)(a * ACC_COLS);
+      for (int ki = 0; ki < kiters; ++ki, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (it / STAGES) & 1u;
+        if (!mbar_wait(&full[s], ph, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t sa = saddr(smem + s * STAGE), sb = sa + A_STAGE;
+        const int kb = ki % p.kblocks;
+        const int kleft = p.K - kb * kElemsPerRow;          // valid elements in this slice
+        const int ksteps = kleft >= kElemsPerRow ? ROWB / 32 : (kleft + kStepElems - 1) / kStepElems;
+#pragma unroll
+        for (int ks = 0; ks < ROWB / 32; ++ks) {
+          if (ks >= ksteps) break;
+#pragma unroll
+          for (int pl = 0; pl < 4; ++pl) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const uint64_t ad = sdesc(sa + t * A_PLANE + ks * 32);
+              const uint64_t bd = sdesc(sb + kY[pl][t] * B_PLANE + ks * 32);
+              const uint32_t acc = (ki > 0 || ks > 0 || t > 0) ? 1u : 0u;
+              umma<BF16>(dbase + pl * BN, ad, bd, kNeg[pl][t] ? kIdNeg : kIdPos, acc);
+            }
+          }
+        }
+        umma_commit(&empty[s]);   // the stage is free once these MMAs retire
+      }
+      if (ok) umma_commit(&tfull[a]);
+    }
+  } else if (warp >= 2) {
+    // -------------------------------------------------------- epilogue --
+    const int sp = warp % 4;                 // TMEM sub-partition (lanes 32 sp ...)
+    const int epi = warp - 2;
+    int local = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
+      const int a = local & 1;
+      const uint32_t aph = (local >> 1) & 1;
+      if (!mbar_wait(&tfull[a], aph, abort_flag)) break;
+      tc_fence_after();
+      const int mt = tile % mtiles, nt = tile / mtiles;
+      const int row = mt * BM + sp * 32 + lane;
+      const int n0 = nt * BN;
+      const uint32_t tb = tmem_base + (uint32_t)(a * ACC_COLS) + ((uint32_t)(sp * 32) << 16);
+      double dsum = 0.0, asum = 0.0;
+      if (p.mode == MODE_RESIDUAL) {
+#pragma unroll 1
+        for (int ch = 0; ch < BN / 16; ++ch) {
+          const int c0 = n0 + ch * 16;
+          // the A values of all four planes of this 16-column chunk first
+          float4 av[4][4];
+          const bool in_row = row < p.M;
+          const bool full16 = p.a_vec && c0 + 16 <= p.N;
+#pragma unroll
+          for (int pl = 0; pl < 4; ++pl) {
+            const float* ar = p.a[pl] + (int64_t)row * p.lda + c0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              if (in_row && full16) {
+                av[pl][q] = __ldcs(reinterpret_cast<const float4*>(ar) + q);
+              } else {
+                float e[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  e[u] = (in_row && c0 + 4 * q + u < p.N) ? ar[4 * q + u] : 0.f;
+                av[pl][q] = make_float4(e[0], e[1], e[2], e[3]);
+              }
+            }
+          }
+          unsigned keep = 0xffffu;   // columns of the chunk that count
+          if (!full16 || p.mask != nullptr) {
+            keep = 0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const bool ok = in_row && c0 + j < p.N &&
+                              (p.mask == nullptr || p.mask[(int64_t)row * p.N + c0 + j] != 0);
+              keep |= (ok ? 1u : 0u) << j;
+            }
+          }
+          float sd = 0.f, sa2 = 0.f;
+#pragma unroll
+          for (int pl = 0; pl < 4; ++pl) {
+            float z[16];
+            tmem_ld16(tb + pl * BN + ch * 16, z);
+            const float* avf = reinterpret_cast<const float*>(av[pl]);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float w = ((keep >> j) & 1u) ? 1.f : 0.f;
+              const float d = (avf[j] - z[j]) * w;
+              sd = fmaf(d, d, sd);
+              sa2 = fmaf(avf[j] * w, avf[j], sa2);
+            }
+          }
+          if (in_row) { dsum += (double)sd; asum += (double)sa2; }
+        }
+      } else {
+#pragma unroll 1
+        for (int pl = 0; pl < 4; ++pl) {
+#pragma unroll 1
+          for (int ch = 0; ch < BN / 16; ++ch) {
+            float z[16];
+            tmem_ld16(tb + pl * BN + ch * 16, z);
+            const int c0 = n0 + ch * 16;
+            if (p.mode == MODE_STORE_Z) {
+              if (row < p.M) {
+                float* zr = p.z[pl] + (int64_t)row * p.ldz + c0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                  if (c0 + j < p.N) zr[j] = z[j];
+              }
+            } else if (row < p.bt_kpad) {   // MODE_SPLIT_T
+#pragma unroll 4
+              for (int j = 0; j < 16; ++j) {
+                const int n = c0 + j;
+                if (n >= p.N) break;
+                float pc[3];
+                split_value<BF16, float>(z[j], p.bt_npieces, pc);
+                for (int q = 0; q < p.bt_npieces; ++q) {
+                  const int64_t idx = (((int64_t)q * 4 + pl) * p.bt_rows + n) * p.bt_kpad + row;
+                  if constexpr (BF16)
+                    reinterpret_cast<__nv_bfloat16*>(p.bt)[idx] = __float2bfloat16_rn(pc[q]);
+                  else
+                    reinterpret_cast<float*>(p.bt)[idx] = pc[q];
+                }
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      if (lane == 0) mbar_arrive(&tempty[a]);
+      if (p.mode == MODE_RESIDUAL) {
+        // fixed-order reduction: warp tree, then the four warps in order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+          asum += __shfl_xor_sync(0xffffffffu, asum, o);
+        }
+        double* rb = red + (local & 1) * 8;
+        if (lane == 0) { rb[epi] = dsum; rb[4 + epi] = asum; }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (epi == 0 && lane == 0) {
+          p.partial[2 * tile] = (rb[0] + rb[1]) + (rb[2] + rb[3]);
+          p.partial[2 * tile + 1] = (rb[4] + rb[5]) + (rb[6] + rb[7]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+  if (threadIdx.x == 0 && *abort_flag) set_status(p.status, QMCUR_ERR_TIMEOUT);
+}
+
+// Operand pieces: dst[(q*4 + t)][i][k] for i < rows_out, k < kpad, taken
+// from S(i, k) (or S(k, i) when TRANS), zero for k >= K.
+template <bool BF16, typename TS, bool TRANS>
+__global__ void k_split(QView S, void* dst, int64_t rows_out, int64_t K, int64_t kpad, int npieces) {
+  __shared__ float tile[4][32][33];
+  const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 32 x 8 threads
+  if (TRANS) {
+    // read S(k0 + ty.., i0 + tx) coalesced along i, transpose through shared memory
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t k = k0 + r, i = i0 + tx;
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        tile[t][r][tx] = (k < K && i < rows_out)
+                             ? (float)reinterpret_cast<const TS*>(S.p[t])[k * S.ld + i] : 0.f;
+    }
+    __syncthreads();
+  }
+  const size_t es = BF16 ? 2 : 4;
+  (void)es;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r, k = k0 + tx;
+    if (i >= rows_out || k >= kpad) continue;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float pc[3] = {0.f, 0.f, 0.f};
+      if (k < K) {
+        if (TRANS) {
+          split_value<BF16, float>(tile[t][tx][r], npieces, pc);
+        } else {
+          const TS x = reinterpret_cast<const TS*>(S.p[t])[i * S.ld + k];
+          split_value<BF16, TS>(x, npieces, pc);
+        }
+      }
+      for (int q = 0; q < npieces; ++q) {
+        const int64_t idx = (((int64_t)q * 4 + t) * rows_out + i) * kpad + k;
+        if (BF16) reinterpret_cast<__nv_bfloat16*>(dst)[idx] = __float2bfloat16_rn(pc[q]);
+        else reinterpret_cast<float*>(dst)[idx] = pc[q];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ host side ---
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// 3-D map over [npieces*4][rows][kpad] with a box of one 64-byte K slice x
+// box_rows rows x 4 planes, 64-byte swizzle, zero fill out of bounds.
+bool make_map(CUtensorMap* map, void* base, bool bf16, int64_t rows, int64_t kpad, int npieces,
+              int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (fn == nullptr) return false;
+  const int es = bf16 ? 2 : 4;
+  cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)(npieces * 4)};
+  cuuint64_t strides[2] = {(cuuint64_t)(kpad * es), (cuuint64_t)(kpad * es * rows)};
+  cuuint32_t box[3] = {(cuuint32_t)(ROWB / es), (cuuint32_t)box_rows, 4};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base,
+            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct TcPlan {
+  bool bf16;
+  int npieces, nterms;
+  int ta[6], tb[6];
+  int64_t epr;   // elements per 64-byte row
+};
+
+TcPlan plan_for(int32_t prec) {
+  TcPlan pl{};
+  pl.bf16 = prec != QMCUR_PREC_TF32X3;
+  pl.npieces = prec == QMCUR_PREC_BF16X6 ? 3 : 2;
+  pl.epr = pl.bf16 ? 32 : 16;
+  // smallest terms first
+  if (prec == QMCUR_PREC_BF16X6) {
+    const int a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
+    pl.nterms = 6;
+    for (int i = 0; i < 6; ++i) { pl.ta[i] = a[i]; pl.tb[i] = b[i]; }
+  } else {
+    const int a[3] = {1, 0, 0}, b[3] = {0, 1, 0};
+    pl.nterms = 3;
+    for (int i = 0; i < 3; ++i) { pl.ta[i] = a[i]; pl.tb[i] = b[i]; }
+  }
+  return pl;
+}
+
+inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+struct TcWs {
+  void *A1, *B1, *A2, *B2;
+  double* partial;
+};
+
+TcWs carve_tc(Carve& cv, const TcPlan& pl, int64_t m, int64_t n, int64_t c, int64_t r) {
+  const int64_t es = pl.bf16 ? 2 : 4;
+  const int64_t kp1 = rup(r, pl.epr), kp2 = rup(c, pl.epr);
+  TcWs w;
+  w.A1 = cv.take<char>((size_t)(pl.npieces * 4 * rup(c, BM) * kp1 * es));
+  w.B1 = cv.take<char>((size_t)(pl.npieces * 4 * n * kp1 * es));
+  w.A2 = cv.take<char>((size_t)(pl.npieces * 4 * m * kp2 * es));
+  w.B2 = cv.take<char>((size_t)(pl.npieces * 4 * n * kp2 * es));
+  const int64_t tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+  w.partial = cv.take<double>((size_t)(2 * tiles));
+  return w;
+}
+
+template <bool BF16>
+qmcur_status launch_split(const qmcur_qmat* S, bool trans, void* dst, int64_t rows_out, int64_t K,
+                          int64_t kpad, int npieces, cudaStream_t st) {
+  dim3 grid((unsigned)((kpad + 31) / 32), (unsigned)((rows_out + 31) / 32));
+  if (grid.y > 65535) return QMCUR_ERR_UNSUPPORTED;
+  QView v = view(S);
+  if (S->dtype == QMCUR_F64) {
+    if (trans) k_split<BF16, double, true><<<grid, 256, 0, st>>>(v, dst, rows_out, K, kpad, npieces);
+    else k_split<BF16, double, false><<<grid, 256, 0, st>>>(v, dst, rows_out, K, kpad, npieces);
+  } else {
+    if (trans) k_split<BF16, float, true><<<grid, 256, 0, st>>>(v, dst, rows_out, K, kpad, npieces);
+    else k_split<BF16, float, false><<<grid, 256, 0, st>>>(v, dst, rows_out, K, kpad, npieces);
+  }
+  return cuda_ok(cudaGetLastError());
+}
+
+template <bool BF16>
+qmcur_status launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& p,
+                         cudaStream_t st) {
+  static bool attr_done[64] = {};
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QMCUR_ERR_CUDA;
+  if (!attr_done[dev]) {
+    if (cudaFuncSetAttribute(k_qgemm_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kTcSmem) != cudaSuccess)
+      return QMCUR_ERR_CUDA;
+    attr_done[dev] = true;
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  const int tiles = ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN);
+  const int grid = tiles < sms ? tiles : sms;
+  k_qgemm_tc<BF16><<<grid, kTcThreads, kTcSmem, st>>>(ma, mb, p);
+  return cuda_ok(cudaGetLastError());
+}
+
+}  // namespace
+
+size_t tc_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec) {
+  Carve cv(nullptr, 0);
+  carve_tc(cv, plan_for(prec), m, n, c, r);
+  return cv.off;
+}
+
+qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
+                                   int32_t prec, qmcur_qmat* Z, const qmcur_qmat* A,
+                                   const uint8_t* mask, double* out3, void* ws, size_t ws_bytes,
+                                   int32_t* dev_status, cudaStream_t st) {
+  const int64_t m = C->rows, c = C->cols, r = R->rows, n = R->cols;
+  if (C->dtype != QMCUR_F32 || R->dtype != QMCUR_F32) return QMCUR_ERR_INVALID_ARG;
+  if (Z != nullptr && Z->dtype != QMCUR_F32) return QMCUR_ERR_INVALID_ARG;
+  if (A != nullptr && A->dtype != QMCUR_F32) return QMCUR_ERR_INVALID_ARG;
+  if (m > INT32_MAX / 2 || n > INT32_MAX / 2) return QMCUR_ERR_UNSUPPORTED;
+  const TcPlan pl = plan_for(prec);
+  Carve cv(ws, ws_bytes);
+  TcWs w = carve_tc(cv, pl, m, n, c, r);
+  if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
+  const int64_t kp1 = rup(r, pl.epr), kp2 = rup(c, pl.epr);
+  qmcur_status s;
+  // operand pieces: U (c x r) and C (m x c) as they are, R (r x n) transposed
+  if (pl.bf16) {
+    if ((s = launch_split<true>(U, false, w.A1, c, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
+    if ((s = launch_split<true>(R, true, w.B1, n, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
+    if ((s = launch_split<true>(C, false, w.A2, m, c, kp2, pl.npieces, st)) != QMCUR_OK) return s;
+  } else {
+    if ((s = launch_split<false>(U, false, w.A1, c, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
+    if ((s = launch_split<false>(R, true, w.B1, n, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
+    if ((s = launch_split<false>(C, false, w.A2, m, c, kp2, pl.npieces, st)) != QMCUR_OK) return s;
+  }
+  CUtensorMap mA1, mB1, mA2, mB2;
+  if (!make_map(&mA1, w.A1, pl.bf16, c, kp1, pl.npieces, BM) ||
+      !make_map(&mB1, w.B1, pl.bf16, n, kp1, pl.npieces, BN) ||
+      !make_map(&mA2, w.A2, pl.bf16, m, kp2, pl.npieces, BM) ||
+      !make_map(&mB2, w.B2, pl.bf16, n, kp2, pl.npieces, BN))
+    return QMCUR_ERR_CUDA;
+  TcParams p1{};
+  p1.M = (int)c;
+  p1.N = (int)n;
+  p1.K = (int)r;
+  p1.kblocks = (int)(kp1 / pl.epr);
+  p1.nterms = pl.nterms;
+  for (int i = 0; i < 6; ++i) { p1.ta[i] = pl.ta[i]; p1.tb[i] = pl.tb[i]; }
+  p1.mode = MODE_SPLIT_T;
+  p1.bt = w.B2;
+  p1.bt_npieces = pl.npieces;
+  p1.bt_rows = n;
+  p1.bt_kpad = kp2;
+  p1.status = dev_status;
+  TcParams p2 = p1;
+  p2.M = (int)m;
+  p2.K = (int)c;
+  p2.kblocks = (int)(kp2 / pl.epr);
+  if (Z != nullptr) {
+    p2.mode = MODE_STORE_Z;
+    for (int t = 0; t < 4; ++t) p2.z[t] = reinterpret_cast<float*>(Z->plane[t]);
+    p2.ldz = Z->ld;
+  } else {
+    p2.mode = MODE_RESIDUAL;
+    for (int t = 0; t < 4; ++t) p2.a[t] = reinterpret_cast<const float*>(A->plane[t]);
+    p2.lda = A->ld;
+    p2.a_vec = A->ld % 4 == 0;
+    for (int t = 0; t < 4; ++t)
+      p2.a_vec = p2.a_vec && reinterpret_cast<uintptr_t>(A->plane[t]) % 16 == 0;
+    p2.mask = mask;
+    p2.partial = w.partial;
+  }
+  if (pl.bf16) {
+    if ((s = launch_gemm<true>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
+    if ((s = launch_gemm<true>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
+  } else {
+    if ((s = launch_gemm<false>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
+    if ((s = launch_gemm<false>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
+  }
+  if (Z == nullptr) {
+    const int64_t tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+    k_residual_fold<<<1, 1024, 0, st>>>(w.partial, tiles, out3);
+  }
+  return cuda_ok(cudaGetLastError());
 }
 
 }  // namespace qmcur

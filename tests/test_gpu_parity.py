@@ -278,3 +278,48 @@ def test_pinv_subspace_needs_cap():
     with pytest.raises(Q.QmcurError) as e:
         _pinv_fast(W, 0)
     assert e.value.code == 7
+
+
+# ----------------------------------------------- tensor-core (tcgen05) GEMMs -
+# Tolerance per split: TF32X3 and BF16X6 carry ~22-24 significant bits per
+# operand (relative Frobenius error ~1e-7 expected, bound 1e-5); BF16X3 carries
+# ~17 bits per operand (hi + lo), so its products are exact to ~2^-16 and the
+# bound is 6e-5.
+TC_TOL = {Q.PREC_TF32X3: 1e-5, Q.PREC_BF16X6: 1e-5, Q.PREC_BF16X3: 6e-5}
+
+
+@pytest.mark.parametrize("prec", [Q.PREC_BF16X3, Q.PREC_BF16X6, Q.PREC_TF32X3])
+@pytest.mark.parametrize("m,n,c,r", [(128, 64, 64, 64), (200, 300, 40, 30), (129, 65, 7, 9),
+                                     (300, 700, 200, 120), (1, 1, 1, 1)])
+def test_reconstruct_tensor_cores(prec, m, n, c, r):
+    rng = np.random.default_rng(m * 7 + n + c)
+    C, U, R = (rng.standard_normal(s).astype(np.float32) for s in
+               ((4, m, c), (4, c, r), (4, r, n)))
+    Zo = O.reconstruct(C.astype(np.float64), U.astype(np.float64), R.astype(np.float64))
+    Z = torch.empty(4, m, n, dtype=torch.float32, device="cuda")
+    ws = Q.workspace(m, n, c, r, prec)
+    st = Q.status_tensor()
+    Q.reconstruct(dev(C), dev(U), dev(R), prec, Z, ws, st)
+    assert run_status(st) == 0
+    assert rel_fro(host(Z), Zo) < TC_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [Q.PREC_BF16X3, Q.PREC_BF16X6, Q.PREC_TF32X3])
+def test_residual_tensor_cores_fused(prec):
+    m, n, c, r = 333, 515, 24, 20
+    A, _ = synth.lowrank_gaussian(m, n, 6, seed=5, noise_rel=1e-2)
+    out = O.qmcur(A.astype(np.float64), c, r, sampler=O.SAMPLER_UNIFORM, seed=4, rank_cap=6)
+    U32_ = out["U"].astype(np.float32)
+    Zo = O.reconstruct(out["C"], U32_.astype(np.float64), out["R"])
+    mask = synth.bernoulli_mask(m, n, seed=6)
+    for msk in (None, mask):
+        rel_o, num_o, den_o = O.residual(A.astype(np.float64), Zo, msk)
+        out3 = torch.empty(3, dtype=torch.float64, device="cuda")
+        ws = Q.workspace(m, n, c, r, prec)
+        st = Q.status_tensor()
+        Q.residual(dev(A), out3, dev(out["C"].astype(np.float32)), dev(U32_),
+                   dev(out["R"].astype(np.float32)), prec, None if msk is None else dev(msk),
+                   None, ws, st)
+        assert run_status(st) == 0
+        o = host(out3)
+        assert abs(o[0] - rel_o) < 1e-5 and abs(o[2] - den_o) < 24 * U32 * den_o
