@@ -35,7 +35,7 @@ WORKLOAD = "gauss2048_rank50_noisy"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3", "bf16x6"])
