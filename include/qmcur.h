@@ -220,6 +220,40 @@ qmcur_status qmcur_residual(const qmcur_qmat* A, const qmcur_qmat* C, const qmcu
                             const qmcur_qmat* Z, double* out3, void* workspace,
                             size_t ws_bytes, int32_t* dev_status, cudaStream_t stream);
 
+/*
+ * qmcur_gather - C = A(:,J) (m x c), R = A(I,:) (r x n), W = A(I,J) (r x c)
+ * for given index sets (Sec. 3.1).  J[c], I[r] device int32 in [0, n), [0, m);
+ * out-of-range entries produce zeros.  C, R, W may each be NULL.
+ */
+qmcur_status qmcur_gather(const qmcur_qmat* A, const int32_t* J, const int32_t* I, int64_t c,
+                          int64_t r, qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W,
+                          cudaStream_t stream);
+
+/*
+ * qmcur_reconstruct_backward - gradient of the masked reconstruction loss
+ *   L(A) = || P_Omega(A - C U R) ||_F^2,  C = A(:,J), R = A(I,:), U = W^+,
+ *   W = A(I,J)
+ * (Eq. 1 with the observed set Omega of Example 4.4), through the
+ * reconstruction GEMMs and the Moore-Penrose inverse:
+ *   dA = scale * dL/dA = scale * (2E + G_C at the columns J + G_R at the rows
+ *   I + G_W at (I, J)),  E = P_Omega(A - Z),  G_C = -2 E (UR)^H,
+ *   G_R = -2 U^H C^H E,  G_U = -2 C^H E R^H,
+ *   G_W = -U^H G_U U^H + (I - W U) G_U^H U U^H + U^H U G_U^H (I - U W)
+ * (the fixed-rank derivative of W^+ of Golub and Pereyra; exact where W has
+ * the rank of U).  FP32 arithmetic.
+ *   A, dA m x n (dA F32 or F64, fully overwritten); C m x c and R r x n F32;
+ *   U c x r and W r x c F32 or F64; mask NULL or m x n bytes (row stride n);
+ *   J[c], I[r] the index sets used to form C, R, W (device int32).
+ *   loss_out: device double scalar L or NULL.  Workspace:
+ *   qmcur_backward_workspace_size(m, n, c, r).
+ */
+size_t qmcur_backward_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r);
+qmcur_status qmcur_reconstruct_backward(const qmcur_qmat* A, const uint8_t* mask, const int32_t* J,
+                                        const int32_t* I, const qmcur_qmat* C, const qmcur_qmat* U,
+                                        const qmcur_qmat* R, const qmcur_qmat* W, double scale,
+                                        qmcur_qmat* dA, double* loss_out, void* workspace,
+                                        size_t ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
 /* Options of qmcur_decompose. */
 typedef struct {
   int32_t  sampler;      /* qmcur_sampler */

@@ -16,6 +16,16 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
                               int32_t* rank_out, uint64_t seed, void* ws, size_t ws_bytes,
                               int32_t* dev_status, cudaStream_t st);
 
+// Backward of the masked reconstruction loss (backward.cu).
+size_t backward_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r);
+qmcur_status launch_backward(const qmcur_qmat* A, const uint8_t* mask, const int32_t* J,
+                             const int32_t* I, const qmcur_qmat* C, const qmcur_qmat* U,
+                             const qmcur_qmat* R, const qmcur_qmat* W, double scale, qmcur_qmat* dA,
+                             double* loss_out, void* ws, size_t ws_bytes, int32_t* dev_status,
+                             cudaStream_t st);
+qmcur_status launch_gather(const qmcur_qmat* A, const int32_t* J, const int32_t* I, int64_t c,
+                           int64_t r, qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W, cudaStream_t st);
+
 // Tensor-core path (qgemm_tc.cu).
 size_t tc_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec);
 qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
@@ -168,6 +178,26 @@ qmcur_status qmcur_residual(const qmcur_qmat* A, const qmcur_qmat* C, const qmcu
     return launch_residual_standalone(A, Z, mask, out3, workspace, ws_bytes, dev_status, stream);
   return launch_reconstruct(C, U, R, prec, nullptr, A, mask, out3, workspace, ws_bytes, dev_status,
                             stream);
+}
+
+qmcur_status qmcur_gather(const qmcur_qmat* A, const int32_t* J, const int32_t* I, int64_t c,
+                          int64_t r, qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W,
+                          cudaStream_t stream) {
+  return launch_gather(A, J, I, c, r, C, R, W, stream);
+}
+
+size_t qmcur_backward_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r) {
+  if (m < 1 || n < 1 || c < 1 || r < 1) return 0;
+  return backward_ws_bytes(m, n, c, r) + 256;
+}
+
+qmcur_status qmcur_reconstruct_backward(const qmcur_qmat* A, const uint8_t* mask, const int32_t* J,
+                                        const int32_t* I, const qmcur_qmat* C, const qmcur_qmat* U,
+                                        const qmcur_qmat* R, const qmcur_qmat* W, double scale,
+                                        qmcur_qmat* dA, double* loss_out, void* workspace,
+                                        size_t ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  return launch_backward(A, mask, J, I, C, U, R, W, scale, dA, loss_out, workspace, ws_bytes,
+                         dev_status, stream);
 }
 
 qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qmcur_opts* o,

@@ -1,0 +1,200 @@
+// Gradient of the masked CUR reconstruction loss (FP32).
+//
+//   L(A) = || P_Omega(A - C U R) ||_F^2,  C = A(:,J), R = A(I,:), W = A(I,J), U = W^+.
+// With E = P_Omega(A - Z), Z = C T, T = U R and <X, Y> = Re tr(X^H Y):
+//   G_C = -2 E T^H,  G_T = -2 C^H E,  G_U = G_T R^H,  G_R = U^H G_T,
+//   G_W = -U^H G_U U^H + (I - W U) G_U^H U U^H + U^H U G_U^H (I - U W)
+// (the derivative of the Moore-Penrose inverse at fixed rank, Golub-Pereyra,
+// in quaternion form), and dL/dA = 2 E + G_C scattered to the columns J,
+// + G_R to the rows I, + G_W to (I, J).  The incoming gradient `scale`
+// multiplies everything.  J and I are sets, so every scatter touches each
+// destination once; the three scatters run one after the other.
+#include "common.cuh"
+#include "small.cuh"
+
+namespace qmcur {
+
+size_t residual_partials(int64_t m, int64_t n);
+
+namespace {
+
+__global__ void k_to_qptr_f32(QView in, QPtr out) {
+  const int64_t total = in.rows * in.cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / in.cols, j = e % in.cols;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      reinterpret_cast<float*>(out.p[t])[i * out.ld + j] = (float)ld_as_double(in, t, i, j);
+  }
+}
+
+// E = mask * (A - Z), in place over Z; dA = 2 s E.
+__global__ void k_residual_matrix(QView A, const uint8_t* __restrict__ mask, QPtr Z, QView dA,
+                                  float two_s) {
+  const int64_t m = A.rows, n = A.cols, total = m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e % n;
+    const bool on = mask == nullptr || mask[e] != 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float* z = reinterpret_cast<float*>(Z.p[t]) + i * Z.ld + j;
+      const float ev = on ? (float)ld_as_double(A, t, i, j) - *z : 0.f;
+      *z = ev;
+      st_from_double(dA, t, i, j, (double)(two_s * ev));
+    }
+  }
+}
+
+// which 0: dA(:, J[b]) += G(:, b); 1: dA(I[a], :) += G(a, :); 2: dA(I[a], J[b]) += G(a, b)
+__global__ void k_scatter_add(QView dA, QPtr G, int64_t rows, int64_t cols, const int32_t* I,
+                              const int32_t* J, int which) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / cols, b = e % cols;
+    const int64_t di = (which == 0) ? a : (int64_t)I[a];
+    const int64_t dj = (which == 1) ? b : (int64_t)J[b];
+    if (di < 0 || di >= dA.rows || dj < 0 || dj >= dA.cols) continue;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float g = reinterpret_cast<const float*>(G.p[t])[a * G.ld + b];
+      st_from_double(dA, t, di, dj, ld_as_double(dA, t, di, dj) + (double)g);
+    }
+  }
+}
+
+// Y += X (same shape)
+__global__ void k_qadd(QPtr X, QPtr Y, int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e % cols;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      reinterpret_cast<float*>(Y.p[t])[i * Y.ld + j] += reinterpret_cast<const float*>(X.p[t])[i * X.ld + j];
+  }
+}
+
+QPtr take_q(Carve& cv, int64_t rows, int64_t cols) {
+  QPtr q;
+  const int64_t ld = (cols + 3) / 4 * 4;
+  float* base = cv.take<float>((size_t)(4 * rows * ld));
+  for (int t = 0; t < 4; ++t) q.p[t] = base ? base + (size_t)t * rows * ld : nullptr;
+  q.ld = ld;
+  q.dtype = QMCUR_F32;
+  return q;
+}
+
+struct BwdWs {
+  QPtr U32, W32, T, E, GC, GT, GU, GR, X1, WU, UW, UUh, UhU, M2, M3, GW;
+  double* partial;
+  double* out3;
+};
+
+BwdWs carve_bwd(Carve& cv, int64_t m, int64_t n, int64_t c, int64_t r) {
+  BwdWs w;
+  w.U32 = take_q(cv, c, r);
+  w.W32 = take_q(cv, r, c);
+  w.T = take_q(cv, c, n);
+  w.E = take_q(cv, m, n);
+  w.GC = take_q(cv, m, c);
+  w.GT = take_q(cv, c, n);
+  w.GU = take_q(cv, c, r);
+  w.GR = take_q(cv, r, n);
+  w.X1 = take_q(cv, r, r);
+  w.WU = take_q(cv, r, r);
+  w.UW = take_q(cv, c, c);
+  w.UUh = take_q(cv, c, c);
+  w.UhU = take_q(cv, r, r);
+  w.M2 = take_q(cv, r, c);
+  w.M3 = take_q(cv, r, c);
+  w.GW = take_q(cv, r, c);
+  w.partial = cv.take<double>(2 * residual_partials(m, n));
+  w.out3 = cv.take<double>(4);
+  return w;
+}
+
+int blocks_for(int64_t total) {
+  int64_t b = (total + 255) / 256;
+  if (b > 4096) b = 4096;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+size_t backward_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r) {
+  Carve cv(nullptr, 0);
+  carve_bwd(cv, m, n, c, r);
+  return cv.off;
+}
+
+qmcur_status launch_backward(const qmcur_qmat* A, const uint8_t* mask, const int32_t* J,
+                             const int32_t* I, const qmcur_qmat* C, const qmcur_qmat* U,
+                             const qmcur_qmat* R, const qmcur_qmat* W, double scale, qmcur_qmat* dA,
+                             double* loss_out, void* ws, size_t ws_bytes, int32_t* dev_status,
+                             cudaStream_t st) {
+  if (!valid_qmat(A) || !valid_qmat(C) || !valid_qmat(U) || !valid_qmat(R) || !valid_qmat(W) ||
+      !valid_qmat(dA) || J == nullptr || I == nullptr)
+    return QMCUR_ERR_INVALID_ARG;
+  const int64_t m = A->rows, n = A->cols, c = C->cols, r = R->rows;
+  if (C->rows != m || R->cols != n || U->rows != c || U->cols != r || W->rows != r ||
+      W->cols != c || dA->rows != m || dA->cols != n || m < 1 || n < 1 || c < 1 || r < 1)
+    return QMCUR_ERR_INVALID_ARG;
+  if (C->dtype != QMCUR_F32 || R->dtype != QMCUR_F32) return QMCUR_ERR_INVALID_ARG;
+  if (m > INT32_MAX || n > INT32_MAX) return QMCUR_ERR_UNSUPPORTED;
+  Carve cv(ws, ws_bytes);
+  BwdWs w = carve_bwd(cv, m, n, c, r);
+  if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
+  const int mi = (int)m, ni = (int)n, ci = (int)c, ri = (int)r;
+  QPtr Cq, Rq;
+  for (int t = 0; t < 4; ++t) { Cq.p[t] = C->plane[t]; Rq.p[t] = R->plane[t]; }
+  Cq.ld = C->ld; Rq.ld = R->ld;
+  Cq.dtype = Rq.dtype = QMCUR_F32;
+  const float s = (float)scale;
+  qmcur_status e;
+  k_to_qptr_f32<<<blocks_for(c * r), 256, 0, st>>>(view(U), w.U32);
+  k_to_qptr_f32<<<blocks_for(r * c), 256, 0, st>>>(view(W), w.W32);
+  // forward pieces: T = U R, Z = C T (into E), loss, E = P_Omega(A - Z), dA = 2 s E
+  if ((e = small_qgemm(false, false, ci, ni, ri, 1.f, w.U32, Rq, 0.f, w.T, st)) != QMCUR_OK) return e;
+  if ((e = small_qgemm(false, false, mi, ni, ci, 1.f, Cq, w.T, 0.f, w.E, st)) != QMCUR_OK) return e;
+  {
+    qmcur_qmat Zq;
+    for (int t = 0; t < 4; ++t) Zq.plane[t] = w.E.p[t];
+    Zq.rows = m; Zq.cols = n; Zq.ld = w.E.ld; Zq.dtype = QMCUR_F32; Zq.reserved = 0;
+    if ((e = launch_residual_standalone(A, &Zq, mask, w.out3, w.partial,
+                                        (size_t)(2 * residual_partials(m, n)) * 8 + 256, dev_status,
+                                        st)) != QMCUR_OK)
+      return e;
+    if (loss_out != nullptr)
+      cudaMemcpyAsync(loss_out, w.out3 + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
+  }
+  k_residual_matrix<<<blocks_for(m * n), 256, 0, st>>>(view(A), mask, w.E, view(dA), 2.f * s);
+  // adjoints of the two GEMMs
+  if ((e = small_qgemm(false, true, mi, ci, ni, -2.f * s, w.E, w.T, 0.f, w.GC, st)) != QMCUR_OK) return e;
+  if ((e = small_qgemm(true, false, ci, ni, mi, -2.f * s, Cq, w.E, 0.f, w.GT, st)) != QMCUR_OK) return e;
+  if ((e = small_qgemm(false, true, ci, ri, ni, 1.f, w.GT, Rq, 0.f, w.GU, st)) != QMCUR_OK) return e;
+  if ((e = small_qgemm(true, false, ri, ni, ci, 1.f, w.U32, w.GT, 0.f, w.GR, st)) != QMCUR_OK) return e;
+  // G_W = -U^H G_U U^H + (I - W U) G_U^H U U^H + U^H U G_U^H (I - U W)
+  if ((e = small_qgemm(true, false, ri, ri, ci, 1.f, w.U32, w.GU, 0.f, w.X1, st)) != QMCUR_OK) return e;
+  if ((e = small_qgemm(false, true, ri, ci, ri, -1.f, w.X1, w.U32, 0.f, w.GW, st)) != QMCUR_OK) return e;
+  if ((e = small_qgemm(false, true, ci, ci, ri, 1.f, w.U32, w.U32, 0.f, w.UUh, st)) != QMCUR_OK) return e;
+  if ((e = small_qgemm(true, false, ri, ci, ci, 1.f, w.GU, w.UUh, 0.f, w.M2, st)) != QMCUR_OK) return e;
+  if ((e = small_qgemm(false, false, ri, ri, ci, 1.f, w.W32, w.U32, 0.f, w.WU, st)) != QMCUR_OK) return e;
+  k_qadd<<<blocks_for(r * c), 256, 0, st>>>(w.M2, w.GW, r, c);
+  if ((e = small_qgemm(false, false, ri, ci, ri, -1.f, w.WU, w.M2, 1.f, w.GW, st)) != QMCUR_OK) return e;
+  if ((e = small_qgemm(true, false, ri, ri, ci, 1.f, w.U32, w.U32, 0.f, w.UhU, st)) != QMCUR_OK) return e;
+  if ((e = small_qgemm(false, true, ri, ci, ri, 1.f, w.UhU, w.GU, 0.f, w.M3, st)) != QMCUR_OK) return e;
+  if ((e = small_qgemm(false, false, ci, ci, ri, 1.f, w.U32, w.W32, 0.f, w.UW, st)) != QMCUR_OK) return e;
+  k_qadd<<<blocks_for(r * c), 256, 0, st>>>(w.M3, w.GW, r, c);
+  if ((e = small_qgemm(false, false, ri, ci, ci, -1.f, w.M3, w.UW, 1.f, w.GW, st)) != QMCUR_OK) return e;
+  // scatters
+  QView vdA = view(dA);
+  k_scatter_add<<<blocks_for(m * c), 256, 0, st>>>(vdA, w.GC, m, c, I, J, 0);
+  k_scatter_add<<<blocks_for(r * n), 256, 0, st>>>(vdA, w.GR, r, n, I, J, 1);
+  k_scatter_add<<<blocks_for(r * c), 256, 0, st>>>(vdA, w.GW, r, c, I, J, 2);
+  return cuda_ok(cudaGetLastError());
+}
+
+}  // namespace qmcur

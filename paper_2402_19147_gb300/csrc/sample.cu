@@ -215,6 +215,25 @@ __global__ void k_gather(QView A, const int32_t* __restrict__ J, const int32_t* 
 
 }  // namespace
 
+qmcur_status launch_gather(const qmcur_qmat* A, const int32_t* J, const int32_t* I, int64_t c,
+                           int64_t r, qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W, cudaStream_t st) {
+  if (!valid_qmat(A) || J == nullptr || I == nullptr || c < 1 || r < 1) return QMCUR_ERR_INVALID_ARG;
+  const int64_t m = A->rows, n = A->cols;
+  if (C && (!valid_qmat(C) || C->rows != m || C->cols != c)) return QMCUR_ERR_INVALID_ARG;
+  if (R && (!valid_qmat(R) || R->rows != r || R->cols != n)) return QMCUR_ERR_INVALID_ARG;
+  if (W && (!valid_qmat(W) || W->rows != r || W->cols != c)) return QMCUR_ERR_INVALID_ARG;
+  if (!C && !R && !W) return QMCUR_OK;
+  QView vA = view(A);
+  QView vC = C ? view(C) : vA, vR = R ? view(R) : vA, vW = W ? view(W) : vA;
+  const int64_t biggest = m * c > r * n ? m * c : r * n;
+  int blocks = (int)((biggest + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_gather<<<dim3(blocks, 3), 256, 0, st>>>(vA, J, I, vC, vR, vW, C != nullptr, R != nullptr,
+                                           W != nullptr);
+  return cuda_ok(cudaGetLastError());
+}
+
 size_t sample_ws_bytes(int64_t m, int64_t n) {
   Carve c(nullptr, 0);
   c.take<double>((size_t)n);

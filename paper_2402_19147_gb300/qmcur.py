@@ -66,6 +66,10 @@ SIGNATURES = {
     "qmcur_pinv_core": (_I32, [_QP, _I32, _D, _I32, _I32, _QP, _P, _P, _P, _SZ, _P, _P]),
     "qmcur_reconstruct": (_I32, [_QP, _QP, _QP, _I32, _QP, _P, _SZ, _P, _P]),
     "qmcur_residual": (_I32, [_QP, _QP, _QP, _QP, _I32, _P, _QP, _P, _P, _SZ, _P, _P]),
+    "qmcur_gather": (_I32, [_QP, _P, _P, _I64, _I64, _QP, _QP, _QP, _P]),
+    "qmcur_backward_workspace_size": (_SZ, [_I64, _I64, _I64, _I64]),
+    "qmcur_reconstruct_backward": (_I32, [_QP, _P, _P, _P, _QP, _QP, _QP, _QP, _D, _QP, _P, _P,
+                                          _SZ, _P, _P]),
     "qmcur_decompose": (_I32, [_QP, _I64, _I64, ctypes.POINTER(Opts), _P, _P, _P, _P,
                                _QP, _QP, _QP, _QP, _P, _P, _P, _P, _SZ, _P, _P]),
 }
@@ -180,6 +184,60 @@ def residual(A, out3, C=None, U=None, R=None, prec=PREC_FP32, mask=None, Z=None,
                                 prec, _ptr(mask), _ref(qmat(Z)), _ptr(out3), _ptr(ws),
                                 0 if ws is None else ws.numel(), _ptr(status),
                                 _stream(stream)), "qmcur_residual")
+
+
+def gather(A, J, I, C=None, R=None, W=None, stream=None):
+    _check(lib().qmcur_gather(_ref(qmat(A)), _ptr(J), _ptr(I), J.numel(), I.numel(),
+                              _ref(qmat(C)), _ref(qmat(R)), _ref(qmat(W)), _stream(stream)),
+           "qmcur_gather")
+
+
+def reconstruct_backward(A, mask, J, I, C, U, R, W, scale, dA, loss_out=None, ws=None,
+                         status=None, stream=None):
+    m, n = A.shape[1], A.shape[2]
+    if ws is None:
+        ws = torch.empty(int(lib().qmcur_backward_workspace_size(m, n, J.numel(), I.numel())),
+                         dtype=torch.uint8, device=A.device)
+    _check(lib().qmcur_reconstruct_backward(_ref(qmat(A)), _ptr(mask), _ptr(J), _ptr(I),
+                                            _ref(qmat(C)), _ref(qmat(U)), _ref(qmat(R)),
+                                            _ref(qmat(W)), float(scale), _ref(qmat(dA)),
+                                            _ptr(loss_out), _ptr(ws), ws.numel(), _ptr(status),
+                                            _stream(stream)), "qmcur_reconstruct_backward")
+
+
+class MaskedCURLoss(torch.autograd.Function):
+    """L(A) = || P_Omega(A - C U R) ||_F^2 for fixed index sets J, I, with
+    C = A(:,J), R = A(I,:), U = W^+ (rank cap), W = A(I,J).  Forward and
+    backward run in libqmcur (FP32 GEMMs, FP32 subspace or FP64 Jacobi
+    pseudo-inverse); the sampling itself is not differentiated."""
+
+    @staticmethod
+    def forward(ctx, A, J, I, mask, rank_cap, rcond=1e-10, pinv_method=PINV_SUBSPACE_FP32):
+        m, n = A.shape[1], A.shape[2]
+        c, r = J.numel(), I.numel()
+        dev = A.device
+        C = torch.empty(4, m, c, dtype=torch.float32, device=dev)
+        R = torch.empty(4, r, n, dtype=torch.float32, device=dev)
+        W = torch.empty(4, r, c, dtype=torch.float64, device=dev)
+        U = torch.empty(4, c, r, dtype=torch.float64, device=dev)
+        st = status_tensor(dev)
+        gather(A, J, I, C, R, W)
+        ws = workspace(m, n, c, r, PREC_FP32, dev)
+        pinv_core(W, U, rcond, rank_cap, 0, None, None, ws, st, method=pinv_method)
+        out3 = torch.empty(3, dtype=torch.float64, device=dev)
+        residual(A, out3, C, U, R, PREC_FP32, mask, None, ws, st)
+        check_status(st, "MaskedCURLoss.forward")
+        ctx.save_for_backward(A, J, I, C, U, R, W)
+        ctx.mask = mask
+        return out3[1].to(A.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        A, J, I, C, U, R, W = ctx.saved_tensors
+        dA = torch.empty_like(A)
+        st = status_tensor(A.device)
+        reconstruct_backward(A, ctx.mask, J, I, C, U, R, W, float(g), dA, status=st)
+        return dA, None, None, None, None, None, None
 
 
 class Decomposition:

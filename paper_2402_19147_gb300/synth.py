@@ -52,27 +52,45 @@ def lowrank_gaussian(m, n, rank, seed, noise_rel=0.0, dtype=np.float32):
 
 
 def smooth_color(m, n, modes, seed, offset=0.5, clip=True, max_freq=16,
-                 dtype=np.float32):
+                 dtype=np.float32, distinct=False, bounded_amp=False):
     """Pure quaternion field X = R i + G j + B k (real plane zero).
 
     For each channel in the order R, G, B the generator draws f (modes ints in
     [0, max_freq]), g (same), phi (U[0, 2pi)), psi (U[0, 2pi)) and
     a (N(0,1) * 0.5 / sqrt(modes)), then sets
     F[y, x] = offset + sum_t a_t cos(2 pi f_t x / n + phi_t) cos(2 pi g_t y / m + psi_t)
-    for row y and column x, clipped to [0, 1] when `clip`.  Without clipping or
-    offset every channel has rank <= modes, so X has quaternion rank
-    <= 3 * modes.
+    for row y and column x, clipped to [0, 1] when `clip`.
+    With `distinct`, all 3*modes column frequencies and all 3*modes row
+    frequencies are instead drawn up front without replacement from
+    [1, max_freq] (first f, then g; channel ch takes entries ch*modes ..), so
+    that with max_freq < min(m, n)/2, no offset and no clipping the Fourier
+    vectors are linearly independent: every channel has rank modes and X has
+    quaternion rank exactly 3*modes.  With `bounded_amp` the amplitudes are
+    a = s * (0.5 + 0.5 v) * 0.5 / sqrt(modes) with v ~ U[0, 1) and s a random
+    sign (both drawn in place of the Gaussian a), so no mode is negligible.
     """
     rng = np.random.default_rng(seed)
     X = np.zeros((4, m, n), dtype=np.float64)
     x = np.arange(n, dtype=np.float64)
     y = np.arange(m, dtype=np.float64)
+    if distinct:
+        fall = rng.choice(np.arange(1, max_freq + 1), size=3 * modes, replace=False)
+        gall = rng.choice(np.arange(1, max_freq + 1), size=3 * modes, replace=False)
     for ch in range(3):
-        f = rng.integers(0, max_freq + 1, size=modes)
-        g = rng.integers(0, max_freq + 1, size=modes)
+        if distinct:
+            f = fall[ch * modes:(ch + 1) * modes]
+            g = gall[ch * modes:(ch + 1) * modes]
+        else:
+            f = rng.integers(0, max_freq + 1, size=modes)
+            g = rng.integers(0, max_freq + 1, size=modes)
         phi = rng.uniform(0.0, 2 * np.pi, size=modes)
         psi = rng.uniform(0.0, 2 * np.pi, size=modes)
-        a = rng.standard_normal(modes) * (0.5 / np.sqrt(modes))
+        if bounded_amp:
+            v = rng.random(modes)
+            sgn = np.where(rng.random(modes) < 0.5, -1.0, 1.0)
+            a = sgn * (0.5 + 0.5 * v) * (0.5 / np.sqrt(modes))
+        else:
+            a = rng.standard_normal(modes) * (0.5 / np.sqrt(modes))
         colf = np.cos(2 * np.pi * np.outer(x, f) / n + phi)     # n x modes
         rowf = np.cos(2 * np.pi * np.outer(y, g) / m + psi)     # m x modes
         F = offset + (rowf * a) @ colf.T
@@ -110,6 +128,17 @@ def batch_problems(count=512, seed=3, ms=(64, 128, 256, 512),
     return out
 
 
+def perturb_off_intersection(X, I, J, rel, seed):
+    """X plus Gaussian noise of standard deviation rel * std(X) on every entry
+    outside the intersection I x J (draw: default_rng(seed), shape of X).
+    The intersection, and with it its rank, is left unchanged."""
+    rng = np.random.default_rng(seed)
+    keep = np.ones(X.shape[1:], dtype=bool)
+    keep[np.asarray(I)[:, None], np.asarray(J)[None, :]] = False
+    noise = rng.standard_normal(X.shape) * (rel * float(np.std(X)))
+    return np.ascontiguousarray((X + noise * keep).astype(X.dtype))
+
+
 # The five workloads, by what they are.  `scale` shrinks a workload for tests.
 WORKLOADS = {
     "gauss256_rank10_fp64": dict(kind="lowrank", m=256, n=256, rank=10, seed=0,
@@ -124,8 +153,10 @@ WORKLOADS = {
     "batch512_uneven": dict(kind="batch", count=512, seed=3, dtype="f32"),
     "color1024x1536_rank60_masked": dict(kind="smooth", m=1024, n=1536, modes=20,
                                          seed=4, offset=0.0, clip=False, dtype="f32",
+                                         distinct=True, max_freq=96, bounded_amp=True,
                                          c=120, r=120, sampler="uniform", rank_cap=60,
-                                         rcond=1e-10, mask_seed=5),
+                                         rcond=1e-10, mask_seed=5, perturb_rel=1e-2,
+                                         perturb_seed=6),
 }
 
 
@@ -140,5 +171,6 @@ def make(name, m=None, n=None):
     if w["kind"] == "smooth":
         return smooth_color(m or w["m"], n or w["n"], w["modes"], w["seed"],
                             offset=w.get("offset", 0.5), clip=w.get("clip", True),
-                            dtype=dt)
+                            max_freq=w.get("max_freq", 16), distinct=w.get("distinct", False),
+                            bounded_amp=w.get("bounded_amp", False), dtype=dt)
     raise ValueError("batch workloads are built with batch_problems()")

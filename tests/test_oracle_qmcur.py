@@ -241,3 +241,12 @@ def test_residual_definition():
     relm, n2, d2 = O.residual(A, Z, mask)
     assert np.isclose(n2, np.sum(((A - Z) ** 2).sum(0) * mask))
     assert np.isclose(d2, np.sum((A ** 2).sum(0) * mask))
+
+
+def test_smooth_field_with_distinct_modes_has_rank_three_times_modes():
+    # the masked-workload recipe at reduced size: 20 distinct modes per channel
+    A = synth.smooth_color(256, 384, 20, 4, offset=0.0, clip=False, max_freq=96,
+                           distinct=True, bounded_amp=True, dtype=np.float64)
+    s = O.qsvd_values(A)
+    assert np.all(A[0] == 0)                        # pure quaternion
+    assert s[59] > 1e-8 * s[0] and s[60] < 1e-11 * s[0]
