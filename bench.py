@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--pinv", default="subspace", choices=["subspace", "jacobi"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "batch512_uneven"])
     return ap.parse_args()
 
 
@@ -404,10 +406,66 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """512 uneven problems decomposed per step by one replay of the batched
+    plan's CUDA graph (one launch per stage, FP32 GEMMs, FP32 Jacobi core)."""
+    import torch
+    from paper_2402_19147_gb300 import qmcur as Q
+    from paper_2402_19147_gb300 import synth
+    torch.cuda.set_device(0)
+    probs = synth.batch_problems(count=512, seed=3)
+    As = [torch.from_numpy(p["X"]).cuda() for p in probs]
+    stream = torch.cuda.current_stream()
+    B = Q.Batch(As, [p["c"] for p in probs], [p["r"] for p in probs],
+                [p["rank"] for p in probs], sampler=Q.SAMPLER_NORM, seed=0, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        B.run(stream)
+    torch.cuda.synchronize()
+    Q.check_status(B.status, "batch warm-up")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    for s, (e0, e1) in enumerate(evs):
+        flush.fill_(s & 0xff)
+        e0.record(stream)
+        B.run(stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    fl = sum(32.0 * (p["c"] * p["r"] * p["n"] + p["m"] * p["c"] * p["n"]) for p in probs)
+    byts = sum(16.0 * p["m"] * p["n"] for p in probs)
+    line = {"metric": METRIC, "value": 512 / (ms / 1e3), "unit": "decompositions/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch512_uneven", "problems": 512, "gemm_prec": "fp32",
+                       "pinv": "fp32-jacobi-per-cta", "graph": True,
+                       "gemm_tiles": [int(x) for x in host_tiles(Q, B)],
+                       "l2": "flushed between steps (256 MiB write)"},
+            "gemm_qtflops_per_step": fl / (ms / 1e3) / 1e12,
+            "input_gbs_per_step": byts / (ms / 1e3) / 1e9,
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def host_tiles(Q, B):
+    import ctypes
+    item = (ctypes.c_byte * 512)()
+    Q._check(Q.lib().qmcur_batch_view(B.handle, 0, ctypes.byref(item)), "qmcur_batch_view")
+    # gemm_tiles are the last two int32 of qmcur_batch_item
+    off = 4 * 8 + 4 * ctypes.sizeof(Q.QMat) + 2 * 8
+    return (ctypes.c_int32 * 2).from_buffer(item, off)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch512_uneven":
+        run_batch(args)
     else:
         run_ours(args)
 

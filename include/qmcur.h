@@ -254,7 +254,7 @@ qmcur_status qmcur_reconstruct_backward(const qmcur_qmat* A, const uint8_t* mask
                                         qmcur_qmat* dA, double* loss_out, void* workspace,
                                         size_t ws_bytes, int32_t* dev_status, cudaStream_t stream);
 
-/* Options of qmcur_decompose. */
+/* Options of qmcur_decompose and qmcur_batch_plan. */
 typedef struct {
   int32_t  sampler;      /* qmcur_sampler */
   int32_t  prec;         /* qmcur_prec of the reconstruction GEMMs */
@@ -283,6 +283,56 @@ qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qm
                              int32_t* rank_out, double* sigma_out, double* out3,
                              void* workspace, size_t ws_bytes, int32_t* dev_status,
                              cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Batched QMCUR: many independent problems of uneven shapes.
+ *
+ * qmcur_batch_plan builds a plan for `count` problems A[b] (host array of
+ * descriptors of F32 device matrices, m_b x n_b), with c[b] sampled columns,
+ * r[b] sampled rows and rank_cap[b] (NULL: no cap).  It allocates the
+ * outputs and scratch of all problems (the only allocating calls of the
+ * library are the plan and its destroy), runs the pipeline once, times the
+ * candidate tile shapes of the two grouped GEMMs on it and keeps the faster
+ * (the autotuner; choices are cached per problem-shape list), then captures
+ * the whole pipeline in a CUDA graph.  Limits: min(c,r) <= 80 and
+ * (max(c,r) + min(c,r)) * min(c,r) * 16 bytes <= 200 KiB (the pseudo-inverse
+ * of each intersection runs in one CTA's shared memory).
+ * Per problem b (Algorithm 1 with U = W^+): probabilities of opts->sampler,
+ * Philox draws with key opts->seed and stream_id = b, gathers, an FP32
+ * one-sided quaternion Jacobi QSVD of W truncated at opts->rcond and
+ * rank_cap[b], T = U R and the relative residual of C T (never written),
+ * all in FP32.  opts->prec and opts->pinv_method are not used.  dev_status
+ * (device int32, may be NULL) receives the first error; per-problem errors
+ * also land in info[2] of the problem.  The plan keeps the pointers it was
+ * given: A[b] and dev_status must stay valid until qmcur_batch_destroy.
+ * qmcur_batch_run replays the graph on `stream` (stream-ordered, no host
+ * synchronisation).  qmcur_batch_view returns the device buffers of one
+ * problem.  The paper decomposes one matrix at a time; batching is this
+ * library's addition.
+ */
+typedef struct {
+  double* col_p;          /* n_b probabilities of the columns */
+  double* row_p;          /* m_b probabilities of the rows    */
+  int32_t* J;             /* c_b sampled columns, ascending   */
+  int32_t* I;             /* r_b sampled rows, ascending      */
+  qmcur_qmat C, R, W, U;  /* F32: m x c, r x n, r x c, c x r  */
+  double* out3;           /* {rel, sum |a - z|^2, sum |a|^2}  */
+  int32_t* info;          /* {rank kept, Jacobi sweeps, status} */
+  int32_t gemm_tiles[2];  /* autotuned tile edge of the two grouped GEMMs */
+} qmcur_batch_item;
+
+qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t* c,
+                              const int64_t* r, const int32_t* rank_cap, const qmcur_opts* opts,
+                              void** plan, int32_t* dev_status, cudaStream_t stream);
+qmcur_status qmcur_batch_run(void* plan, cudaStream_t stream);
+qmcur_status qmcur_batch_view(const void* plan, int32_t index, qmcur_batch_item* out);
+/* Copy one output of problem `index` into dst (device or host memory, at
+ * least the output's size, stream-ordered): what = 0 col_p (n doubles),
+ * 1 row_p (m doubles), 2 J (c int32), 3 I (r int32), 4 C, 5 R, 6 W, 7 U
+ * (four contiguous F32 planes each), 8 out3 (3 doubles), 9 info (3 int32). */
+qmcur_status qmcur_batch_copy(const void* plan, int32_t index, int32_t what, void* dst,
+                              size_t dst_bytes, cudaStream_t stream);
+void qmcur_batch_destroy(void* plan);
 
 #ifdef __cplusplus
 }

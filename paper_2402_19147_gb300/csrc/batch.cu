@@ -1,0 +1,713 @@
+// Batched, grouped QMCUR: many independent problems of uneven shapes
+// decomposed with one launch per stage over a device problem table, the
+// whole pipeline captured once in a CUDA graph (qmcur_batch_plan) and
+// replayed (qmcur_batch_run).
+//
+// Stages (Algorithm 1 per problem, U = W^+ with the rank cap):
+//   k_batch_norms    one CTA per problem: column and row squared norms
+//                    (FP32 runs of 4 planes x 8 entries carried in FP64, fixed
+//                    order), ||A||_F^2, the probabilities (Sec. 3.1);
+//   k_batch_sample   one CTA per index set per problem (the Philox sampler of
+//                    the single-problem path, stream_id = problem index);
+//   k_batch_gather   C, R, W per problem;
+//   k_batch_jacobi   one CTA per problem: FP32 one-sided quaternion Jacobi on
+//                    the (<= 80 x 80) intersection held in shared memory, the
+//                    rcond / rank-cap truncation, U = V Sigma^-2 G^H;
+//   k_batch_gemm     grouped quaternion GEMMs over a flattened tile list
+//                    (T = U R, then Z = C T with the residual fused), tile
+//                    shape chosen per GEMM by timing the candidates at plan
+//                    time (the autotuner);
+//   k_batch_fold     per problem, the tile partials of the residual in order.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "sample_impl.cuh"
+
+namespace qmcur {
+
+constexpr int kBatchMaxCore = 80;      // largest min(r, c) held by k_batch_jacobi
+constexpr int64_t kBatchCoreSmem = 200 * 1024;   // bytes of G and V in shared memory
+
+struct BatchProblem {
+  QView A;                 // m x n, F32
+  int m, n, c, r, rank_cap;
+  double* col_p;           // n
+  double* row_p;           // m
+  int32_t* J;              // c
+  int32_t* I;              // r
+  QView C, R, W, U, T;     // F32: m x c, r x n, r x c, c x r, c x n
+  double* out3;            // {rel, num, den}
+  int32_t* info;           // {rank, sweeps, status}
+  int tile_base2;          // first tile of this problem in the second GEMM's list
+  int tiles2;              // its number of tiles
+};
+
+struct GTile {
+  int prob, m0, n0;
+};
+
+namespace {
+
+__device__ __forceinline__ float4 ldf4(const QView& v, int64_t i, int64_t j) {
+  const int64_t o = i * v.ld + j;
+  return make_float4(reinterpret_cast<const float*>(v.p[0])[o], reinterpret_cast<const float*>(v.p[1])[o],
+                     reinterpret_cast<const float*>(v.p[2])[o], reinterpret_cast<const float*>(v.p[3])[o]);
+}
+__device__ __forceinline__ void stf4(const QView& v, int64_t i, int64_t j, float4 q) {
+  const int64_t o = i * v.ld + j;
+  reinterpret_cast<float*>(v.p[0])[o] = q.x;
+  reinterpret_cast<float*>(v.p[1])[o] = q.y;
+  reinterpret_cast<float*>(v.p[2])[o] = q.z;
+  reinterpret_cast<float*>(v.p[3])[o] = q.w;
+}
+
+// ----------------------------------------------------------------- norms -
+__global__ void __launch_bounds__(256) k_batch_norms(const BatchProblem* probs, int norm,
+                                                     int32_t* status) {
+  const BatchProblem& P = probs[blockIdx.x];
+  const int m = P.m, n = P.n;
+  __shared__ double red[256];
+  // rows: one warp per row, lanes over columns, warp tree in FP64
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int i = warp; i < m; i += 8) {
+    double s = 0.0;
+    for (int j0 = 0; j0 < n; j0 += 32 * 8) {
+      float f = 0.f;
+      for (int j = j0 + lane; j < j0 + 32 * 8 && j < n; j += 32) {
+        const float4 a = ldf4(P.A, i, j);
+        f = fmaf(a.x, a.x, f); f = fmaf(a.y, a.y, f); f = fmaf(a.z, a.z, f); f = fmaf(a.w, a.w, f);
+      }
+      s += (double)f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) P.row_p[i] = s;
+  }
+  // columns: one thread per column, rows in order, FP32 runs of 8 rows
+  double tot = 0.0;
+  for (int j = threadIdx.x; j < n; j += 256) {
+    double s = 0.0;
+    for (int i0 = 0; i0 < m; i0 += 8) {
+      float f = 0.f;
+      for (int i = i0; i < i0 + 8 && i < m; ++i) {
+        const float4 a = ldf4(P.A, i, j);
+        f = fmaf(a.x, a.x, f); f = fmaf(a.y, a.y, f); f = fmaf(a.z, a.z, f); f = fmaf(a.w, a.w, f);
+      }
+      s += (double)f;
+    }
+    P.col_p[j] = s;
+    tot += s;
+  }
+  red[threadIdx.x] = tot;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double F = red[0];
+  if (threadIdx.x == 0) {
+    P.out3[2] = F;
+    int code = 0;
+    if (!isfinite(F)) code = QMCUR_ERR_NONFINITE;
+    else if (norm && F == 0.0) code = QMCUR_ERR_ZERO_NORM;
+    if (code) { P.info[2] = code; set_status(status, code); }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += 256) P.col_p[j] = norm ? P.col_p[j] / F : 1.0 / (double)n;
+  for (int i = threadIdx.x; i < m; i += 256) P.row_p[i] = norm ? P.row_p[i] / F : 1.0 / (double)m;
+}
+
+// ---------------------------------------------------------------- sample -
+__global__ void __launch_bounds__(kSampleThreads)
+k_batch_sample(const BatchProblem* probs, SampleArgs base, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const int b = blockIdx.x / 2, set = blockIdx.x % 2;
+  const BatchProblem& P = probs[b];
+  SampleArgs a = base;
+  a.prob[0] = P.col_p; a.prob[1] = P.row_p;
+  a.N[0] = P.n; a.N[1] = P.m;
+  a.count[0] = P.c; a.count[1] = P.r;
+  a.out[0] = P.J; a.out[1] = P.I;
+  a.P[0] = a.P[1] = nullptr;
+  a.stream_id = (uint32_t)b;
+  a.max_attempts[0] = 64 * (int64_t)P.c + 1024;
+  a.max_attempts[1] = 64 * (int64_t)P.r + 1024;
+  a.status = status;
+  a.attempts_out = nullptr;
+  sample_one_set(a, set, 1, dyn);
+}
+
+// ---------------------------------------------------------------- gather -
+__global__ void k_batch_gather(const BatchProblem* probs) {
+  const BatchProblem& P = probs[blockIdx.y];
+  const int64_t nc = (int64_t)P.m * P.c, nr = (int64_t)P.r * P.n, nw = (int64_t)P.r * P.c;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nc + nr + nw;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i, j, si, sj;
+    const QView* out;
+    if (e < nc) { i = e / P.c; j = e % P.c; si = i; sj = P.J[j]; out = &P.C; }
+    else if (e < nc + nr) { const int64_t f = e - nc; i = f / P.n; j = f % P.n; si = P.I[i]; sj = j; out = &P.R; }
+    else { const int64_t f = e - nc - nr; i = f / P.c; j = f % P.c; si = P.I[i]; sj = P.J[j]; out = &P.W; }
+    const bool in = si >= 0 && si < P.m && sj >= 0 && sj < P.n;
+    stf4(*out, i, j, in ? ldf4(P.A, si, sj) : make_float4(0.f, 0.f, 0.f, 0.f));
+  }
+}
+
+// ------------------------------------------------- FP32 Jacobi per problem -
+__device__ __forceinline__ void circle(int N, int step, int p, int& a, int& b) {
+  const int M = N - 1;
+  if (p == 0) { a = M; b = step % M; }
+  else { a = (step + p) % M; b = (step - p + M) % M; }
+}
+
+__global__ void __launch_bounds__(1024) k_batch_jacobi(const BatchProblem* probs, double rcond,
+                                                       int max_sweeps) {
+  extern __shared__ float4 js[];
+  const BatchProblem& P = probs[blockIdx.x];
+  const int r = P.r, c = P.c;
+  const bool tr = c > r;                 // work on W^H when W is wide
+  const int nr = tr ? c : r, nc = tr ? r : c;
+  float4* G = js;                        // G[j * nr + i], column j contiguous
+  float4* V = js + nr * nc;              // V[j * nc + i]
+  float* sig = reinterpret_cast<float*>(V + nc * nc);
+  int* pos = reinterpret_cast<int*>(sig + nc);
+  __shared__ int rotated, keep_cnt;
+  for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+    const int j = e / nr, i = e % nr;
+    float4 q = tr ? ldf4(P.W, j, i) : ldf4(P.W, i, j);
+    if (tr) { q.y = -q.y; q.z = -q.z; q.w = -q.w; }
+    G[e] = q;
+  }
+  for (int e = threadIdx.x; e < nc * nc; e += blockDim.x)
+    V[e] = make_float4((e / nc == e % nc) ? 1.f : 0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  const float tol = sqrtf((float)nr) * 0x1.0p-23f;
+  const int N = nc + (nc & 1), npairs = N / 2;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    __syncthreads();                     // every thread has read the last flag
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int step = 0; step < N - 1; ++step) {
+      for (int p = warp; p < npairs; p += nwarps) {
+        int a, b;
+        circle(N, step, p, a, b);
+        if (a >= nc || b >= nc) continue;
+        float al = 0.f, be = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+        for (int i = lane; i < nr; i += 32) {
+          const float4 x = G[a * nr + i], y = G[b * nr + i];
+          al += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+          be += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
+          g0 += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+          g1 += x.x * y.y - x.y * y.x - x.z * y.w + x.w * y.z;
+          g2 += x.x * y.z + x.y * y.w - x.z * y.x - x.w * y.y;
+          g3 += x.x * y.w - x.y * y.z + x.z * y.y - x.w * y.x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+          g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+          g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+          g3 += __shfl_xor_sync(0xffffffffu, g3, o);
+        }
+        const float gam = sqrtf(g0 * g0 + g1 * g1 + g2 * g2 + g3 * g3);
+        if (!(al > 0.f) || !(be > 0.f) || !(gam > tol * sqrtf(al) * sqrtf(be)) ||
+            fminf(al, be) < tol * tol * fmaxf(al, be))
+          continue;
+        if (lane == 0) rotated = 1;
+        const float zeta = (be - al) / (2.f * gam);
+        const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        const float cs = 1.f / sqrtf(1.f + t * t), sn = cs * t;
+        const float w0 = g0 / gam, w1 = -g1 / gam, w2 = -g2 / gam, w3 = -g3 / gam;
+        for (int mat = 0; mat < 2; ++mat) {
+          float4* X = mat == 0 ? G : V;
+          const int len = mat == 0 ? nr : nc;
+          for (int i = lane; i < len; i += 32) {
+            const float4 x = X[a * len + i], q = X[b * len + i];
+            const float4 y = make_float4(q.x * w0 - q.y * w1 - q.z * w2 - q.w * w3,
+                                         q.x * w1 + q.y * w0 + q.z * w3 - q.w * w2,
+                                         q.x * w2 - q.y * w3 + q.z * w0 + q.w * w1,
+                                         q.x * w3 + q.y * w2 - q.z * w1 + q.w * w0);
+            X[a * len + i] = make_float4(cs * x.x - sn * y.x, cs * x.y - sn * y.y,
+                                         cs * x.z - sn * y.z, cs * x.w - sn * y.w);
+            X[b * len + i] = make_float4(sn * x.x + cs * y.x, sn * x.y + cs * y.y,
+                                         sn * x.z + cs * y.z, sn * x.w + cs * y.w);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) { ++sweep; break; }
+  }
+  // singular values, order, truncation
+  for (int j = warp; j < nc; j += nwarps) {
+    float s = 0.f;
+    for (int i = lane; i < nr; i += 32) {
+      const float4 q = G[j * nr + i];
+      s += q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sig[j] = sqrtf(s);
+  }
+  if (threadIdx.x == 0) keep_cnt = 0;
+  __syncthreads();
+  float smax = 0.f;
+  for (int j = 0; j < nc; ++j) smax = fmaxf(smax, sig[j]);
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+    int ps = 0;
+    for (int i = 0; i < nc; ++i) ps += (sig[i] > sig[j]) || (sig[i] == sig[j] && i < j);
+    pos[j] = ps;
+    if (smax > 0.f && (double)sig[j] > rcond * (double)smax) atomicAdd(&keep_cnt, 1);
+  }
+  __syncthreads();
+  int k = keep_cnt;
+  if (P.rank_cap > 0 && k > P.rank_cap) k = P.rank_cap;
+  // U[a][b] = sum_{kept j} X[a][j] sigma_j^-2 conj(Y[b][j]); (X, Y) = (V, G) or (G, V)
+  for (int e = threadIdx.x; e < c * r; e += blockDim.x) {
+    const int ai = e / r, bi = e % r;
+    float u0 = 0.f, u1 = 0.f, u2 = 0.f, u3 = 0.f;
+    for (int j = 0; j < nc; ++j) {
+      if (pos[j] >= k) continue;
+      const float w = 1.f / (sig[j] * sig[j]);
+      const float4 x = tr ? G[j * nr + ai] : V[j * nc + ai];
+      const float4 y = tr ? V[j * nc + bi] : G[j * nr + bi];
+      u0 += w * (x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w);
+      u1 += w * (-x.x * y.y + x.y * y.x - x.z * y.w + x.w * y.z);
+      u2 += w * (-x.x * y.z + x.y * y.w + x.z * y.x - x.w * y.y);
+      u3 += w * (-x.x * y.w - x.y * y.z + x.z * y.y + x.w * y.x);
+    }
+    stf4(P.U, ai, bi, make_float4(u0, u1, u2, u3));
+  }
+  if (threadIdx.x == 0) { P.info[0] = k; P.info[1] = sweep; }
+}
+
+// ------------------------------------------------------- grouped GEMMs ---
+// Z = X Y per tile of a problem; which == 0: T = U R (stored), which == 1:
+// C T with the residual against A fused (per-tile FP64 partials).
+template <int BMQ, int BNQ, int TMQ, int TNQ>
+__global__ void __launch_bounds__(256) k_batch_gemm(const BatchProblem* probs, const GTile* tiles,
+                                                    int which, double* partial) {
+  constexpr int BKQ = 8;
+  constexpr int TX = BNQ / TNQ;                 // threads along n
+  static_assert((BMQ / TMQ) * (BNQ / TNQ) == 256, "256 threads");
+  const GTile tl = tiles[blockIdx.x];
+  const BatchProblem& P = probs[tl.prob];
+  const QView& X = which == 0 ? P.U : P.C;
+  const QView& Y = which == 0 ? P.R : P.T;
+  const int M = which == 0 ? P.c : P.m, N = P.n, K = which == 0 ? P.r : P.c;
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  __shared__ float xs[4][BKQ][BMQ];
+  __shared__ float ys[4][BKQ][BNQ];
+  float acc[TMQ][TNQ][4];
+#pragma unroll
+  for (int i = 0; i < TMQ; ++i)
+#pragma unroll
+    for (int j = 0; j < TNQ; ++j)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[i][j][t] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += BKQ) {
+    for (int e = tid; e < BMQ * BKQ; e += 256) {
+      const int mm = e / BKQ, kk = e % BKQ;
+      const int gi = tl.m0 + mm, gk = k0 + kk;
+      const float4 q = (gi < M && gk < K) ? ldf4(X, gi, gk) : make_float4(0.f, 0.f, 0.f, 0.f);
+      xs[0][kk][mm] = q.x; xs[1][kk][mm] = q.y; xs[2][kk][mm] = q.z; xs[3][kk][mm] = q.w;
+    }
+    for (int e = tid; e < BNQ * BKQ; e += 256) {
+      const int kk = e / BNQ, nn = e % BNQ;
+      const int gk = k0 + kk, gj = tl.n0 + nn;
+      const float4 q = (gk < K && gj < N) ? ldf4(Y, gk, gj) : make_float4(0.f, 0.f, 0.f, 0.f);
+      ys[0][kk][nn] = q.x; ys[1][kk][nn] = q.y; ys[2][kk][nn] = q.z; ys[3][kk][nn] = q.w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BKQ; ++kk) {
+      float a[TMQ][4], b[TNQ][4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+#pragma unroll
+        for (int i = 0; i < TMQ; ++i) a[i][t] = xs[t][kk][ty * TMQ + i];
+#pragma unroll
+        for (int j = 0; j < TNQ; ++j) b[j][t] = ys[t][kk][tx * TNQ + j];
+      }
+#pragma unroll
+      for (int i = 0; i < TMQ; ++i)
+#pragma unroll
+        for (int j = 0; j < TNQ; ++j) {
+          float* z = acc[i][j];
+          const float* x = a[i];
+          const float* y = b[j];
+          z[0] = fmaf(x[0], y[0], z[0]); z[0] = fmaf(-x[1], y[1], z[0]);
+          z[0] = fmaf(-x[2], y[2], z[0]); z[0] = fmaf(-x[3], y[3], z[0]);
+          z[1] = fmaf(x[0], y[1], z[1]); z[1] = fmaf(x[1], y[0], z[1]);
+          z[1] = fmaf(x[2], y[3], z[1]); z[1] = fmaf(-x[3], y[2], z[1]);
+          z[2] = fmaf(x[0], y[2], z[2]); z[2] = fmaf(-x[1], y[3], z[2]);
+          z[2] = fmaf(x[2], y[0], z[2]); z[2] = fmaf(x[3], y[1], z[2]);
+          z[3] = fmaf(x[0], y[3], z[3]); z[3] = fmaf(x[1], y[2], z[3]);
+          z[3] = fmaf(-x[2], y[1], z[3]); z[3] = fmaf(x[3], y[0], z[3]);
+        }
+    }
+    __syncthreads();
+  }
+  if (which == 0) {
+#pragma unroll
+    for (int i = 0; i < TMQ; ++i)
+#pragma unroll
+      for (int j = 0; j < TNQ; ++j) {
+        const int gi = tl.m0 + ty * TMQ + i, gj = tl.n0 + tx * TNQ + j;
+        if (gi < M && gj < N) stf4(P.T, gi, gj, make_float4(acc[i][j][0], acc[i][j][1], acc[i][j][2], acc[i][j][3]));
+      }
+    return;
+  }
+  double num = 0.0, den = 0.0;
+#pragma unroll
+  for (int i = 0; i < TMQ; ++i) {
+    float rn = 0.f, rd = 0.f;
+#pragma unroll
+    for (int j = 0; j < TNQ; ++j) {
+      const int gi = tl.m0 + ty * TMQ + i, gj = tl.n0 + tx * TNQ + j;
+      if (gi < M && gj < N) {
+        const float4 av = ldf4(P.A, gi, gj);
+        const float d0 = av.x - acc[i][j][0], d1 = av.y - acc[i][j][1];
+        const float d2 = av.z - acc[i][j][2], d3 = av.w - acc[i][j][3];
+        rn += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+        rd += av.x * av.x + av.y * av.y + av.z * av.z + av.w * av.w;
+      }
+    }
+    num += (double)rn;
+    den += (double)rd;
+  }
+  __shared__ double red[2][256];
+  red[0][tid] = num;
+  red[1][tid] = den;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w) { red[0][tid] += red[0][tid + w]; red[1][tid] += red[1][tid + w]; }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    partial[2 * blockIdx.x] = red[0][0];
+    partial[2 * blockIdx.x + 1] = red[1][0];
+  }
+}
+
+__global__ void k_batch_fold(const BatchProblem* probs, const double* partial) {
+  const BatchProblem& P = probs[blockIdx.x];
+  if (threadIdx.x != 0) return;
+  double num = 0.0, den = 0.0;
+  for (int t = 0; t < P.tiles2; ++t) {
+    num += partial[2 * (P.tile_base2 + t)];
+    den += partial[2 * (P.tile_base2 + t) + 1];
+  }
+  P.out3[0] = den > 0.0 ? sqrt(num / den) : __longlong_as_double(0x7ff8000000000000ll);
+  P.out3[1] = num;
+  P.out3[2] = den;
+}
+
+struct TileCfg {
+  int bm, bn;
+};
+constexpr TileCfg kCfgs[2] = {{64, 64}, {32, 32}};
+
+void launch_batch_gemm(int cfg, const BatchProblem* probs, const GTile* tiles, int ntiles, int which,
+                       double* partial, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  if (cfg == 0) k_batch_gemm<64, 64, 4, 4><<<ntiles, 256, 0, st>>>(probs, tiles, which, partial);
+  else k_batch_gemm<32, 32, 2, 2><<<ntiles, 256, 0, st>>>(probs, tiles, which, partial);
+}
+
+std::vector<GTile> make_tiles(const std::vector<BatchProblem>& ps, int which, int cfg,
+                              std::vector<int>* base = nullptr, std::vector<int>* count = nullptr) {
+  std::vector<GTile> t;
+  for (size_t b = 0; b < ps.size(); ++b) {
+    const int M = which == 0 ? ps[b].c : ps[b].m, N = ps[b].n;
+    if (base) base->push_back((int)t.size());
+    int cnt = 0;
+    for (int m0 = 0; m0 < M; m0 += kCfgs[cfg].bm)
+      for (int n0 = 0; n0 < N; n0 += kCfgs[cfg].bn) { t.push_back(GTile{(int)b, m0, n0}); ++cnt; }
+    if (count) count->push_back(cnt);
+  }
+  return t;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- plan ----
+struct BatchPlan {
+  int count = 0;
+  std::vector<BatchProblem> host;
+  BatchProblem* dprobs = nullptr;
+  GTile* dtiles1 = nullptr;
+  GTile* dtiles2 = nullptr;
+  int ntiles1 = 0, ntiles2 = 0, cfg1 = 0, cfg2 = 0;
+  double* partial = nullptr;
+  void* arena = nullptr;
+  int32_t* status = nullptr;
+  size_t jac_smem = 0, samp_smem = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  qmcur_opts opts{};
+};
+
+static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st) {
+  const int norm = p->opts.sampler == QMCUR_SAMPLER_NORM;
+  k_batch_norms<<<p->count, 256, 0, st>>>(p->dprobs, norm, p->status);
+  SampleArgs base{};
+  base.seed = p->opts.seed;
+  base.norm = norm;
+  k_batch_sample<<<2 * p->count, kSampleThreads, p->samp_smem, st>>>(p->dprobs, base, p->status);
+  k_batch_gather<<<dim3(64, p->count), 256, 0, st>>>(p->dprobs);
+  k_batch_jacobi<<<p->count, 1024, p->jac_smem, st>>>(
+      p->dprobs, p->opts.rcond, p->opts.max_sweeps > 0 ? p->opts.max_sweeps : 30);
+  launch_batch_gemm(p->cfg1, p->dprobs, p->dtiles1, p->ntiles1, 0, nullptr, st);
+  launch_batch_gemm(p->cfg2, p->dprobs, p->dtiles2, p->ntiles2, 1, p->partial, st);
+  k_batch_fold<<<p->count, 32, 0, st>>>(p->dprobs, p->partial);
+  return cuda_ok(cudaGetLastError());
+}
+
+// Time the candidate tile shapes of one grouped GEMM on the real batch.
+static int autotune(BatchPlan* p, int which, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<std::vector<int>, int> cache;
+  std::vector<int> key{which};
+  for (auto& b : p->host) { key.push_back(which == 0 ? b.c : b.m); key.push_back(b.n); key.push_back(b.c); }
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  float best = 1e30f;
+  int best_cfg = 0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int cfg = 0; cfg < 2; ++cfg) {
+    std::vector<GTile> t = make_tiles(p->host, which, cfg);
+    GTile* dt = nullptr;
+    if (cudaMalloc(&dt, t.size() * sizeof(GTile)) != cudaSuccess) continue;
+    cudaMemcpyAsync(dt, t.data(), t.size() * sizeof(GTile), cudaMemcpyHostToDevice, st);
+    double* part = nullptr;
+    cudaMalloc(&part, 2 * t.size() * sizeof(double));
+    launch_batch_gemm(cfg, p->dprobs, dt, (int)t.size(), which, part, st);   // warm
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 3; ++rep) launch_batch_gemm(cfg, p->dprobs, dt, (int)t.size(), which, part, st);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_cfg = cfg; }
+    cudaFree(part);
+    cudaFree(dt);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = best_cfg;
+  return best_cfg;
+}
+
+static void free_plan(BatchPlan* p) {
+  if (p == nullptr) return;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  cudaFree(p->dprobs);
+  cudaFree(p->dtiles1);
+  cudaFree(p->dtiles2);
+  cudaFree(p->partial);
+  cudaFree(p->arena);
+  delete p;
+}
+
+}  // namespace qmcur
+
+using namespace qmcur;
+
+extern "C" {
+
+qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t* c, const int64_t* r,
+                              const int32_t* rank_cap, const qmcur_opts* opts, void** plan_out,
+                              int32_t* dev_status, cudaStream_t stream) {
+  if (count < 1 || A == nullptr || c == nullptr || r == nullptr || opts == nullptr || plan_out == nullptr)
+    return QMCUR_ERR_INVALID_ARG;
+  if (opts->sampler != QMCUR_SAMPLER_NORM && opts->sampler != QMCUR_SAMPLER_UNIFORM) return QMCUR_ERR_INVALID_ARG;
+  for (int b = 0; b < count; ++b) {
+    if (!valid_qmat(&A[b], true, false)) return QMCUR_ERR_INVALID_ARG;
+    if (c[b] < 1 || c[b] > A[b].cols || r[b] < 1 || r[b] > A[b].rows) return QMCUR_ERR_INVALID_ARG;
+    {
+      // the Jacobi core keeps G (n_r x n_c) and V (n_c x n_c) in shared memory
+      const int64_t nr = c[b] > r[b] ? c[b] : r[b], nc = c[b] < r[b] ? c[b] : r[b];
+      if (nc > kBatchMaxCore || (nr * nc + nc * nc) * 16 > kBatchCoreSmem) return QMCUR_ERR_UNSUPPORTED;
+    }
+    if (A[b].rows > (1 << 20) || A[b].cols > 48 * 1024) return QMCUR_ERR_UNSUPPORTED;
+  }
+  BatchPlan* p = new BatchPlan();
+  p->count = count;
+  p->opts = *opts;
+  p->status = dev_status;
+  // one arena: per problem col_p, row_p, J, I, C, R, W, U, T, out3, info
+  std::vector<size_t> off;
+  size_t total = 0;
+  auto take = [&](size_t bytes) { size_t o = total; total += align_up(bytes, 256); return o; };
+  struct Offs { size_t cp, rp, J, I, C, R, W, U, T, o3, info; };
+  std::vector<Offs> os(count);
+  size_t max_rc = 0, max_nm = 0;
+  for (int b = 0; b < count; ++b) {
+    const int64_t m = A[b].rows, n = A[b].cols;
+    Offs& o = os[b];
+    o.cp = take(8 * n); o.rp = take(8 * m); o.J = take(4 * c[b]); o.I = take(4 * r[b]);
+    o.C = take(16 * m * c[b]); o.R = take(16 * r[b] * n); o.W = take(16 * r[b] * c[b]);
+    o.U = take(16 * c[b] * r[b]); o.T = take(16 * c[b] * n); o.o3 = take(24); o.info = take(12);
+    const int64_t nr = c[b] > r[b] ? c[b] : r[b], nc = c[b] < r[b] ? c[b] : r[b];
+    max_rc = std::max(max_rc, (size_t)(nr * nc + nc * nc));
+    max_nm = std::max(max_nm, (size_t)(n > m ? n : m));
+  }
+  if (cudaMalloc(&p->arena, total) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
+  cudaMemsetAsync(p->arena, 0, total, stream);
+  char* base = static_cast<char*>(p->arena);
+  auto q = [&](size_t o, int64_t rows, int64_t cols) {
+    QView v;
+    for (int t = 0; t < 4; ++t) v.p[t] = base + o + (size_t)t * rows * cols * 4;
+    v.rows = rows; v.cols = cols; v.ld = cols; v.dtype = QMCUR_F32;
+    return v;
+  };
+  p->host.resize(count);
+  for (int b = 0; b < count; ++b) {
+    BatchProblem& P = p->host[b];
+    const Offs& o = os[b];
+    P.A = view(&A[b]);
+    P.m = (int)A[b].rows; P.n = (int)A[b].cols; P.c = (int)c[b]; P.r = (int)r[b];
+    P.rank_cap = rank_cap ? rank_cap[b] : 0;
+    P.col_p = reinterpret_cast<double*>(base + o.cp);
+    P.row_p = reinterpret_cast<double*>(base + o.rp);
+    P.J = reinterpret_cast<int32_t*>(base + o.J);
+    P.I = reinterpret_cast<int32_t*>(base + o.I);
+    P.C = q(o.C, P.m, P.c); P.R = q(o.R, P.r, P.n); P.W = q(o.W, P.r, P.c);
+    P.U = q(o.U, P.c, P.r); P.T = q(o.T, P.c, P.n);
+    P.out3 = reinterpret_cast<double*>(base + o.o3);
+    P.info = reinterpret_cast<int32_t*>(base + o.info);
+  }
+  if (cudaMalloc(&p->dprobs, count * sizeof(BatchProblem)) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
+  cudaMemcpyAsync(p->dprobs, p->host.data(), count * sizeof(BatchProblem), cudaMemcpyHostToDevice, stream);
+  p->jac_smem = max_rc * sizeof(float4) + (size_t)kBatchMaxCore * 8 + 64;
+  p->samp_smem = ((max_nm + 31) / 32 * 4 + 15) / 16 * 16 + max_nm * 8;
+  if (cudaFuncSetAttribute(k_batch_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->jac_smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_batch_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->samp_smem) !=
+          cudaSuccess) {
+    free_plan(p);
+    return QMCUR_ERR_CUDA;
+  }
+  // first pass (un-captured): fills T and the operands so that the GEMM
+  // candidates can be timed on real data
+  {
+    p->cfg1 = p->cfg2 = 0;
+    std::vector<GTile> t1 = make_tiles(p->host, 0, 0), t2 = make_tiles(p->host, 1, 0);
+    cudaMalloc(&p->dtiles1, t1.size() * sizeof(GTile));
+    cudaMalloc(&p->dtiles2, t2.size() * sizeof(GTile));
+    cudaMalloc(&p->partial, 2 * t2.size() * sizeof(double));
+    cudaMemcpyAsync(p->dtiles1, t1.data(), t1.size() * sizeof(GTile), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(p->dtiles2, t2.data(), t2.size() * sizeof(GTile), cudaMemcpyHostToDevice, stream);
+    p->ntiles1 = (int)t1.size();
+    p->ntiles2 = (int)t2.size();
+    std::vector<int> b2, c2;
+    make_tiles(p->host, 1, 0, &b2, &c2);
+    for (int b = 0; b < count; ++b) { p->host[b].tile_base2 = b2[b]; p->host[b].tiles2 = c2[b]; }
+    cudaMemcpyAsync(p->dprobs, p->host.data(), count * sizeof(BatchProblem), cudaMemcpyHostToDevice, stream);
+    qmcur_status s = enqueue_batch(p, stream);
+    if (s != QMCUR_OK) { free_plan(p); return s; }
+  }
+  // autotune the two grouped GEMMs, rebuild their tile lists
+  p->cfg1 = autotune(p, 0, stream);
+  p->cfg2 = autotune(p, 1, stream);
+  {
+    cudaFree(p->dtiles1); cudaFree(p->dtiles2); cudaFree(p->partial);
+    std::vector<int> b2, c2;
+    std::vector<GTile> t1 = make_tiles(p->host, 0, p->cfg1), t2 = make_tiles(p->host, 1, p->cfg2, &b2, &c2);
+    for (int b = 0; b < count; ++b) { p->host[b].tile_base2 = b2[b]; p->host[b].tiles2 = c2[b]; }
+    if (cudaMalloc(&p->dtiles1, t1.size() * sizeof(GTile)) != cudaSuccess ||
+        cudaMalloc(&p->dtiles2, t2.size() * sizeof(GTile)) != cudaSuccess ||
+        cudaMalloc(&p->partial, 2 * t2.size() * sizeof(double)) != cudaSuccess) {
+      free_plan(p);
+      return QMCUR_ERR_CUDA;
+    }
+    cudaMemcpyAsync(p->dtiles1, t1.data(), t1.size() * sizeof(GTile), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(p->dtiles2, t2.data(), t2.size() * sizeof(GTile), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(p->dprobs, p->host.data(), count * sizeof(BatchProblem), cudaMemcpyHostToDevice, stream);
+    p->ntiles1 = (int)t1.size();
+    p->ntiles2 = (int)t2.size();
+  }
+  // capture the whole pipeline once, on a private stream (the caller's may be
+  // the legacy default stream, which cannot be captured)
+  if (cudaStreamSynchronize(stream) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
+  cudaStream_t cap = nullptr;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaStreamDestroy(cap);
+    free_plan(p);
+    return QMCUR_ERR_CUDA;
+  }
+  qmcur_status s = enqueue_batch(p, cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(cap, &g);
+  cudaStreamDestroy(cap);
+  if (s != QMCUR_OK || ec != cudaSuccess || g == nullptr) { if (g) cudaGraphDestroy(g); free_plan(p); return s != QMCUR_OK ? s : QMCUR_ERR_CUDA; }
+  p->graph = g;
+  if (cudaGraphInstantiate(&p->exec, g, 0) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
+  *plan_out = p;
+  return QMCUR_OK;
+}
+
+qmcur_status qmcur_batch_run(void* plan, cudaStream_t stream) {
+  if (plan == nullptr) return QMCUR_ERR_INVALID_ARG;
+  return cuda_ok(cudaGraphLaunch(static_cast<BatchPlan*>(plan)->exec, stream));
+}
+
+qmcur_status qmcur_batch_view(const void* plan, int32_t index, qmcur_batch_item* out) {
+  const BatchPlan* p = static_cast<const BatchPlan*>(plan);
+  if (p == nullptr || out == nullptr || index < 0 || index >= p->count) return QMCUR_ERR_INVALID_ARG;
+  const BatchProblem& P = p->host[index];
+  auto toq = [](const QView& v) {
+    qmcur_qmat q;
+    for (int t = 0; t < 4; ++t) q.plane[t] = v.p[t];
+    q.rows = v.rows; q.cols = v.cols; q.ld = v.ld; q.dtype = v.dtype; q.reserved = 0;
+    return q;
+  };
+  out->col_p = P.col_p; out->row_p = P.row_p; out->J = P.J; out->I = P.I;
+  out->C = toq(P.C); out->R = toq(P.R); out->W = toq(P.W); out->U = toq(P.U);
+  out->out3 = P.out3; out->info = P.info;
+  out->gemm_tiles[0] = kCfgs[p->cfg1].bm; out->gemm_tiles[1] = kCfgs[p->cfg2].bm;
+  return QMCUR_OK;
+}
+
+qmcur_status qmcur_batch_copy(const void* plan, int32_t index, int32_t what, void* dst,
+                              size_t dst_bytes, cudaStream_t stream) {
+  const BatchPlan* p = static_cast<const BatchPlan*>(plan);
+  if (p == nullptr || dst == nullptr || index < 0 || index >= p->count) return QMCUR_ERR_INVALID_ARG;
+  const BatchProblem& P = p->host[index];
+  const void* src = nullptr;
+  size_t bytes = 0;
+  switch (what) {
+    case 0: src = P.col_p; bytes = 8 * (size_t)P.n; break;
+    case 1: src = P.row_p; bytes = 8 * (size_t)P.m; break;
+    case 2: src = P.J; bytes = 4 * (size_t)P.c; break;
+    case 3: src = P.I; bytes = 4 * (size_t)P.r; break;
+    case 4: src = P.C.p[0]; bytes = 16 * (size_t)P.m * P.c; break;
+    case 5: src = P.R.p[0]; bytes = 16 * (size_t)P.r * P.n; break;
+    case 6: src = P.W.p[0]; bytes = 16 * (size_t)P.r * P.c; break;
+    case 7: src = P.U.p[0]; bytes = 16 * (size_t)P.c * P.r; break;
+    case 8: src = P.out3; bytes = 24; break;
+    case 9: src = P.info; bytes = 12; break;
+    default: return QMCUR_ERR_INVALID_ARG;
+  }
+  if (dst_bytes < bytes) return QMCUR_ERR_INVALID_ARG;
+  return cuda_ok(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, stream));
+}
+
+void qmcur_batch_destroy(void* plan) { free_plan(static_cast<BatchPlan*>(plan)); }
+
+}  // extern "C"

@@ -70,6 +70,11 @@ SIGNATURES = {
     "qmcur_backward_workspace_size": (_SZ, [_I64, _I64, _I64, _I64]),
     "qmcur_reconstruct_backward": (_I32, [_QP, _P, _P, _P, _QP, _QP, _QP, _QP, _D, _QP, _P, _P,
                                           _SZ, _P, _P]),
+    "qmcur_batch_plan": (_I32, [_I32, _QP, _P, _P, _P, ctypes.POINTER(Opts), _P, _P, _P]),
+    "qmcur_batch_run": (_I32, [_P, _P]),
+    "qmcur_batch_view": (_I32, [_P, _I32, _P]),
+    "qmcur_batch_copy": (_I32, [_P, _I32, _I32, _P, _SZ, _P]),
+    "qmcur_batch_destroy": (None, [_P]),
     "qmcur_decompose": (_I32, [_QP, _I64, _I64, ctypes.POINTER(Opts), _P, _P, _P, _P,
                                _QP, _QP, _QP, _QP, _P, _P, _P, _P, _SZ, _P, _P]),
 }
@@ -238,6 +243,58 @@ class MaskedCURLoss(torch.autograd.Function):
         st = status_tensor(A.device)
         reconstruct_backward(A, ctx.mask, J, I, C, U, R, W, float(g), dA, status=st)
         return dA, None, None, None, None, None, None
+
+
+class Batch:
+    """A batched QMCUR plan (qmcur_batch_plan): problems As[b] ((4, m_b, n_b)
+    float32 CUDA tensors), cs[b] columns, rs[b] rows, rank_caps[b]; one graph
+    replay per run().  get(b, what) copies one output into a new tensor."""
+
+    WHAT = {"col_p": (0, torch.float64), "row_p": (1, torch.float64), "J": (2, torch.int32),
+            "I": (3, torch.int32), "C": (4, torch.float32), "R": (5, torch.float32),
+            "W": (6, torch.float32), "U": (7, torch.float32), "out3": (8, torch.float64),
+            "info": (9, torch.int32)}
+
+    def __init__(self, As, cs, rs, rank_caps=None, sampler=SAMPLER_NORM, seed=0, rcond=1e-10,
+                 max_sweeps=0, stream=None):
+        self.As = list(As)
+        n = len(self.As)
+        self.shapes = [(a.shape[1], a.shape[2], int(c), int(r)) for a, c, r in zip(self.As, cs, rs)]
+        descs = (QMat * n)(*[qmat(a) for a in self.As])
+        carr = (ctypes.c_int64 * n)(*[int(x) for x in cs])
+        rarr = (ctypes.c_int64 * n)(*[int(x) for x in rs])
+        kap = None if rank_caps is None else (ctypes.c_int32 * n)(*[int(x) for x in rank_caps])
+        o = Opts(sampler, PREC_FP32, seed, 0, 0, rcond, 0, max_sweeps, 0, 0)
+        self.status = status_tensor(self.As[0].device)
+        self.handle = ctypes.c_void_p()
+        _check(lib().qmcur_batch_plan(n, descs, carr, rarr, kap, ctypes.byref(o),
+                                      ctypes.byref(self.handle), _ptr(self.status),
+                                      _stream(stream)), "qmcur_batch_plan")
+
+    def run(self, stream=None):
+        _check(lib().qmcur_batch_run(self.handle, _stream(stream)), "qmcur_batch_run")
+
+    def get(self, b, what, stream=None):
+        code, dt = self.WHAT[what]
+        m, n, c, r = self.shapes[b]
+        shape = {"col_p": (n,), "row_p": (m,), "J": (c,), "I": (r,), "C": (4, m, c),
+                 "R": (4, r, n), "W": (4, r, c), "U": (4, c, r), "out3": (3,), "info": (3,)}[what]
+        out = torch.empty(shape, dtype=dt, device=self.As[0].device)
+        _check(lib().qmcur_batch_copy(self.handle, b, code, _ptr(out),
+                                      out.numel() * out.element_size(), _stream(stream)),
+               "qmcur_batch_copy")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value is not None:
+            lib().qmcur_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Decomposition:
