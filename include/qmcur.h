@@ -91,7 +91,7 @@ typedef enum {
   QMCUR_PINV_JACOBI_FP64 = 0,  /* full QSVD by FP64 one-sided Jacobi: any rank
                                   rule, FP64 accuracy, slow on GB300's FP64 rate */
   QMCUR_PINV_SUBSPACE_FP32 = 1 /* rank_cap >= 1 required (k = min(rank_cap, r, c)
-                                  <= 112): top-k subspaces by two FP32 subspace
+                                  <= 100): top-k subspaces by two FP32 subspace
                                   iterations with CholeskyQR2, U = P R^-1 Q^H;
                                   assumes sigma_k > sigma_{k+1} clearly, ignores
                                   rcond, does not write sigma_out             */
@@ -183,7 +183,7 @@ qmcur_status qmcur_sample(const qmcur_qmat* A, int32_t sampler, const double* co
  *            QMCUR_PINV_SUBSPACE_FP32: see the enum; rank_out = {k, 2}.
  *   Device errors: NO_CONVERGENCE, NONFINITE, TIMEOUT (Jacobi);
  *   ILL_CONDITIONED (subspace).  UNSUPPORTED (synchronous) when the subspace
- *   method is asked for without a rank cap or with k > 112.
+ *   method is asked for without a rank cap or with k > 100.
  */
 qmcur_status qmcur_pinv_core(const qmcur_qmat* W, int32_t method, double rcond, int32_t rank_cap,
                              int32_t max_sweeps, qmcur_qmat* U, int32_t* rank_out,

@@ -1,6 +1,7 @@
 // C ABI of libqmcur (declared and documented in include/qmcur.h): argument
 // checks, workspace sizing and the composition of the stages.
 #include "common.cuh"
+#include "small.cuh"
 
 namespace qmcur {
 
@@ -114,7 +115,7 @@ size_t qmcur_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r, int32_t 
   if (m < 1 || n < 1 || c < 1 || r < 1) return 0;
   size_t s = probs_ws_bytes(m, n);
   const size_t s2 = sample_ws_bytes(m, n), s3 = pinv_ws_bytes(r, c), s4 = gemm_ws_bytes(m, n, c, r, prec);
-  const int64_t kmax = (r < c ? r : c) < 112 ? (r < c ? r : c) : 112;
+  const int64_t kmax = (r < c ? r : c) < kSmallCholMax ? (r < c ? r : c) : kSmallCholMax;
   const size_t s5 = pinv_fast_ws_bytes(r, c, kmax);
   if (s5 > s) s = s5;
   if (s2 > s) s = s2;

@@ -12,11 +12,19 @@
 // orth() is CholeskyQR (G = Y^H Y = R^H R, Q = Y R^-1), applied twice
 // (CholeskyQR2) where orthonormality to working accuracy matters.
 //
-// Every step is a small batched quaternion GEMM (op(X) op(Y), op in {N, H})
-// or a one-CTA Cholesky-and-triangular-inverse, so the same kernels also
-// serve many problems at once (one table entry per problem).
-#include "common.cuh"
-#include "small.cuh"
+// Every step is a small quaternion GEMM (op(X) op(Y), op in {N, H}) or a
+// one-CTA Cholesky factor inverse.  All ~30 steps run in ONE cooperative
+// persistent kernel of 512-thread CTAs (two GEMM tile workers of 256 threads
+// each); a bounded grid barrier separates consecutive steps (no launch gaps).
+// A GEMM step is a list of work items (16 x 16 output tile, k-range) dealt to
+// the workers one SM at a time.  Steps with fewer tiles than workers split
+// their k-range; every split writes its partial tile to the workspace and
+// the last of a tile's splits to finish (an atomic count per tile) sums the
+// partials in split order and writes the tile, so the result does not depend
+// on timing.  A Gram step Y^H Y feeds only the Cholesky, which reads the
+// upper triangle, so only tiles on or above the diagonal are formed.  A
+// Cholesky step runs on CTA 0.
+#include "small_impl.cuh"
 
 namespace qmcur {
 namespace {
@@ -33,12 +41,11 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
   return c;
 }
 
-// Gaussian quaternion entries (Box-Muller on two Philox words per pair of
-// components), rows x cols, row stride ld; counter (entry, 0, stream, 7).
-__global__ void k_randn_q(QPtr out, int rows, int cols, uint64_t seed, uint32_t stream) {
-  const int64_t total = (int64_t)rows * cols;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
+// Gaussian quaternion entry e of a matrix with `cols` columns (Box-Muller on
+// two Philox words per pair of components); counter (e_lo, e_hi, stream, 7).
+__device__ __forceinline__ void randn_entry(const QPtr& out, int64_t e, int cols, uint64_t seed,
+                                            uint32_t stream) {
+  {
     const uint4 x = philox(make_uint4((unsigned)e, (unsigned)(e >> 32), stream, 7u),
                            make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
     const float u0 = ((float)x.x + 1.0f) * 0x1.0p-32f, v0 = (float)x.y * 0x1.0p-32f;
@@ -59,17 +66,6 @@ __global__ void k_randn_q(QPtr out, int rows, int cols, uint64_t seed, uint32_t 
   }
 }
 
-__global__ void k_to_f32(QView in, QPtr out) {
-  const int64_t total = in.rows * in.cols;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / in.cols, j = e % in.cols;
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      reinterpret_cast<float*>(out.p[t])[i * out.ld + j] = (float)ld_as_double(in, t, i, j);
-  }
-}
-
 }  // namespace
 
 // Workspace of the subspace method for an r x c intersection with cap k.
@@ -77,6 +73,9 @@ struct FastWs {
   QPtr W32, Om, Y, Q, Z, P, G, R, Ri, T;
   int32_t* info;
 };
+
+// Split-k partial tiles (256 quaternions each) and per-tile arrival counts.
+constexpr int kMaxPartTiles = 1024;
 
 static QPtr carve_q(Carve& cv, int64_t rows, int64_t cols) {
   QPtr q;
@@ -108,24 +107,175 @@ static FastWs carve_fast(Carve& cv, int64_t r, int64_t c, int64_t k) {
 size_t pinv_fast_ws_bytes(int64_t r, int64_t c, int64_t k) {
   Carve cv(nullptr, 0);
   carve_fast(cv, r, c, k);
+  cv.take<float4>((size_t)kMaxPartTiles * kSmTileThreads);   // split-k partials
+  cv.take<unsigned>(4 + kMaxPartTiles);   // grid barrier, then split-k counts
   return cv.off;
 }
 
-// Y (rows x k) -> Q = Y R^-1 by CholeskyQR with `passes` passes (2 =
-// CholeskyQR2).  The inverse triangular factors of the passes are left in
-// Rinv1 (first) and Rinv2 (second), so that Y = Q R2 R1.
-static qmcur_status cholqr(const QPtr& Y, int rows, int k, const QPtr& Q, FastWs& w, int passes,
-                           QPtr Rinv1, QPtr Rinv2, int32_t* status, cudaStream_t st) {
-  qmcur_status s;
-  const QPtr& Qa = passes == 2 ? w.T : Q;
-  if ((s = small_qgemm(true, false, k, k, rows, 1.0f, Y, Y, 0.0f, w.G, st)) != QMCUR_OK) return s;
-  if ((s = small_chol_inv(w.G, k, Rinv1, status, st)) != QMCUR_OK) return s;
-  if ((s = small_qgemm(false, false, rows, k, k, 1.0f, Y, Rinv1, 0.0f, Qa, st)) != QMCUR_OK) return s;
-  if (passes == 1) return QMCUR_OK;
-  if ((s = small_qgemm(true, false, k, k, rows, 1.0f, w.T, w.T, 0.0f, w.G, st)) != QMCUR_OK) return s;
-  if ((s = small_chol_inv(w.G, k, Rinv2, status, st)) != QMCUR_OK) return s;
-  return small_qgemm(false, false, rows, k, k, 1.0f, w.T, Rinv2, 0.0f, Q, st);
+enum { PH_PREP = 0, PH_GEMM = 1, PH_CHOL = 2 };
+
+struct Phase {
+  int kind;
+  int k;        // PH_CHOL: order of G
+  int splits;   // PH_GEMM: k-range splits per tile (1: no partials)
+  int kchunk;   // PH_GEMM: k-range of one split (a multiple of kSmBK)
+  int upper;    // PH_GEMM: square output, only tiles (tm <= tn) are formed
+  SmallGemmArgs g;   // PH_CHOL: g.X = G, g.Z = Rinv
+};
+
+constexpr int kMaxPhases = 40;
+
+struct FusedProg {
+  int nph;
+  Phase ph[kMaxPhases];
+  QView Win;
+  QPtr W32, Om;
+  int r, c, k;
+  uint64_t seed;
+  unsigned* bar;
+  unsigned* cnt;   // kMaxPartTiles split-k arrival counts, zero between steps
+  float4* part;    // kMaxPartTiles partial tiles
+  int32_t* status;
+  int32_t* rank_out;
+};
+
+// Tile (tm, tn) of work tile t: row-major over the tile grid, or for `upper`
+// column-major over the upper triangle (t = tn (tn + 1) / 2 + tm).
+__device__ __forceinline__ void tile_of(int t, int tn_count, int upper, int& tm, int& tn) {
+  if (!upper) {
+    tm = t / tn_count;
+    tn = t % tn_count;
+    return;
+  }
+  int c = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (c * (c + 1) / 2 > t) --c;
+  while ((c + 1) * (c + 2) / 2 <= t) ++c;
+  tn = c;
+  tm = t - c * (c + 1) / 2;
 }
+
+__device__ __forceinline__ float4 f4add(float4 a, const float4 b) {
+  a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+  return a;
+}
+
+constexpr int kFusedThreads = kCholThreads;
+constexpr int kFusedWorkers = kFusedThreads / kSmTileThreads;
+static_assert(kFusedWorkers * kSmTileThreads == kFusedThreads, "whole tile workers");
+
+// Dynamic shared memory of the fused kernel: the larger of the tile workers'
+// slices and the Cholesky buffers.
+constexpr size_t kFusedSmem = (size_t)kFusedWorkers * kSmGemmQuats * 16 > sm_chol_bytes()
+                                  ? (size_t)kFusedWorkers * kSmGemmQuats * 16
+                                  : sm_chol_bytes();
+
+__global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_constant__ FusedProg P) {
+  extern __shared__ __align__(16) unsigned char smf[];
+  const int worker = threadIdx.x / kSmTileThreads, wtid = threadIdx.x % kSmTileThreads;
+  float4* wsm = reinterpret_cast<float4*>(smf) + worker * kSmGemmQuats;
+  for (int q = 0; q < P.nph; ++q) {
+    const Phase& ph = P.ph[q];
+    if (ph.kind == PH_PREP) {
+      const int64_t nW = (int64_t)P.r * P.c, nO = (int64_t)P.c * P.k;
+      for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nW + nO;
+           e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < nW) {
+          const int64_t i = e / P.c, j = e % P.c;
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            reinterpret_cast<float*>(P.W32.p[t])[i * P.W32.ld + j] = (float)ld_as_double(P.Win, t, i, j);
+        } else {
+          const int64_t f = e - nW;
+          randn_entry(P.Om, f, P.k, P.seed, 0x51u);
+        }
+      }
+    } else if (ph.kind == PH_GEMM) {
+      __shared__ int last_sh[kFusedWorkers];
+      const int tmc = (ph.g.M + kSmTS - 1) / kSmTS, tnc = (ph.g.N + kSmTS - 1) / kSmTS;
+      const int ntiles = ph.upper ? tnc * (tnc + 1) / 2 : tmc * tnc;
+      const int items = ntiles * ph.splits;
+      // item -> one per SM first (worker 0 of every CTA), then worker 1
+      for (int t = blockIdx.x + gridDim.x * worker; t < items; t += gridDim.x * kFusedWorkers) {
+        const int tile = t % ntiles, sp = t / ntiles;
+        int tm, tn;
+        tile_of(tile, tnc, ph.upper, tm, tn);
+        const int kb = sp * ph.kchunk;
+        const int ke = kb + ph.kchunk < ph.g.K ? kb + ph.kchunk : ph.g.K;
+        const float4 acc = sm_tile_acc(ph.g, tm, tn, kb, ke, wsm, wtid, 1 + worker);
+        if (ph.splits == 1) {
+          sm_tile_store(ph.g, tm, tn, wtid, acc);
+          continue;
+        }
+        P.part[((size_t)tile * ph.splits + sp) * kSmTileThreads + wtid] = acc;
+        __threadfence();
+        worker_sync(1 + worker);
+        if (wtid == 0)
+          last_sh[worker] = atomicAdd(P.cnt + tile, 1u) == (unsigned)(ph.splits - 1);
+        worker_sync(1 + worker);
+        if (last_sh[worker]) {
+          __threadfence();
+          float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int q2 = 0; q2 < ph.splits; ++q2)
+            sum = f4add(sum, __ldcg(P.part + ((size_t)tile * ph.splits + q2) * kSmTileThreads + wtid));
+          sm_tile_store(ph.g, tm, tn, wtid, sum);
+          if (wtid == 0) P.cnt[tile] = 0u;   // ready for the next step, after the grid barrier
+        }
+      }
+    } else if (blockIdx.x == 0) {
+      sm_chol_inv(ph.g.X, ph.k, ph.g.Z, P.status, smf);
+    }
+    if (q + 1 < P.nph && !grid_sync(P.bar, P.status)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && P.rank_out != nullptr) {
+    P.rank_out[0] = P.k;
+    P.rank_out[1] = 2;
+  }
+}
+
+struct ProgBuilder {
+  FusedProg p{};
+  bool ok = true;
+  int workers = 1;   // tile workers of the launch
+  // Z = op(X) op(Y); `upper`: Z square and only its upper triangle is needed.
+  void gemm(bool xh, bool yh, int M, int N, int K, const QPtr& X, const QPtr& Y, const QPtr& Z,
+            bool upper = false) {
+    if (p.nph >= kMaxPhases) { ok = false; return; }
+    Phase& ph = p.ph[p.nph++];
+    ph.kind = PH_GEMM;
+    ph.g = SmallGemmArgs{X, Y, Z, M, N, K, 1.0f, 0.0f, xh ? 1 : 0, yh ? 1 : 0};
+    const int tmc = (M + kSmTS - 1) / kSmTS, tnc = (N + kSmTS - 1) / kSmTS;
+    ph.upper = (upper && M == N) ? 1 : 0;
+    const int ntiles = ph.upper ? tnc * (tnc + 1) / 2 : tmc * tnc;
+    const int slices = (K + kSmBK - 1) / kSmBK;
+    int splits = workers / ntiles;
+    if (splits > 8) splits = 8;
+    if (splits > slices) splits = slices;
+    if (splits < 2 || ntiles * splits > kMaxPartTiles) splits = 1;
+    const int per = (slices + splits - 1) / splits;
+    ph.kchunk = per * kSmBK;
+    ph.splits = (slices + per - 1) / per;
+  }
+  void chol(const QPtr& G, int k, const QPtr& Rinv) {
+    if (p.nph >= kMaxPhases) { ok = false; return; }
+    Phase& ph = p.ph[p.nph++];
+    ph.kind = PH_CHOL;
+    ph.k = k;
+    ph.g = SmallGemmArgs{G, G, Rinv, k, k, k, 1.0f, 0.0f, 0, 0};
+  }
+  // Y (rows x k) -> Q = Y R^-1 by CholeskyQR with `passes` passes; the
+  // inverse factors are left in Rinv1 (first) and Rinv2 (second): Y = Q R2 R1.
+  void cholqr(const QPtr& Y, int rows, int k, const QPtr& Q, FastWs& w, int passes,
+              const QPtr& Rinv1, const QPtr& Rinv2) {
+    const QPtr& Qa = passes == 2 ? w.T : Q;
+    gemm(true, false, k, k, rows, Y, Y, w.G, true);
+    chol(w.G, k, Rinv1);
+    gemm(false, false, rows, k, k, Y, Rinv1, Qa);
+    if (passes == 1) return;
+    gemm(true, false, k, k, rows, w.T, w.T, w.G, true);
+    chol(w.G, k, Rinv2);
+    gemm(false, false, rows, k, k, w.T, Rinv2, Q);
+  }
+};
 
 qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat* U,
                               int32_t* rank_out, uint64_t seed, void* ws, size_t ws_bytes,
@@ -134,46 +284,64 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
   const int64_t nmin = r < c ? r : c;
   if (rank_cap < 1) return QMCUR_ERR_UNSUPPORTED;   // the method needs the cap
   const int k = (int)(rank_cap < nmin ? rank_cap : nmin);
-  if (k > kSmallCholMax) return QMCUR_ERR_UNSUPPORTED;
+  if (k > kSmallCholMax || r > 65535 || c > 65535) return QMCUR_ERR_UNSUPPORTED;
   Carve cv(ws, ws_bytes);
   FastWs w = carve_fast(cv, r, c, k);
+  float4* part = cv.take<float4>((size_t)kMaxPartTiles * kSmTileThreads);
+  unsigned* bar = cv.take<unsigned>(4 + kMaxPartTiles);
   if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
-  QPtr Rinv1 = w.R, Rinv2 = w.Ri;
-  {
-    int blocks = (int)((r * c + 255) / 256);
-    if (blocks > 2048) blocks = 2048;
-    k_to_f32<<<blocks, 256, 0, st>>>(view(W), w.W32);
-    blocks = (int)((c * k + 255) / 256);
-    if (blocks > 2048) blocks = 2048;
-    k_randn_q<<<blocks, 256, 0, st>>>(w.Om, (int)c, k, seed, 0x51u);
-  }
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pinv_fused, kFusedThreads,
+                                                    kFusedSmem) != cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  if (per_sm < 1) return QMCUR_ERR_CUDA;
+  const QPtr Rinv1 = w.R, Rinv2 = w.Ri;
   const int ri = (int)r, ci = (int)c;
-  qmcur_status s;
-  // Y0 = W Omega -> Q
-  if ((s = small_qgemm(false, false, ri, k, ci, 1.0f, w.W32, w.Om, 0.0f, w.Y, st)) != QMCUR_OK) return s;
-  // Intermediate bases only have to span the subspaces: one CholeskyQR pass.
-  // The last P must be orthonormal to working accuracy and W P = Q R2 R1
-  // exact to it: CholeskyQR2 for both.
-  if ((s = cholqr(w.Y, ri, k, w.Q, w, 1, Rinv1, Rinv2, dev_status, st)) != QMCUR_OK) return s;
+  // one CTA per SM at most: a GEMM step has at most ~2 x SMs useful items
+  const int grid = sms;
+  ProgBuilder b;
+  b.workers = grid * kFusedWorkers;
+  b.p.ph[b.p.nph++].kind = PH_PREP;
+  // Y0 = W Omega; intermediate bases only have to span the subspaces (one
+  // CholeskyQR pass); the last P must be orthonormal to working accuracy and
+  // W P = Q R2 R1 exact to it (CholeskyQR2 for both).
+  b.gemm(false, false, ri, k, ci, w.W32, w.Om, w.Y);
+  b.cholqr(w.Y, ri, k, w.Q, w, 1, Rinv1, Rinv2);
   for (int it = 0; it < 2; ++it) {
     const int passes = it == 1 ? 2 : 1;
-    // P = orth(W^H Q)
-    if ((s = small_qgemm(true, false, ci, k, ri, 1.0f, w.W32, w.Q, 0.0f, w.Z, st)) != QMCUR_OK) return s;
-    if ((s = cholqr(w.Z, ci, k, w.P, w, passes, Rinv1, Rinv2, dev_status, st)) != QMCUR_OK) return s;
-    // Q = orth(W P)
-    if ((s = small_qgemm(false, false, ri, k, ci, 1.0f, w.W32, w.P, 0.0f, w.Y, st)) != QMCUR_OK) return s;
-    if ((s = cholqr(w.Y, ri, k, w.Q, w, passes, Rinv1, Rinv2, dev_status, st)) != QMCUR_OK) return s;
+    b.gemm(true, false, ci, k, ri, w.W32, w.Q, w.Z);        // W^H Q
+    b.cholqr(w.Z, ci, k, w.P, w, passes, Rinv1, Rinv2);     // P
+    b.gemm(false, false, ri, k, ci, w.W32, w.P, w.Y);       // W P
+    b.cholqr(w.Y, ri, k, w.Q, w, passes, Rinv1, Rinv2);     // Q, R
   }
   // U = P R1^-1 R2^-1 Q^H
-  if ((s = small_qgemm(false, false, ci, k, k, 1.0f, w.P, Rinv1, 0.0f, w.Z, st)) != QMCUR_OK) return s;
-  if ((s = small_qgemm(false, false, ci, k, k, 1.0f, w.Z, Rinv2, 0.0f, w.T, st)) != QMCUR_OK) return s;
   QPtr Uo;
   for (int t = 0; t < 4; ++t) Uo.p[t] = U->plane[t];
   Uo.ld = U->ld;
   Uo.dtype = U->dtype;
-  if ((s = small_qgemm(false, true, ci, ri, k, 1.0f, w.T, w.Q, 0.0f, Uo, st)) != QMCUR_OK) return s;
-  if (rank_out != nullptr) small_set_rank(rank_out, k, 2, st);
-  return cuda_ok(cudaGetLastError());
+  b.gemm(false, false, ci, k, k, w.P, Rinv1, w.Z);
+  b.gemm(false, false, ci, k, k, w.Z, Rinv2, w.T);
+  b.gemm(false, true, ci, ri, k, w.T, w.Q, Uo);
+  if (!b.ok) return QMCUR_ERR_UNSUPPORTED;
+  b.p.Win = view(W);
+  b.p.W32 = w.W32;
+  b.p.Om = w.Om;
+  b.p.r = ri;
+  b.p.c = ci;
+  b.p.k = k;
+  b.p.seed = seed;
+  b.p.bar = bar;
+  b.p.cnt = bar + 4;
+  b.p.part = part;
+  b.p.status = dev_status;
+  b.p.rank_out = rank_out;
+  if (cudaMemsetAsync(bar, 0, (4 + kMaxPartTiles) * sizeof(unsigned), st) != cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  void* args[] = {(void*)&b.p};
+  return cuda_ok(cudaLaunchCooperativeKernel((const void*)k_pinv_fused, dim3(grid),
+                                             dim3(kFusedThreads), args, kFusedSmem, st));
 }
 
 }  // namespace qmcur

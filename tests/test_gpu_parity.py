@@ -253,7 +253,9 @@ def _pinv_fast(W, rank_cap):
 
 
 @pytest.mark.parametrize("r,c,k,noise", [(200, 200, 50, 1e-3), (120, 90, 12, 1e-4),
-                                         (64, 80, 30, 0.0), (33, 17, 5, 1e-3)])
+                                         (64, 80, 30, 0.0), (33, 17, 5, 1e-3),
+                                         (150, 131, 100, 1e-3), (9, 11, 1, 1e-3),
+                                         (97, 140, 97, 0.0)])
 def test_pinv_subspace_fp32(r, c, k, noise):
     W = synth.lowrank_gaussian(r, c, k, seed=r + c + k, noise_rel=noise)[0]
     U, info, st = _pinv_fast(W, k)
@@ -277,6 +279,14 @@ def test_pinv_subspace_needs_cap():
     W = np.random.default_rng(0).standard_normal((4, 10, 10))
     with pytest.raises(Q.QmcurError) as e:
         _pinv_fast(W, 0)
+    assert e.value.code == 7
+
+
+def test_pinv_subspace_cap_limit():
+    # k = min(rank_cap, r, c) above 100 is refused before any launch
+    W = np.random.default_rng(1).standard_normal((4, 110, 120))
+    with pytest.raises(Q.QmcurError) as e:
+        _pinv_fast(W, 101)
     assert e.value.code == 7
 
 
