@@ -24,38 +24,34 @@ __device__ __forceinline__ void set_status(int32_t* st, int32_t code) {
   if (st != nullptr) atomicCAS(reinterpret_cast<int*>(st), 0, code);
 }
 
-// Grid-wide barrier of a cooperative launch over bar[0] (arrivals), bar[1]
-// (generation) and bar[2] (abort flag), all zero before the launch.  The
-// wait is bounded; on timeout the abort flag is raised, QMCUR_ERR_TIMEOUT is
-// reported and false is returned (also to every later caller).
-__device__ __forceinline__ bool grid_sync(unsigned* bar, int32_t* status) {
+// Grid-wide barrier of a cooperative launch.  bar[0] counts arrivals over
+// the whole launch (never reset: the n-th barrier completes when it reaches
+// n * gridDim.x, kept by the caller in `target`), bar[2] is the abort flag;
+// both are zero before the launch.  One atomic per CTA, then a bounded poll.
+// On timeout the abort flag is raised, QMCUR_ERR_TIMEOUT is reported and
+// false is returned (also to every later caller).
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int32_t* status, unsigned& target) {
   __shared__ int ok_sh;
   __syncthreads();
+  target += gridDim.x;
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
+    volatile unsigned* vcount = bar;
     volatile unsigned* vabort = bar + 2;
     int ok = (*vabort == 0u);
     if (ok) {
-      const unsigned gen = *vgen;
-      __threadfence();
-      const unsigned arrived = atomicAdd(bar, 1u);
-      if (arrived == gridDim.x - 1) {
-        atomicExch(bar, 0u);
-        __threadfence();
-        atomicAdd(bar + 1, 1u);
-      } else {
-        const long long t0 = clock64();
-        while (*vgen == gen) {
-          if (*vabort != 0u) { ok = 0; break; }
-          if (clock64() - t0 > 4000000000ll) {
-            atomicExch(bar + 2, 1u);
-            set_status(status, QMCUR_ERR_TIMEOUT);
-            ok = 0;
-            break;
-          }
+      __threadfence();   // this CTA's writes before its arrival
+      atomicAdd(bar, 1u);
+      const long long t0 = clock64();
+      while (*vcount < target) {
+        if (*vabort != 0u) { ok = 0; break; }
+        if (clock64() - t0 > 4000000000ll) {
+          atomicExch(bar + 2, 1u);
+          set_status(status, QMCUR_ERR_TIMEOUT);
+          ok = 0;
+          break;
         }
       }
-      __threadfence();
+      __threadfence();   // the other CTAs' writes after their arrivals
     }
     ok_sh = ok;
   }

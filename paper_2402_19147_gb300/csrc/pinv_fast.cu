@@ -12,8 +12,9 @@
 // orth() is CholeskyQR (G = Y^H Y = R^H R, Q = Y R^-1), applied twice
 // (CholeskyQR2) where orthonormality to working accuracy matters.
 //
-// Every step is a small quaternion GEMM (op(X) op(Y), op in {N, H}) or a
-// one-CTA Cholesky factor inverse.  All ~30 steps run in ONE cooperative
+// Every step is a small quaternion GEMM (op(X) op(Y), op in {N, H}), a
+// one-CTA Cholesky factorisation, or a triangular solve Z = Y R^-1 (one warp
+// per row).  All ~30 steps run in ONE cooperative
 // persistent kernel of 512-thread CTAs (two GEMM tile workers of 256 threads
 // each); a bounded grid barrier separates consecutive steps (no launch gaps).
 // A GEMM step is a list of work items (16 x 16 output tile, k-range) dealt to
@@ -23,7 +24,8 @@
 // partials in split order and writes the tile, so the result does not depend
 // on timing.  A Gram step Y^H Y feeds only the Cholesky, which reads the
 // upper triangle, so only tiles on or above the diagonal are formed.  A
-// Cholesky step runs on CTA 0.
+// Cholesky step runs on CTA 0; a triangular-solve step stages R in every
+// CTA's shared memory and deals the rows to the warps, one SM at a time.
 #include "small_impl.cuh"
 
 namespace qmcur {
@@ -70,7 +72,8 @@ __device__ __forceinline__ void randn_entry(const QPtr& out, int64_t e, int cols
 
 // Workspace of the subspace method for an r x c intersection with cap k.
 struct FastWs {
-  QPtr W32, Om, Y, Q, Z, P, G, R, Ri, T;
+  QPtr W32, Om, Y, Q, Z, P, G, T;
+  float *R1, *R2;   // packed factors (rpk_floats(k) floats each)
   int32_t* info;
 };
 
@@ -97,8 +100,8 @@ static FastWs carve_fast(Carve& cv, int64_t r, int64_t c, int64_t k) {
   w.Z = carve_q(cv, mx, k);
   w.P = carve_q(cv, mx, k);
   w.G = carve_q(cv, k, k);
-  w.R = carve_q(cv, k, k);
-  w.Ri = carve_q(cv, k, k);
+  w.R1 = cv.take<float>((size_t)rpk_floats((int)k));
+  w.R2 = cv.take<float>((size_t)rpk_floats((int)k));
   w.T = carve_q(cv, mx, k);
   w.info = cv.take<int32_t>(4);
   return w;
@@ -112,7 +115,7 @@ size_t pinv_fast_ws_bytes(int64_t r, int64_t c, int64_t k) {
   return cv.off;
 }
 
-enum { PH_PREP = 0, PH_GEMM = 1, PH_CHOL = 2 };
+enum { PH_PREP = 0, PH_GEMM = 1, PH_CHOL = 2, PH_TRSM = 3 };
 
 struct Phase {
   int kind;
@@ -120,7 +123,8 @@ struct Phase {
   int splits;   // PH_GEMM: k-range splits per tile (1: no partials)
   int kchunk;   // PH_GEMM: k-range of one split (a multiple of kSmBK)
   int upper;    // PH_GEMM: square output, only tiles (tm <= tn) are formed
-  SmallGemmArgs g;   // PH_CHOL: g.X = G, g.Z = Rinv
+  float* rpk;   // PH_CHOL: the packed factor written; PH_TRSM: the one read
+  SmallGemmArgs g;   // PH_CHOL: g.X = G; PH_TRSM: g.Z = g.X R^-1, g.M rows, g.K = k
 };
 
 constexpr int kMaxPhases = 40;
@@ -163,16 +167,18 @@ constexpr int kFusedThreads = kCholThreads;
 constexpr int kFusedWorkers = kFusedThreads / kSmTileThreads;
 static_assert(kFusedWorkers * kSmTileThreads == kFusedThreads, "whole tile workers");
 
-// Dynamic shared memory of the fused kernel: the larger of the tile workers'
-// slices and the Cholesky buffers.
-constexpr size_t kFusedSmem = (size_t)kFusedWorkers * kSmGemmQuats * 16 > sm_chol_bytes()
-                                  ? (size_t)kFusedWorkers * kSmGemmQuats * 16
-                                  : sm_chol_bytes();
+// Dynamic shared memory of the fused kernel for cap k: the largest of the
+// tile workers' slices, the Cholesky buffers and the staged R.
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t fused_smem(int k) {
+  return cmax(cmax((size_t)kFusedWorkers * kSmGemmQuats * 16, sm_chol_bytes()), sm_trsm_bytes(k));
+}
 
 __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_constant__ FusedProg P) {
   extern __shared__ __align__(16) unsigned char smf[];
   const int worker = threadIdx.x / kSmTileThreads, wtid = threadIdx.x % kSmTileThreads;
   float4* wsm = reinterpret_cast<float4*>(smf) + worker * kSmGemmQuats;
+  unsigned bar_target = 0;
   for (int q = 0; q < P.nph; ++q) {
     const Phase& ph = P.ph[q];
     if (ph.kind == PH_PREP) {
@@ -221,10 +227,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_co
           if (wtid == 0) P.cnt[tile] = 0u;   // ready for the next step, after the grid barrier
         }
       }
+    } else if (ph.kind == PH_TRSM) {
+      if (blockIdx.x < ph.g.M) {   // CTAs without rows skip the staging
+        sm_trsm_stage(ph.rpk, ph.g.K, smf);
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, nw = kFusedThreads / 32;
+        for (int row = blockIdx.x + gridDim.x * warp; row < ph.g.M; row += gridDim.x * nw)
+          sm_trsm_row_any(ph.g.X, ph.g.Z, row, ph.g.K, smf);
+      }
     } else if (blockIdx.x == 0) {
-      sm_chol_inv(ph.g.X, ph.k, ph.g.Z, P.status, smf);
+      sm_chol(ph.g.X, ph.k, ph.rpk, P.status, smf);
     }
-    if (q + 1 < P.nph && !grid_sync(P.bar, P.status)) return;
+    if (q + 1 < P.nph && !grid_sync(P.bar, P.status, bar_target)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && P.rank_out != nullptr) {
     P.rank_out[0] = P.k;
@@ -255,25 +269,37 @@ struct ProgBuilder {
     ph.kchunk = per * kSmBK;
     ph.splits = (slices + per - 1) / per;
   }
-  void chol(const QPtr& G, int k, const QPtr& Rinv) {
+  void chol(const QPtr& G, int k, float* R) {
     if (p.nph >= kMaxPhases) { ok = false; return; }
     Phase& ph = p.ph[p.nph++];
     ph.kind = PH_CHOL;
     ph.k = k;
-    ph.g = SmallGemmArgs{G, G, Rinv, k, k, k, 1.0f, 0.0f, 0, 0};
+    ph.splits = 1;
+    ph.rpk = R;
+    ph.g = SmallGemmArgs{G, G, G, k, k, k, 1.0f, 0.0f, 0, 0};
+  }
+  // Z = Y R^-1 (Y, Z rows x k; Z may be Y)
+  void trsm(const QPtr& Y, float* R, const QPtr& Z, int rows, int k) {
+    if (p.nph >= kMaxPhases) { ok = false; return; }
+    Phase& ph = p.ph[p.nph++];
+    ph.kind = PH_TRSM;
+    ph.k = k;
+    ph.splits = 1;
+    ph.rpk = R;
+    ph.g = SmallGemmArgs{Y, Y, Z, rows, k, k, 1.0f, 0.0f, 0, 0};
   }
   // Y (rows x k) -> Q = Y R^-1 by CholeskyQR with `passes` passes; the
-  // inverse factors are left in Rinv1 (first) and Rinv2 (second): Y = Q R2 R1.
+  // factors are left in R1 (first) and R2 (second): Y = Q R2 R1.
   void cholqr(const QPtr& Y, int rows, int k, const QPtr& Q, FastWs& w, int passes,
-              const QPtr& Rinv1, const QPtr& Rinv2) {
+              float* R1, float* R2) {
     const QPtr& Qa = passes == 2 ? w.T : Q;
     gemm(true, false, k, k, rows, Y, Y, w.G, true);
-    chol(w.G, k, Rinv1);
-    gemm(false, false, rows, k, k, Y, Rinv1, Qa);
+    chol(w.G, k, R1);
+    trsm(Y, R1, Qa, rows, k);
     if (passes == 1) return;
     gemm(true, false, k, k, rows, w.T, w.T, w.G, true);
-    chol(w.G, k, Rinv2);
-    gemm(false, false, rows, k, k, w.T, Rinv2, Q);
+    chol(w.G, k, R2);
+    trsm(w.T, R2, Q, rows, k);
   }
 };
 
@@ -293,11 +319,22 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pinv_fused, kFusedThreads,
-                                                    kFusedSmem) != cudaSuccess)
+      dev < 0 || dev >= 64)
+    return QMCUR_ERR_CUDA;
+  static bool attr_set[64] = {};
+  if (!attr_set[dev]) {
+    if (cudaFuncSetAttribute(k_pinv_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fused_smem(kSmallCholMax)) != cudaSuccess)
+      return QMCUR_ERR_CUDA;
+    attr_set[dev] = true;
+  }
+  const size_t smem = fused_smem(k);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pinv_fused, kFusedThreads, smem) !=
+      cudaSuccess)
     return QMCUR_ERR_CUDA;
   if (per_sm < 1) return QMCUR_ERR_CUDA;
-  const QPtr Rinv1 = w.R, Rinv2 = w.Ri;
+  float* const R1 = w.R1;
+  float* const R2 = w.R2;
   const int ri = (int)r, ci = (int)c;
   // one CTA per SM at most: a GEMM step has at most ~2 x SMs useful items
   const int grid = sms;
@@ -308,21 +345,21 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
   // CholeskyQR pass); the last P must be orthonormal to working accuracy and
   // W P = Q R2 R1 exact to it (CholeskyQR2 for both).
   b.gemm(false, false, ri, k, ci, w.W32, w.Om, w.Y);
-  b.cholqr(w.Y, ri, k, w.Q, w, 1, Rinv1, Rinv2);
+  b.cholqr(w.Y, ri, k, w.Q, w, 1, R1, R2);
   for (int it = 0; it < 2; ++it) {
     const int passes = it == 1 ? 2 : 1;
     b.gemm(true, false, ci, k, ri, w.W32, w.Q, w.Z);        // W^H Q
-    b.cholqr(w.Z, ci, k, w.P, w, passes, Rinv1, Rinv2);     // P
+    b.cholqr(w.Z, ci, k, w.P, w, passes, R1, R2);           // P
     b.gemm(false, false, ri, k, ci, w.W32, w.P, w.Y);       // W P
-    b.cholqr(w.Y, ri, k, w.Q, w, passes, Rinv1, Rinv2);     // Q, R
+    b.cholqr(w.Y, ri, k, w.Q, w, passes, R1, R2);           // Q, R
   }
   // U = P R1^-1 R2^-1 Q^H
   QPtr Uo;
   for (int t = 0; t < 4; ++t) Uo.p[t] = U->plane[t];
   Uo.ld = U->ld;
   Uo.dtype = U->dtype;
-  b.gemm(false, false, ci, k, k, w.P, Rinv1, w.Z);
-  b.gemm(false, false, ci, k, k, w.Z, Rinv2, w.T);
+  b.trsm(w.P, R1, w.Z, ci, k);
+  b.trsm(w.Z, R2, w.T, ci, k);
   b.gemm(false, true, ci, ri, k, w.T, w.Q, Uo);
   if (!b.ok) return QMCUR_ERR_UNSUPPORTED;
   b.p.Win = view(W);
@@ -341,7 +378,7 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
     return QMCUR_ERR_CUDA;
   void* args[] = {(void*)&b.p};
   return cuda_ok(cudaLaunchCooperativeKernel((const void*)k_pinv_fused, dim3(grid),
-                                             dim3(kFusedThreads), args, kFusedSmem, st));
+                                             dim3(kFusedThreads), args, smem, st));
 }
 
 }  // namespace qmcur

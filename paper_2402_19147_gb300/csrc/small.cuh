@@ -1,7 +1,7 @@
 // Small dense quaternion kernels (FP32 compute) used by the subspace
 // pseudo-inverse and the backward pass: op(X) op(Y) GEMMs with op in
 // {identity, conjugate transpose}; the device code (also a one-CTA Cholesky
-// factor inverse) is in small_impl.cuh.
+// factorisation and a warp-per-row triangular solve) is in small_impl.cuh.
 #pragma once
 
 #include "common.cuh"
@@ -15,8 +15,9 @@ struct QPtr {
   int32_t dtype;
 };
 
-// Largest k of the Cholesky factor inverse: its k x k entries are held in
-// registers, at most 20 per thread of a 512-thread CTA.
+// Largest k of the small Cholesky factorisation: the k (k + 1) / 2 entries
+// of the upper triangle are held in registers of a 512-thread CTA, and a
+// triangular-solve row in 4 registers per lane.
 constexpr int kSmallCholMax = 100;
 
 // Z = alpha op(X) op(Y) + beta Z, op(X) M x K, op(Y) K x N.  With xh, X is

@@ -1,7 +1,7 @@
 // Device code of the small dense quaternion kernels, shared by the
 // standalone kernels (small.cu) and the fused subspace pseudo-inverse
-// (pinv_fast.cu).  A GEMM tile is computed by a worker of 256 threads; the
-// Cholesky inverse by one CTA of 512.
+// (pinv_fast.cu).  A GEMM tile is computed by a worker of 256 threads, a
+// Cholesky factor by one CTA of 512, a triangular-solve row by one warp.
 #pragma once
 
 #include "small.cuh"
@@ -133,39 +133,9 @@ __device__ __forceinline__ void sm_gemm_tile(const SmallGemmArgs& a, int tm, int
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky factor inverse of a small Hermitian positive definite matrix.
-//
-// Gaussian elimination of the augmented [G | I] with the pivots in order:
-// after step i every row j > i has had (G_ji / G_ii) times row i subtracted
-// (multipliers on the left, as quaternion row operations must be), so at the
-// end the left block is U' = D L^H and the right block is B = L^-1, where
-// G = L D L^H with L unit lower triangular and D real positive.  With
-// R = D^(1/2) L^H (so G = R^H R, R upper triangular with a real positive
-// diagonal) the inverse needed downstream is R^-1 = B^H D^(-1/2).
-//
-// Storage: the k x k matrix whose row j holds B_jc for c < j and U'_jc for
-// c >= j.  Entry e = s * kCholThreads + tid of this row-major matrix lives in
-// register slot s of thread tid (S = ceil(k^2 / kCholThreads) slots, a
-// template parameter so that no slot is spent on nothing); its row is
-// j = floor(e / k), formed as umulhi(e, floor((2^32 - 1) / k) + 1), which is
-// exact for e, k < 2^16 (the multiplier's excess over 2^32 / k is below 1 and
-// e < 2^16 keeps the product's error under 2^-16 < 1 / k).  Step i reads row
-// i of both blocks from a shared-memory broadcast buffer (B_ii = 1 stored
-// there); the owners of row i + 1 publish it into the other buffer as they
-// update it, so one barrier per step suffices.  Rows grow with the slot
-// index, so the finished rows j <= i occupy a prefix of every warp's slots:
-// the slots are walked downwards and left at the first one whose 32 entries
-// are all finished (a warp-uniform exit).
+// Quaternion helpers.
 
-constexpr int kCholThreads = 512;
-constexpr int kCholSlots = (kSmallCholMax * kSmallCholMax + kCholThreads - 1) / kCholThreads;
-
-// Shared-memory bytes of sm_chol_inv: two row buffers of each block and the pivots.
-__host__ __device__ constexpr size_t sm_chol_bytes() {
-  return (size_t)4 * kSmallCholMax * 16 + (size_t)kSmallCholMax * 4;
-}
-
-// conj(a) b (quaternion product).
+// conj(a) b
 __device__ __forceinline__ float4 q_conj_mul(const float4 a, const float4 b) {
   return make_float4(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w,
                      a.x * b.y - a.y * b.x - a.z * b.w + a.w * b.z,
@@ -173,115 +143,318 @@ __device__ __forceinline__ float4 q_conj_mul(const float4 a, const float4 b) {
                      a.x * b.w - a.y * b.z + a.z * b.y - a.w * b.x);
 }
 
+// acc - conj(a) b
+__device__ __forceinline__ float4 q_sub_conj_mul(float4 acc, const float4 a, const float4 b) {
+  const float4 m = q_conj_mul(a, b);
+  acc.x -= m.x; acc.y -= m.y; acc.z -= m.z; acc.w -= m.w;
+  return acc;
+}
+
+// acc - a b
+__device__ __forceinline__ float4 q_sub_mul(float4 acc, const float4 a, const float4 b) {
+  acc.x -= a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w;
+  acc.y -= a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z;
+  acc.z -= a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y;
+  acc.w -= a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x;
+  return acc;
+}
+
+// a b (quaternion product)
+__device__ __forceinline__ float4 q_mul(const float4 a, const float4 b) {
+  return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w,
+                     a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
+                     a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y,
+                     a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
+}
+
+__device__ __forceinline__ float4 q_add(float4 a, const float4 b) {
+  a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+  return a;
+}
+
+__device__ __forceinline__ float4 q_sub(float4 a, const float4 b) {
+  a.x -= b.x; a.y -= b.y; a.z -= b.z; a.w -= b.w;
+  return a;
+}
+
+__device__ __forceinline__ float4 q_scale(float4 a, float s) {
+  a.x *= s; a.y *= s; a.z *= s; a.w *= s;
+  return a;
+}
+
+__device__ __forceinline__ float q_norm2(const float4 a) {
+  return a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
+}
+
+// Start of row j in the row-major packed upper triangle of a k x k matrix.
+__host__ __device__ __forceinline__ int packed_row(int j, int k) { return j * k - j * (j - 1) / 2; }
+
+// ---------------------------------------------------------------------------
+// Cholesky factor of a small Hermitian positive definite matrix.
+//
+// G = R^H R with R upper triangular and a real positive diagonal (Sec. 2.2's
+// quaternion matrices: R^H is the conjugate transpose).  Right-looking and
+// blocked by kCholNb rows.  For the block of rows b0 .. b0 + nb - 1, whose
+// entries already carry every earlier block's update:
+//   panel:  R11 = chol(A11) (nb x nb) and R12 = R11^-H A12; each thread takes
+//           one column c >= b0 and forms R11 itself (identical arithmetic in
+//           every thread, so no barrier is needed between the two);
+//   update: A22 -= R12^H R12 on the entries (j, c), c >= j >= b0 + nb.
+// Two barriers per block.  The upper triangle, row-major packed, is spread
+// over the CTA: entry e = s * kCholThreads + tid lives in register slot s of
+// thread tid (S = ceil(k (k + 1) / 2 / kCholThreads) slots, a template
+// parameter).  Rows grow with the slot index, so the finished rows occupy a
+// prefix of every warp's slots: the update walks the slots downwards and
+// leaves at the first one whose 32 entries are all finished (warp-uniform).
+// The owners of the next block's rows publish them to shared memory as they
+// update them.
+//
+// Output (the layout the triangular solve stages): the upper triangle of R,
+// row-major packed, one float4 (quaternion) per entry, then 1 / R_ll for
+// l = 0 .. k - 1 as floats: rpk_floats(k) floats in all.
+
+constexpr int kCholThreads = 512;
+constexpr int kCholNb = 4;
+constexpr int kCholPacked = kSmallCholMax * (kSmallCholMax + 1) / 2;
+constexpr int kCholSlots = (kCholPacked + kCholThreads - 1) / kCholThreads;
+
+// Floats of the packed factor: k (k + 1) / 2 quaternions and k reciprocals.
+__host__ __device__ constexpr int rpk_floats(int k) { return 4 * (k * (k + 1) / 2) + k; }
+
+// Shared-memory bytes of sm_chol: raw and factored rows of one block, the pivot floor.
+__host__ __device__ constexpr size_t sm_chol_bytes() {
+  return (size_t)2 * kCholNb * kSmallCholMax * 16 + 16;
+}
+
 template <int S>
-__device__ __forceinline__ void sm_chol_inv_s(const QPtr& G, int k, const QPtr& Rinv,
-                                              int32_t* status, unsigned char* smraw) {
-  float4* rowA = reinterpret_cast<float4*>(smraw);          // [2][kSmallCholMax]
-  float4* rowB = rowA + 2 * kSmallCholMax;                  // [2][kSmallCholMax]
-  float* piv = reinterpret_cast<float*>(rowB + 2 * kSmallCholMax);
+__device__ __forceinline__ void sm_chol_s(const QPtr& G, int k, float* rpk, int32_t* status,
+                                          unsigned char* smraw) {
+  float4* Pn = reinterpret_cast<float4*>(smraw);            // [kCholNb][kSmallCholMax] raw rows
+  float4* Rp = Pn + kCholNb * kSmallCholMax;               // [kCholNb][kSmallCholMax] factored rows
+  float* floor_sh = reinterpret_cast<float*>(Rp + kCholNb * kSmallCholMax);
   const int tid = threadIdx.x;
-  const int kk = k * k;
-  const unsigned kmag = 0xffffffffu / (unsigned)k + 1u;
-  const float4 one = make_float4(1.f, 0.f, 0.f, 0.f);
+  const int np = k * (k + 1) / 2;
   float4 v[S];
+  unsigned jc[(S + 1) / 2];   // (j << 8 | c) in 16 bits, two slots per word
+#pragma unroll
+  for (int s = 0; s < (S + 1) / 2; ++s) jc[s] = 0u;
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const int e = s * kCholThreads + tid;
     v[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (e < kk) {
-      const int j = (int)__umulhi((unsigned)e, kmag), c = e - j * k;
-      if (c >= j) {
-        const int64_t off = (int64_t)j * G.ld + c;
-        v[s] = make_float4(reinterpret_cast<const float*>(G.p[0])[off],
-                           reinterpret_cast<const float*>(G.p[1])[off],
-                           reinterpret_cast<const float*>(G.p[2])[off],
-                           reinterpret_cast<const float*>(G.p[3])[off]);
+    if (e < np) {
+      const float b = 2.0f * (float)k + 1.0f;
+      int j = (int)((b - sqrtf(fmaxf(b * b - 8.0f * (float)e, 0.f))) * 0.5f);
+      if (j < 0) j = 0;
+      if (j > k - 1) j = k - 1;
+      while (j > 0 && packed_row(j, k) > e) --j;
+      while (j + 1 < k && packed_row(j + 1, k) <= e) ++j;
+      const int c = j + (e - packed_row(j, k));
+      jc[s >> 1] |= (((unsigned)j << 8) | (unsigned)c) << (16 * (s & 1));
+      const int64_t off = (int64_t)j * G.ld + c;
+      v[s] = make_float4(reinterpret_cast<const float*>(G.p[0])[off],
+                         reinterpret_cast<const float*>(G.p[1])[off],
+                         reinterpret_cast<const float*>(G.p[2])[off],
+                         reinterpret_cast<const float*>(G.p[3])[off]);
+      if (j < kCholNb) Pn[j * kSmallCholMax + c] = v[s];
+      if (e == 0) {
+        const float g00 = fabsf(v[s].x);
+        *floor_sh = (g00 > 0.f && isfinite(g00) ? g00 : 1.f) * 1e-30f;
       }
-      if (j == 0) rowA[c] = v[s];
     }
   }
-  if (tid == 0) rowB[0] = one;
   __syncthreads();
-  const float g00 = fabsf(rowA[0].x);
-  const float floor_v = (g00 > 0.f && isfinite(g00) ? g00 : 1.f) * 1e-30f;
-  const int wlast = tid | 31;   // the warp's highest thread index
-  for (int i = 0; i < k; ++i) {
-    const float4* rA = rowA + (i & 1) * kSmallCholMax;
-    const float4* rB = rowB + (i & 1) * kSmallCholMax;
-    float4* nA = rowA + ((i + 1) & 1) * kSmallCholMax;
-    float4* nB = rowB + ((i + 1) & 1) * kSmallCholMax;
-    float d = rA[i].x;
-    const bool bad = !(d > 0.f) || !isfinite(d);
-    if (bad) d = floor_v;
-    if (tid == 0) {
-      piv[i] = d;
-      if (bad) set_status(status, QMCUR_ERR_ILL_CONDITIONED);
-      if (i + 1 < k) nB[i + 1] = one;
-    }
-    const float inv_d = 1.0f / d;
-    // Re-derive each slot's (j, c) every step rather than keep 2 S
-    // loop-invariant registers live beside the entries.
-    unsigned kmag_i = kmag;
-    asm volatile("" : "+r"(kmag_i));
-    const int first_live = (i + 1) * k;   // entries below this index are finished
+  const float floor_v = *floor_sh;
+  const int wlast = tid | 31;
+  float4* Rq = reinterpret_cast<float4*>(rpk);
+  float* Rinvd = rpk + 4 * np;
+  for (int b0 = 0; b0 < k; b0 += kCholNb) {
+    const int nb = k - b0 < kCholNb ? k - b0 : kCholNb;
+    // ---- panel: thread tid owns column c = b0 + tid
+    if (tid < k - b0) {
+      const int c = b0 + tid;
+      float4 a[kCholNb][kCholNb];   // A11, upper part used; missing rows act as identity
 #pragma unroll
-    for (int s = S - 1; s >= 0; --s) {
-      if (s * kCholThreads + wlast < first_live) break;
-      const int e = s * kCholThreads + tid;
-      const int j = (int)__umulhi((unsigned)e, kmag_i), c = e - j * k;
-      const bool in = (s < S - 1) || (e < kk);
-      const bool left = c <= i;                       // B block, else U' block when c >= j
-      const bool ok = in && j > i && (left || c >= j);
-      const float4 a = rA[in ? j : 0];
-      const float4 b = left ? rB[c] : rA[c];
-      const float4 m = q_conj_mul(a, b);
-      const float sc = ok ? inv_d : 0.f;
-      v[s].x = fmaf(-m.x, sc, v[s].x);
-      v[s].y = fmaf(-m.y, sc, v[s].y);
-      v[s].z = fmaf(-m.z, sc, v[s].z);
-      v[s].w = fmaf(-m.w, sc, v[s].w);
-      if (ok && j == i + 1) {
-        if (left) nB[c] = v[s];
-        else nA[c] = v[s];
+      for (int p = 0; p < kCholNb; ++p)
+#pragma unroll
+        for (int q = p; q < kCholNb; ++q)
+          a[p][q] = (q < nb) ? Pn[p * kSmallCholMax + b0 + q]
+                             : make_float4(p == q ? 1.f : 0.f, 0.f, 0.f, 0.f);
+      bool bad = false;
+      float rd[kCholNb];
+#pragma unroll
+      for (int p = 0; p < kCholNb; ++p) {
+        float d = a[p][p].x;
+#pragma unroll
+        for (int q = 0; q < p; ++q) d -= q_norm2(a[q][p]);
+        if (!(d > 0.f) || !isfinite(d)) { bad = true; d = floor_v; }
+        rd[p] = __frsqrt_rn(d);   // 1 / R_pp, correctly rounded
+        a[p][p] = make_float4(d * rd[p], 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = p + 1; q < kCholNb; ++q) {   // R_pq = (A_pq - sum_l conj(R_lp) R_lq) / R_pp
+          float4 t = a[p][q];
+#pragma unroll
+          for (int l = 0; l < p; ++l) t = q_sub_conj_mul(t, a[l][p], a[l][q]);
+          a[p][q] = q_scale(t, rd[p]);
+        }
+      }
+      if (bad && tid == 0) set_status(status, QMCUR_ERR_ILL_CONDITIONED);
+      // column c of R12 (or of R11 when c < b0 + nb): y_p = (x_p - sum_l conj(R_lp) y_l) / R_pp
+      float4 y[kCholNb];
+#pragma unroll
+      for (int p = 0; p < kCholNb; ++p) {
+        float4 t = (p < nb && c >= b0 + p) ? Pn[p * kSmallCholMax + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < p; ++l) t = q_sub_conj_mul(t, a[l][p], y[l]);
+        y[p] = (c >= b0 + p) ? q_scale(t, rd[p]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c == b0 + p) y[p] = a[p][p];   // the diagonal exactly as the pivot
+      }
+#pragma unroll
+      for (int p = 0; p < kCholNb; ++p) {
+        Rp[p * kSmallCholMax + c] = (p < nb) ? y[p] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p < nb && c >= b0 + p) Rq[packed_row(b0 + p, k) + c - (b0 + p)] = y[p];
+        if (c == b0 + p) Rinvd[c] = rd[p];
+      }
+    }
+    __syncthreads();
+    // ---- update of the trailing entries; the next block's rows are published
+    const int nb0 = b0 + nb;
+    if (nb0 < k) {
+      const int first_live = packed_row(nb0, k);
+#pragma unroll
+      for (int s = S - 1; s >= 0; --s) {
+        if (s * kCholThreads + wlast < first_live) break;   // warp-uniform
+        const int e = s * kCholThreads + tid;
+        const unsigned w = jc[s >> 1] >> (16 * (s & 1));
+        const int j = (int)((w >> 8) & 0xffu), c = (int)(w & 0xffu);
+        if (e < np && j >= nb0) {   // many entries per thread: skipping idle ones pays here
+          static_assert(kCholNb == 4, "tree sum of four products");
+          const float4 m0 = q_conj_mul(Rp[0 * kSmallCholMax + j], Rp[0 * kSmallCholMax + c]);
+          const float4 m1 = q_conj_mul(Rp[1 * kSmallCholMax + j], Rp[1 * kSmallCholMax + c]);
+          const float4 m2 = q_conj_mul(Rp[2 * kSmallCholMax + j], Rp[2 * kSmallCholMax + c]);
+          const float4 m3 = q_conj_mul(Rp[3 * kSmallCholMax + j], Rp[3 * kSmallCholMax + c]);
+          const float4 t = q_sub(v[s], q_add(q_add(m0, m1), q_add(m2, m3)));
+          v[s] = t;
+          if (j < nb0 + kCholNb) Pn[(j - nb0) * kSmallCholMax + c] = t;
+        }
       }
     }
     __syncthreads();
   }
-  float* O0 = reinterpret_cast<float*>(Rinv.p[0]);
-  float* O1 = reinterpret_cast<float*>(Rinv.p[1]);
-  float* O2 = reinterpret_cast<float*>(Rinv.p[2]);
-  float* O3 = reinterpret_cast<float*>(Rinv.p[3]);
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int e = s * kCholThreads + tid;
-    if (e < kk) {
-      const int j = (int)__umulhi((unsigned)e, kmag), c = e - j * k;
-      const float sc = 1.0f / sqrtf(piv[j]);
-      // Rinv[c][j] = conj(B_jc) D_j^(-1/2) (c < j), D_j^(-1/2) (c == j), 0 (c > j)
-      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (c < j) q = make_float4(v[s].x * sc, -v[s].y * sc, -v[s].z * sc, -v[s].w * sc);
-      else if (c == j) q.x = sc;
-      const int64_t off = (int64_t)c * Rinv.ld + j;
-      O0[off] = q.x; O1[off] = q.y; O2[off] = q.z; O3[off] = q.w;
-    }
-  }
-  __syncthreads();
 }
 
 template <int S>
-__device__ __forceinline__ void sm_chol_inv_from(int need, const QPtr& G, int k, const QPtr& Rinv,
-                                                 int32_t* status, unsigned char* smraw) {
-  if (need <= S) sm_chol_inv_s<S>(G, k, Rinv, status, smraw);
-  else if constexpr (S < kCholSlots) sm_chol_inv_from<S + 1>(need, G, k, Rinv, status, smraw);
+__device__ __forceinline__ void sm_chol_from(int need, const QPtr& G, int k, float* rpk,
+                                             int32_t* status, unsigned char* smraw) {
+  if (need <= S) sm_chol_s<S>(G, k, rpk, status, smraw);
+  else if constexpr (S < kCholSlots) sm_chol_from<S + 1>(need, G, k, rpk, status, smraw);
 }
 
-// One CTA of kCholThreads threads: Rinv = R^-1 where G = R^H R (k x k, FP32,
-// 1 <= k <= kSmallCholMax; only the upper triangle of G is read).  Rinv is
-// written in full (zeros below the diagonal).  A non-positive or non-finite
-// pivot sets ILL_CONDITIONED and continues with a tiny pivot.
-__device__ __forceinline__ void sm_chol_inv(const QPtr& G, int k, const QPtr& Rinv,
-                                            int32_t* status, unsigned char* smraw) {
-  sm_chol_inv_from<1>((k * k + kCholThreads - 1) / kCholThreads, G, k, Rinv, status, smraw);
+// One CTA of kCholThreads threads: the packed factor R (FP32) with G = R^H R,
+// for 1 <= k <= kSmallCholMax (rpk 16-byte aligned, rpk_floats(k) floats).
+// Only the upper triangle of G is read.  A non-positive or non-finite pivot
+// sets ILL_CONDITIONED and continues with a tiny pivot.
+__device__ __forceinline__ void sm_chol(const QPtr& G, int k, float* rpk, int32_t* status,
+                                        unsigned char* smraw) {
+  sm_chol_from<1>((k * (k + 1) / 2 + kCholThreads - 1) / kCholThreads, G, k, rpk, status, smraw);
+}
+
+// ---------------------------------------------------------------------------
+// Triangular solve Z = Y R^-1 (R k x k upper triangular, real diagonal): row
+// z of Z solves z R = y, i.e. z_l = (y_l - sum_{i<l} z_i R_il) / R_ll.  One
+// warp per row, lane owning columns lane + 32 u; column by column, z_l is
+// taken from its owner with shuffles and every later column takes its update
+// at once.  The slot updates are branch-free (clamped indices, selected
+// results): short branchy bodies leave a lone warp waiting on instruction
+// fetch.  R (the packed factor above) is staged in shared memory.
+
+__host__ __device__ constexpr size_t sm_trsm_bytes(int k) { return (size_t)rpk_floats(k) * 4; }
+
+// All threads of the CTA: copy the packed factor into shared memory.
+__device__ __forceinline__ void sm_trsm_stage(const float* rpk, int k, unsigned char* smraw) {
+  const int n4 = (k * (k + 1) / 2), nf = rpk_floats(k);
+  const float4* src = reinterpret_cast<const float4*>(rpk);
+  float4* dst = reinterpret_cast<float4*>(smraw);
+  for (int i0 = threadIdx.x; i0 < n4; i0 += 4 * blockDim.x) {
+    float4 q[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int i = i0 + h * blockDim.x;
+      q[h] = i < n4 ? __ldcg(src + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int i = i0 + h * blockDim.x;
+      if (i < n4) dst[i] = q[h];
+    }
+  }
+  float* fs = reinterpret_cast<float*>(smraw);
+  for (int i = 4 * n4 + threadIdx.x; i < nf; i += blockDim.x) fs[i] = __ldcg(rpk + i);
+}
+
+// One warp: row `row` of Z = Y R^-1 (Z may alias Y), k <= 32 U.
+template <int U>
+__device__ __forceinline__ void sm_trsm_row(const QPtr& Y, const QPtr& Z, int row, int k,
+                                            const unsigned char* smraw) {
+  const float4* Rs = reinterpret_cast<const float4*>(smraw);
+  const float* invd = reinterpret_cast<const float*>(smraw) + 4 * (k * (k + 1) / 2);
+  const int lane = threadIdx.x & 31;
+  float4 t[U];
+  int cc[U];   // column of each slot, clamped into [0, k) for the loads
+  const int64_t yo = (int64_t)row * Y.ld;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int c = lane + 32 * u;
+    cc[u] = c < k ? c : k - 1;
+    t[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (c < k)
+      t[u] = make_float4(reinterpret_cast<const float*>(Y.p[0])[yo + c],
+                         reinterpret_cast<const float*>(Y.p[1])[yo + c],
+                         reinterpret_cast<const float*>(Y.p[2])[yo + c],
+                         reinterpret_cast<const float*>(Y.p[3])[yo + c]);
+  }
+#pragma unroll
+  for (int uu = 0; uu < U; ++uu) {
+    const int lend = k - 32 * uu < 32 ? k - 32 * uu : 32;   // columns of this slot
+    for (int ll = 0; ll < lend; ++ll) {
+      const int l = 32 * uu + ll;
+      const float s = invd[l];
+      const float4 z = make_float4(__shfl_sync(0xffffffffu, t[uu].x, ll) * s,
+                                   __shfl_sync(0xffffffffu, t[uu].y, ll) * s,
+                                   __shfl_sync(0xffffffffu, t[uu].z, ll) * s,
+                                   __shfl_sync(0xffffffffu, t[uu].w, ll) * s);
+      // R_l,c sits at Rrow + c for c >= l; a clamped c below l reads an
+      // earlier entry of the packed array, whose product is discarded.
+      const float4* Rrow = Rs + (packed_row(l, k) - l);
+#pragma unroll
+      for (int u = uu; u < U; ++u) {
+        const int c = lane + 32 * u;
+        const float4 nt = q_sub_mul(t[u], z, Rrow[cc[u] > l ? cc[u] : l]);
+        t[u] = (c > l && c < k) ? nt : t[u];
+      }
+      t[uu] = (lane == ll) ? z : t[uu];
+    }
+  }
+  const int64_t zo = (int64_t)row * Z.ld;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int c = lane + 32 * u;
+    if (c < k) {
+      reinterpret_cast<float*>(Z.p[0])[zo + c] = t[u].x;
+      reinterpret_cast<float*>(Z.p[1])[zo + c] = t[u].y;
+      reinterpret_cast<float*>(Z.p[2])[zo + c] = t[u].z;
+      reinterpret_cast<float*>(Z.p[3])[zo + c] = t[u].w;
+    }
+  }
+}
+
+__device__ __forceinline__ void sm_trsm_row_any(const QPtr& Y, const QPtr& Z, int row, int k,
+                                                const unsigned char* smraw) {
+  static_assert(kSmallCholMax <= 128, "four column slots per lane");
+  if (k <= 32) sm_trsm_row<1>(Y, Z, row, k, smraw);
+  else if (k <= 64) sm_trsm_row<2>(Y, Z, row, k, smraw);
+  else if (k <= 96) sm_trsm_row<3>(Y, Z, row, k, smraw);
+  else sm_trsm_row<4>(Y, Z, row, k, smraw);
 }
 
 }  // namespace qmcur
