@@ -158,6 +158,22 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------- ours -
+def replica_max(x, dist=None, device="cpu"):
+    """Max over ranks of a per-rank time (ms); the identity on one process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, steps, t_max_ms):
+    """Whole-job decompositions/s: every rank decomposes `steps` matrices of its
+    own; the job takes as long as its slowest rank."""
+    return world * steps / (t_max_ms / 1e3)
+
+
 def pinv_flops(w, method, sweeps):
     """Algorithmic real flops of one pseudo-inverse of the r x c intersection."""
     c, r = w["c"], w["r"]
@@ -169,9 +185,13 @@ def pinv_flops(w, method, sweeps):
         # rotation of both columns of G and V (q*w 32 flops, two combinations 16).
         return sweeps * pairs * (nr * 48 + (nr + nc) * 48)
     k = min(w["rank_cap"], nc)
-    # subspace iteration: W Omega, two (W^H Q, W P) pairs; seven CholeskyQR
-    # passes (Gram + Q R^-1, 2 rows k^2 quaternion FMAs each); U = P R^-1 Q^H.
-    qfma = 5 * r * c * k + 7 * 2 * ((r + c) // 2) * k * k + 2 * c * k * k + c * r * k
+    # subspace iteration: W Omega, two (W^H Q, W P) pairs (5 r c k); seven
+    # CholeskyQR passes over `rows` x k bases, each a Hermitian Gram (rows k^2 / 2),
+    # a Cholesky (k^3 / 6) and a triangular solve (rows k^2 / 2); then
+    # U = P R1^-1 R2^-1 Q^H (two solves on c x k, one c r k product).
+    pass_rows = [r, c, r, c, c, r, r]
+    qfma = 5 * r * c * k + sum(rows * k * k + k ** 3 // 6 for rows in pass_rows)
+    qfma += c * k * k + c * r * k
     return 32 * qfma
 
 
@@ -192,7 +212,7 @@ def stage_work(w, prec, sweeps, method="subspace"):
 def launches_per_step(args):
     """Kernels of the library launched per decomposition (counted from the code)."""
     n = 4 + 2                                  # probabilities, sampler + gathers
-    n += 4 if args.pinv == "jacobi" else 32    # pseudo-inverse
+    n += 4 if args.pinv == "jacobi" else 1     # pseudo-inverse (one cooperative kernel)
     n += 3 if args.prec == "fp32" else 6       # GEMMs (+ operand splits) + fold
     return n
 
@@ -316,12 +336,8 @@ def run_ours(args):
         total_ms += e[0].elapsed_time(e[4])
     sweeps = int(D.rank[1].item())
     rel = float(D.out3[0].item())
-    t_max = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / (t_max / 1e3)
+    t_max = replica_max(total_ms, dist, dev)
+    value = replica_value(world, args.steps, t_max)
 
     # end to end through the C ABI with host buffers (pinned), one copy each way
     A_host = torch.from_numpy(A_np).pin_memory()
@@ -341,10 +357,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = replica_max(e2e_ms, dist, dev)
     Q.check_status(D.status, "e2e steps")
 
     if rank != 0:
@@ -390,7 +403,7 @@ def run_ours(args):
         "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak, "traffic": None,
                      "peak_source": pk_kind},
-        "e2e": {"value": world * args.steps / (e2e_ms / 1e3), "unit": "decompositions/s",
+        "e2e": {"value": replica_value(world, args.steps, e2e_ms), "unit": "decompositions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step(args) * args.steps,
         "clocks": clk,
