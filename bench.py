@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="bf16x3", choices=["fp32", "tf32x3", "bf16x3", "bf16x6"])
+    ap.add_argument("--prec", default="bf16mixed",
+                    choices=["fp32", "tf32x3", "bf16x3", "bf16x6", "bf16mixed"])
     ap.add_argument("--pinv", default="subspace", choices=["subspace", "jacobi"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -66,8 +66,13 @@ typedef enum {
                             big*big + big*small + small*big, FP32 accumulate  */
   QMCUR_PREC_BF16X3 = 3, /* tensor cores (tcgen05 kind::f16, BF16): hi + lo
                             parts, products hi*hi + hi*lo + lo*hi              */
-  QMCUR_PREC_BF16X6 = 4  /* tensor cores, BF16 hi + mid + lo parts, the six
+  QMCUR_PREC_BF16X6 = 4, /* tensor cores, BF16 hi + mid + lo parts, the six
                             products of order <= 2, FP32 accumulate            */
+  QMCUR_PREC_BF16_MIXED = 5 /* tensor cores: T = U R with the BF16X6 split and
+                            Z = C T with the BF16X3 split.  U = W^+ can be
+                            ill-conditioned, so cancellation in U R amplifies
+                            operand rounding; C T is the well-conditioned
+                            product and holds ~90% of the flops.            */
 } qmcur_prec;
 
 typedef enum {

@@ -83,7 +83,8 @@ qmcur_status launch_reconstruct(const qmcur_qmat* C, const qmcur_qmat* U, const 
     k_residual_fold<<<1, 1024, 0, st>>>(partial, (int64_t)p1, out3);
     return cuda_ok(cudaGetLastError());
   }
-  if (prec == QMCUR_PREC_TF32X3 || prec == QMCUR_PREC_BF16X3 || prec == QMCUR_PREC_BF16X6)
+  if (prec == QMCUR_PREC_TF32X3 || prec == QMCUR_PREC_BF16X3 || prec == QMCUR_PREC_BF16X6 ||
+      prec == QMCUR_PREC_BF16_MIXED)
     return launch_reconstruct_tc(C, U, R, prec, Z, A, mask, out3, ws, ws_bytes, dev_status, st);
   return QMCUR_ERR_INVALID_ARG;
 }

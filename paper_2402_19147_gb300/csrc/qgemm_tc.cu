@@ -10,6 +10,8 @@
 // Precision: every FP32 operand is split into pieces (BF16 hi/lo or
 // hi/mid/lo, or TF32 big/small); a "term" multiplies one piece of X by one of
 // Y, and the terms (3 or 6) accumulate into the same FP32 TMEM accumulator.
+// The two GEMMs may use different splits (QMCUR_PREC_BF16_MIXED: six terms
+// for T = U R, three for Z = C T).
 //
 // Layout: pieces are stored K-major, [piece][plane][rows][Kpad] (Kpad a
 // multiple of 64 bytes, zero padded), one 3-D tensor map per operand, so a
@@ -543,6 +545,7 @@ struct TcPlan {
 };
 
 TcPlan plan_for(int32_t prec) {
+  if (prec == QMCUR_PREC_BF16_MIXED) prec = QMCUR_PREC_BF16X6;
   TcPlan pl{};
   pl.bf16 = prec != QMCUR_PREC_TF32X3;
   pl.npieces = prec == QMCUR_PREC_BF16X6 ? 3 : 2;
@@ -560,6 +563,12 @@ TcPlan plan_for(int32_t prec) {
   return pl;
 }
 
+// Splits of the two GEMMs: T = U R (first) and Z = C T (second).
+void plans_for(int32_t prec, TcPlan& first, TcPlan& second) {
+  first = plan_for(prec);
+  second = plan_for(prec == QMCUR_PREC_BF16_MIXED ? QMCUR_PREC_BF16X3 : prec);
+}
+
 inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct TcWs {
@@ -567,14 +576,15 @@ struct TcWs {
   double* partial;
 };
 
-TcWs carve_tc(Carve& cv, const TcPlan& pl, int64_t m, int64_t n, int64_t c, int64_t r) {
-  const int64_t es = pl.bf16 ? 2 : 4;
-  const int64_t kp1 = rup(r, pl.epr), kp2 = rup(c, pl.epr);
+TcWs carve_tc(Carve& cv, const TcPlan& p1, const TcPlan& p2, int64_t m, int64_t n, int64_t c,
+              int64_t r) {
+  const int64_t es = p1.bf16 ? 2 : 4;   // both plans have the same element type
+  const int64_t kp1 = rup(r, p1.epr), kp2 = rup(c, p2.epr);
   TcWs w;
-  w.A1 = cv.take<char>((size_t)(pl.npieces * 4 * rup(c, BM) * kp1 * es));
-  w.B1 = cv.take<char>((size_t)(pl.npieces * 4 * n * kp1 * es));
-  w.A2 = cv.take<char>((size_t)(pl.npieces * 4 * m * kp2 * es));
-  w.B2 = cv.take<char>((size_t)(pl.npieces * 4 * n * kp2 * es));
+  w.A1 = cv.take<char>((size_t)(p1.npieces * 4 * rup(c, BM) * kp1 * es));
+  w.B1 = cv.take<char>((size_t)(p1.npieces * 4 * n * kp1 * es));
+  w.A2 = cv.take<char>((size_t)(p2.npieces * 4 * m * kp2 * es));
+  w.B2 = cv.take<char>((size_t)(p2.npieces * 4 * n * kp2 * es));
   const int64_t tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
   w.partial = cv.take<double>((size_t)(2 * tiles));
   return w;
@@ -620,7 +630,9 @@ qmcur_status launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const TcP
 
 size_t tc_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec) {
   Carve cv(nullptr, 0);
-  carve_tc(cv, plan_for(prec), m, n, c, r);
+  TcPlan p1, p2;
+  plans_for(prec, p1, p2);
+  carve_tc(cv, p1, p2, m, n, c, r);
   return cv.off;
 }
 
@@ -633,27 +645,28 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
   if (Z != nullptr && Z->dtype != QMCUR_F32) return QMCUR_ERR_INVALID_ARG;
   if (A != nullptr && A->dtype != QMCUR_F32) return QMCUR_ERR_INVALID_ARG;
   if (m > INT32_MAX / 2 || n > INT32_MAX / 2) return QMCUR_ERR_UNSUPPORTED;
-  const TcPlan pl = plan_for(prec);
+  TcPlan pl, pl2;   // splits of T = U R and of Z = C T
+  plans_for(prec, pl, pl2);
   Carve cv(ws, ws_bytes);
-  TcWs w = carve_tc(cv, pl, m, n, c, r);
+  TcWs w = carve_tc(cv, pl, pl2, m, n, c, r);
   if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
-  const int64_t kp1 = rup(r, pl.epr), kp2 = rup(c, pl.epr);
+  const int64_t kp1 = rup(r, pl.epr), kp2 = rup(c, pl2.epr);
   qmcur_status s;
   // operand pieces: U (c x r) and C (m x c) as they are, R (r x n) transposed
   if (pl.bf16) {
     if ((s = launch_split<true>(U, false, w.A1, c, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
     if ((s = launch_split<true>(R, true, w.B1, n, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
-    if ((s = launch_split<true>(C, false, w.A2, m, c, kp2, pl.npieces, st)) != QMCUR_OK) return s;
+    if ((s = launch_split<true>(C, false, w.A2, m, c, kp2, pl2.npieces, st)) != QMCUR_OK) return s;
   } else {
     if ((s = launch_split<false>(U, false, w.A1, c, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
     if ((s = launch_split<false>(R, true, w.B1, n, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
-    if ((s = launch_split<false>(C, false, w.A2, m, c, kp2, pl.npieces, st)) != QMCUR_OK) return s;
+    if ((s = launch_split<false>(C, false, w.A2, m, c, kp2, pl2.npieces, st)) != QMCUR_OK) return s;
   }
   CUtensorMap mA1, mB1, mA2, mB2;
   if (!make_map(&mA1, w.A1, pl.bf16, c, kp1, pl.npieces, BM) ||
       !make_map(&mB1, w.B1, pl.bf16, n, kp1, pl.npieces, BN) ||
-      !make_map(&mA2, w.A2, pl.bf16, m, kp2, pl.npieces, BM) ||
-      !make_map(&mB2, w.B2, pl.bf16, n, kp2, pl.npieces, BN))
+      !make_map(&mA2, w.A2, pl2.bf16, m, kp2, pl2.npieces, BM) ||
+      !make_map(&mB2, w.B2, pl2.bf16, n, kp2, pl2.npieces, BN))
     return QMCUR_ERR_CUDA;
   TcParams p1{};
   p1.M = (int)c;
@@ -664,14 +677,16 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
   for (int i = 0; i < 6; ++i) { p1.ta[i] = pl.ta[i]; p1.tb[i] = pl.tb[i]; }
   p1.mode = MODE_SPLIT_T;
   p1.bt = w.B2;
-  p1.bt_npieces = pl.npieces;
+  p1.bt_npieces = pl2.npieces;   // T is written in the second GEMM's split
   p1.bt_rows = n;
   p1.bt_kpad = kp2;
   p1.status = dev_status;
   TcParams p2 = p1;
   p2.M = (int)m;
   p2.K = (int)c;
-  p2.kblocks = (int)(kp2 / pl.epr);
+  p2.kblocks = (int)(kp2 / pl2.epr);
+  p2.nterms = pl2.nterms;
+  for (int i = 0; i < 6; ++i) { p2.ta[i] = pl2.ta[i]; p2.tb[i] = pl2.tb[i]; }
   if (Z != nullptr) {
     p2.mode = MODE_STORE_Z;
     for (int t = 0; t < 4; ++t) p2.z[t] = reinterpret_cast<float*>(Z->plane[t]);

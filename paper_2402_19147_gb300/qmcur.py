@@ -19,8 +19,9 @@ LIB_PATH = os.path.join(_PKG, "libqmcur.so")
 F32, F64 = 0, 1
 SAMPLER_UNIFORM, SAMPLER_NORM = 0, 1
 PREC_FP64, PREC_FP32, PREC_TF32X3, PREC_BF16X3, PREC_BF16X6 = 0, 1, 2, 3, 4
+PREC_BF16_MIXED = 5
 PREC_NAMES = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32x3": PREC_TF32X3,
-              "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6}
+              "bf16x3": PREC_BF16X3, "bf16x6": PREC_BF16X6, "bf16mixed": PREC_BF16_MIXED}
 STATUS = {0: "QMCUR_OK", 1: "QMCUR_ERR_INVALID_ARG", 2: "QMCUR_ERR_NONFINITE",
           3: "QMCUR_ERR_ZERO_NORM", 4: "QMCUR_ERR_INSUFFICIENT_SUPPORT",
           5: "QMCUR_ERR_SAMPLE_LIMIT", 6: "QMCUR_ERR_NO_CONVERGENCE",

@@ -53,6 +53,6 @@ def test_host_only_calls(libpath):
     L = Q.lib()
     assert L.qmcur_status_str(0) == b"QMCUR_OK"
     assert L.qmcur_status_str(6) == b"QMCUR_ERR_NO_CONVERGENCE"
-    for prec in range(5):
+    for prec in range(6):
         assert Q.workspace_size(2048, 2048, 200, 200, prec) > 0
     assert Q.workspace_size(0, 10, 1, 1, 1) == 0

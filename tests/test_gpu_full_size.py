@@ -1,0 +1,164 @@
+"""Parity at the workloads' full sizes, in the launch configuration the
+benchmark times: every stage of the decomposition through the C ABI, against
+the FP64 oracle on the same seeded input.
+
+What the oracle cannot afford one by one is checked on samples: rows of
+Z = C (U R), and, for the batch, every 32nd problem.  Two things are checked
+in full:
+* the index sets and gathers, bit-exact;
+* the fused relative residual, against the oracle's residual of the full FP64
+  reconstruction built from the same FP32 U.
+
+Tolerances:
+* probabilities 24 u32 elementwise;
+* the subspace pseudo-inverse 64 u32 kappa^2, kappa = sigma_1 / sigma_k;
+* the residual within 1e-5.
+* The mixed split (BF16X6 for T = U R, BF16X3 for Z = C T): 1e-5 relative
+  Frobenius on the sampled rows of Z.
+* The plain BF16X3 split: its worst-case bound.  A value split into BF16
+  hi + lo is represented to 2^-16 relative, and the dropped lo*lo product is
+  below 2^-16 |x y|.  So each real product errs by at most 3 * 2^-16 |x_t y_s|,
+  and a quaternion product by at most 12 * 2^-16 |x| |y| (the sum over its 16
+  real products, with sum_t |x_t| <= 2 |x|).  Through T = U R and Z = C T,
+  |dZ| <= 24 * 2^-16 |C| |U| |R| entrywise, in quaternion moduli.  That bound
+  is tested in relative Frobenius form over the sampled rows.  Cancellation in
+  U R (U = W^+ of a smooth field) makes it far larger than the error of the
+  mixed split.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import qmcur as O
+from oracle import quat as QT
+from paper_2402_19147_gb300 import qmcur as Q
+from paper_2402_19147_gb300 import synth
+from gpu_util import U32, dev, host, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+
+def _decompose_like_bench(A, w, prec, sampler, seed):
+    """The benchmark's timed step (its default split is the mixed one):
+    probs, sample + gathers, FP32 subspace pseudo-inverse, fused residual;
+    then one Z-storing reconstruction."""
+    m, n, c, r = A.shape[1], A.shape[2], w["c"], w["r"]
+    D = Q.Decomposition(m, n, c, r, prec)
+    Q.probs(A, sampler, D.col_p, D.row_p, None, D.ws, D.status)
+    Q.sample(A, sampler, D.col_p, D.row_p, c, r, seed, 0, D.J, D.I, D.C, D.R, D.W,
+             ws=D.ws, status=D.status)
+    Q.pinv_core(D.W, D.U, w["rcond"], w["rank_cap"], 0, D.rank, D.sigma, D.ws, D.status,
+                method=Q.PINV_SUBSPACE_FP32)
+    Q.residual(A, D.out3, D.C, D.U, D.R, prec, None, None, D.ws, D.status)
+    U32t = D.U.float()
+    Z = torch.empty(4, m, n, dtype=torch.float32, device="cuda")
+    Q.reconstruct(D.C, U32t, D.R, prec, Z, D.ws, D.status)
+    torch.cuda.synchronize()
+    Q.check_status(D.status, "full-size decomposition")
+    return D, U32t, Z
+
+
+def _check_stages(A_np, w, D, U32t, Z, sampler, seed, rows_sample=64):
+    m, n, c, r, k = A_np.shape[1], A_np.shape[2], w["c"], w["r"], w["rank_cap"]
+    A64 = A_np.astype(np.float64)
+    # probabilities
+    po, qo, _ = O.probabilities(A64, sampler)
+    col_p, row_p = host(D.col_p), host(D.row_p)
+    assert np.allclose(col_p, po, rtol=24 * U32, atol=0)
+    assert np.allclose(row_p, qo, rtol=24 * U32, atol=0)
+    # index sets (bit-exact, oracle sampler fed the library's probabilities)
+    Jo, _ = O.sample(col_p, c, seed, 0, 0, sampler)
+    Io, _ = O.sample(row_p, r, seed, 0, 1, sampler)
+    assert np.array_equal(host(D.J), Jo) and np.array_equal(host(D.I), Io)
+    # gathers (bit-exact)
+    Co, Ro, Wo = O.gather(A64, Io, Jo)
+    assert np.array_equal(host(D.C).astype(np.float64), Co)
+    assert np.array_equal(host(D.R).astype(np.float64), Ro)
+    assert np.array_equal(host(D.W), Wo)
+    # pseudo-inverse
+    Uo, ko, so = O.pinv_truncated(Wo, w["rcond"], k)
+    assert int(host(D.rank)[0]) == ko == k
+    kap = so[0] / so[k - 1]
+    errU = rel_fro(host(D.U), Uo)
+    assert errU < 64 * U32 * kap * kap, (errU, kap)
+    # sampled rows of Z = C (U R), oracle on the same FP32 U
+    U64 = host(U32t).astype(np.float64)
+    T = QT.qmatmul(U64, Ro)
+    rows = np.random.default_rng(7).choice(m, size=min(rows_sample, m), replace=False)
+    Zs = QT.qmatmul(Co[:, rows, :], T)
+    errZ = rel_fro(host(Z)[:, rows, :], Zs)
+    # full FP64 reconstruction for the residual
+    Zo = QT.qmatmul(Co, T)
+    rel_o = O.residual(A64, Zo)[0]
+    rel = float(host(D.out3)[0])
+    # BF16X3 worst case through both products: 24 * 2^-16 || |C| |U| |R| || / ||Z||
+    mod = lambda X: np.sqrt((X ** 2).sum(0))
+    bound = 24 * 2.0 ** -16 * np.linalg.norm(mod(Co[:, rows, :]) @ mod(U64) @ mod(Ro)) / np.linalg.norm(Zs)
+    return errU, kap, errZ, rel, rel_o, bound
+
+
+def _bf16x3_error(A, D, U32t, rows_idx, Zs):
+    ws = Q.workspace(A.shape[1], A.shape[2], D.c, D.r, Q.PREC_BF16X3)
+    st = Q.status_tensor()
+    Z = torch.empty(4, A.shape[1], A.shape[2], dtype=torch.float32, device="cuda")
+    Q.reconstruct(D.C, U32t, D.R, Q.PREC_BF16X3, Z, ws, st)
+    torch.cuda.synchronize()
+    Q.check_status(st, "BF16X3 reconstruction")
+    return rel_fro(host(Z)[:, rows_idx, :], Zs)
+
+
+def _full_case(name, sampler_q, sampler_o, seed):
+    w = synth.WORKLOADS[name]
+    A_np = synth.make(name)
+    A = dev(A_np)
+    D, U32t, Z = _decompose_like_bench(A, w, Q.PREC_BF16_MIXED, sampler_q, seed)
+    errU, kap, errZ, rel, rel_o, bound = _check_stages(A_np, w, D, U32t, Z, sampler_o, seed)
+    assert errZ < 1e-5, errZ
+    assert abs(rel - rel_o) < 1e-5, (rel, rel_o)
+    # the three-product split on the same operands, against its bound
+    m = A_np.shape[1]
+    rows = np.random.default_rng(7).choice(m, size=min(64, m), replace=False)
+    Co = host(D.C).astype(np.float64)
+    T = QT.qmatmul(host(U32t).astype(np.float64), host(D.R).astype(np.float64))
+    Zs = QT.qmatmul(Co[:, rows, :], T)
+    e3 = _bf16x3_error(A, D, U32t, rows, Zs)
+    assert e3 < bound, (e3, bound)
+
+
+def test_bench_workload_full_size():
+    _full_case("gauss2048_rank50_noisy", Q.SAMPLER_NORM, O.SAMPLER_NORM, 1234)
+
+
+def test_color4096_full_size():
+    _full_case("color4096_smooth100", Q.SAMPLER_UNIFORM, O.SAMPLER_UNIFORM, 99)
+
+
+def test_batch512_full_size():
+    probs = synth.batch_problems(count=512, seed=3)
+    As = [dev(p["X"]) for p in probs]
+    B = Q.Batch(As, [p["c"] for p in probs], [p["r"] for p in probs],
+                [p["rank"] for p in probs], sampler=Q.SAMPLER_NORM, seed=17)
+    B.run()
+    torch.cuda.synchronize()
+    assert int(B.status.item()) == 0
+    for b, p in enumerate(probs):
+        info = host(B.get(b, "info"))
+        assert info[2] == 0 and info[0] == p["rank"], (b, info)
+        rel = host(B.get(b, "out3"))[0]
+        assert np.isfinite(rel)
+        if b % 32:
+            continue
+        A64 = p["X"].astype(np.float64)
+        col_p, row_p = host(B.get(b, "col_p")), host(B.get(b, "row_p"))
+        Jo, _ = O.sample(col_p, p["c"], 17, b, 0, O.SAMPLER_NORM)
+        Io, _ = O.sample(row_p, p["r"], 17, b, 1, O.SAMPLER_NORM)
+        assert np.array_equal(host(B.get(b, "J")), Jo)
+        assert np.array_equal(host(B.get(b, "I")), Io)
+        Co, Ro, Wo = O.gather(A64, Io, Jo)
+        U = host(B.get(b, "U")).astype(np.float64)
+        Uo, ko, so = O.pinv_truncated(Wo, 1e-10, p["rank"])
+        kap = so[0] / so[ko - 1]
+        assert rel_fro(U, Uo) < 8 * p["c"] * U32 * kap, (b, kap)
+        rel_o = O.residual(A64, O.reconstruct(Co, U, Ro))[0]
+        assert abs(rel - rel_o) < 1e-5, (b, rel, rel_o)
+    B.close()
