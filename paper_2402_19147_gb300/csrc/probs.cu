@@ -3,10 +3,14 @@
 //   QMCUR_uniform p_j = 1/n, q_i = 1/m.
 // One streaming pass over the four planes (HBM bound): a CTA owns a tile of
 // kRows rows x kCols columns; each thread owns 4 adjacent columns, so a warp
-// reads 512 contiguous bytes of a row per plane (float4).  Squares are summed
-// in FP32 over short runs (16 terms for a row piece, 32 for a column piece)
-// and carried in FP64 from there on.  Every reduction has a fixed order, so
-// the result is bit-reproducible and no atomics touch values.
+// reads 512 contiguous bytes of a row per plane (float4), and keeps the loads
+// of kUnroll rows in flight at once (the pass is latency-bound otherwise).
+// Squares are summed in FP32 over short runs (16 terms for a row piece, 32
+// for a column piece) and carried in FP64 from there on.  Every reduction has
+// a fixed order, so the result is bit-reproducible and no atomics touch
+// values.  Three launches: the pass, the fold of the tile partials, and the
+// scaling, in which every CTA forms ||X||_F^2 itself in the same order (GB300's
+// FP64 divide is slow enough that the scaling wants many SMs).
 #include <mutex>
 
 #include "common.cuh"
@@ -14,7 +18,7 @@
 namespace qmcur {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 64;
 constexpr int kRows = 32;              // rows per CTA tile
 constexpr int kFlush = 8;              // FP32 column run length (rows)
 constexpr int kCols = kThreads * 4;    // columns per CTA tile
@@ -58,30 +62,45 @@ k_norm_partial(QView A, bool vec, double* __restrict__ col_part, double* __restr
   const T* P1 = plane<T>(A, 1);
   const T* P2 = plane<T>(A, 2);
   const T* P3 = plane<T>(A, 3);
-  for (int rr = 0; rr < kRows; ++rr) {
-    const int64_t i = i0 + rr;
-    acc_t rs = 0;
-    if (i < m) {
-      T x[4][4];
-      load4<T>(P0 + i * A.ld, j0, n, vec, x[0]);
-      load4<T>(P1 + i * A.ld, j0, n, vec, x[1]);
-      load4<T>(P2 + i * A.ld, j0, n, vec, x[2]);
-      load4<T>(P3 + i * A.ld, j0, n, vec, x[3]);
+  // rows in flight per thread: four planes x four values each
+  constexpr int kUnroll = sizeof(T) == 4 ? 8 : 4;
+  static_assert(kFlush % kUnroll == 0 && kRows % kFlush == 0, "whole runs");
+  for (int r0 = 0; r0 < kRows; r0 += kUnroll) {
+    T x[kUnroll][4][4];
+#pragma unroll
+    for (int h = 0; h < kUnroll; ++h) {
+      const int64_t i = i0 + r0 + h;
+      if (i < m) {
+        load4<T>(P0 + i * A.ld, j0, n, vec, x[h][0]);
+        load4<T>(P1 + i * A.ld, j0, n, vec, x[h][1]);
+        load4<T>(P2 + i * A.ld, j0, n, vec, x[h][2]);
+        load4<T>(P3 + i * A.ld, j0, n, vec, x[h][3]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) x[h][t][u] = T(0);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < kUnroll; ++h) {
+      const int rr = r0 + h;
+      acc_t rs = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         acc_t s = 0;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) s = fma((acc_t)x[t][u], (acc_t)x[t][u], s);
+        for (int t = 0; t < 4; ++t) s = fma((acc_t)x[h][t][u], (acc_t)x[h][t][u], s);
         col32[u] += s;
         rs += s;
       }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-    if (lane == 0) row_warp[rr][warp] = rs;
-    if ((rr + 1) % kFlush == 0) {
+      for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+      if (lane == 0) row_warp[rr][warp] = rs;
+      if ((rr + 1) % kFlush == 0) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) { col64[u] += (double)col32[u]; col32[u] = 0; }
+        for (int u = 0; u < 4; ++u) { col64[u] += (double)col32[u]; col32[u] = 0; }
+      }
     }
   }
 #pragma unroll
@@ -99,51 +118,93 @@ k_norm_partial(QView A, bool vec, double* __restrict__ col_part, double* __restr
   }
 }
 
-// col2[j] = sum over row tiles (fixed order), row2[i] = sum over column tiles.
-__global__ void k_norm_fold(const double* __restrict__ col_part, const double* __restrict__ row_part,
-                            int64_t m, int64_t n, int rtiles, int ctiles, double* __restrict__ col2,
-                            double* __restrict__ row2) {
-  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g < n) {
-    double s = 0.0;
-    for (int t = 0; t < rtiles; ++t) s += col_part[(int64_t)t * n + g];
-    col2[g] = s;
-  } else if (g < n + m) {
-    int64_t i = g - n;
-    double s = 0.0;
-    for (int t = 0; t < ctiles; ++t) s += row_part[(int64_t)t * m + i];
-    row2[i] = s;
+// col2[j] = sum over row tiles, row2[i] = sum over column tiles.  A CTA
+// folds 32 consecutive outputs (columns first, then rows): its kFoldGroups
+// thread groups each sum a contiguous run of tiles left to right (loads
+// issued together), then group 0 adds the group sums in group order; a
+// column CTA also writes the sum of its 32 col2 values (a fixed shuffle
+// tree) to blocktot.  The orders are fixed, so the result is reproducible.
+constexpr int kFoldGroups = 8;
+
+__global__ void __launch_bounds__(32 * kFoldGroups)
+k_norm_fold(const double* __restrict__ col_part, const double* __restrict__ row_part, int64_t m,
+            int64_t n, int rtiles, int ctiles, double* __restrict__ col2,
+            double* __restrict__ row2, double* __restrict__ blocktot) {
+  __shared__ double part[kFoldGroups][32];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int64_t col_blocks = (n + 31) / 32;
+  const bool cols = blockIdx.x < col_blocks;
+  const int64_t base = cols ? (int64_t)blockIdx.x * 32 : ((int64_t)blockIdx.x - col_blocks) * 32;
+  const int64_t len = cols ? n : m, idx = base + lane;
+  const int tiles = cols ? rtiles : ctiles;
+  const double* src = cols ? col_part : row_part;
+  const int per = (tiles + kFoldGroups - 1) / kFoldGroups;
+  const int t0 = grp * per, t1 = t0 + per < tiles ? t0 + per : tiles;
+  double s = 0.0;
+  if (idx < len) {
+    constexpr int kBatch = 8;
+    for (int tb = t0; tb < t1; tb += kBatch) {
+      double v[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) v[u] = tb + u < t1 ? src[(int64_t)(tb + u) * len + idx] : 0.0;
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) s += v[u];
+    }
+  }
+  part[grp][lane] = s;
+  __syncthreads();
+  if (grp == 0) {
+    double tot = 0.0;
+    if (idx < len) {
+      tot = part[0][lane];
+#pragma unroll
+      for (int g = 1; g < kFoldGroups; ++g) tot += part[g][lane];
+      (cols ? col2 : row2)[idx] = tot;
+    }
+    if (cols) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      if (lane == 0) blocktot[blockIdx.x] = tot;
+    }
   }
 }
 
-// F = sum_j col2[j] by one CTA in a fixed order; reports NONFINITE / ZERO_NORM.
-__global__ void __launch_bounds__(1024)
-k_norm_total(const double* __restrict__ col2, int64_t n, double* __restrict__ F_out,
-             double* __restrict__ fro2, int check_zero, int32_t* status) {
-  __shared__ double red[1024];
+// F = the sum of the fold's column-block totals in a fixed order, formed by
+// every CTA (bit-identical copies); CTA 0 reports NONFINITE / ZERO_NORM and
+// writes fro2.  With `scale`
+// the CTAs then write their grid-strided share of col_p = col2 (1 / F) and
+// row_p = row2 (1 / F) (separate buffers: no CTA rewrites what another reads;
+// one FP64 division per CTA, the rest multiplies, within an ulp of col2 / F).
+constexpr int kScaleThreads = 256;
+
+__global__ void __launch_bounds__(kScaleThreads)
+k_norm_total_scale(const double* __restrict__ col2, const double* __restrict__ row2,
+                   const double* __restrict__ blocktot, int64_t m, int64_t n,
+                   double* __restrict__ col_p, double* __restrict__ row_p,
+                   double* __restrict__ fro2, int scale, int32_t* status) {
+  __shared__ double red[kScaleThreads];
   double s = 0.0;
-  for (int64_t j = threadIdx.x; j < n; j += 1024) s += col2[j];
+  const int64_t nb = (n + 31) / 32;
+  for (int64_t j = threadIdx.x; j < nb; j += kScaleThreads) s += blocktot[j];
   red[threadIdx.x] = s;
   __syncthreads();
-  for (int w = 512; w > 0; w >>= 1) {
+  for (int w = kScaleThreads / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    double F = red[0];
-    *F_out = F;
+  const double F = red[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (fro2 != nullptr) *fro2 = F;
     if (!isfinite(F)) set_status(status, QMCUR_ERR_NONFINITE);
-    else if (check_zero && F == 0.0) set_status(status, QMCUR_ERR_ZERO_NORM);
+    else if (scale && F == 0.0) set_status(status, QMCUR_ERR_ZERO_NORM);
   }
-}
-
-__global__ void k_norm_scale(double* __restrict__ col_p, double* __restrict__ row_p, int64_t m,
-                             int64_t n, const double* __restrict__ F_in) {
-  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const double F = *F_in;
-  if (g < n) col_p[g] = col_p[g] / F;
-  else if (g < n + m) row_p[g - n] = row_p[g - n] / F;
+  if (!scale) return;
+  const double rF = 1.0 / F;
+  const int64_t stride = (int64_t)gridDim.x * kScaleThreads;
+  for (int64_t g = (int64_t)blockIdx.x * kScaleThreads + threadIdx.x; g < n + m; g += stride) {
+    if (g < n) col_p[g] = col2[g] * rF;
+    else row_p[g - n] = row2[g - n] * rF;
+  }
 }
 
 __global__ void k_uniform(double* __restrict__ col_p, double* __restrict__ row_p, int64_t m, int64_t n) {
@@ -162,7 +223,7 @@ size_t probs_ws_bytes(int64_t m, int64_t n) {
   c.take<double>((size_t)(rt * n));
   c.take<double>((size_t)(ct * m));
   c.take<double>((size_t)(n + m));
-  c.take<double>(4);
+  c.take<double>((size_t)cdiv(n, 32) + 4);
   return c.off;
 }
 
@@ -185,13 +246,12 @@ qmcur_status launch_probs(const qmcur_qmat* A, int32_t sampler, double* col_p, d
   double* col_part = cv.take<double>((size_t)(rt * n));
   double* row_part = cv.take<double>((size_t)(ct * m));
   double* sums = cv.take<double>((size_t)(n + m));
-  double* F = cv.take<double>(4);
+  double* blocktot = cv.take<double>((size_t)cdiv(n, 32) + 4);
   if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
-  // Norm mode folds the sums straight into the outputs; uniform mode (which
-  // only wants ||A||_F^2) folds them into scratch, the outputs hold 1/n, 1/m.
-  double* col2 = col_p;
-  double* row2 = row_p;
-  if (sampler == QMCUR_SAMPLER_UNIFORM) { col2 = sums; row2 = sums + n; }
+  // The squared norms go to scratch; norm mode then writes the outputs from
+  // them, uniform mode (which only wants ||A||_F^2) keeps 1/n, 1/m.
+  double* col2 = sums;
+  double* row2 = sums + n;
   QView v = view(A);
   const size_t es = esize(A->dtype);
   bool vec = (A->ld * es) % 16 == 0;
@@ -199,9 +259,12 @@ qmcur_status launch_probs(const qmcur_qmat* A, int32_t sampler, double* col_p, d
   dim3 grid((unsigned)ct, (unsigned)rt);
   if (A->dtype == QMCUR_F32) k_norm_partial<float><<<grid, kThreads, 0, st>>>(v, vec, col_part, row_part);
   else k_norm_partial<double><<<grid, kThreads, 0, st>>>(v, vec, col_part, row_part);
-  k_norm_fold<<<fold_blocks, 256, 0, st>>>(col_part, row_part, m, n, (int)rt, (int)ct, col2, row2);
-  k_norm_total<<<1, 1024, 0, st>>>(col2, n, F, fro2, sampler == QMCUR_SAMPLER_NORM, dev_status);
-  if (sampler == QMCUR_SAMPLER_NORM) k_norm_scale<<<fold_blocks, 256, 0, st>>>(col_p, row_p, m, n, F);
+  const int fold_ctas = (int)(cdiv(n, 32) + cdiv(m, 32));
+  k_norm_fold<<<fold_ctas, 32 * kFoldGroups, 0, st>>>(col_part, row_part, m, n, (int)rt, (int)ct,
+                                                      col2, row2, blocktot);
+  const int64_t scale_ctas = cdiv(n + m, kScaleThreads) < 64 ? cdiv(n + m, kScaleThreads) : 64;
+  k_norm_total_scale<<<(unsigned)scale_ctas, kScaleThreads, 0, st>>>(
+      col2, row2, blocktot, m, n, col_p, row_p, fro2, sampler == QMCUR_SAMPLER_NORM, dev_status);
   return cuda_ok(cudaGetLastError());
 }
 

@@ -308,18 +308,25 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
         if (!mbar_wait(&full[s], ph, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t sa = saddr(smem + s * STAGE), sb = sa + A_STAGE;
+        // Descriptors of the stage's first A and B rows; every other operand
+        // of the stage lies a constant number of 16-byte units further on, and
+        // stage offsets stay below 2^18 bytes, so adding (offset >> 4) to the
+        // 14-bit start-address field never carries out of it.
+        const uint64_t ad0 = sdesc(sa), bd0 = sdesc(sb);
         const int kb = ki % p.kblocks;
         const int kleft = p.K - kb * kElemsPerRow;          // valid elements in this slice
         const int ksteps = kleft >= kElemsPerRow ? ROWB / 32 : (kleft + kStepElems - 1) / kStepElems;
 #pragma unroll
         for (int ks = 0; ks < ROWB / 32; ++ks) {
           if (ks >= ksteps) break;
+          // consecutive MMAs write different accumulators (output planes)
+          // and share their A operand
 #pragma unroll
-          for (int pl = 0; pl < 4; ++pl) {
+          for (int t = 0; t < 4; ++t) {
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              const uint64_t ad = sdesc(sa + t * A_PLANE + ks * 32);
-              const uint64_t bd = sdesc(sb + kY[pl][t] * B_PLANE + ks * 32);
+            for (int pl = 0; pl < 4; ++pl) {
+              const uint64_t ad = ad0 + (uint64_t)((t * A_PLANE + ks * 32) >> 4);
+              const uint64_t bd = bd0 + (uint64_t)((kY[pl][t] * B_PLANE + ks * 32) >> 4);
               const uint32_t acc = (ki > 0 || ks > 0 || t > 0) ? 1u : 0u;
               umma<BF16>(dbase + pl * BN, ad, bd, kNeg[pl][t] ? kIdNeg : kIdPos, acc);
             }
