@@ -48,62 +48,129 @@ struct SampleArgs {
   int32_t* attempts_out;  // optional: draws consumed per set (2 ints)
 };
 
+// Exclusive prefix sum of one int per thread over the CTA (kSampleThreads).
+__device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int own = lane < kSampleThreads / 32 ? warp_tot[lane] : 0;
+    int t = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kSampleThreads / 32) warp_tot[lane] = t - own;   // exclusive
+  }
+  __syncthreads();
+  const int r = warp_tot[warp] + x - v;
+  __syncthreads();
+  return r;
+}
+
 // One index set (set 0: J over columns, 1: I over rows) by one CTA of
 // kSampleThreads threads; `dyn` is the CTA's dynamic shared memory.
+//
+// The draws and their acceptance are defined sequentially (draw t in counter
+// order; a draw that repeats an accepted index is rejected; stop when the
+// set is full).  Here warp 0 takes a round's candidates 32 at a time: a
+// candidate is new when its index is not in the bitmap and no earlier
+// candidate of its 32 carries the same index (__match_any_sync); the new
+// ones are taken in lane order until the set is full.  This accepts exactly
+// the indices, and consumes exactly the draws, of the sequential definition.
 __device__ __forceinline__ void sample_one_set(const SampleArgs& a, int set, int P_in_smem,
                                                unsigned char* dyn) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t N = a.N[set];
   const int64_t count = a.count[set];
   const double* p = a.prob[set];
   const int64_t words = (N + 31) / 32;
   // Dynamic shared memory: the acceptance bitmap (and the prefix sums when
-  // they fit), so that the sequential acceptance and the binary searches stay
-  // on chip.
+  // they fit), so that the acceptance and the binary searches stay on chip.
   uint32_t* bits = reinterpret_cast<uint32_t*>(dyn);
   double* P = P_in_smem ? reinterpret_cast<double*>(dyn + ((words * 4 + 15) / 16) * 16) : a.P[set];
 
   __shared__ double blk_total[kPrefixBlocks];
   __shared__ double blk_off[kPrefixBlocks];
-  __shared__ int64_t blk_support[kPrefixBlocks];
-  __shared__ int64_t blk_last[kPrefixBlocks];
+  __shared__ long long red_sup[kSampleThreads / 32];
+  __shared__ long long red_last[kSampleThreads / 32];
   __shared__ double S_sh;
   __shared__ int64_t last_pos_sh;
   __shared__ int abort_sh;
   __shared__ int64_t cand[kSampleThreads];
   __shared__ int64_t accepted_sh;
   __shared__ int64_t used_sh;
-  __shared__ int64_t scan[kSampleThreads];
+  __shared__ int warp_tot[kSampleThreads / 32];
+  static_assert(kPrefixBlocks == kSampleThreads, "one prefix block per thread");
+  static_assert(kPrefixBlocks % 16 == 0, "chain batches of 16");
 
   for (int64_t w = tid; w < words; w += kSampleThreads) bits[w] = 0u;
   if (tid == 0) { abort_sh = 0; accepted_sh = 0; used_sh = 0; S_sh = 0.0; last_pos_sh = -1; }
 
   if (a.norm) {
+    // stage p (coalesced, eight loads in flight per thread)
+    for (int64_t k0 = tid; k0 < N; k0 += 8 * kSampleThreads) {
+      double v[8];
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const int64_t k = k0 + (int64_t)h * kSampleThreads;
+        v[h] = k < N ? p[k] : 0.0;
+      }
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const int64_t k = k0 + (int64_t)h * kSampleThreads;
+        if (k < N) P[k] = v[h];
+      }
+    }
+    __syncthreads();
+    // block b = tid: running sum of its L entries left to right
     const int64_t L = (N + kPrefixBlocks - 1) / kPrefixBlocks;
     const int64_t lo = (int64_t)tid * L;
     const int64_t hi = lo + L < N ? lo + L : N;
     double s = 0.0;
-    int64_t sup = 0, last = -1;
+    long long sup = 0, last = -1;
     for (int64_t k = lo; k < hi; ++k) {
-      const double pk = p[k];
+      const double pk = P[k];
       s = (k == lo) ? pk : __dadd_rn(s, pk);
       P[k] = s;
       if (pk > 0.0) { ++sup; last = k; }
     }
     blk_total[tid] = (lo < hi) ? s : 0.0;
-    blk_support[tid] = sup;
-    blk_last[tid] = last;
+    // support count and last positive index: warp then CTA reductions
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sup += __shfl_xor_sync(0xffffffffu, sup, o);
+      const long long ol = __shfl_xor_sync(0xffffffffu, last, o);
+      last = ol > last ? ol : last;
+    }
+    if (lane == 0) { red_sup[warp] = sup; red_last[warp] = last; }
     __syncthreads();
     if (tid == 0) {
+      // block totals chained left to right (the defined order), read in batches
       double o = 0.0;
-      int64_t support = 0, lastp = -1;
-      for (int b = 0; b < kPrefixBlocks; ++b) {
-        blk_off[b] = o;
-        o = __dadd_rn(o, blk_total[b]);
-        support += blk_support[b];
-        if (blk_last[b] > lastp) lastp = blk_last[b];
+      for (int b0 = 0; b0 < kPrefixBlocks; b0 += 16) {
+        double tv[16];
+#pragma unroll
+        for (int h = 0; h < 16; ++h) tv[h] = blk_total[b0 + h];
+#pragma unroll
+        for (int h = 0; h < 16; ++h) {
+          blk_off[b0 + h] = o;
+          o = __dadd_rn(o, tv[h]);
+        }
       }
       S_sh = o;
+      long long support = 0, lastp = -1;
+      for (int w = 0; w < kSampleThreads / 32; ++w) {
+        support += red_sup[w];
+        if (red_last[w] > lastp) lastp = red_last[w];
+      }
       last_pos_sh = lastp;
       if (support < count) { abort_sh = 1; set_status(a.status, QMCUR_ERR_INSUFFICIENT_SUPPORT); }
     }
@@ -136,19 +203,40 @@ __device__ __forceinline__ void sample_one_set(const SampleArgs& a, int set, int
     }
     cand[tid] = k;
     __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
       int64_t acc = accepted_sh;
-      for (int j = 0; j < kSampleThreads && acc < count; ++j) {
+      int64_t used = used_sh;
+      for (int q = 0; q < kSampleThreads / 32; ++q) {
+        const int j = q * 32 + lane;
         const int64_t kk = cand[j];
-        if (kk < 0) break;
-        used_sh = base + j + 1;
-        const uint32_t bit = 1u << (kk & 31);
-        if (!(bits[kk >> 5] & bit)) { bits[kk >> 5] |= bit; ++acc; }
+        const unsigned vmask = __ballot_sync(0xffffffffu, kk >= 0);
+        const int firstinv = vmask == 0xffffffffu ? 32 : __ffs(~vmask) - 1;   // draws end there
+        const bool live = lane < firstinv;
+        const bool seen = live && ((bits[kk >> 5] >> (kk & 31)) & 1u);
+        const unsigned same = __match_any_sync(0xffffffffu, live ? (unsigned long long)kk
+                                                                  : ~(unsigned long long)lane);
+        const bool isnew = live && !seen && (__ffs(same) - 1) == lane;
+        const unsigned newmask = __ballot_sync(0xffffffffu, isnew);
+        const int64_t need = count - acc;
+        const int rank = __popc(newmask & ((1u << lane) - 1u));
+        if (isnew && rank < need) atomicOr(&bits[kk >> 5], 1u << (kk & 31));
+        const int nnew = __popc(newmask);
+        if (nnew >= need) {
+          // the candidate that fills the set: the need-th new lane
+          const unsigned fin = __ballot_sync(0xffffffffu, isnew && rank == need - 1);
+          used = base + q * 32 + (__ffs(fin) - 1) + 1;
+          acc = count;
+          break;
+        }
+        acc += nnew;
+        used = base + q * 32 + firstinv;
+        __syncwarp();
+        if (firstinv < 32) break;
       }
-      accepted_sh = acc;
+      if (lane == 0) { accepted_sh = acc; used_sh = used; }
     }
     __syncthreads();
-    if (accepted_sh >= count) break;
+    if (accepted_sh >= count || cand[kSampleThreads - 1] < 0) break;
   }
   if (tid == 0) {
     if (accepted_sh < count) set_status(a.status, QMCUR_ERR_SAMPLE_LIMIT);
@@ -159,22 +247,15 @@ __device__ __forceinline__ void sample_one_set(const SampleArgs& a, int set, int
   // Ascending output: each thread owns a contiguous range of bitmap words.
   const int64_t w0 = words * tid / kSampleThreads;
   const int64_t w1 = words * (tid + 1) / kSampleThreads;
-  int64_t mine = 0;
+  int mine = 0;
   for (int64_t w = w0; w < w1; ++w) mine += __popc(bits[w]);
-  scan[tid] = mine;
-  __syncthreads();
-  if (tid == 0) {
-    int64_t run = 0;
-    for (int j = 0; j < kSampleThreads; ++j) { const int64_t v = scan[j]; scan[j] = run; run += v; }
-  }
-  __syncthreads();
-  int64_t pos = scan[tid];
+  int64_t pos = block_exclusive_scan(mine, warp_tot);
   int32_t* out = a.out[set];
   for (int64_t w = w0; w < w1; ++w) {
-    uint32_t b = bits[w];
-    while (b) {
-      const int bit = __ffs(b) - 1;
-      b &= b - 1;
+    uint32_t bb = bits[w];
+    while (bb) {
+      const int bit = __ffs(bb) - 1;
+      bb &= bb - 1;
       if (pos < count) out[pos] = (int32_t)(w * 32 + bit);
       ++pos;
     }
