@@ -198,23 +198,31 @@ k_residual(QView A, QView Z, const uint8_t* __restrict__ mask, double* __restric
 // Fold per-CTA (num, den) pairs in a fixed order: out3 = {rel, num, den}.
 __global__ void __launch_bounds__(1024) k_residual_fold(const double* __restrict__ partial, int64_t count,
                                                         double* __restrict__ out3) {
-  __shared__ double red[2][1024];
+  // strided sums, then a fixed shuffle tree per warp and across the warps
+  __shared__ double red[2][32];
   double num = 0.0, den = 0.0;
   for (int64_t k = threadIdx.x; k < count; k += 1024) { num += partial[2 * k]; den += partial[2 * k + 1]; }
-  red[0][threadIdx.x] = num;
-  red[1][threadIdx.x] = den;
-  __syncthreads();
-  for (int w = 512; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      red[0][threadIdx.x] += red[0][threadIdx.x + w];
-      red[1][threadIdx.x] += red[1][threadIdx.x + w];
-    }
-    __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
   }
-  if (threadIdx.x == 0) {
-    out3[1] = red[0][0];
-    out3[2] = red[1][0];
-    out3[0] = red[1][0] > 0.0 ? sqrt(red[0][0] / red[1][0]) : __longlong_as_double(0x7ff8000000000000ll);
+  if (lane == 0) { red[0][warp] = num; red[1][warp] = den; }
+  __syncthreads();
+  if (warp == 0) {
+    num = red[0][lane];
+    den = red[1][lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      num += __shfl_xor_sync(0xffffffffu, num, o);
+      den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if (lane == 0) {
+      out3[1] = num;
+      out3[2] = den;
+      out3[0] = den > 0.0 ? sqrt(num / den) : __longlong_as_double(0x7ff8000000000000ll);
+    }
   }
 }
 

@@ -47,18 +47,26 @@ __global__ void k_residual_fold(const double* partial, int64_t count, double* ou
 
 namespace {
 
-constexpr int BM = 128, BN = 64;
+constexpr int BM = 128;
 constexpr int ROWB = 64;                      // bytes of K per shared row (one swizzle row)
-constexpr int STAGES = 4;
 constexpr int A_PLANE = BM * ROWB;            // 8 KiB
-constexpr int B_PLANE = BN * ROWB;            // 4 KiB
 constexpr int A_STAGE = 4 * A_PLANE;
-constexpr int B_STAGE = 4 * B_PLANE;
-constexpr int STAGE = A_STAGE + B_STAGE;      // 48 KiB
-constexpr int ACC_COLS = 4 * BN;              // FP32 TMEM columns per accumulator
-constexpr int TMEM_COLS = 2 * ACC_COLS;       // 512: two accumulators
 constexpr int kTcThreads = 192;
-constexpr int kTcSmem = STAGES * STAGE + 1024 + 256;
+
+// Shape of one instantiation: output tiles of BM x BNT (per plane).  BNT = 64
+// for the large product Z = C T; BNT = 32 for T = U R, whose c = O(100) rows
+// give too few 128 x 64 tiles to occupy the GPU.
+template <int BNT>
+struct TcShape {
+  static constexpr int BN = BNT;
+  static constexpr int B_PLANE = BN * ROWB;            // 4 KiB at BN 64
+  static constexpr int B_STAGE = 4 * B_PLANE;
+  static constexpr int STAGE = A_STAGE + B_STAGE;      // 48 KiB at BN 64
+  static constexpr int STAGES = BN == 64 ? 4 : 5;
+  static constexpr int ACC_COLS = 4 * BN;              // FP32 TMEM columns per accumulator
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;       // two accumulators (a power of two)
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+};
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
 enum { MODE_STORE_Z = 0, MODE_RESIDUAL = 1, MODE_SPLIT_T = 2 };
@@ -162,9 +170,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 // Instruction descriptor of kind::f16 (BF16 operands) or kind::tf32: FP32
 // accumulator (bits 4-5 = 1), A/B formats (bits 7-9, 10-12), negate A (bit 13),
 // both operands K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-__host__ __device__ constexpr uint32_t make_idesc(bool bf16, bool neg_a) {
+__host__ __device__ constexpr uint32_t make_idesc(bool bf16, bool neg_a, int n) {
   return (1u << 4) | ((bf16 ? 1u : 2u) << 7) | ((bf16 ? 1u : 2u) << 10) |
-         ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+         ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 template <bool BF16>
@@ -213,27 +221,33 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // Pieces of one value: BF16 (npieces 2 or 3) or TF32 (npieces 2).
 template <bool BF16, typename T>
 __device__ __forceinline__ void split_value(T x, int npieces, float out[3]) {
+  // The pieces carry at most ~24 significant bits, so the split runs in FP32
+  // (GB300's FP64 rate is 1/64 of FP32); each residual below is exact in FP32.
+  const float xf = (float)x;
   if constexpr (BF16) {
-    const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
-    const T r1 = x - (T)__bfloat162float(h);
-    const __nv_bfloat16 m = __float2bfloat16_rn((float)r1);
-    const T r2 = r1 - (T)__bfloat162float(m);
+    const __nv_bfloat16 h = __float2bfloat16_rn(xf);
+    const float r1 = xf - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
     out[0] = __bfloat162float(h);
     out[1] = __bfloat162float(m);
-    out[2] = npieces > 2 ? __bfloat162float(__float2bfloat16_rn((float)r2)) : 0.f;
+    out[2] = npieces > 2 ? __bfloat162float(__float2bfloat16_rn(r2)) : 0.f;
   } else {
-    const float b = tf32_rna((float)x);
+    const float b = tf32_rna(xf);
     out[0] = b;
-    out[1] = (float)(x - (T)b);
+    out[1] = xf - b;
     out[2] = 0.f;
   }
 }
 
 // ------------------------------------------------------------------ kernel -
-template <bool BF16>
+template <bool BF16, int BNT>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
            TcParams p) {
+  using Sh = TcShape<BNT>;
+  constexpr int BN = Sh::BN, B_PLANE = Sh::B_PLANE, STAGE = Sh::STAGE, STAGES = Sh::STAGES;
+  constexpr int ACC_COLS = Sh::ACC_COLS, TMEM_COLS = Sh::TMEM_COLS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -247,7 +261,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 
   constexpr int kY[4][4] = {{0, 1, 2, 3}, {1, 0, 3, 2}, {2, 3, 0, 1}, {3, 2, 1, 0}};
   constexpr int kNeg[4][4] = {{0, 1, 1, 1}, {0, 0, 0, 1}, {0, 1, 0, 0}, {0, 0, 1, 0}};
-  constexpr uint32_t kIdPos = make_idesc(BF16, false), kIdNeg = make_idesc(BF16, true);
+  constexpr uint32_t kIdPos = make_idesc(BF16, false, BN), kIdNeg = make_idesc(BF16, true, BN);
   constexpr int kElemsPerRow = ROWB / (BF16 ? 2 : 4);
   constexpr int kStepElems = 32 / (BF16 ? 2 : 4);          // K of one MMA (32 bytes)
 
@@ -583,6 +597,8 @@ struct TcWs {
   double* partial;
 };
 
+constexpr int kBn1 = 32, kBn2 = 64;   // tile widths of T = U R and Z = C T
+
 TcWs carve_tc(Carve& cv, const TcPlan& p1, const TcPlan& p2, int64_t m, int64_t n, int64_t c,
               int64_t r) {
   const int64_t es = p1.bf16 ? 2 : 4;   // both plans have the same element type
@@ -592,7 +608,7 @@ TcWs carve_tc(Carve& cv, const TcPlan& p1, const TcPlan& p2, int64_t m, int64_t 
   w.B1 = cv.take<char>((size_t)(p1.npieces * 4 * n * kp1 * es));
   w.A2 = cv.take<char>((size_t)(p2.npieces * 4 * m * kp2 * es));
   w.B2 = cv.take<char>((size_t)(p2.npieces * 4 * n * kp2 * es));
-  const int64_t tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+  const int64_t tiles = ((m + BM - 1) / BM) * ((n + kBn2 - 1) / kBn2);
   w.partial = cv.take<double>((size_t)(2 * tiles));
   return w;
 }
@@ -613,23 +629,23 @@ qmcur_status launch_split(const qmcur_qmat* S, bool trans, void* dst, int64_t ro
   return cuda_ok(cudaGetLastError());
 }
 
-template <bool BF16>
+template <bool BF16, int BNT>
 qmcur_status launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& p,
                          cudaStream_t st) {
   static bool attr_done[64] = {};
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QMCUR_ERR_CUDA;
   if (!attr_done[dev]) {
-    if (cudaFuncSetAttribute(k_qgemm_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kTcSmem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_qgemm_tc<BF16, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcShape<BNT>::SMEM) != cudaSuccess)
       return QMCUR_ERR_CUDA;
     attr_done[dev] = true;
   }
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return QMCUR_ERR_CUDA;
-  const int tiles = ((p.M + BM - 1) / BM) * ((p.N + BN - 1) / BN);
+  const int tiles = ((p.M + BM - 1) / BM) * ((p.N + BNT - 1) / BNT);
   const int grid = tiles < sms ? tiles : sms;
-  k_qgemm_tc<BF16><<<grid, kTcThreads, kTcSmem, st>>>(ma, mb, p);
+  k_qgemm_tc<BF16, BNT><<<grid, kTcThreads, TcShape<BNT>::SMEM, st>>>(ma, mb, p);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -671,9 +687,9 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
   }
   CUtensorMap mA1, mB1, mA2, mB2;
   if (!make_map(&mA1, w.A1, pl.bf16, c, kp1, pl.npieces, BM) ||
-      !make_map(&mB1, w.B1, pl.bf16, n, kp1, pl.npieces, BN) ||
+      !make_map(&mB1, w.B1, pl.bf16, n, kp1, pl.npieces, kBn1) ||
       !make_map(&mA2, w.A2, pl2.bf16, m, kp2, pl2.npieces, BM) ||
-      !make_map(&mB2, w.B2, pl2.bf16, n, kp2, pl2.npieces, BN))
+      !make_map(&mB2, w.B2, pl2.bf16, n, kp2, pl2.npieces, kBn2))
     return QMCUR_ERR_CUDA;
   TcParams p1{};
   p1.M = (int)c;
@@ -709,14 +725,14 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
     p2.partial = w.partial;
   }
   if (pl.bf16) {
-    if ((s = launch_gemm<true>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
-    if ((s = launch_gemm<true>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
+    if ((s = launch_gemm<true, kBn1>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
+    if ((s = launch_gemm<true, kBn2>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
   } else {
-    if ((s = launch_gemm<false>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
-    if ((s = launch_gemm<false>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
+    if ((s = launch_gemm<false, kBn1>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
+    if ((s = launch_gemm<false, kBn2>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
   }
   if (Z == nullptr) {
-    const int64_t tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+    const int64_t tiles = ((m + BM - 1) / BM) * ((n + kBn2 - 1) / kBn2);
     k_residual_fold<<<1, 1024, 0, st>>>(w.partial, tiles, out3);
   }
   return cuda_ok(cudaGetLastError());

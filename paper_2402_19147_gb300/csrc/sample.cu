@@ -77,7 +77,7 @@ k_gather_rows_f4(QView A, const int32_t* __restrict__ I, QView out) {
 // shared memory, then takes a row at a time: chunks of kGatherChunk columns
 // (four planes, float4, two per plane per thread in flight) go through
 // shared memory, to R when the row is in I, and C (and W) are picked from
-// them.  J and I are sorted, so a chunk's columns of J are contiguous in J and
+// them.  The pass serves calls that want C.  J and I are sorted, so a chunk's columns of J are contiguous in J and
 // the row's position in I is found by binary search.
 constexpr int kGatherThreads = 256;
 constexpr int kGatherChunk = 2048;
@@ -100,7 +100,7 @@ inline size_t gather_stream_smem(int64_t c, int64_t r) {
 template <typename TW>
 __global__ void __launch_bounds__(kGatherThreads)
 k_gather_stream(QView A, const int32_t* __restrict__ I, const int32_t* __restrict__ J, int r, int c,
-                QView C, QView R, QView W, int hasC, int hasR, int hasW) {
+                QView C, QView R, QView W, int hasR, int hasW) {
   extern __shared__ __align__(16) unsigned char gsm[];
   float* rowbuf = reinterpret_cast<float*>(gsm);                   // [4][kGatherChunk]
   int32_t* Js = reinterpret_cast<int32_t*>(rowbuf + 4 * kGatherChunk);
@@ -110,50 +110,60 @@ k_gather_stream(QView A, const int32_t* __restrict__ I, const int32_t* __restric
   __syncthreads();
   const int64_t m = A.rows, n = A.cols;
   constexpr int kPer = kGatherChunk / 4 / kGatherThreads;   // float4 per plane per thread
-  for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+  // The CTA's work is a flat list of (row, chunk) items: rows blockIdx.x,
+  // blockIdx.x + gridDim.x, ...; the loads of item k + 1 are issued before
+  // item k's columns are picked, so the pass keeps reading while it writes.
+  const int64_t nchunks = (n + kGatherChunk - 1) / kGatherChunk;
+  const int64_t my_rows = blockIdx.x < m ? (m - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t items = my_rows * nchunks;
+  float4 v[4][kPer];
+  auto load_item = [&](int64_t k) {
+    const int64_t i = blockIdx.x + (k / nchunks) * gridDim.x;
+    const int64_t c0 = (k % nchunks) * kGatherChunk;
+    const int cw = (int)(n - c0 < kGatherChunk ? n - c0 : kGatherChunk);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float* arow = reinterpret_cast<const float*>(A.p[t]) + i * A.ld + c0;
+#pragma unroll
+      for (int h = 0; h < kPer; ++h) {
+        const int q = threadIdx.x + h * kGatherThreads;
+        v[t][h] = q < cw / 4 ? reinterpret_cast<const float4*>(arow)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  };
+  if (items > 0) load_item(0);
+  for (int64_t k = 0; k < items; ++k) {
+    const int64_t i = blockIdx.x + (k / nchunks) * gridDim.x;
+    const int64_t c0 = (k % nchunks) * kGatherChunk;
+    const int cw = (int)(n - c0 < kGatherChunk ? n - c0 : kGatherChunk);
     const int ri = first_at_least(Is, r, i);
     const int rpos = (ri < r && (int64_t)Is[ri] == i) ? ri : -1;   // row of R / W, or -1
-    if (!hasC && rpos < 0) continue;
-    const float* arow[4];
+    __syncthreads();   // the previous item's chunk is no longer read
 #pragma unroll
-    for (int t = 0; t < 4; ++t) arow[t] = reinterpret_cast<const float*>(A.p[t]) + i * A.ld;
-    for (int64_t c0 = 0; c0 < n; c0 += kGatherChunk) {
-      const int cw = (int)(n - c0 < kGatherChunk ? n - c0 : kGatherChunk);
-      float4 v[4][kPer];
+    for (int t = 0; t < 4; ++t)
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int h = 0; h < kPer; ++h) {
-          const int q = threadIdx.x + h * kGatherThreads;
-          v[t][h] = q < cw / 4 ? reinterpret_cast<const float4*>(arow[t] + c0)[q]
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int h = 0; h < kPer; ++h) {
+        const int q = threadIdx.x + h * kGatherThreads;
+        if (q < cw / 4) {
+          reinterpret_cast<float4*>(rowbuf + t * kGatherChunk)[q] = v[t][h];
+          if (hasR && rpos >= 0)
+            reinterpret_cast<float4*>(reinterpret_cast<float*>(R.p[t]) + (int64_t)rpos * R.ld + c0)[q] =
+                v[t][h];
         }
-      __syncthreads();   // the previous chunk is no longer read
+      }
+    if (k + 1 < items) load_item(k + 1);
+    __syncthreads();
+    const int b0 = first_at_least(Js, c, c0), b1 = first_at_least(Js, c, c0 + cw);
+    for (int b = b0 + threadIdx.x; b < b1; b += kGatherThreads) {
+      const int64_t jj = (int64_t)Js[b] - c0;
+      // a valid sorted J puts jj in [0, cw); after a sampling error J is
+      // unspecified, and nothing outside the chunk may be read
+      if (jj < 0 || jj >= cw) continue;
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int h = 0; h < kPer; ++h) {
-          const int q = threadIdx.x + h * kGatherThreads;
-          if (q < cw / 4) {
-            reinterpret_cast<float4*>(rowbuf + t * kGatherChunk)[q] = v[t][h];
-            if (hasR && rpos >= 0)
-              reinterpret_cast<float4*>(reinterpret_cast<float*>(R.p[t]) + (int64_t)rpos * R.ld + c0)[q] =
-                  v[t][h];
-          }
-        }
-      __syncthreads();
-      const int b0 = first_at_least(Js, c, c0), b1 = first_at_least(Js, c, c0 + cw);
-      for (int b = b0 + threadIdx.x; b < b1; b += kGatherThreads) {
-        const int64_t jj = (int64_t)Js[b] - c0;
-        // a valid sorted J puts jj in [0, cw); after a sampling error J is
-        // unspecified, and nothing outside the chunk may be read
-        if (jj < 0 || jj >= cw) continue;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const float x = rowbuf[t * kGatherChunk + jj];
-          if (hasC) reinterpret_cast<float*>(C.p[t])[i * C.ld + b] = x;
-          if (hasW && rpos >= 0) reinterpret_cast<TW*>(W.p[t])[(int64_t)rpos * W.ld + b] = (TW)x;
-        }
+      for (int t = 0; t < 4; ++t) {
+        const float x = rowbuf[t * kGatherChunk + jj];
+        reinterpret_cast<float*>(C.p[t])[i * C.ld + b] = x;
+        if (hasW && rpos >= 0) reinterpret_cast<TW*>(W.p[t])[(int64_t)rpos * W.ld + b] = (TW)x;
       }
     }
   }
@@ -181,7 +191,7 @@ qmcur_status gather_one(const QView& A, const int32_t* I, const int32_t* J, cons
 bool stream_ok(const QView& A, int64_t c, int64_t r, const qmcur_qmat* C, const qmcur_qmat* R,
                const qmcur_qmat* W) {
   if (A.dtype != QMCUR_F32 || A.cols % 4 != 0 || A.ld % 4 != 0) return false;
-  if (c > kGatherMaxIdx || r > kGatherMaxIdx) return false;
+  if (c > kGatherMaxIdx || r > kGatherMaxIdx || C == nullptr) return false;   // C drives the pass
   if (C && C->dtype != QMCUR_F32) return false;
   if (R && (R->dtype != QMCUR_F32 || R->ld % 4 != 0)) return false;
   for (int t = 0; t < 4; ++t) {
@@ -215,10 +225,10 @@ qmcur_status gather_stream(const QView& A, const int32_t* J, const int32_t* I, i
   const unsigned grid = (unsigned)(A.rows < want ? A.rows : want);
   if (W != nullptr && W->dtype == QMCUR_F64)
     k_gather_stream<double><<<grid, kGatherThreads, smem, st>>>(
-        A, I, J, (int)r, (int)c, vC, vR, vW, C != nullptr, R != nullptr, W != nullptr);
+        A, I, J, (int)r, (int)c, vC, vR, vW, R != nullptr, W != nullptr);
   else
     k_gather_stream<float><<<grid, kGatherThreads, smem, st>>>(
-        A, I, J, (int)r, (int)c, vC, vR, vW, C != nullptr, R != nullptr, W != nullptr);
+        A, I, J, (int)r, (int)c, vC, vR, vW, R != nullptr, W != nullptr);
   return cuda_ok(cudaGetLastError());
 }
 
