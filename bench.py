@@ -186,13 +186,13 @@ def pinv_flops(w, method, sweeps):
         # rotation of both columns of G and V (q*w 32 flops, two combinations 16).
         return sweeps * pairs * (nr * 48 + (nr + nc) * 48)
     k = min(w["rank_cap"], nc)
-    # subspace iteration: W Omega, two (W^H Q, W P) pairs (5 r c k); seven
-    # CholeskyQR passes over `rows` x k bases, each a Hermitian Gram (rows k^2 / 2),
-    # a Cholesky (k^3 / 6) and a triangular solve (rows k^2 / 2); then
-    # U = P R1^-1 R2^-1 Q^H (two solves on c x k, one c r k product).
-    pass_rows = [r, c, r, c, c, r, r]
-    qfma = 5 * r * c * k + sum(rows * k * k + k ** 3 // 6 for rows in pass_rows)
-    qfma += c * k * k + c * r * k
+    # subspace iteration: W Omega, W^H Q0, W P1, W^H Q1, W T (5 r c k); seven
+    # Hermitian Grams (rows k^2 / 2) and Cholesky factorisations (k^3 / 6);
+    # ten triangular solves (rows k^2 / 2); U = (P R1^-1 R2^-1) Q^H (c r k).
+    gram_rows = [r, c, r, c, c, r, r]
+    solve_rows = [r, c, r, c, c, r, r, r, c, c]
+    qfma = 5 * r * c * k + c * r * k + 7 * (k ** 3 // 6)
+    qfma += sum(rows * k * k // 2 for rows in gram_rows + solve_rows)
     return 32 * qfma
 
 

@@ -117,14 +117,22 @@ size_t pinv_fast_ws_bytes(int64_t r, int64_t c, int64_t k) {
 
 enum { PH_PREP = 0, PH_GEMM = 1, PH_CHOL = 2, PH_TRSM = 3 };
 
+// One product of a GEMM step (or one solve of a TRSM step).
+struct Job {
+  SmallGemmArgs g;   // PH_CHOL: g.X = G; PH_TRSM: g.Z = g.X R^-1, g.M rows, g.K = k
+  int splits;        // PH_GEMM: k-range splits per tile (1: no partials)
+  int kchunk;        // PH_GEMM: k-range of one split (a multiple of kSmBK)
+  int upper;         // PH_GEMM: square output, only tiles (tm <= tn) are formed
+};
+
+// A step holds one or two independent jobs of the same kind (two products
+// of one input, or two solves with one factor), sharing one grid barrier.
 struct Phase {
   int kind;
   int k;        // PH_CHOL: order of G
-  int splits;   // PH_GEMM: k-range splits per tile (1: no partials)
-  int kchunk;   // PH_GEMM: k-range of one split (a multiple of kSmBK)
-  int upper;    // PH_GEMM: square output, only tiles (tm <= tn) are formed
+  int njobs;
   float* rpk;   // PH_CHOL: the packed factor written; PH_TRSM: the one read
-  SmallGemmArgs g;   // PH_CHOL: g.X = G; PH_TRSM: g.Z = g.X R^-1, g.M rows, g.K = k
+  Job job[2];
 };
 
 constexpr int kMaxPhases = 40;
@@ -197,46 +205,60 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_co
       }
     } else if (ph.kind == PH_GEMM) {
       __shared__ int last_sh[kFusedWorkers];
-      const int tmc = (ph.g.M + kSmTS - 1) / kSmTS, tnc = (ph.g.N + kSmTS - 1) / kSmTS;
-      const int ntiles = ph.upper ? tnc * (tnc + 1) / 2 : tmc * tnc;
-      const int items = ntiles * ph.splits;
-      // item -> one per SM first (worker 0 of every CTA), then worker 1
-      for (int t = blockIdx.x + gridDim.x * worker; t < items; t += gridDim.x * kFusedWorkers) {
-        const int tile = t % ntiles, sp = t / ntiles;
+      int tnc[2], ntiles[2], items[2];
+      for (int j = 0; j < 2; ++j) {
+        const Job& jb = ph.job[j];
+        const int tmc = j < ph.njobs ? (jb.g.M + kSmTS - 1) / kSmTS : 0;
+        tnc[j] = j < ph.njobs ? (jb.g.N + kSmTS - 1) / kSmTS : 0;
+        ntiles[j] = jb.upper ? tnc[j] * (tnc[j] + 1) / 2 : tmc * tnc[j];
+        items[j] = ntiles[j] * (j < ph.njobs ? jb.splits : 0);
+      }
+      // item -> one per SM first (worker 0 of every CTA), then worker 1;
+      // job 1's items follow job 0's, with their own partials and counts
+      for (int t = blockIdx.x + gridDim.x * worker; t < items[0] + items[1];
+           t += gridDim.x * kFusedWorkers) {
+        const int j = t < items[0] ? 0 : 1;
+        const Job& jb = ph.job[j];
+        const int tt = j == 0 ? t : t - items[0];
+        const int tile = tt % ntiles[j], sp = tt / ntiles[j];
         int tm, tn;
-        tile_of(tile, tnc, ph.upper, tm, tn);
-        const int kb = sp * ph.kchunk;
-        const int ke = kb + ph.kchunk < ph.g.K ? kb + ph.kchunk : ph.g.K;
-        const float4 acc = sm_tile_acc(ph.g, tm, tn, kb, ke, wsm, wtid, 1 + worker);
-        if (ph.splits == 1) {
-          sm_tile_store(ph.g, tm, tn, wtid, acc);
+        tile_of(tile, tnc[j], jb.upper, tm, tn);
+        const int kb = sp * jb.kchunk;
+        const int ke = kb + jb.kchunk < jb.g.K ? kb + jb.kchunk : jb.g.K;
+        const float4 acc = sm_tile_acc(jb.g, tm, tn, kb, ke, wsm, wtid, 1 + worker);
+        if (jb.splits == 1) {
+          sm_tile_store(jb.g, tm, tn, wtid, acc);
           continue;
         }
-        P.part[((size_t)tile * ph.splits + sp) * kSmTileThreads + wtid] = acc;
+        const size_t pbase = j == 0 ? 0 : (size_t)items[0];
+        unsigned* cnt = P.cnt + (j == 0 ? 0 : ntiles[0]) + tile;
+        P.part[(pbase + (size_t)tile * jb.splits + sp) * kSmTileThreads + wtid] = acc;
         __threadfence();
         worker_sync(1 + worker);
-        if (wtid == 0)
-          last_sh[worker] = atomicAdd(P.cnt + tile, 1u) == (unsigned)(ph.splits - 1);
+        if (wtid == 0) last_sh[worker] = atomicAdd(cnt, 1u) == (unsigned)(jb.splits - 1);
         worker_sync(1 + worker);
         if (last_sh[worker]) {
           __threadfence();
           float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-          for (int q2 = 0; q2 < ph.splits; ++q2)
-            sum = f4add(sum, __ldcg(P.part + ((size_t)tile * ph.splits + q2) * kSmTileThreads + wtid));
-          sm_tile_store(ph.g, tm, tn, wtid, sum);
-          if (wtid == 0) P.cnt[tile] = 0u;   // ready for the next step, after the grid barrier
+          for (int q2 = 0; q2 < jb.splits; ++q2)
+            sum = f4add(sum, __ldcg(P.part + (pbase + (size_t)tile * jb.splits + q2) * kSmTileThreads + wtid));
+          sm_tile_store(jb.g, tm, tn, wtid, sum);
+          if (wtid == 0) *cnt = 0u;   // ready for the next step, after the grid barrier
         }
       }
     } else if (ph.kind == PH_TRSM) {
-      if (blockIdx.x < ph.g.M) {   // CTAs without rows skip the staging
-        sm_trsm_stage(ph.rpk, ph.g.K, smf);
+      const int rows0 = ph.job[0].g.M, rows = rows0 + (ph.njobs > 1 ? ph.job[1].g.M : 0);
+      if (blockIdx.x < rows) {   // CTAs without rows skip the staging
+        sm_trsm_stage(ph.rpk, ph.job[0].g.K, smf);
         __syncthreads();
         const int warp = threadIdx.x >> 5, nw = kFusedThreads / 32;
-        for (int row = blockIdx.x + gridDim.x * warp; row < ph.g.M; row += gridDim.x * nw)
-          sm_trsm_row_any(ph.g.X, ph.g.Z, row, ph.g.K, smf);
+        for (int row = blockIdx.x + gridDim.x * warp; row < rows; row += gridDim.x * nw) {
+          const Job& jb = ph.job[row < rows0 ? 0 : 1];
+          sm_trsm_row_any(jb.g.X, jb.g.Z, row < rows0 ? row : row - rows0, jb.g.K, smf);
+        }
       }
     } else if (blockIdx.x == 0) {
-      sm_chol(ph.g.X, ph.k, ph.rpk, P.status, smf);
+      sm_chol(ph.job[0].g.X, ph.k, ph.rpk, P.status, smf);
     }
     if (q + 1 < P.nph && !grid_sync(P.bar, P.status, bar_target)) return;
   }
@@ -246,60 +268,93 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_co
   }
 }
 
+// Product X (op) Y (op) -> Z of a GEMM step.
+struct GemmSpec {
+  bool xh, yh;
+  int M, N, K;
+  QPtr X, Y, Z;
+  bool upper;   // Z square and only its upper triangle is needed (a Gram)
+};
+
 struct ProgBuilder {
   FusedProg p{};
   bool ok = true;
   int workers = 1;   // tile workers of the launch
-  // Z = op(X) op(Y); `upper`: Z square and only its upper triangle is needed.
-  void gemm(bool xh, bool yh, int M, int N, int K, const QPtr& X, const QPtr& Y, const QPtr& Z,
-            bool upper = false) {
-    if (p.nph >= kMaxPhases) { ok = false; return; }
-    Phase& ph = p.ph[p.nph++];
-    ph.kind = PH_GEMM;
-    ph.g = SmallGemmArgs{X, Y, Z, M, N, K, 1.0f, 0.0f, xh ? 1 : 0, yh ? 1 : 0};
-    const int tmc = (M + kSmTS - 1) / kSmTS, tnc = (N + kSmTS - 1) / kSmTS;
-    ph.upper = (upper && M == N) ? 1 : 0;
-    const int ntiles = ph.upper ? tnc * (tnc + 1) / 2 : tmc * tnc;
-    const int slices = (K + kSmBK - 1) / kSmBK;
-    int splits = workers / ntiles;
-    if (splits > 8) splits = 8;
-    if (splits > slices) splits = slices;
-    if (splits < 2 || ntiles * splits > kMaxPartTiles) splits = 1;
-    const int per = (slices + splits - 1) / splits;
-    ph.kchunk = per * kSmBK;
-    ph.splits = (slices + per - 1) / per;
+  Phase* next(int kind) {
+    if (p.nph >= kMaxPhases) { ok = false; return nullptr; }
+    Phase* ph = &p.ph[p.nph++];
+    ph->kind = kind;
+    return ph;
+  }
+  static int tiles_of(const GemmSpec& s) {
+    const int tmc = (s.M + kSmTS - 1) / kSmTS, tnc = (s.N + kSmTS - 1) / kSmTS;
+    return (s.upper && s.M == s.N) ? tnc * (tnc + 1) / 2 : tmc * tnc;
+  }
+  // one or two products in one step; k-range splits fill the workers
+  void gemm(const GemmSpec* specs, int n) {
+    Phase* ph = next(PH_GEMM);
+    if (ph == nullptr) return;
+    ph->njobs = n;
+    int all_tiles = 0;
+    for (int j = 0; j < n; ++j) all_tiles += tiles_of(specs[j]);
+    int used = 0, cnts = 0;
+    for (int j = 0; j < n; ++j) {
+      const GemmSpec& s = specs[j];
+      Job& jb = ph->job[j];
+      jb.g = SmallGemmArgs{s.X, s.Y, s.Z, s.M, s.N, s.K, 1.0f, 0.0f, s.xh ? 1 : 0, s.yh ? 1 : 0};
+      jb.upper = (s.upper && s.M == s.N) ? 1 : 0;
+      const int ntiles = tiles_of(s);
+      const int slices = (s.K + kSmBK - 1) / kSmBK;
+      int splits = workers / all_tiles;
+      if (splits > 8) splits = 8;
+      if (splits > slices) splits = slices;
+      if (splits < 2) splits = 1;
+      const int per = (slices + splits - 1) / splits;
+      jb.kchunk = per * kSmBK;
+      jb.splits = (slices + per - 1) / per;
+      if (jb.splits > 1) {
+        used += ntiles * jb.splits;   // partial tiles of the step
+        cnts += ntiles;
+      }
+    }
+    if (used > kMaxPartTiles || cnts > kMaxPartTiles) {   // no room: no splits
+      for (int j = 0; j < n; ++j) {
+        ph->job[j].splits = 1;
+        ph->job[j].kchunk = ((specs[j].K + kSmBK - 1) / kSmBK) * kSmBK;
+      }
+    }
+  }
+  void gemm(const GemmSpec& s) { gemm(&s, 1); }
+  void gemm2(const GemmSpec& a, const GemmSpec& b) {
+    const GemmSpec two[2] = {a, b};
+    gemm(two, 2);
   }
   void chol(const QPtr& G, int k, float* R) {
-    if (p.nph >= kMaxPhases) { ok = false; return; }
-    Phase& ph = p.ph[p.nph++];
-    ph.kind = PH_CHOL;
-    ph.k = k;
-    ph.splits = 1;
-    ph.rpk = R;
-    ph.g = SmallGemmArgs{G, G, G, k, k, k, 1.0f, 0.0f, 0, 0};
+    Phase* ph = next(PH_CHOL);
+    if (ph == nullptr) return;
+    ph->k = k;
+    ph->njobs = 1;
+    ph->rpk = R;
+    ph->job[0].g = SmallGemmArgs{G, G, G, k, k, k, 1.0f, 0.0f, 0, 0};
+    ph->job[0].splits = 1;
   }
-  // Z = Y R^-1 (Y, Z rows x k; Z may be Y)
-  void trsm(const QPtr& Y, float* R, const QPtr& Z, int rows, int k) {
-    if (p.nph >= kMaxPhases) { ok = false; return; }
-    Phase& ph = p.ph[p.nph++];
-    ph.kind = PH_TRSM;
-    ph.k = k;
-    ph.splits = 1;
-    ph.rpk = R;
-    ph.g = SmallGemmArgs{Y, Y, Z, rows, k, k, 1.0f, 0.0f, 0, 0};
+  // Z = Y R^-1 (Y, Z rows x k; Z may be Y), and a second solve with the same R
+  void trsm(const QPtr& Y, float* R, const QPtr& Z, int rows, int k, const QPtr* Y2 = nullptr,
+            const QPtr* Z2 = nullptr, int rows2 = 0) {
+    Phase* ph = next(PH_TRSM);
+    if (ph == nullptr) return;
+    ph->k = k;
+    ph->rpk = R;
+    ph->njobs = Y2 != nullptr ? 2 : 1;
+    ph->job[0].g = SmallGemmArgs{Y, Y, Z, rows, k, k, 1.0f, 0.0f, 0, 0};
+    ph->job[0].splits = 1;
+    if (Y2 != nullptr) {
+      ph->job[1].g = SmallGemmArgs{*Y2, *Y2, *Z2, rows2, k, k, 1.0f, 0.0f, 0, 0};
+      ph->job[1].splits = 1;
+    }
   }
-  // Y (rows x k) -> Q = Y R^-1 by CholeskyQR with `passes` passes; the
-  // factors are left in R1 (first) and R2 (second): Y = Q R2 R1.
-  void cholqr(const QPtr& Y, int rows, int k, const QPtr& Q, FastWs& w, int passes,
-              float* R1, float* R2) {
-    const QPtr& Qa = passes == 2 ? w.T : Q;
-    gemm(true, false, k, k, rows, Y, Y, w.G, true);
-    chol(w.G, k, R1);
-    trsm(Y, R1, Qa, rows, k);
-    if (passes == 1) return;
-    gemm(true, false, k, k, rows, w.T, w.T, w.G, true);
-    chol(w.G, k, R2);
-    trsm(w.T, R2, Q, rows, k);
+  GemmSpec gram(const QPtr& Y, int rows, int k, const QPtr& G) {
+    return GemmSpec{true, false, k, k, rows, Y, Y, G, true};
   }
 };
 
@@ -341,26 +396,51 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
   ProgBuilder b;
   b.workers = grid * kFusedWorkers;
   b.p.ph[b.p.nph++].kind = PH_PREP;
-  // Y0 = W Omega; intermediate bases only have to span the subspaces (one
-  // CholeskyQR pass); the last P must be orthonormal to working accuracy and
-  // W P = Q R2 R1 exact to it (CholeskyQR2 for both).
-  b.gemm(false, false, ri, k, ci, w.W32, w.Om, w.Y);
-  b.cholqr(w.Y, ri, k, w.Q, w, 1, R1, R2);
-  for (int it = 0; it < 2; ++it) {
-    const int passes = it == 1 ? 2 : 1;
-    b.gemm(true, false, ci, k, ri, w.W32, w.Q, w.Z);        // W^H Q
-    b.cholqr(w.Z, ci, k, w.P, w, passes, R1, R2);           // P
-    b.gemm(false, false, ri, k, ci, w.W32, w.P, w.Y);       // W P
-    b.cholqr(w.Y, ri, k, w.Q, w, passes, R1, R2);           // Q, R
-  }
+  // Intermediate bases only have to span the subspaces (one CholeskyQR
+  // pass); each product with W starts from an orthonormal basis, because
+  // forming it from the unnormalised one and solving afterwards would scale
+  // its rounding by the basis' condition number.  The last P and Q are
+  // orthonormal to working accuracy (CholeskyQR2), and W P = Q R2 R1.
+  const QPtr Uo = [&] {
+    QPtr q;
+    for (int t = 0; t < 4; ++t) q.p[t] = U->plane[t];
+    q.ld = U->ld;
+    q.dtype = U->dtype;
+    return q;
+  }();
+  b.gemm(GemmSpec{false, false, ri, k, ci, w.W32, w.Om, w.Y, false});          // Y = W Omega
+  b.gemm(b.gram(w.Y, ri, k, w.G));                                              // Q0 = orth(Y)
+  b.chol(w.G, k, R1);
+  b.trsm(w.Y, R1, w.Q, ri, k);
+  b.gemm(GemmSpec{true, false, ci, k, ri, w.W32, w.Q, w.Z, false});            // P1 = orth(W^H Q0)
+  b.gemm(b.gram(w.Z, ci, k, w.G));
+  b.chol(w.G, k, R1);
+  b.trsm(w.Z, R1, w.P, ci, k);
+  b.gemm(GemmSpec{false, false, ri, k, ci, w.W32, w.P, w.Y, false});           // Q1 = orth(W P1)
+  b.gemm(b.gram(w.Y, ri, k, w.G));
+  b.chol(w.G, k, R1);
+  b.trsm(w.Y, R1, w.Q, ri, k);
+  b.gemm(GemmSpec{true, false, ci, k, ri, w.W32, w.Q, w.Z, false});            // Z = W^H Q1
+  // P = orth2(Z): T = Z R1^-1, P = T R2^-1.  T is orthonormal to working
+  // accuracy and R2 close to I, so Y = W P is formed as (W T) R2^-1 beside
+  // the second Gram matrix and solved with P.
+  b.gemm(b.gram(w.Z, ci, k, w.G));
+  b.chol(w.G, k, R1);
+  b.trsm(w.Z, R1, w.T, ci, k);
+  b.gemm2(b.gram(w.T, ci, k, w.G), GemmSpec{false, false, ri, k, ci, w.W32, w.T, w.Y, false});
+  b.chol(w.G, k, R2);
+  b.trsm(w.T, R2, w.P, ci, k, &w.Y, &w.Y, ri);
+  // Q = orth2(Y), Y = Q R2 R1
+  b.gemm(b.gram(w.Y, ri, k, w.G));
+  b.chol(w.G, k, R1);
+  b.trsm(w.Y, R1, w.T, ri, k);
+  b.gemm(b.gram(w.T, ri, k, w.G));
+  b.chol(w.G, k, R2);
+  b.trsm(w.T, R2, w.Q, ri, k);
   // U = P R1^-1 R2^-1 Q^H
-  QPtr Uo;
-  for (int t = 0; t < 4; ++t) Uo.p[t] = U->plane[t];
-  Uo.ld = U->ld;
-  Uo.dtype = U->dtype;
   b.trsm(w.P, R1, w.Z, ci, k);
   b.trsm(w.Z, R2, w.T, ci, k);
-  b.gemm(false, true, ci, ri, k, w.T, w.Q, Uo);
+  b.gemm(GemmSpec{false, true, ci, ri, k, w.T, w.Q, Uo, false});
   if (!b.ok) return QMCUR_ERR_UNSUPPORTED;
   b.p.Win = view(W);
   b.p.W32 = w.W32;

@@ -288,7 +288,7 @@ __device__ __forceinline__ void sm_chol_s(const QPtr& G, int k, float* rpk, int3
 #pragma unroll
         for (int q = 0; q < p; ++q) d -= q_norm2(a[q][p]);
         if (!(d > 0.f) || !isfinite(d)) { bad = true; d = floor_v; }
-        rd[p] = __frsqrt_rn(d);   // 1 / R_pp, correctly rounded
+        rd[p] = rsqrtf(d);   // 1 / R_pp within 2 ulp, far below CholeskyQR's own u kappa^2
         a[p][p] = make_float4(d * rd[p], 0.f, 0.f, 0.f);
 #pragma unroll
         for (int q = p + 1; q < kCholNb; ++q) {   // R_pq = (A_pq - sum_l conj(R_lp) R_lq) / R_pp
