@@ -73,7 +73,6 @@ __device__ __forceinline__ void randn_entry(const QPtr& out, int64_t e, int cols
 // Workspace of the subspace method for an r x c intersection with cap k.
 struct FastWs {
   QPtr W32, Om, Y, Q, Z, P, G, T;
-  float *R1, *R2;   // packed factors (rpk_floats(k) floats each)
   int32_t* info;
 };
 
@@ -100,8 +99,6 @@ static FastWs carve_fast(Carve& cv, int64_t r, int64_t c, int64_t k) {
   w.Z = carve_q(cv, mx, k);
   w.P = carve_q(cv, mx, k);
   w.G = carve_q(cv, k, k);
-  w.R1 = cv.take<float>((size_t)rpk_floats((int)k));
-  w.R2 = cv.take<float>((size_t)rpk_floats((int)k));
   w.T = carve_q(cv, mx, k);
   w.info = cv.take<int32_t>(4);
   return w;
@@ -115,11 +112,11 @@ size_t pinv_fast_ws_bytes(int64_t r, int64_t c, int64_t k) {
   return cv.off;
 }
 
-enum { PH_PREP = 0, PH_GEMM = 1, PH_CHOL = 2, PH_TRSM = 3 };
+enum { PH_PREP = 0, PH_GEMM = 1, PH_SOLVE = 2 };
 
-// One product of a GEMM step (or one solve of a TRSM step).
+// One product of a GEMM step (or one solve of a PH_SOLVE step).
 struct Job {
-  SmallGemmArgs g;   // PH_CHOL: g.X = G; PH_TRSM: g.Z = g.X R^-1, g.M rows, g.K = k
+  SmallGemmArgs g;   // PH_SOLVE: g.Z = g.X R^-1, g.M rows, g.K = k
   int splits;        // PH_GEMM: k-range splits per tile (1: no partials)
   int kchunk;        // PH_GEMM: k-range of one split (a multiple of kSmBK)
   int upper;         // PH_GEMM: square output, only tiles (tm <= tn) are formed
@@ -127,15 +124,18 @@ struct Job {
 
 // A step holds one or two independent jobs of the same kind (two products
 // of one input, or two solves with one factor), sharing one grid barrier.
+// A PH_SOLVE step factors G = R^H R and then solves with R: every CTA that
+// owns rows factors G itself, into its own shared memory, so the factor
+// needs neither a grid barrier nor a round trip through global memory.
 struct Phase {
   int kind;
-  int k;        // PH_CHOL: order of G
+  int k;        // PH_SOLVE: order of G
   int njobs;
-  float* rpk;   // PH_CHOL: the packed factor written; PH_TRSM: the one read
+  QPtr G;       // PH_SOLVE: the Gram matrix (upper triangle read)
   Job job[2];
 };
 
-constexpr int kMaxPhases = 40;
+constexpr int kMaxPhases = 32;
 
 struct FusedProg {
   int nph;
@@ -150,6 +150,8 @@ struct FusedProg {
   int32_t* status;
   int32_t* rank_out;
 };
+
+static_assert(sizeof(FusedProg) <= 32000, "kernel parameter space");
 
 // Tile (tm, tn) of work tile t: row-major over the tile grid, or for `upper`
 // column-major over the upper triangle (t = tn (tn + 1) / 2 + tm).
@@ -175,11 +177,13 @@ constexpr int kFusedThreads = kCholThreads;
 constexpr int kFusedWorkers = kFusedThreads / kSmTileThreads;
 static_assert(kFusedWorkers * kSmTileThreads == kFusedThreads, "whole tile workers");
 
-// Dynamic shared memory of the fused kernel for cap k: the largest of the
-// tile workers' slices, the Cholesky buffers and the staged R.
+// Dynamic shared memory of the fused kernel for cap k: the larger of the
+// tile workers' slices and a solve step's packed R followed by the Cholesky
+// buffers.
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t solve_chol_off(int k) { return (sm_trsm_bytes(k) + 15) / 16 * 16; }
 constexpr size_t fused_smem(int k) {
-  return cmax(cmax((size_t)kFusedWorkers * kSmGemmQuats * 16, sm_chol_bytes()), sm_trsm_bytes(k));
+  return cmax((size_t)kFusedWorkers * kSmGemmQuats * 16, solve_chol_off(k) + sm_chol_bytes());
 }
 
 __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_constant__ FusedProg P) {
@@ -246,19 +250,18 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_co
           if (wtid == 0) *cnt = 0u;   // ready for the next step, after the grid barrier
         }
       }
-    } else if (ph.kind == PH_TRSM) {
+    } else {   // PH_SOLVE
       const int rows0 = ph.job[0].g.M, rows = rows0 + (ph.njobs > 1 ? ph.job[1].g.M : 0);
-      if (blockIdx.x < rows) {   // CTAs without rows skip the staging
-        sm_trsm_stage(ph.rpk, ph.job[0].g.K, smf);
-        __syncthreads();
+      if (blockIdx.x < rows) {   // CTAs without rows skip the factorisation
+        // R packed at the start of shared memory, as the row solves read it;
+        // sm_chol ends with a CTA barrier after its last write
+        sm_chol(ph.G, ph.k, reinterpret_cast<float*>(smf), P.status, smf + solve_chol_off(ph.k));
         const int warp = threadIdx.x >> 5, nw = kFusedThreads / 32;
         for (int row = blockIdx.x + gridDim.x * warp; row < rows; row += gridDim.x * nw) {
           const Job& jb = ph.job[row < rows0 ? 0 : 1];
           sm_trsm_row_any(jb.g.X, jb.g.Z, row < rows0 ? row : row - rows0, jb.g.K, smf);
         }
       }
-    } else if (blockIdx.x == 0) {
-      sm_chol(ph.job[0].g.X, ph.k, ph.rpk, P.status, smf);
     }
     if (q + 1 < P.nph && !grid_sync(P.bar, P.status, bar_target)) return;
   }
@@ -329,22 +332,14 @@ struct ProgBuilder {
     const GemmSpec two[2] = {a, b};
     gemm(two, 2);
   }
-  void chol(const QPtr& G, int k, float* R) {
-    Phase* ph = next(PH_CHOL);
+  // G = R^H R, then Z = Y R^-1 (Y, Z rows x k; Z may be Y), and a second
+  // solve with the same R
+  void solve(const QPtr& G, const QPtr& Y, const QPtr& Z, int rows, int k, const QPtr* Y2 = nullptr,
+             const QPtr* Z2 = nullptr, int rows2 = 0) {
+    Phase* ph = next(PH_SOLVE);
     if (ph == nullptr) return;
     ph->k = k;
-    ph->njobs = 1;
-    ph->rpk = R;
-    ph->job[0].g = SmallGemmArgs{G, G, G, k, k, k, 1.0f, 0.0f, 0, 0};
-    ph->job[0].splits = 1;
-  }
-  // Z = Y R^-1 (Y, Z rows x k; Z may be Y), and a second solve with the same R
-  void trsm(const QPtr& Y, float* R, const QPtr& Z, int rows, int k, const QPtr* Y2 = nullptr,
-            const QPtr* Z2 = nullptr, int rows2 = 0) {
-    Phase* ph = next(PH_TRSM);
-    if (ph == nullptr) return;
-    ph->k = k;
-    ph->rpk = R;
+    ph->G = G;
     ph->njobs = Y2 != nullptr ? 2 : 1;
     ph->job[0].g = SmallGemmArgs{Y, Y, Z, rows, k, k, 1.0f, 0.0f, 0, 0};
     ph->job[0].splits = 1;
@@ -388,8 +383,6 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
       cudaSuccess)
     return QMCUR_ERR_CUDA;
   if (per_sm < 1) return QMCUR_ERR_CUDA;
-  float* const R1 = w.R1;
-  float* const R2 = w.R2;
   const int ri = (int)r, ci = (int)c;
   // one CTA per SM at most: a GEMM step has at most ~2 x SMs useful items
   const int grid = sms;
@@ -410,37 +403,28 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
   }();
   b.gemm(GemmSpec{false, false, ri, k, ci, w.W32, w.Om, w.Y, false});          // Y = W Omega
   b.gemm(b.gram(w.Y, ri, k, w.G));                                              // Q0 = orth(Y)
-  b.chol(w.G, k, R1);
-  b.trsm(w.Y, R1, w.Q, ri, k);
+  b.solve(w.G, w.Y, w.Q, ri, k);
   b.gemm(GemmSpec{true, false, ci, k, ri, w.W32, w.Q, w.Z, false});            // P1 = orth(W^H Q0)
   b.gemm(b.gram(w.Z, ci, k, w.G));
-  b.chol(w.G, k, R1);
-  b.trsm(w.Z, R1, w.P, ci, k);
+  b.solve(w.G, w.Z, w.P, ci, k);
   b.gemm(GemmSpec{false, false, ri, k, ci, w.W32, w.P, w.Y, false});           // Q1 = orth(W P1)
   b.gemm(b.gram(w.Y, ri, k, w.G));
-  b.chol(w.G, k, R1);
-  b.trsm(w.Y, R1, w.Q, ri, k);
+  b.solve(w.G, w.Y, w.Q, ri, k);
   b.gemm(GemmSpec{true, false, ci, k, ri, w.W32, w.Q, w.Z, false});            // Z = W^H Q1
   // P = orth2(Z): T = Z R1^-1, P = T R2^-1.  T is orthonormal to working
   // accuracy and R2 close to I, so Y = W P is formed as (W T) R2^-1 beside
   // the second Gram matrix and solved with P.
   b.gemm(b.gram(w.Z, ci, k, w.G));
-  b.chol(w.G, k, R1);
-  b.trsm(w.Z, R1, w.T, ci, k);
+  b.solve(w.G, w.Z, w.T, ci, k);
   b.gemm2(b.gram(w.T, ci, k, w.G), GemmSpec{false, false, ri, k, ci, w.W32, w.T, w.Y, false});
-  b.chol(w.G, k, R2);
-  b.trsm(w.T, R2, w.P, ci, k, &w.Y, &w.Y, ri);
-  // Q = orth2(Y), Y = Q R2 R1
+  b.solve(w.G, w.T, w.P, ci, k, &w.Y, &w.Y, ri);
+  // Q = orth2(Y), Y = Q R2 R1, and U = P R1^-1 R2^-1 Q^H: the solves of P
+  // ride along with those of the basis, one factor at a time
   b.gemm(b.gram(w.Y, ri, k, w.G));
-  b.chol(w.G, k, R1);
-  b.trsm(w.Y, R1, w.T, ri, k);
+  b.solve(w.G, w.Y, w.T, ri, k, &w.P, &w.Z, ci);                               // R1
   b.gemm(b.gram(w.T, ri, k, w.G));
-  b.chol(w.G, k, R2);
-  b.trsm(w.T, R2, w.Q, ri, k);
-  // U = P R1^-1 R2^-1 Q^H
-  b.trsm(w.P, R1, w.Z, ci, k);
-  b.trsm(w.Z, R2, w.T, ci, k);
-  b.gemm(GemmSpec{false, true, ci, ri, k, w.T, w.Q, Uo, false});
+  b.solve(w.G, w.T, w.Q, ri, k, &w.Z, &w.Y, ci);                               // R2
+  b.gemm(GemmSpec{false, true, ci, ri, k, w.Y, w.Q, Uo, false});
   if (!b.ok) return QMCUR_ERR_UNSUPPORTED;
   b.p.Win = view(W);
   b.p.W32 = w.W32;

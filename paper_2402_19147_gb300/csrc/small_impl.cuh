@@ -366,31 +366,9 @@ __device__ __forceinline__ void sm_chol(const QPtr& G, int k, float* rpk, int32_
 // taken from its owner with shuffles and every later column takes its update
 // at once.  The slot updates are branch-free (clamped indices, selected
 // results): short branchy bodies leave a lone warp waiting on instruction
-// fetch.  R (the packed factor above) is staged in shared memory.
+// fetch.  R (the packed factor above) sits in shared memory.
 
 __host__ __device__ constexpr size_t sm_trsm_bytes(int k) { return (size_t)rpk_floats(k) * 4; }
-
-// All threads of the CTA: copy the packed factor into shared memory.
-__device__ __forceinline__ void sm_trsm_stage(const float* rpk, int k, unsigned char* smraw) {
-  const int n4 = (k * (k + 1) / 2), nf = rpk_floats(k);
-  const float4* src = reinterpret_cast<const float4*>(rpk);
-  float4* dst = reinterpret_cast<float4*>(smraw);
-  for (int i0 = threadIdx.x; i0 < n4; i0 += 4 * blockDim.x) {
-    float4 q[4];
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const int i = i0 + h * blockDim.x;
-      q[h] = i < n4 ? __ldcg(src + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const int i = i0 + h * blockDim.x;
-      if (i < n4) dst[i] = q[h];
-    }
-  }
-  float* fs = reinterpret_cast<float*>(smraw);
-  for (int i = 4 * n4 + threadIdx.x; i < nf; i += blockDim.x) fs[i] = __ldcg(rpk + i);
-}
 
 // One warp: row `row` of Z = Y R^-1 (Z may alias Y), k <= 32 U.
 template <int U>
