@@ -253,11 +253,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_co
     } else {   // PH_SOLVE
       const int rows0 = ph.job[0].g.M, rows = rows0 + (ph.njobs > 1 ? ph.job[1].g.M : 0);
       if (blockIdx.x < rows) {   // CTAs without rows skip the factorisation
+        SolveJobs sj;
+        sj.Y0 = ph.job[0].g.X;
+        sj.Z0 = ph.job[0].g.Z;
+        sj.Y1 = ph.job[1].g.X;
+        sj.Z1 = ph.job[1].g.Z;
+        sj.rows0 = rows0;
+        sj.rows = rows;
         // R packed at the start of shared memory, as the row solves read it;
-        // sm_chol ends with a CTA barrier after its last write
-        sm_chol(ph.G, ph.k, reinterpret_cast<float*>(smf), P.status, smf + solve_chol_off(ph.k));
+        // the first kSolveRowWarps rows of this CTA are solved along the way
+        const int rode = sm_chol(ph.G, ph.k, reinterpret_cast<float*>(smf), P.status,
+                                 smf + solve_chol_off(ph.k), &sj);
         const int warp = threadIdx.x >> 5, nw = kFusedThreads / 32;
-        for (int row = blockIdx.x + gridDim.x * warp; row < rows; row += gridDim.x * nw) {
+        for (int i = rode + warp;; i += nw) {
+          const int row = solve_row_of(i);
+          if (row >= rows) break;
           const Job& jb = ph.job[row < rows0 ? 0 : 1];
           sm_trsm_row_any(jb.g.X, jb.g.Z, row < rows0 ? row : row - rows0, jb.g.K, smf);
         }

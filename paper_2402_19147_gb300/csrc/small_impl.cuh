@@ -226,14 +226,159 @@ __host__ __device__ constexpr size_t sm_chol_bytes() {
   return (size_t)2 * kCholNb * kSmallCholMax * 16 + 16;
 }
 
+// ---------------------------------------------------------------------------
+// Row solves that ride along with the factorisation.  Z = Y R^-1 needs, for
+// its column l, only rows 0 .. l of R.  Rows b0 .. b0 + nb - 1 are final once
+// the panel of block b0 has passed its barrier, so a warp that holds a row of
+// Y can take the columns of block b while the panel of block b + 1 runs.  The
+// panel only occupies the warps of the first kSolvePanelWarps (its column
+// threads); the other warps of the CTA each carry one row.  The arithmetic per
+// column is that of the plain row solve below: z_l = t_l / R_ll, taken from
+// its owner lane with shuffles, then t_c -= z_l R_lc for every later column.
+// The row warps sit on the SM sub-partitions (warp % 4) that hold no panel
+// warp, so that they do not take issue slots from the panel.
+
+// One or two solves with one factor: rows [0, rows0) belong to the first.
+struct SolveJobs {
+  QPtr Y0, Y1, Z0, Z1;
+  int rows0, rows;
+};
+
+// One of two plane sets, selected field by field (selecting between the two
+// structs would take their addresses and put them on the stack).
+__device__ __forceinline__ QPtr qptr_pick(bool second, const QPtr& a, const QPtr& b) {
+  QPtr q;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) q.p[t] = second ? b.p[t] : a.p[t];
+  q.ld = second ? b.ld : a.ld;
+  q.dtype = second ? b.dtype : a.dtype;
+  return q;
+}
+
+// Row i of the CTA's rows (row-warp i, or past the row warps: the plain row
+// solve takes those once R is complete).
+__device__ __forceinline__ int solve_row_of(int i) { return blockIdx.x + gridDim.x * i; }
+
+// Panel warps of order k (their sub-partitions are 0 .. pw - 1), row warps
+// (the warps of the other sub-partitions), and the row-warp index of a warp.
+__device__ __forceinline__ int solve_panel_warps(int k) { return (k + 31) / 32; }
+__device__ __forceinline__ int solve_row_warps(int k) {
+  return (4 - solve_panel_warps(k)) * (kCholThreads / 128);
+}
+__device__ __forceinline__ int solve_row_index(int warp, int k) {
+  const int pw = solve_panel_warps(k);
+  return (warp & 3) < pw ? -1 : (warp >> 2) * (4 - pw) + ((warp & 3) - pw);
+}
+
+template <int U>   // column slots per lane: k <= 32 U
+struct SolveRow {
+  float4 t[U];
+  int row;   // -1: this warp carries no row
+  int job;
+  int local;
+
+  __device__ __forceinline__ void load(const SolveJobs& sj, int k) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    row = -1;
+#pragma unroll
+    for (int u = 0; u < U; ++u) t[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ri = solve_row_index(warp, k);
+    if (ri < 0) return;
+    const int rg = solve_row_of(ri);
+    if (rg >= sj.rows) return;
+    row = rg;
+    job = rg < sj.rows0 ? 0 : 1;
+    local = job == 0 ? rg : rg - sj.rows0;
+    const QPtr Y = qptr_pick(job != 0, sj.Y0, sj.Y1);
+    const int64_t yo = (int64_t)local * Y.ld;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = lane + 32 * u;
+      if (c < k)
+        t[u] = make_float4(reinterpret_cast<const float*>(Y.p[0])[yo + c],
+                           reinterpret_cast<const float*>(Y.p[1])[yo + c],
+                           reinterpret_cast<const float*>(Y.p[2])[yo + c],
+                           reinterpret_cast<const float*>(Y.p[3])[yo + c]);
+    }
+  }
+
+  // Columns l0 .. l0 + nb - 1 of slot UB (l0 >> 5 == UB) from the packed R.
+  template <int UB>
+  __device__ __forceinline__ void cols_u(int l0, int nb, int k, const float* rpk) {
+    const float4* Rs = reinterpret_cast<const float4*>(rpk);
+    const float* invd = rpk + 4 * (k * (k + 1) / 2);
+    const int lane = threadIdx.x & 31;
+    for (int l = l0; l < l0 + nb; ++l) {
+      const int ll = l & 31;
+      const float s = invd[l];
+      const float4 z = make_float4(__shfl_sync(0xffffffffu, t[UB].x, ll) * s,
+                                   __shfl_sync(0xffffffffu, t[UB].y, ll) * s,
+                                   __shfl_sync(0xffffffffu, t[UB].z, ll) * s,
+                                   __shfl_sync(0xffffffffu, t[UB].w, ll) * s);
+      // R_l,c sits at Rrow + c for c >= l; a clamped c below l reads an
+      // earlier entry of the packed array, whose product is discarded.
+      const float4* Rrow = Rs + (packed_row(l, k) - l);
+#pragma unroll
+      for (int u = UB; u < U; ++u) {
+        if (32 * u < k) {   // warp-uniform: the slot holds columns
+          const int c = lane + 32 * u;
+          const int cc = c < k ? c : k - 1;
+          const float4 nt = q_sub_mul(t[u], z, Rrow[cc > l ? cc : l]);
+          t[u] = (c > l && c < k) ? nt : t[u];
+        }
+      }
+      t[UB] = (lane == ll) ? z : t[UB];
+    }
+  }
+
+  // Columns l0 .. l0 + nb - 1, within one 32-column slot.
+  __device__ __forceinline__ void cols(int l0, int nb, int k, const float* rpk) {
+    static_assert(U >= 1 && U <= 3, "one case per slot");
+    const int ub = l0 >> 5;
+    if (ub == 0) cols_u<0>(l0, nb, k, rpk);
+    else if (U > 1 && ub == 1) cols_u<(U > 1 ? 1 : 0)>(l0, nb, k, rpk);
+    else if (U > 2) cols_u<(U > 2 ? 2 : 0)>(l0, nb, k, rpk);
+  }
+
+  __device__ __forceinline__ void store(const SolveJobs& sj, int k) const {
+    const int lane = threadIdx.x & 31;
+    const QPtr Z = qptr_pick(job != 0, sj.Z0, sj.Z1);
+    const int64_t zo = (int64_t)local * Z.ld;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = lane + 32 * u;
+      if (c < k) {
+        reinterpret_cast<float*>(Z.p[0])[zo + c] = t[u].x;
+        reinterpret_cast<float*>(Z.p[1])[zo + c] = t[u].y;
+        reinterpret_cast<float*>(Z.p[2])[zo + c] = t[u].z;
+        reinterpret_cast<float*>(Z.p[3])[zo + c] = t[u].w;
+      }
+    }
+  }
+};
+
+// Row slots of the ride-along solves for S register slots of the factor (the
+// largest k with S slots is at most 32 RU), or 0: no ride-along, the caller
+// solves every row.  From S = 5 (k > 63) on, the row state on top of the
+// factor's slots would spill registers.
+__host__ __device__ constexpr int chol_ride_slots(int S) {
+  return S >= 5 ? 0 : S * kCholThreads <= 32 * 33 / 2 ? 1 : 2;
+}
+
 template <int S>
-__device__ __forceinline__ void sm_chol_s(const QPtr& G, int k, float* rpk, int32_t* status,
-                                          unsigned char* smraw) {
+__device__ __forceinline__ int sm_chol_s(const QPtr& G, int k, float* rpk, int32_t* status,
+                                          unsigned char* smraw, const SolveJobs* sj) {
+  static_assert(32 % kCholNb == 0, "a block of columns stays in one slot");
+  constexpr int RU = chol_ride_slots(S);
+  constexpr int RUs = RU > 0 ? RU : 1;
   float4* Pn = reinterpret_cast<float4*>(smraw);            // [kCholNb][kSmallCholMax] raw rows
   float4* Rp = Pn + kCholNb * kSmallCholMax;               // [kCholNb][kSmallCholMax] factored rows
   float* floor_sh = reinterpret_cast<float*>(Rp + kCholNb * kSmallCholMax);
   const int tid = threadIdx.x;
   const int np = k * (k + 1) / 2;
+  SolveRow<RUs> rs;
+  rs.row = -1;
+  if (RU > 0 && sj != nullptr) rs.load(*sj, k);   // the loads overlap those of G
   float4 v[S];
   unsigned jc[(S + 1) / 2];   // (j << 8 | c) in 16 bits, two slots per word
 #pragma unroll
@@ -299,6 +444,7 @@ __device__ __forceinline__ void sm_chol_s(const QPtr& G, int k, float* rpk, int3
         }
       }
       if (bad && tid == 0) set_status(status, QMCUR_ERR_ILL_CONDITIONED);
+      // the pivot rows of this block are final after the next barrier
       // column c of R12 (or of R11 when c < b0 + nb): y_p = (x_p - sum_l conj(R_lp) y_l) / R_pp
       float4 y[kCholNb];
 #pragma unroll
@@ -315,6 +461,8 @@ __device__ __forceinline__ void sm_chol_s(const QPtr& G, int k, float* rpk, int3
         if (p < nb && c >= b0 + p) Rq[packed_row(b0 + p, k) + c - (b0 + p)] = y[p];
         if (c == b0 + p) Rinvd[c] = rd[p];
       }
+    } else if (RU > 0 && rs.row >= 0 && b0 > 0) {
+      rs.cols(b0 - kCholNb, kCholNb, k, rpk);   // the previous block's columns
     }
     __syncthreads();
     // ---- update of the trailing entries; the next block's rows are published
@@ -328,12 +476,19 @@ __device__ __forceinline__ void sm_chol_s(const QPtr& G, int k, float* rpk, int3
         const unsigned w = jc[s >> 1] >> (16 * (s & 1));
         const int j = (int)((w >> 8) & 0xffu), c = (int)(w & 0xffu);
         if (e < np && j >= nb0) {   // many entries per thread: skipping idle ones pays here
-          static_assert(kCholNb == 4, "tree sum of four products");
-          const float4 m0 = q_conj_mul(Rp[0 * kSmallCholMax + j], Rp[0 * kSmallCholMax + c]);
-          const float4 m1 = q_conj_mul(Rp[1 * kSmallCholMax + j], Rp[1 * kSmallCholMax + c]);
-          const float4 m2 = q_conj_mul(Rp[2 * kSmallCholMax + j], Rp[2 * kSmallCholMax + c]);
-          const float4 m3 = q_conj_mul(Rp[3 * kSmallCholMax + j], Rp[3 * kSmallCholMax + c]);
-          const float4 t = q_sub(v[s], q_add(q_add(m0, m1), q_add(m2, m3)));
+          float4 t;
+          if constexpr (kCholNb == 4) {   // tree sum of the four products
+            const float4 m0 = q_conj_mul(Rp[0 * kSmallCholMax + j], Rp[0 * kSmallCholMax + c]);
+            const float4 m1 = q_conj_mul(Rp[1 * kSmallCholMax + j], Rp[1 * kSmallCholMax + c]);
+            const float4 m2 = q_conj_mul(Rp[2 * kSmallCholMax + j], Rp[2 * kSmallCholMax + c]);
+            const float4 m3 = q_conj_mul(Rp[3 * kSmallCholMax + j], Rp[3 * kSmallCholMax + c]);
+            t = q_sub(v[s], q_add(q_add(m0, m1), q_add(m2, m3)));
+          } else {
+            t = v[s];
+#pragma unroll
+            for (int p = 0; p < kCholNb; ++p)
+              t = q_sub_conj_mul(t, Rp[p * kSmallCholMax + j], Rp[p * kSmallCholMax + c]);
+          }
           v[s] = t;
           if (j < nb0 + kCholNb) Pn[(j - nb0) * kSmallCholMax + c] = t;
         }
@@ -341,22 +496,34 @@ __device__ __forceinline__ void sm_chol_s(const QPtr& G, int k, float* rpk, int3
     }
     __syncthreads();
   }
+  if (RU > 0 && rs.row >= 0) {
+    const int lb0 = (k - 1) / kCholNb * kCholNb;
+    rs.cols(lb0, k - lb0, k, rpk);
+    rs.store(*sj, k);
+  }
+  return RU > 0 && sj != nullptr ? solve_row_warps(k) : 0;
 }
 
 template <int S>
-__device__ __forceinline__ void sm_chol_from(int need, const QPtr& G, int k, float* rpk,
-                                             int32_t* status, unsigned char* smraw) {
-  if (need <= S) sm_chol_s<S>(G, k, rpk, status, smraw);
-  else if constexpr (S < kCholSlots) sm_chol_from<S + 1>(need, G, k, rpk, status, smraw);
+__device__ __forceinline__ int sm_chol_from(int need, const QPtr& G, int k, float* rpk,
+                                            int32_t* status, unsigned char* smraw,
+                                            const SolveJobs* sj) {
+  if (need <= S) return sm_chol_s<S>(G, k, rpk, status, smraw, sj);
+  if constexpr (S < kCholSlots) return sm_chol_from<S + 1>(need, G, k, rpk, status, smraw, sj);
+  return 0;
 }
 
 // One CTA of kCholThreads threads: the packed factor R (FP32) with G = R^H R,
 // for 1 <= k <= kSmallCholMax (rpk 16-byte aligned, rpk_floats(k) floats).
 // Only the upper triangle of G is read.  A non-positive or non-finite pivot
-// sets ILL_CONDITIONED and continues with a tiny pivot.
-__device__ __forceinline__ void sm_chol(const QPtr& G, int k, float* rpk, int32_t* status,
-                                        unsigned char* smraw) {
-  sm_chol_from<1>((k * (k + 1) / 2 + kCholThreads - 1) / kCholThreads, G, k, rpk, status, smraw);
+// sets ILL_CONDITIONED and continues with a tiny pivot.  With sj, rpk must be
+// in shared memory.  Returns n, the number of row warps: the rows
+// solve_row_of(i), i < n, of the solves Z = Y R^-1 were done along the way;
+// the other rows (all of them when n = 0) are left to the caller.
+__device__ __forceinline__ int sm_chol(const QPtr& G, int k, float* rpk, int32_t* status,
+                                        unsigned char* smraw, const SolveJobs* sj = nullptr) {
+  return sm_chol_from<1>((k * (k + 1) / 2 + kCholThreads - 1) / kCholThreads, G, k, rpk, status,
+                         smraw, sj);
 }
 
 // ---------------------------------------------------------------------------
