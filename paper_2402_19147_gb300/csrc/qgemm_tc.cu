@@ -51,7 +51,8 @@ constexpr int BM = 128;
 constexpr int ROWB = 64;                      // bytes of K per shared row (one swizzle row)
 constexpr int A_PLANE = BM * ROWB;            // 8 KiB
 constexpr int A_STAGE = 4 * A_PLANE;
-constexpr int kTcThreads = 192;
+constexpr int kEpiWarps = 8;                  // two per TMEM sub-partition
+constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 
 // Shape of one instantiation: output tiles of BM x BNT (per plane).  BNT = 64
 // for the large product Z = C T; BNT = 32 for T = U R, whose c = O(100) rows
@@ -62,10 +63,13 @@ struct TcShape {
   static constexpr int B_PLANE = BN * ROWB;            // 4 KiB at BN 64
   static constexpr int B_STAGE = 4 * B_PLANE;
   static constexpr int STAGE = A_STAGE + B_STAGE;      // 48 KiB at BN 64
-  static constexpr int STAGES = BN == 64 ? 4 : 5;
+  static constexpr int STAGES = BN == 128 ? 3 : BN == 64 ? 4 : 5;
   static constexpr int ACC_COLS = 4 * BN;              // FP32 TMEM columns per accumulator
-  static constexpr int TMEM_COLS = 2 * ACC_COLS;       // two accumulators (a power of two)
-  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+  // two accumulators where they fit the 512 columns, so that the epilogue of
+  // one tile overlaps the MMAs of the next; one at BN 128
+  static constexpr int NACC = 2 * ACC_COLS <= 512 ? 2 : 1;
+  static constexpr int TMEM_COLS = NACC * ACC_COLS;    // a power of two
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 512;   // barriers, TMEM slot, reductions
 };
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
@@ -247,7 +251,8 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
            TcParams p) {
   using Sh = TcShape<BNT>;
   constexpr int BN = Sh::BN, B_PLANE = Sh::B_PLANE, STAGE = Sh::STAGE, STAGES = Sh::STAGES;
-  constexpr int ACC_COLS = Sh::ACC_COLS, TMEM_COLS = Sh::TMEM_COLS;
+  constexpr int ACC_COLS = Sh::ACC_COLS, TMEM_COLS = Sh::TMEM_COLS, NACC = Sh::NACC;
+  static_assert(BN % 32 == 0 && TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM allocation");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -272,7 +277,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], 4); }
+    for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], kEpiWarps); }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -311,8 +316,8 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     int local = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++local) {
-      const int a = local & 1;
-      const uint32_t aph = (local >> 1) & 1;
+      const int a = local % NACC;
+      const uint32_t aph = (local / NACC) & 1;
       if (!mbar_wait(&tempty[a], aph ^ 1u, abort_flag)) break;
       tc_fence_after();
       const uint32_t dbase = tmem_base + (uint32_t)(a * ACC_COLS);
@@ -354,41 +359,53 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     // -------------------------------------------------------- epilogue --
     const int sp = warp % 4;                 // TMEM sub-partition (lanes 32 sp ...)
     const int epi = warp - 2;
+    const int half = epi / 4;                // the two warps of a sub-partition take alternate chunks
     int local = 0;
+    // A values of all four planes of one 16-column chunk (row `row`)
+    auto load_a = [&](float4 (&av)[4][4], int row, int c0) {
+      const bool in_row = row < p.M;
+      const bool full16 = p.a_vec && c0 + 16 <= p.N;
+#pragma unroll
+      for (int pl = 0; pl < 4; ++pl) {
+        const float* ar = p.a[pl] + (int64_t)row * p.lda + c0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (in_row && full16) {
+            av[pl][q] = __ldcs(reinterpret_cast<const float4*>(ar) + q);
+          } else {
+            float e[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e[u] = (in_row && c0 + 4 * q + u < p.N) ? ar[4 * q + u] : 0.f;
+            av[pl][q] = make_float4(e[0], e[1], e[2], e[3]);
+          }
+        }
+      }
+    };
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
-      const int a = local & 1;
-      const uint32_t aph = (local >> 1) & 1;
-      if (!mbar_wait(&tfull[a], aph, abort_flag)) break;
-      tc_fence_after();
+      const int a = local % NACC;
+      const uint32_t aph = (local / NACC) & 1;
       const int mt = tile % mtiles, nt = tile / mtiles;
       const int row = mt * BM + sp * 32 + lane;
       const int n0 = nt * BN;
+      // the residual's first A chunk is fetched while the MMAs still run
+      float4 anext[4][4];
+      if (p.mode == MODE_RESIDUAL) load_a(anext, row, n0 + 16 * half);
+      if (!mbar_wait(&tfull[a], aph, abort_flag)) break;
+      tc_fence_after();
       const uint32_t tb = tmem_base + (uint32_t)(a * ACC_COLS) + ((uint32_t)(sp * 32) << 16);
       double dsum = 0.0, asum = 0.0;
       if (p.mode == MODE_RESIDUAL) {
 #pragma unroll 1
-        for (int ch = 0; ch < BN / 16; ++ch) {
+        for (int ch = half; ch < BN / 16; ch += 2) {
           const int c0 = n0 + ch * 16;
-          // the A values of all four planes of this 16-column chunk first
           float4 av[4][4];
+#pragma unroll
+          for (int pl = 0; pl < 4; ++pl)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) av[pl][q] = anext[pl][q];
+          if (ch + 2 < BN / 16) load_a(anext, row, c0 + 32);   // this warp's next chunk in flight
           const bool in_row = row < p.M;
           const bool full16 = p.a_vec && c0 + 16 <= p.N;
-#pragma unroll
-          for (int pl = 0; pl < 4; ++pl) {
-            const float* ar = p.a[pl] + (int64_t)row * p.lda + c0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              if (in_row && full16) {
-                av[pl][q] = __ldcs(reinterpret_cast<const float4*>(ar) + q);
-              } else {
-                float e[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                  e[u] = (in_row && c0 + 4 * q + u < p.N) ? ar[4 * q + u] : 0.f;
-                av[pl][q] = make_float4(e[0], e[1], e[2], e[3]);
-              }
-            }
-          }
           unsigned keep = 0xffffu;   // columns of the chunk that count
           if (!full16 || p.mask != nullptr) {
             keep = 0;
@@ -419,7 +436,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 #pragma unroll 1
         for (int pl = 0; pl < 4; ++pl) {
 #pragma unroll 1
-          for (int ch = 0; ch < BN / 16; ++ch) {
+          for (int ch = half; ch < BN / 16; ch += 2) {
             float z[16];
             tmem_ld16(tb + pl * BN + ch * 16, z);
             const int c0 = n0 + ch * 16;
@@ -431,18 +448,31 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
                   if (c0 + j < p.N) zr[j] = z[j];
               }
             } else if (row < p.bt_kpad) {   // MODE_SPLIT_T
-#pragma unroll 4
+              // all 16 splits first (independent chains: one warp per
+              // sub-partition has nothing else to hide their latency with),
+              // then the stores, lanes along the contiguous K of T^T
+              float pc[3][16];
+#pragma unroll
               for (int j = 0; j < 16; ++j) {
-                const int n = c0 + j;
-                if (n >= p.N) break;
-                float pc[3];
-                split_value<BF16, float>(z[j], p.bt_npieces, pc);
-                for (int q = 0; q < p.bt_npieces; ++q) {
-                  const int64_t idx = (((int64_t)q * 4 + pl) * p.bt_rows + n) * p.bt_kpad + row;
+                float o[3];
+                split_value<BF16, float>(z[j], p.bt_npieces, o);
+                pc[0][j] = o[0];
+                pc[1][j] = o[1];
+                pc[2][j] = o[2];
+              }
+              const int64_t piece = (int64_t)4 * p.bt_rows * p.bt_kpad;
+              const int64_t base = ((int64_t)pl * p.bt_rows + c0) * p.bt_kpad + row;
+#pragma unroll
+              for (int q = 0; q < 3; ++q) {
+                if (q >= p.bt_npieces) break;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                  if (c0 + j >= p.N) continue;
+                  const int64_t idx = base + q * piece + (int64_t)j * p.bt_kpad;
                   if constexpr (BF16)
-                    reinterpret_cast<__nv_bfloat16*>(p.bt)[idx] = __float2bfloat16_rn(pc[q]);
+                    reinterpret_cast<__nv_bfloat16*>(p.bt)[idx] = __float2bfloat16_rn(pc[q][j]);
                   else
-                    reinterpret_cast<float*>(p.bt)[idx] = pc[q];
+                    reinterpret_cast<float*>(p.bt)[idx] = pc[q][j];
                 }
               }
             }
@@ -458,12 +488,13 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
           dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
           asum += __shfl_xor_sync(0xffffffffu, asum, o);
         }
-        double* rb = red + (local & 1) * 8;
-        if (lane == 0) { rb[epi] = dsum; rb[4 + epi] = asum; }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        double* rb = red + (local & 1) * 2 * kEpiWarps;
+        if (lane == 0) { rb[epi] = dsum; rb[kEpiWarps + epi] = asum; }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
         if (epi == 0 && lane == 0) {
-          p.partial[2 * tile] = (rb[0] + rb[1]) + (rb[2] + rb[3]);
-          p.partial[2 * tile + 1] = (rb[4] + rb[5]) + (rb[6] + rb[7]);
+          static_assert(kEpiWarps == 8, "fixed-order sum of eight warps");
+          p.partial[2 * tile] = ((rb[0] + rb[1]) + (rb[2] + rb[3])) + ((rb[4] + rb[5]) + (rb[6] + rb[7]));
+          p.partial[2 * tile + 1] = ((rb[8] + rb[9]) + (rb[10] + rb[11])) + ((rb[12] + rb[13]) + (rb[14] + rb[15]));
         }
       }
     }
@@ -597,7 +628,7 @@ struct TcWs {
   double* partial;
 };
 
-constexpr int kBn1 = 32, kBn2 = 64;   // tile widths of T = U R and Z = C T
+constexpr int kBn1 = 32, kBn2 = 128;   // tile widths of T = U R and Z = C T
 
 TcWs carve_tc(Carve& cv, const TcPlan& p1, const TcPlan& p2, int64_t m, int64_t n, int64_t c,
               int64_t r) {
