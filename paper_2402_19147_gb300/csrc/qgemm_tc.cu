@@ -57,23 +57,32 @@ constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 // Shape of one instantiation: output tiles of BM x BNT (per plane).  BNT = 64
 // for the large product Z = C T; BNT = 32 for T = U R, whose c = O(100) rows
 // give too few 128 x 64 tiles to occupy the GPU.
+constexpr int pow2_at_least(int x) {
+  int p = 32;
+  while (p < x) p *= 2;
+  return p;
+}
+
 template <int BNT>
 struct TcShape {
   static constexpr int BN = BNT;
   static constexpr int B_PLANE = BN * ROWB;            // 4 KiB at BN 64
   static constexpr int B_STAGE = 4 * B_PLANE;
   static constexpr int STAGE = A_STAGE + B_STAGE;      // 48 KiB at BN 64
-  static constexpr int STAGES = BN == 128 ? 3 : BN == 64 ? 4 : 5;
+  static constexpr int STAGES = BN >= 112 ? 3 : BN == 64 ? 4 : 5;
   static constexpr int ACC_COLS = 4 * BN;              // FP32 TMEM columns per accumulator
   // two accumulators where they fit the 512 columns, so that the epilogue of
   // one tile overlaps the MMAs of the next; one at BN 128
   static constexpr int NACC = 2 * ACC_COLS <= 512 ? 2 : 1;
-  static constexpr int TMEM_COLS = NACC * ACC_COLS;    // a power of two
+  static constexpr int TMEM_COLS = pow2_at_least(NACC * ACC_COLS);   // the allocation unit
   static constexpr int SMEM = STAGES * STAGE + 1024 + 512;   // barriers, TMEM slot, reductions
 };
 constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
-enum { MODE_STORE_Z = 0, MODE_RESIDUAL = 1, MODE_SPLIT_T = 2 };
+// MODE_STORE_ZT stores the tile transposed, z[t][col][row] with ldz between
+// columns: the lanes of a warp hold consecutive rows, so each store of one
+// column is one contiguous 128-byte line.
+enum { MODE_STORE_Z = 0, MODE_RESIDUAL = 1, MODE_STORE_ZT = 2 };
 
 struct TcParams {
   int M, N;
@@ -82,19 +91,17 @@ struct TcParams {
   int nterms;
   int ta[6], tb[6];       // piece of X and of Y of each term
   int mode;
+  int nsplit;             // K-range splits per tile; split s of a tile stores to z + s * zsplit
   // MODE_STORE_Z
   float* z[4];
-  int64_t ldz;
+  int64_t ldz, zsplit;
+  int z_vec;              // planes (and split offsets) 16-byte aligned and ldz % 4 == 0
   // MODE_RESIDUAL
   const float* a[4];
   int64_t lda;
   int a_vec;              // planes 16-byte aligned and lda % 4 == 0
   const uint8_t* mask;
   double* partial;
-  // MODE_SPLIT_T: pieces of Z^T into [piece][plane][bt_rows][bt_kpad]
-  void* bt;
-  int bt_npieces;
-  int64_t bt_rows, bt_kpad;
   int32_t* status;
 };
 
@@ -245,14 +252,17 @@ __device__ __forceinline__ void split_value(T x, int npieces, float out[3]) {
 }
 
 // ------------------------------------------------------------------ kernel -
-template <bool BF16, int BNT>
+// REV: Z = sum_k Y[n][k] X[m][k] (the B operand on the left of each
+// quaternion product) instead of X[m][k] Y[n][k]; the two differ in the sign
+// of the cross terms.  Work item w is split w % nsplit of tile w / nsplit.
+template <bool BF16, int BNT, bool REV>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
            TcParams p) {
   using Sh = TcShape<BNT>;
   constexpr int BN = Sh::BN, B_PLANE = Sh::B_PLANE, STAGE = Sh::STAGE, STAGES = Sh::STAGES;
   constexpr int ACC_COLS = Sh::ACC_COLS, TMEM_COLS = Sh::TMEM_COLS, NACC = Sh::NACC;
-  static_assert(BN % 32 == 0 && TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM allocation");
+  static_assert(BN % 16 == 0 && TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM allocation");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -265,7 +275,8 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
   double* red = reinterpret_cast<double*>(tmem_slot + 2);   // [2][4]
 
   constexpr int kY[4][4] = {{0, 1, 2, 3}, {1, 0, 3, 2}, {2, 3, 0, 1}, {3, 2, 1, 0}};
-  constexpr int kNeg[4][4] = {{0, 1, 1, 1}, {0, 0, 0, 1}, {0, 1, 0, 0}, {0, 0, 1, 0}};
+  constexpr int kNegFwd[4][4] = {{0, 1, 1, 1}, {0, 0, 0, 1}, {0, 1, 0, 0}, {0, 0, 1, 0}};
+  constexpr int kNegRev[4][4] = {{0, 1, 1, 1}, {0, 0, 1, 0}, {0, 0, 0, 1}, {0, 1, 0, 0}};
   constexpr uint32_t kIdPos = make_idesc(BF16, false, BN), kIdNeg = make_idesc(BF16, true, BN);
   constexpr int kElemsPerRow = ROWB / (BF16 ? 2 : 4);
   constexpr int kStepElems = 32 / (BF16 ? 2 : 4);          // K of one MMA (32 bytes)
@@ -274,6 +285,8 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
   const int mtiles = (p.M + BM - 1) / BM, ntiles = (p.N + BN - 1) / BN;
   const int tiles = mtiles * ntiles;
   const int kiters = p.nterms * p.kblocks;
+  const int items = tiles * p.nsplit;
+  const int kper = (kiters + p.nsplit - 1) / p.nsplit;   // every split non-empty (host)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -297,10 +310,12 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     // ---------------------------------------------------- TMA producer --
     uint32_t it = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      const int tile = item / p.nsplit, split = item % p.nsplit;
       const int mt = tile % mtiles, nt = tile / mtiles;
-      for (int term = 0; term < p.nterms && ok; ++term)
-        for (int kb = 0; kb < p.kblocks; ++kb, ++it) {
+      const int k0 = split * kper, k1 = min(k0 + kper, kiters);
+      for (int ki = k0; ki < k1; ++ki, ++it) {
+          const int term = ki / p.kblocks, kb = ki % p.kblocks;
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) { ok = false; break; }
@@ -315,13 +330,15 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     uint32_t it = 0;
     int local = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++local) {
+    for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++local) {
+      const int split = item % p.nsplit;
+      const int k0 = split * kper, k1 = min(k0 + kper, kiters);
       const int a = local % NACC;
       const uint32_t aph = (local / NACC) & 1;
       if (!mbar_wait(&tempty[a], aph ^ 1u, abort_flag)) break;
       tc_fence_after();
       const uint32_t dbase = tmem_base + (uint32_t)(a * ACC_COLS);
-      for (int ki = 0; ki < kiters; ++ki, ++it) {
+      for (int ki = k0; ki < k1; ++ki, ++it) {
         const int s = it % STAGES;
         const uint32_t ph = (it / STAGES) & 1u;
         if (!mbar_wait(&full[s], ph, abort_flag)) { ok = false; break; }
@@ -346,8 +363,9 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
             for (int pl = 0; pl < 4; ++pl) {
               const uint64_t ad = ad0 + (uint64_t)((t * A_PLANE + ks * 32) >> 4);
               const uint64_t bd = bd0 + (uint64_t)((kY[pl][t] * B_PLANE + ks * 32) >> 4);
-              const uint32_t acc = (ki > 0 || ks > 0 || t > 0) ? 1u : 0u;
-              umma<BF16>(dbase + pl * BN, ad, bd, kNeg[pl][t] ? kIdNeg : kIdPos, acc);
+              const uint32_t acc = (ki > k0 || ks > 0 || t > 0) ? 1u : 0u;
+              const int neg = REV ? kNegRev[pl][t] : kNegFwd[pl][t];
+              umma<BF16>(dbase + pl * BN, ad, bd, neg ? kIdNeg : kIdPos, acc);
             }
           }
         }
@@ -381,7 +399,8 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
         }
       }
     };
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++local) {
+    for (int item = blockIdx.x; item < items; item += gridDim.x, ++local) {
+      const int tile = item / p.nsplit, split = item % p.nsplit;
       const int a = local % NACC;
       const uint32_t aph = (local / NACC) & 1;
       const int mt = tile % mtiles, nt = tile / mtiles;
@@ -440,40 +459,24 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
             float z[16];
             tmem_ld16(tb + pl * BN + ch * 16, z);
             const int c0 = n0 + ch * 16;
-            if (p.mode == MODE_STORE_Z) {
+            if (p.mode == MODE_STORE_ZT) {
               if (row < p.M) {
-                float* zr = p.z[pl] + (int64_t)row * p.ldz + c0;
+                float* zc = p.z[pl] + split * p.zsplit + (int64_t)c0 * p.ldz + row;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                  if (c0 + j < p.N) zc[(int64_t)j * p.ldz] = z[j];
+              }
+            } else if (row < p.M) {   // MODE_STORE_Z
+              float* zr = p.z[pl] + split * p.zsplit + (int64_t)row * p.ldz + c0;
+              if (c0 + 16 <= p.N && p.z_vec) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  reinterpret_cast<float4*>(zr)[q] =
+                      make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+              } else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
                   if (c0 + j < p.N) zr[j] = z[j];
-              }
-            } else if (row < p.bt_kpad) {   // MODE_SPLIT_T
-              // all 16 splits first (independent chains: one warp per
-              // sub-partition has nothing else to hide their latency with),
-              // then the stores, lanes along the contiguous K of T^T
-              float pc[3][16];
-#pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                float o[3];
-                split_value<BF16, float>(z[j], p.bt_npieces, o);
-                pc[0][j] = o[0];
-                pc[1][j] = o[1];
-                pc[2][j] = o[2];
-              }
-              const int64_t piece = (int64_t)4 * p.bt_rows * p.bt_kpad;
-              const int64_t base = ((int64_t)pl * p.bt_rows + c0) * p.bt_kpad + row;
-#pragma unroll
-              for (int q = 0; q < 3; ++q) {
-                if (q >= p.bt_npieces) break;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                  if (c0 + j >= p.N) continue;
-                  const int64_t idx = base + q * piece + (int64_t)j * p.bt_kpad;
-                  if constexpr (BF16)
-                    reinterpret_cast<__nv_bfloat16*>(p.bt)[idx] = __float2bfloat16_rn(pc[q][j]);
-                  else
-                    reinterpret_cast<float*>(p.bt)[idx] = pc[q][j];
-                }
               }
             }
           }
@@ -482,7 +485,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
       tc_fence_before();
       if (lane == 0) mbar_arrive(&tempty[a]);
       if (p.mode == MODE_RESIDUAL) {
-        // fixed-order reduction: warp tree, then the four warps in order
+        // fixed-order reduction: warp tree, then the eight warps in order
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
@@ -548,6 +551,83 @@ __global__ void k_split(QView S, void* dst, int64_t rows_out, int64_t K, int64_t
         const int64_t idx = (((int64_t)q * 4 + t) * rows_out + i) * kpad + k;
         if (BF16) reinterpret_cast<__nv_bfloat16*>(dst)[idx] = __float2bfloat16_rn(pc[q]);
         else reinterpret_cast<float*>(dst)[idx] = pc[q];
+      }
+    }
+  }
+}
+
+// Pieces of T^T from the split partials of T^T = R^T (x) U, stored
+// transposed: P[split][t][i][j] (column i of T^T, row j; ld = ldp, a multiple of 4).
+// For j < rows and i < kpad: v = P[0] + P[1] + ... in split order (zero for
+// i >= c), then dst[(q*4 + t)][j][i] = piece q of plane t.  A CTA takes 32
+// columns x 64 rows through shared memory: every load of all planes and
+// splits is in flight at once, read along j in pairs, written along i in
+// pairs.
+constexpr int kRedI = 32, kRedJ = 64;
+constexpr int kMaxSplits = 4;   // K splits of T^T at most
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_t_reduce(const float* __restrict__ P, int nsplit,
+                                                  int64_t split_stride, int64_t plane_stride,
+                                                  int64_t ldp, int64_t rows, int64_t c, int64_t kpad,
+                                                  int npieces, void* dst) {
+  __shared__ float tile[4][kRedI][kRedJ + 1];
+  const int tid = threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * kRedI, j0 = (int64_t)blockIdx.y * kRedJ;
+  {
+    const int jl = 2 * (tid % 32), r0 = tid / 32;   // rows j0 + jl, j0 + jl + 1; columns r0 + 8 k
+    const int64_t j = j0 + jl;
+#pragma unroll
+    for (int k = 0; k < kRedI / 8; ++k) {
+      const int r = r0 + 8 * k;
+      const int64_t i = i0 + r;
+      float2 v[4] = {};
+      if (i < c && j < rows) {   // j + 1 < ldp: the pair stays in the padded column
+        const float* src = P + i * ldp + j;
+        float2 x[kMaxSplits][4];   // every load of the column pair issued before the sums
+#pragma unroll
+        for (int sp = 0; sp < kMaxSplits; ++sp)
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            x[sp][t] = sp < nsplit
+                           ? __ldcs(reinterpret_cast<const float2*>(src + sp * split_stride + t * plane_stride))
+                           : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int sp = 0; sp < kMaxSplits; ++sp)
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            v[t].x += x[sp][t].x;
+            v[t].y += x[sp][t].y;
+          }
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        tile[t][r][jl] = v[t].x;
+        tile[t][r][jl + 1] = v[t].y;
+      }
+    }
+  }
+  __syncthreads();
+  const int il = 2 * (tid % 16), jr0 = tid / 16;   // columns i0 + il, + 1; rows jr0 + 16 k
+  const int64_t i = i0 + il;
+#pragma unroll 1
+  for (int k = 0; k < kRedJ / 16; ++k) {
+    const int jr = jr0 + 16 * k;
+    const int64_t j = j0 + jr;
+    if (j >= rows || i >= kpad) continue;   // kpad is even: i + 1 < kpad as well
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float p0[3], p1[3];
+      split_value<BF16, float>(tile[t][il][jr], npieces, p0);
+      split_value<BF16, float>(tile[t][il + 1][jr], npieces, p1);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q >= npieces) break;
+        const int64_t idx = (((int64_t)q * 4 + t) * rows + j) * kpad + i;
+        if constexpr (BF16)
+          *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(dst) + idx) =
+              __floats2bfloat162_rn(p0[q], p1[q]);
+        else
+          *reinterpret_cast<float2*>(reinterpret_cast<float*>(dst) + idx) = make_float2(p0[q], p1[q]);
       }
     }
   }
@@ -625,10 +705,28 @@ inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 struct TcWs {
   void *A1, *B1, *A2, *B2;
+  float* P;   // split partials of T^T: [split][plane][n][kpad of Z = C T]
   double* partial;
 };
 
-constexpr int kBn1 = 32, kBn2 = 128;   // tile widths of T = U R and Z = C T
+// Tile widths: T^T = R^T (x) U (N over c) and Z = C T (N over n).  Both use
+// MMAs of N >= 112: an MMA costs about the same issue time up to N = 128, so
+// narrower ones waste the tensor pipe.
+constexpr int kBn1 = 112, kBn2 = 128;
+constexpr int kSplitItems = 128;   // work items T^T aims for (tiles x K splits)
+
+// K splits of T^T, from the shape alone (the workspace depends on it); every
+// split non-empty.
+int t_splits(int64_t n, int64_t c, const TcPlan& p1, int64_t kp1) {
+  const int64_t tiles = ((n + BM - 1) / BM) * ((c + kBn1 - 1) / kBn1);
+  const int kiters = p1.nterms * (int)(kp1 / p1.epr);
+  int64_t ns = kSplitItems / tiles;
+  if (ns > kMaxSplits) ns = kMaxSplits;
+  if (ns > kiters) ns = kiters;
+  if (ns < 1) ns = 1;
+  const int per = (int)((kiters + ns - 1) / ns);
+  return (kiters + per - 1) / per;
+}
 
 TcWs carve_tc(Carve& cv, const TcPlan& p1, const TcPlan& p2, int64_t m, int64_t n, int64_t c,
               int64_t r) {
@@ -639,6 +737,7 @@ TcWs carve_tc(Carve& cv, const TcPlan& p1, const TcPlan& p2, int64_t m, int64_t 
   w.B1 = cv.take<char>((size_t)(p1.npieces * 4 * n * kp1 * es));
   w.A2 = cv.take<char>((size_t)(p2.npieces * 4 * m * kp2 * es));
   w.B2 = cv.take<char>((size_t)(p2.npieces * 4 * n * kp2 * es));
+  w.P = cv.take<float>((size_t)(t_splits(n, c, p1, kp1) * 4 * kp2 * rup(n, 4)));
   const int64_t tiles = ((m + BM - 1) / BM) * ((n + kBn2 - 1) / kBn2);
   w.partial = cv.take<double>((size_t)(2 * tiles));
   return w;
@@ -660,23 +759,23 @@ qmcur_status launch_split(const qmcur_qmat* S, bool trans, void* dst, int64_t ro
   return cuda_ok(cudaGetLastError());
 }
 
-template <bool BF16, int BNT>
+template <bool BF16, int BNT, bool REV>
 qmcur_status launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& p,
                          cudaStream_t st) {
   static bool attr_done[64] = {};
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QMCUR_ERR_CUDA;
   if (!attr_done[dev]) {
-    if (cudaFuncSetAttribute(k_qgemm_tc<BF16, BNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_qgemm_tc<BF16, BNT, REV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TcShape<BNT>::SMEM) != cudaSuccess)
       return QMCUR_ERR_CUDA;
     attr_done[dev] = true;
   }
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return QMCUR_ERR_CUDA;
-  const int tiles = ((p.M + BM - 1) / BM) * ((p.N + BNT - 1) / BNT);
-  const int grid = tiles < sms ? tiles : sms;
-  k_qgemm_tc<BF16, BNT><<<grid, kTcThreads, TcShape<BNT>::SMEM, st>>>(ma, mb, p);
+  const int items = ((p.M + BM - 1) / BM) * ((p.N + BNT - 1) / BNT) * p.nsplit;
+  const int grid = items < sms ? items : sms;
+  k_qgemm_tc<BF16, BNT, REV><<<grid, kTcThreads, TcShape<BNT>::SMEM, st>>>(ma, mb, p);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -716,28 +815,36 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
     if ((s = launch_split<false>(R, true, w.B1, n, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
     if ((s = launch_split<false>(C, false, w.A2, m, c, kp2, pl2.npieces, st)) != QMCUR_OK) return s;
   }
+  // T^T = R^T (x) U: M over n (R's pieces, K-major), N over c (U's pieces),
+  // the reversed product; its split partials are summed and cut into the
+  // pieces of Z = C T's B operand by k_t_reduce.
   CUtensorMap mA1, mB1, mA2, mB2;
-  if (!make_map(&mA1, w.A1, pl.bf16, c, kp1, pl.npieces, BM) ||
-      !make_map(&mB1, w.B1, pl.bf16, n, kp1, pl.npieces, kBn1) ||
+  if (!make_map(&mA1, w.B1, pl.bf16, n, kp1, pl.npieces, BM) ||
+      !make_map(&mB1, w.A1, pl.bf16, c, kp1, pl.npieces, kBn1) ||
       !make_map(&mA2, w.A2, pl2.bf16, m, kp2, pl2.npieces, BM) ||
       !make_map(&mB2, w.B2, pl2.bf16, n, kp2, pl2.npieces, kBn2))
     return QMCUR_ERR_CUDA;
+  const int nsplit = t_splits(n, c, pl, kp1);
   TcParams p1{};
-  p1.M = (int)c;
-  p1.N = (int)n;
+  p1.M = (int)n;
+  p1.N = (int)c;
   p1.K = (int)r;
   p1.kblocks = (int)(kp1 / pl.epr);
   p1.nterms = pl.nterms;
-  for (int i = 0; i < 6; ++i) { p1.ta[i] = pl.ta[i]; p1.tb[i] = pl.tb[i]; }
-  p1.mode = MODE_SPLIT_T;
-  p1.bt = w.B2;
-  p1.bt_npieces = pl2.npieces;   // T is written in the second GEMM's split
-  p1.bt_rows = n;
-  p1.bt_kpad = kp2;
+  for (int i = 0; i < 6; ++i) { p1.ta[i] = pl.tb[i]; p1.tb[i] = pl.ta[i]; }   // R's piece, U's piece
+  p1.mode = MODE_STORE_ZT;
+  p1.nsplit = nsplit;
+  const int64_t ldp = rup(n, 4);   // partial columns padded for paired loads
+  for (int t = 0; t < 4; ++t) p1.z[t] = w.P + (int64_t)t * kp2 * ldp;
+  p1.ldz = ldp;
+  p1.zsplit = 4 * kp2 * ldp;
   p1.status = dev_status;
   TcParams p2 = p1;
   p2.M = (int)m;
+  p2.N = (int)n;
   p2.K = (int)c;
+  p2.nsplit = 1;
+  p2.zsplit = 0;
   p2.kblocks = (int)(kp2 / pl2.epr);
   p2.nterms = pl2.nterms;
   for (int i = 0; i < 6; ++i) { p2.ta[i] = pl2.ta[i]; p2.tb[i] = pl2.tb[i]; }
@@ -745,6 +852,9 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
     p2.mode = MODE_STORE_Z;
     for (int t = 0; t < 4; ++t) p2.z[t] = reinterpret_cast<float*>(Z->plane[t]);
     p2.ldz = Z->ld;
+    p2.z_vec = Z->ld % 4 == 0;
+    for (int t = 0; t < 4; ++t)
+      p2.z_vec = p2.z_vec && reinterpret_cast<uintptr_t>(Z->plane[t]) % 16 == 0;
   } else {
     p2.mode = MODE_RESIDUAL;
     for (int t = 0; t < 4; ++t) p2.a[t] = reinterpret_cast<const float*>(A->plane[t]);
@@ -755,12 +865,18 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
     p2.mask = mask;
     p2.partial = w.partial;
   }
+  if ((n + kRedJ - 1) / kRedJ > 65535) return QMCUR_ERR_UNSUPPORTED;
+  const dim3 rgrid((unsigned)((kp2 + kRedI - 1) / kRedI), (unsigned)((n + kRedJ - 1) / kRedJ));
   if (pl.bf16) {
-    if ((s = launch_gemm<true, kBn1>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
-    if ((s = launch_gemm<true, kBn2>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
+    if ((s = launch_gemm<true, kBn1, true>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
+    k_t_reduce<true><<<rgrid, 256, 0, st>>>(w.P, nsplit, p1.zsplit, kp2 * ldp, ldp, n, c, kp2,
+                                            pl2.npieces, w.B2);
+    if ((s = launch_gemm<true, kBn2, false>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
   } else {
-    if ((s = launch_gemm<false, kBn1>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
-    if ((s = launch_gemm<false, kBn2>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
+    if ((s = launch_gemm<false, kBn1, true>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
+    k_t_reduce<false><<<rgrid, 256, 0, st>>>(w.P, nsplit, p1.zsplit, kp2 * ldp, ldp, n, c, kp2,
+                                             pl2.npieces, w.B2);
+    if ((s = launch_gemm<false, kBn2, false>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
   }
   if (Z == nullptr) {
     const int64_t tiles = ((m + BM - 1) / BM) * ((n + kBn2 - 1) / kBn2);
