@@ -136,6 +136,7 @@ struct Phase {
 };
 
 constexpr int kMaxPhases = 32;
+constexpr int kMaxSplits = 8;   // k-range splits of a GEMM step at most
 
 struct FusedProg {
   int nph;
@@ -243,9 +244,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_co
         worker_sync(1 + worker);
         if (last_sh[worker]) {
           __threadfence();
+          // every partial in flight at once, then the sum in split order
+          const float4* src = P.part + (pbase + (size_t)tile * jb.splits) * kSmTileThreads + wtid;
+          float4 part[kMaxSplits];
+#pragma unroll
+          for (int q2 = 0; q2 < kMaxSplits; ++q2)
+            part[q2] = q2 < jb.splits ? __ldcg(src + (size_t)q2 * kSmTileThreads) : make_float4(0.f, 0.f, 0.f, 0.f);
           float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-          for (int q2 = 0; q2 < jb.splits; ++q2)
-            sum = f4add(sum, __ldcg(P.part + (pbase + (size_t)tile * jb.splits + q2) * kSmTileThreads + wtid));
+#pragma unroll
+          for (int q2 = 0; q2 < kMaxSplits; ++q2) sum = f4add(sum, part[q2]);
           sm_tile_store(jb.g, tm, tn, wtid, sum);
           if (wtid == 0) *cnt = 0u;   // ready for the next step, after the grid barrier
         }
@@ -319,7 +326,7 @@ struct ProgBuilder {
       const int ntiles = tiles_of(s);
       const int slices = (s.K + kSmBK - 1) / kSmBK;
       int splits = workers / all_tiles;
-      if (splits > 8) splits = 8;
+      if (splits > kMaxSplits) splits = kMaxSplits;
       if (splits > slices) splits = slices;
       if (splits < 2) splits = 1;
       const int per = (slices + splits - 1) / splits;
