@@ -214,7 +214,9 @@ def launches_per_step(args):
     """Kernels of the library launched per decomposition (counted from the code)."""
     n = 3 + 2                                  # probabilities (pass, fold, scale), sampler + gathers
     n += 4 if args.pinv == "jacobi" else 1     # pseudo-inverse (one cooperative kernel)
-    n += 3 if args.prec == "fp32" else 6       # GEMMs (+ operand splits) + fold
+    # FP32: T = U R, Z = C T with the residual, fold.  Split paths: three
+    # operand splits, T^T = R^T U, the split-k reduce of T^T, Z = C T, fold.
+    n += 3 if args.prec == "fp32" else 7
     return n
 
 
