@@ -214,9 +214,10 @@ def launches_per_step(args):
     """Kernels of the library launched per decomposition (counted from the code)."""
     n = 3 + 2                                  # probabilities (pass, fold, scale), sampler + gathers
     n += 4 if args.pinv == "jacobi" else 1     # pseudo-inverse (one cooperative kernel)
-    # FP32: T = U R, Z = C T with the residual, fold.  Split paths: three
-    # operand splits, T^T = R^T U, the split-k reduce of T^T, Z = C T, fold.
-    n += 3 if args.prec == "fp32" else 7
+    # FP32: T = U R, Z = C T with the residual, fold.  Split paths: the
+    # operand splits (one launch), T^T = R^T U, the split-k reduce of T^T, and
+    # Z = C T with the residual, whose last CTA folds the partials.
+    n += 3 if args.prec == "fp32" else 4
     return n
 
 

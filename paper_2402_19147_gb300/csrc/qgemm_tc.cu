@@ -19,18 +19,21 @@
 // slice into shared memory (64-byte swizzle).  K steps that lie entirely in
 // the padding are not issued.
 //
-// Kernel: persistent, warp-specialised (6 warps).  Warp 0 lane 0 issues TMA
-// loads into a 4-stage ring; warp 1 owns the TMEM allocation and its lane 0
-// issues the MMAs (M = 128, N = 64 per MMA, four output planes side by side
-// in TMEM, two accumulator buffers so the epilogue of one tile overlaps the
-// MMAs of the next); warps 2-5 are the epilogue, each reading its own
-// 32-lane TMEM sub-partition (one output row per thread).  Epilogue modes:
+// Kernel: persistent, warp-specialised (10 warps).  Warp 0 lane 0 issues TMA
+// loads into a ring of 3-5 stages; warp 1 owns the TMEM allocation and its
+// lane 0 issues the MMAs (M = 128, N = BN per MMA: 112 for T^T = R^T U, 128
+// for Z = C T; the four output planes side by side in TMEM, with two
+// accumulator buffers where 2 x 4 x BN columns fit in 512, so that the
+// epilogue of one tile overlaps the MMAs of the next); warps 2-9 are the
+// epilogue, two per 32-lane TMEM sub-partition (one output row per thread),
+// taking alternate 16-column chunks.  Epilogue modes:
 //   STORE_Z   write Z (FP32 planes);
 //   RESIDUAL  never write Z: read the matching tile of A and accumulate
 //             sum |a - z|^2, sum |a|^2 (optionally over a mask) into one FP64
-//             pair per tile, folded later in a fixed order;
-//   SPLIT_T   write the pieces of Z^T straight into the K-major B operand of
-//             a following GEMM (T = U R feeding C T).
+//             pair per tile; the last CTA to finish folds the pairs in a
+//             fixed order into {rel, num, den};
+//   STORE_ZT  write the tile transposed (T^T's split-K partials, summed and
+//             cut into the pieces of Z = C T's B operand by k_t_reduce).
 // Every wait is bounded: on timeout the kernel raises an abort flag, the
 // roles drain, TMEM is freed and QMCUR_ERR_TIMEOUT is reported.
 #include <cuda.h>
@@ -41,9 +44,6 @@
 #include "common.cuh"
 
 namespace qmcur {
-
-size_t residual_partials(int64_t m, int64_t n);
-__global__ void k_residual_fold(const double* partial, int64_t count, double* out3);
 
 namespace {
 
@@ -101,7 +101,9 @@ struct TcParams {
   int64_t lda;
   int a_vec;              // planes 16-byte aligned and lda % 4 == 0
   const uint8_t* mask;
-  double* partial;
+  double* partial;        // two doubles per tile
+  double* out3;           // the last CTA folds the partials into out3
+  unsigned* done;         // arrival count of that fold, zero at launch
   int32_t* status;
 };
 
@@ -498,6 +500,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
           static_assert(kEpiWarps == 8, "fixed-order sum of eight warps");
           p.partial[2 * tile] = ((rb[0] + rb[1]) + (rb[2] + rb[3])) + ((rb[4] + rb[5]) + (rb[6] + rb[7]));
           p.partial[2 * tile + 1] = ((rb[8] + rb[9]) + (rb[10] + rb[11])) + ((rb[12] + rb[13]) + (rb[14] + rb[15]));
+          __threadfence();   // visible to the CTA that folds the partials
         }
       }
     }
@@ -511,46 +514,149 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
                  : "memory");
   }
   if (threadIdx.x == 0 && *abort_flag) set_status(p.status, QMCUR_ERR_TIMEOUT);
+  if (p.mode == MODE_RESIDUAL && p.done != nullptr) {
+    // The last CTA to finish folds the per-item partials into out3 in a fixed
+    // order: strided sums, a shuffle tree per warp, then the warps in order.
+    __shared__ int s_last;
+    __shared__ double s_red[2][kTcThreads / 32];
+    if (threadIdx.x == 0) s_last = atomicAdd(p.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      const int64_t count = tiles;
+      double num = 0.0, den = 0.0;
+      for (int64_t k = threadIdx.x; k < count; k += kTcThreads) {
+        num += __ldcg(p.partial + 2 * k);
+        den += __ldcg(p.partial + 2 * k + 1);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+      }
+      if (lane == 0) { s_red[0][warp] = num; s_red[1][warp] = den; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        num = 0.0;
+        den = 0.0;
+        for (int w = 0; w < kTcThreads / 32; ++w) { num += s_red[0][w]; den += s_red[1][w]; }
+        p.out3[1] = num;
+        p.out3[2] = den;
+        p.out3[0] = den > 0.0 ? sqrt(num / den) : __longlong_as_double(0x7ff8000000000000ll);
+      }
+    }
+  }
 }
 
-// Operand pieces: dst[(q*4 + t)][i][k] for i < rows_out, k < kpad, taken
-// from S(i, k) (or S(k, i) when TRANS), zero for k >= K.
-template <bool BF16, typename TS, bool TRANS>
-__global__ void k_split(QView S, void* dst, int64_t rows_out, int64_t K, int64_t kpad, int npieces) {
-  __shared__ float tile[4][32][33];
-  const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 32 x 8 threads
-  if (TRANS) {
-    // read S(k0 + ty.., i0 + tx) coalesced along i, transpose through shared memory
-    for (int r = ty; r < 32; r += 8) {
-      const int64_t k = k0 + r, i = i0 + tx;
+
+// Operand pieces of up to three operands in one launch: for job j,
+// dst[(q*4 + t)][i][k] for i < rows_out, k < kpad is piece q of plane t of
+// S(i, k) (or S(k, i) when trans), zero for k >= K.  A CTA owns a tile of
+// 32 rows x 64 k: every load of the tile is issued before the first store
+// (the tile passes through shared memory, which also transposes it), then
+// each lane splits a pair of k and writes the pieces in pairs.
+constexpr int kSplitRows = 32, kSplitK = 64, kSplitPitch = kSplitK + 2;
+constexpr int kMaxSplitJobs = 3;
+struct SplitJob {
+  QView S;
+  void* dst;
+  int64_t rows_out, K, kpad;
+  int npieces, trans, f64, vec2;   // vec2: non-trans rows read as float2
+  int tiles_k, first_tile;         // tiles along k; index of the job's first tile
+};
+struct SplitJobs {
+  SplitJob j[kMaxSplitJobs];
+  int count;
+};
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_split_ops(const __grid_constant__ SplitJobs jobs) {
+  __shared__ __align__(16) float tile[4][kSplitRows][kSplitPitch];
+  int jb = 0;
+#pragma unroll
+  for (int q = 1; q < kMaxSplitJobs; ++q)
+    if (q < jobs.count && (int)blockIdx.x >= jobs.j[q].first_tile) jb = q;
+  const SplitJob& J = jobs.j[jb];
+  const int tl = (int)blockIdx.x - J.first_tile;
+  const int64_t i0 = (int64_t)(tl / J.tiles_k) * kSplitRows, k0 = (int64_t)(tl % J.tiles_k) * kSplitK;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  if (!J.trans) {
+    // S(i0 + warp + 8u, k0 + 2 lane + {0, 1}): 16 loads per thread
+    const int64_t k = k0 + 2 * lane;
+    float2 v[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + warp + 8 * u;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float2 x = make_float2(0.f, 0.f);
+        if (i < J.rows_out && k < J.K) {
+          if (J.f64) {
+            const double* src = reinterpret_cast<const double*>(J.S.p[t]) + i * J.S.ld + k;
+            x.x = (float)src[0];
+            if (k + 1 < J.K) x.y = (float)src[1];
+          } else {
+            const float* src = reinterpret_cast<const float*>(J.S.p[t]) + i * J.S.ld + k;
+            if (J.vec2 && k + 1 < J.K) {
+              x = *reinterpret_cast<const float2*>(src);
+            } else {
+              x.x = src[0];
+              if (k + 1 < J.K) x.y = src[1];
+            }
+          }
+        }
+        v[u][t] = x;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int t = 0; t < 4; ++t)
-        tile[t][r][tx] = (k < K && i < rows_out)
-                             ? (float)reinterpret_cast<const TS*>(S.p[t])[k * S.ld + i] : 0.f;
+        *reinterpret_cast<float2*>(&tile[t][warp + 8 * u][2 * lane]) = v[u][t];
+  } else {
+    // S(k0 + warp + 8u, i0 + lane), coalesced along i: 32 loads per thread
+    const int64_t i = i0 + lane;
+    float v[8][4];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t k = k0 + warp + 8 * u;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float x = 0.f;
+        if (i < J.rows_out && k < J.K)
+          x = J.f64 ? (float)reinterpret_cast<const double*>(J.S.p[t])[k * J.S.ld + i]
+                    : reinterpret_cast<const float*>(J.S.p[t])[k * J.S.ld + i];
+        v[u][t] = x;
+      }
     }
-    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) tile[t][lane][warp + 8 * u] = v[u][t];
   }
-  const size_t es = BF16 ? 2 : 4;
-  (void)es;
-  for (int r = ty; r < 32; r += 8) {
-    const int64_t i = i0 + r, k = k0 + tx;
-    if (i >= rows_out || k >= kpad) continue;
+  __syncthreads();
+  const int64_t k = k0 + 2 * lane;   // kpad is even: k < kpad implies k + 1 < kpad
+  if (k >= J.kpad) return;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int il = warp + 8 * u;
+    const int64_t i = i0 + il;
+    if (i >= J.rows_out) break;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      float pc[3] = {0.f, 0.f, 0.f};
-      if (k < K) {
-        if (TRANS) {
-          split_value<BF16, float>(tile[t][tx][r], npieces, pc);
-        } else {
-          const TS x = reinterpret_cast<const TS*>(S.p[t])[i * S.ld + k];
-          split_value<BF16, TS>(x, npieces, pc);
-        }
-      }
-      for (int q = 0; q < npieces; ++q) {
-        const int64_t idx = (((int64_t)q * 4 + t) * rows_out + i) * kpad + k;
-        if (BF16) reinterpret_cast<__nv_bfloat16*>(dst)[idx] = __float2bfloat16_rn(pc[q]);
-        else reinterpret_cast<float*>(dst)[idx] = pc[q];
+      const float2 x = *reinterpret_cast<const float2*>(&tile[t][il][2 * lane]);
+      float p0[3], p1[3];
+      split_value<BF16, float>(x.x, J.npieces, p0);
+      split_value<BF16, float>(x.y, J.npieces, p1);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q >= J.npieces) break;
+        const int64_t idx = (((int64_t)q * 4 + t) * J.rows_out + i) * J.kpad + k;
+        if constexpr (BF16)
+          *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(J.dst) + idx) =
+              __floats2bfloat162_rn(p0[q], p1[q]);
+        else
+          *reinterpret_cast<float2*>(reinterpret_cast<float*>(J.dst) + idx) = make_float2(p0[q], p1[q]);
       }
     }
   }
@@ -569,9 +675,11 @@ template <bool BF16>
 __global__ void __launch_bounds__(256) k_t_reduce(const float* __restrict__ P, int nsplit,
                                                   int64_t split_stride, int64_t plane_stride,
                                                   int64_t ldp, int64_t rows, int64_t c, int64_t kpad,
-                                                  int npieces, void* dst) {
+                                                  int npieces, void* dst, unsigned* done) {
   __shared__ float tile[4][kRedI][kRedJ + 1];
   const int tid = threadIdx.x;
+  // arrival count of the residual fold of the GEMM that follows on the stream
+  if (done != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *done = 0u;
   const int64_t i0 = (int64_t)blockIdx.x * kRedI, j0 = (int64_t)blockIdx.y * kRedJ;
   {
     const int jl = 2 * (tid % 32), r0 = tid / 32;   // rows j0 + jl, j0 + jl + 1; columns r0 + 8 k
@@ -706,7 +814,8 @@ inline int64_t rup(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 struct TcWs {
   void *A1, *B1, *A2, *B2;
   float* P;   // split partials of T^T: [split][plane][n][kpad of Z = C T]
-  double* partial;
+  double* partial;   // residual partials of Z = C T, two per tile
+  unsigned* done;    // arrival count of the residual fold
 };
 
 // Tile widths: T^T = R^T (x) U (N over c) and Z = C T (N over n).  Both use
@@ -740,22 +849,37 @@ TcWs carve_tc(Carve& cv, const TcPlan& p1, const TcPlan& p2, int64_t m, int64_t 
   w.P = cv.take<float>((size_t)(t_splits(n, c, p1, kp1) * 4 * kp2 * rup(n, 4)));
   const int64_t tiles = ((m + BM - 1) / BM) * ((n + kBn2 - 1) / kBn2);
   w.partial = cv.take<double>((size_t)(2 * tiles));
+  w.done = cv.take<unsigned>(1);
   return w;
 }
 
+// Adds the pieces of operand S (rows_out x K as stored, or K x rows_out when
+// trans) to a split launch.
+bool add_split(SplitJobs& js, int& tiles, const qmcur_qmat* S, bool trans, void* dst,
+               int64_t rows_out, int64_t K, int64_t kpad, int npieces) {
+  if (js.count >= kMaxSplitJobs || kpad % 2 != 0) return false;
+  SplitJob& j = js.j[js.count++];
+  j.S = view(S);
+  j.dst = dst;
+  j.rows_out = rows_out;
+  j.K = K;
+  j.kpad = kpad;
+  j.npieces = npieces;
+  j.trans = trans ? 1 : 0;
+  j.f64 = S->dtype == QMCUR_F64 ? 1 : 0;
+  j.vec2 = S->ld % 2 == 0;
+  for (int t = 0; t < 4; ++t) j.vec2 = j.vec2 && reinterpret_cast<uintptr_t>(S->plane[t]) % 8 == 0;
+  j.tiles_k = (int)((kpad + kSplitK - 1) / kSplitK);
+  j.first_tile = tiles;
+  const int64_t t = (int64_t)j.tiles_k * ((rows_out + kSplitRows - 1) / kSplitRows);
+  if (tiles + t > INT32_MAX) return false;
+  tiles += (int)t;
+  return true;
+}
+
 template <bool BF16>
-qmcur_status launch_split(const qmcur_qmat* S, bool trans, void* dst, int64_t rows_out, int64_t K,
-                          int64_t kpad, int npieces, cudaStream_t st) {
-  dim3 grid((unsigned)((kpad + 31) / 32), (unsigned)((rows_out + 31) / 32));
-  if (grid.y > 65535) return QMCUR_ERR_UNSUPPORTED;
-  QView v = view(S);
-  if (S->dtype == QMCUR_F64) {
-    if (trans) k_split<BF16, double, true><<<grid, 256, 0, st>>>(v, dst, rows_out, K, kpad, npieces);
-    else k_split<BF16, double, false><<<grid, 256, 0, st>>>(v, dst, rows_out, K, kpad, npieces);
-  } else {
-    if (trans) k_split<BF16, float, true><<<grid, 256, 0, st>>>(v, dst, rows_out, K, kpad, npieces);
-    else k_split<BF16, float, false><<<grid, 256, 0, st>>>(v, dst, rows_out, K, kpad, npieces);
-  }
+qmcur_status launch_splits(const SplitJobs& js, int tiles, cudaStream_t st) {
+  k_split_ops<BF16><<<(unsigned)tiles, 256, 0, st>>>(js);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -805,16 +929,16 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
   if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
   const int64_t kp1 = rup(r, pl.epr), kp2 = rup(c, pl2.epr);
   qmcur_status s;
-  // operand pieces: U (c x r) and C (m x c) as they are, R (r x n) transposed
-  if (pl.bf16) {
-    if ((s = launch_split<true>(U, false, w.A1, c, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
-    if ((s = launch_split<true>(R, true, w.B1, n, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
-    if ((s = launch_split<true>(C, false, w.A2, m, c, kp2, pl2.npieces, st)) != QMCUR_OK) return s;
-  } else {
-    if ((s = launch_split<false>(U, false, w.A1, c, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
-    if ((s = launch_split<false>(R, true, w.B1, n, r, kp1, pl.npieces, st)) != QMCUR_OK) return s;
-    if ((s = launch_split<false>(C, false, w.A2, m, c, kp2, pl2.npieces, st)) != QMCUR_OK) return s;
-  }
+  // operand pieces, one launch: U (c x r) and C (m x c) as they are, R (r x n)
+  // transposed
+  SplitJobs js{};
+  int stiles = 0;
+  if (!add_split(js, stiles, U, false, w.A1, c, r, kp1, pl.npieces) ||
+      !add_split(js, stiles, R, true, w.B1, n, r, kp1, pl.npieces) ||
+      !add_split(js, stiles, C, false, w.A2, m, c, kp2, pl2.npieces))
+    return QMCUR_ERR_UNSUPPORTED;
+  s = pl.bf16 ? launch_splits<true>(js, stiles, st) : launch_splits<false>(js, stiles, st);
+  if (s != QMCUR_OK) return s;
   // T^T = R^T (x) U: M over n (R's pieces, K-major), N over c (U's pieces),
   // the reversed product; its split partials are summed and cut into the
   // pieces of Z = C T's B operand by k_t_reduce.
@@ -864,23 +988,22 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
       p2.a_vec = p2.a_vec && reinterpret_cast<uintptr_t>(A->plane[t]) % 16 == 0;
     p2.mask = mask;
     p2.partial = w.partial;
+    p2.out3 = out3;
+    p2.done = w.done;
   }
   if ((n + kRedJ - 1) / kRedJ > 65535) return QMCUR_ERR_UNSUPPORTED;
   const dim3 rgrid((unsigned)((kp2 + kRedI - 1) / kRedI), (unsigned)((n + kRedJ - 1) / kRedJ));
+  // (the residual GEMM folds its own partials: k_t_reduce zeroes the count)
   if (pl.bf16) {
     if ((s = launch_gemm<true, kBn1, true>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
     k_t_reduce<true><<<rgrid, 256, 0, st>>>(w.P, nsplit, p1.zsplit, kp2 * ldp, ldp, n, c, kp2,
-                                            pl2.npieces, w.B2);
+                                            pl2.npieces, w.B2, w.done);
     if ((s = launch_gemm<true, kBn2, false>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
   } else {
     if ((s = launch_gemm<false, kBn1, true>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
     k_t_reduce<false><<<rgrid, 256, 0, st>>>(w.P, nsplit, p1.zsplit, kp2 * ldp, ldp, n, c, kp2,
-                                             pl2.npieces, w.B2);
+                                             pl2.npieces, w.B2, w.done);
     if ((s = launch_gemm<false, kBn2, false>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
-  }
-  if (Z == nullptr) {
-    const int64_t tiles = ((m + BM - 1) / BM) * ((n + kBn2 - 1) / kBn2);
-    k_residual_fold<<<1, 1024, 0, st>>>(w.partial, tiles, out3);
   }
   return cuda_ok(cudaGetLastError());
 }

@@ -337,3 +337,10 @@ def test_residual_tensor_cores_fused(prec):
         assert run_status(st) == 0
         o = host(out3)
         assert abs(o[0] - rel_o) < 1e-5 and abs(o[2] - den_o) < 24 * U32 * den_o
+        # a second call on the same workspace folds the same partials in the
+        # same order: bit-identical sums
+        Q.residual(dev(A), out3, dev(out["C"].astype(np.float32)), dev(U32_),
+                   dev(out["R"].astype(np.float32)), prec, None if msk is None else dev(msk),
+                   None, ws, st)
+        assert run_status(st) == 0
+        assert np.array_equal(host(out3), o)
