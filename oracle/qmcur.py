@@ -19,6 +19,9 @@ Steps, in the order of Algorithm 1 (Sec. 3.1):
 * ``residual``        - ||X - Z||_F / ||X||_F (Example 4.2's relative error).
 * ``core_paper``      - the paper's own core C^+ X R^+ (Algorithm 1 step 3), used to
                         check that it equals W^+ when rank(W) = rank(X).
+* ``complete_step``,  - Algorithm 2 (Example 4.4): quaternion matrix completion by
+  ``complete``          repeated QMCUR approximation and re-imposition of the
+                        observed entries, with its relative-change stopping test.
 
 Parity status: every function is pinned by tests/test_oracle_*.py (Hamilton
 table, complex-adjoint homomorphism, Penrose conditions, reduction to
@@ -260,3 +263,59 @@ def qmcur(A, c, r, sampler=SAMPLER_NORM, seed=0, stream_id=0, rcond=1e-10,
     rel, num2, den2 = residual(A, Z)
     return dict(p=p, q=q, F=F, J=J, I=I, C=C, R=R, W=W, U=U, rank=rank,
                 sigma=sigma, Z=Z, rel=rel, num2=num2, den2=den2)
+
+
+# -------------------------------------------------------------- Algorithm 2 -
+def complete_step(X, mask, I, J, rcond=1e-10, rank_cap=0):
+    """One iteration of Algorithm 2 (Example 4.4) with fixed index sets I, J.
+
+    M = C U R is the QMCUR approximation of the current iterate X^t
+    (Algorithm 1 with U = W^+, the truncated inverse of W = X^t(I,J)); then
+    X^{t+1} = P_{Omega^c}(M) + P_Omega(X^t), where P_Omega(X^t) = P_Omega(Y)
+    because every iterate keeps the observed entries.  The stopping quantity
+    is delta = ||X^{t+1} - X^t||_F / ||X^t||_F.
+    Returns (X^{t+1}, delta, num2, den2, rank) with num2 = ||X^{t+1} - X^t||_F^2
+    and den2 = ||X^t||_F^2.
+    """
+    X = as_q(X)
+    obs = np.asarray(mask) != 0
+    C, R, W = gather(X, I, J)
+    U, rank, _ = pinv_truncated(W, rcond, rank_cap)
+    M = reconstruct(C, U, R)
+    Xn = np.where(obs[None], X, M)
+    num2 = fro2(Xn - X)
+    den2 = fro2(X)
+    delta = float(np.sqrt(num2 / den2)) if den2 > 0 else float("nan")
+    return Xn, delta, num2, den2, rank
+
+
+def complete(Y, mask, c, r, sampler=SAMPLER_UNIFORM, seed=0, stream_id=0, rcond=1e-10,
+             rank_cap=0, tol=1e-4, t_max=200, col_p=None, row_p=None):
+    """Algorithm 2: recover the unobserved entries of Y (mask 0) by iterating
+    complete_step from X^0 = P_Omega(Y).
+
+    The index sets are inputs of Algorithm 2; they are drawn once, from the
+    probabilities of X^0 (Algorithm 1 steps 1-2), and kept for every
+    iteration.  Iterations t = 0, 1, ... run until delta_t <= tol or t >= t_max,
+    so at most t_max + 1 of them.  col_p / row_p may replace the probabilities
+    of X^0 (the tests pass the library's, so that index sets agree bit for bit).
+    """
+    Y = as_q(Y)
+    obs = np.asarray(mask) != 0
+    X = np.where(obs[None], Y, 0.0)
+    p, q, _ = probabilities(X, sampler)
+    if col_p is not None:
+        p = np.asarray(col_p, dtype=np.float64)
+    if row_p is not None:
+        q = np.asarray(row_p, dtype=np.float64)
+    J, _ = sample(p, c, seed, stream_id, 0, sampler)
+    I, _ = sample(q, r, seed, stream_id, 1, sampler)
+    history = []
+    t = 0
+    while True:
+        X, delta, _, _, rank = complete_step(X, mask, I, J, rcond, rank_cap)
+        history.append(delta)
+        if delta <= tol or t >= t_max:
+            break
+        t += 1
+    return dict(X=X, I=I, J=J, iters=len(history), history=history, rank=rank)
