@@ -289,30 +289,29 @@ def complete_step(X, mask, I, J, rcond=1e-10, rank_cap=0):
     return Xn, delta, num2, den2, rank
 
 
-def complete(Y, mask, c, r, sampler=SAMPLER_UNIFORM, seed=0, stream_id=0, rcond=1e-10,
-             rank_cap=0, tol=1e-4, t_max=200, col_p=None, row_p=None):
-    """Algorithm 2: recover the unobserved entries of Y (mask 0) by iterating
-    complete_step from X^0 = P_Omega(Y).
+def complete(Y, mask, c, r, sampler=SAMPLER_UNIFORM, seed=0, rcond=1e-10, rank_cap=0,
+             tol=1e-4, t_max=200, probs_hook=None):
+    """Algorithm 2: recover the unobserved entries of Y (mask 0) from
+    X^0 = P_Omega(Y) by iterating Algorithm 1 and complete_step.
 
-    The index sets are inputs of Algorithm 2; they are drawn once, from the
-    probabilities of X^0 (Algorithm 1 steps 1-2), and kept for every
-    iteration.  Iterations t = 0, 1, ... run until delta_t <= tol or t >= t_max,
-    so at most t_max + 1 of them.  col_p / row_p may replace the probabilities
-    of X^0 (the tests pass the library's, so that index sets agree bit for bit).
+    Iteration t runs Algorithm 1 in full on X^t: probabilities of X^t, then
+    J and I drawn with Philox key `seed` and stream_id = t (new index sets at
+    every iteration), then the masked update.  Iterations t = 0, 1, ... run
+    until delta_t <= tol or t >= t_max, so at most t_max + 1 of them.
+    probs_hook(t, X^t) may return (p, q) to replace the probabilities (the
+    tests pass the library's, so that index sets agree bit for bit).
     """
     Y = as_q(Y)
     obs = np.asarray(mask) != 0
     X = np.where(obs[None], Y, 0.0)
-    p, q, _ = probabilities(X, sampler)
-    if col_p is not None:
-        p = np.asarray(col_p, dtype=np.float64)
-    if row_p is not None:
-        q = np.asarray(row_p, dtype=np.float64)
-    J, _ = sample(p, c, seed, stream_id, 0, sampler)
-    I, _ = sample(q, r, seed, stream_id, 1, sampler)
     history = []
     t = 0
     while True:
+        p, q, _ = probabilities(X, sampler)
+        if probs_hook is not None:
+            p, q = probs_hook(t, X)
+        J, _ = sample(p, c, seed, t, 0, sampler)
+        I, _ = sample(q, r, seed, t, 1, sampler)
         X, delta, _, _, rank = complete_step(X, mask, I, J, rcond, rank_cap)
         history.append(delta)
         if delta <= tol or t >= t_max:

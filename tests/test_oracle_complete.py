@@ -104,7 +104,7 @@ def test_recovers_missing_entries_of_an_exactly_low_rank_matrix():
     m, n, k = 60, 80, 3
     Xt, _ = synth.lowrank_gaussian(m, n, k, seed=15, dtype=np.float64)
     mask = synth.bernoulli_mask(m, n, seed=16, p_observed=0.6)
-    out = O.complete(Xt, mask, 30, 30, sampler=O.SAMPLER_UNIFORM, seed=17, rank_cap=k,
+    out = O.complete(Xt, mask, 12, 12, sampler=O.SAMPLER_UNIFORM, seed=17, rank_cap=k,
                      tol=1e-12, t_max=400)
     miss = mask == 0
     err = np.linalg.norm((out["X"] - Xt)[:, miss]) / np.linalg.norm(Xt[:, miss])
