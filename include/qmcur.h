@@ -289,6 +289,42 @@ qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qm
                              void* workspace, size_t ws_bytes, int32_t* dev_status,
                              cudaStream_t stream);
 
+/*
+ * qmcur_complete_step - one iteration of Algorithm 2 (Example 4.4, quaternion
+ * matrix completion from the observed entries Omega).  Iteration t runs
+ * Algorithm 1 in full on the current iterate X^t and then re-imposes the
+ * observed entries:
+ *   col_p, row_p = the probabilities of X^t (opts->sampler, as qmcur_probs);
+ *   J, I drawn as qmcur_sample with key opts->seed and opts->stream_id (pass
+ *   stream_id = t: every iteration draws new index sets);
+ *   C = X^t(:,J), R = X^t(I,:), W = X^t(I,J); U = W^+ truncated by
+ *   opts->rcond / opts->rank_cap through opts->pinv_method;
+ *   M = C (U R), and in place X^{t+1} = P_{Omega^c}(M) + P_Omega(X^t).
+ * The observed entries of X are never written, so from X^0 = P_Omega(Y)
+ * every iterate keeps Y's observed values.  M is never stored: the update
+ * happens in the epilogue of the product C (U R).
+ *   X        m x n, updated in place (F32 for the tensor-core precisions and
+ *            QMCUR_PREC_FP32, F64 for QMCUR_PREC_FP64).
+ *   mask     device uint8 m x n (row stride n), nonzero = observed; NULL
+ *            means every entry is observed (X does not change).
+ *   col_p[n], row_p[m], J[c], I[r], C (m x c), R (r x n), W (r x c, F64),
+ *            U (c x r, F64): caller-owned device buffers that receive the
+ *            iteration's probabilities, index sets and factors, as in
+ *            qmcur_decompose; C and R must not alias X.
+ *   rank_out device int32[2] or NULL, as in qmcur_pinv_core.
+ *   out3     device double[3]: {delta, ||X^{t+1} - X^t||_F^2, ||X^t||_F^2},
+ *            delta = Algorithm 2's relative change; stop when delta <= 1e-4
+ *            or t >= t_max.  Sums are reduced in a fixed order.
+ *   Requires 1 <= c <= n, 1 <= r <= m.
+ *   Device errors: those of qmcur_probs, qmcur_sample, qmcur_pinv_core;
+ *   TIMEOUT.
+ */
+qmcur_status qmcur_complete_step(qmcur_qmat* X, const uint8_t* mask, int64_t c, int64_t r,
+                                 const qmcur_opts* opts, double* col_p, double* row_p, int32_t* J,
+                                 int32_t* I, qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W,
+                                 qmcur_qmat* U, int32_t* rank_out, double* out3, void* workspace,
+                                 size_t ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * Batched QMCUR: many independent problems of uneven shapes.
  *

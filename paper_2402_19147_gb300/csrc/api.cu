@@ -8,7 +8,8 @@ namespace qmcur {
 size_t simt_partials(int64_t m, int64_t n);
 size_t residual_partials(int64_t m, int64_t n);
 qmcur_status launch_qgemm_simt(const QView& X, const QView& Y, const QView* Z, const QView* A,
-                               const uint8_t* mask, double* partial, bool fp64, cudaStream_t st);
+                               const uint8_t* mask, double* partial, bool fp64, cudaStream_t st,
+                               bool complete);
 __global__ void k_residual_fold(const double* partial, int64_t count, double* out3);
 
 // Subspace pseudo-inverse (pinv_fast.cu).
@@ -32,7 +33,7 @@ size_t tc_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec);
 qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
                                    int32_t prec, qmcur_qmat* Z, const qmcur_qmat* A,
                                    const uint8_t* mask, double* out3, void* ws, size_t ws_bytes,
-                                   int32_t* dev_status, cudaStream_t st);
+                                   int32_t* dev_status, cudaStream_t st, bool complete);
 
 size_t gemm_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec) {
   if (prec == QMCUR_PREC_FP64 || prec == QMCUR_PREC_FP32) {
@@ -48,8 +49,9 @@ size_t gemm_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec) {
 qmcur_status launch_reconstruct(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
                                 int32_t prec, qmcur_qmat* Z, const qmcur_qmat* A,
                                 const uint8_t* mask, double* out3, void* ws, size_t ws_bytes,
-                                int32_t* dev_status, cudaStream_t st) {
+                                int32_t* dev_status, cudaStream_t st, bool complete) {
   if (!valid_qmat(C) || !valid_qmat(U) || !valid_qmat(R)) return QMCUR_ERR_INVALID_ARG;
+  if (complete && (Z != nullptr || A == nullptr || out3 == nullptr)) return QMCUR_ERR_INVALID_ARG;
   const int64_t m = C->rows, c = C->cols, r = R->rows, n = R->cols;
   if (U->rows != c || U->cols != r || m < 1 || n < 1 || c < 1 || r < 1) return QMCUR_ERR_INVALID_ARG;
   if (Z != nullptr && (!valid_qmat(Z) || Z->rows != m || Z->cols != n)) return QMCUR_ERR_INVALID_ARG;
@@ -71,21 +73,23 @@ qmcur_status launch_reconstruct(const qmcur_qmat* C, const qmcur_qmat* U, const 
     for (int t = 0; t < 4; ++t) T.p[t] = tbuf + (size_t)t * c * n * es;
     T.rows = c; T.cols = n; T.ld = n; T.dtype = fp64 ? QMCUR_F64 : QMCUR_F32;
     QView vU = view(U), vR = view(R), vC = view(C);
-    qmcur_status s = launch_qgemm_simt(vU, vR, &T, nullptr, nullptr, nullptr, fp64, st);
+    qmcur_status s = launch_qgemm_simt(vU, vR, &T, nullptr, nullptr, nullptr, fp64, st, false);
     if (s != QMCUR_OK) return s;
     if (Z != nullptr) {
       QView vZ = view(Z);
-      return launch_qgemm_simt(vC, T, &vZ, nullptr, nullptr, nullptr, fp64, st);
+      return launch_qgemm_simt(vC, T, &vZ, nullptr, nullptr, nullptr, fp64, st, false);
     }
     QView vA = view(A);
-    s = launch_qgemm_simt(vC, T, nullptr, &vA, mask, partial, fp64, st);
+    if (complete && fp64 && A->dtype != QMCUR_F64) return QMCUR_ERR_INVALID_ARG;
+    s = launch_qgemm_simt(vC, T, complete ? &vA : nullptr, &vA, mask, partial, fp64, st, complete);
     if (s != QMCUR_OK) return s;
     k_residual_fold<<<1, 1024, 0, st>>>(partial, (int64_t)p1, out3);
     return cuda_ok(cudaGetLastError());
   }
   if (prec == QMCUR_PREC_TF32X3 || prec == QMCUR_PREC_BF16X3 || prec == QMCUR_PREC_BF16X6 ||
       prec == QMCUR_PREC_BF16_MIXED)
-    return launch_reconstruct_tc(C, U, R, prec, Z, A, mask, out3, ws, ws_bytes, dev_status, st);
+    return launch_reconstruct_tc(C, U, R, prec, Z, A, mask, out3, ws, ws_bytes, dev_status, st,
+                                 complete);
   return QMCUR_ERR_INVALID_ARG;
 }
 
@@ -220,6 +224,28 @@ qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qm
   if (s != QMCUR_OK) return s;
   return launch_reconstruct(C, U, R, o->prec, nullptr, A, nullptr, out3, workspace, ws_bytes,
                             dev_status, stream);
+}
+
+qmcur_status qmcur_complete_step(qmcur_qmat* X, const uint8_t* mask, int64_t c, int64_t r,
+                                 const qmcur_opts* o, double* col_p, double* row_p, int32_t* J,
+                                 int32_t* I, qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W,
+                                 qmcur_qmat* U, int32_t* rank_out, double* out3, void* workspace,
+                                 size_t ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  if (X == nullptr || o == nullptr || C == nullptr || R == nullptr || W == nullptr ||
+      U == nullptr || out3 == nullptr || !valid_qmat(X))
+    return QMCUR_ERR_INVALID_ARG;
+  if (C->plane[0] == X->plane[0] || R->plane[0] == X->plane[0]) return QMCUR_ERR_INVALID_ARG;
+  qmcur_status s = launch_probs(X, o->sampler, col_p, row_p, nullptr, workspace, ws_bytes,
+                                dev_status, stream);
+  if (s != QMCUR_OK) return s;
+  s = launch_sample(X, o->sampler, col_p, row_p, c, r, o->seed, o->stream_id, o->max_attempts, J,
+                    I, C, R, W, workspace, ws_bytes, dev_status, stream);
+  if (s != QMCUR_OK) return s;
+  s = pinv_dispatch(W, o->pinv_method, o->rcond, o->rank_cap, o->max_sweeps, U, rank_out, nullptr,
+                    workspace, ws_bytes, dev_status, stream);
+  if (s != QMCUR_OK) return s;
+  return launch_reconstruct(C, U, R, o->prec, nullptr, X, mask, out3, workspace, ws_bytes,
+                            dev_status, stream, true);
 }
 
 }  // extern "C"

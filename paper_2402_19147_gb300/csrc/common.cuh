@@ -148,11 +148,12 @@ qmcur_status launch_pinv(const qmcur_qmat* W, double rcond, int32_t rank_cap, in
                          qmcur_qmat* U, int32_t* rank_out, double* sigma_out, void* ws,
                          size_t ws_bytes, int32_t* dev_status, cudaStream_t st);
 // Z = C (U R); if Z == nullptr the product is not written and, with A != nullptr,
-// the residual sums are formed instead (fused epilogue).
+// the residual sums are formed instead (fused epilogue).  With `complete`, A is
+// the iterate of a masked completion step (Algorithm 2) and is updated in place.
 qmcur_status launch_reconstruct(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
                                 int32_t prec, qmcur_qmat* Z, const qmcur_qmat* A,
                                 const uint8_t* mask, double* out3, void* ws, size_t ws_bytes,
-                                int32_t* dev_status, cudaStream_t st);
+                                int32_t* dev_status, cudaStream_t st, bool complete = false);
 qmcur_status launch_residual_standalone(const qmcur_qmat* A, const qmcur_qmat* Z,
                                         const uint8_t* mask, double* out3, void* ws,
                                         size_t ws_bytes, int32_t* dev_status, cudaStream_t st);

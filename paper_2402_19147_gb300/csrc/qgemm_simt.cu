@@ -12,7 +12,10 @@
 // MODE_STORE writes Z.  MODE_RESIDUAL never writes Z: the epilogue reads the
 // matching tile of A and accumulates sum |a - z|^2 and sum |a|^2 (optionally
 // over the observed set Omega of a mask) into one FP64 pair per CTA, folded
-// afterwards in a fixed order.
+// afterwards in a fixed order.  MODE_COMPLETE is one step of masked
+// completion (Algorithm 2): A is the iterate, its unobserved entries (mask 0)
+// are overwritten in place by Z (the Z view aliases A), and the pair is
+// {sum over unobserved of |z - a|^2, sum over all of |a|^2}.
 #include "common.cuh"
 
 namespace qmcur {
@@ -20,7 +23,7 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4, kGemmThreads = 256;
 
-enum { MODE_STORE = 0, MODE_RESIDUAL = 1 };
+enum { MODE_STORE = 0, MODE_RESIDUAL = 1, MODE_COMPLETE = 2 };
 
 template <typename T>
 struct QAcc { T v[4]; };
@@ -115,6 +118,46 @@ k_qgemm_simt(QView X, QView Y, QView Z, QView A, const uint8_t* __restrict__ mas
 #pragma unroll
           for (int t = 0; t < 4; ++t) st_from_double(Z, t, gi, gj, (double)acc[i][j][t]);
       }
+  } else if constexpr (MODE == MODE_COMPLETE) {
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      T rn = T(0), rd = T(0);
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int64_t gi = m0 + ty * TM + i, gj = n0 + tx * TN + j;
+        if (gi < M && gj < N) {
+          const bool observed = mask == nullptr || mask[gi * N + gj] != 0;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const T av = (T)ld_as_double(A, t, gi, gj);
+            rd = fma(av, av, rd);
+            if (!observed) {
+              const T d = acc[i][j][t] - av;
+              rn = fma(d, d, rn);
+            }
+          }
+          if (!observed)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) st_from_double(Z, t, gi, gj, (double)acc[i][j][t]);
+        }
+      }
+      num += (double)rn;
+      den += (double)rd;
+    }
+    __shared__ double redc[2][kGemmThreads];
+    redc[0][tid] = num;
+    redc[1][tid] = den;
+    __syncthreads();
+    for (int w = kGemmThreads / 2; w > 0; w >>= 1) {
+      if (tid < w) { redc[0][tid] += redc[0][tid + w]; redc[1][tid] += redc[1][tid + w]; }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      const int64_t cta = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+      partial[2 * cta] = redc[0][0];
+      partial[2 * cta + 1] = redc[1][0];
+    }
   } else {
     double num = 0.0, den = 0.0;
 #pragma unroll
@@ -234,9 +277,12 @@ size_t residual_partials(int64_t m, int64_t n) {
   return (size_t)(((m + 31) / 32) * ((n + 255) / 256));
 }
 
-// X (M x K) times Y (K x N) -> Z or fused residual against A.
+// X (M x K) times Y (K x N) -> Z, or the fused residual against A, or (complete)
+// one masked completion step of A in place (Z must then view A's planes).
 qmcur_status launch_qgemm_simt(const QView& X, const QView& Y, const QView* Z, const QView* A,
-                               const uint8_t* mask, double* partial, bool fp64, cudaStream_t st) {
+                               const uint8_t* mask, double* partial, bool fp64, cudaStream_t st,
+                               bool complete) {
+  if (complete && (Z == nullptr || A == nullptr)) return QMCUR_ERR_INVALID_ARG;
   const int64_t M = X.rows, N = Y.cols;
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
   if (grid.y > 65535) return QMCUR_ERR_UNSUPPORTED;
@@ -244,6 +290,17 @@ qmcur_status launch_qgemm_simt(const QView& X, const QView& Y, const QView* Z, c
   const QView& z = Z ? *Z : dummy;
   const QView& a = A ? *A : dummy;
   const bool xd = X.dtype == QMCUR_F64, yd = Y.dtype == QMCUR_F64;
+  if (complete) {
+    if (fp64) {
+      if (!xd || !yd) return QMCUR_ERR_INVALID_ARG;
+      k_qgemm_simt<double, double, double, MODE_COMPLETE><<<grid, kGemmThreads, 0, st>>>(X, Y, z, a, mask, partial);
+    } else {
+      if (yd) return QMCUR_ERR_INVALID_ARG;
+      if (xd) k_qgemm_simt<double, float, float, MODE_COMPLETE><<<grid, kGemmThreads, 0, st>>>(X, Y, z, a, mask, partial);
+      else k_qgemm_simt<float, float, float, MODE_COMPLETE><<<grid, kGemmThreads, 0, st>>>(X, Y, z, a, mask, partial);
+    }
+    return cuda_ok(cudaGetLastError());
+  }
   if (fp64) {
     if (!xd || !yd) return QMCUR_ERR_INVALID_ARG;
     if (Z) k_qgemm_simt<double, double, double, MODE_STORE><<<grid, kGemmThreads, 0, st>>>(X, Y, z, a, mask, partial);

@@ -82,7 +82,11 @@ constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 // MODE_STORE_ZT stores the tile transposed, z[t][col][row] with ldz between
 // columns: the lanes of a warp hold consecutive rows, so each store of one
 // column is one contiguous 128-byte line.
-enum { MODE_STORE_Z = 0, MODE_RESIDUAL = 1, MODE_STORE_ZT = 2 };
+// MODE_COMPLETE is one step of masked completion (Algorithm 2): A is the
+// iterate X^t, and each unobserved entry (mask 0) is overwritten in place by
+// z, while the sums are sum over unobserved entries of |z - a|^2 and sum over
+// all entries of |a|^2 (the stopping test's ||X^{t+1} - X^t||^2 and ||X^t||^2).
+enum { MODE_STORE_Z = 0, MODE_RESIDUAL = 1, MODE_STORE_ZT = 2, MODE_COMPLETE = 3 };
 
 struct TcParams {
   int M, N;
@@ -410,12 +414,14 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
       const int n0 = nt * BN;
       // the residual's first A chunk is fetched while the MMAs still run
       float4 anext[4][4];
-      if (p.mode == MODE_RESIDUAL) load_a(anext, row, n0 + 16 * half);
+      const bool sums = p.mode == MODE_RESIDUAL || p.mode == MODE_COMPLETE;
+      if (sums) load_a(anext, row, n0 + 16 * half);
       if (!mbar_wait(&tfull[a], aph, abort_flag)) break;
       tc_fence_after();
       const uint32_t tb = tmem_base + (uint32_t)(a * ACC_COLS) + ((uint32_t)(sp * 32) << 16);
       double dsum = 0.0, asum = 0.0;
-      if (p.mode == MODE_RESIDUAL) {
+      if (sums) {
+        const bool cmpl = p.mode == MODE_COMPLETE;
 #pragma unroll 1
         for (int ch = half; ch < BN / 16; ch += 2) {
           const int c0 = n0 + ch * 16;
@@ -427,16 +433,23 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
           if (ch + 2 < BN / 16) load_a(anext, row, c0 + 32);   // this warp's next chunk in flight
           const bool in_row = row < p.M;
           const bool full16 = p.a_vec && c0 + 16 <= p.N;
-          unsigned keep = 0xffffu;   // columns of the chunk that count
-          if (!full16 || p.mask != nullptr) {
-            keep = 0;
+          // inb: columns inside Z; obs: observed (mask nonzero, or no mask).
+          // RESIDUAL sums both norms over inb & obs; COMPLETE sums the change
+          // over inb & ~obs and |a|^2 over inb.
+          unsigned inb = 0xffffu, obs = 0xffffu;
+          if (!full16 || !in_row) {
+            inb = 0;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const bool ok = in_row && c0 + j < p.N &&
-                              (p.mask == nullptr || p.mask[(int64_t)row * p.N + c0 + j] != 0);
-              keep |= (ok ? 1u : 0u) << j;
-            }
+            for (int j = 0; j < 16; ++j) inb |= ((in_row && c0 + j < p.N) ? 1u : 0u) << j;
           }
+          if (p.mask != nullptr) {
+            obs = 0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              obs |= (((inb >> j) & 1u) && p.mask[(int64_t)row * p.N + c0 + j] != 0 ? 1u : 0u) << j;
+          }
+          const unsigned wnum = cmpl ? (inb & ~obs) : (inb & obs);
+          const unsigned wden = cmpl ? inb : (inb & obs);
           float sd = 0.f, sa2 = 0.f;
 #pragma unroll
           for (int pl = 0; pl < 4; ++pl) {
@@ -445,10 +458,27 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
             const float* avf = reinterpret_cast<const float*>(av[pl]);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-              const float w = ((keep >> j) & 1u) ? 1.f : 0.f;
-              const float d = (avf[j] - z[j]) * w;
+              const float wn = ((wnum >> j) & 1u) ? 1.f : 0.f;
+              const float wd = ((wden >> j) & 1u) ? 1.f : 0.f;
+              const float d = (avf[j] - z[j]) * wn;
               sd = fmaf(d, d, sd);
-              sa2 = fmaf(avf[j] * w, avf[j], sa2);
+              sa2 = fmaf(avf[j] * wd, avf[j], sa2);
+            }
+            if (cmpl && in_row) {
+              // X^{t+1}: the observed entries keep a, the others take z
+              float* xr = p.z[pl] + (int64_t)row * p.ldz + c0;
+              float v[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) v[j] = ((obs >> j) & 1u) ? avf[j] : z[j];
+              if (full16 && p.z_vec) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  reinterpret_cast<float4*>(xr)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+              } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                  if ((inb >> j) & 1u) xr[j] = v[j];
+              }
             }
           }
           if (in_row) { dsum += (double)sd; asum += (double)sa2; }
@@ -486,7 +516,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
       }
       tc_fence_before();
       if (lane == 0) mbar_arrive(&tempty[a]);
-      if (p.mode == MODE_RESIDUAL) {
+      if (sums) {
         // fixed-order reduction: warp tree, then the eight warps in order
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -514,7 +544,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
                  : "memory");
   }
   if (threadIdx.x == 0 && *abort_flag) set_status(p.status, QMCUR_ERR_TIMEOUT);
-  if (p.mode == MODE_RESIDUAL && p.done != nullptr) {
+  if ((p.mode == MODE_RESIDUAL || p.mode == MODE_COMPLETE) && p.done != nullptr) {
     // The last CTA to finish folds the per-item partials into out3 in a fixed
     // order: strided sums, a shuffle tree per warp, then the warps in order.
     __shared__ int s_last;
@@ -916,7 +946,7 @@ size_t tc_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec) {
 qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
                                    int32_t prec, qmcur_qmat* Z, const qmcur_qmat* A,
                                    const uint8_t* mask, double* out3, void* ws, size_t ws_bytes,
-                                   int32_t* dev_status, cudaStream_t st) {
+                                   int32_t* dev_status, cudaStream_t st, bool complete) {
   const int64_t m = C->rows, c = C->cols, r = R->rows, n = R->cols;
   if (C->dtype != QMCUR_F32 || R->dtype != QMCUR_F32) return QMCUR_ERR_INVALID_ARG;
   if (Z != nullptr && Z->dtype != QMCUR_F32) return QMCUR_ERR_INVALID_ARG;
@@ -980,12 +1010,17 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
     for (int t = 0; t < 4; ++t)
       p2.z_vec = p2.z_vec && reinterpret_cast<uintptr_t>(Z->plane[t]) % 16 == 0;
   } else {
-    p2.mode = MODE_RESIDUAL;
+    p2.mode = complete ? MODE_COMPLETE : MODE_RESIDUAL;
     for (int t = 0; t < 4; ++t) p2.a[t] = reinterpret_cast<const float*>(A->plane[t]);
     p2.lda = A->ld;
     p2.a_vec = A->ld % 4 == 0;
     for (int t = 0; t < 4; ++t)
       p2.a_vec = p2.a_vec && reinterpret_cast<uintptr_t>(A->plane[t]) % 16 == 0;
+    if (complete) {   // the iterate is updated in place
+      for (int t = 0; t < 4; ++t) p2.z[t] = reinterpret_cast<float*>(A->plane[t]);
+      p2.ldz = A->ld;
+      p2.z_vec = p2.a_vec;
+    }
     p2.mask = mask;
     p2.partial = w.partial;
     p2.out3 = out3;

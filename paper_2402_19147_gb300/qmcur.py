@@ -78,6 +78,8 @@ SIGNATURES = {
     "qmcur_batch_destroy": (None, [_P]),
     "qmcur_decompose": (_I32, [_QP, _I64, _I64, ctypes.POINTER(Opts), _P, _P, _P, _P,
                                _QP, _QP, _QP, _QP, _P, _P, _P, _P, _SZ, _P, _P]),
+    "qmcur_complete_step": (_I32, [_QP, _P, _I64, _I64, ctypes.POINTER(Opts), _P, _P, _P, _P,
+                                   _QP, _QP, _QP, _QP, _P, _P, _P, _SZ, _P, _P]),
 }
 
 
@@ -330,6 +332,64 @@ def decompose(A, D, sampler=SAMPLER_NORM, seed=0, stream_id=0, rcond=1e-10, rank
                                  _ptr(D.rank), _ptr(D.sigma), _ptr(D.out3), _ptr(D.ws),
                                  D.ws.numel(), _ptr(D.status), _stream(stream)),
            "qmcur_decompose")
+
+
+class Completion:
+    """Device buffers of Algorithm 2 (quaternion matrix completion) on an
+    m x n iterate with c columns and r rows per iteration: the probabilities,
+    index sets and factors of the last iteration, and out3 = {delta, ||dX||^2,
+    ||X||^2}."""
+
+    def __init__(self, m, n, c, r, prec, dtype=torch.float32, device="cuda"):
+        self.m, self.n, self.c, self.r, self.prec = m, n, c, r, prec
+        f = dict(device=device)
+        self.col_p = torch.empty(n, dtype=torch.float64, **f)
+        self.row_p = torch.empty(m, dtype=torch.float64, **f)
+        self.J = torch.empty(c, dtype=torch.int32, **f)
+        self.I = torch.empty(r, dtype=torch.int32, **f)
+        self.C = torch.empty(4, m, c, dtype=dtype, **f)
+        self.R = torch.empty(4, r, n, dtype=dtype, **f)
+        self.W = torch.empty(4, r, c, dtype=torch.float64, **f)
+        self.U = torch.empty(4, c, r, dtype=torch.float64, **f)
+        self.rank = torch.zeros(2, dtype=torch.int32, **f)
+        self.out3 = torch.empty(3, dtype=torch.float64, **f)
+        self.status = torch.zeros(1, dtype=torch.int32, **f)
+        self.ws = workspace(m, n, c, r, prec, device)
+
+
+def complete_step(X, mask, S, t, sampler=SAMPLER_UNIFORM, seed=0, rcond=1e-10, rank_cap=0,
+                  max_sweeps=0, pinv_method=PINV_SUBSPACE_FP32, stream=None):
+    """Iteration t of Algorithm 2 on X in place (qmcur_complete_step) with the
+    buffers of the Completion S; S.out3[0] is the stopping test's relative
+    change."""
+    o = Opts(sampler, S.prec, seed, t, 0, rcond, rank_cap, max_sweeps, pinv_method, 0)
+    _check(lib().qmcur_complete_step(_ref(qmat(X)), _ptr(mask), S.c, S.r, ctypes.byref(o),
+                                     _ptr(S.col_p), _ptr(S.row_p), _ptr(S.J), _ptr(S.I),
+                                     _ref(qmat(S.C)), _ref(qmat(S.R)), _ref(qmat(S.W)),
+                                     _ref(qmat(S.U)), _ptr(S.rank), _ptr(S.out3), _ptr(S.ws),
+                                     S.ws.numel(), _ptr(S.status), _stream(stream)),
+           "qmcur_complete_step")
+
+
+def complete(Y, mask, c, r, rank_cap, prec=PREC_BF16_MIXED, sampler=SAMPLER_UNIFORM, seed=0,
+             rcond=1e-10, tol=1e-4, t_max=200, pinv_method=PINV_SUBSPACE_FP32, stream=None):
+    """Algorithm 2 from X^0 = P_Omega(Y): complete_step for t = 0, 1, ... until
+    delta <= tol or t >= t_max.  The loop reads delta back after each
+    iteration (one 8-byte device-to-host copy).  Returns (X, S, history)."""
+    m, n = Y.shape[1], Y.shape[2]
+    S = Completion(m, n, c, r, prec, Y.dtype, Y.device)
+    X = torch.where(mask.bool().unsqueeze(0), Y, torch.zeros((), dtype=Y.dtype, device=Y.device))
+    history = []
+    t = 0
+    while True:
+        complete_step(X, mask, S, t, sampler, seed, rcond, rank_cap, 0, pinv_method, stream)
+        delta = float(S.out3[0].item())
+        check_status(S.status, "complete")
+        history.append(delta)
+        if delta <= tol or t >= t_max:
+            break
+        t += 1
+    return X, S, history
 
 
 def check_status(status, where="device"):

@@ -139,7 +139,7 @@ def perturb_off_intersection(X, I, J, rel, seed):
     return np.ascontiguousarray((X + noise * keep).astype(X.dtype))
 
 
-# The five workloads, by what they are.  `scale` shrinks a workload for tests.
+# The workloads, by what they are.  `scale` shrinks a workload for tests.
 WORKLOADS = {
     "gauss256_rank10_fp64": dict(kind="lowrank", m=256, n=256, rank=10, seed=0,
                                  noise_rel=0.0, dtype="f64", c=40, r=40,
@@ -157,6 +157,14 @@ WORKLOADS = {
                                          c=120, r=120, sampler="uniform", rank_cap=60,
                                          rcond=1e-10, mask_seed=5, perturb_rel=1e-2,
                                          perturb_seed=6),
+    # Algorithm 2 (Example 4.4) on a Kodak-sized (512 x 768) colour field:
+    # 10 distinct modes per channel plus the 0.5 offset, no clipping, so the
+    # quaternion rank is exactly 31; 70% of the pixels missing (MR = 70%).
+    "color512x768_rank31_mr70": dict(kind="smooth", m=512, n=768, modes=10, seed=7,
+                                     offset=0.5, clip=False, dtype="f32", distinct=True,
+                                     max_freq=64, bounded_amp=True, c=124, r=124,
+                                     sampler="uniform", rank_cap=31, rcond=1e-10, mask_seed=8,
+                                     p_observed=0.3, tol=1e-4, t_max=200),
 }
 
 
