@@ -17,8 +17,9 @@ Steps, in the order of Algorithm 1 (Sec. 3.1):
                         SVD of its complex adjoint, truncated at rcond and rank_cap.
 * ``reconstruct``     - Z = C (U R) (Eq. 1, Algorithm 1 output).
 * ``residual``        - ||X - Z||_F / ||X||_F (Example 4.2's relative error).
-* ``core_paper``      - the paper's own core C^+ X R^+ (Algorithm 1 step 3), used to
-                        check that it equals W^+ when rank(W) = rank(X).
+* ``core_paper``      - the paper's own core C^+ X R^+ (Algorithm 1 step 3), with
+                        C^+ and R^+ truncated by the rule of W^+; it equals W^+
+                        when rank(W) = rank(X).
 * ``complete_step``,  - Algorithm 2 (Example 4.4): quaternion matrix completion by
   ``complete``          repeated QMCUR approximation and re-imposition of the
                         observed entries, with its relative-change stopping test.
@@ -206,11 +207,6 @@ def pinv_truncated(W, rcond=1e-10, rank_cap=0):
     return from_complex_adjoint(Xp), k, sq.copy()
 
 
-def pinv_plain(W):
-    """Untruncated-by-cap pseudo-inverse with a tiny relative cut (for C^+, R^+)."""
-    return pinv_truncated(W, rcond=1e-13, rank_cap=0)[0]
-
-
 # ----------------------------------------------------------------- Eq. (1) -
 def reconstruct(C, U, R):
     """Z = C (U R) (Eq. 1), right product first as the library does."""
@@ -235,9 +231,16 @@ def residual(A, Z, mask=None):
     return float(np.sqrt(num2 / den2)) if den2 > 0 else float("nan"), num2, den2
 
 
-def core_paper(A, C, R):
-    """The paper's core U = C^+ X R^+ (Algorithm 1 step 3, Eq. 2)."""
-    return qmatmul(qmatmul(pinv_plain(C), as_q(A)), pinv_plain(R))
+def core_paper(A, C, R, rcond=1e-13, rank_cap=0):
+    """The paper's core U = C^+ X R^+ (Algorithm 1 step 3).
+
+    C^+ and R^+ are truncated by the same rule as W^+ (pinv_truncated: keep
+    sigma_i > rcond * sigma_1, at most rank_cap of them); the defaults keep
+    every numerically nonzero singular value, i.e. the plain C^+ X R^+.
+    """
+    Cp = pinv_truncated(C, rcond, rank_cap)[0]
+    Rp = pinv_truncated(R, rcond, rank_cap)[0]
+    return qmatmul(qmatmul(Cp, as_q(A)), Rp)
 
 
 # -------------------------------------------------------------- Algorithm 1 -
