@@ -290,6 +290,27 @@ qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qm
                              cudaStream_t stream);
 
 /*
+ * qmcur_core_paper - the paper's own core U = C^+ X R^+ (Algorithm 1 step 3),
+ * the least-squares core: no U gives a smaller ||X - C U R||_F.  It equals
+ * W^+ of the intersection when rank(W) = rank(X) (Lemma 1), and is the
+ * steadier choice on noisy data.
+ *   C^+ and R^+ are truncated like W^+ in qmcur_pinv_core (method, rcond,
+ *   rank_cap; the subspace method needs rank_cap >= 1 and k <= 100), then
+ *   U = C^+ (X R^+) is formed at precision prec as in qmcur_reconstruct.
+ *   X  m x n input; C m x c, R r x n (F32, e.g. from qmcur_sample).
+ *   Cp c x m and Rp n x r: caller-owned buffers that receive C^+ and R^+
+ *   (F32; F64 allowed with QMCUR_PREC_FP64).
+ *   U  c x r output (F32; F64 with QMCUR_PREC_FP64).
+ *   Workspace: qmcur_core_paper_workspace_size(m, n, c, r, prec).
+ *   Device errors: those of qmcur_pinv_core; TIMEOUT.
+ */
+size_t qmcur_core_paper_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec);
+qmcur_status qmcur_core_paper(const qmcur_qmat* X, const qmcur_qmat* C, const qmcur_qmat* R,
+                              int32_t method, double rcond, int32_t rank_cap, int32_t prec,
+                              qmcur_qmat* Cp, qmcur_qmat* Rp, qmcur_qmat* U, void* workspace,
+                              size_t ws_bytes, int32_t* dev_status, cudaStream_t stream);
+
+/*
  * qmcur_complete_step - one iteration of Algorithm 2 (Example 4.4, quaternion
  * matrix completion from the observed entries Omega).  Iteration t runs
  * Algorithm 1 in full on the current iterate X^t and then re-imposes the

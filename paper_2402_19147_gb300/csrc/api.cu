@@ -226,6 +226,47 @@ qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qm
                             dev_status, stream);
 }
 
+size_t qmcur_core_paper_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r,
+                                       int32_t prec) {
+  if (m < 1 || n < 1 || c < 1 || r < 1) return 0;
+  // C^+ of the m x c C and R^+ of the r x n R by either method, then the
+  // product C^+ (X R^+): a reconstruction with m' = c, n' = r, c' = m, r' = n
+  const int64_t kc = (m < c ? m : c) < kSmallCholMax ? (m < c ? m : c) : kSmallCholMax;
+  const int64_t kr = (r < n ? r : n) < kSmallCholMax ? (r < n ? r : n) : kSmallCholMax;
+  size_t s = pinv_ws_bytes(m, c);
+  const size_t s2 = pinv_ws_bytes(r, n), s3 = pinv_fast_ws_bytes(m, c, kc),
+               s4 = pinv_fast_ws_bytes(r, n, kr), s5 = gemm_ws_bytes(c, r, m, n, prec);
+  if (s2 > s) s = s2;
+  if (s3 > s) s = s3;
+  if (s4 > s) s = s4;
+  if (s5 > s) s = s5;
+  return s + 256;
+}
+
+qmcur_status qmcur_core_paper(const qmcur_qmat* X, const qmcur_qmat* C, const qmcur_qmat* R,
+                              int32_t method, double rcond, int32_t rank_cap, int32_t prec,
+                              qmcur_qmat* Cp, qmcur_qmat* Rp, qmcur_qmat* U, void* workspace,
+                              size_t ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  if (!valid_qmat(X) || !valid_qmat(C) || !valid_qmat(R) || !valid_qmat(Cp) || !valid_qmat(Rp) ||
+      !valid_qmat(U))
+    return QMCUR_ERR_INVALID_ARG;
+  const int64_t m = X->rows, n = X->cols, c = C->cols, r = R->rows;
+  if (C->rows != m || R->cols != n || Cp->rows != c || Cp->cols != m || Rp->rows != n ||
+      Rp->cols != r || U->rows != c || U->cols != r)
+    return QMCUR_ERR_INVALID_ARG;
+  if (Cp->dtype != QMCUR_F32 || Rp->dtype != QMCUR_F32 || U->dtype != QMCUR_F32) {
+    if (prec != QMCUR_PREC_FP64) return QMCUR_ERR_INVALID_ARG;
+  }
+  qmcur_status s = pinv_dispatch(C, method, rcond, rank_cap, 0, Cp, nullptr, nullptr, workspace,
+                                 ws_bytes, dev_status, stream);
+  if (s != QMCUR_OK) return s;
+  s = pinv_dispatch(R, method, rcond, rank_cap, 0, Rp, nullptr, nullptr, workspace, ws_bytes,
+                    dev_status, stream);
+  if (s != QMCUR_OK) return s;
+  return launch_reconstruct(Cp, X, Rp, prec, U, nullptr, nullptr, nullptr, workspace, ws_bytes,
+                            dev_status, stream);
+}
+
 qmcur_status qmcur_complete_step(qmcur_qmat* X, const uint8_t* mask, int64_t c, int64_t r,
                                  const qmcur_opts* o, double* col_p, double* row_p, int32_t* J,
                                  int32_t* I, qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W,

@@ -78,6 +78,9 @@ SIGNATURES = {
     "qmcur_batch_destroy": (None, [_P]),
     "qmcur_decompose": (_I32, [_QP, _I64, _I64, ctypes.POINTER(Opts), _P, _P, _P, _P,
                                _QP, _QP, _QP, _QP, _P, _P, _P, _P, _SZ, _P, _P]),
+    "qmcur_core_paper_workspace_size": (_SZ, [_I64, _I64, _I64, _I64, _I32]),
+    "qmcur_core_paper": (_I32, [_QP, _QP, _QP, _I32, _D, _I32, _I32, _QP, _QP, _QP, _P, _SZ, _P,
+                                _P]),
     "qmcur_complete_step": (_I32, [_QP, _P, _I64, _I64, ctypes.POINTER(Opts), _P, _P, _P, _P,
                                    _QP, _QP, _QP, _QP, _P, _P, _P, _SZ, _P, _P]),
 }
@@ -332,6 +335,20 @@ def decompose(A, D, sampler=SAMPLER_NORM, seed=0, stream_id=0, rcond=1e-10, rank
                                  _ptr(D.rank), _ptr(D.sigma), _ptr(D.out3), _ptr(D.ws),
                                  D.ws.numel(), _ptr(D.status), _stream(stream)),
            "qmcur_decompose")
+
+
+def core_paper(X, C, R, Cp, Rp, U, prec=PREC_BF16_MIXED, rcond=1e-10, rank_cap=0,
+               method=PINV_SUBSPACE_FP32, ws=None, status=None, stream=None):
+    """The paper's core U = C^+ X R^+ (qmcur_core_paper); Cp (c x m) and Rp
+    (n x r) receive C^+ and R^+."""
+    if ws is None:
+        m, n, c, r = X.shape[1], X.shape[2], C.shape[2], R.shape[1]
+        ws = torch.empty(int(lib().qmcur_core_paper_workspace_size(m, n, c, r, prec)),
+                         dtype=torch.uint8, device=X.device)
+    _check(lib().qmcur_core_paper(_ref(qmat(X)), _ref(qmat(C)), _ref(qmat(R)), method, rcond,
+                                  rank_cap, prec, _ref(qmat(Cp)), _ref(qmat(Rp)), _ref(qmat(U)),
+                                  _ptr(ws), ws.numel(), _ptr(status), _stream(stream)),
+           "qmcur_core_paper")
 
 
 class Completion:
