@@ -846,6 +846,7 @@ struct TcWs {
   float* P;   // split partials of T^T: [split][plane][n][kpad of Z = C T]
   double* partial;   // residual partials of Z = C T, two per tile
   unsigned* done;    // arrival count of the residual fold
+  float* Pz;         // K-split partials of a stored Z with few tiles: [split][plane][m][ldp]
 };
 
 // Tile widths: T^T = R^T (x) U (N over c) and Z = C T (N over n).  Both use
@@ -867,6 +868,38 @@ int t_splits(int64_t n, int64_t c, const TcPlan& p1, int64_t kp1) {
   return (kiters + per - 1) / per;
 }
 
+// K splits of a stored Z = C T whose tiles are too few to occupy the GPU
+// (a small output with a long K, e.g. the paper's core C^+ (X R^+)); 1 when
+// the tiles suffice.  From the shape alone; every split at least 4 stages.
+constexpr int kZSplitItems = 152, kMaxZSplits = 32;
+int z_splits(int64_t m, int64_t n, const TcPlan& p2, int64_t kp2) {
+  const int64_t tiles = ((m + BM - 1) / BM) * ((n + kBn2 - 1) / kBn2);
+  const int kiters = p2.nterms * (int)(kp2 / p2.epr);
+  int64_t ns = kZSplitItems / tiles;
+  if (ns > kMaxZSplits) ns = kMaxZSplits;
+  if (ns > kiters / 4) ns = kiters / 4;
+  if (ns < 2) return 1;
+  const int per = (int)((kiters + ns - 1) / ns);
+  return (kiters + per - 1) / per;
+}
+
+// Stored Z from its K-split partials: Z[t](i, j) = sum over s, in split
+// order, of P[s][t][i][j] (P row stride ldp).
+__global__ void __launch_bounds__(256) k_z_reduce(const float* __restrict__ P, int nsplit,
+                                                  int64_t split_stride, int64_t plane_stride,
+                                                  int64_t ldp, int64_t m, int64_t n, QView Z) {
+  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j >= n) return;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const float* src = P + t * plane_stride + i * ldp + j;
+    float v = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp) v += __ldcs(src + sp * split_stride);
+    reinterpret_cast<float*>(Z.p[t])[i * Z.ld + j] = v;
+  }
+}
+
 TcWs carve_tc(Carve& cv, const TcPlan& p1, const TcPlan& p2, int64_t m, int64_t n, int64_t c,
               int64_t r) {
   const int64_t es = p1.bf16 ? 2 : 4;   // both plans have the same element type
@@ -880,6 +913,8 @@ TcWs carve_tc(Carve& cv, const TcPlan& p1, const TcPlan& p2, int64_t m, int64_t 
   const int64_t tiles = ((m + BM - 1) / BM) * ((n + kBn2 - 1) / kBn2);
   w.partial = cv.take<double>((size_t)(2 * tiles));
   w.done = cv.take<unsigned>(1);
+  const int nsz = z_splits(m, n, p2, kp2);
+  w.Pz = nsz > 1 ? cv.take<float>((size_t)(nsz * 4 * m * rup(n, 4))) : nullptr;
   return w;
 }
 
@@ -1002,7 +1037,17 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
   p2.kblocks = (int)(kp2 / pl2.epr);
   p2.nterms = pl2.nterms;
   for (int i = 0; i < 6; ++i) { p2.ta[i] = pl2.ta[i]; p2.tb[i] = pl2.tb[i]; }
-  if (Z != nullptr) {
+  const int nsz = Z != nullptr ? z_splits(m, n, pl2, kp2) : 1;
+  const int64_t ldpz = rup(n, 4);
+  if (nsz > 1 && m > 65535) return QMCUR_ERR_UNSUPPORTED;   // k_z_reduce's grid
+  if (Z != nullptr && nsz > 1) {   // partials, summed by k_z_reduce
+    p2.mode = MODE_STORE_Z;
+    p2.nsplit = nsz;
+    for (int t = 0; t < 4; ++t) p2.z[t] = w.Pz + (int64_t)t * m * ldpz;
+    p2.ldz = ldpz;
+    p2.zsplit = 4 * m * ldpz;
+    p2.z_vec = 1;   // 256-byte aligned base, plane and row strides multiples of 4 floats
+  } else if (Z != nullptr) {
     p2.mode = MODE_STORE_Z;
     for (int t = 0; t < 4; ++t) p2.z[t] = reinterpret_cast<float*>(Z->plane[t]);
     p2.ldz = Z->ld;
@@ -1039,6 +1084,10 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
     k_t_reduce<false><<<rgrid, 256, 0, st>>>(w.P, nsplit, p1.zsplit, kp2 * ldp, ldp, n, c, kp2,
                                              pl2.npieces, w.B2, w.done);
     if ((s = launch_gemm<false, kBn2, false>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
+  }
+  if (Z != nullptr && nsz > 1) {
+    const dim3 zgrid((unsigned)((n + 255) / 256), (unsigned)m);
+    k_z_reduce<<<zgrid, 256, 0, st>>>(w.Pz, nsz, p2.zsplit, m * ldpz, ldpz, m, n, view(Z));
   }
   return cuda_ok(cudaGetLastError());
 }
