@@ -16,6 +16,8 @@ Workloads (the paper's own data sets are not available, so these stand in):
 * ``batch_problems`` - the uneven batch of small low-rank problems.
 * ``bernoulli_mask`` - an observation set Omega (Example 4.4's random missing
   entries), one bit per quaternion entry.
+* ``svd_lowrank`` - X = W_k Sigma_k V_k^H with orthonormal quaternion columns
+  in W_k, V_k (Example 4.1's model), plus ``gaussian_noise``.
 """
 import numpy as np
 
@@ -98,6 +100,44 @@ def smooth_color(m, n, modes, seed, offset=0.5, clip=True, max_freq=16,
             F = np.clip(F, 0.0, 1.0)
         X[ch + 1] = F
     return np.ascontiguousarray(X.astype(dtype))
+
+
+def _orthonormal_columns(rng, m, k):
+    """A quaternion m x k matrix Q with Q^H Q = I: the polar factor of a
+    Gaussian quaternion matrix G, G (G^H G)^{-1/2}.  It is formed on the
+    complex adjoint chi(G) = [[Ga, Gb], [-conj(Gb), conj(Ga)]] (G = Ga + Gb j),
+    whose polar factor U V^H (numpy's SVD) is chi(Q), and read back from the
+    first block row."""
+    G = rng.standard_normal((4, m, k))
+    Ga, Gb = G[0] + 1j * G[1], G[2] + 1j * G[3]
+    chi = np.block([[Ga, Gb], [-Gb.conj(), Ga.conj()]])
+    Us, _, Vh = np.linalg.svd(chi, full_matrices=False)
+    P = Us @ Vh
+    Qa, Qb = P[:m, :k], P[:m, k:]
+    return np.stack([Qa.real, Qa.imag, Qb.real, Qb.imag])
+
+
+def svd_lowrank(m, n, k, seed, smin=1.0, smax=10.0, dtype=np.float64):
+    """X = W_k Sigma_k V_k^H (Example 4.1): W_k (m x k) and V_k (n x k) with
+    orthonormal quaternion columns, Sigma_k = diag of k values drawn
+    uniformly from [smin, smax], sorted descending.  Draw order from
+    default_rng(seed): W_k's Gaussian, V_k's Gaussian, the k values.
+    Returns (X, W_k, V_k, sigma)."""
+    rng = np.random.default_rng(seed)
+    Wk = _orthonormal_columns(rng, m, k)
+    Vk = _orthonormal_columns(rng, n, k)
+    sig = np.sort(rng.uniform(smin, smax, size=k))[::-1].copy()
+    WS = Wk * sig[None, None, :]
+    VkH = np.stack([Vk[0].T, -Vk[1].T, -Vk[2].T, -Vk[3].T])   # conjugate transpose
+    X = _cd_product(WS, VkH)
+    return X.astype(dtype), Wk, Vk, sig
+
+
+def gaussian_noise(m, n, sigma, seed, dtype=np.float64):
+    """E = E0 + E1 i + E2 j + E3 k with i.i.d. N(0, sigma^2) components
+    (Example 4.1; its "variance sigma" is read as the standard deviation)."""
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((4, m, n)) * sigma).astype(dtype)
 
 
 def bernoulli_mask(m, n, seed, p_observed=0.5):
