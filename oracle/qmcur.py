@@ -20,6 +20,8 @@ Steps, in the order of Algorithm 1 (Sec. 3.1):
 * ``core_paper``      - the paper's own core C^+ X R^+ (Algorithm 1 step 3), with
                         C^+ and R^+ truncated by the rule of W^+; it equals W^+
                         when rank(W) = rank(X).
+* ``qsvd_truncated``  - the rank-k truncated QSVD X_k = P_k Sigma_k V_k^H (Sec. 2.2),
+                        the comparator of Example 4.2.
 * ``complete_step``,  - Algorithm 2 (Example 4.4): quaternion matrix completion by
   ``complete``          repeated QMCUR approximation and re-imposition of the
                         observed entries, with its relative-change stopping test.
@@ -182,6 +184,22 @@ def qsvd_values(W):
     """
     s = np.linalg.svd(complex_adjoint(W), compute_uv=False)
     return s[0::2].copy()
+
+
+def qsvd_truncated(X, rank, rcond=0.0):
+    """Rank-k truncated QSVD X_k = P_k Sigma_k V_k^H (Sec. 2.2; Example 4.2's
+    comparator), keeping the k = rank largest quaternion singular values that
+    exceed rcond * sigma_1.  Formed as the truncated SVD of the complex
+    adjoint, whose singular values come in equal pairs: the 2k leading
+    triplets are chi(X_k).  Returns (X_k, k, sigma)."""
+    X = as_q(X)
+    Pc, s, Vh = np.linalg.svd(complex_adjoint(X), full_matrices=False)
+    sq = s[0::2]
+    k = min(int(rank), sq.size)
+    if rcond > 0.0 and sq.size:
+        k = min(k, int(np.count_nonzero(sq > rcond * sq[0])))
+    kk = 2 * k
+    return from_complex_adjoint((Pc[:, :kk] * s[:kk]) @ Vh[:kk]), k, sq.copy()
 
 
 def pinv_truncated(W, rcond=1e-10, rank_cap=0):
