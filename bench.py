@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "batch512_uneven", "color512x768_rank31_mr70"])
+                    choices=[WORKLOAD, "batch512_uneven", "color512x768_rank31_mr70",
+                             "qsvd_vs_qmcur"])
     ap.add_argument("--core", default="intersection", choices=["intersection", "paper"],
                     help="decomposition workload: U = W^+ (default) or the paper's C^+ X R^+")
     ap.add_argument("--sampler", default=None, choices=["uniform", "norm"],
@@ -217,7 +218,7 @@ def stage_work(w, prec, sweeps, method="subspace"):
 def launches_per_step(args):
     """Kernels of the library launched per decomposition (counted from the code)."""
     n = 3 + 2                                  # probabilities (pass, fold, scale), sampler + gathers
-    n += 4 if args.pinv == "jacobi" else 1     # pseudo-inverse (one cooperative kernel)
+    n += 5 if args.pinv == "jacobi" else 1     # pseudo-inverse (one cooperative kernel)
     # FP32: T = U R, Z = C T with the residual, fold.  Split paths: the
     # operand splits (one launch), T^T = R^T U, the split-k reduce of T^T, and
     # Z = C T with the residual, whose last CTA folds the partials.
@@ -598,6 +599,86 @@ def run_core_paper(args):
     print(json.dumps(line), flush=True)
 
 
+def run_qsvd_vs_qmcur(args):
+    """Example 4.2: the rank-10 truncated QSVD against QMCUR_length and
+    QMCUR_uniform on X~ = X + E, X of rank 10 (Gaussian quaternion factors),
+    m = n = 50 .. 500, noise sigma in {0, 1e-7, 1e-4, 1e-1} (per-component
+    std, relative to entries of unit scale).  QMCUR takes c = r = ceil(k ln k)
+    = 24 and the rank-10 cap of W^+.  Both run in FP64 (QSVD: one-sided
+    Jacobi; QMCUR: FP64 GEMMs and Jacobi core); QMCUR is also timed on its
+    default path (mixed BF16, FP32 subspace core).  Error: ||B - X||_F/||X||_F
+    against the clean X; time: CUDA events, median of `steps` runs."""
+    import math
+    import torch
+    from paper_2402_19147_gb300 import qmcur as Q
+    from paper_2402_19147_gb300 import synth
+    torch.cuda.set_device(0)
+    k = 10
+    cr = int(math.ceil(k * math.log(k)))
+    stream = torch.cuda.current_stream()
+    rows = []
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for m in (50, 100, 200, 300, 400, 500):
+        X0, _ = synth.lowrank_gaussian(m, m, k, seed=80 + m, dtype=np.float64)
+        for sig in (0.0, 1e-7, 1e-4, 1e-1):
+            Xt = X0 + (synth.gaussian_noise(m, m, sig, seed=90 + m) if sig > 0 else 0.0)
+            Xd = torch.from_numpy(Xt).cuda()
+            X0d = torch.from_numpy(X0).cuda()
+            B = torch.empty_like(Xd)
+            st = Q.status_tensor()
+            wsq = torch.empty(int(Q.lib().qmcur_qsvd_workspace_size(m, m)), dtype=torch.uint8,
+                              device="cuda")
+            rk = torch.zeros(2, dtype=torch.int32, device="cuda")
+            t_qsvd = timed(lambda: Q.qsvd_truncated(Xd, B, k, max_sweeps=80, rank_out=rk,
+                                                    ws=wsq, status=st), args.steps)
+            e_qsvd = float(torch.linalg.vector_norm(B - X0d) / torch.linalg.vector_norm(X0d))
+            row = {"m": m, "sigma": sig, "qsvd_ms": t_qsvd, "qsvd_rel_err": e_qsvd,
+                   "qsvd_sweeps": int(rk[1]), "qsvd_status": Q.STATUS[int(st.item())]}
+            st.zero_()
+            for name, smp in (("length", Q.SAMPLER_NORM), ("uniform", Q.SAMPLER_UNIFORM)):
+                D = Q.Decomposition(m, m, cr, cr, Q.PREC_FP64, dtype=torch.float64)
+                Z = torch.empty_like(Xd)
+
+                def qmcur64():
+                    Q.decompose(Xd, D, sampler=smp, seed=1, rank_cap=k, stream=stream,
+                                pinv_method=Q.PINV_JACOBI_FP64)
+                    Q.reconstruct(D.C, D.U, D.R, Q.PREC_FP64, Z, D.ws, D.status, stream)
+                row[name + "_fp64_ms"] = timed(qmcur64, args.steps)
+                row[name + "_rel_err"] = float(torch.linalg.vector_norm(Z - X0d) /
+                                               torch.linalg.vector_norm(X0d))
+                Xf = Xd.float()
+                Df = Q.Decomposition(m, m, cr, cr, Q.PREC_BF16_MIXED)
+                row[name + "_default_ms"] = timed(
+                    lambda: Q.decompose(Xf, Df, sampler=smp, seed=1, rank_cap=k, stream=stream,
+                                        pinv_method=Q.PINV_SUBSPACE_FP32), args.steps)
+                Q.check_status(D.status, "qmcur fp64")
+                Q.check_status(Df.status, "qmcur default")
+            rows.append(row)
+    line = {"metric": "Example 4.2: truncated QSVD vs QMCUR, relative error and time",
+            "value": rows[-1]["qsvd_ms"] / rows[-1]["uniform_fp64_ms"],
+            "unit": "QSVD time / QMCUR_uniform time at m = 500, sigma = 0.1 (FP64 both)",
+            "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True,
+            "data": "synthetic", "dtype": "f64",
+            "config": {"workload": "qsvd_vs_qmcur", "rank": k, "c": cr, "r": cr,
+                       "sizes": [50, 100, 200, 300, 400, 500],
+                       "sigmas": [0.0, 1e-7, 1e-4, 1e-1]},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_complete(args):
     """Algorithm 2 (quaternion matrix completion, Example 4.4) on a 512 x 768
     colour field with 70% of its pixels missing.  A step is one iteration:
@@ -716,6 +797,8 @@ def main():
         run_batch(args)
     elif args.workload == "color512x768_rank31_mr70":
         run_complete(args)
+    elif args.workload == "qsvd_vs_qmcur":
+        run_qsvd_vs_qmcur(args)
     elif args.core == "paper":
         run_core_paper(args)
     else:

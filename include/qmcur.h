@@ -290,6 +290,25 @@ qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qm
                              cudaStream_t stream);
 
 /*
+ * qmcur_qsvd_truncated - the rank-k truncated QSVD approximation
+ * B = X_k = P_k Sigma_k V_k^H of Sec. 2.2, the comparator of Example 4.2
+ * (QSVD against QMCUR).  The QSVD is computed as in qmcur_pinv_core's
+ * QMCUR_PINV_JACOBI_FP64 (one-sided quaternion Jacobi in FP64); the k = rank
+ * largest singular values above rcond * sigma_1 are kept.
+ *   X        m x n input (F32 or F64).
+ *   B        m x n output (F32 or F64), fully overwritten.
+ *   rank_out device int32[2] or NULL: {k kept, sweeps}; sigma_out device
+ *            double[min(m, n)] or NULL: all singular values, descending.
+ *   max_sweeps <= 0 selects 40.  Workspace: qmcur_qsvd_workspace_size(m, n).
+ *   Device errors: NO_CONVERGENCE, NONFINITE, TIMEOUT.
+ */
+size_t qmcur_qsvd_workspace_size(int64_t m, int64_t n);
+qmcur_status qmcur_qsvd_truncated(const qmcur_qmat* X, int32_t rank, double rcond,
+                                  int32_t max_sweeps, qmcur_qmat* B, int32_t* rank_out,
+                                  double* sigma_out, void* workspace, size_t ws_bytes,
+                                  int32_t* dev_status, cudaStream_t stream);
+
+/*
  * qmcur_core_paper - the paper's own core U = C^+ X R^+ (Algorithm 1 step 3),
  * the least-squares core: no U gives a smaller ||X - C U R||_F.  It equals
  * W^+ of the intersection when rank(W) = rank(X) (Lemma 1), and is the

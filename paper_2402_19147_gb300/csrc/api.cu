@@ -267,6 +267,19 @@ qmcur_status qmcur_core_paper(const qmcur_qmat* X, const qmcur_qmat* C, const qm
                             dev_status, stream);
 }
 
+size_t qmcur_qsvd_workspace_size(int64_t m, int64_t n) {
+  if (m < 1 || n < 1) return 0;
+  return pinv_ws_bytes(m, n) + 256;
+}
+
+qmcur_status qmcur_qsvd_truncated(const qmcur_qmat* X, int32_t rank, double rcond,
+                                  int32_t max_sweeps, qmcur_qmat* B, int32_t* rank_out,
+                                  double* sigma_out, void* workspace, size_t ws_bytes,
+                                  int32_t* dev_status, cudaStream_t stream) {
+  return launch_qsvd_truncated(X, rcond, rank, max_sweeps, B, rank_out, sigma_out, workspace,
+                               ws_bytes, dev_status, stream);
+}
+
 qmcur_status qmcur_complete_step(qmcur_qmat* X, const uint8_t* mask, int64_t c, int64_t r,
                                  const qmcur_opts* o, double* col_p, double* row_p, int32_t* J,
                                  int32_t* I, qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W,

@@ -147,6 +147,10 @@ qmcur_status launch_sample(const qmcur_qmat* A, int32_t sampler, const double* c
 qmcur_status launch_pinv(const qmcur_qmat* W, double rcond, int32_t rank_cap, int32_t max_sweeps,
                          qmcur_qmat* U, int32_t* rank_out, double* sigma_out, void* ws,
                          size_t ws_bytes, int32_t* dev_status, cudaStream_t st);
+qmcur_status launch_qsvd_truncated(const qmcur_qmat* W, double rcond, int32_t rank,
+                                   int32_t max_sweeps, qmcur_qmat* B, int32_t* rank_out,
+                                   double* sigma_out, void* ws, size_t ws_bytes,
+                                   int32_t* dev_status, cudaStream_t st);
 // Z = C (U R); if Z == nullptr the product is not written and, with A != nullptr,
 // the residual sums are formed instead (fused epilogue).  With `complete`, A is
 // the iterate of a masked completion step (Algorithm 2) and is updated in place.

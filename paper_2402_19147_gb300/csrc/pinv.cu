@@ -47,6 +47,7 @@ struct PinvArgs {
   int max_sweeps;
   unsigned* bar;     // [0] arrive count, [1] generation, [2] abort flag
   unsigned* rot;     // per-sweep rotation counters [max_sweeps]
+  const double* colnorm2;   // |g_j|^2 of the initial columns (k_pinv_colnorm)
   int* sweeps_done;
   int32_t* status;
 };
@@ -134,10 +135,35 @@ __device__ __forceinline__ double block_sum128(double v, double* sh, int slot) {
   return 0.0;
 }
 
+// |g_j|^2 of every initial column, one CTA per column, in a fixed order.
+__global__ void __launch_bounds__(kPinvThreads) k_pinv_colnorm(const double* G, int64_t nr,
+                                                               double* colnorm2) {
+  __shared__ double red[4];
+  const double* g = G + (int64_t)blockIdx.x * nr * 4;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < nr * 4; i += kPinvThreads) s += g[i] * g[i];
+  block_sum128(s, red, 0);
+  __syncthreads();
+  if (threadIdx.x == 0) colnorm2[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
+}
+
 __global__ void __launch_bounds__(kPinvThreads) k_pinv_jacobi(PinvArgs a) {
   __shared__ double red[6 * 4];
   __shared__ int rotated_sh;
+  __shared__ double floor_sh;
   const int64_t nc = a.nc, nr = a.nr;
+  // Pairs of columns that are both below (n_c tol)^2 of the largest column
+  // norm^2 are numerically zero (an exactly low-rank input leaves many, at
+  // about (sqrt(n_r) u |X|)^2): rotating them only stirs rounding noise and
+  // never converges.  The floor sits at singular values ~1e-13 sigma_1 and
+  // below, far under any truncation.
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int64_t j = 0; j < nc; ++j) mx = fmax(mx, a.colnorm2[j]);
+    floor_sh = (double)nc * (double)nc * a.tol * a.tol * mx;
+  }
+  __syncthreads();
+  const double zero_floor = floor_sh;
   const int64_t N = (nc % 2 == 0) ? nc : nc + 1;
   const int64_t npairs = N / 2;
   const int64_t steps = N - 1;
@@ -179,7 +205,7 @@ __global__ void __launch_bounds__(kPinvThreads) k_pinv_jacobi(PinvArgs a) {
         // smaller column is below tol relative to the larger one (numerically
         // zero next to it: rotating it only stirs rounding noise).
         if (!(al > 0.0) || !(be > 0.0) || !(gam > a.tol * sqrt(al) * sqrt(be)) ||
-            fmin(al, be) < a.tol * a.tol * fmax(al, be))
+            fmin(al, be) < a.tol * a.tol * fmax(al, be) || fmax(al, be) < zero_floor)
           continue;
         if (threadIdx.x == 0) rotated_sh = 1;
         const double zeta = (be - al) / (2.0 * gam);
@@ -276,8 +302,10 @@ k_pinv_select(const double* G, int64_t nr, int64_t nc, double rcond, int rank_ca
 }
 
 // U[a][b] = sum_pos X[a][j] w_pos conj(Y[b][j]), j = kidx[pos]; U is c x r.
+// With unit_w the weights are 1: the truncated QSVD approximation itself.
 __global__ void k_pinv_form(const double* X, int64_t ldx, const double* Y, int64_t ldy,
-                            const int* kidx, const double* kw, const int* k_in, QView U) {
+                            const int* kidx, const double* kw, const int* k_in, QView U,
+                            int unit_w) {
   const int64_t c = U.rows, r = U.cols;
   const int k = *k_in;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < c * r;
@@ -286,7 +314,7 @@ __global__ void k_pinv_form(const double* X, int64_t ldx, const double* Y, int64
     double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
     for (int pos = 0; pos < k; ++pos) {
       const int64_t j = kidx[pos];
-      const double w = kw[pos];
+      const double w = unit_w ? 1.0 : kw[pos];
       const Q4 x = ldq(X, j * ldx + ai), y = ldq(Y, j * ldy + bi);
       // x * conj(y), scaled by w
       r0 += w * (x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w);
@@ -333,18 +361,13 @@ size_t pinv_ws_bytes(int64_t r, int64_t c) {
   return cv.off;
 }
 
-qmcur_status launch_pinv(const qmcur_qmat* W, double rcond, int32_t rank_cap, int32_t max_sweeps,
-                         qmcur_qmat* U, int32_t* rank_out, double* sigma_out, void* ws,
-                         size_t ws_bytes, int32_t* dev_status, cudaStream_t st) {
-  if (!valid_qmat(W) || !valid_qmat(U)) return QMCUR_ERR_INVALID_ARG;
+namespace {
+
+// The one-sided Jacobi sweeps on W (r x c) into the workspace carve w:
+// G (orthogonal columns) and V, sweeps counted in w.sweeps.
+qmcur_status run_jacobi(const qmcur_qmat* W, const PinvWs& w, int max_sweeps, int32_t* dev_status,
+                        cudaStream_t st) {
   const int64_t r = W->rows, c = W->cols;
-  if (r < 1 || c < 1 || U->rows != c || U->cols != r) return QMCUR_ERR_INVALID_ARG;
-  if (!(rcond >= 0.0)) return QMCUR_ERR_INVALID_ARG;
-  if (max_sweeps <= 0) max_sweeps = kDefaultSweeps;
-  if (max_sweeps > kMaxSweeps) max_sweeps = kMaxSweeps;
-  Carve cv(ws, ws_bytes);
-  PinvWs w = carve_pinv(cv, r, c, kMaxSweeps);
-  if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
   PinvArgs a;
   a.W = view(W);
   a.G = w.G;
@@ -358,12 +381,15 @@ qmcur_status launch_pinv(const qmcur_qmat* W, double rcond, int32_t rank_cap, in
   a.rot = w.rot;
   a.sweeps_done = w.sweeps;
   a.status = dev_status;
+  a.colnorm2 = w.sig;   // the singular values overwrite it after the sweeps
   {
     const int64_t total = a.nr * a.nc + a.nc * a.nc;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 2048) blocks = 2048;
     k_pinv_init<<<blocks, 256, 0, st>>>(a);
   }
+  if (a.nc > 2147483647) return QMCUR_ERR_UNSUPPORTED;
+  k_pinv_colnorm<<<(unsigned)a.nc, kPinvThreads, 0, st>>>(a.G, a.nr, w.sig);
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return QMCUR_ERR_CUDA;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return QMCUR_ERR_CUDA;
@@ -377,18 +403,70 @@ qmcur_status launch_pinv(const qmcur_qmat* W, double rcond, int32_t rank_cap, in
   void* args[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pinv_jacobi, dim3((unsigned)grid),
                                               dim3(kPinvThreads), args, 0, st);
-  if (e != cudaSuccess) return QMCUR_ERR_CUDA;
-  k_pinv_select<<<1, 1024, 0, st>>>(w.G, a.nr, a.nc, rcond, rank_cap, w.sig, w.pos, w.kidx, w.kw,
+  return e == cudaSuccess ? QMCUR_OK : QMCUR_ERR_CUDA;
+}
+
+}  // namespace
+
+qmcur_status launch_pinv(const qmcur_qmat* W, double rcond, int32_t rank_cap, int32_t max_sweeps,
+                         qmcur_qmat* U, int32_t* rank_out, double* sigma_out, void* ws,
+                         size_t ws_bytes, int32_t* dev_status, cudaStream_t st) {
+  if (!valid_qmat(W) || !valid_qmat(U)) return QMCUR_ERR_INVALID_ARG;
+  const int64_t r = W->rows, c = W->cols;
+  if (r < 1 || c < 1 || U->rows != c || U->cols != r) return QMCUR_ERR_INVALID_ARG;
+  if (!(rcond >= 0.0)) return QMCUR_ERR_INVALID_ARG;
+  if (max_sweeps <= 0) max_sweeps = kDefaultSweeps;
+  if (max_sweeps > kMaxSweeps) max_sweeps = kMaxSweeps;
+  Carve cv(ws, ws_bytes);
+  PinvWs w = carve_pinv(cv, r, c, kMaxSweeps);
+  if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
+  qmcur_status s = run_jacobi(W, w, max_sweeps, dev_status, st);
+  if (s != QMCUR_OK) return s;
+  const bool transposed = c > r;
+  const int64_t nc = transposed ? r : c, nr = transposed ? c : r;
+  k_pinv_select<<<1, 1024, 0, st>>>(w.G, nr, nc, rcond, rank_cap, w.sig, w.pos, w.kidx, w.kw,
                                      w.k, rank_out, sigma_out, w.sweeps, dev_status);
   {
-    const double* X = a.transposed ? w.G : w.V;
-    const int64_t ldx = a.transposed ? a.nr : a.nc;
-    const double* Y = a.transposed ? w.V : w.G;
-    const int64_t ldy = a.transposed ? a.nc : a.nr;
+    const double* X = transposed ? w.G : w.V;
+    const int64_t ldx = transposed ? nr : nc;
+    const double* Y = transposed ? w.V : w.G;
+    const int64_t ldy = transposed ? nc : nr;
     int blocks = (int)((c * r + 255) / 256);
     if (blocks > 4096) blocks = 4096;
-    k_pinv_form<<<blocks, 256, 0, st>>>(X, ldx, Y, ldy, w.kidx, w.kw, w.k, view(U));
+    k_pinv_form<<<blocks, 256, 0, st>>>(X, ldx, Y, ldy, w.kidx, w.kw, w.k, view(U), 0);
   }
+  return cuda_ok(cudaGetLastError());
+}
+
+// The rank-k truncated QSVD approximation B = X_k of the r x c matrix W: the
+// same Jacobi sweeps, then B = sum over kept j of g_j v_j^H (c <= r, G = W V)
+// or v_j g_j^H (c > r, G = W^H V).
+qmcur_status launch_qsvd_truncated(const qmcur_qmat* W, double rcond, int32_t rank,
+                                   int32_t max_sweeps, qmcur_qmat* B, int32_t* rank_out,
+                                   double* sigma_out, void* ws, size_t ws_bytes,
+                                   int32_t* dev_status, cudaStream_t st) {
+  if (!valid_qmat(W) || !valid_qmat(B) || rank < 1) return QMCUR_ERR_INVALID_ARG;
+  const int64_t r = W->rows, c = W->cols;
+  if (r < 1 || c < 1 || B->rows != r || B->cols != c) return QMCUR_ERR_INVALID_ARG;
+  if (!(rcond >= 0.0)) return QMCUR_ERR_INVALID_ARG;
+  if (max_sweeps <= 0) max_sweeps = kDefaultSweeps;
+  if (max_sweeps > kMaxSweeps) max_sweeps = kMaxSweeps;
+  Carve cv(ws, ws_bytes);
+  PinvWs w = carve_pinv(cv, r, c, kMaxSweeps);
+  if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
+  qmcur_status s = run_jacobi(W, w, max_sweeps, dev_status, st);
+  if (s != QMCUR_OK) return s;
+  const bool transposed = c > r;
+  const int64_t nc = transposed ? r : c, nr = transposed ? c : r;
+  k_pinv_select<<<1, 1024, 0, st>>>(w.G, nr, nc, rcond, rank, w.sig, w.pos, w.kidx, w.kw, w.k,
+                                     rank_out, sigma_out, w.sweeps, dev_status);
+  const double* X = transposed ? w.V : w.G;
+  const int64_t ldx = transposed ? nc : nr;
+  const double* Y = transposed ? w.G : w.V;
+  const int64_t ldy = transposed ? nr : nc;
+  int blocks = (int)((r * c + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_pinv_form<<<blocks, 256, 0, st>>>(X, ldx, Y, ldy, w.kidx, w.kw, w.k, view(B), 1);
   return cuda_ok(cudaGetLastError());
 }
 

@@ -78,6 +78,8 @@ SIGNATURES = {
     "qmcur_batch_destroy": (None, [_P]),
     "qmcur_decompose": (_I32, [_QP, _I64, _I64, ctypes.POINTER(Opts), _P, _P, _P, _P,
                                _QP, _QP, _QP, _QP, _P, _P, _P, _P, _SZ, _P, _P]),
+    "qmcur_qsvd_workspace_size": (_SZ, [_I64, _I64]),
+    "qmcur_qsvd_truncated": (_I32, [_QP, _I32, _D, _I32, _QP, _P, _P, _P, _SZ, _P, _P]),
     "qmcur_core_paper_workspace_size": (_SZ, [_I64, _I64, _I64, _I64, _I32]),
     "qmcur_core_paper": (_I32, [_QP, _QP, _QP, _I32, _D, _I32, _I32, _QP, _QP, _QP, _P, _SZ, _P,
                                 _P]),
@@ -335,6 +337,17 @@ def decompose(A, D, sampler=SAMPLER_NORM, seed=0, stream_id=0, rcond=1e-10, rank
                                  _ptr(D.rank), _ptr(D.sigma), _ptr(D.out3), _ptr(D.ws),
                                  D.ws.numel(), _ptr(D.status), _stream(stream)),
            "qmcur_decompose")
+
+
+def qsvd_truncated(X, B, rank, rcond=0.0, max_sweeps=0, rank_out=None, sigma_out=None, ws=None,
+                   status=None, stream=None):
+    """B = the rank-k truncated QSVD approximation of X (qmcur_qsvd_truncated)."""
+    if ws is None:
+        ws = torch.empty(int(lib().qmcur_qsvd_workspace_size(X.shape[1], X.shape[2])),
+                         dtype=torch.uint8, device=X.device)
+    _check(lib().qmcur_qsvd_truncated(_ref(qmat(X)), rank, rcond, max_sweeps, _ref(qmat(B)),
+                                      _ptr(rank_out), _ptr(sigma_out), _ptr(ws), ws.numel(),
+                                      _ptr(status), _stream(stream)), "qmcur_qsvd_truncated")
 
 
 def core_paper(X, C, R, Cp, Rp, U, prec=PREC_BF16_MIXED, rcond=1e-10, rank_cap=0,
