@@ -261,7 +261,7 @@ __device__ __forceinline__ void split_value(T x, int npieces, float out[3]) {
 // REV: Z = sum_k Y[n][k] X[m][k] (the B operand on the left of each
 // quaternion product) instead of X[m][k] Y[n][k]; the two differ in the sign
 // of the cross terms.  Work item w is split w % nsplit of tile w / nsplit.
-template <bool BF16, int BNT, bool REV>
+template <bool BF16, int BNT, bool REV, int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
            TcParams p) {
@@ -286,6 +286,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
   constexpr uint32_t kIdPos = make_idesc(BF16, false, BN), kIdNeg = make_idesc(BF16, true, BN);
   constexpr int kElemsPerRow = ROWB / (BF16 ? 2 : 4);
   constexpr int kStepElems = 32 / (BF16 ? 2 : 4);          // K of one MMA (32 bytes)
+  constexpr bool sums_mode = MODE == MODE_RESIDUAL || MODE == MODE_COMPLETE;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int mtiles = (p.M + BM - 1) / BM, ntiles = (p.N + BN - 1) / BN;
@@ -414,14 +415,13 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
       const int n0 = nt * BN;
       // the residual's first A chunk is fetched while the MMAs still run
       float4 anext[4][4];
-      const bool sums = p.mode == MODE_RESIDUAL || p.mode == MODE_COMPLETE;
-      if (sums) load_a(anext, row, n0 + 16 * half);
+      if constexpr (sums_mode) load_a(anext, row, n0 + 16 * half);
       if (!mbar_wait(&tfull[a], aph, abort_flag)) break;
       tc_fence_after();
       const uint32_t tb = tmem_base + (uint32_t)(a * ACC_COLS) + ((uint32_t)(sp * 32) << 16);
       double dsum = 0.0, asum = 0.0;
-      if (sums) {
-        const bool cmpl = p.mode == MODE_COMPLETE;
+      if constexpr (sums_mode) {
+        constexpr bool cmpl = MODE == MODE_COMPLETE;
 #pragma unroll 1
         for (int ch = half; ch < BN / 16; ch += 2) {
           const int c0 = n0 + ch * 16;
@@ -433,51 +433,71 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
           if (ch + 2 < BN / 16) load_a(anext, row, c0 + 32);   // this warp's next chunk in flight
           const bool in_row = row < p.M;
           const bool full16 = p.a_vec && c0 + 16 <= p.N;
-          // inb: columns inside Z; obs: observed (mask nonzero, or no mask).
-          // RESIDUAL sums both norms over inb & obs; COMPLETE sums the change
-          // over inb & ~obs and |a|^2 over inb.
-          unsigned inb = 0xffffu, obs = 0xffffu;
-          if (!full16 || !in_row) {
-            inb = 0;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) inb |= ((in_row && c0 + j < p.N) ? 1u : 0u) << j;
-          }
-          if (p.mask != nullptr) {
-            obs = 0;
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              obs |= (((inb >> j) & 1u) && p.mask[(int64_t)row * p.N + c0 + j] != 0 ? 1u : 0u) << j;
-          }
-          const unsigned wnum = cmpl ? (inb & ~obs) : (inb & obs);
-          const unsigned wden = cmpl ? inb : (inb & obs);
           float sd = 0.f, sa2 = 0.f;
+          if constexpr (!cmpl) {
+            unsigned keep = 0xffffu;   // columns of the chunk that count
+            if (!full16 || p.mask != nullptr) {
+              keep = 0;
 #pragma unroll
-          for (int pl = 0; pl < 4; ++pl) {
-            float z[16];
-            tmem_ld16(tb + pl * BN + ch * 16, z);
-            const float* avf = reinterpret_cast<const float*>(av[pl]);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const float wn = ((wnum >> j) & 1u) ? 1.f : 0.f;
-              const float wd = ((wden >> j) & 1u) ? 1.f : 0.f;
-              const float d = (avf[j] - z[j]) * wn;
-              sd = fmaf(d, d, sd);
-              sa2 = fmaf(avf[j] * wd, avf[j], sa2);
+              for (int j = 0; j < 16; ++j) {
+                const bool ok = in_row && c0 + j < p.N &&
+                                (p.mask == nullptr || p.mask[(int64_t)row * p.N + c0 + j] != 0);
+                keep |= (ok ? 1u : 0u) << j;
+              }
             }
-            if (cmpl && in_row) {
-              // X^{t+1}: the observed entries keep a, the others take z
-              float* xr = p.z[pl] + (int64_t)row * p.ldz + c0;
-              float v[16];
 #pragma unroll
-              for (int j = 0; j < 16; ++j) v[j] = ((obs >> j) & 1u) ? avf[j] : z[j];
-              if (full16 && p.z_vec) {
+            for (int pl = 0; pl < 4; ++pl) {
+              float z[16];
+              tmem_ld16(tb + pl * BN + ch * 16, z);
+              const float* avf = reinterpret_cast<const float*>(av[pl]);
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                  reinterpret_cast<float4*>(xr)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-              } else {
+              for (int j = 0; j < 16; ++j) {
+                const float w = ((keep >> j) & 1u) ? 1.f : 0.f;
+                const float d = (avf[j] - z[j]) * w;
+                sd = fmaf(d, d, sd);
+                sa2 = fmaf(avf[j] * w, avf[j], sa2);
+              }
+            }
+          } else {
+            // inb: columns inside Z; obs: observed (mask nonzero, or no
+            // mask).  The change sums over inb & ~obs, |a|^2 over inb.
+            unsigned inb = 0xffffu, obs = 0xffffu;
+            if (!full16 || !in_row) {
+              inb = 0;
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                  if ((inb >> j) & 1u) xr[j] = v[j];
+              for (int j = 0; j < 16; ++j) inb |= ((in_row && c0 + j < p.N) ? 1u : 0u) << j;
+            }
+            if (p.mask != nullptr) {
+              obs = 0;
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                obs |= (((inb >> j) & 1u) && p.mask[(int64_t)row * p.N + c0 + j] != 0 ? 1u : 0u) << j;
+            }
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl) {
+              float z[16];
+              tmem_ld16(tb + pl * BN + ch * 16, z);
+              const float* avf = reinterpret_cast<const float*>(av[pl]);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const bool moved = ((inb & ~obs) >> j) & 1u;
+                const float d = moved ? z[j] - avf[j] : 0.f;
+                sd = fmaf(d, d, sd);
+                const float a2 = ((inb >> j) & 1u) ? avf[j] : 0.f;
+                sa2 = fmaf(a2, a2, sa2);
+                z[j] = ((obs >> j) & 1u) ? avf[j] : z[j];   // X^{t+1}
+              }
+              if (in_row) {
+                float* xr = p.z[pl] + (int64_t)row * p.ldz + c0;
+                if (full16 && p.z_vec) {
+#pragma unroll
+                  for (int q = 0; q < 4; ++q)
+                    reinterpret_cast<float4*>(xr)[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+                } else {
+#pragma unroll
+                  for (int j = 0; j < 16; ++j)
+                    if ((inb >> j) & 1u) xr[j] = z[j];
+                }
               }
             }
           }
@@ -491,7 +511,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
             float z[16];
             tmem_ld16(tb + pl * BN + ch * 16, z);
             const int c0 = n0 + ch * 16;
-            if (p.mode == MODE_STORE_ZT) {
+            if constexpr (MODE == MODE_STORE_ZT) {
               if (row < p.M) {
                 float* zc = p.z[pl] + split * p.zsplit + (int64_t)c0 * p.ldz + row;
 #pragma unroll
@@ -516,7 +536,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
       }
       tc_fence_before();
       if (lane == 0) mbar_arrive(&tempty[a]);
-      if (sums) {
+      if constexpr (sums_mode) {
         // fixed-order reduction: warp tree, then the eight warps in order
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -544,7 +564,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
                  : "memory");
   }
   if (threadIdx.x == 0 && *abort_flag) set_status(p.status, QMCUR_ERR_TIMEOUT);
-  if ((p.mode == MODE_RESIDUAL || p.mode == MODE_COMPLETE) && p.done != nullptr) {
+  if (sums_mode && p.done != nullptr) {
     // The last CTA to finish folds the per-item partials into out3 in a fixed
     // order: strided sums, a shuffle tree per warp, then the warps in order.
     __shared__ int s_last;
@@ -948,14 +968,15 @@ qmcur_status launch_splits(const SplitJobs& js, int tiles, cudaStream_t st) {
   return cuda_ok(cudaGetLastError());
 }
 
-template <bool BF16, int BNT, bool REV>
-qmcur_status launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& p,
-                         cudaStream_t st) {
+template <bool BF16, int BNT, bool REV, int MODE>
+qmcur_status launch_gemm_mode(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& p,
+                              cudaStream_t st) {
   static bool attr_done[64] = {};
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QMCUR_ERR_CUDA;
   if (!attr_done[dev]) {
-    if (cudaFuncSetAttribute(k_qgemm_tc<BF16, BNT, REV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_qgemm_tc<BF16, BNT, REV, MODE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TcShape<BNT>::SMEM) != cudaSuccess)
       return QMCUR_ERR_CUDA;
     attr_done[dev] = true;
@@ -964,8 +985,27 @@ qmcur_status launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const TcP
     return QMCUR_ERR_CUDA;
   const int items = ((p.M + BM - 1) / BM) * ((p.N + BNT - 1) / BNT) * p.nsplit;
   const int grid = items < sms ? items : sms;
-  k_qgemm_tc<BF16, BNT, REV><<<grid, kTcThreads, TcShape<BNT>::SMEM, st>>>(ma, mb, p);
+  k_qgemm_tc<BF16, BNT, REV, MODE><<<grid, kTcThreads, TcShape<BNT>::SMEM, st>>>(ma, mb, p);
   return cuda_ok(cudaGetLastError());
+}
+
+// One instantiation per epilogue mode, so that each carries only its own
+// epilogue's registers.  Tᵀ (REV) only stores transposed; Z = C T stores,
+// folds the residual or updates the completion iterate.
+template <bool BF16, int BNT, bool REV>
+qmcur_status launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& p,
+                         cudaStream_t st) {
+  if constexpr (REV) {
+    if (p.mode != MODE_STORE_ZT) return QMCUR_ERR_INVALID_ARG;
+    return launch_gemm_mode<BF16, BNT, REV, MODE_STORE_ZT>(ma, mb, p, st);
+  } else {
+    switch (p.mode) {
+      case MODE_STORE_Z: return launch_gemm_mode<BF16, BNT, REV, MODE_STORE_Z>(ma, mb, p, st);
+      case MODE_RESIDUAL: return launch_gemm_mode<BF16, BNT, REV, MODE_RESIDUAL>(ma, mb, p, st);
+      case MODE_COMPLETE: return launch_gemm_mode<BF16, BNT, REV, MODE_COMPLETE>(ma, mb, p, st);
+      default: return QMCUR_ERR_INVALID_ARG;
+    }
+  }
 }
 
 }  // namespace
