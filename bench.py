@@ -473,7 +473,8 @@ def run_ours(args):
 
 def run_batch(args):
     """512 uneven problems decomposed per step by one replay of the batched
-    plan's CUDA graph (one launch per stage, FP32 GEMMs, FP32 Jacobi core)."""
+    plan's CUDA graph (one launch per stage, FP32 GEMMs; the core per --pinv:
+    the FP32 subspace program, one CTA per problem, or the FP32 Jacobi)."""
     import torch
     from paper_2402_19147_gb300 import qmcur as Q
     from paper_2402_19147_gb300 import synth
@@ -481,8 +482,10 @@ def run_batch(args):
     probs = synth.batch_problems(count=512, seed=3)
     As = [torch.from_numpy(p["X"]).cuda() for p in probs]
     stream = torch.cuda.current_stream()
+    pinv_method = Q.PINV_SUBSPACE_FP32 if args.pinv == "subspace" else Q.PINV_JACOBI_FP64
     B = Q.Batch(As, [p["c"] for p in probs], [p["r"] for p in probs],
-                [p["rank"] for p in probs], sampler=Q.SAMPLER_NORM, seed=0, stream=stream)
+                [p["rank"] for p in probs], sampler=Q.SAMPLER_NORM, seed=0, stream=stream,
+                pinv_method=pinv_method)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         B.run(stream)
@@ -507,7 +510,8 @@ def run_batch(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "batch512_uneven", "problems": 512, "gemm_prec": "fp32",
-                       "pinv": "fp32-jacobi-per-cta", "graph": True,
+                       "pinv": ("fp32-subspace-per-cta" if args.pinv == "subspace"
+                                else "fp32-jacobi-per-cta"), "graph": True,
                        "gemm_tiles": [int(x) for x in host_tiles(Q, B)],
                        "l2": "flushed between steps (256 MiB write)"},
             "gemm_qtflops_per_step": fl / (ms / 1e3) / 1e12,

@@ -379,10 +379,15 @@ qmcur_status qmcur_complete_step(qmcur_qmat* X, const uint8_t* mask, int64_t c, 
  * (max(c,r) + min(c,r)) * min(c,r) * 16 bytes <= 200 KiB (the pseudo-inverse
  * of each intersection runs in one CTA's shared memory).
  * Per problem b (Algorithm 1 with U = W^+): probabilities of opts->sampler,
- * Philox draws with key opts->seed and stream_id = b, gathers, an FP32
- * one-sided quaternion Jacobi QSVD of W truncated at opts->rcond and
- * rank_cap[b], T = U R and the relative residual of C T (never written),
- * all in FP32.  opts->prec and opts->pinv_method are not used.  dev_status
+ * Philox draws with key opts->seed and stream_id = b, gathers, the core,
+ * T = U R and the relative residual of C T (never written), all in FP32.
+ * The core follows opts->pinv_method: QMCUR_PINV_JACOBI_FP64 (the default
+ * value 0) selects an FP32 one-sided quaternion Jacobi QSVD of W per CTA,
+ * truncated at opts->rcond and rank_cap[b] (limits above);
+ * QMCUR_PINV_SUBSPACE_FP32 runs the FP32 subspace method of qmcur_pinv_core
+ * with one CTA per problem (rank_cap required, k <= 100, no shared-memory
+ * limit on the intersection; largest problems first).  opts->prec is not
+ * used.  dev_status
  * (device int32, may be NULL) receives the first error; per-problem errors
  * also land in info[2] of the problem.  The plan keeps the pointers it was
  * given: A[b] and dev_status must stay valid until qmcur_batch_destroy.

@@ -13,6 +13,10 @@
 //   k_batch_jacobi   one CTA per problem: FP32 one-sided quaternion Jacobi on
 //                    the (<= 80 x 80) intersection held in shared memory, the
 //                    rcond / rank-cap truncation, U = V Sigma^-2 G^H;
+//   or k_pinv_fused_each (opts->pinv_method = QMCUR_PINV_SUBSPACE_FP32):
+//                    one CTA per problem runs the FP32 subspace program of
+//                    the single-problem path (pinv_fast.cu) on its own
+//                    intersection, largest problems first;
 //   k_batch_gemm     grouped quaternion GEMMs over a flattened tile list
 //                    (T = U R, then Z = C T with the residual fused), tile
 //                    shape chosen per GEMM by timing the candidates at plan
@@ -24,8 +28,18 @@
 #include <vector>
 
 #include "sample_impl.cuh"
+#include "small.cuh"
 
 namespace qmcur {
+
+// The subspace core, one problem per CTA (pinv_fast.cu).
+size_t pinv_each_ws_bytes(int64_t r, int64_t c, int64_t k);
+size_t pinv_each_prog_bytes();
+qmcur_status pinv_each_build(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat* U,
+                             int32_t* rank_out, uint64_t seed, void* ws, size_t ws_bytes,
+                             int32_t* dev_status, void* prog_out, int* k_out);
+qmcur_status pinv_each_launch(const void* dprogs, const int* dorder, int count, int kmax,
+                              cudaStream_t st);
 
 constexpr int kBatchMaxCore = 80;      // largest min(r, c) held by k_batch_jacobi
 constexpr int64_t kBatchCoreSmem = 200 * 1024;   // bytes of G and V in shared memory
@@ -449,6 +463,11 @@ struct BatchPlan {
   void* arena = nullptr;
   int32_t* status = nullptr;
   size_t jac_smem = 0, samp_smem = 0;
+  bool subspace = false;      // the core: subspace programs instead of the Jacobi
+  void* progs = nullptr;      // device: one subspace program per problem
+  int* order = nullptr;       // device: problems, largest first
+  void* pinv_arena = nullptr;
+  int kmax = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   qmcur_opts opts{};
@@ -462,8 +481,13 @@ static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st) {
   base.norm = norm;
   k_batch_sample<<<2 * p->count, kSampleThreads, p->samp_smem, st>>>(p->dprobs, base, p->status);
   k_batch_gather<<<dim3(64, p->count), 256, 0, st>>>(p->dprobs);
-  k_batch_jacobi<<<p->count, 1024, p->jac_smem, st>>>(
-      p->dprobs, p->opts.rcond, p->opts.max_sweeps > 0 ? p->opts.max_sweeps : 30);
+  if (p->subspace) {
+    const qmcur_status s = pinv_each_launch(p->progs, p->order, p->count, p->kmax, st);
+    if (s != QMCUR_OK) return s;
+  } else {
+    k_batch_jacobi<<<p->count, 1024, p->jac_smem, st>>>(
+        p->dprobs, p->opts.rcond, p->opts.max_sweeps > 0 ? p->opts.max_sweeps : 30);
+  }
   launch_batch_gemm(p->cfg1, p->dprobs, p->dtiles1, p->ntiles1, 0, nullptr, st);
   launch_batch_gemm(p->cfg2, p->dprobs, p->dtiles2, p->ntiles2, 1, p->partial, st);
   k_batch_fold<<<p->count, 32, 0, st>>>(p->dprobs, p->partial);
@@ -520,6 +544,9 @@ static void free_plan(BatchPlan* p) {
   cudaFree(p->dtiles2);
   cudaFree(p->partial);
   cudaFree(p->arena);
+  cudaFree(p->progs);
+  cudaFree(p->order);
+  cudaFree(p->pinv_arena);
   delete p;
 }
 
@@ -535,10 +562,16 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
   if (count < 1 || A == nullptr || c == nullptr || r == nullptr || opts == nullptr || plan_out == nullptr)
     return QMCUR_ERR_INVALID_ARG;
   if (opts->sampler != QMCUR_SAMPLER_NORM && opts->sampler != QMCUR_SAMPLER_UNIFORM) return QMCUR_ERR_INVALID_ARG;
+  const bool subspace = opts->pinv_method == QMCUR_PINV_SUBSPACE_FP32;
+  if (subspace && rank_cap == nullptr) return QMCUR_ERR_UNSUPPORTED;   // the method needs caps
   for (int b = 0; b < count; ++b) {
     if (!valid_qmat(&A[b], true, false)) return QMCUR_ERR_INVALID_ARG;
     if (c[b] < 1 || c[b] > A[b].cols || r[b] < 1 || r[b] > A[b].rows) return QMCUR_ERR_INVALID_ARG;
-    {
+    if (subspace) {
+      const int64_t nmin = c[b] < r[b] ? c[b] : r[b];
+      const int64_t k = rank_cap[b] < nmin ? rank_cap[b] : nmin;
+      if (rank_cap[b] < 1 || k > kSmallCholMax) return QMCUR_ERR_UNSUPPORTED;
+    } else {
       // the Jacobi core keeps G (n_r x n_c) and V (n_c x n_c) in shared memory
       const int64_t nr = c[b] > r[b] ? c[b] : r[b], nc = c[b] < r[b] ? c[b] : r[b];
       if (nc > kBatchMaxCore || (nr * nc + nc * nc) * 16 > kBatchCoreSmem) return QMCUR_ERR_UNSUPPORTED;
@@ -591,12 +624,60 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     P.out3 = reinterpret_cast<double*>(base + o.o3);
     P.info = reinterpret_cast<int32_t*>(base + o.info);
   }
+  if (subspace) {
+    // one subspace program per problem over its own carve of one arena;
+    // CTA order: the most work (r c k + max(r, c) k^2) first
+    p->subspace = true;
+    std::vector<size_t> woff(count);
+    size_t wtotal = 0;
+    for (int b = 0; b < count; ++b) {
+      const int64_t nmin = c[b] < r[b] ? c[b] : r[b];
+      const int64_t k = rank_cap[b] < nmin ? rank_cap[b] : nmin;
+      woff[b] = wtotal;
+      wtotal += align_up(pinv_each_ws_bytes(r[b], c[b], k), 256);
+    }
+    const size_t pb = pinv_each_prog_bytes();
+    std::vector<char> hprogs((size_t)count * pb);
+    std::vector<double> work(count);
+    if (cudaMalloc(&p->pinv_arena, wtotal) != cudaSuccess ||
+        cudaMalloc(&p->progs, hprogs.size()) != cudaSuccess ||
+        cudaMalloc(&p->order, count * sizeof(int)) != cudaSuccess) {
+      free_plan(p);
+      return QMCUR_ERR_CUDA;
+    }
+    for (int b = 0; b < count; ++b) {
+      const BatchProblem& P = p->host[b];
+      auto toq = [](const QView& v) {
+        qmcur_qmat q;
+        for (int t = 0; t < 4; ++t) q.plane[t] = v.p[t];
+        q.rows = v.rows; q.cols = v.cols; q.ld = v.ld; q.dtype = v.dtype; q.reserved = 0;
+        return q;
+      };
+      qmcur_qmat Wq = toq(P.W), Uq = toq(P.U);
+      int k = 0;
+      const qmcur_status s = pinv_each_build(
+          &Wq, P.rank_cap, &Uq, P.info, opts->seed ^ (0x9e3779b97f4a7c15ull + (uint64_t)b),
+          static_cast<char*>(p->pinv_arena) + woff[b], wtotal - woff[b], dev_status,
+          hprogs.data() + (size_t)b * pb, &k);
+      if (s != QMCUR_OK) { free_plan(p); return s; }
+      p->kmax = std::max(p->kmax, k);
+      const double rr = (double)P.r, cc = (double)P.c;
+      work[b] = rr * cc * k + std::max(rr, cc) * k * k;
+    }
+    std::vector<int> ord(count);
+    for (int b = 0; b < count; ++b) ord[b] = b;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return work[x] > work[y]; });
+    cudaMemcpyAsync(p->progs, hprogs.data(), hprogs.size(), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(p->order, ord.data(), count * sizeof(int), cudaMemcpyHostToDevice, stream);
+    // the host copies above must be complete before the vectors go away
+    if (cudaStreamSynchronize(stream) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
+  }
   if (cudaMalloc(&p->dprobs, count * sizeof(BatchProblem)) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
   cudaMemcpyAsync(p->dprobs, p->host.data(), count * sizeof(BatchProblem), cudaMemcpyHostToDevice, stream);
   p->jac_smem = max_rc * sizeof(float4) + (size_t)kBatchMaxCore * 8 + 64;
   p->samp_smem = ((max_nm + 31) / 32 * 4 + 15) / 16 * 16 + max_nm * 8;
-  if (cudaFuncSetAttribute(k_batch_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->jac_smem) !=
-          cudaSuccess ||
+  if ((!subspace && cudaFuncSetAttribute(k_batch_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)p->jac_smem) != cudaSuccess) ||
       cudaFuncSetAttribute(k_batch_sample, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->samp_smem) !=
           cudaSuccess) {
     free_plan(p);

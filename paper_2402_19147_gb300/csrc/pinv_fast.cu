@@ -187,7 +187,10 @@ constexpr size_t fused_smem(int k) {
   return cmax((size_t)kFusedWorkers * kSmGemmQuats * 16, solve_chol_off(k) + sm_chol_bytes());
 }
 
-__global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_constant__ FusedProg P) {
+// The program's steps, run by vg CTAs of which this is number vb: vg = the
+// grid with a grid barrier between steps (one problem on the whole GPU), or
+// vg = 1 with a CTA barrier (one problem per CTA, the batched path).
+__device__ __forceinline__ void fused_program(const FusedProg& P, int vb, int vg) {
   extern __shared__ __align__(16) unsigned char smf[];
   const int worker = threadIdx.x / kSmTileThreads, wtid = threadIdx.x % kSmTileThreads;
   float4* wsm = reinterpret_cast<float4*>(smf) + worker * kSmGemmQuats;
@@ -196,8 +199,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_co
     const Phase& ph = P.ph[q];
     if (ph.kind == PH_PREP) {
       const int64_t nW = (int64_t)P.r * P.c, nO = (int64_t)P.c * P.k;
-      for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nW + nO;
-           e += (int64_t)gridDim.x * blockDim.x) {
+      for (int64_t e = (int64_t)vb * blockDim.x + threadIdx.x; e < nW + nO;
+           e += (int64_t)vg * blockDim.x) {
         if (e < nW) {
           const int64_t i = e / P.c, j = e % P.c;
 #pragma unroll
@@ -220,8 +223,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_co
       }
       // item -> one per SM first (worker 0 of every CTA), then worker 1;
       // job 1's items follow job 0's, with their own partials and counts
-      for (int t = blockIdx.x + gridDim.x * worker; t < items[0] + items[1];
-           t += gridDim.x * kFusedWorkers) {
+      for (int t = vb + vg * worker; t < items[0] + items[1]; t += vg * kFusedWorkers) {
         const int j = t < items[0] ? 0 : 1;
         const Job& jb = ph.job[j];
         const int tt = j == 0 ? t : t - items[0];
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_co
       }
     } else {   // PH_SOLVE
       const int rows0 = ph.job[0].g.M, rows = rows0 + (ph.njobs > 1 ? ph.job[1].g.M : 0);
-      if (blockIdx.x < rows) {   // CTAs without rows skip the factorisation
+      if (vb < rows) {   // CTAs without rows skip the factorisation
         SolveJobs sj;
         sj.Y0 = ph.job[0].g.X;
         sj.Z0 = ph.job[0].g.Z;
@@ -267,25 +269,41 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_co
         sj.Z1 = ph.job[1].g.Z;
         sj.rows0 = rows0;
         sj.rows = rows;
+        sj.vb = vb;
+        sj.vg = vg;
         // R packed at the start of shared memory, as the row solves read it;
         // the first kSolveRowWarps rows of this CTA are solved along the way
         const int rode = sm_chol(ph.G, ph.k, reinterpret_cast<float*>(smf), P.status,
                                  smf + solve_chol_off(ph.k), &sj);
         const int warp = threadIdx.x >> 5, nw = kFusedThreads / 32;
         for (int i = rode + warp;; i += nw) {
-          const int row = solve_row_of(i);
+          const int row = solve_row_of(i, vb, vg);
           if (row >= rows) break;
           const Job& jb = ph.job[row < rows0 ? 0 : 1];
           sm_trsm_row_any(jb.g.X, jb.g.Z, row < rows0 ? row : row - rows0, jb.g.K, smf);
         }
       }
     }
-    if (q + 1 < P.nph && !grid_sync(P.bar, P.status, bar_target)) return;
+    if (q + 1 < P.nph) {
+      if (vg == 1) __syncthreads();   // the CTA's own global writes, then its reads
+      else if (!grid_sync(P.bar, P.status, bar_target)) return;
+    }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && P.rank_out != nullptr) {
+  if (vb == 0 && threadIdx.x == 0 && P.rank_out != nullptr) {
     P.rank_out[0] = P.k;
     P.rank_out[1] = 2;
   }
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 1) k_pinv_fused(const __grid_constant__ FusedProg P) {
+  fused_program(P, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// One problem per CTA: CTA b runs the program progs[order[b]] alone (the
+// order puts the largest problems first, so that the small ones fill in).
+__global__ void __launch_bounds__(kFusedThreads) k_pinv_fused_each(const FusedProg* __restrict__ progs,
+                                                                   const int* __restrict__ order) {
+  fused_program(progs[order[blockIdx.x]], 0, 1);
 }
 
 // Product X (op) Y (op) -> Z of a GEMM step.
@@ -370,41 +388,10 @@ struct ProgBuilder {
   }
 };
 
-qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat* U,
-                              int32_t* rank_out, uint64_t seed, void* ws, size_t ws_bytes,
-                              int32_t* dev_status, cudaStream_t st) {
-  const int64_t r = W->rows, c = W->cols;
-  const int64_t nmin = r < c ? r : c;
-  if (rank_cap < 1) return QMCUR_ERR_UNSUPPORTED;   // the method needs the cap
-  const int k = (int)(rank_cap < nmin ? rank_cap : nmin);
-  if (k > kSmallCholMax || r > 65535 || c > 65535) return QMCUR_ERR_UNSUPPORTED;
-  Carve cv(ws, ws_bytes);
-  FastWs w = carve_fast(cv, r, c, k);
-  float4* part = cv.take<float4>((size_t)kMaxPartTiles * kSmTileThreads);
-  unsigned* bar = cv.take<unsigned>(4 + kMaxPartTiles);
-  if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
-  int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      dev < 0 || dev >= 64)
-    return QMCUR_ERR_CUDA;
-  static bool attr_set[64] = {};
-  if (!attr_set[dev]) {
-    if (cudaFuncSetAttribute(k_pinv_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)fused_smem(kSmallCholMax)) != cudaSuccess)
-      return QMCUR_ERR_CUDA;
-    attr_set[dev] = true;
-  }
-  const size_t smem = fused_smem(k);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pinv_fused, kFusedThreads, smem) !=
-      cudaSuccess)
-    return QMCUR_ERR_CUDA;
-  if (per_sm < 1) return QMCUR_ERR_CUDA;
-  const int ri = (int)r, ci = (int)c;
-  // one CTA per SM at most: a GEMM step has at most ~2 x SMs useful items
-  const int grid = sms;
-  ProgBuilder b;
-  b.workers = grid * kFusedWorkers;
+// The subspace program for the r x c W with cap k into b (its workers set),
+// over the carve w; U receives W_k^+.
+static void build_program(ProgBuilder& b, const FastWs& w, const qmcur_qmat* U, int ri, int ci,
+                          int k) {
   b.p.ph[b.p.nph++].kind = PH_PREP;
   // Intermediate bases only have to span the subspaces (one CholeskyQR
   // pass); each product with W starts from an orthonormal basis, because
@@ -442,6 +429,44 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
   b.gemm(b.gram(w.T, ri, k, w.G));
   b.solve(w.G, w.T, w.Q, ri, k, &w.Z, &w.Y, ci);                               // R2
   b.gemm(GemmSpec{false, true, ci, ri, k, w.Y, w.Q, Uo, false});
+}
+
+qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat* U,
+                              int32_t* rank_out, uint64_t seed, void* ws, size_t ws_bytes,
+                              int32_t* dev_status, cudaStream_t st) {
+  const int64_t r = W->rows, c = W->cols;
+  const int64_t nmin = r < c ? r : c;
+  if (rank_cap < 1) return QMCUR_ERR_UNSUPPORTED;   // the method needs the cap
+  const int k = (int)(rank_cap < nmin ? rank_cap : nmin);
+  if (k > kSmallCholMax || r > 65535 || c > 65535) return QMCUR_ERR_UNSUPPORTED;
+  Carve cv(ws, ws_bytes);
+  FastWs w = carve_fast(cv, r, c, k);
+  float4* part = cv.take<float4>((size_t)kMaxPartTiles * kSmTileThreads);
+  unsigned* bar = cv.take<unsigned>(4 + kMaxPartTiles);
+  if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      dev < 0 || dev >= 64)
+    return QMCUR_ERR_CUDA;
+  static bool attr_set[64] = {};
+  if (!attr_set[dev]) {
+    if (cudaFuncSetAttribute(k_pinv_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)fused_smem(kSmallCholMax)) != cudaSuccess)
+      return QMCUR_ERR_CUDA;
+    attr_set[dev] = true;
+  }
+  const size_t smem = fused_smem(k);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pinv_fused, kFusedThreads, smem) !=
+      cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  if (per_sm < 1) return QMCUR_ERR_CUDA;
+  const int ri = (int)r, ci = (int)c;
+  // one CTA per SM at most: a GEMM step has at most ~2 x SMs useful items
+  const int grid = sms;
+  ProgBuilder b;
+  b.workers = grid * kFusedWorkers;
+  build_program(b, w, U, ri, ci, k);
   if (!b.ok) return QMCUR_ERR_UNSUPPORTED;
   b.p.Win = view(W);
   b.p.W32 = w.W32;
@@ -460,6 +485,61 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
   void* args[] = {(void*)&b.p};
   return cuda_ok(cudaLaunchCooperativeKernel((const void*)k_pinv_fused, dim3(grid),
                                              dim3(kFusedThreads), args, smem, st));
+}
+
+// ---------------------------------------------------------------------------
+// One problem per CTA (the batched path): each problem's program, built with
+// a single tile worker (no split-k partials), over its own carve of the
+// batch's arena; CTA b runs the program order[b].
+
+size_t pinv_each_ws_bytes(int64_t r, int64_t c, int64_t k) {
+  Carve cv(nullptr, 0);
+  carve_fast(cv, r, c, k);
+  return cv.off;
+}
+
+size_t pinv_each_prog_bytes() { return sizeof(FusedProg); }
+
+qmcur_status pinv_each_build(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat* U,
+                             int32_t* rank_out, uint64_t seed, void* ws, size_t ws_bytes,
+                             int32_t* dev_status, void* prog_out, int* k_out) {
+  const int64_t r = W->rows, c = W->cols;
+  const int64_t nmin = r < c ? r : c;
+  if (rank_cap < 1) return QMCUR_ERR_UNSUPPORTED;
+  const int k = (int)(rank_cap < nmin ? rank_cap : nmin);
+  if (k > kSmallCholMax || r > 65535 || c > 65535) return QMCUR_ERR_UNSUPPORTED;
+  Carve cv(ws, ws_bytes);
+  FastWs w = carve_fast(cv, r, c, k);
+  if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
+  ProgBuilder b;
+  b.workers = 1;   // one CTA: never split k (no partial tiles)
+  build_program(b, w, U, (int)r, (int)c, k);
+  if (!b.ok) return QMCUR_ERR_UNSUPPORTED;
+  b.p.Win = view(W);
+  b.p.W32 = w.W32;
+  b.p.Om = w.Om;
+  b.p.r = (int)r;
+  b.p.c = (int)c;
+  b.p.k = k;
+  b.p.seed = seed;
+  b.p.bar = nullptr;
+  b.p.cnt = nullptr;
+  b.p.part = nullptr;
+  b.p.status = dev_status;
+  b.p.rank_out = rank_out;
+  *static_cast<FusedProg*>(prog_out) = b.p;
+  *k_out = k;
+  return QMCUR_OK;
+}
+
+qmcur_status pinv_each_launch(const void* dprogs, const int* dorder, int count, int kmax,
+                              cudaStream_t st) {
+  const size_t smem = fused_smem(kmax);
+  if (cudaFuncSetAttribute(k_pinv_fused_each, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  k_pinv_fused_each<<<count, kFusedThreads, smem, st>>>(static_cast<const FusedProg*>(dprogs), dorder);
+  return cuda_ok(cudaGetLastError());
 }
 
 }  // namespace qmcur

@@ -242,6 +242,7 @@ __host__ __device__ constexpr size_t sm_chol_bytes() {
 struct SolveJobs {
   QPtr Y0, Y1, Z0, Z1;
   int rows0, rows;
+  int vb, vg;   // this CTA's index and the number of CTAs sharing the rows
 };
 
 // One of two plane sets, selected field by field (selecting between the two
@@ -257,7 +258,8 @@ __device__ __forceinline__ QPtr qptr_pick(bool second, const QPtr& a, const QPtr
 
 // Row i of the CTA's rows (row-warp i, or past the row warps: the plain row
 // solve takes those once R is complete).
-__device__ __forceinline__ int solve_row_of(int i) { return blockIdx.x + gridDim.x * i; }
+// (vb, vg): the CTA's index among the vg CTAs that share the solve.
+__device__ __forceinline__ int solve_row_of(int i, int vb, int vg) { return vb + vg * i; }
 
 // Panel warps of order k (their sub-partitions are 0 .. pw - 1), row warps
 // (the warps of the other sub-partitions), and the row-warp index of a warp.
@@ -284,7 +286,7 @@ struct SolveRow {
     for (int u = 0; u < U; ++u) t[u] = make_float4(0.f, 0.f, 0.f, 0.f);
     const int ri = solve_row_index(warp, k);
     if (ri < 0) return;
-    const int rg = solve_row_of(ri);
+    const int rg = solve_row_of(ri, sj.vb, sj.vg);
     if (rg >= sj.rows) return;
     row = rg;
     job = rg < sj.rows0 ? 0 : 1;
@@ -518,7 +520,7 @@ __device__ __forceinline__ int sm_chol_from(int need, const QPtr& G, int k, floa
 // Only the upper triangle of G is read.  A non-positive or non-finite pivot
 // sets ILL_CONDITIONED and continues with a tiny pivot.  With sj, rpk must be
 // in shared memory.  Returns n, the number of row warps: the rows
-// solve_row_of(i), i < n, of the solves Z = Y R^-1 were done along the way;
+// solve_row_of(i, vb, vg), i < n, of the solves Z = Y R^-1 were done along the way;
 // the other rows (all of them when n = 0) are left to the caller.
 __device__ __forceinline__ int sm_chol(const QPtr& G, int k, float* rpk, int32_t* status,
                                         unsigned char* smraw, const SolveJobs* sj = nullptr) {

@@ -264,7 +264,7 @@ class Batch:
             "info": (9, torch.int32)}
 
     def __init__(self, As, cs, rs, rank_caps=None, sampler=SAMPLER_NORM, seed=0, rcond=1e-10,
-                 max_sweeps=0, stream=None):
+                 max_sweeps=0, stream=None, pinv_method=PINV_JACOBI_FP64):
         self.As = list(As)
         n = len(self.As)
         self.shapes = [(a.shape[1], a.shape[2], int(c), int(r)) for a, c, r in zip(self.As, cs, rs)]
@@ -272,7 +272,7 @@ class Batch:
         carr = (ctypes.c_int64 * n)(*[int(x) for x in cs])
         rarr = (ctypes.c_int64 * n)(*[int(x) for x in rs])
         kap = None if rank_caps is None else (ctypes.c_int32 * n)(*[int(x) for x in rank_caps])
-        o = Opts(sampler, PREC_FP32, seed, 0, 0, rcond, 0, max_sweeps, 0, 0)
+        o = Opts(sampler, PREC_FP32, seed, 0, 0, rcond, 0, max_sweeps, pinv_method, 0)
         self.status = status_tensor(self.As[0].device)
         self.handle = ctypes.c_void_p()
         _check(lib().qmcur_batch_plan(n, descs, carr, rarr, kap, ctypes.byref(o),
