@@ -4,9 +4,10 @@
 // replayed (qmcur_batch_run).
 //
 // Stages (Algorithm 1 per problem, U = W^+ with the rank cap):
-//   k_batch_norms    one CTA per problem: column and row squared norms
-//                    (FP32 runs of 4 planes x 8 entries carried in FP64, fixed
-//                    order), ||A||_F^2, the probabilities (Sec. 3.1);
+//   k_batch_norm_chunk, k_batch_norm_fold   column and row squared norms (FP32
+//                    runs of 4 planes x 8 entries carried in FP64, fixed
+//                    order; A read once, in 32-row chunks), ||A||_F^2, the
+//                    probabilities (Sec. 3.1);
 //   k_batch_sample   one CTA per index set per problem (the Philox sampler of
 //                    the single-problem path, stream_id = problem index);
 //   k_batch_gather   C, R, W per problem;
@@ -56,6 +57,7 @@ struct BatchProblem {
   int32_t* info;           // {rank, sweeps, status}
   int tile_base2;          // first tile of this problem in the second GEMM's list
   int tiles2;              // its number of tiles
+  int64_t colpart_off;     // its column partials in the norms' scratch (doubles)
 };
 
 struct GTile {
@@ -78,14 +80,37 @@ __device__ __forceinline__ void stf4(const QView& v, int64_t i, int64_t j, float
 }
 
 // ----------------------------------------------------------------- norms -
-__global__ void __launch_bounds__(256) k_batch_norms(const BatchProblem* probs, int norm,
-                                                     int32_t* status) {
-  const BatchProblem& P = probs[blockIdx.x];
+// Two passes.  k_batch_norm_chunk: CTA (chunk, b) takes rows 32 chunk ..
+// 32 chunk + 31 of problem b, reading each entry once from HBM: the rows'
+// squared norms (one warp per row, lanes over columns, FP32 runs of 8
+// entries carried in FP64, a warp tree) are complete; the columns' sums over
+// the chunk (one thread per column, FP32 runs of 8 rows, in order) go to
+// colpart.  k_batch_norm_fold: one CTA per problem adds the chunks' column
+// sums in chunk order, forms ||A||_F^2 and the probabilities (Sec. 3.1).
+constexpr int kNormChunk = 32;
+
+__global__ void __launch_bounds__(256) k_batch_norm_chunk(const BatchProblem* probs,
+                                                          double* colpart_base) {
+  const BatchProblem& P = probs[blockIdx.y];
   const int m = P.m, n = P.n;
-  __shared__ double red[256];
-  // rows: one warp per row, lanes over columns, warp tree in FP64
+  const int i0 = blockIdx.x * kNormChunk;
+  if (i0 >= m) return;
+  const int i1 = i0 + kNormChunk < m ? i0 + kNormChunk : m;
+  double* colpart = colpart_base + P.colpart_off + (int64_t)blockIdx.x * n;
+  for (int j = threadIdx.x; j < n; j += 256) {
+    double s = 0.0;
+    for (int r0 = i0; r0 < i1; r0 += 8) {
+      float f = 0.f;
+      for (int i = r0; i < r0 + 8 && i < i1; ++i) {
+        const float4 a = ldf4(P.A, i, j);
+        f = fmaf(a.x, a.x, f); f = fmaf(a.y, a.y, f); f = fmaf(a.z, a.z, f); f = fmaf(a.w, a.w, f);
+      }
+      s += (double)f;
+    }
+    colpart[j] = s;
+  }
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int i = warp; i < m; i += 8) {
+  for (int i = i0 + warp; i < i1; i += 8) {
     double s = 0.0;
     for (int j0 = 0; j0 < n; j0 += 32 * 8) {
       float f = 0.f;
@@ -99,18 +124,19 @@ __global__ void __launch_bounds__(256) k_batch_norms(const BatchProblem* probs, 
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) P.row_p[i] = s;
   }
-  // columns: one thread per column, rows in order, FP32 runs of 8 rows
+}
+
+__global__ void __launch_bounds__(256) k_batch_norm_fold(const BatchProblem* probs,
+                                                         const double* colpart_base, int norm,
+                                                         int32_t* status) {
+  const BatchProblem& P = probs[blockIdx.x];
+  const int m = P.m, n = P.n, chunks = (m + kNormChunk - 1) / kNormChunk;
+  const double* colpart = colpart_base + P.colpart_off;
+  __shared__ double red[256];
   double tot = 0.0;
   for (int j = threadIdx.x; j < n; j += 256) {
     double s = 0.0;
-    for (int i0 = 0; i0 < m; i0 += 8) {
-      float f = 0.f;
-      for (int i = i0; i < i0 + 8 && i < m; ++i) {
-        const float4 a = ldf4(P.A, i, j);
-        f = fmaf(a.x, a.x, f); f = fmaf(a.y, a.y, f); f = fmaf(a.z, a.z, f); f = fmaf(a.w, a.w, f);
-      }
-      s += (double)f;
-    }
+    for (int c = 0; c < chunks; ++c) s += colpart[(int64_t)c * n + j];
     P.col_p[j] = s;
     tot += s;
   }
@@ -468,6 +494,8 @@ struct BatchPlan {
   int* order = nullptr;       // device: problems, largest first
   void* pinv_arena = nullptr;
   int kmax = 0;
+  double* colpart = nullptr;  // the norms' per-chunk column sums
+  int max_chunks = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   qmcur_opts opts{};
@@ -475,7 +503,8 @@ struct BatchPlan {
 
 static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st) {
   const int norm = p->opts.sampler == QMCUR_SAMPLER_NORM;
-  k_batch_norms<<<p->count, 256, 0, st>>>(p->dprobs, norm, p->status);
+  k_batch_norm_chunk<<<dim3(p->max_chunks, p->count), 256, 0, st>>>(p->dprobs, p->colpart);
+  k_batch_norm_fold<<<p->count, 256, 0, st>>>(p->dprobs, p->colpart, norm, p->status);
   SampleArgs base{};
   base.seed = p->opts.seed;
   base.norm = norm;
@@ -547,6 +576,7 @@ static void free_plan(BatchPlan* p) {
   cudaFree(p->progs);
   cudaFree(p->order);
   cudaFree(p->pinv_arena);
+  cudaFree(p->colpart);
   delete p;
 }
 
@@ -671,6 +701,19 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     cudaMemcpyAsync(p->order, ord.data(), count * sizeof(int), cudaMemcpyHostToDevice, stream);
     // the host copies above must be complete before the vectors go away
     if (cudaStreamSynchronize(stream) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
+  }
+  {
+    int64_t coff = 0;
+    for (int b = 0; b < count; ++b) {
+      const int chunks = (p->host[b].m + kNormChunk - 1) / kNormChunk;
+      p->host[b].colpart_off = coff;
+      coff += (int64_t)chunks * p->host[b].n;
+      p->max_chunks = std::max(p->max_chunks, chunks);
+    }
+    if (p->max_chunks > 65535 || cudaMalloc(&p->colpart, (size_t)coff * sizeof(double)) != cudaSuccess) {
+      free_plan(p);
+      return QMCUR_ERR_CUDA;
+    }
   }
   if (cudaMalloc(&p->dprobs, count * sizeof(BatchProblem)) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
   cudaMemcpyAsync(p->dprobs, p->host.data(), count * sizeof(BatchProblem), cudaMemcpyHostToDevice, stream);
