@@ -258,6 +258,12 @@ def gemm_check(Q, A, D, prec, stream, reps=5):
     return out
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# kernels that can be the dominant one, from one ncu capture of the current
+# code (profiles/qgemm_tc_pinv_gauss2048_rank50_bf16mixed.md).
+NCU_TRAFFIC = {("pinv", "subspace"): 1.551616e6}
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -451,7 +457,9 @@ def run_ours(args):
         "gemm_tflops": gemm_tflops, "gemm_tflops_plain_fp32": gchk["tflops_fp32"],
         "gemm_rel_err_vs_fp64_oracle": gchk["rel_err"], "rel_residual": rel,
         "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
-                     "unit": unit, "frac": achieved / peak, "traffic": None,
+                     "unit": unit, "frac": achieved / peak,
+                     "traffic": NCU_TRAFFIC.get((dom, args.pinv)) if args.prec != "fp32" else None,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes read + write)",
                      "peak_source": pk_kind},
         "e2e": {"value": replica_value(world, args.steps, e2e_ms), "unit": "decompositions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
