@@ -888,12 +888,24 @@ int t_splits(int64_t n, int64_t c, const TcPlan& p1, int64_t kp1) {
   return (kiters + per - 1) / per;
 }
 
+// Tile width of Z = C T: 128, or 64 or 32 when 128-wide tiles would leave
+// more than half the SMs idle (a small output: its epilogue may be
+// nonlinear, so K cannot always be split; narrower tiles also give two
+// accumulators in TMEM, so the epilogue overlaps the next tile).
+constexpr int kZTileFloor = 76;
+int z_bn(int64_t m, int64_t n) {
+  int bn = kBn2;
+  while (bn > 32 && ((m + BM - 1) / BM) * ((n + bn - 1) / bn) < kZTileFloor) bn /= 2;
+  return bn;
+}
+
 // K splits of a stored Z = C T whose tiles are too few to occupy the GPU
 // (a small output with a long K, e.g. the paper's core C^+ (X R^+)); 1 when
 // the tiles suffice.  From the shape alone; every split at least 4 stages.
 constexpr int kZSplitItems = 152, kMaxZSplits = 32;
 int z_splits(int64_t m, int64_t n, const TcPlan& p2, int64_t kp2) {
-  const int64_t tiles = ((m + BM - 1) / BM) * ((n + kBn2 - 1) / kBn2);
+  const int bn = z_bn(m, n);
+  const int64_t tiles = ((m + BM - 1) / BM) * ((n + bn - 1) / bn);
   const int kiters = p2.nterms * (int)(kp2 / p2.epr);
   int64_t ns = kZSplitItems / tiles;
   if (ns > kMaxZSplits) ns = kMaxZSplits;
@@ -930,7 +942,8 @@ TcWs carve_tc(Carve& cv, const TcPlan& p1, const TcPlan& p2, int64_t m, int64_t 
   w.A2 = cv.take<char>((size_t)(p2.npieces * 4 * m * kp2 * es));
   w.B2 = cv.take<char>((size_t)(p2.npieces * 4 * n * kp2 * es));
   w.P = cv.take<float>((size_t)(t_splits(n, c, p1, kp1) * 4 * kp2 * rup(n, 4)));
-  const int64_t tiles = ((m + BM - 1) / BM) * ((n + kBn2 - 1) / kBn2);
+  const int bn2 = z_bn(m, n);
+  const int64_t tiles = ((m + BM - 1) / BM) * ((n + bn2 - 1) / bn2);
   w.partial = cv.take<double>((size_t)(2 * tiles));
   w.done = cv.take<unsigned>(1);
   const int nsz = z_splits(m, n, p2, kp2);
@@ -1008,6 +1021,18 @@ qmcur_status launch_gemm(const CUtensorMap& ma, const CUtensorMap& mb, const TcP
   }
 }
 
+// Z = C T at the tile width z_bn chose.
+template <bool BF16>
+qmcur_status launch_z(int bn, const CUtensorMap& ma, const CUtensorMap& mb, const TcParams& p,
+                      cudaStream_t st) {
+  switch (bn) {
+    case 128: return launch_gemm<BF16, 128, false>(ma, mb, p, st);
+    case 64: return launch_gemm<BF16, 64, false>(ma, mb, p, st);
+    case 32: return launch_gemm<BF16, 32, false>(ma, mb, p, st);
+    default: return QMCUR_ERR_INVALID_ARG;
+  }
+}
+
 }  // namespace
 
 size_t tc_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec) {
@@ -1051,7 +1076,7 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
   if (!make_map(&mA1, w.B1, pl.bf16, n, kp1, pl.npieces, BM) ||
       !make_map(&mB1, w.A1, pl.bf16, c, kp1, pl.npieces, kBn1) ||
       !make_map(&mA2, w.A2, pl2.bf16, m, kp2, pl2.npieces, BM) ||
-      !make_map(&mB2, w.B2, pl2.bf16, n, kp2, pl2.npieces, kBn2))
+      !make_map(&mB2, w.B2, pl2.bf16, n, kp2, pl2.npieces, z_bn(m, n)))
     return QMCUR_ERR_CUDA;
   const int nsplit = t_splits(n, c, pl, kp1);
   TcParams p1{};
@@ -1118,12 +1143,12 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
     if ((s = launch_gemm<true, kBn1, true>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
     k_t_reduce<true><<<rgrid, 256, 0, st>>>(w.P, nsplit, p1.zsplit, kp2 * ldp, ldp, n, c, kp2,
                                             pl2.npieces, w.B2, w.done);
-    if ((s = launch_gemm<true, kBn2, false>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
+    if ((s = launch_z<true>(z_bn(m, n), mA2, mB2, p2, st)) != QMCUR_OK) return s;
   } else {
     if ((s = launch_gemm<false, kBn1, true>(mA1, mB1, p1, st)) != QMCUR_OK) return s;
     k_t_reduce<false><<<rgrid, 256, 0, st>>>(w.P, nsplit, p1.zsplit, kp2 * ldp, ldp, n, c, kp2,
                                              pl2.npieces, w.B2, w.done);
-    if ((s = launch_gemm<false, kBn2, false>(mA2, mB2, p2, st)) != QMCUR_OK) return s;
+    if ((s = launch_z<false>(z_bn(m, n), mA2, mB2, p2, st)) != QMCUR_OK) return s;
   }
   if (Z != nullptr && nsz > 1) {
     const dim3 zgrid((unsigned)((n + 255) / 256), (unsigned)m);

@@ -303,8 +303,10 @@ TC_TOL = {Q.PREC_TF32X3: 1e-5, Q.PREC_BF16X6: 1e-5, Q.PREC_BF16X3: 6e-5,
 @pytest.mark.parametrize("prec", [Q.PREC_BF16X3, Q.PREC_BF16X6, Q.PREC_TF32X3,
                                   Q.PREC_BF16_MIXED])
 @pytest.mark.parametrize("m,n,c,r", [(128, 64, 64, 64), (200, 300, 40, 30), (129, 65, 7, 9),
-                                     (300, 700, 200, 120), (1, 1, 1, 1)])
+                                     (300, 700, 200, 120), (1, 1, 1, 1), (2048, 512, 48, 40)])
 def test_reconstruct_tensor_cores(prec, m, n, c, r):
+    # Z = C T's tile width follows the tile count: 2048 x 512 takes 64 columns,
+    # the smaller shapes 32 (and K splits), the full-size tests 128
     rng = np.random.default_rng(m * 7 + n + c)
     C, U, R = (rng.standard_normal(s).astype(np.float32) for s in
                ((4, m, c), (4, c, r), (4, r, n)))
