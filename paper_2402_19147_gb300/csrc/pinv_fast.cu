@@ -12,20 +12,22 @@
 // orth() is CholeskyQR (G = Y^H Y = R^H R, Q = Y R^-1), applied twice
 // (CholeskyQR2) where orthonormality to working accuracy matters.
 //
-// Every step is a small quaternion GEMM (op(X) op(Y), op in {N, H}), a
-// one-CTA Cholesky factorisation, or a triangular solve Z = Y R^-1 (one warp
-// per row).  All ~30 steps run in ONE cooperative
-// persistent kernel of 512-thread CTAs (two GEMM tile workers of 256 threads
-// each); a bounded grid barrier separates consecutive steps (no launch gaps).
-// A GEMM step is a list of work items (16 x 16 output tile, k-range) dealt to
-// the workers one SM at a time.  Steps with fewer tiles than workers split
-// their k-range; every split writes its partial tile to the workspace and
-// the last of a tile's splits to finish (an atomic count per tile) sums the
-// partials in split order and writes the tile, so the result does not depend
-// on timing.  A Gram step Y^H Y feeds only the Cholesky, which reads the
-// upper triangle, so only tiles on or above the diagonal are formed.  A
-// Cholesky step runs on CTA 0; a triangular-solve step stages R in every
-// CTA's shared memory and deals the rows to the warps, one SM at a time.
+// Every step is a small quaternion GEMM (op(X) op(Y), op in {N, H}) or a
+// solve: G = R^H R (Cholesky) then Z = Y R^-1 (one warp per row).  The 20
+// steps run in ONE persistent kernel of 512-thread CTAs (two GEMM tile
+// workers of 256 threads each) over a virtual grid of vg CTAs: the whole GPU
+// with a bounded grid barrier between steps (k_pinv_fused, one problem), or
+// one CTA with a CTA barrier (k_pinv_fused_each, one problem per CTA, the
+// batched path).  A GEMM step is a list of work items (16 x 16 output tile,
+// k-range) dealt to the workers one SM at a time.  Steps with fewer tiles
+// than workers split their k-range; every split writes its partial tile to
+// the workspace and the last of a tile's splits to finish (an atomic count
+// per tile) sums the partials in split order and writes the tile, so the
+// result does not depend on timing.  A Gram step Y^H Y feeds only the
+// Cholesky, which reads the upper triangle, so only tiles on or above the
+// diagonal are formed.  In a solve step every CTA that owns rows factors G
+// itself (identical arithmetic, so identical factors, without a barrier),
+// and the warps that hold rows solve them along with the factorisation.
 #include "small_impl.cuh"
 
 namespace qmcur {
