@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "batch512_uneven", "color512x768_rank31_mr70",
+                    choices=[WORKLOAD, "color4096_smooth100", "batch512_uneven",
+                             "color512x768_rank31_mr70",
                              "qsvd_vs_qmcur"])
     ap.add_argument("--core", default="intersection", choices=["intersection", "paper"],
                     help="decomposition workload: U = W^+ (default) or the paper's C^+ X R^+")
@@ -53,9 +54,22 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config():
+DECOMP_WORKLOADS = (WORKLOAD, "color4096_smooth100")
+
+
+def workload_name(args=None):
+    """The decomposition workload: the 2048 x 2048 rank-50 matrix (default), or
+    the 4096 x 4096 colour field (c = r = 500, rank cap 100)."""
+    if args is not None and getattr(args, "workload", None) in DECOMP_WORKLOADS:
+        return args.workload
+    return WORKLOAD
+
+
+def workload_config(args=None):
     from paper_2402_19147_gb300 import synth
-    w = dict(synth.WORKLOADS[WORKLOAD])
+    w = dict(synth.WORKLOADS[workload_name(args)])
+    if args is not None and getattr(args, "sampler", None):
+        w["sampler"] = args.sampler
     return w
 
 
@@ -143,15 +157,15 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2402_19147_gb300 import synth
-    w = workload_config()
-    A = synth.make(WORKLOAD)
+    w = workload_config(args)
+    A = synth.make(workload_name(args))
     rate, done, el = oracle_rate(A, w, args.cpu_seconds)
     cores = cpu_threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "decompositions/s",
         "n_gpus": args.gpus, "steps": done, "warmup": 0, "ms_per_step": 1e3 * el / done,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "m": w["m"], "n": w["n"],
+        "data": "synthetic", "config": {"workload": workload_name(args), "m": w["m"], "n": w["n"],
                                         "c": w["c"], "r": w["r"], "rank_cap": w["rank_cap"],
                                         "sampler": w["sampler"]},
         "cpu_baseline": {"value": rate, "unit": "decompositions/s", "cores": cores,
@@ -296,12 +310,12 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = workload_config()
+    w = workload_config(args)
     m, n, c, r = w["m"], w["n"], w["c"], w["r"]
     prec = Q.PREC_NAMES[args.prec]
     sampler = Q.SAMPLER_NORM if w["sampler"] == "norm" else Q.SAMPLER_UNIFORM
     pinv_method = Q.PINV_SUBSPACE_FP32 if args.pinv == "subspace" else Q.PINV_JACOBI_FP64
-    A_np = synth.make(WORKLOAD)
+    A_np = synth.make(workload_name(args))
     A = torch.from_numpy(A_np).to(dev)
     D = Q.Decomposition(m, n, c, r, prec, device=dev)
     stream = torch.cuda.current_stream()
@@ -442,13 +456,23 @@ def run_ours(args):
         else:
             peak = pk["bf16_tflops"]
     gemm_tflops = work["gemm"][1] / (stage_ms["gemm"] / args.steps / 1e3) / 1e12
+    # split paths: the tensor pipe runs several BF16 (or TF32) products per
+    # quaternion flop; the effective peak divides the measured one by the
+    # flop-weighted product count (T = U R and Z = C T may differ, BF16X6 /
+    # BF16X3 in the mixed split; TF32 runs at half the BF16 rate)
+    f1, f2 = 32.0 * c * r * n, 32.0 * m * c * n
+    nprod = {"bf16x3": (3, 3), "bf16x6": (6, 6), "bf16mixed": (6, 3), "tf32x3": (6, 6)}
+    eff = None
+    if args.prec in nprod:
+        p1, p2 = nprod[args.prec]
+        eff = peaks()[0]["bf16_tflops"] * (f1 + f2) / (p1 * f1 + p2 * f2)
     gchk = gemm_check(Q, A, D, Q.PREC_NAMES[args.prec], stream)
     line = {
         "metric": METRIC, "value": value, "unit": "decompositions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.prec == "fp32" else args.prec, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": m, "n": n, "c": c, "r": r,
+        "config": {"workload": workload_name(args), "m": m, "n": n, "c": c, "r": r,
                    "rank_cap": w["rank_cap"], "sampler": w["sampler"], "gemm_prec": args.prec,
                    "pinv": "fp32-subspace" if args.pinv == "subspace" else "fp64-jacobi",
                    "parallelism": "replicas" if world > 1 else "single",
@@ -458,6 +482,8 @@ def run_ours(args):
         "gemm_rel_err_vs_fp64_oracle": gchk["rel_err"], "rel_residual": rel,
         "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak,
+                     "gemm_effective_peak": eff,
+                     "gemm_frac_of_effective_peak": gemm_tflops / eff if eff else None,
                      "traffic": NCU_TRAFFIC.get((dom, args.pinv)) if args.prec != "fp32" else None,
                      "traffic_unit": "bytes per launch (ncu dram__bytes read + write)",
                      "peak_source": pk_kind},
@@ -540,11 +566,11 @@ def run_core_paper(args):
     from paper_2402_19147_gb300 import synth
     from oracle import qmcur as O
     torch.cuda.set_device(0)
-    w = workload_config()
+    w = workload_config(args)
     m, n, c, r, k = w["m"], w["n"], w["c"], w["r"], w["rank_cap"]
     sampler = Q.SAMPLER_NORM if w["sampler"] == "norm" else Q.SAMPLER_UNIFORM
     prec = Q.PREC_NAMES[args.prec]
-    A_np = synth.make(WORKLOAD)
+    A_np = synth.make(workload_name(args))
     A = torch.from_numpy(A_np).cuda()
     D = Q.Decomposition(m, n, c, r, prec)
     f = dict(dtype=torch.float32, device="cuda")
@@ -601,7 +627,7 @@ def run_core_paper(args):
             "value": 1e3 / ms, "unit": "decompositions/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": m, "n": n, "c": c, "r": r, "rank_cap": k,
+            "config": {"workload": workload_name(args), "m": m, "n": n, "c": c, "r": r, "rank_cap": k,
                        "sampler": w["sampler"], "core": "C^+ X R^+ (FP32 subspace inverses)",
                        "gemm_prec": args.prec, "l2": "flushed between steps (256 MiB write)"},
             "stage_ms": stage_ms, "core_rel_err_vs_fp64_oracle": err,
@@ -813,6 +839,8 @@ def main():
         run_qsvd_vs_qmcur(args)
     elif args.core == "paper":
         run_core_paper(args)
+    elif args.workload not in DECOMP_WORKLOADS:
+        raise SystemExit("unknown workload " + args.workload)
     else:
         run_ours(args)
 
