@@ -272,6 +272,70 @@ def gemm_check(Q, A, D, prec, stream, reps=5):
     return out
 
 
+def fp64_check(Q, A, D, w, prec, sampler, stream, steps=10, warmup=3, rows=256):
+    """The decomposition against the FP64 pseudo-inverse, on one step's own
+    index sets: the pseudo-inverse's error against the oracle's (LAPACK QSVD in
+    FP64) and the error of C U R on a sample of rows against the oracle's
+    C W^+ R in FP64.  Then the whole step timed with the FP64 one-sided Jacobi
+    pseudo-inverse in place of the selected one (same probabilities, sampler,
+    gathers and GEMMs), and that pseudo-inverse's own error."""
+    import torch
+    from oracle import qmcur as O
+    m, n, c, r = D.m, D.n, D.c, D.r
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=A.device)
+    Wn = D.W.cpu().numpy()
+    Uo, k_o, _ = O.pinv_truncated(Wn, w["rcond"], w["rank_cap"])
+    sel = torch.from_numpy(np.random.default_rng(0).choice(m, size=min(rows, m), replace=False))
+    Cs = D.C[:, sel.to(D.C.device)].double().cpu().numpy()
+    Rn = D.R.double().cpu().numpy()
+    Zo = O.reconstruct(Cs, Uo, Rn)
+
+    def errors():
+        Z = torch.empty(4, m, n, dtype=torch.float32, device=A.device)
+        Q.reconstruct(D.C, D.U.float(), D.R, prec, Z, D.ws, D.status, stream)
+        torch.cuda.synchronize()
+        Zs = Z[:, sel.to(Z.device)].double().cpu().numpy()
+        Un = D.U.cpu().numpy()
+        return (float(np.linalg.norm(Un - Uo) / np.linalg.norm(Uo)),
+                float(np.linalg.norm(Zs - Zo) / np.linalg.norm(Zo)))
+
+    out = {"oracle_rank": int(k_o), "rows_sampled": int(sel.numel())}
+    out["pinv_rel_err"], out["cur_rel_err"] = errors()
+    # the FP64 Jacobi pseudo-inverse of the same W
+    Q.pinv_core(D.W, D.U, w["rcond"], w["rank_cap"], 0, D.rank, D.sigma, D.ws, D.status,
+                stream, method=Q.PINV_JACOBI_FP64)
+    torch.cuda.synchronize()
+    Q.check_status(D.status, "FP64 Jacobi pseudo-inverse")
+    fp64 = {"oracle_rank": int(k_o)}
+    fp64["pinv_rel_err"], fp64["cur_rel_err"] = errors()
+
+    def step(seed):
+        Q.probs(A, sampler, D.col_p, D.row_p, None, D.ws, D.status, stream)
+        Q.sample(A, sampler, D.col_p, D.row_p, c, r, seed, 0, D.J, D.I, D.C, D.R, D.W,
+                 ws=D.ws, status=D.status, stream=stream)
+        Q.pinv_core(D.W, D.U, w["rcond"], w["rank_cap"], 0, D.rank, D.sigma, D.ws, D.status,
+                    stream, method=Q.PINV_JACOBI_FP64)
+        Q.residual(A, D.out3, D.C, D.U, D.R, prec, None, None, D.ws, D.status, stream)
+
+    for s_ in range(warmup):
+        step(2000 + s_)
+    torch.cuda.synchronize()
+    ms = 0.0
+    for s_ in range(steps):
+        flush.fill_(s_ & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(s_)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    Q.check_status(D.status, "FP64 Jacobi steps")
+    fp64.update({"value": 1e3 * steps / ms, "unit": "decompositions/s", "steps": steps,
+                 "warmup": warmup, "ms_per_step": ms / steps,
+                 "sweeps_last_step": int(D.rank[1].item())})
+    return out, fp64
+
+
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # kernels that can be the dominant one, from one ncu capture of the current
 # code (profiles/qgemm_tc_pinv_gauss2048_rank50_bf16mixed.md).
@@ -467,6 +531,7 @@ def run_ours(args):
         p1, p2 = nprod[args.prec]
         eff = peaks()[0]["bf16_tflops"] * (f1 + f2) / (p1 * f1 + p2 * f2)
     gchk = gemm_check(Q, A, D, Q.PREC_NAMES[args.prec], stream)
+    pchk, fp64 = fp64_check(Q, A, D, w, prec, sampler, stream)
     line = {
         "metric": METRIC, "value": value, "unit": "decompositions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
@@ -480,6 +545,13 @@ def run_ours(args):
         "stage_ms": {k: v / args.steps for k, v in stage_ms.items()},
         "gemm_tflops": gemm_tflops, "gemm_tflops_plain_fp32": gchk["tflops_fp32"],
         "gemm_rel_err_vs_fp64_oracle": gchk["rel_err"], "rel_residual": rel,
+        # the selected pseudo-inverse against the oracle's FP64 QSVD one on the
+        # same W, and C U R against the oracle's C W^+ R (FP64) on sampled rows
+        "pinv_rel_err_vs_fp64_oracle": pchk["pinv_rel_err"],
+        "cur_rel_err_vs_fp64_oracle": pchk["cur_rel_err"],
+        "cur_check_rows": pchk["rows_sampled"],
+        # the whole step with the FP64 one-sided Jacobi pseudo-inverse instead
+        "fp64_jacobi_pinv": fp64,
         "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak,
                      "gemm_effective_peak": eff,
