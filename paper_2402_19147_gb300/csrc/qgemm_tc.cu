@@ -22,7 +22,8 @@
 // Kernel: persistent, warp-specialised (10 warps).  Warp 0 lane 0 issues TMA
 // loads into a ring of 3-5 stages; warp 1 owns the TMEM allocation and its
 // lane 0 issues the MMAs (M = 128, N = BN per MMA: 112 for T^T = R^T U, 128
-// for Z = C T; the four output planes side by side in TMEM, with two
+// or 112 for Z = C T, narrower for small outputs; the four output planes
+// side by side in TMEM, with two
 // accumulator buffers where 2 x 4 x BN columns fit in 512, so that the
 // epilogue of one tile overlaps the MMAs of the next); warps 2-9 are the
 // epilogue, two per 32-lane TMEM sub-partition (one output row per thread),
@@ -891,11 +892,22 @@ int t_splits(int64_t n, int64_t c, const TcPlan& p1, int64_t kp1) {
 // Tile width of Z = C T: 128, or 64 or 32 when 128-wide tiles would leave
 // more than half the SMs idle (a small output: its epilogue may be
 // nonlinear, so K cannot always be split; narrower tiles also give two
-// accumulators in TMEM, so the epilogue overlaps the next tile).
+// accumulators in TMEM, so the epilogue overlaps the next tile).  Otherwise
+// 112 when that takes fewer waves x width over the 152 SMs: a tile's time
+// grows with its width (the MMAs are bound by shared-memory reads, which
+// scale with N), and 2048 columns in 19 tiles of 112 fill two whole waves
+// where 16 tiles of 128 leave the second wave a third empty.
 constexpr int kZTileFloor = 76;
+constexpr int kWaveSms = 152;
 int z_bn(int64_t m, int64_t n) {
   int bn = kBn2;
   while (bn > 32 && ((m + BM - 1) / BM) * ((n + bn - 1) / bn) < kZTileFloor) bn /= 2;
+  if (bn == kBn2) {
+    const int64_t mt = (m + BM - 1) / BM;
+    const int64_t w128 = (mt * ((n + 127) / 128) + kWaveSms - 1) / kWaveSms;
+    const int64_t w112 = (mt * ((n + 111) / 112) + kWaveSms - 1) / kWaveSms;
+    if (w112 * 112 < w128 * 128) bn = 112;
+  }
   return bn;
 }
 
@@ -1027,6 +1039,7 @@ qmcur_status launch_z(int bn, const CUtensorMap& ma, const CUtensorMap& mb, cons
                       cudaStream_t st) {
   switch (bn) {
     case 128: return launch_gemm<BF16, 128, false>(ma, mb, p, st);
+    case 112: return launch_gemm<BF16, 112, false>(ma, mb, p, st);
     case 64: return launch_gemm<BF16, 64, false>(ma, mb, p, st);
     case 32: return launch_gemm<BF16, 32, false>(ma, mb, p, st);
     default: return QMCUR_ERR_INVALID_ARG;

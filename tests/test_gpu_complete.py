@@ -76,8 +76,11 @@ def _check(X0, mask, X, S, I, J, Xn, delta, tol):
 
 
 @pytest.mark.parametrize("prec", [Q.PREC_FP32, Q.PREC_BF16_MIXED])
-def test_step_matches_oracle_jacobi(prec):
-    X0, mask = _case(333, 515, 6, seed=21, p_observed=0.5)
+@pytest.mark.parametrize("m,n", [(333, 515), (1100, 1500)])
+def test_step_matches_oracle_jacobi(prec, m, n):
+    # the split path's update runs 32-column tiles at 333 x 515 and
+    # 112-column tiles (ragged rows, 44-column last tile) at 1100 x 1500
+    X0, mask = _case(m, n, 6, seed=21, p_observed=0.5)
     X, S = _one_step(X0, mask, 24, 20, 6, prec, Q.PINV_JACOBI_FP64)
     I, J, Xn, delta, _ = _oracle_step(X0, mask, S, 6, Q.SAMPLER_UNIFORM)
     _check(X0, mask, X, S, I, J, Xn, delta, 2e-5)

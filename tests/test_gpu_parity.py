@@ -303,10 +303,12 @@ TC_TOL = {Q.PREC_TF32X3: 1e-5, Q.PREC_BF16X6: 1e-5, Q.PREC_BF16X3: 6e-5,
 @pytest.mark.parametrize("prec", [Q.PREC_BF16X3, Q.PREC_BF16X6, Q.PREC_TF32X3,
                                   Q.PREC_BF16_MIXED])
 @pytest.mark.parametrize("m,n,c,r", [(128, 64, 64, 64), (200, 300, 40, 30), (129, 65, 7, 9),
-                                     (300, 700, 200, 120), (1, 1, 1, 1), (2048, 512, 48, 40)])
+                                     (300, 700, 200, 120), (1, 1, 1, 1), (2048, 512, 48, 40),
+                                     (1100, 1500, 48, 40)])
 def test_reconstruct_tensor_cores(prec, m, n, c, r):
     # Z = C T's tile width follows the tile count: 2048 x 512 takes 64 columns,
-    # the smaller shapes 32 (and K splits), the full-size tests 128
+    # the smaller shapes 32 (and K splits), 1100 x 1500 and 2048 x 2048 take
+    # 112 (ragged rows and a 44-column last tile here), 4096 x 4096 128
     rng = np.random.default_rng(m * 7 + n + c)
     C, U, R = (rng.standard_normal(s).astype(np.float32) for s in
                ((4, m, c), (4, c, r), (4, r, n)))
@@ -321,8 +323,10 @@ def test_reconstruct_tensor_cores(prec, m, n, c, r):
 
 @pytest.mark.parametrize("prec", [Q.PREC_BF16X3, Q.PREC_BF16X6, Q.PREC_TF32X3,
                                   Q.PREC_BF16_MIXED])
-def test_residual_tensor_cores_fused(prec):
-    m, n, c, r = 333, 515, 24, 20
+@pytest.mark.parametrize("m,n", [(333, 515), (1100, 1500)])
+def test_residual_tensor_cores_fused(prec, m, n):
+    # 333 x 515 runs 32-column tiles, 1100 x 1500 112-column tiles
+    c, r = 24, 20
     A, _ = synth.lowrank_gaussian(m, n, 6, seed=5, noise_rel=1e-2)
     out = O.qmcur(A.astype(np.float64), c, r, sampler=O.SAMPLER_UNIFORM, seed=4, rank_cap=6)
     U32_ = out["U"].astype(np.float32)
