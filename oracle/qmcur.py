@@ -32,6 +32,8 @@ numpy.linalg.pinv in the real and complex cases, exact recovery on exactly
 low-rank inputs, Lemma 1, Philox known-answer vectors, brute-force inverse CDF,
 chi-square frequencies of the sampler).
 """
+import math
+
 import numpy as np
 
 from .quat import (as_q, qmatmul, conj_transpose, complex_adjoint,
@@ -41,7 +43,6 @@ from .philox import philox4x32_10
 SAMPLER_UNIFORM = 0
 SAMPLER_NORM = 1
 
-PREFIX_BLOCKS = 256     # number of contiguous blocks of the fixed-order prefix sum
 
 
 # ----------------------------------------------------------------- Sec. 3.1 -
@@ -77,41 +78,35 @@ def probabilities(A, sampler=SAMPLER_NORM):
 
 
 # -------------------------------------------------------- Algorithm 1, 1-2 -
-def blocked_prefix(p):
-    """Inclusive prefix sums of p in a fixed association order.
+def fixed_point_prefix(p):
+    """Probabilities as 64-bit fixed-point integers and their prefix sums.
 
-    The n entries are cut into PREFIX_BLOCKS contiguous blocks of length
-    L = ceil(n / PREFIX_BLOCKS).  Inside block b the sums run left to right;
-    the block totals are chained left to right into offsets O_b; the prefix
-    at entry k of block b is O_b + s_k.  Every operation is one IEEE double
-    addition rounded to nearest, so any implementation that follows this
-    order gets the same bits.  Returns (P, S) with S the grand total.
+    With M = max p_k = f 2^e (f in [1, 2)) and B = 63 - ceil(log2 n), every
+    p_k becomes q_k = floor(p_k 2^E), E = B - 1 - e: an exact scaling by a
+    power of two, then truncation.  So q_k < 2^B, the total S = sum q_k is
+    below 2^63, and the largest entry keeps B bits (52 at n = 2048).  The
+    prefix sums P_k = q_0 + ... + q_k are exact integers, so they do not
+    depend on the order of the additions (a parallel scan gives the same
+    bits) and they are non-decreasing.  Returns (P, S) as Python-int-valued
+    uint64 arrays / int; an entry with q_k = 0 can never be drawn.
     """
     p = np.asarray(p, dtype=np.float64)
     n = p.shape[0]
-    L = -(-n // PREFIX_BLOCKS)
-    P = np.empty(n)
-    offset = 0.0
-    for b in range(PREFIX_BLOCKS):
-        lo = b * L
-        hi = min(n, lo + L)
-        s = 0.0
-        for k in range(lo, hi):
-            s = float(p[k]) if k == lo else s + float(p[k])
-            P[k] = offset + s
-        offset = offset + s
-    return P, offset
+    M = float(p.max()) if n else 0.0
+    if not M > 0.0:
+        return np.zeros(n, dtype=np.uint64), 0
+    e = math.frexp(M)[1] - 1                       # M = f 2^e, f in [1, 2)
+    B = 63 - (n - 1).bit_length()                  # 63 - ceil(log2 n)
+    E = B - 1 - e
+    q = [int(math.ldexp(float(x), E)) for x in p]  # exact scaling, truncated
+    P = np.array(np.cumsum(np.array(q, dtype=object)), dtype=np.uint64)
+    return P, int(P[-1])
 
 
 def _draw_word(seed, stream_id, which, t):
     key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
     ctr = (t & 0xFFFFFFFF, (t >> 32) & 0xFFFFFFFF, stream_id & 0xFFFFFFFF, which)
     return philox4x32_10(ctr, key)
-
-
-def uniform53(x0, x1):
-    """u = ((x0 << 32 | x1) >> 11) * 2^-53, an exact double in [0, 1)."""
-    return float(((x0 << 32) | x1) >> 11) * (2.0 ** -53)
 
 
 def sample(p, count, seed, stream_id, which, sampler, max_attempts=0):
@@ -123,10 +118,10 @@ def sample(p, count, seed, stream_id, which, sampler, max_attempts=0):
       the accepted set is returned sorted ascending.
     * Draw t uses Philox4x32-10 with key = (seed_lo, seed_hi) and counter =
       (t_lo, t_hi, stream_id, which), which = 0 for columns, 1 for rows.
-    * QMCUR_length (norm): u = uniform53(x0, x1), target = u * S (one rounded
-      multiply), index = first k with P[k] > target, P and S from
-      ``blocked_prefix``.  If no such k exists (target rounded up to S) the
-      last index with p > 0 is taken.
+    * QMCUR_length (norm): w = (x0 << 32 | x1) >> 11, a 53-bit integer;
+      target = (w S) >> 53, exact in integers and below S; index = first k
+      with P[k] > target, P and S from ``fixed_point_prefix``.  So index k
+      is drawn with probability q_k / S up to 2^-53.
     * QMCUR_uniform: index = (x0 * n) >> 32 (integer multiply-shift).
     * At most max_attempts draws (0 selects 64*count + 1024); running out
       raises RuntimeError (the library reports QMCUR_ERR_SAMPLE_LIMIT).
@@ -138,11 +133,10 @@ def sample(p, count, seed, stream_id, which, sampler, max_attempts=0):
     if max_attempts <= 0:
         max_attempts = 64 * count + 1024
     if sampler == SAMPLER_NORM:
-        support = int(np.count_nonzero(p > 0))
+        P, S = fixed_point_prefix(p)
+        support = int(np.count_nonzero(np.diff(P, prepend=np.uint64(0)))) if S else 0
         if support < count:
             raise ValueError("fewer positive probabilities than requested indices")
-        P, S = blocked_prefix(p)
-        last_pos = int(np.nonzero(p > 0)[0][-1])
     chosen = []
     taken = np.zeros(n, dtype=bool)
     t = 0
@@ -152,10 +146,9 @@ def sample(p, count, seed, stream_id, which, sampler, max_attempts=0):
         x0, x1, _, _ = _draw_word(seed, stream_id, which, t)
         t += 1
         if sampler == SAMPLER_NORM:
-            target = uniform53(x0, x1) * S
-            k = int(np.searchsorted(P, target, side="right"))
-            if k >= n:
-                k = last_pos
+            w = ((x0 << 32) | x1) >> 11
+            target = (w * S) >> 53
+            k = int(np.searchsorted(P, np.uint64(target), side="right"))
         else:
             k = (x0 * n) >> 32
         if not taken[k]:

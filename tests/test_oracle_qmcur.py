@@ -1,5 +1,7 @@
 """Pins of the QMCUR oracle (Algorithm 1, Sec. 3.1-3.2) against closed forms,
 invariants, special cases reducing to numpy/LAPACK, brute force and statistics."""
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -64,31 +66,38 @@ def test_probabilities_errors():
 
 # ------------------------------------------------------------------ sampling -
 @pytest.mark.parametrize("n", [1, 5, 256, 257, 1000, 4096])
-def test_blocked_prefix_properties(n):
+def test_fixed_point_prefix_properties(n):
     rng = np.random.default_rng(n)
     p = rng.random(n)
     p[rng.random(n) < 0.2] = 0.0
-    P, S = O.blocked_prefix(p)
-    assert P[-1] == S
-    assert np.all(np.diff(P) >= 0)
-    assert np.allclose(P, np.cumsum(p), rtol=1e-13, atol=0)
-    if n <= O.PREFIX_BLOCKS:
-        # one entry per block: the order degenerates to the plain sequential chain
-        acc = 0.0
-        for k in range(n):
-            acc = acc + p[k]
-            assert P[k] == acc
+    p[0] = 0.75                        # a maximum with a known exponent (e = -1)
+    P, S = O.fixed_point_prefix(p)
+    B = 63 - (n - 1).bit_length()
+    q = np.diff(P, prepend=np.uint64(0)).astype(object)
+    # the largest entry is scaled into [2^(B-1), 2^B): 0.75 -> 0.75 2^B exactly
+    assert int(q[0]) == 3 << (B - 2)
+    # every entry is the exact truncation p_k 2^E, E = B, checked in rationals
+    for k in range(n):
+        x = Fraction(p[k]) * (1 << B)
+        assert int(q[k]) == x.numerator // x.denominator
+    # exact integer sums: S below 2^63, P non-decreasing, zeros never drawn
+    assert S == int(sum(q)) < (1 << 63) and P[-1] == S
+    assert np.all(np.diff(P.astype(object)) >= 0)
+    assert all(int(q[k]) == 0 for k in range(n) if p[k] == 0.0)
+    # scale invariance: multiplying p by a power of two gives the same integers
+    P2, S2 = O.fixed_point_prefix(p * 2.0 ** -40)
+    assert np.array_equal(P2, P) and S2 == S
 
 
 def test_inverse_cdf_brute_force():
     rng = np.random.default_rng(7)
     p = rng.random(300)
     p[::7] = 0.0
-    P, S = O.blocked_prefix(p)
+    P, S = O.fixed_point_prefix(p)
     for _ in range(2000):
-        target = rng.random() * S
-        k = int(np.searchsorted(P, target, side="right"))
-        lin = next(i for i in range(len(P)) if P[i] > target)
+        target = int(rng.integers(0, S))
+        k = int(np.searchsorted(P, np.uint64(target), side="right"))
+        lin = next(i for i in range(len(P)) if int(P[i]) > target)
         assert k == lin and p[k] > 0
 
 
@@ -111,12 +120,11 @@ def test_sample_sets_and_determinism():
 def test_first_draw_follows_p_chi_square():
     # frequency of the first draw over many seeds matches p (chi-square, 7 dof)
     p = np.array([0.05, 0.1, 0.15, 0.2, 0.0, 0.25, 0.05, 0.1, 0.1])
-    P, S = O.blocked_prefix(p)
     N = 20000
     counts = np.zeros(len(p))
     for s in range(N):
-        x0, x1, _, _ = O._draw_word(s, 0, 0, 0)
-        counts[int(np.searchsorted(P, O.uniform53(x0, x1) * S, side="right"))] += 1
+        J, _ = O.sample(p, 1, seed=s, stream_id=0, which=0, sampler=O.SAMPLER_NORM)
+        counts[int(J[0])] += 1
     assert counts[4] == 0
     nz = p > 0
     chi2 = np.sum((counts[nz] - N * p[nz]) ** 2 / (N * p[nz]))
