@@ -154,17 +154,19 @@ qmcur_status qmcur_probs_noalloc(const qmcur_qmat* A, int32_t sampler, double* c
  *   Draws are without replacement: a draw repeating an accepted index is
  *   rejected.  Draw t uses Philox4x32-10 (Salmon et al., SC'11) with key
  *   (seed_lo, seed_hi) and counter (t_lo, t_hi, stream_id, which), which = 0
- *   for J, 1 for I.  Norm sampler: u = ((x0<<32|x1)>>11) 2^-53, target = u*S,
- *   index = first k with P[k] > target, P the prefix sums of the probabilities
- *   taken in 256 contiguous blocks (within-block left to right, block totals
- *   chained left to right, every addition IEEE double round-to-nearest).
+ *   for J, 1 for I.  Norm sampler, in exact integers: with M = max p_k =
+ *   f 2^e (f in [1, 2)) and B = 63 - ceil(log2 N), q_k = floor(p_k 2^(B-1-e)),
+ *   P the prefix sums of the q_k, S = P[N-1] < 2^63; w = (x0<<32|x1)>>11,
+ *   target = (w S) >> 53, index = first k with P[k] > target.  Probabilities
+ *   must be finite and >= 0; an entry below M 2^-B is never drawn.
  *   Uniform sampler: index = (x0 * n) >> 32, col_p / row_p may be NULL.
  *   max_attempts <= 0 selects 64*count + 1024 draws per set.
  *   J (device int32[c]) and I (device int32[r]) are written sorted ascending.
  *   C, R, W may each be NULL; C and R take A's dtype or the other one (F32/F64
  *   conversion on the fly); W may be F32 or F64.
  *   Requires 1 <= c <= n, 1 <= r <= m.
- *   Device errors: INSUFFICIENT_SUPPORT, SAMPLE_LIMIT.
+ *   Device errors: INSUFFICIENT_SUPPORT, SAMPLE_LIMIT, NONFINITE (a
+ *   non-finite probability).
  */
 qmcur_status qmcur_sample(const qmcur_qmat* A, int32_t sampler, const double* col_p,
                           const double* row_p, int64_t c, int64_t r, uint64_t seed,

@@ -2,11 +2,13 @@
 // {q_i}, then gather C = X(:,J), R = X(I,:) and the intersection W = X(I,J).
 //
 // k_sample runs one CTA per index set (CTA 0 -> J, CTA 1 -> I).
-//  * Norm sampler: the prefix sums of p are taken in 256 contiguous blocks
-//    (thread b sums block b left to right, thread 0 chains the 256 block
-//    totals left to right, then every entry adds its block offset); every
-//    operation is an explicit round-to-nearest double add/multiply, so the
-//    bits match any other implementation of the same order.
+//  * Norm sampler, in exact integers: with M = max p_k = f 2^e and
+//    B = 63 - ceil(log2 N), q_k = floor(p_k 2^(B - 1 - e)) (an exact
+//    power-of-two scaling, then truncation), so the sum S of the q_k is
+//    below 2^63.  Their prefix sums are exact, so the CTA takes them in any
+//    order: thread b sums block b, a shuffle scan gives the block offsets.
+//    A draw's 53-bit word w gives target = (w S) >> 53 < S, and the index
+//    is the first k with P[k] > target (binary search).
 //  * Draw t: Philox4x32-10 (Salmon et al., SC'11), key (seed_lo, seed_hi),
 //    counter (t_lo, t_hi, stream_id, which).  256 draws are generated in
 //    parallel per round and accepted in counter order, repeats rejected (a
@@ -272,8 +274,8 @@ qmcur_status launch_gather(const qmcur_qmat* A, const int32_t* J, const int32_t*
 
 size_t sample_ws_bytes(int64_t m, int64_t n) {
   Carve c(nullptr, 0);
-  c.take<double>((size_t)n);
-  c.take<double>((size_t)m);
+  c.take<unsigned long long>((size_t)n);
+  c.take<unsigned long long>((size_t)m);
   c.take<uint32_t>((size_t)((n + 31) / 32));
   c.take<uint32_t>((size_t)((m + 31) / 32));
   c.take<int32_t>(2);
@@ -295,8 +297,8 @@ qmcur_status launch_sample(const qmcur_qmat* A, int32_t sampler, const double* c
   if (W && (!valid_qmat(W) || W->rows != r || W->cols != c)) return QMCUR_ERR_INVALID_ARG;
   Carve cv(ws, ws_bytes);
   SampleArgs a;
-  a.P[0] = cv.take<double>((size_t)n);
-  a.P[1] = cv.take<double>((size_t)m);
+  a.P[0] = cv.take<unsigned long long>((size_t)n);
+  a.P[1] = cv.take<unsigned long long>((size_t)m);
   a.bits[0] = cv.take<uint32_t>((size_t)((n + 31) / 32));
   a.bits[1] = cv.take<uint32_t>((size_t)((m + 31) / 32));
   a.attempts_out = cv.take<int32_t>(2);

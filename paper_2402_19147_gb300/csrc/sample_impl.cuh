@@ -23,7 +23,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 }
 
 // First k in [0, N) with P[k] > target, N if none.
-__device__ __forceinline__ int64_t upper_bound(const double* P, int64_t N, double target) {
+__device__ __forceinline__ int64_t upper_bound(const unsigned long long* P, int64_t N,
+                                               unsigned long long target) {
   int64_t lo = 0, hi = N;
   while (lo < hi) {
     int64_t mid = (lo + hi) >> 1;
@@ -38,7 +39,7 @@ struct SampleArgs {
   int64_t N[2];
   int64_t count[2];
   int32_t* out[2];
-  double* P[2];
+  unsigned long long* P[2];   // scratch: the prefix sums when they do not fit shared memory
   uint32_t* bits[2];
   uint64_t seed;
   uint32_t stream_id;
@@ -75,6 +76,35 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* warp_tot) {
   return r;
 }
 
+// Exclusive prefix sum of one uint64 per thread over the CTA (kSampleThreads);
+// integer sums, so the order of the additions does not matter.
+__device__ __forceinline__ unsigned long long block_exclusive_scan_u64(unsigned long long v,
+                                                                       unsigned long long* warp_tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long own = lane < kSampleThreads / 32 ? warp_tot[lane] : 0ull;
+    unsigned long long t = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kSampleThreads / 32) warp_tot[lane] = t - own;   // exclusive
+  }
+  __syncthreads();
+  const unsigned long long r = warp_tot[warp] + x - v;
+  __syncthreads();
+  return r;
+}
+
 // One index set (set 0: J over columns, 1: I over rows) by one CTA of
 // kSampleThreads threads; `dyn` is the CTA's dynamic shared memory.
 //
@@ -95,27 +125,29 @@ __device__ __forceinline__ void sample_one_set(const SampleArgs& a, int set, int
   // Dynamic shared memory: the acceptance bitmap (and the prefix sums when
   // they fit), so that the acceptance and the binary searches stay on chip.
   uint32_t* bits = reinterpret_cast<uint32_t*>(dyn);
-  double* P = P_in_smem ? reinterpret_cast<double*>(dyn + ((words * 4 + 15) / 16) * 16) : a.P[set];
+  unsigned long long* P =
+      P_in_smem ? reinterpret_cast<unsigned long long*>(dyn + ((words * 4 + 15) / 16) * 16)
+                : a.P[set];
 
-  __shared__ double blk_total[kPrefixBlocks];
-  __shared__ double blk_off[kPrefixBlocks];
+  __shared__ unsigned long long warp_tot64[kSampleThreads / 32];
+  __shared__ double red_max[kSampleThreads / 32];
   __shared__ long long red_sup[kSampleThreads / 32];
-  __shared__ long long red_last[kSampleThreads / 32];
-  __shared__ double S_sh;
-  __shared__ int64_t last_pos_sh;
+  __shared__ unsigned long long S_sh;
+  __shared__ int E_sh;
   __shared__ int abort_sh;
   __shared__ int64_t cand[kSampleThreads];
   __shared__ int64_t accepted_sh;
   __shared__ int64_t used_sh;
   __shared__ int warp_tot[kSampleThreads / 32];
-  static_assert(kPrefixBlocks == kSampleThreads, "one prefix block per thread");
-  static_assert(kPrefixBlocks % 16 == 0, "chain batches of 16");
 
   for (int64_t w = tid; w < words; w += kSampleThreads) bits[w] = 0u;
-  if (tid == 0) { abort_sh = 0; accepted_sh = 0; used_sh = 0; S_sh = 0.0; last_pos_sh = -1; }
+  if (tid == 0) { abort_sh = 0; accepted_sh = 0; used_sh = 0; S_sh = 0ull; E_sh = 0; }
 
+  static_assert(kPrefixBlocks == kSampleThreads, "one prefix block per thread");
   if (a.norm) {
-    // stage p (coalesced, eight loads in flight per thread)
+    // stage p as doubles (coalesced, eight loads in flight per thread) and
+    // take its maximum (exact in any order)
+    double pmax = 0.0;
     for (int64_t k0 = tid; k0 < N; k0 += 8 * kSampleThreads) {
       double v[8];
 #pragma unroll
@@ -126,64 +158,65 @@ __device__ __forceinline__ void sample_one_set(const SampleArgs& a, int set, int
 #pragma unroll
       for (int h = 0; h < 8; ++h) {
         const int64_t k = k0 + (int64_t)h * kSampleThreads;
-        if (k < N) P[k] = v[h];
+        if (k < N) {
+          reinterpret_cast<double*>(P)[k] = v[h];
+          pmax = fmax(pmax, v[h]);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pmax = fmax(pmax, __shfl_xor_sync(0xffffffffu, pmax, o));
+    if (lane == 0) red_max[warp] = pmax;
+    __syncthreads();
+    if (tid == 0) {
+      double M = red_max[0];
+      for (int w = 1; w < kSampleThreads / 32; ++w) M = fmax(M, red_max[w]);
+      if (!isfinite(M)) {
+        abort_sh = 1;
+        set_status(a.status, QMCUR_ERR_NONFINITE);
+      } else if (!(M > 0.0)) {
+        abort_sh = 1;
+        set_status(a.status, QMCUR_ERR_INSUFFICIENT_SUPPORT);
+      } else {
+        // q_k = floor(p_k 2^E), E = B - 1 - e with M = f 2^e, B = 63 - ceil(log2 N)
+        const int clog = N > 1 ? 64 - __clzll((unsigned long long)(N - 1)) : 0;
+        E_sh = (63 - clog) - 1 - ilogb(M);
       }
     }
     __syncthreads();
-    // block b = tid: running sum of its L entries left to right
+    if (abort_sh) return;
+    const int E = E_sh;
+    // block b = tid: q_k and their running sum left to right, in place
     const int64_t L = (N + kPrefixBlocks - 1) / kPrefixBlocks;
     const int64_t lo = (int64_t)tid * L;
     const int64_t hi = lo + L < N ? lo + L : N;
-    double s = 0.0;
-    long long sup = 0, last = -1;
+    unsigned long long run = 0ull;
+    long long sup = 0;
     for (int64_t k = lo; k < hi; ++k) {
-      const double pk = P[k];
-      s = (k == lo) ? pk : __dadd_rn(s, pk);
-      P[k] = s;
-      if (pk > 0.0) { ++sup; last = k; }
+      const double pk = reinterpret_cast<const double*>(P)[k];
+      const unsigned long long q = pk > 0.0 ? __double2ull_rz(ldexp(pk, E)) : 0ull;
+      run += q;
+      P[k] = run;
+      sup += q != 0ull;
     }
-    blk_total[tid] = (lo < hi) ? s : 0.0;
-    // support count and last positive index: warp then CTA reductions
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      sup += __shfl_xor_sync(0xffffffffu, sup, o);
-      const long long ol = __shfl_xor_sync(0xffffffffu, last, o);
-      last = ol > last ? ol : last;
-    }
-    if (lane == 0) { red_sup[warp] = sup; red_last[warp] = last; }
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) sup += __shfl_xor_sync(0xffffffffu, sup, o);
+    if (lane == 0) red_sup[warp] = sup;
+    const unsigned long long off = block_exclusive_scan_u64(run, warp_tot64);   // syncs
+    for (int64_t k = lo; k < hi; ++k) P[k] += off;
     if (tid == 0) {
-      // block totals chained left to right (the defined order), read in batches
-      double o = 0.0;
-      for (int b0 = 0; b0 < kPrefixBlocks; b0 += 16) {
-        double tv[16];
-#pragma unroll
-        for (int h = 0; h < 16; ++h) tv[h] = blk_total[b0 + h];
-#pragma unroll
-        for (int h = 0; h < 16; ++h) {
-          blk_off[b0 + h] = o;
-          o = __dadd_rn(o, tv[h]);
-        }
-      }
-      S_sh = o;
-      long long support = 0, lastp = -1;
-      for (int w = 0; w < kSampleThreads / 32; ++w) {
-        support += red_sup[w];
-        if (red_last[w] > lastp) lastp = red_last[w];
-      }
-      last_pos_sh = lastp;
+      long long support = 0;
+      for (int w = 0; w < kSampleThreads / 32; ++w) support += red_sup[w];
       if (support < count) { abort_sh = 1; set_status(a.status, QMCUR_ERR_INSUFFICIENT_SUPPORT); }
     }
     __syncthreads();
-    const double off = blk_off[tid];
-    for (int64_t k = lo; k < hi; ++k) P[k] = __dadd_rn(off, P[k]);
+    if (tid == 0) S_sh = P[N - 1];
   }
   __syncthreads();
   if (abort_sh) return;
 
   const uint2 key = make_uint2((unsigned)(a.seed & 0xffffffffu), (unsigned)(a.seed >> 32));
-  const double S = S_sh;
-  const int64_t last_pos = last_pos_sh;
+  const unsigned long long S = S_sh;
   const int64_t max_att = a.max_attempts[set];
   for (int64_t base = 0; base < max_att; base += kSampleThreads) {
     const int64_t t = base + tid;
@@ -192,11 +225,12 @@ __device__ __forceinline__ void sample_one_set(const SampleArgs& a, int set, int
       const uint4 x = philox4x32_10(
           make_uint4((unsigned)(t & 0xffffffff), (unsigned)(t >> 32), a.stream_id, (unsigned)set), key);
       if (a.norm) {
-        const uint64_t w = (((uint64_t)x.x << 32) | (uint64_t)x.y) >> 11;
-        const double u = __dmul_rn((double)w, 0x1.0p-53);
-        const double target = __dmul_rn(u, S);
+        // target = (w S) >> 53 for the 53-bit word w: below S, so some P[k] exceeds it
+        const unsigned long long w = (((unsigned long long)x.x << 32) | (unsigned long long)x.y) >> 11;
+        const unsigned long long lo64 = w * S, hi64 = __umul64hi(w, S);
+        const unsigned long long target = (hi64 << 11) | (lo64 >> 53);
         k = upper_bound(P, N, target);
-        if (k >= N) k = last_pos;
+        if (k >= N) k = N - 1;   // unreachable: P[N - 1] = S > target
       } else {
         k = (int64_t)(((uint64_t)x.x * (uint64_t)N) >> 32);
       }
