@@ -106,6 +106,44 @@ def test_sample_bit_exact_and_gather(sampler, m, n, c, r, seed):
     assert np.array_equal(host(W), Wo)
 
 
+@pytest.mark.parametrize("case", ["wide_range", "subnormal_max", "unnormalised", "n1",
+                                  "one_heavy"])
+def test_sample_fixed_point_edges(case):
+    # explicit probability vectors: the integer scaling is taken from the
+    # largest entry, so entries far below it are never drawn on either side,
+    # a subnormal maximum still scales into B bits, and any positive scale
+    # of p draws the same indices
+    rng = np.random.default_rng(31)
+    n, c = 300, 40
+    if case == "wide_range":
+        c = 10
+        p = 10.0 ** rng.uniform(-30, 0, n)
+    elif case == "subnormal_max":
+        p = rng.random(n) * 2.0 ** -1060
+    elif case == "unnormalised":
+        p = rng.random(n) * 3.7e5
+    elif case == "n1":
+        n, c = 1, 1
+        p = np.array([0.3])
+    else:
+        p = np.full(n, 1e-3)
+        p[17] = 1.0
+    m, r = n, c
+    A_t = dev(np.ones((4, m, n), dtype=np.float32))
+    col_p = torch.tensor(p, dtype=torch.float64, device="cuda")
+    row_p = torch.tensor(p[::-1].copy(), dtype=torch.float64, device="cuda")
+    J, I, *_, st = _sample(A_t, Q.SAMPLER_NORM, col_p, row_p, c, r, 5, 3, gather=False)
+    assert st == 0
+    Jo, _ = O.sample(p, c, 5, 3, 0, Q.SAMPLER_NORM)
+    Io, _ = O.sample(p[::-1].copy(), r, 5, 3, 1, Q.SAMPLER_NORM)
+    assert np.array_equal(host(J), Jo) and np.array_equal(host(I), Io)
+    if case == "unnormalised":
+        # the same draws from p scaled by a power of two
+        J2, I2, *_, st = _sample(A_t, Q.SAMPLER_NORM, col_p * 2.0 ** -30, row_p * 2.0 ** -30,
+                                 c, r, 5, 3, gather=False)
+        assert st == 0 and np.array_equal(host(J2), Jo) and np.array_equal(host(I2), Io)
+
+
 def test_sample_status_codes():
     A = np.zeros((4, 50, 60), dtype=np.float32)
     A[0, :, 3] = 1.0
