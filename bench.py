@@ -103,14 +103,22 @@ def oracle_rate(A, w, seconds):
 
 # -------------------------------------------------------------------- clocks -
 class Clocks:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples of the SM clock and the throttle reasons.  start()
+    returns once the sampler is producing lines, so the timed region that
+    follows it is covered; stop() keeps the samples whose timestamps fall
+    inside [start, stop].  A timed region shorter than the sampling interval
+    has none: then the samples just before and after it are reported, and
+    "window" says so."""
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 10
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.path = None
+        self.begin = self.end = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -118,37 +126,59 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 10.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.005)
+        self.begin = time.time()
 
     def stop(self):
+        self.end = time.time()
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(2.5 * self.INTERVAL_MS / 1e3)     # the sample right after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
+        from datetime import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        samples = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                sm, mx = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
+            samples.append((ts, sm, mx, {nm for nm, v in zip(names, f[6:10])
+                                         if v.lower() == "active"}))
         os.unlink(self.path)
+        inside = [x for x in samples if self.begin <= x[0] <= self.end]
+        window = "inside the timed region"
+        if not inside and samples:
+            before = [x for x in samples if x[0] < self.begin][-1:]
+            after = [x for x in samples if x[0] > self.end][:1]
+            inside = before + after
+            window = "the samples just before and after the timed region (shorter than %d ms)" % (
+                self.INTERVAL_MS)
+        sm = [x[1] for x in inside]
+        reasons = set()
+        for x in inside:
+            reasons |= x[3]
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "sm_max_mhz": max(x[2] for x in inside) if inside else None,
+                "reasons": sorted(reasons), "samples": len(inside), "window": window,
+                "timed_region_s": round(self.end - self.begin, 4)}
 
 
 # --------------------------------------------------------------- reference -
