@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(256) k_split_ops(const __grid_constant__ Split
 #pragma unroll
   for (int q = 1; q < kMaxSplitJobs; ++q)
     if (q < jobs.count && (int)blockIdx.x >= jobs.j[q].first_tile) jb = q;
-  const SplitJob& J = jobs.j[jb];
+  const SplitJob J = jobs.j[jb];   // by value: the fields are read once
   const int tl = (int)blockIdx.x - J.first_tile;
   const int64_t i0 = (int64_t)(tl / J.tiles_k) * kSplitRows, k0 = (int64_t)(tl % J.tiles_k) * kSplitK;
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
@@ -688,11 +688,13 @@ __global__ void __launch_bounds__(256) k_split_ops(const __grid_constant__ Split
   __syncthreads();
   const int64_t k = k0 + 2 * lane;   // kpad is even: k < kpad implies k + 1 < kpad
   if (k >= J.kpad) return;
+  const int64_t plane_stride = J.rows_out * J.kpad;   // between (piece, plane) blocks
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int il = warp + 8 * u;
     const int64_t i = i0 + il;
     if (i >= J.rows_out) break;
+    const int64_t rowoff = i * J.kpad + k;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const float2 x = *reinterpret_cast<const float2*>(&tile[t][il][2 * lane]);
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(256) k_split_ops(const __grid_constant__ Split
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         if (q >= J.npieces) break;
-        const int64_t idx = (((int64_t)q * 4 + t) * J.rows_out + i) * J.kpad + k;
+        const int64_t idx = (int64_t)(q * 4 + t) * plane_stride + rowoff;
         if constexpr (BF16)
           *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(J.dst) + idx) =
               __floats2bfloat162_rn(p0[q], p1[q]);
@@ -768,11 +770,13 @@ __global__ void __launch_bounds__(256) k_t_reduce(const float* __restrict__ P, i
   __syncthreads();
   const int il = 2 * (tid % 16), jr0 = tid / 16;   // columns i0 + il, + 1; rows jr0 + 16 k
   const int64_t i = i0 + il;
+  const int64_t out_stride = rows * kpad;            // between (piece, plane) blocks
 #pragma unroll 1
   for (int k = 0; k < kRedJ / 16; ++k) {
     const int jr = jr0 + 16 * k;
     const int64_t j = j0 + jr;
     if (j >= rows || i >= kpad) continue;   // kpad is even: i + 1 < kpad as well
+    const int64_t rowoff = j * kpad + i;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       float p0[3], p1[3];
@@ -781,7 +785,7 @@ __global__ void __launch_bounds__(256) k_t_reduce(const float* __restrict__ P, i
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
         if (q >= npieces) break;
-        const int64_t idx = (((int64_t)q * 4 + t) * rows + j) * kpad + i;
+        const int64_t idx = (int64_t)(q * 4 + t) * out_stride + rowoff;
         if constexpr (BF16)
           *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(dst) + idx) =
               __floats2bfloat162_rn(p0[q], p1[q]);

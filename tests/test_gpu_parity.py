@@ -32,7 +32,7 @@ def _lib():
 
 
 # ----------------------------------------------------------- probabilities -
-@pytest.mark.parametrize("m,n", [(300, 700), (1, 5), (64, 1025), (257, 33)])
+@pytest.mark.parametrize("m,n", [(300, 700), (1, 5), (64, 1025), (257, 33), (3, 40000)])
 def test_probs_norm_fp32(m, n):
     A = synth.lowrank_gaussian(m, n, 3, seed=m + n, noise_rel=0.1)[0]
     col_p, row_p, fro2, st = probs(dev(A), Q.SAMPLER_NORM)
