@@ -32,8 +32,11 @@ def _lib():
 
 
 # ----------------------------------------------------------- probabilities -
-@pytest.mark.parametrize("m,n", [(300, 700), (1, 5), (64, 1025), (257, 33), (3, 40000)])
+@pytest.mark.parametrize("m,n", [(300, 700), (1, 5), (64, 1025), (257, 33), (3, 40000),
+                                 (333, 516)])
 def test_probs_norm_fp32(m, n):
+    # ragged tiles: 333 x 516 leaves 13 rows in the last row tile and 4
+    # columns in the last column tile; n % 4 != 0 takes scalar loads
     A = synth.lowrank_gaussian(m, n, 3, seed=m + n, noise_rel=0.1)[0]
     col_p, row_p, fro2, st = probs(dev(A), Q.SAMPLER_NORM)
     assert st == 0
