@@ -105,6 +105,21 @@ typedef enum {
 /* Human-readable name of a status code (static string). */
 const char* qmcur_status_str(int32_t status);
 
+/*
+ * qmcur_set_max_ctas - CTA budget of the persistent kernels (the
+ * pseudo-inverse's cooperative launches and the tensor-core GEMMs) that the
+ * calling host thread launches from now on: 0 (the default) = one CTA per
+ * SM; n > 0 = at most n.  The pseudo-inverse is latency-bound and the GEMMs
+ * are throughput-bound, so two decompositions on two streams, each held to
+ * half of the SMs, overlap one's pseudo-inverse with the other's GEMMs.
+ * Keep the budgets of concurrently running streams at or below the SM count
+ * in sum: the pseudo-inverse is a cooperative launch that needs all its CTAs
+ * resident (its grid barriers give up after ~2 s with QMCUR_ERR_TIMEOUT).
+ * qmcur_decompose's opts->max_ctas overrides it for the call.
+ * Host errors: INVALID_ARG (n < 0).
+ */
+qmcur_status qmcur_set_max_ctas(int32_t max_ctas);
+
 /* Bytes of workspace that suffice for every call below on an m x n input with
  * c sampled columns and r sampled rows at precision `prec`. */
 size_t qmcur_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec);
@@ -272,7 +287,10 @@ typedef struct {
   int32_t  rank_cap;     /* <= 0: no cap */
   int32_t  max_sweeps;   /* <= 0: default */
   int32_t  pinv_method;  /* qmcur_pinv_method */
-  int32_t  reserved;
+  int32_t  max_ctas;     /* n > 0: at most n CTAs for the persistent kernels
+                            (pseudo-inverse, tensor-core GEMMs) of this call, as
+                            qmcur_set_max_ctas(n) would give; 0: the calling
+                            thread's budget (qmcur_decompose only) */
 } qmcur_opts;
 
 /*

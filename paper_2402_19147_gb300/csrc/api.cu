@@ -116,6 +116,12 @@ const char* qmcur_status_str(int32_t s) {
   }
 }
 
+qmcur_status qmcur_set_max_ctas(int32_t max_ctas) {
+  if (max_ctas < 0) return QMCUR_ERR_INVALID_ARG;
+  cta_budget_ref() = max_ctas;
+  return QMCUR_OK;
+}
+
 size_t qmcur_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r, int32_t prec) {
   if (m < 1 || n < 1 || c < 1 || r < 1) return 0;
   size_t s = probs_ws_bytes(m, n);
@@ -214,6 +220,8 @@ qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qm
                              cudaStream_t stream) {
   if (A == nullptr || o == nullptr || C == nullptr || R == nullptr || W == nullptr || U == nullptr)
     return QMCUR_ERR_INVALID_ARG;
+  if (o->max_ctas < 0) return QMCUR_ERR_INVALID_ARG;
+  CtaBudgetScope budget(o->max_ctas > 0 ? o->max_ctas : cta_budget_ref());
   qmcur_status s = launch_probs(A, o->sampler, col_p, row_p, nullptr, workspace, ws_bytes, dev_status, stream);
   if (s != QMCUR_OK) return s;
   s = launch_sample(A, o->sampler, col_p, row_p, c, r, o->seed, o->stream_id, o->max_attempts, J, I,

@@ -164,4 +164,23 @@ qmcur_status launch_residual_standalone(const qmcur_qmat* A, const qmcur_qmat* Z
 
 inline qmcur_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? QMCUR_OK : QMCUR_ERR_CUDA; }
 
+// CTA budget of the persistent kernels (the pseudo-inverse's cooperative
+// launches and the tensor-core GEMMs) launched by this host thread: 0 = one
+// CTA per SM.  qmcur_decompose sets it from its options for the duration of
+// the call, so that two decompositions on two streams can each hold part of
+// the SMs at once.
+inline int& cta_budget_ref() {
+  static thread_local int budget = 0;
+  return budget;
+}
+inline int cta_cap(int sms) {
+  const int b = cta_budget_ref();
+  return b > 0 && b < sms ? b : sms;
+}
+struct CtaBudgetScope {
+  int saved;
+  explicit CtaBudgetScope(int b) : saved(cta_budget_ref()) { cta_budget_ref() = b > 0 ? b : 0; }
+  ~CtaBudgetScope() { cta_budget_ref() = saved; }
+};
+
 }  // namespace qmcur

@@ -397,7 +397,7 @@ qmcur_status run_jacobi(const qmcur_qmat* W, const PinvWs& w, int max_sweeps, in
     return QMCUR_ERR_CUDA;
   const int64_t N = (a.nc % 2 == 0) ? a.nc : a.nc + 1;
   int64_t grid = N / 2;
-  const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  const int64_t cap = (int64_t)cta_cap(sms) * (per_sm > 0 ? per_sm : 1);
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
   void* args[] = {&a};

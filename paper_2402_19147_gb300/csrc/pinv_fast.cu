@@ -465,7 +465,7 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
   if (per_sm < 1) return QMCUR_ERR_CUDA;
   const int ri = (int)r, ci = (int)c;
   // one CTA per SM at most: a GEMM step has at most ~2 x SMs useful items
-  const int grid = sms;
+  const int grid = cta_cap(sms);
   ProgBuilder b;
   b.workers = grid * kFusedWorkers;
   build_program(b, w, U, ri, ci, k);

@@ -1013,7 +1013,8 @@ qmcur_status launch_gemm_mode(const CUtensorMap& ma, const CUtensorMap& mb, cons
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return QMCUR_ERR_CUDA;
   const int items = ((p.M + BM - 1) / BM) * ((p.N + BNT - 1) / BNT) * p.nsplit;
-  const int grid = items < sms ? items : sms;
+  const int cap = cta_cap(sms);
+  const int grid = items < cap ? items : cap;
   k_qgemm_tc<BF16, BNT, REV, MODE><<<grid, kTcThreads, TcShape<BNT>::SMEM, st>>>(ma, mb, p);
   return cuda_ok(cudaGetLastError());
 }

@@ -47,7 +47,7 @@ class Opts(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32),
                 ("max_attempts", ctypes.c_int32), ("rcond", ctypes.c_double),
                 ("rank_cap", ctypes.c_int32), ("max_sweeps", ctypes.c_int32),
-                ("pinv_method", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("pinv_method", ctypes.c_int32), ("max_ctas", ctypes.c_int32)]
 
 
 _lib = None
@@ -59,6 +59,7 @@ _I64, _I32, _U32, _U64, _D, _SZ = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint
 # name -> (restype, argtypes); the exported symbols of include/qmcur.h
 SIGNATURES = {
     "qmcur_status_str": (ctypes.c_char_p, [_I32]),
+    "qmcur_set_max_ctas": (_I32, [_I32]),
     "qmcur_workspace_size": (_SZ, [_I64, _I64, _I64, _I64, _I32]),
     "qmcur_probs": (_I32, [_QP, _I32, _P, _P, _P, _P, _SZ, _P, _P]),
     "qmcur_probs_noalloc": (_I32, [_QP, _I32, _P, _P, _P, _P, _P]),
@@ -326,11 +327,20 @@ class Decomposition:
         self.ws = workspace(m, n, c, r, prec, device)
 
 
+def set_max_ctas(max_ctas):
+    """CTA budget of the persistent kernels this thread launches (qmcur_set_max_ctas);
+    0 = one CTA per SM."""
+    _check(lib().qmcur_set_max_ctas(int(max_ctas)), "qmcur_set_max_ctas")
+
+
 def decompose(A, D, sampler=SAMPLER_NORM, seed=0, stream_id=0, rcond=1e-10, rank_cap=0,
-              max_sweeps=0, max_attempts=0, stream=None, pinv_method=PINV_JACOBI_FP64):
-    """One whole QMCUR decomposition of A into the buffers of D (qmcur_decompose)."""
+              max_sweeps=0, max_attempts=0, stream=None, pinv_method=PINV_JACOBI_FP64,
+              max_ctas=0):
+    """One whole QMCUR decomposition of A into the buffers of D (qmcur_decompose).
+    max_ctas > 0 caps the CTAs of its persistent kernels (pseudo-inverse and
+    tensor-core GEMMs), so that decompositions on two streams share the GPU."""
     o = Opts(sampler, D.prec, seed, stream_id, max_attempts, rcond, rank_cap, max_sweeps,
-             pinv_method, 0)
+             pinv_method, max_ctas)
     qs = [qmat(D.C), qmat(D.R), qmat(D.W), qmat(D.U)]
     _check(lib().qmcur_decompose(_ref(qmat(A)), D.c, D.r, ctypes.byref(o), _ptr(D.col_p),
                                  _ptr(D.row_p), _ptr(D.J), _ptr(D.I), *[_ref(q) for q in qs],

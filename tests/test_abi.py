@@ -56,3 +56,6 @@ def test_host_only_calls(libpath):
     for prec in range(6):
         assert Q.workspace_size(2048, 2048, 200, 200, prec) > 0
     assert Q.workspace_size(0, 10, 1, 1, 1) == 0
+    # the CTA budget is host state of the calling thread
+    assert L.qmcur_set_max_ctas(-1) == 1            # INVALID_ARG
+    assert L.qmcur_set_max_ctas(76) == 0 and L.qmcur_set_max_ctas(0) == 0
