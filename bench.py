@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--prec", default="bf16mixed",
                     choices=["fp32", "tf32x3", "bf16x3", "bf16x6", "bf16mixed"])
     ap.add_argument("--pinv", default="subspace", choices=["subspace", "jacobi"])
+    ap.add_argument("--streams", type=int, default=8,
+                    help="decompositions in flight, each stream's persistent kernels on "
+                         "SMs / streams CTAs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default=WORKLOAD,
@@ -463,22 +466,24 @@ def run_ours(args):
     value_seq = replica_value(world, args.steps, t_seq)
     stage_seq = dict(stage_ms)
 
-    # ---- the headline: two decompositions in flight.  Each stream's
-    # persistent kernels (the cooperative pseudo-inverse and the tensor-core
-    # GEMMs) hold half of the SMs, so one decomposition's latency-bound
-    # pseudo-inverse runs beside the other's throughput-bound GEMMs.  The two
-    # budgets sum to the SM count, so both cooperative grids can always be
-    # resident at once.  Inputs larger than L2 stand in for the flush: four
-    # row-rotated copies of A (the same spectrum), cycled.
+    # ---- the headline: NS decompositions in flight on NS streams.  Each
+    # stream's persistent kernels (the cooperative pseudo-inverse and the
+    # tensor-core GEMMs) hold SMs / NS CTAs, so the latency-bound
+    # pseudo-inverses of some decompositions run beside the throughput-bound
+    # GEMMs of others.  The budgets sum to at most the SM count, so all the
+    # cooperative grids can always be resident at once.  Inputs larger than
+    # L2 stand in for the flush: four row-rotated copies of A (the same
+    # spectrum), cycled.
+    NS = max(1, args.streams)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    budget = sms // 2
-    Dp = [D, Q.Decomposition(m, n, c, r, prec, device=dev)]
-    Sp = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    budget = max(1, sms // NS)
+    Dp = [D] + [Q.Decomposition(m, n, c, r, prec, device=dev) for _ in range(NS - 1)]
+    Sp = [torch.cuda.Stream(device=dev) for _ in range(NS)]
     Ain = [A] + [torch.roll(A, shifts=97 * (q + 1), dims=1).contiguous() for q in range(3)]
     in_bytes = sum(x.numel() * x.element_size() for x in Ain)
 
     def pstep(sd, ev=None):
-        b = sd % 2
+        b = sd % NS
         st, Db, Ak = Sp[b], Dp[b], Ain[sd % len(Ain)]
 
         def mark(i):
@@ -505,7 +510,7 @@ def run_ours(args):
         Q.check_status(Db.status, "pipelined warm-up")
     evp = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ends = [torch.cuda.Event() for _ in range(2)]
+    ends = [torch.cuda.Event() for _ in range(NS)]
     clocks = Clocks(torch.cuda.current_device())
     if dist is not None:
         dist.barrier()
@@ -516,7 +521,7 @@ def run_ours(args):
         st.wait_event(p0)
     for sd in range(args.steps):
         pstep(sd, evp[sd])
-    for b in range(2):
+    for b in range(NS):
         ends[b].record(Sp[b])
         cur.wait_event(ends[b])
     p1.record(cur)
@@ -536,22 +541,22 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers (pinned): every step
     # uploads its own input and reads back its results (J, I, U, residual).
-    # As in the headline, two decompositions are in flight on two compute
-    # streams, each held to half of the SMs; buffer set b belongs to stream
-    # b.  The upload of step s + 1 (one copy stream) and the read-back of step
-    # s (another) overlap the decompositions, ordered by events; the timed
+    # As in the headline, NS decompositions are in flight on NS compute
+    # streams with the same CTA budgets; buffer set b belongs to stream b.
+    # The upload of step s + 1 (one copy stream) and the read-back of step s
+    # (another) overlap the decompositions, ordered by events; the timed
     # region spans all K steps, copies included.
     A_host = torch.from_numpy(A_np).pin_memory()
     Ds = Dp
-    Abuf = [torch.empty_like(A), torch.empty_like(A)]
+    Abuf = [torch.empty_like(A) for _ in range(NS)]
     outs = [[torch.empty_like(x, device="cpu").pin_memory() for x in (d.J, d.I, d.U, d.out3)]
             for d in Ds]
     h2d = A_host.numel() * A_host.element_size()
     d2h = sum(o.numel() * o.element_size() for o in outs[0])
     up_s, back_s = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-    up = [torch.cuda.Event() for _ in range(2)]     # input of buffer b uploaded
-    done = [torch.cuda.Event() for _ in range(2)]   # decomposition on buffer b finished
-    back = [torch.cuda.Event() for _ in range(2)]   # results of buffer b read back
+    up = [torch.cuda.Event() for _ in range(NS)]     # input of buffer b uploaded
+    done = [torch.cuda.Event() for _ in range(NS)]   # decomposition on buffer b finished
+    back = [torch.cuda.Event() for _ in range(NS)]   # results of buffer b read back
 
     def upload(b, after=None):
         with torch.cuda.stream(up_s):
@@ -565,26 +570,26 @@ def run_ours(args):
                     rcond=w["rcond"], rank_cap=w["rank_cap"], stream=Sp[b],
                     pinv_method=pinv_method, max_ctas=budget)
 
-    for b in range(2):
+    for b in range(NS):
         Abuf[b].copy_(A)
-        decompose_on(b, b)        # warm both buffer sets
+        decompose_on(b, b)        # warm every buffer set
     torch.cuda.synchronize()
     for Db in Ds:
         Q.check_status(Db.status, "e2e warm-up")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(cur)
-    for st in (up_s, back_s, Sp[0], Sp[1]):
+    for st in [up_s, back_s] + Sp:
         st.wait_event(e0)
     upload(0)
     for s in range(args.steps):
-        b = s % 2
+        b = s % NS
         if s + 1 < args.steps:
-            nb = (s + 1) % 2
-            # step s - 1 no longer reads Abuf[nb]
-            upload(nb, after=done[nb] if s >= 1 else None)
+            nb = (s + 1) % NS
+            # step s + 1 - NS, the buffer's previous user, no longer reads Abuf[nb]
+            upload(nb, after=done[nb] if s + 1 >= NS else None)
         Sp[b].wait_event(up[b])
-        if s >= 2:
-            Sp[b].wait_event(back[b])           # step s - 2's results are read back
+        if s >= NS:
+            Sp[b].wait_event(back[b])           # step s - NS's results are read back
         decompose_on(b, s)
         done[b].record(Sp[b])
         with torch.cuda.stream(back_s):
@@ -592,9 +597,8 @@ def run_ours(args):
             for o, x in zip(outs[b], (Ds[b].J, Ds[b].I, Ds[b].U, Ds[b].out3)):
                 o.copy_(x, non_blocking=True)
             back[b].record(back_s)
-    cur.wait_event(back[(args.steps - 1) % 2])
-    if args.steps > 1:
-        cur.wait_event(back[args.steps % 2])
+    for b in range(min(NS, args.steps)):
+        cur.wait_event(back[b])
     e1.record(cur)
     e1.synchronize()
     e2e_ms = e0.elapsed_time(e1)
@@ -607,26 +611,39 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     work = stage_work(w, args.prec, sweeps, args.pinv)
-    dom = max(stages, key=lambda k: stage_ms[k])
-    bound, amount, unit = work[dom]
-    per_launch_s = stage_ms[dom] / args.steps / 1e3
-    pk, pk_kind = peaks()
-    if unit == "GB/s":
-        achieved = amount / per_launch_s / 1e9
-        peak = pk["hbm_gbs"]
-    else:
-        achieved = amount / per_launch_s / 1e12
-        if dom == "pinv" and args.pinv == "jacobi":
-            peak = alu_peak_tflops("fp64")
-            pk_kind = "nominal FP64 1.25 TFLOP/s"
-        elif dom == "pinv":
-            peak = alu_peak_tflops("fp32")
-            pk_kind = "FP32 CUDA-core 152 SMs x 128 lanes x 2 x 2.07 GHz"
-        elif bound == "alu":
-            peak = alu_peak_tflops("fp32")
-            pk_kind = "FP32 CUDA-core 152 SMs x 128 lanes x 2 x 2.07 GHz"
+
+    def roofline_of(st_ms, share):
+        """The stage that takes the most time on its stream, against the peak
+        of the SMs its persistent kernels hold (share = CTA budget / SMs)."""
+        dom = max(stages, key=lambda k: st_ms[k])
+        bound, amount, unit = work[dom]
+        per_launch_s = st_ms[dom] / args.steps / 1e3
+        pk, pk_kind = peaks()
+        if unit == "GB/s":
+            achieved = amount / per_launch_s / 1e9
+            peak = pk["hbm_gbs"]
         else:
-            peak = pk["bf16_tflops"]
+            achieved = amount / per_launch_s / 1e12
+            if dom == "pinv" and args.pinv == "jacobi":
+                peak = alu_peak_tflops("fp64")
+                pk_kind = "nominal FP64 1.25 TFLOP/s"
+            elif dom == "pinv" or bound == "alu":
+                peak = alu_peak_tflops("fp32")
+                pk_kind = "FP32 CUDA-core 152 SMs x 128 lanes x 2 x 2.07 GHz"
+            else:
+                peak = pk["bf16_tflops"]
+            if share < 1.0:
+                peak *= share
+                pk_kind += "; x %d/%d, the SMs the stream's persistent kernels hold" % (
+                    budget, sms)
+        return {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak,
+                "traffic": NCU_TRAFFIC.get((dom, args.pinv)) if args.prec != "fp32" else None,
+                "traffic_unit": "bytes per launch (ncu dram__bytes read + write)",
+                "peak_source": pk_kind}
+
+    roof = roofline_of(stage_ms, budget / sms if NS > 1 else 1.0)
+    roof_seq = roofline_of(stage_seq, 1.0)
     # the GEMM stage's own rate: from the one-stream run, where it has every SM
     gemm_tflops = work["gemm"][1] / (stage_seq["gemm"] / args.steps / 1e3) / 1e12
     # split paths: the tensor pipe runs several BF16 (or TF32) products per
@@ -650,10 +667,10 @@ def run_ours(args):
                    "rank_cap": w["rank_cap"], "sampler": w["sampler"], "gemm_prec": args.prec,
                    "pinv": "fp32-subspace" if args.pinv == "subspace" else "fp64-jacobi",
                    "parallelism": "replicas" if world > 1 else "single",
-                   "streams": 2, "max_ctas_per_stream": budget,
+                   "streams": NS, "max_ctas_per_stream": budget,
                    "l2": "inputs larger than L2: 4 row-rotated copies of A (%d MiB) cycled"
                          % (in_bytes >> 20)},
-        # per-stage durations on each decomposition's own stream (the two
+        # per-stage durations on each decomposition's own stream (the
         # streams overlap, so these add up to more than ms_per_step)
         "stage_ms": {k: v / args.steps for k, v in stage_ms.items()},
         # the same decompositions one at a time on one stream, every SM each,
@@ -670,18 +687,14 @@ def run_ours(args):
         "cur_check_rows": pchk["rows_sampled"],
         # the whole step with the FP64 one-sided Jacobi pseudo-inverse instead
         "fp64_jacobi_pinv": fp64,
-        "roofline": {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
-                     "unit": unit, "frac": achieved / peak,
-                     "gemm_effective_peak": eff,
-                     "gemm_frac_of_effective_peak": gemm_tflops / eff if eff else None,
-                     "traffic": NCU_TRAFFIC.get((dom, args.pinv)) if args.prec != "fp32" else None,
-                     "traffic_unit": "bytes per launch (ncu dram__bytes read + write)",
-                     "peak_source": pk_kind},
+        "roofline": dict(roof, gemm_effective_peak=eff,
+                         gemm_frac_of_effective_peak=gemm_tflops / eff if eff else None),
+        "roofline_sequential": roof_seq,
         "e2e": {"value": replica_value(world, args.steps, e2e_ms), "unit": "decompositions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "pipelining": "two decompositions in flight on two streams (half the SMs "
-                              "each); step s+1's upload and step s's read-back overlap "
-                              "the decompositions"},
+                "pipelining": "%d decompositions in flight on %d streams (%d CTAs each for "
+                              "the persistent kernels); step s+1's upload and step s's "
+                              "read-back overlap the decompositions" % (NS, NS, budget)},
         "gpu_launches": launches_per_step(args) * args.steps,
         "clocks": clk,
     }

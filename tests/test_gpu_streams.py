@@ -1,6 +1,6 @@
-"""Decompositions on two streams at once, each held to half of the SMs
-(qmcur_opts.max_ctas / qmcur_set_max_ctas), against the same decompositions
-run alone with one CTA per SM.
+"""Decompositions on two or four streams at once, each held to SMs / streams
+CTAs (qmcur_opts.max_ctas / qmcur_set_max_ctas), against the same
+decompositions run alone with one CTA per SM.
 
 * index sets: bit-exact (the sampler does not depend on the CTA budget);
 * FP64 Jacobi pseudo-inverse: bit-exact (each column pair's arithmetic is the
@@ -38,8 +38,9 @@ def _run(A, Ds, streams, seeds, method, k, budget):
         Q.check_status(D.status, "decompose")
 
 
+@pytest.mark.parametrize("nstreams", [2, 4])
 @pytest.mark.parametrize("method", [Q.PINV_SUBSPACE_FP32, Q.PINV_JACOBI_FP64])
-def test_two_streams_half_the_sms_each(method):
+def test_streams_share_the_sms(method, nstreams):
     m, n, c, r, k = 1024, 1536, 80, 72, 20
     A_np, _ = synth.lowrank_gaussian(m, n, k, seed=41, noise_rel=1e-3)
     A = torch.from_numpy(A_np).cuda()
@@ -48,8 +49,8 @@ def test_two_streams_half_the_sms_each(method):
     ref = [Q.Decomposition(m, n, c, r, Q.PREC_BF16_MIXED) for _ in seeds]
     got = [Q.Decomposition(m, n, c, r, Q.PREC_BF16_MIXED) for _ in seeds]
     _run(A, ref, [torch.cuda.current_stream()], seeds, method, k, 0)
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    _run(A, got, streams, seeds, method, k, sms // 2)
+    streams = [torch.cuda.Stream() for _ in range(nstreams)]
+    _run(A, got, streams, seeds, method, k, sms // nstreams)
     for a, b in zip(ref, got):
         assert np.array_equal(host(a.J), host(b.J)) and np.array_equal(host(a.I), host(b.I))
         ua, ub = host(a.U), host(b.U)
