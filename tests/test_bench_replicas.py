@@ -60,3 +60,41 @@ def test_reference_arm_other_ranks_do_no_work(capsys, monkeypatch):
     import argparse
     bench.run_reference(argparse.Namespace(gpus=2, cpu_seconds=0.0))
     assert capsys.readouterr().out == ""
+
+
+def test_clock_samples_kept_inside_the_timed_region(tmp_path, monkeypatch):
+    # the sampler's lines carry timestamps; only those inside [start, stop]
+    # count, and a region shorter than the interval reports its neighbours
+    sys.path.insert(0, ROOT)
+    import bench
+    from datetime import datetime
+
+    def line(ts, sm, reason="Not Active"):
+        stamp = datetime.fromtimestamp(ts).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return "%s, 0, %d, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, %s\n" % (
+            stamp, sm, reason)
+
+    class FakeProc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            pass
+
+    t0 = 1.8e9
+    for lines, begin, end, want in (
+            ([line(t0 - 0.02, 1500), line(t0 + 0.01, 2070), line(t0 + 0.03, 2000),
+              line(t0 + 0.06, 1400, "Active")], t0, t0 + 0.04,
+             {"sm_mhz": 2035.0, "samples": 2, "reasons": []}),
+            ([line(t0 - 0.02, 1980), line(t0 + 0.02, 2070, "Active")], t0, t0 + 0.005,
+             {"sm_mhz": 2025.0, "samples": 2, "reasons": ["sw_power_cap"]})):
+        c = bench.Clocks(0)
+        c.path = str(tmp_path / "clk.csv")
+        with open(c.path, "w") as f:
+            f.writelines(lines)
+        c.proc, c.begin = FakeProc(), begin
+        monkeypatch.setattr(bench.time, "time", lambda: end)
+        monkeypatch.setattr(bench.time, "sleep", lambda s: None)
+        got = c.stop()
+        for k, v in want.items():
+            assert got[k] == v, (k, got)
