@@ -481,6 +481,7 @@ def run_ours(args):
     Sp = [torch.cuda.Stream(device=dev) for _ in range(NS)]
     Ain = [A] + [torch.roll(A, shifts=97 * (q + 1), dims=1).contiguous() for q in range(3)]
     in_bytes = sum(x.numel() * x.element_size() for x in Ain)
+    torch.cuda.synchronize()   # the copies above ran on the current stream, not on Sp
 
     def pstep(sd, ev=None):
         b = sd % NS
@@ -572,6 +573,8 @@ def run_ours(args):
 
     for b in range(NS):
         Abuf[b].copy_(A)
+    torch.cuda.synchronize()      # the copies ran on the current stream, not on Sp
+    for b in range(NS):
         decompose_on(b, b)        # warm every buffer set
     torch.cuda.synchronize()
     for Db in Ds:

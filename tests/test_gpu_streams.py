@@ -29,6 +29,8 @@ def _lib():
 
 
 def _run(A, Ds, streams, seeds, method, k, budget):
+    # the buffers were zeroed on the current stream; the streams below are others
+    torch.cuda.synchronize()
     for i, (D, sd) in enumerate(zip(Ds, seeds)):
         Q.decompose(A, D, sampler=Q.SAMPLER_NORM, seed=sd, stream_id=0, rcond=1e-10,
                     rank_cap=k, stream=streams[i % len(streams)], pinv_method=method,
