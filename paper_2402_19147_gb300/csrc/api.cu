@@ -138,6 +138,7 @@ size_t qmcur_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r, int32_t 
 qmcur_status qmcur_probs(const qmcur_qmat* A, int32_t sampler, double* col_p, double* row_p,
                          double* fro2, void* workspace, size_t ws_bytes, int32_t* dev_status,
                          cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_probs");
   return launch_probs(A, sampler, col_p, row_p, fro2, workspace, ws_bytes, dev_status, stream);
 }
 
@@ -146,6 +147,7 @@ qmcur_status qmcur_sample(const qmcur_qmat* A, int32_t sampler, const double* co
                           uint32_t stream_id, int32_t max_attempts, int32_t* J, int32_t* I,
                           qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W, void* workspace,
                           size_t ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_sample");
   return launch_sample(A, sampler, col_p, row_p, c, r, seed, stream_id, max_attempts, J, I, C, R, W,
                        workspace, ws_bytes, dev_status, stream);
 }
@@ -169,6 +171,7 @@ qmcur_status qmcur_pinv_core(const qmcur_qmat* W, int32_t method, double rcond, 
                              int32_t max_sweeps, qmcur_qmat* U, int32_t* rank_out,
                              double* sigma_out, void* workspace, size_t ws_bytes,
                              int32_t* dev_status, cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_pinv_core");
   return pinv_dispatch(W, method, rcond, rank_cap, max_sweeps, U, rank_out, sigma_out, workspace,
                        ws_bytes, dev_status, stream);
 }
@@ -176,6 +179,7 @@ qmcur_status qmcur_pinv_core(const qmcur_qmat* W, int32_t method, double rcond, 
 qmcur_status qmcur_reconstruct(const qmcur_qmat* C, const qmcur_qmat* U, const qmcur_qmat* R,
                                int32_t prec, qmcur_qmat* Z, void* workspace, size_t ws_bytes,
                                int32_t* dev_status, cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_reconstruct");
   if (Z == nullptr) return QMCUR_ERR_INVALID_ARG;
   return launch_reconstruct(C, U, R, prec, Z, nullptr, nullptr, nullptr, workspace, ws_bytes,
                             dev_status, stream);
@@ -185,6 +189,7 @@ qmcur_status qmcur_residual(const qmcur_qmat* A, const qmcur_qmat* C, const qmcu
                             const qmcur_qmat* R, int32_t prec, const uint8_t* mask,
                             const qmcur_qmat* Z, double* out3, void* workspace,
                             size_t ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_residual");
   if (A == nullptr || out3 == nullptr) return QMCUR_ERR_INVALID_ARG;
   if (Z != nullptr)
     return launch_residual_standalone(A, Z, mask, out3, workspace, ws_bytes, dev_status, stream);
@@ -195,6 +200,7 @@ qmcur_status qmcur_residual(const qmcur_qmat* A, const qmcur_qmat* C, const qmcu
 qmcur_status qmcur_gather(const qmcur_qmat* A, const int32_t* J, const int32_t* I, int64_t c,
                           int64_t r, qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W,
                           cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_gather");
   return launch_gather(A, J, I, c, r, C, R, W, stream);
 }
 
@@ -208,6 +214,7 @@ qmcur_status qmcur_reconstruct_backward(const qmcur_qmat* A, const uint8_t* mask
                                         const qmcur_qmat* R, const qmcur_qmat* W, double scale,
                                         qmcur_qmat* dA, double* loss_out, void* workspace,
                                         size_t ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_reconstruct_backward");
   return launch_backward(A, mask, J, I, C, U, R, W, scale, dA, loss_out, workspace, ws_bytes,
                          dev_status, stream);
 }
@@ -218,6 +225,7 @@ qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qm
                              int32_t* rank_out, double* sigma_out, double* out3,
                              void* workspace, size_t ws_bytes, int32_t* dev_status,
                              cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_decompose");
   if (A == nullptr || o == nullptr || C == nullptr || R == nullptr || W == nullptr || U == nullptr)
     return QMCUR_ERR_INVALID_ARG;
   if (o->max_ctas < 0) return QMCUR_ERR_INVALID_ARG;
@@ -255,6 +263,7 @@ qmcur_status qmcur_core_paper(const qmcur_qmat* X, const qmcur_qmat* C, const qm
                               int32_t method, double rcond, int32_t rank_cap, int32_t prec,
                               qmcur_qmat* Cp, qmcur_qmat* Rp, qmcur_qmat* U, void* workspace,
                               size_t ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_core_paper");
   if (!valid_qmat(X) || !valid_qmat(C) || !valid_qmat(R) || !valid_qmat(Cp) || !valid_qmat(Rp) ||
       !valid_qmat(U))
     return QMCUR_ERR_INVALID_ARG;
@@ -284,6 +293,7 @@ qmcur_status qmcur_qsvd_truncated(const qmcur_qmat* X, int32_t rank, double rcon
                                   int32_t max_sweeps, qmcur_qmat* B, int32_t* rank_out,
                                   double* sigma_out, void* workspace, size_t ws_bytes,
                                   int32_t* dev_status, cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_qsvd_truncated");
   return launch_qsvd_truncated(X, rcond, rank, max_sweeps, B, rank_out, sigma_out, workspace,
                                ws_bytes, dev_status, stream);
 }
@@ -293,6 +303,7 @@ qmcur_status qmcur_complete_step(qmcur_qmat* X, const uint8_t* mask, int64_t c, 
                                  int32_t* I, qmcur_qmat* C, qmcur_qmat* R, qmcur_qmat* W,
                                  qmcur_qmat* U, int32_t* rank_out, double* out3, void* workspace,
                                  size_t ws_bytes, int32_t* dev_status, cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_complete_step");
   if (X == nullptr || o == nullptr || C == nullptr || R == nullptr || W == nullptr ||
       U == nullptr || out3 == nullptr || !valid_qmat(X))
     return QMCUR_ERR_INVALID_ARG;

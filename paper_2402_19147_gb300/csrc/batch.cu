@@ -589,6 +589,7 @@ extern "C" {
 qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t* c, const int64_t* r,
                               const int32_t* rank_cap, const qmcur_opts* opts, void** plan_out,
                               int32_t* dev_status, cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_batch_plan");
   if (count < 1 || A == nullptr || c == nullptr || r == nullptr || opts == nullptr || plan_out == nullptr)
     return QMCUR_ERR_INVALID_ARG;
   if (opts->sampler != QMCUR_SAMPLER_NORM && opts->sampler != QMCUR_SAMPLER_UNIFORM) return QMCUR_ERR_INVALID_ARG;
@@ -787,6 +788,7 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
 }
 
 qmcur_status qmcur_batch_run(void* plan, cudaStream_t stream) {
+  NvtxRange nvtx_range("qmcur_batch_run");
   if (plan == nullptr) return QMCUR_ERR_INVALID_ARG;
   return cuda_ok(cudaGraphLaunch(static_cast<BatchPlan*>(plan)->exec, stream));
 }

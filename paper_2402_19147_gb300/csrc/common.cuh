@@ -3,6 +3,7 @@
 // include/qmcur.h for the storage and error conventions.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -163,6 +164,16 @@ qmcur_status launch_residual_standalone(const qmcur_qmat* A, const qmcur_qmat* Z
                                         size_t ws_bytes, int32_t* dev_status, cudaStream_t st);
 
 inline qmcur_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? QMCUR_OK : QMCUR_ERR_CUDA; }
+
+// A named NVTX range around one C-ABI call, so that a profiler's timeline
+// groups each call's kernels under the entry point's name; without a
+// profiler attached the push and pop do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // CTA budget of the persistent kernels (the pseudo-inverse's cooperative
 // launches and the tensor-core GEMMs) launched by this host thread: 0 = one

@@ -309,6 +309,7 @@ qmcur_status scratch_address(void** out) {
 extern "C" qmcur_status qmcur_probs_noalloc(const qmcur_qmat* A, int32_t sampler, double* col_p,
                                             double* row_p, double* fro2, int32_t* dev_status,
                                             cudaStream_t stream) {
+  qmcur::NvtxRange nvtx_range("qmcur_probs_noalloc");
   using namespace qmcur;
   if (!valid_qmat(A)) return QMCUR_ERR_INVALID_ARG;
   if (probs_ws_bytes(A->rows, A->cols) > kNoAllocScratchBytes) return QMCUR_ERR_UNSUPPORTED;
