@@ -301,6 +301,11 @@ typedef struct {
  *   W (r x c, F64), U (c x r, F64), rank_out[2], sigma_out[min(r,c)] (may be
  *   NULL), out3[3] as in qmcur_residual.  col_p[n], row_p[m] (device) receive
  *   the probabilities.
+ *   opts->max_ctas > 0 holds the persistent kernels of this call to that many
+ *   CTAs (see qmcur_set_max_ctas); several decompositions on several streams
+ *   then share the SMs.
+ *   Host errors: INVALID_ARG (a NULL argument, opts->max_ctas < 0, or any
+ *   error of the four calls).  Device errors: those of the four calls.
  */
 qmcur_status qmcur_decompose(const qmcur_qmat* A, int64_t c, int64_t r, const qmcur_opts* opts,
                              double* col_p, double* row_p, int32_t* J, int32_t* I,
