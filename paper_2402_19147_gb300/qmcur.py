@@ -349,6 +349,40 @@ def decompose(A, D, sampler=SAMPLER_NORM, seed=0, stream_id=0, rcond=1e-10, rank
            "qmcur_decompose")
 
 
+def decompose_many(As, Ds, seeds, nstreams=8, sampler=SAMPLER_NORM, stream_id=0, rcond=1e-10,
+                   rank_cap=0, max_sweeps=0, max_attempts=0, pinv_method=PINV_SUBSPACE_FP32,
+                   stream=None):
+    """Decompose As[i] into the buffers of Ds[i] with seed seeds[i] (qmcur_decompose),
+    nstreams of them in flight.  Each of the nstreams streams holds its
+    persistent kernels to SMs // nstreams CTAs, so the budgets never exceed
+    the SM count and the cooperative pseudo-inverses can always be resident
+    together; the latency-bound pseudo-inverses of some decompositions then
+    run beside the GEMMs of others.  The work is ordered after what `stream`
+    (default: the current stream) has queued, and `stream` waits for all of
+    it; As and Ds must stay alive until `stream` gets past that point."""
+    if not (len(As) == len(Ds) == len(seeds)):
+        raise ValueError("As, Ds and seeds differ in length")
+    if not As:
+        return
+    cur = stream if stream is not None else torch.cuda.current_stream()
+    dev = As[0].device
+    ns = max(1, min(int(nstreams), len(As)))
+    budget = max(1, torch.cuda.get_device_properties(dev).multi_processor_count // ns)
+    streams = [torch.cuda.Stream(device=dev) for _ in range(ns)]
+    start = torch.cuda.Event()
+    start.record(cur)
+    for st in streams:
+        st.wait_event(start)
+    for i, (A, D, sd) in enumerate(zip(As, Ds, seeds)):
+        decompose(A, D, sampler=sampler, seed=sd, stream_id=stream_id, rcond=rcond,
+                  rank_cap=rank_cap, max_sweeps=max_sweeps, max_attempts=max_attempts,
+                  stream=streams[i % ns], pinv_method=pinv_method, max_ctas=budget)
+    for st in streams:
+        done = torch.cuda.Event()
+        done.record(st)
+        cur.wait_event(done)
+
+
 def qsvd_truncated(X, B, rank, rcond=0.0, max_sweeps=0, rank_out=None, sigma_out=None, ws=None,
                    status=None, stream=None):
     """B = the rank-k truncated QSVD approximation of X (qmcur_qsvd_truncated)."""

@@ -87,3 +87,29 @@ def test_thread_budget_applies_to_the_stage_calls():
     # the Jacobi core and the GEMMs give the same bits at any budget
     for U, rel in outs[1:]:
         assert np.array_equal(U, outs[0][0]) and rel == outs[0][1]
+
+
+def test_decompose_many_matches_one_at_a_time():
+    # the binding's many-matrix helper: eight in flight on eight streams
+    m, n, c, r, k = 768, 1024, 64, 56, 16
+    A_np, _ = synth.lowrank_gaussian(m, n, k, seed=47, noise_rel=1e-3)
+    As = [torch.from_numpy(A_np).cuda()]
+    As += [torch.roll(As[0], shifts=31 * q, dims=1).contiguous() for q in range(1, 4)]
+    seeds = list(range(10, 18))
+    inputs = [As[i % 4] for i in range(len(seeds))]
+    ref = [Q.Decomposition(m, n, c, r, Q.PREC_BF16_MIXED) for _ in seeds]
+    got = [Q.Decomposition(m, n, c, r, Q.PREC_BF16_MIXED) for _ in seeds]
+    torch.cuda.synchronize()
+    for A, D, sd in zip(inputs, ref, seeds):
+        Q.decompose(A, D, sampler=Q.SAMPLER_NORM, seed=sd, rank_cap=k,
+                    pinv_method=Q.PINV_SUBSPACE_FP32)
+    Q.decompose_many(inputs, got, seeds, nstreams=8, sampler=Q.SAMPLER_NORM, rank_cap=k)
+    torch.cuda.current_stream().synchronize()
+    for a, b in zip(ref, got):
+        Q.check_status(a.status, "one at a time")
+        Q.check_status(b.status, "many")
+        assert np.array_equal(host(a.J), host(b.J)) and np.array_equal(host(a.I), host(b.I))
+        ua, ub = host(a.U), host(b.U)
+        assert np.linalg.norm(ua - ub) <= 1e-4 * np.linalg.norm(ua)
+        ra, rb = host(a.out3)[0], host(b.out3)[0]
+        assert abs(ra - rb) <= 1e-5 * ra
