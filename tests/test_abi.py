@@ -59,3 +59,11 @@ def test_host_only_calls(libpath):
     # the CTA budget is host state of the calling thread
     assert L.qmcur_set_max_ctas(-1) == 1            # INVALID_ARG
     assert L.qmcur_set_max_ctas(76) == 0 and L.qmcur_set_max_ctas(0) == 0
+
+
+def test_decompose_many_checks_its_lists():
+    # host-side validation before any device work
+    from paper_2402_19147_gb300 import qmcur as Q
+    with pytest.raises(ValueError):
+        Q.decompose_many([object()], [], [0])
+    Q.decompose_many([], [], [])           # nothing to do
