@@ -149,9 +149,11 @@ qmcur_status qmcur_probs(const qmcur_qmat* A, int32_t sampler, double* col_p, do
  * has no counterpart: this is a memory-management variant of the call above.
  *   Allocates nothing.  Its scratch is a static 8 MiB device array inside the
  *   library, held on every GPU that loads the library until the process
- *   exits.  Inputs needing more (ceil(m/32) n + ceil(n/1024) m + n + m + 4
- *   doubles, padded to 256 bytes per part, above 8 MiB; about m n <= 3e7)
- *   are rejected with QMCUR_ERR_UNSUPPORTED before anything is enqueued.
+ *   exits.  Inputs needing more (ceil(m/32) n + ceil(n/256) m + n + m +
+ *   ceil(n/32) + 4 doubles, each part padded to 256 bytes, above 8 MiB;
+ *   about m n <= 3e7) are rejected with QMCUR_ERR_UNSUPPORTED before
+ *   anything is enqueued.  The uniform sampler with fro2 == NULL reads no
+ *   input and needs no scratch, so it takes any size.
  *   The first call on a device looks up the array's device address (a CUDA
  *   runtime query, no allocation); make that first call before any stream
  *   capture on that device.  All calls on a device share the array and it

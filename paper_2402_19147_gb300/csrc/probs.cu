@@ -312,7 +312,10 @@ extern "C" qmcur_status qmcur_probs_noalloc(const qmcur_qmat* A, int32_t sampler
   qmcur::NvtxRange nvtx_range("qmcur_probs_noalloc");
   using namespace qmcur;
   if (!valid_qmat(A)) return QMCUR_ERR_INVALID_ARG;
-  if (probs_ws_bytes(A->rows, A->cols) > kNoAllocScratchBytes) return QMCUR_ERR_UNSUPPORTED;
+  // the uniform sampler without ||A||_F^2 reads neither A nor scratch
+  const bool needs_scratch = !(sampler == QMCUR_SAMPLER_UNIFORM && fro2 == nullptr);
+  if (needs_scratch && probs_ws_bytes(A->rows, A->cols) > kNoAllocScratchBytes)
+    return QMCUR_ERR_UNSUPPORTED;
   void* scratch = nullptr;
   const qmcur_status s = scratch_address(&scratch);
   if (s != QMCUR_OK) return s;

@@ -55,9 +55,10 @@ constexpr int A_STAGE = 4 * A_PLANE;
 constexpr int kEpiWarps = 8;                  // two per TMEM sub-partition
 constexpr int kTcThreads = 64 + 32 * kEpiWarps;
 
-// Shape of one instantiation: output tiles of BM x BNT (per plane).  BNT = 64
-// for the large product Z = C T; BNT = 32 for T = U R, whose c = O(100) rows
-// give too few 128 x 64 tiles to occupy the GPU.
+// Shape of one instantiation: output tiles of BM x BNT (per plane).  The
+// reversed product T^T = R^T U always takes BNT = kBn1 = 112 columns of U's c;
+// Z = C T takes 128 or 112 (whichever fills whole waves over the SMs better),
+// halved to 64 or 32 when the output has too few tiles (z_bn).
 constexpr int pow2_at_least(int x) {
   int p = 32;
   while (p < x) p *= 2;

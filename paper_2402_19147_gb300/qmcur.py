@@ -28,6 +28,8 @@ STATUS = {0: "QMCUR_OK", 1: "QMCUR_ERR_INVALID_ARG", 2: "QMCUR_ERR_NONFINITE",
           7: "QMCUR_ERR_UNSUPPORTED", 8: "QMCUR_ERR_CUDA", 9: "QMCUR_ERR_TIMEOUT",
           10: "QMCUR_ERR_ILL_CONDITIONED"}
 PINV_JACOBI_FP64, PINV_SUBSPACE_FP32 = 0, 1
+# pseudo-inverse methods that need rank_cap >= 1 (QMCUR_ERR_UNSUPPORTED otherwise)
+_CAPPED_METHODS = (PINV_SUBSPACE_FP32,)
 
 
 class QmcurError(RuntimeError):
@@ -350,7 +352,7 @@ def decompose(A, D, sampler=SAMPLER_NORM, seed=0, stream_id=0, rcond=1e-10, rank
 
 
 def decompose_many(As, Ds, seeds, nstreams=8, sampler=SAMPLER_NORM, stream_id=0, rcond=1e-10,
-                   rank_cap=0, max_sweeps=0, max_attempts=0, pinv_method=PINV_SUBSPACE_FP32,
+                   rank_cap=0, max_sweeps=0, max_attempts=0, pinv_method=PINV_JACOBI_FP64,
                    stream=None):
     """Decompose As[i] into the buffers of Ds[i] with seed seeds[i] (qmcur_decompose),
     nstreams of them in flight.  Each of the nstreams streams holds its
@@ -359,9 +361,15 @@ def decompose_many(As, Ds, seeds, nstreams=8, sampler=SAMPLER_NORM, stream_id=0,
     together; the latency-bound pseudo-inverses of some decompositions then
     run beside the GEMMs of others.  The work is ordered after what `stream`
     (default: the current stream) has queued, and `stream` waits for all of
-    it; As and Ds must stay alive until `stream` gets past that point."""
+    it, also when a call raises part way (the decompositions already queued
+    stay ordered before `stream`'s later work); As and Ds must stay alive
+    until `stream` gets past that point.  The pseudo-inverse method is
+    checked before anything is queued: the methods that need a rank cap
+    raise ValueError when rank_cap < 1."""
     if not (len(As) == len(Ds) == len(seeds)):
         raise ValueError("As, Ds and seeds differ in length")
+    if pinv_method in _CAPPED_METHODS and int(rank_cap) < 1:
+        raise ValueError("pinv_method %d needs rank_cap >= 1" % pinv_method)
     if not As:
         return
     cur = stream if stream is not None else torch.cuda.current_stream()
@@ -373,14 +381,16 @@ def decompose_many(As, Ds, seeds, nstreams=8, sampler=SAMPLER_NORM, stream_id=0,
     start.record(cur)
     for st in streams:
         st.wait_event(start)
-    for i, (A, D, sd) in enumerate(zip(As, Ds, seeds)):
-        decompose(A, D, sampler=sampler, seed=sd, stream_id=stream_id, rcond=rcond,
-                  rank_cap=rank_cap, max_sweeps=max_sweeps, max_attempts=max_attempts,
-                  stream=streams[i % ns], pinv_method=pinv_method, max_ctas=budget)
-    for st in streams:
-        done = torch.cuda.Event()
-        done.record(st)
-        cur.wait_event(done)
+    try:
+        for i, (A, D, sd) in enumerate(zip(As, Ds, seeds)):
+            decompose(A, D, sampler=sampler, seed=sd, stream_id=stream_id, rcond=rcond,
+                      rank_cap=rank_cap, max_sweeps=max_sweeps, max_attempts=max_attempts,
+                      stream=streams[i % ns], pinv_method=pinv_method, max_ctas=budget)
+    finally:
+        for st in streams:
+            done = torch.cuda.Event()
+            done.record(st)
+            cur.wait_event(done)
 
 
 def qsvd_truncated(X, B, rank, rcond=0.0, max_sweeps=0, rank_out=None, sigma_out=None, ws=None,

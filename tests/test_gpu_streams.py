@@ -103,7 +103,8 @@ def test_decompose_many_matches_one_at_a_time():
     for A, D, sd in zip(inputs, ref, seeds):
         Q.decompose(A, D, sampler=Q.SAMPLER_NORM, seed=sd, rank_cap=k,
                     pinv_method=Q.PINV_SUBSPACE_FP32)
-    Q.decompose_many(inputs, got, seeds, nstreams=8, sampler=Q.SAMPLER_NORM, rank_cap=k)
+    Q.decompose_many(inputs, got, seeds, nstreams=8, sampler=Q.SAMPLER_NORM, rank_cap=k,
+                     pinv_method=Q.PINV_SUBSPACE_FP32)
     torch.cuda.current_stream().synchronize()
     for a, b in zip(ref, got):
         Q.check_status(a.status, "one at a time")
@@ -113,3 +114,46 @@ def test_decompose_many_matches_one_at_a_time():
         assert np.linalg.norm(ua - ub) <= 1e-4 * np.linalg.norm(ua)
         ra, rb = host(a.out3)[0], host(b.out3)[0]
         assert abs(ra - rb) <= 1e-5 * ra
+
+
+def test_decompose_many_defaults():
+    # with its defaults (FP64 Jacobi core, no rank cap) the helper runs and
+    # matches one decomposition at a time bit for bit
+    m, n, c, r = 256, 320, 24, 20
+    A = torch.from_numpy(synth.lowrank_gaussian(m, n, 6, seed=51, noise_rel=0.0)[0]).cuda()
+    seeds = [1, 2, 3]
+    ref = [Q.Decomposition(m, n, c, r, Q.PREC_FP32) for _ in seeds]
+    got = [Q.Decomposition(m, n, c, r, Q.PREC_FP32) for _ in seeds]
+    torch.cuda.synchronize()
+    for D, sd in zip(ref, seeds):
+        Q.decompose(A, D, seed=sd)
+    Q.decompose_many([A] * 3, got, seeds, nstreams=2)
+    torch.cuda.current_stream().synchronize()
+    for a, b in zip(ref, got):
+        Q.check_status(a.status, "one at a time")
+        Q.check_status(b.status, "many")
+        assert np.array_equal(host(a.J), host(b.J)) and np.array_equal(host(a.U), host(b.U))
+        assert host(a.out3)[0] == host(b.out3)[0]
+
+
+def test_decompose_many_failure_keeps_the_join():
+    # the third entry's C has one row too few, so its qmcur_decompose fails
+    # on the host (the gather's shape check, before the gather is queued;
+    # its probabilities fit their buffers) after two decompositions were
+    # queued on side streams; the current stream must still wait for those two
+    m, n, c, r, k = 512, 640, 40, 36, 8
+    A = torch.from_numpy(synth.lowrank_gaussian(m, n, k, seed=53, noise_rel=1e-3)[0]).cuda()
+    Ds = [Q.Decomposition(m, n, c, r, Q.PREC_FP32) for _ in range(3)]
+    Ds[2].C = torch.empty(4, m - 1, c, dtype=torch.float32, device="cuda")
+    for D in Ds:
+        D.out3.fill_(float("nan"))
+    with pytest.raises(Q.QmcurError):
+        Q.decompose_many([A, A, A], Ds, [5, 6, 7], nstreams=3, rank_cap=k)
+    cur = torch.cuda.current_stream()
+    seen = torch.stack([Ds[0].out3[0].clone(), Ds[1].out3[0].clone()])   # queued on cur
+    cur.synchronize()
+    vals = host(seen)
+    assert np.all(np.isfinite(vals)) and np.all(vals > 0)
+    torch.cuda.synchronize()
+    Q.check_status(Ds[0].status, "first")
+    Q.check_status(Ds[1].status, "second")
