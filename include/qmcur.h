@@ -95,11 +95,23 @@ typedef enum {
 typedef enum {
   QMCUR_PINV_JACOBI_FP64 = 0,  /* full QSVD by FP64 one-sided Jacobi: any rank
                                   rule, FP64 accuracy, slow on GB300's FP64 rate */
-  QMCUR_PINV_SUBSPACE_FP32 = 1 /* rank_cap >= 1 required (k = min(rank_cap, r, c)
+  QMCUR_PINV_SUBSPACE_FP32 = 1, /* rank_cap >= 1 required (k = min(rank_cap, r, c)
                                   <= 100): top-k subspaces by two FP32 subspace
                                   iterations with CholeskyQR2, U = P R^-1 Q^H;
                                   assumes sigma_k > sigma_{k+1} clearly, ignores
                                   rcond, does not write sigma_out             */
+  QMCUR_PINV_REFINED_FP64 = 2  /* rank_cap >= 1 required (k = min(rank_cap, r, c)
+                                  <= 100, r, c <= 16384, rcond <= 1e-6): the top-k
+                                  right singular subspace to FP64 accuracy by
+                                  subspace iteration with FP64 products and FP32
+                                  Cholesky preconditioners, iterated until the
+                                  predicted subspace angle is below 1e-14, then
+                                  U = P (W P)^+ by CholeskyQR2 with an FP64
+                                  orthogonality correction.  Keeps exactly k
+                                  singular values (so sigma_k must exceed
+                                  rcond sigma_1); the iteration count grows as
+                                  1 / log(sigma_k / sigma_{k+1}); does not write
+                                  sigma_out                                   */
 } qmcur_pinv_method;
 
 /* Human-readable name of a status code (static string). */
@@ -205,9 +217,16 @@ qmcur_status qmcur_sample(const qmcur_qmat* A, int32_t sampler, const double* co
  *            in FP64 by one-sided (Hestenes) Jacobi rotations in quaternion
  *            arithmetic; max_sweeps <= 0 selects 40; rank_out[1] = sweeps.
  *            QMCUR_PINV_SUBSPACE_FP32: see the enum; rank_out = {k, 2}.
+ *            QMCUR_PINV_REFINED_FP64: see the enum; max_sweeps is the
+ *            iteration limit (<= 0 selects 30, at most 64); rank_out =
+ *            {k, iterations}.
  *   Device errors: NO_CONVERGENCE, NONFINITE, TIMEOUT (Jacobi);
- *   ILL_CONDITIONED (subspace).  UNSUPPORTED (synchronous) when the subspace
- *   method is asked for without a rank cap or with k > 100.
+ *   ILL_CONDITIONED (subspace, refined: a non-positive FP32 Cholesky pivot,
+ *   i.e. sigma_1 / sigma_k beyond ~1e3); NO_CONVERGENCE, TIMEOUT (refined:
+ *   no usable gap at k within the iteration limit; U is still written).
+ *   UNSUPPORTED (synchronous) when the subspace or refined method is asked
+ *   for without a rank cap, with k > 100, or (refined) with rcond > 1e-6 or
+ *   r, c > 16384.
  */
 qmcur_status qmcur_pinv_core(const qmcur_qmat* W, int32_t method, double rcond, int32_t rank_cap,
                              int32_t max_sweeps, qmcur_qmat* U, int32_t* rank_out,

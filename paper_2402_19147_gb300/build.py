@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqmcur.so")
-SOURCES = ["api.cu", "probs.cu", "sample.cu", "pinv.cu", "pinv_fast.cu", "small.cu",
+SOURCES = ["api.cu", "probs.cu", "sample.cu", "pinv.cu", "pinv_fast.cu", "pinv_refine.cu", "small.cu",
            "qgemm_simt.cu", "qgemm_tc.cu", "backward.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -18,6 +18,12 @@ qmcur_status launch_pinv_fast(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat*
                               int32_t* rank_out, uint64_t seed, void* ws, size_t ws_bytes,
                               int32_t* dev_status, cudaStream_t st);
 
+// FP64-accurate refined subspace pseudo-inverse (pinv_refine.cu).
+size_t pinv_refine_ws_bytes(int64_t r, int64_t c, int64_t k);
+qmcur_status launch_pinv_refine(const qmcur_qmat* W, double rcond, int32_t rank_cap,
+                                int32_t max_iter, qmcur_qmat* U, int32_t* rank_out, uint64_t seed,
+                                void* ws, size_t ws_bytes, int32_t* dev_status, cudaStream_t st);
+
 // Backward of the masked reconstruction loss (backward.cu).
 size_t backward_ws_bytes(int64_t m, int64_t n, int64_t c, int64_t r);
 qmcur_status launch_backward(const qmcur_qmat* A, const uint8_t* mask, const int32_t* J,
@@ -128,7 +134,9 @@ size_t qmcur_workspace_size(int64_t m, int64_t n, int64_t c, int64_t r, int32_t 
   const size_t s2 = sample_ws_bytes(m, n), s3 = pinv_ws_bytes(r, c), s4 = gemm_ws_bytes(m, n, c, r, prec);
   const int64_t kmax = (r < c ? r : c) < kSmallCholMax ? (r < c ? r : c) : kSmallCholMax;
   const size_t s5 = pinv_fast_ws_bytes(r, c, kmax);
+  const size_t s6 = pinv_refine_ws_bytes(r, c, kmax);
   if (s5 > s) s = s5;
+  if (s6 > s) s = s6;
   if (s2 > s) s = s2;
   if (s3 > s) s = s3;
   if (s4 > s) s = s4;
@@ -159,6 +167,9 @@ static qmcur_status pinv_dispatch(const qmcur_qmat* W, int32_t method, double rc
   if (method == QMCUR_PINV_JACOBI_FP64)
     return launch_pinv(W, rcond, rank_cap, max_sweeps, U, rank_out, sigma_out, workspace,
                        ws_bytes, dev_status, stream);
+  if (method == QMCUR_PINV_REFINED_FP64)
+    return launch_pinv_refine(W, rcond, rank_cap, max_sweeps, U, rank_out, 0x9e3779b97f4a7c15ull,
+                              workspace, ws_bytes, dev_status, stream);
   if (method != QMCUR_PINV_SUBSPACE_FP32) return QMCUR_ERR_INVALID_ARG;
   if (!valid_qmat(W) || !valid_qmat(U)) return QMCUR_ERR_INVALID_ARG;
   if (W->rows < 1 || W->cols < 1 || U->rows != W->cols || U->cols != W->rows)
@@ -252,6 +263,9 @@ size_t qmcur_core_paper_workspace_size(int64_t m, int64_t n, int64_t c, int64_t 
   size_t s = pinv_ws_bytes(m, c);
   const size_t s2 = pinv_ws_bytes(r, n), s3 = pinv_fast_ws_bytes(m, c, kc),
                s4 = pinv_fast_ws_bytes(r, n, kr), s5 = gemm_ws_bytes(c, r, m, n, prec);
+  const size_t s6 = pinv_refine_ws_bytes(m, c, kc), s7 = pinv_refine_ws_bytes(r, n, kr);
+  if (s6 > s) s = s6;
+  if (s7 > s) s = s7;
   if (s2 > s) s = s2;
   if (s3 > s) s = s3;
   if (s4 > s) s = s4;

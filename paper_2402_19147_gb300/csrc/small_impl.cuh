@@ -369,7 +369,8 @@ __host__ __device__ constexpr int chol_ride_slots(int S) {
 
 template <int S>
 __device__ __forceinline__ int sm_chol_s(const QPtr& G, int k, float* rpk, int32_t* status,
-                                          unsigned char* smraw, const SolveJobs* sj) {
+                                          unsigned char* smraw, const SolveJobs* sj,
+                                          float diag_shift_rel) {
   static_assert(32 % kCholNb == 0, "a block of columns stays in one slot");
   constexpr int RU = chol_ride_slots(S);
   constexpr int RUs = RU > 0 ? RU : 1;
@@ -381,6 +382,25 @@ __device__ __forceinline__ int sm_chol_s(const QPtr& G, int k, float* rpk, int32
   SolveRow<RUs> rs;
   rs.row = -1;
   if (RU > 0 && sj != nullptr) rs.load(*sj, k);   // the loads overlap those of G
+  // optional shift of the diagonal by diag_shift_rel * max_l G_ll (a shifted
+  // factor of an ill-conditioned G, for callers that only precondition with it)
+  float shift = 0.f;
+  if (diag_shift_rel > 0.f) {
+    __shared__ float dmax_sh;
+    if (tid < 32) {
+      float mx = 0.f;
+      for (int l = tid; l < k; l += 32) {
+        const int64_t off = (int64_t)l * G.ld + l;
+        mx = fmaxf(mx, G.dtype == QMCUR_F64 ? (float)reinterpret_cast<const double*>(G.p[0])[off]
+                                            : reinterpret_cast<const float*>(G.p[0])[off]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (tid == 0) dmax_sh = mx;
+    }
+    __syncthreads();
+    shift = diag_shift_rel * dmax_sh;
+  }
   float4 v[S];
   unsigned jc[(S + 1) / 2];   // (j << 8 | c) in 16 bits, two slots per word
 #pragma unroll
@@ -399,10 +419,17 @@ __device__ __forceinline__ int sm_chol_s(const QPtr& G, int k, float* rpk, int32
       const int c = j + (e - packed_row(j, k));
       jc[s >> 1] |= (((unsigned)j << 8) | (unsigned)c) << (16 * (s & 1));
       const int64_t off = (int64_t)j * G.ld + c;
-      v[s] = make_float4(reinterpret_cast<const float*>(G.p[0])[off],
-                         reinterpret_cast<const float*>(G.p[1])[off],
-                         reinterpret_cast<const float*>(G.p[2])[off],
-                         reinterpret_cast<const float*>(G.p[3])[off]);
+      if (G.dtype == QMCUR_F64)   // an FP64 Gram matrix, factored in FP32
+        v[s] = make_float4((float)reinterpret_cast<const double*>(G.p[0])[off],
+                           (float)reinterpret_cast<const double*>(G.p[1])[off],
+                           (float)reinterpret_cast<const double*>(G.p[2])[off],
+                           (float)reinterpret_cast<const double*>(G.p[3])[off]);
+      else
+        v[s] = make_float4(reinterpret_cast<const float*>(G.p[0])[off],
+                           reinterpret_cast<const float*>(G.p[1])[off],
+                           reinterpret_cast<const float*>(G.p[2])[off],
+                           reinterpret_cast<const float*>(G.p[3])[off]);
+      if (j == c) v[s].x += shift;
       if (j < kCholNb) Pn[j * kSmallCholMax + c] = v[s];
       if (e == 0) {
         const float g00 = fabsf(v[s].x);
@@ -509,23 +536,27 @@ __device__ __forceinline__ int sm_chol_s(const QPtr& G, int k, float* rpk, int32
 template <int S>
 __device__ __forceinline__ int sm_chol_from(int need, const QPtr& G, int k, float* rpk,
                                             int32_t* status, unsigned char* smraw,
-                                            const SolveJobs* sj) {
-  if (need <= S) return sm_chol_s<S>(G, k, rpk, status, smraw, sj);
-  if constexpr (S < kCholSlots) return sm_chol_from<S + 1>(need, G, k, rpk, status, smraw, sj);
+                                            const SolveJobs* sj, float diag_shift_rel) {
+  if (need <= S) return sm_chol_s<S>(G, k, rpk, status, smraw, sj, diag_shift_rel);
+  if constexpr (S < kCholSlots)
+    return sm_chol_from<S + 1>(need, G, k, rpk, status, smraw, sj, diag_shift_rel);
   return 0;
 }
 
 // One CTA of kCholThreads threads: the packed factor R (FP32) with G = R^H R,
 // for 1 <= k <= kSmallCholMax (rpk 16-byte aligned, rpk_floats(k) floats).
-// Only the upper triangle of G is read.  A non-positive or non-finite pivot
+// Only the upper triangle of G is read; G may be FP32 or FP64 (rounded to
+// FP32 as it is read).  diag_shift_rel > 0 factors G + diag_shift_rel *
+// max_l G_ll I instead.  A non-positive or non-finite pivot
 // sets ILL_CONDITIONED and continues with a tiny pivot.  With sj, rpk must be
 // in shared memory.  Returns n, the number of row warps: the rows
 // solve_row_of(i, vb, vg), i < n, of the solves Z = Y R^-1 were done along the way;
 // the other rows (all of them when n = 0) are left to the caller.
 __device__ __forceinline__ int sm_chol(const QPtr& G, int k, float* rpk, int32_t* status,
-                                        unsigned char* smraw, const SolveJobs* sj = nullptr) {
+                                        unsigned char* smraw, const SolveJobs* sj = nullptr,
+                                        float diag_shift_rel = 0.f) {
   return sm_chol_from<1>((k * (k + 1) / 2 + kCholThreads - 1) / kCholThreads, G, k, rpk, status,
-                         smraw, sj);
+                         smraw, sj, diag_shift_rel);
 }
 
 // ---------------------------------------------------------------------------

@@ -27,9 +27,9 @@ STATUS = {0: "QMCUR_OK", 1: "QMCUR_ERR_INVALID_ARG", 2: "QMCUR_ERR_NONFINITE",
           5: "QMCUR_ERR_SAMPLE_LIMIT", 6: "QMCUR_ERR_NO_CONVERGENCE",
           7: "QMCUR_ERR_UNSUPPORTED", 8: "QMCUR_ERR_CUDA", 9: "QMCUR_ERR_TIMEOUT",
           10: "QMCUR_ERR_ILL_CONDITIONED"}
-PINV_JACOBI_FP64, PINV_SUBSPACE_FP32 = 0, 1
+PINV_JACOBI_FP64, PINV_SUBSPACE_FP32, PINV_REFINED_FP64 = 0, 1, 2
 # pseudo-inverse methods that need rank_cap >= 1 (QMCUR_ERR_UNSUPPORTED otherwise)
-_CAPPED_METHODS = (PINV_SUBSPACE_FP32,)
+_CAPPED_METHODS = (PINV_SUBSPACE_FP32, PINV_REFINED_FP64)
 
 
 class QmcurError(RuntimeError):
