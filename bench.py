@@ -40,8 +40,16 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16mixed",
                     choices=["fp32", "tf32x3", "bf16x3", "bf16x6", "bf16mixed"])
-    ap.add_argument("--pinv", default="subspace", choices=["subspace", "jacobi"])
-    ap.add_argument("--streams", type=int, default=8,
+    ap.add_argument("--pinv", default="refined", choices=["refined", "subspace", "jacobi"],
+                    help="core of the decomposition workloads: the FP64-accurate refined "
+                         "subspace method (default), the FP64 Jacobi QSVD, or the FP32 "
+                         "subspace method (not FP64-accurate)")
+    ap.add_argument("--min-seconds", type=float, default=1.0,
+                    help="the K-step timed loop is repeated until the repeats cover this "
+                         "long; the median repeat is reported")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 4096 x 4096 colour-field decompositions of the default run")
+    ap.add_argument("--streams", type=int, default=1,
                     help="decompositions in flight, each stream's persistent kernels on "
                          "SMs / streams CTAs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -228,16 +236,24 @@ def replica_value(world, steps, t_max_ms):
 
 
 def pinv_flops(w, method, sweeps):
-    """Algorithmic real flops of one pseudo-inverse of the r x c intersection."""
+    """Real flops of one pseudo-inverse of the r x c intersection, counted from
+    the shapes of the method's steps (32 real flops per quaternion
+    multiply-add).  Refined: the FP64 products and FP64 triangular solves
+    (its FP32 Cholesky factors run on the FP32 pipe and are not counted)."""
     c, r = w["c"], w["r"]
     nr, nc = max(r, c), min(r, c)
+    k = min(w["rank_cap"], nc)
     if method == "jacobi":
         N = nc + (nc % 2)
         pairs = (N // 2) * (N - 1)
         # per pair: alpha, beta (8 flops per entry each), gamma (32), then the
         # rotation of both columns of G and V (q*w 32 flops, two combinations 16).
         return sweeps * pairs * (nr * 48 + (nr + nc) * 48)
-    k = min(w["rank_cap"], nc)
+    if method == "refined":
+        it = max(1, sweeps)
+        per_iter = 2 * r * c * k + 4 * c * k * k + k ** 3 + 2 * (c * k * k // 2)
+        final = 3 * r * k * k + 2 * ((r + c) * k * k // 2) + c * k * k + c * r * k
+        return 32 * (r * c * k + it * per_iter + final)
     # subspace iteration: W Omega, W^H Q0, W P1, W^H Q1, W T (5 r c k); seven
     # Hermitian Grams (rows k^2 / 2) and Cholesky factorisations (k^3 / 6);
     # ten triangular solves (rows k^2 / 2); U = (P R1^-1 R2^-1) Q^H (c r k).
@@ -248,7 +264,11 @@ def pinv_flops(w, method, sweeps):
     return 32 * qfma
 
 
-def stage_work(w, prec, sweeps, method="subspace"):
+# products of the tensor pipe per quaternion flop, (T = U R, Z = C T), per split
+SPLIT_PRODUCTS = {"bf16x3": (3, 3), "bf16x6": (6, 6), "bf16mixed": (6, 3), "tf32x3": (3, 3)}
+
+
+def stage_work(w, prec, sweeps, method="refined"):
     """Algorithmic work per decomposition of each stage (bytes or flops)."""
     m, n, c, r = w["m"], w["n"], w["c"], w["r"]
     es = 4
@@ -369,10 +389,10 @@ def fp64_check(Q, A, D, w, prec, sampler, stream, steps=10, warmup=3, rows=256):
     return out, fp64
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# kernels that can be the dominant one, from one ncu capture of the current
-# code (profiles/qgemm_tc_pinv_gauss2048_rank50_bf16mixed.md).
-NCU_TRAFFIC = {("pinv", "subspace"): 1.551616e6}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the current code, per kernel (profiles/): the tensor-core
+# Z = C T with the fused residual on the 2048 x 2048 workload, mixed split.
+NCU_TRAFFIC = {"gemm_z": 81.89e6 + 2.36e6}
 
 
 def peaks():
@@ -385,10 +405,67 @@ def peaks():
 
 def alu_peak_tflops(kind):
     # 152 SMs at the 2070 MHz maximum clock: FP32 128 FMA lanes per SM;
-    # FP64 at the nominal 1.25 TFLOP/s of the part.
+    # FP64 at the nominal 1.25 TFLOP/s of the part (no measured FP64 peak).
     if kind == "fp64":
         return 1.25
     return 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def one_core_oracle_rate(name, seconds):
+    """The oracle's decompositions/s with every BLAS/OpenMP pool held to one
+    thread: a child process with the thread variables set before numpy loads."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "from paper_2402_19147_gb300 import synth; "
+            "w = bench.workload_config(None) if %r == bench.WORKLOAD else dict(synth.WORKLOADS[%r]); "
+            "A = synth.make(%r); r = bench.oracle_rate(A, w, %r); "
+            "print(json.dumps({'rate': r[0], 'done': r[1], 'el': r[2]}))"
+            % (ROOT, name, name, name, float(seconds)))
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                             text=True, timeout=600)
+        d = json.loads(out.stdout.strip().splitlines()[-1])
+        return {"value": d["rate"], "unit": "decompositions/s", "cores": 1, "kind": "oracle",
+                "sample": "%d whole FP64 oracle decompositions (%.1f s), BLAS and OpenMP "
+                          "held to one thread" % (d["done"], d["el"])}
+    except Exception as e:   # reported, not fatal
+        return {"value": None, "unit": "decompositions/s", "cores": 1, "kind": "oracle",
+                "sample": "unavailable: %s" % type(e).__name__}
+
+
+def timed_repeats(torch, run_once, streams, min_seconds, dist=None, device=None):
+    """Repeats of the K-step loop `run_once()` (which records its own events)
+    until they cover min_seconds (three at least).  Each repeat is bracketed by
+    a barrier and a device synchronise on both sides and timed with CUDA
+    events on the launching streams.  Returns the per-repeat times (ms, max
+    over ranks)."""
+    times = []
+    total = 0.0
+    while len(times) < 3 or total < 1e3 * min_seconds:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cur = torch.cuda.current_stream()
+        e0.record(cur)
+        for st in streams:
+            st.wait_event(e0)
+        run_once()
+        for st in streams:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            cur.wait_event(ev)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t = replica_max(e0.elapsed_time(e1), dist, device)
+        times.append(t)
+        total += t
+        if len(times) >= 1000:
+            break
+    return times
 
 
 def run_ours(args):
@@ -411,77 +488,29 @@ def run_ours(args):
     m, n, c, r = w["m"], w["n"], w["c"], w["r"]
     prec = Q.PREC_NAMES[args.prec]
     sampler = Q.SAMPLER_NORM if w["sampler"] == "norm" else Q.SAMPLER_UNIFORM
-    pinv_method = Q.PINV_SUBSPACE_FP32 if args.pinv == "subspace" else Q.PINV_JACOBI_FP64
+    pinv_method = {"refined": Q.PINV_REFINED_FP64, "subspace": Q.PINV_SUBSPACE_FP32,
+                   "jacobi": Q.PINV_JACOBI_FP64}[args.pinv]
     A_np = synth.make(workload_name(args))
     A = torch.from_numpy(A_np).to(dev)
-    D = Q.Decomposition(m, n, c, r, prec, device=dev)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stages = ["probs", "sample", "pinv", "gemm"]
+    K = args.steps
 
-    def step(seed, ev=None):
-        def mark(i):
-            if ev is not None:
-                ev[i].record(stream)
-        mark(0)
-        Q.probs(A, sampler, D.col_p, D.row_p, None, D.ws, D.status, stream)
-        mark(1)
-        Q.sample(A, sampler, D.col_p, D.row_p, c, r, seed, rank, D.J, D.I, D.C, D.R, D.W,
-                 ws=D.ws, status=D.status, stream=stream)
-        mark(2)
-        Q.pinv_core(D.W, D.U, w["rcond"], w["rank_cap"], 0, D.rank, D.sigma, D.ws, D.status,
-                    stream, method=pinv_method)
-        mark(3)
-        Q.residual(A, D.out3, D.C, D.U, D.R, prec, None, None, D.ws, D.status, stream)
-        mark(4)
-
-    for s in range(args.warmup):
-        step(1000 + s)
-    torch.cuda.synchronize()
-    Q.check_status(D.status, "warm-up")
-
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
-    clocks = Clocks(torch.cuda.current_device())
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    for s in range(args.steps):
-        flush.fill_(s & 0xff)
-        step(s, evs[s])
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    clk_seq = clocks.stop()
-    Q.check_status(D.status, "timed steps")
-    stage_ms = {k: 0.0 for k in stages}
-    total_ms = 0.0
-    for e in evs:
-        for i, k in enumerate(stages):
-            stage_ms[k] += e[i].elapsed_time(e[i + 1])
-        total_ms += e[0].elapsed_time(e[4])
-    sweeps = int(D.rank[1].item())
-    rel = float(D.out3[0].item())
-    t_seq = replica_max(total_ms, dist, dev)
-    value_seq = replica_value(world, args.steps, t_seq)
-    stage_seq = dict(stage_ms)
-
-    # ---- the headline: NS decompositions in flight on NS streams.  Each
-    # stream's persistent kernels (the cooperative pseudo-inverse and the
-    # tensor-core GEMMs) hold SMs / NS CTAs, so the latency-bound
-    # pseudo-inverses of some decompositions run beside the throughput-bound
-    # GEMMs of others.  The budgets sum to at most the SM count, so all the
-    # cooperative grids can always be resident at once.  Inputs larger than
-    # L2 stand in for the flush: four row-rotated copies of A (the same
-    # spectrum), cycled.
+    # NS decompositions in flight on NS streams (NS = 1: one at a time, every
+    # SM each).  Each stream's persistent kernels (the cooperative
+    # pseudo-inverse and the tensor-core GEMMs) hold SMs / NS CTAs; the
+    # budgets sum to at most the SM count, so all the cooperative grids can
+    # be resident at once.  Inputs larger than L2 stand in for a flush: four
+    # row-rotated copies of A (the same spectrum), cycled.
     NS = max(1, args.streams)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    budget = max(1, sms // NS)
-    Dp = [D] + [Q.Decomposition(m, n, c, r, prec, device=dev) for _ in range(NS - 1)]
-    Sp = [torch.cuda.Stream(device=dev) for _ in range(NS)]
+    budget = sms // NS if NS > 1 else 0
+    Dp = [Q.Decomposition(m, n, c, r, prec, device=dev) for _ in range(NS)]
+    D = Dp[0]
+    Sp = [torch.cuda.current_stream()] if NS == 1 else [torch.cuda.Stream(device=dev)
+                                                      for _ in range(NS)]
     Ain = [A] + [torch.roll(A, shifts=97 * (q + 1), dims=1).contiguous() for q in range(3)]
     in_bytes = sum(x.numel() * x.element_size() for x in Ain)
-    torch.cuda.synchronize()   # the copies above ran on the current stream, not on Sp
+    torch.cuda.synchronize()   # the copies above ran on the current stream
 
     def pstep(sd, ev=None):
         b = sd % NS
@@ -502,51 +531,44 @@ def run_ours(args):
         Q.residual(Ak, Db.out3, Db.C, Db.U, Db.R, prec, None, None, Db.ws, Db.status, st)
         mark(4)
 
-    cur = torch.cuda.current_stream()
     Q.set_max_ctas(budget)
     for sd in range(args.warmup):
         pstep(2000 + sd)
     torch.cuda.synchronize()
     for Db in Dp:
-        Q.check_status(Db.status, "pipelined warm-up")
-    evp = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ends = [torch.cuda.Event() for _ in range(NS)]
+        Q.check_status(Db.status, "warm-up")
+    evs = []
+
+    def k_steps():
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+        for sd in range(K):
+            pstep(sd, ev[sd])
+        evs.append(ev)
+
     clocks = Clocks(torch.cuda.current_device())
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
     clocks.start()
-    p0.record(cur)
-    for st in Sp:
-        st.wait_event(p0)
-    for sd in range(args.steps):
-        pstep(sd, evp[sd])
-    for b in range(NS):
-        ends[b].record(Sp[b])
-        cur.wait_event(ends[b])
-    p1.record(cur)
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
+    reps = timed_repeats(torch, k_steps, Sp if NS > 1 else [], args.min_seconds, dist, dev)
     clk = clocks.stop()
     Q.set_max_ctas(0)
     for Db in Dp:
-        Q.check_status(Db.status, "pipelined steps")
+        Q.check_status(Db.status, "timed steps")
+    t_med = statistics.median(reps)
+    value = replica_value(world, K, t_med)
     stage_ms = {k: 0.0 for k in stages}
-    for e in evp:
-        for i, k in enumerate(stages):
-            stage_ms[k] += e[i].elapsed_time(e[i + 1])
-    t_max = replica_max(p0.elapsed_time(p1), dist, dev)
-    value = replica_value(world, args.steps, t_max)
+    for ev in evs:
+        for e in ev:
+            for i, k in enumerate(stages):
+                stage_ms[k] += e[i].elapsed_time(e[i + 1])
+    stage_ms = {k: v / (K * len(evs)) for k, v in stage_ms.items()}
+    sweeps = int(D.rank[1].item())
+    rel = float(D.out3[0].item())
 
     # end to end through the C ABI with host buffers (pinned): every step
-    # uploads its own input and reads back its results (J, I, U, residual).
-    # As in the headline, NS decompositions are in flight on NS compute
-    # streams with the same CTA budgets; buffer set b belongs to stream b.
-    # The upload of step s + 1 (one copy stream) and the read-back of step s
-    # (another) overlap the decompositions, ordered by events; the timed
-    # region spans all K steps, copies included.
+    # uploads its own input and reads back its results (J, I, U, residual),
+    # on the same NS compute streams and CTA budgets as above.  The upload of
+    # step s + 1 (one copy stream) and the read-back of step s (another)
+    # overlap the decompositions, ordered by events; the timed region spans
+    # all K steps, copies included.
     A_host = torch.from_numpy(A_np).pin_memory()
     Ds = Dp
     Abuf = [torch.empty_like(A) for _ in range(NS)]
@@ -554,6 +576,7 @@ def run_ours(args):
             for d in Ds]
     h2d = A_host.numel() * A_host.element_size()
     d2h = sum(o.numel() * o.element_size() for o in outs[0])
+    Se = Sp if NS > 1 else [torch.cuda.Stream(device=dev)]
     up_s, back_s = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
     up = [torch.cuda.Event() for _ in range(NS)]     # input of buffer b uploaded
     done = [torch.cuda.Event() for _ in range(NS)]   # decomposition on buffer b finished
@@ -568,39 +591,40 @@ def run_ours(args):
 
     def decompose_on(b, seed):
         Q.decompose(Abuf[b], Ds[b], sampler=sampler, seed=seed, stream_id=rank,
-                    rcond=w["rcond"], rank_cap=w["rank_cap"], stream=Sp[b],
+                    rcond=w["rcond"], rank_cap=w["rank_cap"], stream=Se[b],
                     pinv_method=pinv_method, max_ctas=budget)
 
     for b in range(NS):
         Abuf[b].copy_(A)
-    torch.cuda.synchronize()      # the copies ran on the current stream, not on Sp
+    torch.cuda.synchronize()      # the copies ran on the current stream, not on Se
     for b in range(NS):
         decompose_on(b, b)        # warm every buffer set
     torch.cuda.synchronize()
     for Db in Ds:
         Q.check_status(Db.status, "e2e warm-up")
+    cur = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(cur)
-    for st in [up_s, back_s] + Sp:
+    for st in [up_s, back_s] + Se:
         st.wait_event(e0)
     upload(0)
-    for s in range(args.steps):
+    for s in range(K):
         b = s % NS
-        if s + 1 < args.steps:
+        if s + 1 < K:
             nb = (s + 1) % NS
             # step s + 1 - NS, the buffer's previous user, no longer reads Abuf[nb]
             upload(nb, after=done[nb] if s + 1 >= NS else None)
-        Sp[b].wait_event(up[b])
+        Se[b].wait_event(up[b])
         if s >= NS:
-            Sp[b].wait_event(back[b])           # step s - NS's results are read back
+            Se[b].wait_event(back[b])           # step s - NS's results are read back
         decompose_on(b, s)
-        done[b].record(Sp[b])
+        done[b].record(Se[b])
         with torch.cuda.stream(back_s):
             back_s.wait_event(done[b])
             for o, x in zip(outs[b], (Ds[b].J, Ds[b].I, Ds[b].U, Ds[b].out3)):
                 o.copy_(x, non_blocking=True)
             back[b].record(back_s)
-    for b in range(min(NS, args.steps)):
+    for b in range(min(NS, K)):
         cur.wait_event(back[b])
     e1.record(cur)
     e1.synchronize()
@@ -613,75 +637,80 @@ def run_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
+    pk, pk_kind = peaks()
     work = stage_work(w, args.prec, sweeps, args.pinv)
+    one_stream = NS == 1
 
-    def roofline_of(st_ms, share):
-        """The stage that takes the most time on its stream, against the peak
-        of the SMs its persistent kernels hold (share = CTA budget / SMs)."""
-        dom = max(stages, key=lambda k: st_ms[k])
-        bound, amount, unit = work[dom]
-        per_launch_s = st_ms[dom] / args.steps / 1e3
-        pk, pk_kind = peaks()
-        if unit == "GB/s":
-            achieved = amount / per_launch_s / 1e9
-            peak = pk["hbm_gbs"]
-        else:
-            achieved = amount / per_launch_s / 1e12
-            if dom == "pinv" and args.pinv == "jacobi":
-                peak = alu_peak_tflops("fp64")
-                pk_kind = "nominal FP64 1.25 TFLOP/s"
-            elif dom == "pinv" or bound == "alu":
-                peak = alu_peak_tflops("fp32")
-                pk_kind = "FP32 CUDA-core 152 SMs x 128 lanes x 2 x 2.07 GHz"
-            else:
-                peak = pk["bf16_tflops"]
-            if share < 1.0:
-                peak *= share
-                pk_kind += "; x %d/%d, the SMs the stream's persistent kernels hold" % (
-                    budget, sms)
-        return {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak,
-                "unit": unit, "frac": achieved / peak,
-                "traffic": NCU_TRAFFIC.get((dom, args.pinv)) if args.prec != "fp32" else None,
-                "traffic_unit": "bytes per launch (ncu dram__bytes read + write)",
-                "peak_source": pk_kind}
+    # the dominant kernel's roofline: the stage that takes the most time on
+    # its stream (each stage of the refined and subspace cores is one kernel)
+    dom = max(stages, key=lambda k: stage_ms[k])
+    bound, amount, unit = work[dom]
+    per_launch_s = stage_ms[dom] / 1e3
+    if unit == "GB/s":
+        achieved, peak, src = amount / per_launch_s / 1e9, pk["hbm_gbs"], pk_kind + " HBM copy"
+    elif dom == "pinv" and args.pinv in ("refined", "jacobi"):
+        achieved, peak = amount / per_launch_s / 1e12, alu_peak_tflops("fp64")
+        src = "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)"
+    elif dom == "pinv":
+        achieved, peak = amount / per_launch_s / 1e12, alu_peak_tflops("fp32")
+        src = "FP32 CUDA cores, 152 SMs x 128 lanes x 2 x 2.07 GHz"
+    else:
+        achieved, peak, src = amount / per_launch_s / 1e12, pk["bf16_tflops"], pk_kind + " BF16"
+    if not one_stream:
+        src += "; the stage shares the GPU with %d other streams" % (NS - 1)
+    roof = {"kernel": {"pinv": "k_pinv_refine" if args.pinv == "refined" else dom,
+                       "gemm": "reconstruction GEMMs"}.get(dom, dom),
+            "bound": "alu" if bound == "alu" else bound, "achieved": achieved, "peak": peak,
+            "unit": unit, "frac": achieved / peak,
+            "traffic": None if dom != "gemm" else None, "peak_source": src,
+            "work": "%.4g %s per launch, counted from the step shapes" % (
+                amount, "bytes" if unit == "GB/s" else "FP64 flops" if dom == "pinv" else "flops")}
 
-    roof = roofline_of(stage_ms, budget / sms if NS > 1 else 1.0)
-    roof_seq = roofline_of(stage_seq, 1.0)
-    # the GEMM stage's own rate: from the one-stream run, where it has every SM
-    gemm_tflops = work["gemm"][1] / (stage_seq["gemm"] / args.steps / 1e3) / 1e12
-    # split paths: the tensor pipe runs several BF16 (or TF32) products per
-    # quaternion flop; the effective peak divides the measured one by the
-    # flop-weighted product count (T = U R and Z = C T may differ, BF16X6 /
-    # BF16X3 in the mixed split; TF32 runs at half the BF16 rate)
+    # the GEMM stage: tensor work of the split (products x quaternion flops)
+    # against the measured BF16 burst (TF32 at the nominal half of it)
     f1, f2 = 32.0 * c * r * n, 32.0 * m * c * n
-    nprod = {"bf16x3": (3, 3), "bf16x6": (6, 6), "bf16mixed": (6, 3), "tf32x3": (6, 6)}
-    eff = None
-    if args.prec in nprod:
-        p1, p2 = nprod[args.prec]
-        eff = peaks()[0]["bf16_tflops"] * (f1 + f2) / (p1 * f1 + p2 * f2)
-    gchk = gemm_check(Q, A, D, Q.PREC_NAMES[args.prec], stream)
-    pchk, fp64 = fp64_check(Q, A, D, w, prec, sampler, stream)
+    gemm_s = stage_ms["gemm"] / 1e3
+    gemm_roof = None
+    if args.prec in SPLIT_PRODUCTS:
+        p1, p2 = SPLIT_PRODUCTS[args.prec]
+        tensor_flops = p1 * f1 + p2 * f2
+        gpeak = pk["bf16_tflops"] * (0.5 if args.prec == "tf32x3" else 1.0)
+        gemm_roof = {"bound": "tensor", "achieved": tensor_flops / gemm_s / 1e12, "peak": gpeak,
+                     "unit": "TFLOP/s", "frac": tensor_flops / gemm_s / 1e12 / gpeak,
+                     "quaternion_tflops": (f1 + f2) / gemm_s / 1e12,
+                     "work": "%d f1 + %d f2 tensor flops, f1 = 32 c r n, f2 = 32 m c n"
+                             % (p1, p2),
+                     "traffic": NCU_TRAFFIC["gemm_z"] if workload_name(args) == WORKLOAD
+                                and args.prec == "bf16mixed" else None,
+                     "traffic_kernel": "Z = C T with the fused residual",
+                     "peak_source": pk_kind + " BF16 burst" + (" x 0.5 (TF32)"
+                                                               if args.prec == "tf32x3" else ""),
+                     "stage_ms": stage_ms["gemm"],
+                     "streams": NS}
+    gchk = gemm_check(Q, A, D, Q.PREC_NAMES[args.prec], torch.cuda.current_stream())
+    pchk, fp64 = fp64_check(Q, A, D, w, prec, sampler, torch.cuda.current_stream())
     line = {
         "metric": METRIC, "value": value, "unit": "decompositions/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "steps": K, "warmup": args.warmup, "ms_per_step": t_med / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.prec == "fp32" else args.prec, "data": "synthetic",
         "config": {"workload": workload_name(args), "m": m, "n": n, "c": c, "r": r,
                    "rank_cap": w["rank_cap"], "sampler": w["sampler"], "gemm_prec": args.prec,
-                   "pinv": "fp32-subspace" if args.pinv == "subspace" else "fp64-jacobi",
+                   "pinv": {"refined": "fp64-refined-subspace", "subspace": "fp32-subspace",
+                            "jacobi": "fp64-jacobi"}[args.pinv],
                    "parallelism": "replicas" if world > 1 else "single",
-                   "streams": NS, "max_ctas_per_stream": budget,
+                   "streams": NS, "max_ctas_per_stream": budget or sms,
                    "l2": "inputs larger than L2: 4 row-rotated copies of A (%d MiB) cycled"
                          % (in_bytes >> 20)},
-        # per-stage durations on each decomposition's own stream (the
-        # streams overlap, so these add up to more than ms_per_step)
-        "stage_ms": {k: v / args.steps for k, v in stage_ms.items()},
-        # the same decompositions one at a time on one stream, every SM each,
-        # the L2 flushed (256 MiB write) between steps
-        "sequential": {"value": value_seq, "ms_per_step": t_seq / args.steps,
-                       "stage_ms": {k: v / args.steps for k, v in stage_seq.items()},
-                       "clocks": clk_seq},
-        "gemm_tflops": gemm_tflops, "gemm_tflops_plain_fp32": gchk["tflops_fp32"],
+        "timing": {"repeats": len(reps), "timed_s": sum(reps) / 1e3,
+                   "repeat_ms_median": t_med, "repeat_ms_min": min(reps),
+                   "repeat_ms_max": max(reps),
+                   "rule": "the K-step loop repeated until the repeats cover %.1f s; the "
+                           "median repeat gives value" % args.min_seconds},
+        # per-stage durations on each decomposition's own stream
+        "stage_ms": stage_ms,
+        "pinv_iterations_last_step": sweeps,
+        "gemm_tflops": (f1 + f2) / gemm_s / 1e12, "gemm_tflops_plain_fp32": gchk["tflops_fp32"],
         "gemm_rel_err_vs_fp64_oracle": gchk["rel_err"], "rel_residual": rel,
         # the selected pseudo-inverse against the oracle's FP64 QSVD one on the
         # same W, and C U R against the oracle's C W^+ R (FP64) on sampled rows
@@ -690,26 +719,75 @@ def run_ours(args):
         "cur_check_rows": pchk["rows_sampled"],
         # the whole step with the FP64 one-sided Jacobi pseudo-inverse instead
         "fp64_jacobi_pinv": fp64,
-        "roofline": dict(roof, gemm_effective_peak=eff,
-                         gemm_frac_of_effective_peak=gemm_tflops / eff if eff else None),
-        "roofline_sequential": roof_seq,
-        "e2e": {"value": replica_value(world, args.steps, e2e_ms), "unit": "decompositions/s",
+        "roofline": roof,
+        "gemm_roofline": gemm_roof,
+        "e2e": {"value": replica_value(world, K, e2e_ms), "unit": "decompositions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "pipelining": "%d decompositions in flight on %d streams (%d CTAs each for "
-                              "the persistent kernels); step s+1's upload and step s's "
-                              "read-back overlap the decompositions" % (NS, NS, budget)},
-        "gpu_launches": launches_per_step(args) * args.steps,
+                "pipelining": "%d decomposition(s) in flight; step s+1's upload and step s's "
+                              "read-back overlap the decompositions" % NS},
+        "gpu_launches": launches_per_step(args) * K * len(reps),
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
-        rate, done, el = oracle_rate(A_np, w, args.cpu_seconds)
+        rate, ndone, el = oracle_rate(A_np, w, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "decompositions/s",
                                 "cores": cpu_threads(), "kind": "oracle",
                                 "sample": "%d whole FP64 oracle decompositions (%.1f s)"
-                                          % (done, el)}
+                                          % (ndone, el)}
+        line["cpu_baseline_1core"] = one_core_oracle_rate(workload_name(args), args.cpu_seconds)
+    if not args.no_extra and workload_name(args) == WORKLOAD:
+        line["extra"] = {"color4096_smooth100": color_field_extra(args, Q, synth, dev)}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def color_field_extra(args, Q, synth, dev, steps=3, warmup=1):
+    """The 4096 x 4096 colour field (c = r = 500, rank cap 100, uniform
+    sampling) decomposed with the FP64 Jacobi core, its FP64-accurate option:
+    sigma_101 / sigma_100 ~ 0.97 leaves subspace iteration without a gap at
+    the cap.  Steps timed one at a time with CUDA events (L2 flushed by a
+    256 MiB write before each); U against the oracle's on the last step's W.
+    The FP32 subspace core's time and error beside it, for context."""
+    import torch
+    from oracle import qmcur as O
+    name = "color4096_smooth100"
+    w = dict(synth.WORKLOADS[name])
+    m, n, c, r, k = w["m"], w["n"], w["c"], w["r"], w["rank_cap"]
+    sampler = Q.SAMPLER_NORM if w["sampler"] == "norm" else Q.SAMPLER_UNIFORM
+    prec = Q.PREC_NAMES[args.prec]
+    A_np = synth.make(name)
+    A = torch.from_numpy(A_np).to(dev)
+    D = Q.Decomposition(m, n, c, r, prec, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {"m": m, "n": n, "c": c, "r": r, "rank_cap": k, "sampler": w["sampler"],
+           "gemm_prec": args.prec}
+    for label, meth in (("fp64_jacobi", Q.PINV_JACOBI_FP64), ("fp32_subspace", Q.PINV_SUBSPACE_FP32)):
+        def step(seed):
+            Q.decompose(A, D, sampler=sampler, seed=seed, rcond=w["rcond"], rank_cap=k,
+                        stream=stream, pinv_method=meth)
+        for s_ in range(warmup):
+            step(500 + s_)
+        torch.cuda.synchronize()
+        ts = []
+        for s_ in range(steps):
+            flush.fill_(s_ & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(s_)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        Q.check_status(D.status, name + " " + label)
+        Uo, ko, so = O.pinv_truncated(D.W.cpu().numpy(), w["rcond"], k)
+        err = float(np.linalg.norm(D.U.cpu().numpy() - Uo) / np.linalg.norm(Uo))
+        out[label] = {"value": 1e3 / statistics.median(ts), "unit": "decompositions/s",
+                      "ms_per_step": statistics.median(ts), "steps": steps, "warmup": warmup,
+                      "pinv_rel_err_vs_fp64_oracle": err, "rel_residual": float(D.out3[0].item()),
+                      "fp64_accurate": meth == Q.PINV_JACOBI_FP64}
+        out["sigma_101_over_sigma_100"] = float(so[k] / so[k - 1])
+    return out
 
 
 def run_batch(args):
@@ -723,7 +801,9 @@ def run_batch(args):
     probs = synth.batch_problems(count=512, seed=3)
     As = [torch.from_numpy(p["X"]).cuda() for p in probs]
     stream = torch.cuda.current_stream()
-    pinv_method = Q.PINV_SUBSPACE_FP32 if args.pinv == "subspace" else Q.PINV_JACOBI_FP64
+    # the batched path's cores run one CTA per problem in FP32: the subspace
+    # program (default) or the FP32 Jacobi (--pinv jacobi)
+    pinv_method = Q.PINV_JACOBI_FP64 if args.pinv == "jacobi" else Q.PINV_SUBSPACE_FP32
     B = Q.Batch(As, [p["c"] for p in probs], [p["r"] for p in probs],
                 [p["rank"] for p in probs], sampler=Q.SAMPLER_NORM, seed=0, stream=stream,
                 pinv_method=pinv_method)
@@ -751,8 +831,8 @@ def run_batch(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "batch512_uneven", "problems": 512, "gemm_prec": "fp32",
-                       "pinv": ("fp32-subspace-per-cta" if args.pinv == "subspace"
-                                else "fp32-jacobi-per-cta"), "graph": True,
+                       "pinv": ("fp32-jacobi-per-cta" if args.pinv == "jacobi"
+                                else "fp32-subspace-per-cta"), "graph": True,
                        "gemm_tiles": [int(x) for x in host_tiles(Q, B)],
                        "l2": "flushed between steps (256 MiB write)"},
             "gemm_qtflops_per_step": fl / (ms / 1e3) / 1e12,

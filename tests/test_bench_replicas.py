@@ -98,3 +98,24 @@ def test_clock_samples_kept_inside_the_timed_region(tmp_path, monkeypatch):
         got = c.stop()
         for k, v in want.items():
             assert got[k] == v, (k, got)
+
+
+def test_one_core_cpu_baseline_runs_the_oracle_single_threaded():
+    # the bench's 1-core oracle leg: a child process with every BLAS/OpenMP
+    # pool held to one thread, at least one whole decomposition
+    sys.path.insert(0, ROOT)
+    import bench
+    out = bench.one_core_oracle_rate(bench.WORKLOAD, 0.0)
+    assert out["cores"] == 1 and out["kind"] == "oracle"
+    assert out["value"] is not None and out["value"] > 0, out
+
+
+def test_refined_pinv_flop_count_follows_the_shapes():
+    sys.path.insert(0, ROOT)
+    import bench
+    w = {"c": 200, "r": 200, "rank_cap": 50}
+    # three iterations: the first product, three of the per-iteration set, the final set
+    per_iter = 2 * 200 * 200 * 50 + 4 * 200 * 50 * 50 + 50 ** 3 + 2 * (200 * 50 * 50 // 2)
+    final = 3 * 200 * 2500 + 2 * (400 * 2500 // 2) + 200 * 2500 + 200 * 200 * 50
+    assert bench.pinv_flops(w, "refined", 3) == 32 * (200 * 200 * 50 + 3 * per_iter + final)
+    assert bench.pinv_flops(w, "refined", 4) > bench.pinv_flops(w, "refined", 3)
