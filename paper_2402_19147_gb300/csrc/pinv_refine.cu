@@ -50,6 +50,8 @@
 // identical factors, no barrier) and solves its rows, one warp per row.
 // Every CTA evaluates the stopping rule itself from the same global values,
 // so all take the same branch.
+#include <type_traits>
+
 #include "small_impl.cuh"
 
 namespace qmcur {
@@ -125,6 +127,7 @@ struct RfJob {
   double alpha, beta;
   int minus_eye;
   int norm;
+  int fp64;             // native FP64 tiles (else float-float on the FP32 pipe)
   int splits, kchunk;   // filled by plan_jobs
   int tiles, tn;        // output tiles, tiles along N
 };
@@ -183,32 +186,111 @@ __device__ __forceinline__ void worker_bar(int id) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kRfTileThreads) : "memory");
 }
 
-// Accumulates entry (ty, tx) of tile (tm, tn) over [kb, ke) with one worker.
-// The loads are laid out so that consecutive threads read consecutive
-// addresses of the operand's storage.
-__device__ Q64 rf_tile_acc(const RfJob& j, int tm, int tn, int kb, int ke, Q64* sm, int tid,
-                           int bar_id) {
-  Q64 (*xs)[kRfBK + 1] = reinterpret_cast<Q64 (*)[kRfBK + 1]>(sm);
-  Q64 (*ys)[kRfTS + 1] = reinterpret_cast<Q64 (*)[kRfTS + 1]>(sm + kRfTS * (kRfBK + 1));
+// Float-float arithmetic on the FP32 pipe (GB300 runs FP32 at 64x its FP64
+// rate).  An FP64 operand v is carried as the pair (h, l) = (fl32(v),
+// fl32(v - h)), 48 significant bits.  A real product (a_h + a_l)(b_h + b_l)
+// adds into the running pair (S, C) as
+//   p = a_h b_h, e = fma(a_h, b_h, -p)         (exact product: p + e)
+//   S, err = TwoSum(S, p)                     (exact sum: S + err)
+//   C += err + e + a_h b_l + a_l b_h          (the small terms in FP32)
+// (Knuth's TwoSum and the FMA product split, as in the compensated dot
+// product of Ogita, Rump and Oishi, "Accurate sum and dot product", 2005).
+// The result S + C carries about 2^-46 of sum |a b|.  The rn intrinsics keep
+// the compiler from fusing the rounded product p into a later add.
+struct __align__(16) QFF { float4 h, l; };
+
+__device__ __forceinline__ QFF ff_split(const Q64& v) {
+  QFF r;
+  r.h = make_float4(__double2float_rn(v.x), __double2float_rn(v.y), __double2float_rn(v.z),
+                    __double2float_rn(v.w));
+  r.l = make_float4(__double2float_rn(v.x - (double)r.h.x), __double2float_rn(v.y - (double)r.h.y),
+                    __double2float_rn(v.z - (double)r.h.z), __double2float_rn(v.w - (double)r.h.w));
+  return r;
+}
+
+// (S, C) += sg (ah + al)(bh + bl), sg = +1 or -1 (applied to a)
+template <int SG>
+__device__ __forceinline__ void ff_mac(float& S, float& C, float ah, float al, float bh, float bl) {
+  const float a = SG > 0 ? ah : -ah, a2 = SG > 0 ? al : -al;
+  const float p = __fmul_rn(a, bh);
+  const float e = __fmaf_rn(a, bh, -p);
+  const float sn = __fadd_rn(S, p);
+  const float bp = __fsub_rn(sn, S);
+  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(sn, bp)), __fsub_rn(p, bp));
+  S = sn;
+  C = __fadd_rn(C, __fadd_rn(err, e));
+  C = __fmaf_rn(a, bl, C);
+  C = __fmaf_rn(a2, bh, C);
+}
+
+// acc += x y, Hamilton product (Sec. 2.2), in float-float
+__device__ __forceinline__ void ff_qmac(float S[4], float C[4], const QFF& x, const QFF& y) {
+  const float4 xh = x.h, xl = x.l, yh = y.h, yl = y.l;
+  ff_mac<+1>(S[0], C[0], xh.x, xl.x, yh.x, yl.x); ff_mac<-1>(S[0], C[0], xh.y, xl.y, yh.y, yl.y);
+  ff_mac<-1>(S[0], C[0], xh.z, xl.z, yh.z, yl.z); ff_mac<-1>(S[0], C[0], xh.w, xl.w, yh.w, yl.w);
+  ff_mac<+1>(S[1], C[1], xh.x, xl.x, yh.y, yl.y); ff_mac<+1>(S[1], C[1], xh.y, xl.y, yh.x, yl.x);
+  ff_mac<+1>(S[1], C[1], xh.z, xl.z, yh.w, yl.w); ff_mac<-1>(S[1], C[1], xh.w, xl.w, yh.z, yl.z);
+  ff_mac<+1>(S[2], C[2], xh.x, xl.x, yh.z, yl.z); ff_mac<-1>(S[2], C[2], xh.y, xl.y, yh.w, yl.w);
+  ff_mac<+1>(S[2], C[2], xh.z, xl.z, yh.x, yl.x); ff_mac<+1>(S[2], C[2], xh.w, xl.w, yh.y, yl.y);
+  ff_mac<+1>(S[3], C[3], xh.x, xl.x, yh.w, yl.w); ff_mac<+1>(S[3], C[3], xh.y, xl.y, yh.z, yl.z);
+  ff_mac<-1>(S[3], C[3], xh.z, xl.z, yh.y, yl.y); ff_mac<+1>(S[3], C[3], xh.w, xl.w, yh.x, yl.x);
+}
+
+// Accumulates entry (ty, tx) of tile (tm, tn) over [kb, ke) with one worker,
+// in float-float (FF) or in native FP64.  The loads are laid out so that
+// consecutive threads read consecutive addresses of the operand's storage.
+template <bool FF>
+__device__ __noinline__ Q64 rf_tile_acc_t(const RfJob& j, int tm, int tn, int kb, int ke, Q64* sm, int tid,
+                             int bar_id) {
+  using E = typename std::conditional<FF, QFF, Q64>::type;
+  static_assert(sizeof(E) == sizeof(Q64), "one slot layout");
+  E (*xs)[kRfBK + 1] = reinterpret_cast<E (*)[kRfBK + 1]>(sm);
+  E (*ys)[kRfTS + 1] = reinterpret_cast<E (*)[kRfTS + 1]>(sm + kRfTS * (kRfBK + 1));
   const int tx = tid % kRfTS, ty = tid / kRfTS;
   const int m0 = tm * kRfTS, n0 = tn * kRfTS;
   Q64 acc = q64_zero();
+  float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
+  const int xa = tid / kRfBK, xb = tid % kRfBK;          // xh = 0: contiguous along l
+  const int xr = j.xh ? xb : xa, xl = j.xh ? xa : xb;    // xh = 1: contiguous along rows
+  const int yl = j.yh ? tid % kRfBK : tid / kRfTS;       // yh = 1: contiguous along l
+  const int yc = j.yh ? tid / kRfBK : tid % kRfTS;       // yh = 0: contiguous along columns
   for (int k0 = kb; k0 < ke; k0 += kRfBK) {
-    // op(X) slice 16 x 16: thread -> (row, l) with the contiguous index fastest
-    const int xa = tid / kRfBK, xb = tid % kRfBK;          // xh = 0: contiguous along l
-    const int xr = j.xh ? xb : xa, xl = j.xh ? xa : xb;    // xh = 1: contiguous along rows
     const Q64 xv = ld_opx(j.X, j.xh, j.M, ke, m0 + xr, k0 + xl);
-    const int yl = j.yh ? tid % kRfBK : tid / kRfTS;       // yh = 1: contiguous along l
-    const int yc = j.yh ? tid / kRfBK : tid % kRfTS;       // yh = 0: contiguous along columns
     const Q64 yv = ld_opy(j.Y, j.yh, ke, j.N, k0 + yl, n0 + yc);
     worker_bar(bar_id);   // the previous slice is no longer read
-    xs[xr][xl] = xv;
-    ys[yl][yc] = yv;
+    if constexpr (FF) {
+      xs[xr][xl] = ff_split(xv);
+      ys[yl][yc] = ff_split(yv);
+    } else {
+      xs[xr][xl] = xv;
+      ys[yl][yc] = yv;
+    }
     worker_bar(bar_id);
     const int lend = ke - k0 < kRfBK ? ke - k0 : kRfBK;
-    for (int l = 0; l < lend; ++l) q64_fma(acc, xs[ty][l], ys[l][tx]);
+    if constexpr (FF) {
+      if (lend == kRfBK) {
+#pragma unroll 4
+        for (int l = 0; l < kRfBK; ++l) ff_qmac(S, C, xs[ty][l], ys[l][tx]);
+      } else {
+        for (int l = 0; l < lend; ++l) ff_qmac(S, C, xs[ty][l], ys[l][tx]);
+      }
+    } else {
+      for (int l = 0; l < lend; ++l) q64_fma(acc, xs[ty][l], ys[l][tx]);
+    }
+  }
+  if constexpr (FF) {
+    acc.x = (double)S[0] + (double)C[0];
+    acc.y = (double)S[1] + (double)C[1];
+    acc.z = (double)S[2] + (double)C[2];
+    acc.w = (double)S[3] + (double)C[3];
   }
   return acc;
+}
+
+__device__ __forceinline__ Q64 rf_tile_acc(const RfJob& j, int tm, int tn, int kb, int ke, Q64* sm,
+                                           int tid, int bar_id) {
+  return j.fp64 ? rf_tile_acc_t<false>(j, tm, tn, kb, ke, sm, tid, bar_id)
+                : rf_tile_acc_t<true>(j, tm, tn, kb, ke, sm, tid, bar_id);
 }
 
 __device__ __forceinline__ double rf_sq(const Q64& a) {
@@ -366,7 +448,7 @@ __device__ void rf_trsm_row(const QPtr& Y, const QPtr& Z, int row, int k, const 
   }
 }
 
-__device__ void rf_trsm_row_any(const QPtr& Y, const QPtr& Z, int row, int k, const float* rpk) {
+__device__ __noinline__ void rf_trsm_row_any(const QPtr& Y, const QPtr& Z, int row, int k, const float* rpk) {
   if (k <= 32) rf_trsm_row<1>(Y, Z, row, k, rpk);
   else if (k <= 64) rf_trsm_row<2>(Y, Z, row, k, rpk);
   else if (k <= 96) rf_trsm_row<3>(Y, Z, row, k, rpk);
@@ -481,31 +563,40 @@ struct StopState {
 
 // Whether the P about to be formed at iteration s is within kAngleTol of S.
 // rho_s (from nd = ||Z - P M'||^2, nz = ||Z||^2) times 4 kappa^2 bounds the
-// angle of the current P; rho below the rounding floor is extrapolated from
-// the last reliable value at the observed contraction.  Iteration 1 starts
+// angle of the current P, and the angle shrinks by a constant factor per
+// iteration.  rho has a floor set by the float-float products that form Z
+// (about 2^-46 sqrt(k) relative): values above 32 times it are reliable.
+// Below it, rho is extrapolated from the last reliable value at the
+// contraction seen between two reliable values; with only one reliable value,
+// the fall from it onto the floor bounds the contraction.  Iteration 1 starts
 // from the random block, whose rho means nothing.
 __device__ __forceinline__ bool stop_now(StopState& st, int s, double nd, double nz, double kap2,
                                          int k) {
   if (s < 2 || !(nz > 0.0)) return false;
   const double rho = sqrt(fmax(nd, 0.0) / nz);
-  const double reliable = 64.0 * 0x1.0p-53 * sqrt(2.0 * k);
-  double est;
+  const double reliable = 32.0 * 0x1.0p-46 * sqrt((double)k);
+  double est, contr;
   if (rho > reliable) {
     if (st.prev_s > 0) st.contr = fmin(rho / st.prev_rho, 0.999);
     st.prev_rho = rho;
     st.prev_s = s;
     st.floor_hits = 0;
     est = rho;
+    contr = st.contr;
   } else if (st.prev_s > 0 && st.contr > 0.0) {
     est = st.prev_rho * pow(st.contr, (double)(s - st.prev_s));
+    contr = st.contr;
+  } else if (st.prev_s > 0) {
+    est = rho;
+    contr = fmin(reliable / st.prev_rho, 0.999);   // at most the fall onto the floor
   } else {
-    // at the floor with no history: W^H W leaves span(P) invariant to
-    // working accuracy; twice in a row settles it
+    // at the floor with no history: W^H W leaves span(P) invariant to the
+    // products' accuracy; twice in a row settles it
     return ++st.floor_hits >= 2 || 4.0 * rho * kap2 <= kAngleTol;
   }
   const double angle = 4.0 * est * kap2;
   if (angle <= kAngleTol) return true;
-  return st.contr > 0.0 && angle * st.contr <= kAngleTol;
+  return contr > 0.0 && angle * contr <= kAngleTol;
 }
 
 __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_constant__ RfArgs a) {
@@ -551,12 +642,14 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
     jb[0].Zin = a.M;
     jb[0].alpha = -1.0;
     jb[0].beta = 1.0;
+    jb[0].fp64 = 1;
     plan_jobs(jb, 1, a.workers);
     rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
     if (!rf_sync(a, target)) return;
     jb[0] = job(a.Zp, 1, a.Zp, 0, a.Gp, k, k, c);   // G' = Z'^H Z'
     jb[1] = job(P, 0, a.Mp, 0, a.Z, c, k, k);       // ||Z - P M'||, ||Z||
     jb[1].norm = 1;
+    jb[1].fp64 = 1;   // its cancellation sets the floor of rho
     plan_jobs(jb, 2, a.workers);
     rf_gemm_step(a, jb, 2, a.norms + 2 * s, vb, vg, smr);
     if (!rf_sync(a, target)) return;
