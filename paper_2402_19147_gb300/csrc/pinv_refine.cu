@@ -1,5 +1,5 @@
-// Rank-capped pseudo-inverse U = W_k^+ to FP64 accuracy on GB300, whose FP64
-// units run at 1/64 of its FP32 rate (about 2 FP64 FMA per clock per SM).
+// Rank-capped pseudo-inverse U = W_k^+ to FP64-level accuracy on GB300, whose
+// FP64 units run at 1/64 of its FP32 rate (about 2 FP64 FMA per clock per SM).
 //
 // The truncated inverse of Sec. 2.2 / Algorithm 1 keeps the k = rank_cap
 // largest singular triplets of W (r x c): U = V_k Sigma_k^-1 P_k^H.  It only
@@ -7,18 +7,26 @@
 // P of S (full column rank, not necessarily orthonormal),
 //   U = P (W P)^+,
 // because W P = P_k Sigma_k (V_k^H P) and (V_k^H P) is invertible.  So the
-// method finds S to FP64 accuracy by subspace iteration with FP64 products
-// (all SMs), and never factors anything in FP64: every k x k Cholesky factor
-// is taken in FP32 (one CTA, shared memory) and used only as a right
-// preconditioner, Z R^-1 with the FP32 R applied in FP64 arithmetic.  Such a
-// solve changes the basis but not its span, so the FP32 rounding of R never
-// reaches the result; it only leaves the bases orthonormal to FP32 accuracy,
-// and the one place where orthonormality matters (the final Q^+ = Q^H) is
-// corrected to first order with the FP64 Gram matrix E = Q^H Q - I.
+// method finds S to working accuracy by subspace iteration and never factors
+// anything in high precision: every k x k Cholesky factor is taken in FP32
+// (one CTA, shared memory) and used only as a right preconditioner, Z R^-1
+// with the FP32 R applied in the working precision.  Such a solve changes the
+// basis but not its span, so the FP32 rounding of R never reaches the
+// result; it only leaves the bases orthonormal to FP32 accuracy, and the one
+// place where orthonormality matters (the final Q^+ = Q^H) is corrected to
+// first order with the Gram matrix E = Q^H Q - I.
+//
+// Working precision: float-float on the FP32 pipe.  Every intermediate matrix
+// is stored as an unevaluated pair of FP32 values per entry (h, l), h = fl(h +
+// l), about 48 significant bits; products accumulate exactly-rounded FP32
+// products and sums with their error terms (TwoProd by FMA and Knuth's
+// TwoSum, as in the compensated dot product of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 2005), so that a
+// product carries about 2^-46 of sum |x| |y|.  W is split into pairs once.
 //
 // Iteration s, from P (c x k, near-orthonormal) and Y = W P:
-//   Z  = W^H Y                         FP64 product (c x k, K = r)
-//   M  = P^H Z,  E = P^H P - I          FP64 Gram products (k x k)
+//   Z  = W^H Y                         product (c x k, K = r)
+//   M  = P^H Z,  E = P^H P - I          Gram products (k x k)
 //   R_Y = chol32(M);  Z' = Z R_Y^-1     (= W^H Q with Q = Y R_Y^-1, the
 //                                        left basis normalised)
 //   M' = M - E M                        (P (I - E) P^H: the projector on span P
@@ -50,8 +58,6 @@
 // identical factors, no barrier) and solves its rows, one warp per row.
 // Every CTA evaluates the stopping rule itself from the same global values,
 // so all take the same branch.
-#include <type_traits>
-
 #include "small_impl.cuh"
 
 namespace qmcur {
@@ -72,90 +78,146 @@ constexpr float kCholShift = 1e-5f;                  // relative diagonal shift 
 
 static_assert(kRfWorkers * kRfTileThreads == kRfThreads, "whole tile workers");
 
-struct __align__(16) Q64 { double x, y, z, w; };
+// ---------------------------------------------------------------------------
+// Float-float arithmetic.  A pair (h, l) stands for h + l.  The rn
+// intrinsics keep the compiler from fusing a rounded product into a later
+// add, which would break the error terms.
 
-__device__ __forceinline__ Q64 q64_zero() { return Q64{0.0, 0.0, 0.0, 0.0}; }
+struct __align__(16) QFF { float4 h, l; };   // one quaternion entry as pairs
 
-// acc += a b (Hamilton product, Sec. 2.2), FP64
-__device__ __forceinline__ void q64_fma(Q64& acc, const Q64& a, const Q64& b) {
-  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x); acc.x = fma(-a.z, b.z, acc.x); acc.x = fma(-a.w, b.w, acc.x);
-  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y); acc.y = fma(a.z, b.w, acc.y); acc.y = fma(-a.w, b.z, acc.y);
-  acc.z = fma(a.x, b.z, acc.z); acc.z = fma(-a.y, b.w, acc.z); acc.z = fma(a.z, b.x, acc.z); acc.z = fma(a.w, b.y, acc.z);
-  acc.w = fma(a.x, b.w, acc.w); acc.w = fma(a.y, b.z, acc.w); acc.w = fma(-a.z, b.y, acc.w); acc.w = fma(a.w, b.x, acc.w);
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
-// acc -= a b with b given in FP32 (a factor entry)
-__device__ __forceinline__ void q64_fms_f(Q64& acc, const Q64& a, const float4 bf) {
-  const double bx = bf.x, by = bf.y, bz = bf.z, bw = bf.w;
-  acc.x -= a.x * bx - a.y * by - a.z * bz - a.w * bw;
-  acc.y -= a.x * by + a.y * bx + a.z * bw - a.w * bz;
-  acc.z -= a.x * bz - a.y * bw + a.z * bx + a.w * by;
-  acc.w -= a.x * bw + a.y * bz - a.z * by + a.w * bx;
+// (h, l) = the pair of s + c, renormalised
+__device__ __forceinline__ void ff_norm(float s, float c, float& h, float& l) {
+  float e;
+  two_sum(s, c, h, e);
+  l = e;
 }
 
-__device__ __forceinline__ double ldp(const QPtr& q, int t, int64_t off) {
-  if (q.dtype == QMCUR_F64) return reinterpret_cast<const double*>(q.p[t])[off];
-  return (double)reinterpret_cast<const float*>(q.p[t])[off];
+// r = a + b
+__device__ __forceinline__ void ff_add1(float ah, float al, float bh, float bl, float& rh, float& rl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  ff_norm(s, __fadd_rn(__fadd_rn(al, bl), e), rh, rl);
 }
 
-__device__ __forceinline__ Q64 ldq64(const QPtr& q, int64_t off) {
-  return Q64{ldp(q, 0, off), ldp(q, 1, off), ldp(q, 2, off), ldp(q, 3, off)};
+__device__ __forceinline__ QFF qff_add(const QFF& a, const QFF& b) {
+  QFF r;
+  ff_add1(a.h.x, a.l.x, b.h.x, b.l.x, r.h.x, r.l.x);
+  ff_add1(a.h.y, a.l.y, b.h.y, b.l.y, r.h.y, r.l.y);
+  ff_add1(a.h.z, a.l.z, b.h.z, b.l.z, r.h.z, r.l.z);
+  ff_add1(a.h.w, a.l.w, b.h.w, b.l.w, r.h.w, r.l.w);
+  return r;
 }
 
-__device__ __forceinline__ void stq64(const QPtr& q, int64_t off, const Q64& v) {
-  if (q.dtype == QMCUR_F64) {
-    reinterpret_cast<double*>(q.p[0])[off] = v.x;
-    reinterpret_cast<double*>(q.p[1])[off] = v.y;
-    reinterpret_cast<double*>(q.p[2])[off] = v.z;
-    reinterpret_cast<double*>(q.p[3])[off] = v.w;
+__device__ __forceinline__ QFF qff_neg(QFF a) {
+  a.h = make_float4(-a.h.x, -a.h.y, -a.h.z, -a.h.w);
+  a.l = make_float4(-a.l.x, -a.l.y, -a.l.z, -a.l.w);
+  return a;
+}
+
+__device__ __forceinline__ QFF qff_zero() {
+  return QFF{make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+}
+
+// Loads and stores: kDtypeFF planes hold float2 (h, l) per entry; F64 and F32
+// planes (the caller's W and U) are split / rounded on the way.
+__device__ __forceinline__ QFF ldff(const QPtr& q, int64_t off) {
+  QFF v;
+  if (q.dtype == kDtypeFF) {
+    const float2 a = reinterpret_cast<const float2*>(q.p[0])[off];
+    const float2 b = reinterpret_cast<const float2*>(q.p[1])[off];
+    const float2 c = reinterpret_cast<const float2*>(q.p[2])[off];
+    const float2 d = reinterpret_cast<const float2*>(q.p[3])[off];
+    v.h = make_float4(a.x, b.x, c.x, d.x);
+    v.l = make_float4(a.y, b.y, c.y, d.y);
+  } else if (q.dtype == QMCUR_F64) {
+    float hh[4], ll[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const double x = reinterpret_cast<const double*>(q.p[t])[off];
+      hh[t] = __double2float_rn(x);
+      ll[t] = __double2float_rn(x - (double)hh[t]);
+    }
+    v.h = make_float4(hh[0], hh[1], hh[2], hh[3]);
+    v.l = make_float4(ll[0], ll[1], ll[2], ll[3]);
   } else {
-    reinterpret_cast<float*>(q.p[0])[off] = (float)v.x;
-    reinterpret_cast<float*>(q.p[1])[off] = (float)v.y;
-    reinterpret_cast<float*>(q.p[2])[off] = (float)v.z;
-    reinterpret_cast<float*>(q.p[3])[off] = (float)v.w;
+    v.h = make_float4(reinterpret_cast<const float*>(q.p[0])[off],
+                      reinterpret_cast<const float*>(q.p[1])[off],
+                      reinterpret_cast<const float*>(q.p[2])[off],
+                      reinterpret_cast<const float*>(q.p[3])[off]);
+    v.l = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  return v;
+}
+
+__device__ __forceinline__ void stff(const QPtr& q, int64_t off, const QFF& v) {
+  if (q.dtype == kDtypeFF) {
+    reinterpret_cast<float2*>(q.p[0])[off] = make_float2(v.h.x, v.l.x);
+    reinterpret_cast<float2*>(q.p[1])[off] = make_float2(v.h.y, v.l.y);
+    reinterpret_cast<float2*>(q.p[2])[off] = make_float2(v.h.z, v.l.z);
+    reinterpret_cast<float2*>(q.p[3])[off] = make_float2(v.h.w, v.l.w);
+  } else if (q.dtype == QMCUR_F64) {
+    reinterpret_cast<double*>(q.p[0])[off] = (double)v.h.x + (double)v.l.x;
+    reinterpret_cast<double*>(q.p[1])[off] = (double)v.h.y + (double)v.l.y;
+    reinterpret_cast<double*>(q.p[2])[off] = (double)v.h.z + (double)v.l.z;
+    reinterpret_cast<double*>(q.p[3])[off] = (double)v.h.w + (double)v.l.w;
+  } else {
+    reinterpret_cast<float*>(q.p[0])[off] = __fadd_rn(v.h.x, v.l.x);
+    reinterpret_cast<float*>(q.p[1])[off] = __fadd_rn(v.h.y, v.l.y);
+    reinterpret_cast<float*>(q.p[2])[off] = __fadd_rn(v.h.z, v.l.z);
+    reinterpret_cast<float*>(q.p[3])[off] = __fadd_rn(v.h.w, v.l.w);
   }
 }
 
 // One product of a step: Zout = alpha op(X) op(Y) + beta Zin - [minus_eye] I,
-// op(X) M x K (X stored K x M when xh: op(X) = X^H), op(Y) K x N likewise.
-// With norm, nothing is stored: the step folds ||Zin - op(X) op(Y)||_F^2 and
-// ||Zin||_F^2 into norm_out[0..1] (fixed order).
+// alpha in {1, -1}, beta in {0, 1}; op(X) M x K (X stored K x M when xh:
+// op(X) = X^H), op(Y) K x N likewise.  With norm, nothing is stored: the step
+// folds ||Zin - op(X) op(Y)||_F^2 and ||Zin||_F^2 into norm_out[0..1] (fixed
+// order).
 struct RfJob {
   QPtr X, Y, Zin, Zout;
   int M, N, K;
   int xh, yh;
-  double alpha, beta;
+  int neg;              // alpha = -1
+  int add_in;           // beta = 1
   int minus_eye;
   int norm;
-  int fp64;             // native FP64 tiles (else float-float on the FP32 pipe)
+  float scale;          // exact power of two applied to the stored result (0: none)
   int splits, kchunk;   // filled by plan_jobs
   int tiles, tn;        // output tiles, tiles along N
 };
 
 struct RfArgs {
   QPtr W;              // r x c input (F32 or F64 planes)
+  QPtr Wf;             // W as pairs
   int r, c, k;
   int max_iter;
   uint64_t seed;
-  // FP64 workspaces
+  // float-float workspaces
   QPtr P[2], Y, Z, Zp, M, E, Mp, Gp, G1, G2, E2, Q1, Q2, T1, T2, V;
   QPtr U;              // c x r output
-  Q64* part;           // kRfMaxParts x kRfTileThreads split partials
+  QFF* part;           // kRfMaxParts x kRfTileThreads split partials
   unsigned* cnt;       // kRfMaxTiles split-tile arrival counts, then the norm fold's
   double* normpart;    // kRfMaxTiles x 2 tile norm partials
   double* norms;       // (kRfMaxIter + 1) x 2
   double* kap2;        // kRfMaxIter + 1
   unsigned* bar;       // grid barrier words
+  unsigned* wmax;      // bits of max |W_ij| over the planes (atomicMax, zeroed)
   int32_t* status;
   int32_t* rank_out;
   int workers;         // gridDim.x * kRfWorkers (for the split plans)
 };
 
 // smem: two tile workers' operand slices, or the packed factor + Cholesky buffers
-constexpr int kRfWorkerQ64 = 2 * kRfTS * (kRfBK + 1);
+constexpr int kRfWorkerQ = 2 * kRfTS * (kRfBK + 1);
 constexpr size_t rf_chol_off(int k) { return (sm_trsm_bytes(k) + 15) / 16 * 16; }
 constexpr size_t rf_smem(int k) {
-  const size_t g = (size_t)kRfWorkers * kRfWorkerQ64 * sizeof(Q64);
+  const size_t g = (size_t)kRfWorkers * kRfWorkerQ * sizeof(QFF);
   const size_t s = rf_chol_off(k) + sm_chol_bytes();
   return g > s ? g : s;
 }
@@ -163,160 +225,148 @@ constexpr size_t rf_smem(int k) {
 // ---------------------------------------------------------------------------
 // Products.
 
-// Entry (row i, k-index l) of op(X) for an M x K operand view (X stored K x M
-// and conjugated when xh); zero outside.
-__device__ __forceinline__ Q64 ld_opx(const QPtr& X, int xh, int M, int K, int i, int l) {
-  if (i >= M || l >= K) return q64_zero();
-  if (!xh) return ldq64(X, (int64_t)i * X.ld + l);
-  Q64 v = ldq64(X, (int64_t)l * X.ld + i);
-  v.y = -v.y; v.z = -v.z; v.w = -v.w;
+__device__ __forceinline__ QFF qff_conj(QFF v) {
+  v.h.y = -v.h.y; v.h.z = -v.h.z; v.h.w = -v.h.w;
+  v.l.y = -v.l.y; v.l.z = -v.l.z; v.l.w = -v.l.w;
   return v;
 }
 
+// Entry (row i, k-index l) of op(X) for an M x K operand view (X stored K x M
+// and conjugated when xh); zero outside.
+__device__ __forceinline__ QFF ld_opx(const QPtr& X, int xh, int M, int K, int i, int l) {
+  if (i >= M || l >= K) return qff_zero();
+  if (!xh) return ldff(X, (int64_t)i * X.ld + l);
+  return qff_conj(ldff(X, (int64_t)l * X.ld + i));
+}
+
 // Entry (k-index l, column j) of op(Y) for a K x N operand view.
-__device__ __forceinline__ Q64 ld_opy(const QPtr& Y, int yh, int K, int N, int l, int j) {
-  if (l >= K || j >= N) return q64_zero();
-  if (!yh) return ldq64(Y, (int64_t)l * Y.ld + j);
-  Q64 v = ldq64(Y, (int64_t)j * Y.ld + l);
-  v.y = -v.y; v.z = -v.z; v.w = -v.w;
-  return v;
+__device__ __forceinline__ QFF ld_opy(const QPtr& Y, int yh, int K, int N, int l, int j) {
+  if (l >= K || j >= N) return qff_zero();
+  if (!yh) return ldff(Y, (int64_t)l * Y.ld + j);
+  return qff_conj(ldff(Y, (int64_t)j * Y.ld + l));
 }
 
 __device__ __forceinline__ void worker_bar(int id) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kRfTileThreads) : "memory");
 }
 
-// Float-float arithmetic on the FP32 pipe (GB300 runs FP32 at 64x its FP64
-// rate).  An FP64 operand v is carried as the pair (h, l) = (fl32(v),
-// fl32(v - h)), 48 significant bits.  A real product (a_h + a_l)(b_h + b_l)
-// adds into the running pair (S, C) as
-//   p = a_h b_h, e = fma(a_h, b_h, -p)         (exact product: p + e)
-//   S, err = TwoSum(S, p)                     (exact sum: S + err)
-//   C += err + e + a_h b_l + a_l b_h          (the small terms in FP32)
-// (Knuth's TwoSum and the FMA product split, as in the compensated dot
-// product of Ogita, Rump and Oishi, "Accurate sum and dot product", 2005).
-// The result S + C carries about 2^-46 of sum |a b|.  The rn intrinsics keep
-// the compiler from fusing the rounded product p into a later add.
-struct __align__(16) QFF { float4 h, l; };
-
-__device__ __forceinline__ QFF ff_split(const Q64& v) {
-  QFF r;
-  r.h = make_float4(__double2float_rn(v.x), __double2float_rn(v.y), __double2float_rn(v.z),
-                    __double2float_rn(v.w));
-  r.l = make_float4(__double2float_rn(v.x - (double)r.h.x), __double2float_rn(v.y - (double)r.h.y),
-                    __double2float_rn(v.z - (double)r.h.z), __double2float_rn(v.w - (double)r.h.w));
-  return r;
-}
-
-// (S, C) += sg (ah + al)(bh + bl), sg = +1 or -1 (applied to a)
-template <int SG>
-__device__ __forceinline__ void ff_mac(float& S, float& C, float ah, float al, float bh, float bl) {
-  const float a = SG > 0 ? ah : -ah, a2 = SG > 0 ? al : -al;
-  const float p = __fmul_rn(a, bh);
-  const float e = __fmaf_rn(a, bh, -p);
-  const float sn = __fadd_rn(S, p);
-  const float bp = __fsub_rn(sn, S);
-  const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(sn, bp)), __fsub_rn(p, bp));
+// The four real products of one quaternion component, added into (S, C):
+// p_i = sg_i a_i b_i exactly as (p_i, e_i); the four are summed pairwise with
+// their errors before one TwoSum into S, which keeps the dependency chain
+// through S one TwoSum long per k step; the cross terms a_h b_l + a_l b_h go
+// to C in FP32.
+template <int S0, int S1, int S2, int S3>
+__device__ __forceinline__ void ff_comp4(float& S, float& C, float a0, float a0l, float b0,
+                                         float b0l, float a1, float a1l, float b1, float b1l,
+                                         float a2, float a2l, float b2, float b2l, float a3,
+                                         float a3l, float b3, float b3l) {
+  const float x0 = S0 > 0 ? a0 : -a0, x1 = S1 > 0 ? a1 : -a1;
+  const float x2 = S2 > 0 ? a2 : -a2, x3 = S3 > 0 ? a3 : -a3;
+  const float y0 = S0 > 0 ? a0l : -a0l, y1 = S1 > 0 ? a1l : -a1l;
+  const float y2 = S2 > 0 ? a2l : -a2l, y3 = S3 > 0 ? a3l : -a3l;
+  const float p0 = __fmul_rn(x0, b0), p1 = __fmul_rn(x1, b1);
+  const float p2 = __fmul_rn(x2, b2), p3 = __fmul_rn(x3, b3);
+  float c = __fmaf_rn(x0, b0, -p0);
+  c = __fadd_rn(c, __fmaf_rn(x1, b1, -p1));
+  c = __fadd_rn(c, __fmaf_rn(x2, b2, -p2));
+  c = __fadd_rn(c, __fmaf_rn(x3, b3, -p3));
+  float s01, e01, s23, e23, s, e;
+  two_sum(p0, p1, s01, e01);
+  two_sum(p2, p3, s23, e23);
+  two_sum(s01, s23, s, e);
+  float sn, en;
+  two_sum(S, s, sn, en);
   S = sn;
-  C = __fadd_rn(C, __fadd_rn(err, e));
-  C = __fmaf_rn(a, bl, C);
-  C = __fmaf_rn(a2, bh, C);
+  c = __fadd_rn(c, __fadd_rn(__fadd_rn(e01, e23), __fadd_rn(e, en)));
+  c = __fmaf_rn(x0, b0l, c); c = __fmaf_rn(y0, b0, c);
+  c = __fmaf_rn(x1, b1l, c); c = __fmaf_rn(y1, b1, c);
+  c = __fmaf_rn(x2, b2l, c); c = __fmaf_rn(y2, b2, c);
+  c = __fmaf_rn(x3, b3l, c); c = __fmaf_rn(y3, b3, c);
+  C = __fadd_rn(C, c);
 }
 
-// acc += x y, Hamilton product (Sec. 2.2), in float-float
+// (S, C) += x y, the Hamilton product (Sec. 2.2) in float-float
 __device__ __forceinline__ void ff_qmac(float S[4], float C[4], const QFF& x, const QFF& y) {
-  const float4 xh = x.h, xl = x.l, yh = y.h, yl = y.l;
-  ff_mac<+1>(S[0], C[0], xh.x, xl.x, yh.x, yl.x); ff_mac<-1>(S[0], C[0], xh.y, xl.y, yh.y, yl.y);
-  ff_mac<-1>(S[0], C[0], xh.z, xl.z, yh.z, yl.z); ff_mac<-1>(S[0], C[0], xh.w, xl.w, yh.w, yl.w);
-  ff_mac<+1>(S[1], C[1], xh.x, xl.x, yh.y, yl.y); ff_mac<+1>(S[1], C[1], xh.y, xl.y, yh.x, yl.x);
-  ff_mac<+1>(S[1], C[1], xh.z, xl.z, yh.w, yl.w); ff_mac<-1>(S[1], C[1], xh.w, xl.w, yh.z, yl.z);
-  ff_mac<+1>(S[2], C[2], xh.x, xl.x, yh.z, yl.z); ff_mac<-1>(S[2], C[2], xh.y, xl.y, yh.w, yl.w);
-  ff_mac<+1>(S[2], C[2], xh.z, xl.z, yh.x, yl.x); ff_mac<+1>(S[2], C[2], xh.w, xl.w, yh.y, yl.y);
-  ff_mac<+1>(S[3], C[3], xh.x, xl.x, yh.w, yl.w); ff_mac<+1>(S[3], C[3], xh.y, xl.y, yh.z, yl.z);
-  ff_mac<-1>(S[3], C[3], xh.z, xl.z, yh.y, yl.y); ff_mac<+1>(S[3], C[3], xh.w, xl.w, yh.x, yl.x);
+  const float4 a = x.h, al = x.l, b = y.h, bl = y.l;
+  // z0 = x0 y0 - x1 y1 - x2 y2 - x3 y3
+  ff_comp4<+1, -1, -1, -1>(S[0], C[0], a.x, al.x, b.x, bl.x, a.y, al.y, b.y, bl.y, a.z, al.z, b.z,
+                           bl.z, a.w, al.w, b.w, bl.w);
+  // z1 = x0 y1 + x1 y0 + x2 y3 - x3 y2
+  ff_comp4<+1, +1, +1, -1>(S[1], C[1], a.x, al.x, b.y, bl.y, a.y, al.y, b.x, bl.x, a.z, al.z, b.w,
+                           bl.w, a.w, al.w, b.z, bl.z);
+  // z2 = x0 y2 - x1 y3 + x2 y0 + x3 y1
+  ff_comp4<+1, -1, +1, +1>(S[2], C[2], a.x, al.x, b.z, bl.z, a.y, al.y, b.w, bl.w, a.z, al.z, b.x,
+                           bl.x, a.w, al.w, b.y, bl.y);
+  // z3 = x0 y3 + x1 y2 - x2 y1 + x3 y0
+  ff_comp4<+1, +1, -1, +1>(S[3], C[3], a.x, al.x, b.w, bl.w, a.y, al.y, b.z, bl.z, a.z, al.z, b.y,
+                           bl.y, a.w, al.w, b.x, bl.x);
 }
 
-// Accumulates entry (ty, tx) of tile (tm, tn) over [kb, ke) with one worker,
-// in float-float (FF) or in native FP64.  The loads are laid out so that
-// consecutive threads read consecutive addresses of the operand's storage.
-template <bool FF>
-__device__ __noinline__ Q64 rf_tile_acc_t(const RfJob& j, int tm, int tn, int kb, int ke, Q64* sm, int tid,
-                             int bar_id) {
-  using E = typename std::conditional<FF, QFF, Q64>::type;
-  static_assert(sizeof(E) == sizeof(Q64), "one slot layout");
-  E (*xs)[kRfBK + 1] = reinterpret_cast<E (*)[kRfBK + 1]>(sm);
-  E (*ys)[kRfTS + 1] = reinterpret_cast<E (*)[kRfTS + 1]>(sm + kRfTS * (kRfBK + 1));
+// Accumulates entry (ty, tx) of tile (tm, tn) over [kb, ke) with one worker.
+// The loads are laid out so that consecutive threads read consecutive
+// addresses of the operand's storage.
+__device__ __noinline__ QFF rf_tile_acc(const RfJob& j, int tm, int tn, int kb, int ke, QFF* sm,
+                                        int tid, int bar_id) {
+  QFF (*xs)[kRfBK + 1] = reinterpret_cast<QFF (*)[kRfBK + 1]>(sm);
+  QFF (*ys)[kRfTS + 1] = reinterpret_cast<QFF (*)[kRfTS + 1]>(sm + kRfTS * (kRfBK + 1));
   const int tx = tid % kRfTS, ty = tid / kRfTS;
   const int m0 = tm * kRfTS, n0 = tn * kRfTS;
-  Q64 acc = q64_zero();
   float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
   const int xa = tid / kRfBK, xb = tid % kRfBK;          // xh = 0: contiguous along l
   const int xr = j.xh ? xb : xa, xl = j.xh ? xa : xb;    // xh = 1: contiguous along rows
   const int yl = j.yh ? tid % kRfBK : tid / kRfTS;       // yh = 1: contiguous along l
   const int yc = j.yh ? tid / kRfBK : tid % kRfTS;       // yh = 0: contiguous along columns
+  QFF xv = ld_opx(j.X, j.xh, j.M, ke, m0 + xr, kb + xl);
+  QFF yv = ld_opy(j.Y, j.yh, ke, j.N, kb + yl, n0 + yc);
   for (int k0 = kb; k0 < ke; k0 += kRfBK) {
-    const Q64 xv = ld_opx(j.X, j.xh, j.M, ke, m0 + xr, k0 + xl);
-    const Q64 yv = ld_opy(j.Y, j.yh, ke, j.N, k0 + yl, n0 + yc);
     worker_bar(bar_id);   // the previous slice is no longer read
-    if constexpr (FF) {
-      xs[xr][xl] = ff_split(xv);
-      ys[yl][yc] = ff_split(yv);
-    } else {
-      xs[xr][xl] = xv;
-      ys[yl][yc] = yv;
-    }
+    xs[xr][xl] = xv;
+    ys[yl][yc] = yv;
     worker_bar(bar_id);
+    if (k0 + kRfBK < ke) {   // the next slice's loads in flight during this one
+      xv = ld_opx(j.X, j.xh, j.M, ke, m0 + xr, k0 + kRfBK + xl);
+      yv = ld_opy(j.Y, j.yh, ke, j.N, k0 + kRfBK + yl, n0 + yc);
+    }
     const int lend = ke - k0 < kRfBK ? ke - k0 : kRfBK;
-    if constexpr (FF) {
-      if (lend == kRfBK) {
-#pragma unroll 4
-        for (int l = 0; l < kRfBK; ++l) ff_qmac(S, C, xs[ty][l], ys[l][tx]);
-      } else {
-        for (int l = 0; l < lend; ++l) ff_qmac(S, C, xs[ty][l], ys[l][tx]);
-      }
+    if (lend == kRfBK) {
+#pragma unroll 2
+      for (int l = 0; l < kRfBK; ++l) ff_qmac(S, C, xs[ty][l], ys[l][tx]);
     } else {
-      for (int l = 0; l < lend; ++l) q64_fma(acc, xs[ty][l], ys[l][tx]);
+      for (int l = 0; l < lend; ++l) ff_qmac(S, C, xs[ty][l], ys[l][tx]);
     }
   }
-  if constexpr (FF) {
-    acc.x = (double)S[0] + (double)C[0];
-    acc.y = (double)S[1] + (double)C[1];
-    acc.z = (double)S[2] + (double)C[2];
-    acc.w = (double)S[3] + (double)C[3];
-  }
+  QFF acc;
+  ff_norm(S[0], C[0], acc.h.x, acc.l.x);
+  ff_norm(S[1], C[1], acc.h.y, acc.l.y);
+  ff_norm(S[2], C[2], acc.h.z, acc.l.z);
+  ff_norm(S[3], C[3], acc.h.w, acc.l.w);
   return acc;
 }
 
-__device__ __forceinline__ Q64 rf_tile_acc(const RfJob& j, int tm, int tn, int kb, int ke, Q64* sm,
-                                           int tid, int bar_id) {
-  return j.fp64 ? rf_tile_acc_t<false>(j, tm, tn, kb, ke, sm, tid, bar_id)
-                : rf_tile_acc_t<true>(j, tm, tn, kb, ke, sm, tid, bar_id);
-}
-
-__device__ __forceinline__ double rf_sq(const Q64& a) {
-  return a.x * a.x + a.y * a.y + a.z * a.z + a.w * a.w;
-}
-
-// Epilogue of one finished tile entry: store, or the norm partials.
-__device__ void rf_epilogue(const RfJob& j, int tm, int tn, int tid, const Q64& acc,
-                            double* nd, double* nz) {
+// Epilogue of one finished tile entry: store, or the norm partials (of the
+// leading parts: only the size of rho matters).
+__device__ void rf_epilogue(const RfJob& j, int tm, int tn, int tid, const QFF& acc, double* nd,
+                            double* nz) {
   const int i = tm * kRfTS + tid / kRfTS, c = tn * kRfTS + tid % kRfTS;
   if (i >= j.M || c >= j.N) return;
   const int64_t oin = (int64_t)i * j.Zin.ld + c;
   if (j.norm) {
-    const Q64 z = ldq64(j.Zin, oin);
-    const Q64 d{z.x - acc.x, z.y - acc.y, z.z - acc.z, z.w - acc.w};
-    *nd += rf_sq(d);
-    *nz += rf_sq(z);
+    const QFF z = ldff(j.Zin, oin);
+    const QFF d = qff_add(z, qff_neg(acc));
+    const double dx = d.h.x, dy = d.h.y, dz = d.h.z, dw = d.h.w;
+    const double zx = z.h.x, zy = z.h.y, zz = z.h.z, zw = z.h.w;
+    *nd += dx * dx + dy * dy + dz * dz + dw * dw;
+    *nz += zx * zx + zy * zy + zz * zz + zw * zw;
     return;
   }
-  Q64 v{j.alpha * acc.x, j.alpha * acc.y, j.alpha * acc.z, j.alpha * acc.w};
-  if (j.beta != 0.0) {
-    const Q64 z = ldq64(j.Zin, oin);
-    v.x += j.beta * z.x; v.y += j.beta * z.y; v.z += j.beta * z.z; v.w += j.beta * z.w;
+  QFF v = j.neg ? qff_neg(acc) : acc;
+  if (j.add_in) v = qff_add(v, ldff(j.Zin, oin));
+  if (j.minus_eye && i == c) ff_add1(v.h.x, v.l.x, -1.f, 0.f, v.h.x, v.l.x);
+  if (j.scale != 0.f) {   // a power of two: exact
+    v.h = make_float4(v.h.x * j.scale, v.h.y * j.scale, v.h.z * j.scale, v.h.w * j.scale);
+    v.l = make_float4(v.l.x * j.scale, v.l.y * j.scale, v.l.z * j.scale, v.l.w * j.scale);
   }
-  if (j.minus_eye && i == c) v.x -= 1.0;
-  stq64(j.Zout, (int64_t)i * j.Zout.ld + c, v);
+  stff(j.Zout, (int64_t)i * j.Zout.ld + c, v);
 }
 
 // Sum of a worker's 256 values in a fixed order (warp shuffles, then warps).
@@ -338,7 +388,7 @@ __device__ void rf_gemm_step(const RfArgs& a, const RfJob* jobs, int njobs, doub
   __shared__ int last_sh[kRfWorkers];
   __shared__ double red_sh[kRfWorkers][kRfTileThreads / 32];
   const int worker = threadIdx.x / kRfTileThreads, wtid = threadIdx.x % kRfTileThreads;
-  Q64* wsm = reinterpret_cast<Q64*>(smem) + worker * kRfWorkerQ64;
+  QFF* wsm = reinterpret_cast<QFF*>(smem) + worker * kRfWorkerQ;
   const int bar_id = 1 + worker;
   int items[3], ibase[3], tbase[3], pbase[3];
   int total = 0, tiles_total = 0, parts_total = 0;
@@ -362,9 +412,9 @@ __device__ void rf_gemm_step(const RfArgs& a, const RfJob* jobs, int njobs, doub
     const int tm = tile / j.tn, tn = tile % j.tn;
     const int kb = sp * j.kchunk;
     const int ke = kb + j.kchunk < j.K ? kb + j.kchunk : j.K;
-    Q64 acc = rf_tile_acc(j, tm, tn, kb, ke, wsm, wtid, bar_id);
+    QFF acc = rf_tile_acc(j, tm, tn, kb, ke, wsm, wtid, bar_id);
     if (j.splits > 1) {
-      Q64* slot = a.part + ((size_t)pbase[q] + (size_t)tile * j.splits + sp) * kRfTileThreads;
+      QFF* slot = a.part + ((size_t)pbase[q] + (size_t)tile * j.splits + sp) * kRfTileThreads;
       slot[wtid] = acc;
       __threadfence();
       worker_bar(bar_id);
@@ -372,33 +422,33 @@ __device__ void rf_gemm_step(const RfArgs& a, const RfJob* jobs, int njobs, doub
       worker_bar(bar_id);
       if (!last_sh[worker]) continue;
       __threadfence();
-      const Q64* src = a.part + ((size_t)pbase[q] + (size_t)tile * j.splits) * kRfTileThreads + wtid;
-      acc = q64_zero();
+      const QFF* src = a.part + ((size_t)pbase[q] + (size_t)tile * j.splits) * kRfTileThreads + wtid;
+      acc = qff_zero();
       for (int s = 0; s < j.splits; ++s) {   // in k order; written by other SMs
-        const double* p = reinterpret_cast<const double*>(src + (size_t)s * kRfTileThreads);
-        acc.x += __ldcg(p); acc.y += __ldcg(p + 1); acc.z += __ldcg(p + 2); acc.w += __ldcg(p + 3);
+        const float4* p = reinterpret_cast<const float4*>(src + (size_t)s * kRfTileThreads);
+        acc = qff_add(acc, QFF{__ldcg(p), __ldcg(p + 1)});
       }
       if (wtid == 0) a.cnt[tbase[q] + tile] = 0u;   // ready for the next step
     }
     double nd = 0.0, nz = 0.0;
     rf_epilogue(j, tm, tn, wtid, acc, &nd, &nz);
     if (j.norm) {
-      nd = rf_worker_sum(nd, red_sh[worker], wtid, bar_id);
-      nz = rf_worker_sum(nz, red_sh[worker], wtid, bar_id);
+      const double sd = rf_worker_sum(nd, red_sh[worker], wtid, bar_id);
+      const double sz = rf_worker_sum(nz, red_sh[worker], wtid, bar_id);
       if (wtid == 0) {
-        a.normpart[2 * tile] = nd;
-        a.normpart[2 * tile + 1] = nz;
+        a.normpart[2 * tile] = sd;
+        a.normpart[2 * tile + 1] = sz;
         __threadfence();
         const unsigned done = atomicAdd(a.cnt + kRfMaxTiles, 1u);
         if (done == (unsigned)(j.tiles - 1)) {   // the last tile folds, in tile order
           __threadfence();
-          double sd = 0.0, sz = 0.0;
+          double fd = 0.0, fz = 0.0;
           for (int u = 0; u < j.tiles; ++u) {
-            sd += __ldcg(a.normpart + 2 * u);
-            sz += __ldcg(a.normpart + 2 * u + 1);
+            fd += __ldcg(a.normpart + 2 * u);
+            fz += __ldcg(a.normpart + 2 * u + 1);
           }
-          norm_out[0] = sd;
-          norm_out[1] = sz;
+          norm_out[0] = fd;
+          norm_out[1] = fz;
           a.cnt[kRfMaxTiles] = 0u;
         }
       }
@@ -409,46 +459,95 @@ __device__ void rf_gemm_step(const RfArgs& a, const RfJob* jobs, int njobs, doub
 // ---------------------------------------------------------------------------
 // Solves.
 
-// One warp: row `row` of Z = Y R^-1 in FP64 with the packed FP32 factor R
-// (R_ll taken as 1 / invd[l]); k <= 32 U.
+// (S, C) += sg (ah + al) b for an exact FP32 b (a factor entry)
+template <int SG>
+__device__ __forceinline__ void ff_mac1(float& S, float& C, float ah, float al, float b) {
+  const float a = SG > 0 ? ah : -ah, a2 = SG > 0 ? al : -al;
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  float sn, err;
+  two_sum(S, p, sn, err);
+  S = sn;
+  C = __fadd_rn(C, __fadd_rn(err, e));
+  C = __fmaf_rn(a2, b, C);
+}
+
+// t -= z r in float-float, r an FP32 quaternion (Hamilton product z r)
+__device__ __forceinline__ void ff_qmsub1(float4& th, float4& tl, const float4 zh, const float4 zl,
+                                          const float4 r) {
+  ff_mac1<-1>(th.x, tl.x, zh.x, zl.x, r.x); ff_mac1<+1>(th.x, tl.x, zh.y, zl.y, r.y);
+  ff_mac1<+1>(th.x, tl.x, zh.z, zl.z, r.z); ff_mac1<+1>(th.x, tl.x, zh.w, zl.w, r.w);
+  ff_mac1<-1>(th.y, tl.y, zh.x, zl.x, r.y); ff_mac1<-1>(th.y, tl.y, zh.y, zl.y, r.x);
+  ff_mac1<-1>(th.y, tl.y, zh.z, zl.z, r.w); ff_mac1<+1>(th.y, tl.y, zh.w, zl.w, r.z);
+  ff_mac1<-1>(th.z, tl.z, zh.x, zl.x, r.z); ff_mac1<+1>(th.z, tl.z, zh.y, zl.y, r.w);
+  ff_mac1<-1>(th.z, tl.z, zh.z, zl.z, r.x); ff_mac1<-1>(th.z, tl.z, zh.w, zl.w, r.y);
+  ff_mac1<-1>(th.w, tl.w, zh.x, zl.x, r.w); ff_mac1<-1>(th.w, tl.w, zh.y, zl.y, r.z);
+  ff_mac1<+1>(th.w, tl.w, zh.z, zl.z, r.y); ff_mac1<-1>(th.w, tl.w, zh.w, zl.w, r.x);
+}
+
+// z = t s in float-float, s an exact FP32 scalar
+__device__ __forceinline__ void ff_scale1(float& zh, float& zl, float th, float tl, float sc) {
+  zh = __fmul_rn(th, sc);
+  zl = __fmaf_rn(tl, sc, __fmaf_rn(th, sc, -zh));
+}
+
+__device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// One warp: row `row` of Z = Y R^-1 in float-float with the packed FP32
+// factor R (R_ll taken as 1 / invd[l], so that every solve with this factor
+// applies the same matrix); k <= 32 U.  Each column l: z_l = t_l / R_ll from
+// its owner lane, then t_c -= z_l R_lc for the later columns of every lane.
 template <int U>
 __device__ void rf_trsm_row(const QPtr& Y, const QPtr& Z, int row, int k, const float* rpk) {
   const float4* Rs = reinterpret_cast<const float4*>(rpk);
   const float* invd = rpk + 4 * (k * (k + 1) / 2);
   const int lane = threadIdx.x & 31;
-  Q64 t[U];
+  float4 th[U], tl[U];
   const int64_t yo = (int64_t)row * Y.ld;
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int c = lane + 32 * u;
-    t[u] = c < k ? ldq64(Y, yo + c) : q64_zero();
+    const QFF v = c < k ? ldff(Y, yo + c) : qff_zero();
+    th[u] = v.h;
+    tl[u] = v.l;
   }
 #pragma unroll
   for (int uu = 0; uu < U; ++uu) {
     const int lend = k - 32 * uu < 32 ? k - 32 * uu : 32;
     for (int ll = 0; ll < lend; ++ll) {
       const int l = 32 * uu + ll;
-      const double s = (double)invd[l];
-      const Q64 z{__shfl_sync(0xffffffffu, t[uu].x, ll) * s, __shfl_sync(0xffffffffu, t[uu].y, ll) * s,
-                  __shfl_sync(0xffffffffu, t[uu].z, ll) * s, __shfl_sync(0xffffffffu, t[uu].w, ll) * s};
+      const float sc = invd[l];
+      float4 zh, zl;
+      ff_scale1(zh.x, zl.x, shfl_f(th[uu].x, ll), shfl_f(tl[uu].x, ll), sc);
+      ff_scale1(zh.y, zl.y, shfl_f(th[uu].y, ll), shfl_f(tl[uu].y, ll), sc);
+      ff_scale1(zh.z, zl.z, shfl_f(th[uu].z, ll), shfl_f(tl[uu].z, ll), sc);
+      ff_scale1(zh.w, zl.w, shfl_f(th[uu].w, ll), shfl_f(tl[uu].w, ll), sc);
       const float4* Rrow = Rs + (packed_row(l, k) - l);   // R_l,c at Rrow + c, c >= l
 #pragma unroll
       for (int u = uu; u < U; ++u) {
         const int c = lane + 32 * u;
-        if (c > l && c < k) q64_fms_f(t[u], z, Rrow[c]);
+        if (c > l && c < k) ff_qmsub1(th[u], tl[u], zh, zl, Rrow[c]);
       }
-      if (lane == ll) t[uu] = z;
+      if (lane == ll) { th[uu] = zh; tl[uu] = zl; }
     }
   }
   const int64_t zo = (int64_t)row * Z.ld;
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int c = lane + 32 * u;
-    if (c < k) stq64(Z, zo + c, t[u]);
+    if (c < k) {
+      QFF v;
+      ff_norm(th[u].x, tl[u].x, v.h.x, v.l.x);
+      ff_norm(th[u].y, tl[u].y, v.h.y, v.l.y);
+      ff_norm(th[u].z, tl[u].z, v.h.z, v.l.z);
+      ff_norm(th[u].w, tl[u].w, v.h.w, v.l.w);
+      stff(Z, zo + c, v);
+    }
   }
 }
 
-__device__ __noinline__ void rf_trsm_row_any(const QPtr& Y, const QPtr& Z, int row, int k, const float* rpk) {
+__device__ __noinline__ void rf_trsm_row_any(const QPtr& Y, const QPtr& Z, int row, int k,
+                                             const float* rpk) {
   if (k <= 32) rf_trsm_row<1>(Y, Z, row, k, rpk);
   else if (k <= 64) rf_trsm_row<2>(Y, Z, row, k, rpk);
   else if (k <= 96) rf_trsm_row<3>(Y, Z, row, k, rpk);
@@ -505,7 +604,6 @@ __device__ __forceinline__ RfJob job(const QPtr& X, int xh, const QPtr& Y, int y
   RfJob j{};
   j.X = X; j.Y = Y; j.Zin = Z; j.Zout = Z;
   j.M = M; j.N = N; j.K = K; j.xh = xh; j.yh = yh;
-  j.alpha = 1.0; j.beta = 0.0;
   return j;
 }
 
@@ -605,18 +703,53 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
   const int vb = blockIdx.x, vg = gridDim.x;
   const int r = a.r, c = a.c, k = a.k;
   unsigned target = 0;
-  // random start block P0 (entries uniform in [-1/2, 1/2), Philox counters)
-  for (int64_t e = (int64_t)vb * blockDim.x + threadIdx.x; e < (int64_t)c * k;
+  // The pairs keep FP32's exponent range and Z = W^H W P scales as |W|^2, so
+  // W is scaled by an exact power of two 2^-e to max |W_ij| in [1, 2); U is
+  // scaled back by 2^-e in its store ((2^-e W)^+ = 2^e W^+).
+  const int64_t nW = (int64_t)r * c, nP = (int64_t)c * k;
+  {
+    float mx = 0.f;
+    for (int64_t e = (int64_t)vb * blockDim.x + threadIdx.x; e < nW; e += (int64_t)vg * blockDim.x) {
+      const QFF v = ldff(a.W, (e / c) * a.W.ld + e % c);
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.h.x), fabsf(v.h.y)), fmaxf(fabsf(v.h.z), fabsf(v.h.w))));
+      if (!isfinite(v.h.x + v.h.y + v.h.z + v.h.w)) mx = INFINITY;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(a.wmax, __float_as_uint(mx));
+  }
+  if (!rf_sync(a, target)) return;
+  const float wm = __uint_as_float(__ldcg(a.wmax));
+  if (!isfinite(wm)) {
+    if (vb == 0 && threadIdx.x == 0) set_status(a.status, QMCUR_ERR_NONFINITE);
+    return;   // every CTA alike
+  }
+  const int wexp = wm > 0.f ? ilogbf(wm) : 0;
+  const float wsc = ldexpf(1.f, -wexp);
+  // W split into pairs once; random start block P0 (FP32 entries uniform in
+  // [-1/2, 1/2), Philox counters)
+  for (int64_t e = (int64_t)vb * blockDim.x + threadIdx.x; e < nW + nP;
        e += (int64_t)vg * blockDim.x) {
-    const uint4 x = rf_philox(make_uint4((unsigned)e, (unsigned)(e >> 32), 0x52u, 0x46u),
-                              make_uint2((unsigned)a.seed, (unsigned)(a.seed >> 32)));
-    const int64_t off = (e / k) * a.P[0].ld + e % k;
-    stq64(a.P[0], off, Q64{(double)x.x * 0x1.0p-32 - 0.5, (double)x.y * 0x1.0p-32 - 0.5,
-                           (double)x.z * 0x1.0p-32 - 0.5, (double)x.w * 0x1.0p-32 - 0.5});
+    if (e < nW) {
+      const int64_t i = e / c, j = e % c;
+      QFF v = ldff(a.W, i * a.W.ld + j);
+      v.h = make_float4(v.h.x * wsc, v.h.y * wsc, v.h.z * wsc, v.h.w * wsc);
+      v.l = make_float4(v.l.x * wsc, v.l.y * wsc, v.l.z * wsc, v.l.w * wsc);
+      stff(a.Wf, i * a.Wf.ld + j, v);
+    } else {
+      const int64_t f = e - nW;
+      const uint4 x = rf_philox(make_uint4((unsigned)f, (unsigned)(f >> 32), 0x52u, 0x46u),
+                                make_uint2((unsigned)a.seed, (unsigned)(a.seed >> 32)));
+      const float s = 0x1.0p-24f;
+      QFF v = qff_zero();
+      v.h = make_float4((float)(x.x >> 8) * s - 0.5f, (float)(x.y >> 8) * s - 0.5f,
+                        (float)(x.z >> 8) * s - 0.5f, (float)(x.w >> 8) * s - 0.5f);
+      stff(a.P[0], (f / k) * a.P[0].ld + f % k, v);
+    }
   }
   if (!rf_sync(a, target)) return;
   RfJob jb[3];
-  jb[0] = job(a.W, 0, a.P[0], 0, a.Y, r, k, c);   // Y = W P0
+  jb[0] = job(a.Wf, 0, a.P[0], 0, a.Y, r, k, c);   // Y = W P0
   plan_jobs(jb, 1, a.workers);
   rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
   if (!rf_sync(a, target)) return;
@@ -626,7 +759,7 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
   for (; s <= a.max_iter; ++s) {
     const QPtr& P = a.P[cur];
     const QPtr& Pn = a.P[cur ^ 1];
-    jb[0] = job(a.W, 1, a.Y, 0, a.Z, c, k, r);   // Z = W^H Y
+    jb[0] = job(a.Wf, 1, a.Y, 0, a.Z, c, k, r);   // Z = W^H Y
     plan_jobs(jb, 1, a.workers);
     rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
     if (!rf_sync(a, target)) return;
@@ -640,16 +773,14 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
     rf_solve_step(a, a.M, a.Z, a.Zp, c, nullptr, nullptr, 0, a.kap2 + s, vb, vg, smr);
     jb[0] = job(a.E, 0, a.M, 0, a.Mp, k, k, k);
     jb[0].Zin = a.M;
-    jb[0].alpha = -1.0;
-    jb[0].beta = 1.0;
-    jb[0].fp64 = 1;
+    jb[0].neg = 1;
+    jb[0].add_in = 1;
     plan_jobs(jb, 1, a.workers);
     rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
     if (!rf_sync(a, target)) return;
     jb[0] = job(a.Zp, 1, a.Zp, 0, a.Gp, k, k, c);   // G' = Z'^H Z'
     jb[1] = job(P, 0, a.Mp, 0, a.Z, c, k, k);       // ||Z - P M'||, ||Z||
     jb[1].norm = 1;
-    jb[1].fp64 = 1;   // its cancellation sets the floor of rho
     plan_jobs(jb, 2, a.workers);
     rf_gemm_step(a, jb, 2, a.norms + 2 * s, vb, vg, smr);
     if (!rf_sync(a, target)) return;
@@ -660,7 +791,7 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
     converged = stop_sh != 0;
     rf_solve_step(a, a.Gp, a.Zp, Pn, c, nullptr, nullptr, 0, nullptr, vb, vg, smr);   // P <- Z' R'^-1
     if (!rf_sync(a, target)) return;
-    jb[0] = job(a.W, 0, Pn, 0, a.Y, r, k, c);    // Y = W P
+    jb[0] = job(a.Wf, 0, Pn, 0, a.Y, r, k, c);    // Y = W P
     plan_jobs(jb, 1, a.workers);
     rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
     if (!rf_sync(a, target)) return;
@@ -688,12 +819,13 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
   if (!rf_sync(a, target)) return;
   jb[0] = job(a.T2, 0, a.E2, 0, a.V, c, k, k);   // V = T2 - T2 E2
   jb[0].Zin = a.T2;
-  jb[0].alpha = -1.0;
-  jb[0].beta = 1.0;
+  jb[0].neg = 1;
+  jb[0].add_in = 1;
   plan_jobs(jb, 1, a.workers);
   rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
   if (!rf_sync(a, target)) return;
-  jb[0] = job(a.V, 0, a.Q2, 1, a.U, c, r, k);    // U = V Q2^H
+  jb[0] = job(a.V, 0, a.Q2, 1, a.U, c, r, k);    // U = V Q2^H, back to W's scale
+  jb[0].scale = wsc;
   plan_jobs(jb, 1, a.workers);
   rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
   if (vb == 0 && threadIdx.x == 0) {
@@ -703,13 +835,14 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
   }
 }
 
-QPtr carve64(Carve& cv, int64_t rows, int64_t cols) {
+// A rows x cols matrix of pairs: four planes of float2, row stride ld.
+QPtr carve_ff(Carve& cv, int64_t rows, int64_t cols) {
   QPtr q;
   const int64_t ld = (cols + 1) / 2 * 2;
-  double* base = cv.take<double>((size_t)(4 * rows * ld));
+  float2* base = cv.take<float2>((size_t)(4 * rows * ld));
   for (int t = 0; t < 4; ++t) q.p[t] = base ? base + (size_t)t * rows * ld : nullptr;
   q.ld = ld;
-  q.dtype = QMCUR_F64;
+  q.dtype = kDtypeFF;
   return q;
 }
 
@@ -722,30 +855,32 @@ struct RfWs {
 RfWs carve_refine(Carve& cv, int64_t r, int64_t c, int64_t k) {
   RfWs w{};
   RfArgs& a = w.a;
-  a.P[0] = carve64(cv, c, k);
-  a.P[1] = carve64(cv, c, k);
-  a.Y = carve64(cv, r, k);
-  a.Z = carve64(cv, c, k);
-  a.Zp = carve64(cv, c, k);
-  a.M = carve64(cv, k, k);
-  a.E = carve64(cv, k, k);
-  a.Mp = carve64(cv, k, k);
-  a.Gp = carve64(cv, k, k);
-  a.G1 = carve64(cv, k, k);
-  a.G2 = carve64(cv, k, k);
-  a.E2 = carve64(cv, k, k);
-  a.Q1 = carve64(cv, r, k);
-  a.Q2 = carve64(cv, r, k);
-  a.T1 = carve64(cv, c, k);
-  a.T2 = carve64(cv, c, k);
-  a.V = carve64(cv, c, k);
-  a.part = cv.take<Q64>((size_t)kRfMaxParts * kRfTileThreads);
+  a.Wf = carve_ff(cv, r, c);
+  a.P[0] = carve_ff(cv, c, k);
+  a.P[1] = carve_ff(cv, c, k);
+  a.Y = carve_ff(cv, r, k);
+  a.Z = carve_ff(cv, c, k);
+  a.Zp = carve_ff(cv, c, k);
+  a.M = carve_ff(cv, k, k);
+  a.E = carve_ff(cv, k, k);
+  a.Mp = carve_ff(cv, k, k);
+  a.Gp = carve_ff(cv, k, k);
+  a.G1 = carve_ff(cv, k, k);
+  a.G2 = carve_ff(cv, k, k);
+  a.E2 = carve_ff(cv, k, k);
+  a.Q1 = carve_ff(cv, r, k);
+  a.Q2 = carve_ff(cv, r, k);
+  a.T1 = carve_ff(cv, c, k);
+  a.T2 = carve_ff(cv, c, k);
+  a.V = carve_ff(cv, c, k);
+  a.part = cv.take<QFF>((size_t)kRfMaxParts * kRfTileThreads);
   a.normpart = cv.take<double>((size_t)2 * kRfMaxTiles);
   a.norms = cv.take<double>((size_t)2 * (kRfMaxIter + 1));
   a.kap2 = cv.take<double>((size_t)(kRfMaxIter + 1));
   w.zero_base = cv.take<unsigned>((size_t)(kRfMaxTiles + 8));
   w.zero_bytes = (size_t)(kRfMaxTiles + 8) * sizeof(unsigned);
   a.cnt = w.zero_base;
+  a.wmax = w.zero_base + kRfMaxTiles + 2;
   a.bar = w.zero_base + kRfMaxTiles + 4;
   return w;
 }

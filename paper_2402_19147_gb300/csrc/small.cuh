@@ -8,6 +8,11 @@
 
 namespace qmcur {
 
+// Element type of workspace planes that hold float-float pairs: each plane
+// entry is a float2 (h, l) standing for h + l (internal to the library,
+// beside QMCUR_F32 and QMCUR_F64).
+constexpr int32_t kDtypeFF = 2;
+
 // Four plane pointers with a common row stride (elements) and element type.
 struct QPtr {
   void* p[4];

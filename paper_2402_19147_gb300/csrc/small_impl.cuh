@@ -391,8 +391,9 @@ __device__ __forceinline__ int sm_chol_s(const QPtr& G, int k, float* rpk, int32
       float mx = 0.f;
       for (int l = tid; l < k; l += 32) {
         const int64_t off = (int64_t)l * G.ld + l;
-        mx = fmaxf(mx, G.dtype == QMCUR_F64 ? (float)reinterpret_cast<const double*>(G.p[0])[off]
-                                            : reinterpret_cast<const float*>(G.p[0])[off]);
+        mx = fmaxf(mx, G.dtype == kDtypeFF ? reinterpret_cast<const float2*>(G.p[0])[off].x
+                       : G.dtype == QMCUR_F64 ? (float)reinterpret_cast<const double*>(G.p[0])[off]
+                                              : reinterpret_cast<const float*>(G.p[0])[off]);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -419,7 +420,12 @@ __device__ __forceinline__ int sm_chol_s(const QPtr& G, int k, float* rpk, int32
       const int c = j + (e - packed_row(j, k));
       jc[s >> 1] |= (((unsigned)j << 8) | (unsigned)c) << (16 * (s & 1));
       const int64_t off = (int64_t)j * G.ld + c;
-      if (G.dtype == QMCUR_F64)   // an FP64 Gram matrix, factored in FP32
+      if (G.dtype == kDtypeFF)    // a float-float Gram matrix: its leading parts
+        v[s] = make_float4(reinterpret_cast<const float2*>(G.p[0])[off].x,
+                           reinterpret_cast<const float2*>(G.p[1])[off].x,
+                           reinterpret_cast<const float2*>(G.p[2])[off].x,
+                           reinterpret_cast<const float2*>(G.p[3])[off].x);
+      else if (G.dtype == QMCUR_F64)   // an FP64 Gram matrix, factored in FP32
         v[s] = make_float4((float)reinterpret_cast<const double*>(G.p[0])[off],
                            (float)reinterpret_cast<const double*>(G.p[1])[off],
                            (float)reinterpret_cast<const double*>(G.p[2])[off],
@@ -545,8 +551,8 @@ __device__ __forceinline__ int sm_chol_from(int need, const QPtr& G, int k, floa
 
 // One CTA of kCholThreads threads: the packed factor R (FP32) with G = R^H R,
 // for 1 <= k <= kSmallCholMax (rpk 16-byte aligned, rpk_floats(k) floats).
-// Only the upper triangle of G is read; G may be FP32 or FP64 (rounded to
-// FP32 as it is read).  diag_shift_rel > 0 factors G + diag_shift_rel *
+// Only the upper triangle of G is read; G may be FP32, FP64 or float-float
+// pairs (rounded to FP32 as it is read).  diag_shift_rel > 0 factors G + diag_shift_rel *
 // max_l G_ll I instead.  A non-positive or non-finite pivot
 // sets ILL_CONDITIONED and continues with a tiny pivot.  With sj, rpk must be
 // in shared memory.  Returns n, the number of row warps: the rows
