@@ -390,9 +390,10 @@ def fp64_check(Q, A, D, w, prec, sampler, stream, steps=10, warmup=3, rows=256):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the current code, per kernel (profiles/): the tensor-core
-# Z = C T with the fused residual on the 2048 x 2048 workload, mixed split.
-NCU_TRAFFIC = {"gemm_z": 81.89e6 + 2.36e6}
+# ncu capture of the current code, per kernel (profiles/), on the 2048 x 2048
+# workload: the tensor-core Z = C T with the fused residual (mixed split) and
+# the refined pseudo-inverse of its 200 x 200 intersection.
+NCU_TRAFFIC = {"gemm_z": 81.89e6 + 2.36e6, "pinv_refine": 1.97e6 + 69.90e6}
 
 
 def peaks():
@@ -403,11 +404,21 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# FP32 instructions of one float-float quaternion multiply-add in the refined
+# core's products (csrc/pinv_refine.cu, ff_comp4 x 4 components: 4 products,
+# 4 product errors, 4 TwoSums of 6, 11 adds and 8 cross-term FMAs each)
+FF_OPS_PER_QMAC = 188
+
+
 def alu_peak_tflops(kind):
     # 152 SMs at the 2070 MHz maximum clock: FP32 128 FMA lanes per SM;
-    # FP64 at the nominal 1.25 TFLOP/s of the part (no measured FP64 peak).
+    # FP64 at the nominal 1.25 TFLOP/s of the part (no measured FP64 peak);
+    # float-float: the FP32 instruction rate over FF_OPS_PER_QMAC instructions
+    # per 32 algorithmic flops of a quaternion multiply-add.
     if kind == "fp64":
         return 1.25
+    if kind == "ff":
+        return 152 * 128 * 2.070e9 * 32 / FF_OPS_PER_QMAC / 1e12
     return 152 * 128 * 2 * 2.070e9 / 1e12
 
 
@@ -648,7 +659,12 @@ def run_ours(args):
     per_launch_s = stage_ms[dom] / 1e3
     if unit == "GB/s":
         achieved, peak, src = amount / per_launch_s / 1e9, pk["hbm_gbs"], pk_kind + " HBM copy"
-    elif dom == "pinv" and args.pinv in ("refined", "jacobi"):
+    elif dom == "pinv" and args.pinv == "refined":
+        achieved, peak = amount / per_launch_s / 1e12, alu_peak_tflops("ff")
+        src = ("float-float on the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz / %d instructions "
+               "per quaternion multiply-add (32 flops); %.2f of the nominal FP64 1.25 TFLOP/s"
+               % (FF_OPS_PER_QMAC, amount / per_launch_s / 1e12 / 1.25))
+    elif dom == "pinv" and args.pinv == "jacobi":
         achieved, peak = amount / per_launch_s / 1e12, alu_peak_tflops("fp64")
         src = "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)"
     elif dom == "pinv":
@@ -664,7 +680,11 @@ def run_ours(args):
             "unit": unit, "frac": achieved / peak,
             "traffic": None if dom != "gemm" else None, "peak_source": src,
             "work": "%.4g %s per launch, counted from the step shapes" % (
-                amount, "bytes" if unit == "GB/s" else "FP64 flops" if dom == "pinv" else "flops")}
+                amount, "bytes" if unit == "GB/s" else "flops")}
+    if dom == "pinv" and args.pinv == "refined" and workload_name(args) == WORKLOAD:
+        roof["traffic"] = NCU_TRAFFIC["pinv_refine"]
+        roof["traffic_note"] = ("L2 write-backs of the split-k partials; the kernel reads "
+                                "W once (1.3 MB)")
 
     # the GEMM stage: tensor work of the split (products x quaternion flops)
     # against the measured BF16 burst (TF32 at the nominal half of it)
