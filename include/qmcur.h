@@ -283,7 +283,10 @@ qmcur_status qmcur_gather(const qmcur_qmat* A, const int32_t* J, const int32_t* 
  *   G_R = -2 U^H C^H E,  G_U = -2 C^H E R^H,
  *   G_W = -U^H G_U U^H + (I - W U) G_U^H U U^H + U^H U G_U^H (I - U W)
  * (the fixed-rank derivative of W^+ of Golub and Pereyra; exact where W has
- * the rank of U).  FP32 arithmetic.
+ * the rank of U).  FP32-level arithmetic: the six large products (T = U R,
+ * Z = C T, G_C, G_T = -2 C^H E, G_U = G_T R^H and U^H G_T) run on the tensor
+ * cores (tcgen05) in the six-product BF16 split of QMCUR_PREC_BF16X6, the
+ * small products of G_W in FP32 on the CUDA cores.
  *   A, dA m x n (dA F32 or F64, fully overwritten); C m x c and R r x n F32;
  *   U c x r and W r x c F32 or F64; mask NULL or m x n bytes (row stride n);
  *   J[c], I[r] the index sets used to form C, R, W (device int32).

@@ -1,4 +1,6 @@
-// Gradient of the masked CUR reconstruction loss (FP32).
+// Gradient of the masked CUR reconstruction loss (FP32-level accuracy: the six
+// large products on the tensor cores in the six-product BF16 split, the
+// small pseudo-inverse adjoint products in FP32 on the CUDA cores).
 //
 //   L(A) = || P_Omega(A - C U R) ||_F^2,  C = A(:,J), R = A(I,:), W = A(I,J), U = W^+.
 // With E = P_Omega(A - Z), Z = C T, T = U R and <X, Y> = Re tr(X^H Y):
@@ -15,6 +17,15 @@
 namespace qmcur {
 
 size_t residual_partials(int64_t m, int64_t n);
+size_t tc_gemm_ws_bytes(int64_t M, int64_t N, int64_t K, int32_t prec);
+qmcur_status tc_gemm(const QView& X, bool xh, const QView& Y, bool yh, int64_t M, int64_t N,
+                     int64_t K, float alpha, const QView& Z, int32_t prec, void* ws,
+                     size_t ws_bytes, int32_t* dev_status, cudaStream_t st);
+
+// The six large products (T = U R, Z = C T and the four GEMM adjoints) run on
+// the tensor cores in the six-product BF16 split, which carries FP32-level
+// accuracy (each operand as three BF16 pieces, the products of order <= 2).
+constexpr int32_t kBwdTcPrec = QMCUR_PREC_BF16X6;
 
 namespace {
 
@@ -91,7 +102,32 @@ struct BwdWs {
   QPtr U32, W32, T, E, GC, GT, GU, GR, X1, WU, UW, UUh, UhU, M2, M3, GW;
   double* partial;
   double* out3;
+  void* tc;          // operand pieces and K-split partials of the tensor-core products
+  size_t tc_bytes;
 };
+
+// Workspace of the largest of the six tensor-core products.
+size_t bwd_tc_bytes(int64_t m, int64_t n, int64_t c, int64_t r) {
+  const int32_t p = kBwdTcPrec;
+  size_t b = tc_gemm_ws_bytes(c, n, r, p);                     // T = U R
+  const size_t s[5] = {tc_gemm_ws_bytes(m, n, c, p),            // Z = C T
+                       tc_gemm_ws_bytes(m, c, n, p),            // G_C = E T^H
+                       tc_gemm_ws_bytes(c, n, m, p),            // G_T = C^H E
+                       tc_gemm_ws_bytes(c, r, n, p),            // G_U = G_T R^H
+                       tc_gemm_ws_bytes(r, n, c, p)};           // G_R = U^H G_T
+  for (size_t x : s) b = x > b ? x : b;
+  return b;
+}
+
+QView qv(const QPtr& q, int64_t rows, int64_t cols) {
+  QView v;
+  for (int t = 0; t < 4; ++t) v.p[t] = q.p[t];
+  v.rows = rows;
+  v.cols = cols;
+  v.ld = q.ld;
+  v.dtype = q.dtype;
+  return v;
+}
 
 BwdWs carve_bwd(Carve& cv, int64_t m, int64_t n, int64_t c, int64_t r) {
   BwdWs w;
@@ -113,6 +149,8 @@ BwdWs carve_bwd(Carve& cv, int64_t m, int64_t n, int64_t c, int64_t r) {
   w.GW = take_q(cv, r, c);
   w.partial = cv.take<double>(2 * residual_partials(m, n));
   w.out3 = cv.take<double>(4);
+  w.tc_bytes = bwd_tc_bytes(m, n, c, r);
+  w.tc = cv.take<char>(w.tc_bytes);
   return w;
 }
 
@@ -147,7 +185,7 @@ qmcur_status launch_backward(const qmcur_qmat* A, const uint8_t* mask, const int
   Carve cv(ws, ws_bytes);
   BwdWs w = carve_bwd(cv, m, n, c, r);
   if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
-  const int mi = (int)m, ni = (int)n, ci = (int)c, ri = (int)r;
+  const int ci = (int)c, ri = (int)r;
   QPtr Cq, Rq;
   for (int t = 0; t < 4; ++t) { Cq.p[t] = C->plane[t]; Rq.p[t] = R->plane[t]; }
   Cq.ld = C->ld; Rq.ld = R->ld;
@@ -156,9 +194,16 @@ qmcur_status launch_backward(const qmcur_qmat* A, const uint8_t* mask, const int
   qmcur_status e;
   k_to_qptr_f32<<<blocks_for(c * r), 256, 0, st>>>(view(U), w.U32);
   k_to_qptr_f32<<<blocks_for(r * c), 256, 0, st>>>(view(W), w.W32);
+  const QView vU = qv(w.U32, c, r), vR = qv(Rq, r, n), vC = qv(Cq, m, c), vT = qv(w.T, c, n),
+              vE = qv(w.E, m, n), vGT = qv(w.GT, c, n);
+  auto tc = [&](const QView& X, bool xh, const QView& Y, bool yh, int64_t M, int64_t N,
+                int64_t K, float alpha, const QPtr& Z) {
+    return tc_gemm(X, xh, Y, yh, M, N, K, alpha, qv(Z, M, N), kBwdTcPrec, w.tc, w.tc_bytes,
+                   dev_status, st);
+  };
   // forward pieces: T = U R, Z = C T (into E), loss, E = P_Omega(A - Z), dA = 2 s E
-  if ((e = small_qgemm(false, false, ci, ni, ri, 1.f, w.U32, Rq, 0.f, w.T, st)) != QMCUR_OK) return e;
-  if ((e = small_qgemm(false, false, mi, ni, ci, 1.f, Cq, w.T, 0.f, w.E, st)) != QMCUR_OK) return e;
+  if ((e = tc(vU, false, vR, false, c, n, r, 1.f, w.T)) != QMCUR_OK) return e;
+  if ((e = tc(vC, false, vT, false, m, n, c, 1.f, w.E)) != QMCUR_OK) return e;
   {
     qmcur_qmat Zq;
     for (int t = 0; t < 4; ++t) Zq.plane[t] = w.E.p[t];
@@ -171,11 +216,12 @@ qmcur_status launch_backward(const qmcur_qmat* A, const uint8_t* mask, const int
       cudaMemcpyAsync(loss_out, w.out3 + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
   }
   k_residual_matrix<<<blocks_for(m * n), 256, 0, st>>>(view(A), mask, w.E, view(dA), 2.f * s);
-  // adjoints of the two GEMMs
-  if ((e = small_qgemm(false, true, mi, ci, ni, -2.f * s, w.E, w.T, 0.f, w.GC, st)) != QMCUR_OK) return e;
-  if ((e = small_qgemm(true, false, ci, ni, mi, -2.f * s, Cq, w.E, 0.f, w.GT, st)) != QMCUR_OK) return e;
-  if ((e = small_qgemm(false, true, ci, ri, ni, 1.f, w.GT, Rq, 0.f, w.GU, st)) != QMCUR_OK) return e;
-  if ((e = small_qgemm(true, false, ri, ni, ci, 1.f, w.U32, w.GT, 0.f, w.GR, st)) != QMCUR_OK) return e;
+  // adjoints of the two GEMMs (the conjugate transposes of Sec. 2.2: X^H Y
+  // and X Y^H, never plain transposes, which do not reverse quaternion products)
+  if ((e = tc(vE, false, vT, true, m, c, n, -2.f * s, w.GC)) != QMCUR_OK) return e;
+  if ((e = tc(vC, true, vE, false, c, n, m, -2.f * s, w.GT)) != QMCUR_OK) return e;
+  if ((e = tc(vGT, false, vR, true, c, r, n, 1.f, w.GU)) != QMCUR_OK) return e;
+  if ((e = tc(vU, true, vGT, false, r, n, c, 1.f, w.GR)) != QMCUR_OK) return e;
   // G_W = -U^H G_U U^H + (I - W U) G_U^H U U^H + U^H U G_U^H (I - U W)
   if ((e = small_qgemm(true, false, ri, ri, ci, 1.f, w.U32, w.GU, 0.f, w.X1, st)) != QMCUR_OK) return e;
   if ((e = small_qgemm(false, true, ri, ci, ri, -1.f, w.X1, w.U32, 0.f, w.GW, st)) != QMCUR_OK) return e;

@@ -615,6 +615,8 @@ struct SplitJob {
   int64_t rows_out, K, kpad;
   int npieces, trans, f64, vec2;   // vec2: non-trans rows read as float2
   int tiles_k, first_tile;         // tiles along k; index of the job's first tile
+  float scale;                     // every value is multiplied by scale before the split,
+  int conj;                        // and planes 1..3 by -1 with conj (conjugate, Sec. 2.2)
 };
 struct SplitJobs {
   SplitJob j[kMaxSplitJobs];
@@ -698,7 +700,10 @@ __global__ void __launch_bounds__(256) k_split_ops(const __grid_constant__ Split
     const int64_t rowoff = i * J.kpad + k;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      const float2 x = *reinterpret_cast<const float2*>(&tile[t][il][2 * lane]);
+      float2 x = *reinterpret_cast<const float2*>(&tile[t][il][2 * lane]);
+      const float sg = (J.conj && t > 0) ? -J.scale : J.scale;
+      x.x *= sg;
+      x.y *= sg;
       float p0[3], p1[3];
       split_value<BF16, float>(x.x, J.npieces, p0);
       split_value<BF16, float>(x.y, J.npieces, p1);
@@ -970,26 +975,34 @@ TcWs carve_tc(Carve& cv, const TcPlan& p1, const TcPlan& p2, int64_t m, int64_t 
 
 // Adds the pieces of operand S (rows_out x K as stored, or K x rows_out when
 // trans) to a split launch.
-bool add_split(SplitJobs& js, int& tiles, const qmcur_qmat* S, bool trans, void* dst,
-               int64_t rows_out, int64_t K, int64_t kpad, int npieces) {
+bool add_split_view(SplitJobs& js, int& tiles, const QView& S, bool trans, void* dst,
+                    int64_t rows_out, int64_t K, int64_t kpad, int npieces, float scale = 1.f,
+                    bool conj = false) {
   if (js.count >= kMaxSplitJobs || kpad % 2 != 0) return false;
   SplitJob& j = js.j[js.count++];
-  j.S = view(S);
+  j.S = S;
   j.dst = dst;
   j.rows_out = rows_out;
   j.K = K;
   j.kpad = kpad;
   j.npieces = npieces;
   j.trans = trans ? 1 : 0;
-  j.f64 = S->dtype == QMCUR_F64 ? 1 : 0;
-  j.vec2 = S->ld % 2 == 0;
-  for (int t = 0; t < 4; ++t) j.vec2 = j.vec2 && reinterpret_cast<uintptr_t>(S->plane[t]) % 8 == 0;
+  j.f64 = S.dtype == QMCUR_F64 ? 1 : 0;
+  j.scale = scale;
+  j.conj = conj ? 1 : 0;
+  j.vec2 = S.ld % 2 == 0;
+  for (int t = 0; t < 4; ++t) j.vec2 = j.vec2 && reinterpret_cast<uintptr_t>(S.p[t]) % 8 == 0;
   j.tiles_k = (int)((kpad + kSplitK - 1) / kSplitK);
   j.first_tile = tiles;
   const int64_t t = (int64_t)j.tiles_k * ((rows_out + kSplitRows - 1) / kSplitRows);
   if (tiles + t > INT32_MAX) return false;
   tiles += (int)t;
   return true;
+}
+
+bool add_split(SplitJobs& js, int& tiles, const qmcur_qmat* S, bool trans, void* dst,
+               int64_t rows_out, int64_t K, int64_t kpad, int npieces) {
+  return add_split_view(js, tiles, view(S), trans, dst, rows_out, K, kpad, npieces);
 }
 
 template <bool BF16>
@@ -1172,6 +1185,102 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
   if (Z != nullptr && nsz > 1) {
     const dim3 zgrid((unsigned)((n + 255) / 256), (unsigned)m);
     k_z_reduce<<<zgrid, 256, 0, st>>>(w.Pz, nsz, p2.zsplit, m * ldpz, ldpz, m, n, view(Z));
+  }
+  return cuda_ok(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// One general product on the tensor cores: Z = alpha op(X) op(Y), op(X)
+// M x K, op(Y) K x N, op = identity or the conjugate transpose (X^H: X
+// stored K x M, xh), Z (M x N, F32) stored.  The kernel multiplies operand
+// pieces laid out K-major (A[i][k] = op(X)[i][k], B[j][k] = op(Y)[k][j]), so
+// each operand is split straight or transposed, conjugated for an ^H, and
+// alpha is folded into X's pieces.  K splits with partials summed by
+// k_z_reduce when the output has too few tiles to occupy the GPU.
+
+namespace {
+
+struct TcGemmWs {
+  void *A, *B;
+  float* Pz;
+};
+
+TcGemmWs carve_tc_gemm(Carve& cv, const TcPlan& pl, int64_t M, int64_t N, int64_t K) {
+  const int64_t es = pl.bf16 ? 2 : 4;
+  const int64_t kp = rup(K, pl.epr);
+  TcGemmWs w;
+  w.A = cv.take<char>((size_t)(pl.npieces * 4 * M * kp * es));
+  w.B = cv.take<char>((size_t)(pl.npieces * 4 * N * kp * es));
+  const int nsz = z_splits(M, N, pl, kp);
+  w.Pz = nsz > 1 ? cv.take<float>((size_t)(nsz * 4 * M * rup(N, 4))) : nullptr;
+  return w;
+}
+
+}  // namespace
+
+size_t tc_gemm_ws_bytes(int64_t M, int64_t N, int64_t K, int32_t prec) {
+  Carve cv(nullptr, 0);
+  carve_tc_gemm(cv, plan_for(prec), M, N, K);
+  return cv.off;
+}
+
+qmcur_status tc_gemm(const QView& X, bool xh, const QView& Y, bool yh, int64_t M, int64_t N,
+                     int64_t K, float alpha, const QView& Z, int32_t prec, void* ws,
+                     size_t ws_bytes, int32_t* dev_status, cudaStream_t st) {
+  if (prec != QMCUR_PREC_TF32X3 && prec != QMCUR_PREC_BF16X3 && prec != QMCUR_PREC_BF16X6)
+    return QMCUR_ERR_INVALID_ARG;
+  if (M < 1 || N < 1 || K < 1 || M > INT32_MAX / 2 || N > INT32_MAX / 2 || K > INT32_MAX / 2)
+    return QMCUR_ERR_UNSUPPORTED;
+  if (Z.dtype != QMCUR_F32 || Z.rows != M || Z.cols != N) return QMCUR_ERR_INVALID_ARG;
+  const TcPlan pl = plan_for(prec);
+  const int64_t kp = rup(K, pl.epr);
+  Carve cv(ws, ws_bytes);
+  TcGemmWs w = carve_tc_gemm(cv, pl, M, N, K);
+  if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
+  SplitJobs js{};
+  int tiles = 0;
+  // A[i][k] = op(X)[i][k]: X (M x K) as stored, or X^H from X (K x M) read transposed
+  // B[j][k] = op(Y)[k][j]: Y (K x N) read transposed, or Y^H from Y (N x K) as stored
+  if (!add_split_view(js, tiles, X, xh, w.A, M, K, kp, pl.npieces, alpha, xh) ||
+      !add_split_view(js, tiles, Y, !yh, w.B, N, K, kp, pl.npieces, 1.f, yh))
+    return QMCUR_ERR_UNSUPPORTED;
+  qmcur_status s = pl.bf16 ? launch_splits<true>(js, tiles, st) : launch_splits<false>(js, tiles, st);
+  if (s != QMCUR_OK) return s;
+  const int bn = z_bn(M, N);
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, w.A, pl.bf16, M, kp, pl.npieces, BM) ||
+      !make_map(&mB, w.B, pl.bf16, N, kp, pl.npieces, bn))
+    return QMCUR_ERR_CUDA;
+  TcParams p{};
+  p.M = (int)M;
+  p.N = (int)N;
+  p.K = (int)K;
+  p.kblocks = (int)(kp / pl.epr);
+  p.nterms = pl.nterms;
+  for (int i = 0; i < 6; ++i) { p.ta[i] = pl.ta[i]; p.tb[i] = pl.tb[i]; }
+  p.mode = MODE_STORE_Z;
+  p.status = dev_status;
+  const int nsz = z_splits(M, N, pl, kp);
+  const int64_t ldpz = rup(N, 4);
+  if (nsz > 1 && M > 65535) return QMCUR_ERR_UNSUPPORTED;   // k_z_reduce's grid
+  if (nsz > 1) {
+    p.nsplit = nsz;
+    for (int t = 0; t < 4; ++t) p.z[t] = w.Pz + (int64_t)t * M * ldpz;
+    p.ldz = ldpz;
+    p.zsplit = 4 * M * ldpz;
+    p.z_vec = 1;
+  } else {
+    p.nsplit = 1;
+    for (int t = 0; t < 4; ++t) p.z[t] = reinterpret_cast<float*>(Z.p[t]);
+    p.ldz = Z.ld;
+    p.z_vec = Z.ld % 4 == 0;
+    for (int t = 0; t < 4; ++t) p.z_vec = p.z_vec && reinterpret_cast<uintptr_t>(Z.p[t]) % 16 == 0;
+  }
+  s = pl.bf16 ? launch_z<true>(bn, mA, mB, p, st) : launch_z<false>(bn, mA, mB, p, st);
+  if (s != QMCUR_OK) return s;
+  if (nsz > 1) {
+    const dim3 zgrid((unsigned)((N + 255) / 256), (unsigned)M);
+    k_z_reduce<<<zgrid, 256, 0, st>>>(w.Pz, nsz, p.zsplit, M * ldpz, ldpz, M, N, Z);
   }
   return cuda_ok(cudaGetLastError());
 }
