@@ -758,6 +758,10 @@ def run_ours(args):
     if not args.no_extra and workload_name(args) == WORKLOAD:
         line["extra"] = {"color4096_smooth100": color_field_extra(args, Q, synth, dev),
                          "color1024x1536_rank60_masked": backward_extra(Q, synth, dev)}
+        bl = batch_measure(args, Q, synth, dev, 10, 3)
+        line["extra"]["batch512_uneven"] = {k: bl[k] for k in (
+            "value", "unit", "ms_per_step", "steps", "warmup", "config", "fp32_gemms",
+            "speedup_over_fp32", "residual_max_abs_diff_vs_fp32", "z_product")}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -885,53 +889,84 @@ def color_field_extra(args, Q, synth, dev, steps=3, warmup=1):
 
 def run_batch(args):
     """512 uneven problems decomposed per step by one replay of the batched
-    plan's CUDA graph (one launch per stage, FP32 GEMMs; the core per --pinv:
-    the FP32 subspace program, one CTA per problem, or the FP32 Jacobi)."""
+    plan's CUDA graph (one launch per stage; the core per --pinv: the FP32
+    subspace program, one CTA per problem, or the FP32 Jacobi).  Two plans of
+    the same batch are timed side by side: Z = C T with the fused residual as
+    the grouped FP32 CUDA-core GEMM, and as one grouped tcgen05 launch in the
+    split of --prec (BF16X3 for this product under bf16mixed); value is the
+    split plan's.  Their residuals are compared problem by problem."""
     import torch
     from paper_2402_19147_gb300 import qmcur as Q
     from paper_2402_19147_gb300 import synth
     torch.cuda.set_device(0)
+    line = batch_measure(args, Q, synth, torch.device("cuda", 0), args.steps, args.warmup)
+    print(json.dumps(line), flush=True)
+
+
+def batch_measure(args, Q, synth, dev, steps, warmup):
+    import torch
     probs = synth.batch_problems(count=512, seed=3)
-    As = [torch.from_numpy(p["X"]).cuda() for p in probs]
+    As = [torch.from_numpy(p["X"]).to(dev) for p in probs]
     stream = torch.cuda.current_stream()
-    # the batched path's cores run one CTA per problem in FP32: the subspace
-    # program (default) or the FP32 Jacobi (--pinv jacobi)
     pinv_method = Q.PINV_JACOBI_FP64 if args.pinv == "jacobi" else Q.PINV_SUBSPACE_FP32
-    B = Q.Batch(As, [p["c"] for p in probs], [p["r"] for p in probs],
-                [p["rank"] for p in probs], sampler=Q.SAMPLER_NORM, seed=0, stream=stream,
-                pinv_method=pinv_method)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    for _ in range(args.warmup):
-        B.run(stream)
-    torch.cuda.synchronize()
-    Q.check_status(B.status, "batch warm-up")
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
+    split = args.prec if args.prec != "fp32" else "bf16mixed"
+    plans = {}
+    for name, pc in (("fp32", Q.PREC_FP32), (split, Q.PREC_NAMES[split])):
+        plans[name] = Q.Batch(As, [p["c"] for p in probs], [p["r"] for p in probs],
+                              [p["rank"] for p in probs], sampler=Q.SAMPLER_NORM, seed=0,
+                              stream=stream, pinv_method=pinv_method, prec=pc)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    res = {}
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    for s, (e0, e1) in enumerate(evs):
-        flush.fill_(s & 0xff)
-        e0.record(stream)
-        B.run(stream)
-        e1.record(stream)
-    torch.cuda.synchronize()
+    for name, B in plans.items():
+        for _ in range(warmup):
+            B.run(stream)
+        torch.cuda.synchronize()
+        Q.check_status(B.status, "batch warm-up")
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for s_, (e0, e1) in enumerate(evs):
+            flush.fill_(s_ & 0xff)
+            e0.record(stream)
+            B.run(stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        Q.check_status(B.status, "batch steps")
+        res[name] = statistics.median([a.elapsed_time(b) for a, b in evs])
     clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    rel = {name: np.array([float(B.get(b, "out3")[0].item()) for b in range(len(probs))])
+           for name, B in plans.items()}
     fl = sum(32.0 * (p["c"] * p["r"] * p["n"] + p["m"] * p["c"] * p["n"]) for p in probs)
+    flz = sum(32.0 * p["m"] * p["c"] * p["n"] for p in probs)
     byts = sum(16.0 * p["m"] * p["n"] for p in probs)
+    ms, ms32 = res[split], res["fp32"]
+    pk, pk_kind = peaks()
+    nprod = SPLIT_PRODUCTS[split][1]
+    tiles = [int(x) for x in host_tiles(Q, plans[split])]
     line = {"metric": METRIC, "value": 512 / (ms / 1e3), "unit": "decompositions/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": split,
             "data": "synthetic",
-            "config": {"workload": "batch512_uneven", "problems": 512, "gemm_prec": "fp32",
+            "config": {"workload": "batch512_uneven", "problems": 512, "gemm_prec": split,
                        "pinv": ("fp32-jacobi-per-cta" if args.pinv == "jacobi"
                                 else "fp32-subspace-per-cta"), "graph": True,
-                       "gemm_tiles": [int(x) for x in host_tiles(Q, B)],
+                       "gemm_tiles": {"t_simt": tiles[0], "z_tcgen05_bn": tiles[1]},
                        "l2": "flushed between steps (256 MiB write)"},
+            "fp32_gemms": {"value": 512 / (ms32 / 1e3), "unit": "decompositions/s",
+                           "ms_per_step": ms32},
+            "speedup_over_fp32": ms32 / ms,
+            "residual_max_abs_diff_vs_fp32": float(np.max(np.abs(rel[split] - rel["fp32"]))),
             "gemm_qtflops_per_step": fl / (ms / 1e3) / 1e12,
             "input_gbs_per_step": byts / (ms / 1e3) / 1e9,
+            "z_product": {"tensor_flops": nprod * flz, "hbm_bytes_a": byts,
+                          "peak_tensor_tflops": pk["bf16_tflops"] *
+                                                (0.5 if split == "tf32x3" else 1.0),
+                          "peak_hbm_gbs": pk["hbm_gbs"], "peak_source": pk_kind},
             "clocks": clk}
-    print(json.dumps(line), flush=True)
+    for B in plans.values():
+        B.close()
+    return line
 
 
 def run_core_paper(args):

@@ -435,8 +435,13 @@ qmcur_status qmcur_complete_step(qmcur_qmat* X, const uint8_t* mask, int64_t c, 
  * truncated at opts->rcond and rank_cap[b] (limits above);
  * QMCUR_PINV_SUBSPACE_FP32 runs the FP32 subspace method of qmcur_pinv_core
  * with one CTA per problem (rank_cap required, k <= 100, no shared-memory
- * limit on the intersection; largest problems first).  opts->prec is not
- * used.  dev_status
+ * limit on the intersection; largest problems first).  opts->prec selects the
+ * arithmetic of Z = C T with the fused residual: QMCUR_PREC_FP32 (or FP64) a
+ * grouped FP32 CUDA-core GEMM; QMCUR_PREC_BF16X3, BF16X6, TF32X3 or
+ * BF16_MIXED (= BF16X3 for this product) one grouped tcgen05 launch over the
+ * split operands of all problems, stacked along rows (the plan allocates
+ * them), with its tile width (128 or 64 columns) chosen by timing both; in
+ * every case T = U R runs in FP32 on the CUDA cores.  dev_status
  * (device int32, may be NULL) receives the first error; per-problem errors
  * also land in info[2] of the problem.  The plan keeps the pointers it was
  * given: A[b] and dev_status must stay valid until qmcur_batch_destroy.

@@ -30,6 +30,7 @@
 
 #include "sample_impl.cuh"
 #include "small.cuh"
+#include "tc_group.cuh"
 
 namespace qmcur {
 
@@ -499,6 +500,17 @@ struct BatchPlan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   qmcur_opts opts{};
+  // Z = C T on the tensor cores (opts.prec a split precision): the stacked
+  // operand pieces, the split jobs, the group tables and the tile width
+  bool tc = false;
+  void* A_all = nullptr;
+  void* B_all = nullptr;
+  int64_t rows_a = 0, rows_b = 0, kpad = 0;
+  TcSplitJob* djobs = nullptr;
+  int njobs = 0, split_tiles = 0;
+  TcGroupProb* dgprobs = nullptr;
+  TcGroupTile* dgtiles = nullptr;
+  int ngtiles = 0, tc_bn = 128;
 };
 
 static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st) {
@@ -518,9 +530,87 @@ static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st) {
         p->dprobs, p->opts.rcond, p->opts.max_sweeps > 0 ? p->opts.max_sweeps : 30);
   }
   launch_batch_gemm(p->cfg1, p->dprobs, p->dtiles1, p->ntiles1, 0, nullptr, st);
-  launch_batch_gemm(p->cfg2, p->dprobs, p->dtiles2, p->ntiles2, 1, p->partial, st);
+  if (p->tc) {
+    qmcur_status s = tc_group_split(p->opts.prec, p->djobs, p->njobs, p->split_tiles, st);
+    if (s != QMCUR_OK) return s;
+    s = tc_group_residual(p->opts.prec, p->tc_bn, p->A_all, p->rows_a, p->B_all, p->rows_b,
+                          p->kpad, p->dgtiles, p->ngtiles, p->dgprobs, p->partial, p->status, st);
+    if (s != QMCUR_OK) return s;
+  } else {
+    launch_batch_gemm(p->cfg2, p->dprobs, p->dtiles2, p->ntiles2, 1, p->partial, st);
+  }
   k_batch_fold<<<p->count, 32, 0, st>>>(p->dprobs, p->partial);
   return cuda_ok(cudaGetLastError());
+}
+
+// The tile list of the grouped tensor-core Z = C T at tile width bn (128
+// rows of a problem's output by bn columns), with each problem's first tile
+// and tile count for the fold.
+static std::vector<TcGroupTile> group_tiles(const std::vector<BatchProblem>& ps, int bn,
+                                            std::vector<int>* base, std::vector<int>* count) {
+  std::vector<TcGroupTile> t;
+  for (size_t b = 0; b < ps.size(); ++b) {
+    base->push_back((int)t.size());
+    int cnt = 0;
+    for (int m0 = 0; m0 < ps[b].m; m0 += 128)
+      for (int n0 = 0; n0 < ps[b].n; n0 += bn) { t.push_back(TcGroupTile{(int)b, m0, n0}); ++cnt; }
+    count->push_back(cnt);
+  }
+  return t;
+}
+
+// Sets the grouped tiles of width bn (device list, partials, fold ranges).
+static qmcur_status set_group_tiles(BatchPlan* p, int bn, cudaStream_t st) {
+  std::vector<int> b2, c2;
+  std::vector<TcGroupTile> t = group_tiles(p->host, bn, &b2, &c2);
+  cudaFree(p->dgtiles);
+  cudaFree(p->partial);
+  p->dgtiles = nullptr;
+  p->partial = nullptr;
+  if (cudaMalloc(&p->dgtiles, t.size() * sizeof(TcGroupTile)) != cudaSuccess ||
+      cudaMalloc(&p->partial, 2 * t.size() * sizeof(double)) != cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  if (cudaMemcpyAsync(p->dgtiles, t.data(), t.size() * sizeof(TcGroupTile), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  for (int b = 0; b < p->count; ++b) { p->host[b].tile_base2 = b2[b]; p->host[b].tiles2 = c2[b]; }
+  p->ngtiles = (int)t.size();
+  p->tc_bn = bn;
+  if (cudaMemcpyAsync(p->dprobs, p->host.data(), p->count * sizeof(BatchProblem),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  // the host vector must outlive its copy
+  return cudaStreamSynchronize(st) == cudaSuccess ? QMCUR_OK : QMCUR_ERR_CUDA;
+}
+
+// Time the grouped Z = C T at the candidate tile widths on the real batch
+// (after a first pass has filled T); the faster stays.
+static qmcur_status autotune_group(BatchPlan* p, cudaStream_t st) {
+  float best = 1e30f;
+  int best_bn = 128;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cands[2] = {128, 64};
+  for (int bn : cands) {
+    qmcur_status s = set_group_tiles(p, bn, st);
+    if (s != QMCUR_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+    auto run = [&]() {
+      return tc_group_residual(p->opts.prec, bn, p->A_all, p->rows_a, p->B_all, p->rows_b, p->kpad,
+                               p->dgtiles, p->ngtiles, p->dgprobs, p->partial, p->status, st);
+    };
+    if ((s = run()) != QMCUR_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 3; ++rep) run();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_bn = bn; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return set_group_tiles(p, best_bn, st);
 }
 
 // Time the candidate tile shapes of one grouped GEMM on the real batch.
@@ -577,6 +667,11 @@ static void free_plan(BatchPlan* p) {
   cudaFree(p->order);
   cudaFree(p->pinv_arena);
   cudaFree(p->colpart);
+  cudaFree(p->A_all);
+  cudaFree(p->B_all);
+  cudaFree(p->djobs);
+  cudaFree(p->dgprobs);
+  cudaFree(p->dgtiles);
   delete p;
 }
 
@@ -609,10 +704,14 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     }
     if (A[b].rows > (1 << 20) || A[b].cols > 48 * 1024) return QMCUR_ERR_UNSUPPORTED;
   }
+  const int32_t pr = opts->prec;
+  const bool tc = pr == QMCUR_PREC_BF16X3 || pr == QMCUR_PREC_BF16X6 ||
+                  pr == QMCUR_PREC_BF16_MIXED || pr == QMCUR_PREC_TF32X3;
   BatchPlan* p = new BatchPlan();
   p->count = count;
   p->opts = *opts;
   p->status = dev_status;
+  p->tc = tc;
   // one arena: per problem col_p, row_p, J, I, C, R, W, U, T, out3, info
   std::vector<size_t> off;
   size_t total = 0;
@@ -727,6 +826,79 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     free_plan(p);
     return QMCUR_ERR_CUDA;
   }
+  if (tc) {
+    // stacked operand pieces of Z = C T: every problem's C (m x c) as rows of
+    // A_all and its T^T (n x c) as rows of B_all, K padded to the largest c
+    const int64_t epr = tc_group_epr(pr);
+    std::vector<int64_t> arow(count), brow(count);
+    int64_t cmax = 1;
+    for (int b = 0; b < count; ++b) {
+      arow[b] = p->rows_a;
+      brow[b] = p->rows_b;
+      p->rows_a += p->host[b].m;
+      p->rows_b += p->host[b].n;
+      cmax = std::max<int64_t>(cmax, p->host[b].c);
+    }
+    p->kpad = (cmax + epr - 1) / epr * epr;
+    if (p->rows_a > INT32_MAX / 2 || p->rows_b > INT32_MAX / 2) { free_plan(p); return QMCUR_ERR_UNSUPPORTED; }
+    const size_t ba = tc_group_piece_bytes(pr, p->rows_a, p->kpad);
+    const size_t bb = tc_group_piece_bytes(pr, p->rows_b, p->kpad);
+    std::vector<TcSplitJob> jobs;
+    std::vector<TcGroupProb> gp(count);
+    int tiles = 0;
+    auto add_job = [&](const QView& S, bool trans, void* dst, int64_t rows, int64_t K, int64_t row0,
+                       int64_t rows_total) {
+      TcSplitJob j{};
+      j.S = S;
+      j.dst = dst;
+      j.rows = rows;
+      j.K = K;
+      j.kp_job = (K + epr - 1) / epr * epr;
+      j.kpad = p->kpad;
+      j.row0 = row0;
+      j.plane_stride = rows_total * p->kpad;
+      j.trans = trans ? 1 : 0;
+      j.tiles_k = (int)((j.kp_job + 63) / 64);
+      j.first_tile = tiles;
+      tiles += j.tiles_k * (int)((rows + 31) / 32);
+      jobs.push_back(j);
+    };
+    if (cudaMalloc(&p->A_all, ba) != cudaSuccess || cudaMalloc(&p->B_all, bb) != cudaSuccess) {
+      free_plan(p);
+      return QMCUR_ERR_CUDA;
+    }
+    cudaMemsetAsync(p->A_all, 0, ba, stream);
+    cudaMemsetAsync(p->B_all, 0, bb, stream);
+    for (int b = 0; b < count; ++b) {
+      const BatchProblem& P = p->host[b];
+      add_job(P.C, false, p->A_all, P.m, P.c, arow[b], p->rows_a);   // A[i][k] = C[i][k]
+      add_job(P.T, true, p->B_all, P.n, P.c, brow[b], p->rows_b);    // B[j][k] = T[k][j]
+      TcGroupProb& g = gp[b];
+      bool av = P.A.ld % 4 == 0;
+      for (int t = 0; t < 4; ++t) {
+        g.a[t] = reinterpret_cast<const float*>(P.A.p[t]);
+        av = av && reinterpret_cast<uintptr_t>(P.A.p[t]) % 16 == 0;
+      }
+      g.lda = P.A.ld;
+      g.m = P.m;
+      g.n = P.n;
+      g.K = P.c;
+      g.kblocks = (int)(((P.c + epr - 1) / epr * epr) / epr);
+      g.arow = (int)arow[b];
+      g.brow = (int)brow[b];
+      g.a_vec = av ? 1 : 0;
+    }
+    p->njobs = (int)jobs.size();
+    p->split_tiles = tiles;
+    if (cudaMalloc(&p->djobs, jobs.size() * sizeof(TcSplitJob)) != cudaSuccess ||
+        cudaMalloc(&p->dgprobs, gp.size() * sizeof(TcGroupProb)) != cudaSuccess) {
+      free_plan(p);
+      return QMCUR_ERR_CUDA;
+    }
+    cudaMemcpyAsync(p->djobs, jobs.data(), jobs.size() * sizeof(TcSplitJob), cudaMemcpyHostToDevice, stream);
+    cudaMemcpyAsync(p->dgprobs, gp.data(), gp.size() * sizeof(TcGroupProb), cudaMemcpyHostToDevice, stream);
+    if (cudaStreamSynchronize(stream) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
+  }
   // first pass (un-captured): fills T and the operands so that the GEMM
   // candidates can be timed on real data
   {
@@ -743,20 +915,27 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     make_tiles(p->host, 1, 0, &b2, &c2);
     for (int b = 0; b < count; ++b) { p->host[b].tile_base2 = b2[b]; p->host[b].tiles2 = c2[b]; }
     cudaMemcpyAsync(p->dprobs, p->host.data(), count * sizeof(BatchProblem), cudaMemcpyHostToDevice, stream);
+    if (tc) {
+      const qmcur_status s = set_group_tiles(p, 128, stream);
+      if (s != QMCUR_OK) { free_plan(p); return s; }
+    }
     qmcur_status s = enqueue_batch(p, stream);
     if (s != QMCUR_OK) { free_plan(p); return s; }
   }
   // autotune the two grouped GEMMs, rebuild their tile lists
   p->cfg1 = autotune(p, 0, stream);
-  p->cfg2 = autotune(p, 1, stream);
+  if (!tc) p->cfg2 = autotune(p, 1, stream);
   {
-    cudaFree(p->dtiles1); cudaFree(p->dtiles2); cudaFree(p->partial);
+    cudaFree(p->dtiles1); cudaFree(p->dtiles2);
+    p->dtiles1 = p->dtiles2 = nullptr;
+    if (!tc) { cudaFree(p->partial); p->partial = nullptr; }
     std::vector<int> b2, c2;
     std::vector<GTile> t1 = make_tiles(p->host, 0, p->cfg1), t2 = make_tiles(p->host, 1, p->cfg2, &b2, &c2);
-    for (int b = 0; b < count; ++b) { p->host[b].tile_base2 = b2[b]; p->host[b].tiles2 = c2[b]; }
+    if (!tc)
+      for (int b = 0; b < count; ++b) { p->host[b].tile_base2 = b2[b]; p->host[b].tiles2 = c2[b]; }
     if (cudaMalloc(&p->dtiles1, t1.size() * sizeof(GTile)) != cudaSuccess ||
         cudaMalloc(&p->dtiles2, t2.size() * sizeof(GTile)) != cudaSuccess ||
-        cudaMalloc(&p->partial, 2 * t2.size() * sizeof(double)) != cudaSuccess) {
+        (!tc && cudaMalloc(&p->partial, 2 * t2.size() * sizeof(double)) != cudaSuccess)) {
       free_plan(p);
       return QMCUR_ERR_CUDA;
     }
@@ -765,6 +944,12 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     cudaMemcpyAsync(p->dprobs, p->host.data(), count * sizeof(BatchProblem), cudaMemcpyHostToDevice, stream);
     p->ntiles1 = (int)t1.size();
     p->ntiles2 = (int)t2.size();
+    if (cudaStreamSynchronize(stream) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
+  }
+  if (tc) {
+    // T of the first pass is current (the SIMT T = U R did not change)
+    const qmcur_status s = autotune_group(p, stream);
+    if (s != QMCUR_OK) { free_plan(p); return s; }
   }
   // capture the whole pipeline once, on a private stream (the caller's may be
   // the legacy default stream, which cannot be captured)
@@ -806,7 +991,8 @@ qmcur_status qmcur_batch_view(const void* plan, int32_t index, qmcur_batch_item*
   out->col_p = P.col_p; out->row_p = P.row_p; out->J = P.J; out->I = P.I;
   out->C = toq(P.C); out->R = toq(P.R); out->W = toq(P.W); out->U = toq(P.U);
   out->out3 = P.out3; out->info = P.info;
-  out->gemm_tiles[0] = kCfgs[p->cfg1].bm; out->gemm_tiles[1] = kCfgs[p->cfg2].bm;
+  out->gemm_tiles[0] = kCfgs[p->cfg1].bm;
+  out->gemm_tiles[1] = p->tc ? p->tc_bn : kCfgs[p->cfg2].bm;
   return QMCUR_OK;
 }
 

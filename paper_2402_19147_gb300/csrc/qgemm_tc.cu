@@ -43,6 +43,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "tc_group.cuh"
 
 namespace qmcur {
 
@@ -88,7 +89,10 @@ constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 // iterate X^t, and each unobserved entry (mask 0) is overwritten in place by
 // z, while the sums are sum over unobserved entries of |z - a|^2 and sum over
 // all entries of |a|^2 (the stopping test's ||X^{t+1} - X^t||^2 and ||X^t||^2).
-enum { MODE_STORE_Z = 0, MODE_RESIDUAL = 1, MODE_STORE_ZT = 2, MODE_COMPLETE = 3 };
+// MODE_GROUPED is MODE_RESIDUAL over the tiles of many problems (tc_group.cuh):
+// each tile's coordinates, inner dimension and A come from the group tables,
+// and its partials go to partial[2 tile], with no fold in the kernel.
+enum { MODE_STORE_Z = 0, MODE_RESIDUAL = 1, MODE_STORE_ZT = 2, MODE_COMPLETE = 3, MODE_GROUPED = 4 };
 
 struct TcParams {
   int M, N;
@@ -111,6 +115,10 @@ struct TcParams {
   double* out3;           // the last CTA folds the partials into out3
   unsigned* done;         // arrival count of that fold, zero at launch
   int32_t* status;
+  // MODE_GROUPED
+  const TcGroupTile* gtiles;
+  const TcGroupProb* gprobs;
+  int gcount;
 };
 
 // ------------------------------------------------------------- PTX helpers -
@@ -288,13 +296,14 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
   constexpr uint32_t kIdPos = make_idesc(BF16, false, BN), kIdNeg = make_idesc(BF16, true, BN);
   constexpr int kElemsPerRow = ROWB / (BF16 ? 2 : 4);
   constexpr int kStepElems = 32 / (BF16 ? 2 : 4);          // K of one MMA (32 bytes)
-  constexpr bool sums_mode = MODE == MODE_RESIDUAL || MODE == MODE_COMPLETE;
+  constexpr bool grouped = MODE == MODE_GROUPED;
+  constexpr bool sums_mode = MODE == MODE_RESIDUAL || MODE == MODE_COMPLETE || grouped;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int mtiles = (p.M + BM - 1) / BM, ntiles = (p.N + BN - 1) / BN;
   const int tiles = mtiles * ntiles;
   const int kiters = p.nterms * p.kblocks;
-  const int items = tiles * p.nsplit;
+  const int items = grouped ? p.gcount : tiles * p.nsplit;
   const int kper = (kiters + p.nsplit - 1) / p.nsplit;   // every split non-empty (host)
 
   if (threadIdx.x == 0) {
@@ -320,18 +329,33 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     uint32_t it = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      const int tile = item / p.nsplit, split = item % p.nsplit;
-      const int mt = tile % mtiles, nt = tile / mtiles;
-      const int k0 = split * kper, k1 = min(k0 + kper, kiters);
+      int arow, brow, kbl, k0, k1;
+      if constexpr (grouped) {
+        const TcGroupTile tl = p.gtiles[item];
+        const TcGroupProb& gp = p.gprobs[tl.prob];
+        arow = gp.arow + tl.m0;
+        brow = gp.brow + tl.n0;
+        kbl = gp.kblocks;
+        k0 = 0;
+        k1 = p.nterms * kbl;
+      } else {
+        const int tile = item / p.nsplit, split = item % p.nsplit;
+        const int mt = tile % mtiles, nt = tile / mtiles;
+        arow = mt * BM;
+        brow = nt * BN;
+        kbl = p.kblocks;
+        k0 = split * kper;
+        k1 = min(k0 + kper, kiters);
+      }
       for (int ki = k0; ki < k1; ++ki, ++it) {
-          const int term = ki / p.kblocks, kb = ki % p.kblocks;
+          const int term = ki / kbl, kb = ki % kbl;
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) { ok = false; break; }
           mbar_expect_tx(&full[s], STAGE);
           const uint32_t sa = saddr(smem + s * STAGE);
-          tma_load_3d(sa, &mapA, &full[s], kb * kElemsPerRow, mt * BM, p.ta[term] * 4);
-          tma_load_3d(sa + A_STAGE, &mapB, &full[s], kb * kElemsPerRow, nt * BN, p.tb[term] * 4);
+          tma_load_3d(sa, &mapA, &full[s], kb * kElemsPerRow, arow, p.ta[term] * 4);
+          tma_load_3d(sa + A_STAGE, &mapB, &full[s], kb * kElemsPerRow, brow, p.tb[term] * 4);
         }
     }
   } else if (warp == 1 && lane == 0) {
@@ -340,8 +364,20 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     int local = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x, ++local) {
-      const int split = item % p.nsplit;
-      const int k0 = split * kper, k1 = min(k0 + kper, kiters);
+      int kbl, kval, k0, k1;
+      if constexpr (grouped) {
+        const TcGroupProb& gp = p.gprobs[p.gtiles[item].prob];
+        kbl = gp.kblocks;
+        kval = gp.K;
+        k0 = 0;
+        k1 = p.nterms * kbl;
+      } else {
+        const int split = item % p.nsplit;
+        kbl = p.kblocks;
+        kval = p.K;
+        k0 = split * kper;
+        k1 = min(k0 + kper, kiters);
+      }
       const int a = local % NACC;
       const uint32_t aph = (local / NACC) & 1;
       if (!mbar_wait(&tempty[a], aph ^ 1u, abort_flag)) break;
@@ -358,8 +394,8 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
         // stage offsets stay below 2^18 bytes, so adding (offset >> 4) to the
         // 14-bit start-address field never carries out of it.
         const uint64_t ad0 = sdesc(sa), bd0 = sdesc(sb);
-        const int kb = ki % p.kblocks;
-        const int kleft = p.K - kb * kElemsPerRow;          // valid elements in this slice
+        const int kb = ki % kbl;
+        const int kleft = kval - kb * kElemsPerRow;         // valid elements in this slice
         const int ksteps = kleft >= kElemsPerRow ? ROWB / 32 : (kleft + kStepElems - 1) / kStepElems;
 #pragma unroll
         for (int ks = 0; ks < ROWB / 32; ++ks) {
@@ -388,13 +424,24 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     const int epi = warp - 2;
     const int half = epi / 4;                // the two warps of a sub-partition take alternate chunks
     int local = 0;
+    // the current tile's problem (the group tables, or p itself)
+    // (grouped only; otherwise the accessors below read p directly)
+    int Mv = 0, Nv = 0, avec = 0;
+    int64_t ldav = 0;
+    const float* ap[4] = {nullptr, nullptr, nullptr, nullptr};
+    auto EM = [&]() -> int { if constexpr (grouped) return Mv; else return p.M; };
+    auto EN = [&]() -> int { if constexpr (grouped) return Nv; else return p.N; };
+    auto EAV = [&]() -> int { if constexpr (grouped) return avec; else return p.a_vec; };
+    auto ELD = [&]() -> int64_t { if constexpr (grouped) return ldav; else return p.lda; };
+    auto EAP = [&](int pl) -> const float* { if constexpr (grouped) return ap[pl]; else return p.a[pl]; };
+    auto EMASK = [&]() -> const uint8_t* { if constexpr (grouped) return nullptr; else return p.mask; };
     // A values of all four planes of one 16-column chunk (row `row`)
     auto load_a = [&](float4 (&av)[4][4], int row, int c0) {
-      const bool in_row = row < p.M;
-      const bool full16 = p.a_vec && c0 + 16 <= p.N;
+      const bool in_row = row < EM();
+      const bool full16 = EAV() && c0 + 16 <= EN();
 #pragma unroll
       for (int pl = 0; pl < 4; ++pl) {
-        const float* ar = p.a[pl] + (int64_t)row * p.lda + c0;
+        const float* ar = EAP(pl) + (int64_t)row * ELD() + c0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (in_row && full16) {
@@ -402,19 +449,33 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
           } else {
             float e[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) e[u] = (in_row && c0 + 4 * q + u < p.N) ? ar[4 * q + u] : 0.f;
+            for (int u = 0; u < 4; ++u) e[u] = (in_row && c0 + 4 * q + u < EN()) ? ar[4 * q + u] : 0.f;
             av[pl][q] = make_float4(e[0], e[1], e[2], e[3]);
           }
         }
       }
     };
     for (int item = blockIdx.x; item < items; item += gridDim.x, ++local) {
-      const int tile = item / p.nsplit, split = item % p.nsplit;
+      const int tile = grouped ? item : item / p.nsplit, split = grouped ? 0 : item % p.nsplit;
       const int a = local % NACC;
       const uint32_t aph = (local / NACC) & 1;
-      const int mt = tile % mtiles, nt = tile / mtiles;
-      const int row = mt * BM + sp * 32 + lane;
-      const int n0 = nt * BN;
+      int row, n0;
+      if constexpr (grouped) {
+        const TcGroupTile tl = p.gtiles[item];
+        const TcGroupProb& gp = p.gprobs[tl.prob];
+        Mv = gp.m;
+        Nv = gp.n;
+        avec = gp.a_vec;
+        ldav = gp.lda;
+#pragma unroll
+        for (int pl = 0; pl < 4; ++pl) ap[pl] = gp.a[pl];
+        row = tl.m0 + sp * 32 + lane;
+        n0 = tl.n0;
+      } else {
+        const int mt = tile % mtiles, nt = tile / mtiles;
+        row = mt * BM + sp * 32 + lane;
+        n0 = nt * BN;
+      }
       // the residual's first A chunk is fetched while the MMAs still run
       float4 anext[4][4];
       if constexpr (sums_mode) load_a(anext, row, n0 + 16 * half);
@@ -433,17 +494,17 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
 #pragma unroll
             for (int q = 0; q < 4; ++q) av[pl][q] = anext[pl][q];
           if (ch + 2 < BN / 16) load_a(anext, row, c0 + 32);   // this warp's next chunk in flight
-          const bool in_row = row < p.M;
-          const bool full16 = p.a_vec && c0 + 16 <= p.N;
+          const bool in_row = row < EM();
+          const bool full16 = EAV() && c0 + 16 <= EN();
           float sd = 0.f, sa2 = 0.f;
           if constexpr (!cmpl) {
             unsigned keep = 0xffffu;   // columns of the chunk that count
-            if (!full16 || p.mask != nullptr) {
+            if (!full16 || EMASK() != nullptr) {
               keep = 0;
 #pragma unroll
               for (int j = 0; j < 16; ++j) {
-                const bool ok = in_row && c0 + j < p.N &&
-                                (p.mask == nullptr || p.mask[(int64_t)row * p.N + c0 + j] != 0);
+                const bool ok = in_row && c0 + j < EN() &&
+                                (EMASK() == nullptr || EMASK()[(int64_t)row * EN() + c0 + j] != 0);
                 keep |= (ok ? 1u : 0u) << j;
               }
             }
@@ -1026,7 +1087,8 @@ qmcur_status launch_gemm_mode(const CUtensorMap& ma, const CUtensorMap& mb, cons
   }
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return QMCUR_ERR_CUDA;
-  const int items = ((p.M + BM - 1) / BM) * ((p.N + BNT - 1) / BNT) * p.nsplit;
+  const int items = MODE == MODE_GROUPED ? p.gcount
+                                         : ((p.M + BM - 1) / BM) * ((p.N + BNT - 1) / BNT) * p.nsplit;
   const int cap = cta_cap(sms);
   const int grid = items < cap ? items : cap;
   k_qgemm_tc<BF16, BNT, REV, MODE><<<grid, kTcThreads, TcShape<BNT>::SMEM, st>>>(ma, mb, p);
@@ -1283,6 +1345,143 @@ qmcur_status tc_gemm(const QView& X, bool xh, const QView& Y, bool yh, int64_t M
     k_z_reduce<<<zgrid, 256, 0, st>>>(w.Pz, nsz, p.zsplit, M * ldpz, ldpz, M, N, Z);
   }
   return cuda_ok(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Grouped products of the batched path (tc_group.cuh).
+
+namespace {
+
+// Pieces of many operands from a device job table: CTA b takes tile
+// b - first_tile of the job whose tiles hold b (binary search over the
+// table's first tiles), 32 rows x 64 k through shared memory as in
+// k_split_ops, and writes the pieces into the job's rows of its stacked
+// buffer.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_split_table(const TcSplitJob* __restrict__ jobs, int njobs,
+                                                     int npieces) {
+  __shared__ __align__(16) float tile[4][kSplitRows][kSplitPitch];
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {   // the last job whose first tile is <= blockIdx.x
+    const int mid = (lo + hi + 1) / 2;
+    if (jobs[mid].first_tile <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const TcSplitJob& J = jobs[lo];
+  const int tl = (int)blockIdx.x - J.first_tile;
+  const int64_t i0 = (int64_t)(tl / J.tiles_k) * kSplitRows, k0 = (int64_t)(tl % J.tiles_k) * kSplitK;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const float* planes[4] = {reinterpret_cast<const float*>(J.S.p[0]), reinterpret_cast<const float*>(J.S.p[1]),
+                            reinterpret_cast<const float*>(J.S.p[2]), reinterpret_cast<const float*>(J.S.p[3])};
+  if (!J.trans) {
+    const int64_t k = k0 + 2 * lane;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + warp + 8 * u;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float2 x = make_float2(0.f, 0.f);
+        if (i < J.rows && k < J.K) {
+          const float* src = planes[t] + i * J.S.ld + k;
+          x.x = src[0];
+          if (k + 1 < J.K) x.y = src[1];
+        }
+        *reinterpret_cast<float2*>(&tile[t][warp + 8 * u][2 * lane]) = x;
+      }
+    }
+  } else {
+    const int64_t i = i0 + lane;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t k = k0 + warp + 8 * u;
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        tile[t][lane][warp + 8 * u] = (i < J.rows && k < J.K) ? planes[t][k * J.S.ld + i] : 0.f;
+    }
+  }
+  __syncthreads();
+  const int64_t k = k0 + 2 * lane;   // kp_job is even
+  if (k >= J.kp_job) return;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int il = warp + 8 * u;
+    const int64_t i = i0 + il;
+    if (i >= J.rows) break;
+    const int64_t rowoff = (J.row0 + i) * J.kpad + k;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float2 x = *reinterpret_cast<const float2*>(&tile[t][il][2 * lane]);
+      float p0[3], p1[3];
+      split_value<BF16, float>(x.x, npieces, p0);
+      split_value<BF16, float>(x.y, npieces, p1);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q >= npieces) break;
+        const int64_t idx = (int64_t)(q * 4 + t) * J.plane_stride + rowoff;
+        if constexpr (BF16)
+          *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(J.dst) + idx) =
+              __floats2bfloat162_rn(p0[q], p1[q]);
+        else
+          *reinterpret_cast<float2*>(reinterpret_cast<float*>(J.dst) + idx) = make_float2(p0[q], p1[q]);
+      }
+    }
+  }
+}
+
+// The plan of Z = C T for a batch precision (the second product's split).
+TcPlan group_plan(int32_t prec) {
+  TcPlan a, b;
+  plans_for(prec, a, b);
+  return b;
+}
+
+}  // namespace
+
+int tc_group_epr(int32_t prec) { return (int)group_plan(prec).epr; }
+int tc_group_npieces(int32_t prec) { return group_plan(prec).npieces; }
+
+size_t tc_group_piece_bytes(int32_t prec, int64_t rows, int64_t kpad) {
+  const TcPlan pl = group_plan(prec);
+  return (size_t)pl.npieces * 4 * rows * kpad * (pl.bf16 ? 2 : 4);
+}
+
+qmcur_status tc_group_split(int32_t prec, const TcSplitJob* jobs, int njobs, int tiles,
+                            cudaStream_t st) {
+  if (njobs < 1 || tiles < 1) return QMCUR_ERR_INVALID_ARG;
+  const TcPlan pl = group_plan(prec);
+  if (pl.bf16) k_split_table<true><<<tiles, 256, 0, st>>>(jobs, njobs, pl.npieces);
+  else k_split_table<false><<<tiles, 256, 0, st>>>(jobs, njobs, pl.npieces);
+  return cuda_ok(cudaGetLastError());
+}
+
+qmcur_status tc_group_residual(int32_t prec, int bn, const void* A_all, int64_t rows_a,
+                               const void* B_all, int64_t rows_b, int64_t kpad,
+                               const TcGroupTile* tiles, int ntiles, const TcGroupProb* probs,
+                               double* partial, int32_t* dev_status, cudaStream_t st) {
+  if (ntiles < 1 || (bn != 64 && bn != 128)) return QMCUR_ERR_INVALID_ARG;
+  const TcPlan pl = group_plan(prec);
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, const_cast<void*>(A_all), pl.bf16, rows_a, kpad, pl.npieces, BM) ||
+      !make_map(&mB, const_cast<void*>(B_all), pl.bf16, rows_b, kpad, pl.npieces, bn))
+    return QMCUR_ERR_CUDA;
+  TcParams p{};
+  p.M = 1;
+  p.N = 1;
+  p.nterms = pl.nterms;
+  for (int i = 0; i < 6; ++i) { p.ta[i] = pl.ta[i]; p.tb[i] = pl.tb[i]; }
+  p.mode = MODE_GROUPED;
+  p.nsplit = 1;
+  p.partial = partial;
+  p.done = nullptr;   // k_batch_fold folds per problem
+  p.status = dev_status;
+  p.gtiles = tiles;
+  p.gprobs = probs;
+  p.gcount = ntiles;
+  if (pl.bf16)
+    return bn == 64 ? launch_gemm_mode<true, 64, false, MODE_GROUPED>(mA, mB, p, st)
+                    : launch_gemm_mode<true, 128, false, MODE_GROUPED>(mA, mB, p, st);
+  return bn == 64 ? launch_gemm_mode<false, 64, false, MODE_GROUPED>(mA, mB, p, st)
+                  : launch_gemm_mode<false, 128, false, MODE_GROUPED>(mA, mB, p, st);
 }
 
 }  // namespace qmcur

@@ -259,7 +259,9 @@ class MaskedCURLoss(torch.autograd.Function):
 class Batch:
     """A batched QMCUR plan (qmcur_batch_plan): problems As[b] ((4, m_b, n_b)
     float32 CUDA tensors), cs[b] columns, rs[b] rows, rank_caps[b]; one graph
-    replay per run().  get(b, what) copies one output into a new tensor."""
+    replay per run().  prec selects the arithmetic of the grouped Z = C T
+    (PREC_FP32: CUDA cores; a split precision: one grouped tcgen05 launch).
+    get(b, what) copies one output into a new tensor."""
 
     WHAT = {"col_p": (0, torch.float64), "row_p": (1, torch.float64), "J": (2, torch.int32),
             "I": (3, torch.int32), "C": (4, torch.float32), "R": (5, torch.float32),
@@ -267,7 +269,7 @@ class Batch:
             "info": (9, torch.int32)}
 
     def __init__(self, As, cs, rs, rank_caps=None, sampler=SAMPLER_NORM, seed=0, rcond=1e-10,
-                 max_sweeps=0, stream=None, pinv_method=PINV_JACOBI_FP64):
+                 max_sweeps=0, stream=None, pinv_method=PINV_JACOBI_FP64, prec=PREC_FP32):
         self.As = list(As)
         n = len(self.As)
         self.shapes = [(a.shape[1], a.shape[2], int(c), int(r)) for a, c, r in zip(self.As, cs, rs)]
@@ -275,7 +277,7 @@ class Batch:
         carr = (ctypes.c_int64 * n)(*[int(x) for x in cs])
         rarr = (ctypes.c_int64 * n)(*[int(x) for x in rs])
         kap = None if rank_caps is None else (ctypes.c_int32 * n)(*[int(x) for x in rank_caps])
-        o = Opts(sampler, PREC_FP32, seed, 0, 0, rcond, 0, max_sweeps, pinv_method, 0)
+        o = Opts(sampler, prec, seed, 0, 0, rcond, 0, max_sweeps, pinv_method, 0)
         self.status = status_tensor(self.As[0].device)
         self.handle = ctypes.c_void_p()
         _check(lib().qmcur_batch_plan(n, descs, carr, rarr, kap, ctypes.byref(o),

@@ -70,3 +70,42 @@ def test_batch_replay_is_deterministic(batch):
     again = [host(B.get(b, "out3")) for b in range(len(probs))]
     for a, b in zip(first, again):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [Q.PREC_BF16_MIXED, Q.PREC_BF16X6, Q.PREC_TF32X3],
+                         ids=["bf16mixed", "bf16x6", "tf32x3"])
+def test_batch_tensor_core_residual(prec):
+    # the grouped tcgen05 Z = C T (stacked operand pieces of all problems, one
+    # launch) against the oracle's residual of the same U, and against the
+    # CUDA-core FP32 plan of the same batch: both within 1e-5; everything
+    # before the product (probabilities, draws, gathers, core, T = U R) is
+    # shared, so U and the index sets agree bit for bit
+    probs = synth.batch_problems(count=24, seed=3)
+    As = [dev(p["X"]) for p in probs]
+    args = ([p["c"] for p in probs], [p["r"] for p in probs], [p["rank"] for p in probs])
+    kw = dict(sampler=Q.SAMPLER_NORM, seed=11, pinv_method=Q.PINV_SUBSPACE_FP32)
+    F = Q.Batch(As, *args, prec=Q.PREC_FP32, **kw)
+    T = Q.Batch(As, *args, prec=prec, **kw)
+    F.run()
+    T.run()
+    torch.cuda.synchronize()
+    assert int(F.status.item()) == 0 and int(T.status.item()) == 0
+    for b, p in enumerate(probs):
+        U = host(T.get(b, "U"))
+        assert np.array_equal(U, host(F.get(b, "U")))
+        assert np.array_equal(host(T.get(b, "J")), host(F.get(b, "J")))
+        A64 = p["X"].astype(np.float64)
+        Co = host(T.get(b, "C")).astype(np.float64)
+        I = host(T.get(b, "I"))
+        Ro = A64[:, I, :]
+        rel_o = O.residual(A64, O.reconstruct(Co, U.astype(np.float64), Ro))[0]
+        rel, rel_f = host(T.get(b, "out3"))[0], host(F.get(b, "out3"))[0]
+        assert abs(rel - rel_o) < 1e-5, (b, rel, rel_o)
+        assert abs(rel - rel_f) < 1e-5, (b, rel, rel_f)
+    again = [host(T.get(b, "out3")) for b in range(len(probs))]
+    T.run()
+    torch.cuda.synchronize()
+    for b in range(len(probs)):
+        assert np.array_equal(again[b], host(T.get(b, "out3")))   # fixed-order folds
+    F.close()
+    T.close()

@@ -150,15 +150,18 @@ def test_color4096_full_size():
                Q.PINV_JACOBI_FP64, _gap_bound)
 
 
-@pytest.mark.parametrize("method", [Q.PINV_SUBSPACE_FP32, Q.PINV_JACOBI_FP64],
-                         ids=["subspace", "jacobi"])
-def test_batch512_full_size(method):
-    # the subspace core is the benchmarked one
+@pytest.mark.parametrize("method,prec", [(Q.PINV_SUBSPACE_FP32, Q.PREC_FP32),
+                                         (Q.PINV_JACOBI_FP64, Q.PREC_FP32),
+                                         (Q.PINV_SUBSPACE_FP32, Q.PREC_BF16_MIXED)],
+                         ids=["subspace", "jacobi", "subspace-bf16"])
+def test_batch512_full_size(method, prec):
+    # the subspace core is the benchmarked one, with the FP32 and the split
+    # (grouped tcgen05) Z = C T
     probs = synth.batch_problems(count=512, seed=3)
     As = [dev(p["X"]) for p in probs]
     B = Q.Batch(As, [p["c"] for p in probs], [p["r"] for p in probs],
                 [p["rank"] for p in probs], sampler=Q.SAMPLER_NORM, seed=17,
-                pinv_method=method)
+                pinv_method=method, prec=prec)
     B.run()
     torch.cuda.synchronize()
     assert int(B.status.item()) == 0
