@@ -25,14 +25,13 @@
 // product carries about 2^-46 of sum |x| |y|.  W is split into pairs once.
 //
 // Iteration s, from P (c x k, near-orthonormal) and Y = W P:
-//   Z  = W^H Y                         product (c x k, K = r)
-//   M  = P^H Z,  E = P^H P - I          Gram products (k x k)
-//   R_Y = chol32(M);  Z' = Z R_Y^-1     (= W^H Q with Q = Y R_Y^-1, the
-//                                        left basis normalised)
-//   M' = M - E M                        (P (I - E) P^H: the projector on span P
-//                                        to first order in E)
-//   G' = Z'^H Z';  rho_s = ||Z - P M'||_F / ||Z||_F
-//   R' = chol32(G');  P <- Z' R'^-1;  Y <- W P
+//   Z = W^H Y;  M = Y^H Y (= P^H Z);  E = P^H P - I
+//   R_Y = chol32(M);  Z' = Z R_Y^-1      (= W^H Q with Q = Y R_Y^-1, the left
+//                                         basis normalised);  M' = M - E M
+//                                        (P (I - E) P^H: the projector on
+//                                         span P to first order in E)
+//   G' = Z'^H Z';  X = W Z';  rho_s = ||Z - P M'||_F / ||Z||_F
+//   R' = chol32(G');  P <- Z' R'^-1;  Y <- X R'^-1 (= W P)
 // rho_s measures how far W^H W moves span(P); times kappa^2 (kappa^2 taken
 // from the diagonal of R_Y, whose Gram M ~ Sigma_k^2) it bounds the angle of
 // span(P) to S, and the angle shrinks by (sigma_{k+1} / sigma_k)^2 per
@@ -42,41 +41,47 @@
 // (QMCUR_ERR_NO_CONVERGENCE: the spectrum has no usable gap at k).
 //
 // Then U = P (W P)^+ by CholeskyQR2 with FP32 factors:
-//   Y = W P;  R1 = chol32(Y^H Y);  Q1 = Y R1^-1, T1 = P R1^-1
-//   R2 = chol32(Q1^H Q1);  Q2 = Q1 R2^-1, T2 = T1 R2^-1      (Y = Q2 R2 R1,
-//                                                            P = T2 R2 R1)
+//   G1 = Y^H Y;  R1 = chol32(G1);  Q1 = Y R1^-1, T1 = P R1^-1
+//   G2 = Q1^H Q1;  R2 = chol32(G2);  Q2 = Q1 R2^-1, T2 = T1 R2^-1
+//                                            (Y = Q2 R2 R1, P = T2 R2 R1)
 //   E2 = Q2^H Q2 - I;  V = T2 - T2 E2 ~ T2 (I + E2)^-1;  U = V Q2^H,
 // i.e. U = T2 Q2^+ = P (R2 R1)^-1 Q2^+ = P Y^+, with ||E2|| ~ u32 ||E1||, so
 // that the first-order correction leaves O(||E2||^2) behind.
 //
 // Everything runs in ONE cooperative persistent kernel of one 512-thread CTA
-// per SM, with a bounded grid barrier between steps.  A product step is a
-// list of (16 x 16 output tile, k-range) items dealt to the 2 x SMs tile
-// workers; items of one tile sum their partials in k order (the last to
-// arrive does it), so results do not depend on timing.  In a solve step every
-// CTA that holds rows factors the Gram matrix itself (identical arithmetic,
-// identical factors, no barrier) and solves its rows, one warp per row.
-// Every CTA evaluates the stopping rule itself from the same global values,
-// so all take the same branch.
+// per SM, with a bounded grid barrier between steps (4 per iteration).  A
+// product step cuts its products into (8 x 8 output tile, 16-deep k-slice)
+// units and deals each of the 8 x SMs tile workers (64 threads, one per tile
+// entry, each carrying the quaternion's four components) one contiguous run
+// of units, so every worker gets the same work to within one slice; a tile
+// split over several runs sums their partials in k order (the last run to
+// arrive does it), so results do not depend on timing.  In a solve step
+// every CTA that holds rows factors the Gram matrix itself (identical
+// arithmetic, identical factors, no barrier) and solves its rows, one warp
+// per row.  Every CTA evaluates the stopping rule itself from the same global
+// values, so all take the same branch.
 #include "small_impl.cuh"
 
 namespace qmcur {
 namespace {
 
 constexpr int kRfThreads = kCholThreads;             // 512
-constexpr int kRfTileThreads = 256;
+constexpr int kRfTileThreads = 64;                   // a worker: one thread per tile entry
 constexpr int kRfWorkers = kRfThreads / kRfTileThreads;
-constexpr int kRfTS = 16;                            // output tile edge (quaternions)
+constexpr int kRfTS = 8;                             // output tile edge (quaternions)
 constexpr int kRfBK = 16;                            // k-slice
-constexpr int kRfMaxSplits = 8;
-constexpr int kRfMaxParts = 1024;                    // split partial tiles per step
-constexpr int kRfMaxTiles = 8192;                    // tiles of a norm product, split-tile counters
-constexpr int kRfMaxDim = 16384;                     // r, c at most (tiles of the norm product)
+constexpr int kRfMaxGrid = 160;                      // CTAs at most (one per SM)
+constexpr int kRfMaxWorkers = kRfMaxGrid * kRfWorkers;
+constexpr int kRfMaxTiles = 32768;                   // tiles of the norm product
+constexpr int kRfMaxDim = 16384;                     // r, c at most
 constexpr int kRfMaxIter = 64;
 constexpr double kAngleTol = 1e-14;                  // target angle of span(P) to S
 constexpr float kCholShift = 1e-5f;                  // relative diagonal shift of a retried factor
 
 static_assert(kRfWorkers * kRfTileThreads == kRfThreads, "whole tile workers");
+static_assert(kRfTS * kRfTS == kRfTileThreads, "one thread per tile entry");
+static_assert((kRfMaxDim + kRfTS - 1) / kRfTS * ((kSmallCholMax + kRfTS - 1) / kRfTS) <= kRfMaxTiles,
+              "norm tiles");
 
 // ---------------------------------------------------------------------------
 // Float-float arithmetic.  A pair (h, l) stands for h + l.  The rn
@@ -105,6 +110,16 @@ __device__ __forceinline__ void ff_add1(float ah, float al, float bh, float bl, 
   ff_norm(s, __fadd_rn(__fadd_rn(al, bl), e), rh, rl);
 }
 
+__device__ __forceinline__ QFF qff_zero() {
+  return QFF{make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+}
+
+__device__ __forceinline__ QFF qff_conj(QFF v) {
+  v.h.y = -v.h.y; v.h.z = -v.h.z; v.h.w = -v.h.w;
+  v.l.y = -v.l.y; v.l.z = -v.l.z; v.l.w = -v.l.w;
+  return v;
+}
+
 __device__ __forceinline__ QFF qff_add(const QFF& a, const QFF& b) {
   QFF r;
   ff_add1(a.h.x, a.l.x, b.h.x, b.l.x, r.h.x, r.l.x);
@@ -120,12 +135,9 @@ __device__ __forceinline__ QFF qff_neg(QFF a) {
   return a;
 }
 
-__device__ __forceinline__ QFF qff_zero() {
-  return QFF{make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-}
-
 // Loads and stores: kDtypeFF planes hold float2 (h, l) per entry; F64 and F32
-// planes (the caller's W and U) are split / rounded on the way.
+// planes (the caller's W and U, the FP32 factor inverses) are split / rounded
+// on the way.
 __device__ __forceinline__ QFF ldff(const QPtr& q, int64_t off) {
   QFF v;
   if (q.dtype == kDtypeFF) {
@@ -178,7 +190,8 @@ __device__ __forceinline__ void stff(const QPtr& q, int64_t off, const QFF& v) {
 // alpha in {1, -1}, beta in {0, 1}; op(X) M x K (X stored K x M when xh:
 // op(X) = X^H), op(Y) K x N likewise.  With norm, nothing is stored: the step
 // folds ||Zin - op(X) op(Y)||_F^2 and ||Zin||_F^2 into norm_out[0..1] (fixed
-// order).
+// order).  With upper, only the tiles on and above the diagonal are formed
+// (a Hermitian result that is read through its upper triangle).
 struct RfJob {
   QPtr X, Y, Zin, Zout;
   int M, N, K;
@@ -187,9 +200,12 @@ struct RfJob {
   int add_in;           // beta = 1
   int minus_eye;
   int norm;
+  int upper;
   float scale;          // exact power of two applied to the stored result (0: none)
-  int splits, kchunk;   // filled by plan_jobs
-  int tiles, tn;        // output tiles, tiles along N
+  // filled by rf_plan
+  int tm, tn;           // tile rows, tile columns
+  int slices;           // k-slices of a full-depth tile
+  int units, ubase;     // units of the job, first unit in the step
 };
 
 struct RfArgs {
@@ -199,10 +215,10 @@ struct RfArgs {
   int max_iter;
   uint64_t seed;
   // float-float workspaces
-  QPtr P[2], Y, Z, Zp, M, E, Mp, Gp, G1, G2, E2, Q1, Q2, T1, T2, V;
+  QPtr P[2], Y, Z, Zp, X, M, E, Mp, Gp, G1, G2, E2, Q1, Q2, T1, T2, V;
   QPtr U;              // c x r output
-  QFF* part;           // kRfMaxParts x kRfTileThreads split partials
-  unsigned* cnt;       // kRfMaxTiles split-tile arrival counts, then the norm fold's
+  QFF* part;           // 2 x kRfMaxWorkers x kRfTileThreads partials of split tiles
+  unsigned* cnt;       // kRfMaxWorkers split-tile arrival counts, then the norm fold's
   double* normpart;    // kRfMaxTiles x 2 tile norm partials
   double* norms;       // (kRfMaxIter + 1) x 2
   double* kap2;        // kRfMaxIter + 1
@@ -210,41 +226,21 @@ struct RfArgs {
   unsigned* wmax;      // bits of max |W_ij| over the planes (atomicMax, zeroed)
   int32_t* status;
   int32_t* rank_out;
-  int workers;         // gridDim.x * kRfWorkers (for the split plans)
+  int workers;         // gridDim.x * kRfWorkers
 };
 
-// smem: two tile workers' operand slices, or the packed factor + Cholesky buffers
-constexpr int kRfWorkerQ = 2 * kRfTS * (kRfBK + 1);
+// Shared memory: the tile workers' double-buffered operand slices, or the
+// packed factor and the Cholesky buffers.
+constexpr int kRfWorkerQ = 2 * kRfTS * (kRfBK + 1) + 2 * kRfBK * (kRfTS + 1);
 constexpr size_t rf_chol_off(int k) { return (sm_trsm_bytes(k) + 15) / 16 * 16; }
 constexpr size_t rf_smem(int k) {
   const size_t g = (size_t)kRfWorkers * kRfWorkerQ * sizeof(QFF);
-  const size_t s = rf_chol_off(k) + sm_chol_bytes();
-  return g > s ? g : s;
+  const size_t f = rf_chol_off(k) + sm_chol_bytes();
+  return g > f ? g : f;
 }
 
 // ---------------------------------------------------------------------------
 // Products.
-
-__device__ __forceinline__ QFF qff_conj(QFF v) {
-  v.h.y = -v.h.y; v.h.z = -v.h.z; v.h.w = -v.h.w;
-  v.l.y = -v.l.y; v.l.z = -v.l.z; v.l.w = -v.l.w;
-  return v;
-}
-
-// Entry (row i, k-index l) of op(X) for an M x K operand view (X stored K x M
-// and conjugated when xh); zero outside.
-__device__ __forceinline__ QFF ld_opx(const QPtr& X, int xh, int M, int K, int i, int l) {
-  if (i >= M || l >= K) return qff_zero();
-  if (!xh) return ldff(X, (int64_t)i * X.ld + l);
-  return qff_conj(ldff(X, (int64_t)l * X.ld + i));
-}
-
-// Entry (k-index l, column j) of op(Y) for a K x N operand view.
-__device__ __forceinline__ QFF ld_opy(const QPtr& Y, int yh, int K, int N, int l, int j) {
-  if (l >= K || j >= N) return qff_zero();
-  if (!yh) return ldff(Y, (int64_t)l * Y.ld + j);
-  return qff_conj(ldff(Y, (int64_t)j * Y.ld + l));
-}
 
 __device__ __forceinline__ void worker_bar(int id) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kRfTileThreads) : "memory");
@@ -285,6 +281,12 @@ __device__ __forceinline__ void ff_comp4(float& S, float& C, float a0, float a0l
   C = __fadd_rn(C, c);
 }
 
+// The operands of one product as a tile worker reads them.
+struct RfOp {
+  QPtr X, Y;
+  int M, N, xh, yh;
+};
+
 // (S, C) += x y, the Hamilton product (Sec. 2.2) in float-float
 __device__ __forceinline__ void ff_qmac(float S[4], float C[4], const QFF& x, const QFF& y) {
   const float4 a = x.h, al = x.l, b = y.h, bl = y.l;
@@ -302,38 +304,73 @@ __device__ __forceinline__ void ff_qmac(float S[4], float C[4], const QFF& x, co
                            bl.y, a.w, al.w, b.x, bl.x);
 }
 
-// Accumulates entry (ty, tx) of tile (tm, tn) over [kb, ke) with one worker.
-// The loads are laid out so that consecutive threads read consecutive
-// addresses of the operand's storage.
-__device__ __noinline__ QFF rf_tile_acc(const RfJob& j, int tm, int tn, int kb, int ke, QFF* sm,
+// Entry (ty, tx) = (tid / 8, tid % 8) of tile (tm, tn), accumulated over
+// [kb, ke) by one worker; the thread carries the four components (four
+// independent dependency chains).  Slices are double-buffered (one barrier
+// per slice); each thread loads two entries of the X slice and two of the Y
+// slice, laid out so that consecutive threads read consecutive addresses of
+// the operand's storage.
+__device__ __noinline__ QFF rf_tile_acc(const RfOp op, int tm, int tn, int kb, int ke, QFF* sm,
                                         int tid, int bar_id) {
-  QFF (*xs)[kRfBK + 1] = reinterpret_cast<QFF (*)[kRfBK + 1]>(sm);
-  QFF (*ys)[kRfTS + 1] = reinterpret_cast<QFF (*)[kRfTS + 1]>(sm + kRfTS * (kRfBK + 1));
-  const int tx = tid % kRfTS, ty = tid / kRfTS;
+  QFF (*xs)[kRfTS][kRfBK + 1] = reinterpret_cast<QFF (*)[kRfTS][kRfBK + 1]>(sm);
+  QFF (*ys)[kRfBK][kRfTS + 1] =
+      reinterpret_cast<QFF (*)[kRfBK][kRfTS + 1]>(sm + 2 * kRfTS * (kRfBK + 1));
+  const int ty = tid / kRfTS, tx = tid % kRfTS;
+  const int xl_along = !op.xh, yl_along = op.yh;   // storage contiguous along l
+  int xi[2], xk[2], yj[2], yk[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = tid + u * kRfTileThreads;   // 0 .. 127
+    xi[u] = xl_along ? (e >> 4) : (e & 7);
+    xk[u] = xl_along ? (e & 15) : (e >> 3);
+    yj[u] = yl_along ? (e >> 4) : (e & 7);
+    yk[u] = yl_along ? (e & 15) : (e >> 3);
+  }
   const int m0 = tm * kRfTS, n0 = tn * kRfTS;
+  auto ldx = [&](int l0, int u) -> QFF {
+    const int i = m0 + xi[u], l = l0 + xk[u];
+    if (i >= op.M || l >= ke) return qff_zero();
+    if (!op.xh) return ldff(op.X, (int64_t)i * op.X.ld + l);
+    return qff_conj(ldff(op.X, (int64_t)l * op.X.ld + i));
+  };
+  auto ldy = [&](int l0, int u) -> QFF {
+    const int j = n0 + yj[u], l = l0 + yk[u];
+    if (j >= op.N || l >= ke) return qff_zero();
+    if (!op.yh) return ldff(op.Y, (int64_t)l * op.Y.ld + j);
+    return qff_conj(ldff(op.Y, (int64_t)j * op.Y.ld + l));
+  };
+  QFF vx0 = ldx(kb, 0), vx1 = ldx(kb, 1), vy0 = ldy(kb, 0), vy1 = ldy(kb, 1);
+  xs[0][xi[0]][xk[0]] = vx0;
+  xs[0][xi[1]][xk[1]] = vx1;
+  ys[0][yk[0]][yj[0]] = vy0;
+  ys[0][yk[1]][yj[1]] = vy1;
+  worker_bar(bar_id);
   float S[4] = {0.f, 0.f, 0.f, 0.f}, C[4] = {0.f, 0.f, 0.f, 0.f};
-  const int xa = tid / kRfBK, xb = tid % kRfBK;          // xh = 0: contiguous along l
-  const int xr = j.xh ? xb : xa, xl = j.xh ? xa : xb;    // xh = 1: contiguous along rows
-  const int yl = j.yh ? tid % kRfBK : tid / kRfTS;       // yh = 1: contiguous along l
-  const int yc = j.yh ? tid / kRfBK : tid % kRfTS;       // yh = 0: contiguous along columns
-  QFF xv = ld_opx(j.X, j.xh, j.M, ke, m0 + xr, kb + xl);
-  QFF yv = ld_opy(j.Y, j.yh, ke, j.N, kb + yl, n0 + yc);
-  for (int k0 = kb; k0 < ke; k0 += kRfBK) {
-    worker_bar(bar_id);   // the previous slice is no longer read
-    xs[xr][xl] = xv;
-    ys[yl][yc] = yv;
-    worker_bar(bar_id);
-    if (k0 + kRfBK < ke) {   // the next slice's loads in flight during this one
-      xv = ld_opx(j.X, j.xh, j.M, ke, m0 + xr, k0 + kRfBK + xl);
-      yv = ld_opy(j.Y, j.yh, ke, j.N, k0 + kRfBK + yl, n0 + yc);
+  int b = 0;
+  for (int k0 = kb; k0 < ke; k0 += kRfBK, b ^= 1) {
+    const bool more = k0 + kRfBK < ke;
+    if (more) {
+      vx0 = ldx(k0 + kRfBK, 0);
+      vx1 = ldx(k0 + kRfBK, 1);
+      vy0 = ldy(k0 + kRfBK, 0);
+      vy1 = ldy(k0 + kRfBK, 1);
     }
+    const QFF* xr = xs[b][ty];
+    const QFF (*yr)[kRfTS + 1] = ys[b];
     const int lend = ke - k0 < kRfBK ? ke - k0 : kRfBK;
     if (lend == kRfBK) {
 #pragma unroll 2
-      for (int l = 0; l < kRfBK; ++l) ff_qmac(S, C, xs[ty][l], ys[l][tx]);
+      for (int l = 0; l < kRfBK; ++l) ff_qmac(S, C, xr[l], yr[l][tx]);
     } else {
-      for (int l = 0; l < lend; ++l) ff_qmac(S, C, xs[ty][l], ys[l][tx]);
+      for (int l = 0; l < lend; ++l) ff_qmac(S, C, xr[l], yr[l][tx]);
     }
+    if (more) {
+      xs[b ^ 1][xi[0]][xk[0]] = vx0;
+      xs[b ^ 1][xi[1]][xk[1]] = vx1;
+      ys[b ^ 1][yk[0]][yj[0]] = vy0;
+      ys[b ^ 1][yk[1]][yj[1]] = vy1;
+    }
+    worker_bar(bar_id);   // the next slice is stored; this one is no longer read
   }
   QFF acc;
   ff_norm(S[0], C[0], acc.h.x, acc.l.x);
@@ -382,79 +419,144 @@ __device__ double rf_worker_sum(double v, double* sh, int tid, int bar_id) {
   return s;
 }
 
+// Units of every job and their place in the step; returns the step's total.
+__device__ int rf_plan(RfJob* jobs, int n) {
+  int total = 0;
+  for (int q = 0; q < n; ++q) {
+    RfJob& j = jobs[q];
+    j.tm = (j.M + kRfTS - 1) / kRfTS;
+    j.tn = (j.N + kRfTS - 1) / kRfTS;
+    j.slices = (j.K + kRfBK - 1) / kRfBK;
+    if (j.upper) {
+      j.units = 0;
+      for (int t = 0; t < j.tm; ++t) j.units += (j.tn > t ? j.tn - t : 0) * j.slices;
+    } else {
+      j.units = j.tm * j.tn * j.slices;
+    }
+    j.ubase = total;
+    total += j.units;
+  }
+  return total;
+}
+
+// Tile (tm, tn) and slice s of unit ul of a job.
+__device__ __forceinline__ void rf_locate(const RfJob& j, int ul, int& tm, int& tn, int& s) {
+  if (j.upper) {
+    tm = 0;
+    for (int ru = j.tn * j.slices; ul >= ru && tm + 1 < j.tm; ru = (j.tn - tm) * j.slices) {
+      ul -= ru;
+      ++tm;
+    }
+    tn = tm + ul / j.slices;
+    s = ul % j.slices;
+  } else {
+    const int t = ul / j.slices;
+    s = ul - t * j.slices;
+    tm = t / j.tn;
+    tn = t - tm * j.tn;
+  }
+}
+
+// Worker w of nw takes units [rf_start(w), rf_start(w + 1)).
+__device__ __forceinline__ int rf_start(int w, int nw, int total) {
+  return (int)(((int64_t)w * total) / nw);
+}
+
+// The worker whose run holds unit x.
+__device__ __forceinline__ int rf_owner(int x, int nw, int total) {
+  return (int)((((int64_t)x + 1) * nw - 1) / total);
+}
+
 // One step of up to three independent products (at most one with `norm`).
-__device__ void rf_gemm_step(const RfArgs& a, const RfJob* jobs, int njobs, double* norm_out,
-                             int vb, int vg, unsigned char* smem) {
+// The workers of CTA b are workers kRfWorkers b .. kRfWorkers (b + 1) - 1,
+// so that small steps spread over the SMs.  A run that covers a tile only in part leaves its
+// partial in the slot of its first tile (2w) or of its last (2w + 1); the
+// tile's counter is that of the worker holding its first unit (no other
+// split tile starts in that worker's run), and the last run to arrive sums
+// the partials in run order.
+__device__ __noinline__ void rf_gemm_step(const RfArgs& a, RfJob* jobs, int njobs, double* norm_out,
+                             unsigned char* smem) {
   __shared__ int last_sh[kRfWorkers];
   __shared__ double red_sh[kRfWorkers][kRfTileThreads / 32];
   const int worker = threadIdx.x / kRfTileThreads, wtid = threadIdx.x % kRfTileThreads;
   QFF* wsm = reinterpret_cast<QFF*>(smem) + worker * kRfWorkerQ;
   const int bar_id = 1 + worker;
-  int items[3], ibase[3], tbase[3], pbase[3];
-  int total = 0, tiles_total = 0, parts_total = 0;
-  for (int q = 0; q < 3; ++q) {
-    items[q] = q < njobs ? jobs[q].tiles * jobs[q].splits : 0;
-    ibase[q] = total;
-    tbase[q] = tiles_total;
-    pbase[q] = parts_total;
-    total += items[q];
-    if (q < njobs && jobs[q].splits > 1) {   // counters and partials: split jobs only
-      tiles_total += jobs[q].tiles;
-      parts_total += items[q];
-    }
-  }
-  // one item per worker 0 of every CTA first, then worker 1
-  for (int t = vb + vg * worker; t < total; t += vg * kRfWorkers) {
-    const int q = t < ibase[1] ? 0 : (t < ibase[2] ? 1 : 2);
+  const int total = rf_plan(jobs, njobs);
+  const int nw = a.workers;
+  const int w = kRfWorkers * blockIdx.x + worker;
+  const int u_begin = rf_start(w, nw, total), u_end = rf_start(w + 1, nw, total);
+  for (int u = u_begin; u < u_end;) {
+    int q = 0;
+    while (q + 1 < njobs && u >= jobs[q + 1].ubase) ++q;
     const RfJob& j = jobs[q];
-    const int tt = t - ibase[q];
-    const int tile = tt % j.tiles, sp = tt / j.tiles;
-    const int tm = tile / j.tn, tn = tile % j.tn;
-    const int kb = sp * j.kchunk;
-    const int ke = kb + j.kchunk < j.K ? kb + j.kchunk : j.K;
-    QFF acc = rf_tile_acc(j, tm, tn, kb, ke, wsm, wtid, bar_id);
-    if (j.splits > 1) {
-      QFF* slot = a.part + ((size_t)pbase[q] + (size_t)tile * j.splits + sp) * kRfTileThreads;
-      slot[wtid] = acc;
+    int tm, tn, s;
+    rf_locate(j, u - j.ubase, tm, tn, s);
+    const int ns = j.slices;
+    const int tile_u0 = u - s;
+    const int s_end = ns < s + (u_end - u) ? ns : s + (u_end - u);
+    const int ke = s_end * kRfBK < j.K ? s_end * kRfBK : j.K;
+    const RfOp op{j.X, j.Y, j.M, j.N, j.xh, j.yh};
+    QFF acc = rf_tile_acc(op, tm, tn, s * kRfBK, ke, wsm, wtid, bar_id);
+    u += s_end - s;
+    if (s > 0 || s_end < ns) {   // a tile split over several runs
+      // the runs holding the tile's units, in k order: from the owner of a
+      // unit, the next run starts where that owner's ends (runs may be empty)
+      const int wa = rf_owner(tile_u0, nw, total);
+      int nseg = 0;
+      for (int x = tile_u0; x < tile_u0 + ns; x = rf_start(rf_owner(x, nw, total) + 1, nw, total))
+        ++nseg;
+      const int slot = rf_start(w, nw, total) >= tile_u0 ? 2 * w : 2 * w + 1;
+      a.part[(size_t)slot * kRfTileThreads + wtid] = acc;
       __threadfence();
       worker_bar(bar_id);
-      if (wtid == 0) last_sh[worker] = atomicAdd(a.cnt + tbase[q] + tile, 1u) == (unsigned)(j.splits - 1);
+      if (wtid == 0) last_sh[worker] = atomicAdd(a.cnt + wa, 1u) == (unsigned)(nseg - 1);
       worker_bar(bar_id);
       if (!last_sh[worker]) continue;
       __threadfence();
-      const QFF* src = a.part + ((size_t)pbase[q] + (size_t)tile * j.splits) * kRfTileThreads + wtid;
       acc = qff_zero();
-      for (int s = 0; s < j.splits; ++s) {   // in k order; written by other SMs
-        const float4* p = reinterpret_cast<const float4*>(src + (size_t)s * kRfTileThreads);
+      for (int x = tile_u0; x < tile_u0 + ns;) {   // in k order; written by other SMs
+        const int v = rf_owner(x, nw, total);
+        const int sv = rf_start(v, nw, total) >= tile_u0 ? 2 * v : 2 * v + 1;
+        const float4* p = reinterpret_cast<const float4*>(a.part + (size_t)sv * kRfTileThreads + wtid);
         acc = qff_add(acc, QFF{__ldcg(p), __ldcg(p + 1)});
+        x = rf_start(v + 1, nw, total);
       }
-      if (wtid == 0) a.cnt[tbase[q] + tile] = 0u;   // ready for the next step
+      if (wtid == 0) a.cnt[wa] = 0u;   // ready for the next step
     }
     double nd = 0.0, nz = 0.0;
     rf_epilogue(j, tm, tn, wtid, acc, &nd, &nz);
     if (j.norm) {
+      const int tile = tm * j.tn + tn;
       const double sd = rf_worker_sum(nd, red_sh[worker], wtid, bar_id);
       const double sz = rf_worker_sum(nz, red_sh[worker], wtid, bar_id);
       if (wtid == 0) {
         a.normpart[2 * tile] = sd;
         a.normpart[2 * tile + 1] = sz;
         __threadfence();
-        const unsigned done = atomicAdd(a.cnt + kRfMaxTiles, 1u);
-        if (done == (unsigned)(j.tiles - 1)) {   // the last tile folds, in tile order
-          __threadfence();
-          double fd = 0.0, fz = 0.0;
-          for (int u = 0; u < j.tiles; ++u) {
-            fd += __ldcg(a.normpart + 2 * u);
-            fz += __ldcg(a.normpart + 2 * u + 1);
-          }
+        last_sh[worker] = atomicAdd(a.cnt + kRfMaxWorkers, 1u) == (unsigned)(j.tm * j.tn - 1);
+      }
+      worker_bar(bar_id);
+      if (last_sh[worker]) {   // the last tile folds them all: strided, then in thread order
+        __threadfence();
+        double fd = 0.0, fz = 0.0;
+        for (int t = wtid; t < j.tm * j.tn; t += kRfTileThreads) {
+          fd += __ldcg(a.normpart + 2 * t);
+          fz += __ldcg(a.normpart + 2 * t + 1);
+        }
+        fd = rf_worker_sum(fd, red_sh[worker], wtid, bar_id);
+        fz = rf_worker_sum(fz, red_sh[worker], wtid, bar_id);
+        if (wtid == 0) {
           norm_out[0] = fd;
           norm_out[1] = fz;
-          a.cnt[kRfMaxTiles] = 0u;
+          a.cnt[kRfMaxWorkers] = 0u;
         }
       }
     }
   }
 }
+
+// ---------------------------------------------------------------------------
+// Factors.
 
 // ---------------------------------------------------------------------------
 // Solves.
@@ -607,34 +709,6 @@ __device__ __forceinline__ RfJob job(const QPtr& X, int xh, const QPtr& Y, int y
   return j;
 }
 
-// k-range splits: enough items to give every worker one, at most kRfMaxSplits,
-// and the partials of all split jobs of a step within kRfMaxParts.
-__device__ void plan_jobs(RfJob* jobs, int n, int workers) {
-  int tiles_all = 0;
-  for (int q = 0; q < n; ++q) {
-    jobs[q].tn = (jobs[q].N + kRfTS - 1) / kRfTS;
-    jobs[q].tiles = ((jobs[q].M + kRfTS - 1) / kRfTS) * jobs[q].tn;
-    tiles_all += jobs[q].tiles;
-  }
-  int parts = 0;
-  for (int q = 0; q < n; ++q) {
-    const int slices = (jobs[q].K + kRfBK - 1) / kRfBK;
-    int sp = workers / (tiles_all > 0 ? tiles_all : 1);
-    if (sp > kRfMaxSplits) sp = kRfMaxSplits;
-    if (sp > slices) sp = slices;
-    if (sp < 1) sp = 1;
-    const int per = (slices + sp - 1) / sp;
-    jobs[q].kchunk = per * kRfBK;
-    jobs[q].splits = (slices + per - 1) / per;
-    if (jobs[q].splits > 1) parts += jobs[q].tiles * jobs[q].splits;
-  }
-  if (parts > kRfMaxParts)
-    for (int q = 0; q < n; ++q) {
-      jobs[q].splits = 1;
-      jobs[q].kchunk = ((jobs[q].K + kRfBK - 1) / kRfBK) * kRfBK;
-    }
-}
-
 __device__ __forceinline__ bool rf_sync(const RfArgs& a, unsigned& target) {
   return grid_sync(a.bar, a.status, target);
 }
@@ -750,8 +824,7 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
   if (!rf_sync(a, target)) return;
   RfJob jb[3];
   jb[0] = job(a.Wf, 0, a.P[0], 0, a.Y, r, k, c);   // Y = W P0
-  plan_jobs(jb, 1, a.workers);
-  rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
+  rf_gemm_step(a, jb, 1, nullptr, smr);
   if (!rf_sync(a, target)) return;
   StopState st{0.0, 0, 0.0, 0};
   int cur = 0, s = 1;
@@ -760,14 +833,10 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
     const QPtr& P = a.P[cur];
     const QPtr& Pn = a.P[cur ^ 1];
     jb[0] = job(a.Wf, 1, a.Y, 0, a.Z, c, k, r);   // Z = W^H Y
-    plan_jobs(jb, 1, a.workers);
-    rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
-    if (!rf_sync(a, target)) return;
-    jb[0] = job(P, 1, a.Z, 0, a.M, k, k, c);     // M = P^H Z
-    jb[1] = job(P, 1, P, 0, a.E, k, k, c);       // E = P^H P - I
-    jb[1].minus_eye = 1;
-    plan_jobs(jb, 2, a.workers);
-    rf_gemm_step(a, jb, 2, nullptr, vb, vg, smr);
+    jb[1] = job(a.Y, 1, a.Y, 0, a.M, k, k, r);    // M = Y^H Y
+    jb[2] = job(P, 1, P, 0, a.E, k, k, c);        // E = P^H P - I
+    jb[2].minus_eye = 1;
+    rf_gemm_step(a, jb, 3, nullptr, smr);
     if (!rf_sync(a, target)) return;
     // Z' = Z R_Y^-1 with R_Y = chol32(M); then M' = M - E M on the tile workers
     rf_solve_step(a, a.M, a.Z, a.Zp, c, nullptr, nullptr, 0, a.kap2 + s, vb, vg, smr);
@@ -775,25 +844,22 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
     jb[0].Zin = a.M;
     jb[0].neg = 1;
     jb[0].add_in = 1;
-    plan_jobs(jb, 1, a.workers);
-    rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
+    rf_gemm_step(a, jb, 1, nullptr, smr);
     if (!rf_sync(a, target)) return;
     jb[0] = job(a.Zp, 1, a.Zp, 0, a.Gp, k, k, c);   // G' = Z'^H Z'
-    jb[1] = job(P, 0, a.Mp, 0, a.Z, c, k, k);       // ||Z - P M'||, ||Z||
-    jb[1].norm = 1;
-    plan_jobs(jb, 2, a.workers);
-    rf_gemm_step(a, jb, 2, a.norms + 2 * s, vb, vg, smr);
+    jb[0].upper = 1;
+    jb[1] = job(a.Wf, 0, a.Zp, 0, a.X, r, k, c);    // X = W Z'
+    jb[2] = job(P, 0, a.Mp, 0, a.Z, c, k, k);       // ||Z - P M'||, ||Z||
+    jb[2].norm = 1;
+    rf_gemm_step(a, jb, 3, a.norms + 2 * s, smr);
     if (!rf_sync(a, target)) return;
     if (threadIdx.x == 0)
       stop_sh = stop_now(st, s, __ldcg(a.norms + 2 * s), __ldcg(a.norms + 2 * s + 1),
                          __ldcg(a.kap2 + s), k);
     __syncthreads();
     converged = stop_sh != 0;
-    rf_solve_step(a, a.Gp, a.Zp, Pn, c, nullptr, nullptr, 0, nullptr, vb, vg, smr);   // P <- Z' R'^-1
-    if (!rf_sync(a, target)) return;
-    jb[0] = job(a.Wf, 0, Pn, 0, a.Y, r, k, c);    // Y = W P
-    plan_jobs(jb, 1, a.workers);
-    rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
+    // R' = chol32(G'):  P <- Z' R'^-1,  Y <- X R'^-1 (= W P)
+    rf_solve_step(a, a.Gp, a.Zp, Pn, c, &a.X, &a.Y, r, nullptr, vb, vg, smr);
     if (!rf_sync(a, target)) return;
     cur ^= 1;
     if (converged) break;
@@ -801,33 +867,30 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
   const QPtr& P = a.P[cur];
   // U = P (W P)^+ by CholeskyQR2 with FP32 factors and the E2 correction
   jb[0] = job(a.Y, 1, a.Y, 0, a.G1, k, k, r);
-  plan_jobs(jb, 1, a.workers);
-  rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
+  jb[0].upper = 1;
+  rf_gemm_step(a, jb, 1, nullptr, smr);
   if (!rf_sync(a, target)) return;
   rf_solve_step(a, a.G1, a.Y, a.Q1, r, &P, &a.T1, c, nullptr, vb, vg, smr);
   if (!rf_sync(a, target)) return;
   jb[0] = job(a.Q1, 1, a.Q1, 0, a.G2, k, k, r);
-  plan_jobs(jb, 1, a.workers);
-  rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
+  jb[0].upper = 1;
+  rf_gemm_step(a, jb, 1, nullptr, smr);
   if (!rf_sync(a, target)) return;
   rf_solve_step(a, a.G2, a.Q1, a.Q2, r, &a.T1, &a.T2, c, nullptr, vb, vg, smr);
   if (!rf_sync(a, target)) return;
   jb[0] = job(a.Q2, 1, a.Q2, 0, a.E2, k, k, r);
   jb[0].minus_eye = 1;
-  plan_jobs(jb, 1, a.workers);
-  rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
+  rf_gemm_step(a, jb, 1, nullptr, smr);
   if (!rf_sync(a, target)) return;
   jb[0] = job(a.T2, 0, a.E2, 0, a.V, c, k, k);   // V = T2 - T2 E2
   jb[0].Zin = a.T2;
   jb[0].neg = 1;
   jb[0].add_in = 1;
-  plan_jobs(jb, 1, a.workers);
-  rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
+  rf_gemm_step(a, jb, 1, nullptr, smr);
   if (!rf_sync(a, target)) return;
   jb[0] = job(a.V, 0, a.Q2, 1, a.U, c, r, k);    // U = V Q2^H, back to W's scale
   jb[0].scale = wsc;
-  plan_jobs(jb, 1, a.workers);
-  rf_gemm_step(a, jb, 1, nullptr, vb, vg, smr);
+  rf_gemm_step(a, jb, 1, nullptr, smr);
   if (vb == 0 && threadIdx.x == 0) {
     const int iters = s <= a.max_iter ? s : a.max_iter;
     if (a.rank_out != nullptr) { a.rank_out[0] = k; a.rank_out[1] = iters; }
@@ -861,6 +924,7 @@ RfWs carve_refine(Carve& cv, int64_t r, int64_t c, int64_t k) {
   a.Y = carve_ff(cv, r, k);
   a.Z = carve_ff(cv, c, k);
   a.Zp = carve_ff(cv, c, k);
+  a.X = carve_ff(cv, r, k);
   a.M = carve_ff(cv, k, k);
   a.E = carve_ff(cv, k, k);
   a.Mp = carve_ff(cv, k, k);
@@ -873,15 +937,15 @@ RfWs carve_refine(Carve& cv, int64_t r, int64_t c, int64_t k) {
   a.T1 = carve_ff(cv, c, k);
   a.T2 = carve_ff(cv, c, k);
   a.V = carve_ff(cv, c, k);
-  a.part = cv.take<QFF>((size_t)kRfMaxParts * kRfTileThreads);
+  a.part = cv.take<QFF>((size_t)2 * kRfMaxWorkers * kRfTileThreads);
   a.normpart = cv.take<double>((size_t)2 * kRfMaxTiles);
   a.norms = cv.take<double>((size_t)2 * (kRfMaxIter + 1));
   a.kap2 = cv.take<double>((size_t)(kRfMaxIter + 1));
-  w.zero_base = cv.take<unsigned>((size_t)(kRfMaxTiles + 8));
-  w.zero_bytes = (size_t)(kRfMaxTiles + 8) * sizeof(unsigned);
-  a.cnt = w.zero_base;
-  a.wmax = w.zero_base + kRfMaxTiles + 2;
-  a.bar = w.zero_base + kRfMaxTiles + 4;
+  w.zero_base = cv.take<unsigned>((size_t)(kRfMaxWorkers + 8));
+  w.zero_bytes = (size_t)(kRfMaxWorkers + 8) * sizeof(unsigned);
+  a.cnt = w.zero_base;                     // kRfMaxWorkers + 1 counters
+  a.wmax = w.zero_base + kRfMaxWorkers + 2;
+  a.bar = w.zero_base + kRfMaxWorkers + 4;
   return w;
 }
 
@@ -930,7 +994,8 @@ qmcur_status launch_pinv_refine(const qmcur_qmat* W, double rcond, int32_t rank_
       cudaSuccess)
     return QMCUR_ERR_CUDA;
   if (per_sm < 1) return QMCUR_ERR_CUDA;
-  const int grid = cta_cap(sms);
+  int grid = cta_cap(sms);
+  if (grid > kRfMaxGrid) grid = kRfMaxGrid;
   RfArgs& a = w.a;
   for (int t = 0; t < 4; ++t) a.W.p[t] = W->plane[t];
   a.W.ld = W->ld;
