@@ -393,7 +393,7 @@ def fp64_check(Q, A, D, w, prec, sampler, stream, steps=10, warmup=3, rows=256):
 # ncu capture of the current code, per kernel (profiles/), on the 2048 x 2048
 # workload: the tensor-core Z = C T with the fused residual (mixed split) and
 # the refined pseudo-inverse of its 200 x 200 intersection.
-NCU_TRAFFIC = {"gemm_z": 81.89e6 + 2.36e6, "pinv_refine": 1.97e6 + 69.90e6}
+NCU_TRAFFIC = {"gemm_z": 81.89e6 + 2.36e6, "pinv_refine": 8.95e6 + 270.02e6}
 
 
 def peaks():
@@ -683,8 +683,9 @@ def run_ours(args):
                 amount, "bytes" if unit == "GB/s" else "flops")}
     if dom == "pinv" and args.pinv == "refined" and workload_name(args) == WORKLOAD:
         roof["traffic"] = NCU_TRAFFIC["pinv_refine"]
-        roof["traffic_note"] = ("L2 write-backs of the split-k partials; the kernel reads "
-                                "W once (1.3 MB)")
+        roof["traffic_note"] = ("almost all writes: L2 write-backs of the split-tile "
+                                "partials and float-float intermediates of its 27 steps "
+                                "(325 GB/s); the kernel reads W once (1.3 MB)")
 
     # the GEMM stage: tensor work of the split (products x quaternion flops)
     # against the measured BF16 burst (TF32 at the nominal half of it)
@@ -916,7 +917,7 @@ def batch_measure(args, Q, synth, dev, steps, warmup):
                               [p["rank"] for p in probs], sampler=Q.SAMPLER_NORM, seed=0,
                               stream=stream, pinv_method=pinv_method, prec=pc)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    res = {}
+    res, stages = {}, {}
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     for name, B in plans.items():
@@ -934,6 +935,7 @@ def batch_measure(args, Q, synth, dev, steps, warmup):
         torch.cuda.synchronize()
         Q.check_status(B.status, "batch steps")
         res[name] = statistics.median([a.elapsed_time(b) for a, b in evs])
+        stages[name] = B.stage_ms()   # the last timed replay
     clk = clocks.stop()
     rel = {name: np.array([float(B.get(b, "out3")[0].item()) for b in range(len(probs))])
            for name, B in plans.items()}
@@ -944,6 +946,21 @@ def batch_measure(args, Q, synth, dev, steps, warmup):
     pk, pk_kind = peaks()
     nprod = SPLIT_PRODUCTS[split][1]
     tiles = [int(x) for x in host_tiles(Q, plans[split])]
+    # the Z = C T stage (operand splits, grouped tcgen05 product, fused residual)
+    # against min(tensor peak, HBM bandwidth x its intensity); algorithmic bytes:
+    # A read once, C and T as FP32
+    zms = stages[split]["z_gemm_residual"]
+    zbytes = byts + sum(16.0 * (p["m"] * p["c"] + p["c"] * p["n"]) for p in probs)
+    tpk = pk["bf16_tflops"] * (0.5 if split == "tf32x3" else 1.0)
+    hpk = pk["hbm_gbs"] * (nprod * flz / zbytes) / 1e3
+    zach = nprod * flz / (zms / 1e3) / 1e12
+    roof = {"kernel": "k_split_table + k_qgemm_tc (grouped, residual epilogue)",
+            "bound": "tensor" if tpk <= hpk else "hbm", "achieved": zach, "peak": min(tpk, hpk),
+            "unit": "TFLOP/s", "frac": zach / min(tpk, hpk), "traffic": None,
+            "work": "%d BF16 products x 32 m c n per problem; bytes 16 (m n + m c + c n)" % nprod,
+            "intensity_flop_per_byte": nprod * flz / zbytes, "stage_ms": zms,
+            "tensor_peak": tpk, "hbm_bound_tflops": hpk,
+            "peak_source": "measured BF16 burst and HBM copy (" + pk_kind + ")"}
     line = {"metric": METRIC, "value": 512 / (ms / 1e3), "unit": "decompositions/s",
             "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": split,
@@ -956,6 +973,7 @@ def batch_measure(args, Q, synth, dev, steps, warmup):
             "fp32_gemms": {"value": 512 / (ms32 / 1e3), "unit": "decompositions/s",
                            "ms_per_step": ms32},
             "speedup_over_fp32": ms32 / ms,
+            "stage_ms": stages[split], "stage_ms_fp32": stages["fp32"], "roofline": roof,
             "residual_max_abs_diff_vs_fp32": float(np.max(np.abs(rel[split] - rel["fp32"]))),
             "gemm_qtflops_per_step": fl / (ms / 1e3) / 1e12,
             "input_gbs_per_step": byts / (ms / 1e3) / 1e9,

@@ -465,6 +465,13 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
                               const int64_t* r, const int32_t* rank_cap, const qmcur_opts* opts,
                               void** plan, int32_t* dev_status, cudaStream_t stream);
 qmcur_status qmcur_batch_run(void* plan, cudaStream_t stream);
+/* Durations of the stages of the last replay (milliseconds, from events the
+ * graph records at the stage boundaries): ms[0] norms, [1] index draws,
+ * [2] gathers, [3] core, [4] T = U R, [5] Z = C T with the residual (the
+ * operand splits included), [6] the residual fold; n <= 7 of them.  Waits
+ * on the host for the last replay to finish; INVALID_ARG for a bad plan,
+ * ms or n. */
+qmcur_status qmcur_batch_stage_ms(void* plan, float* ms, int32_t n);
 qmcur_status qmcur_batch_view(const void* plan, int32_t index, qmcur_batch_item* out);
 /* Copy one output of problem `index` into dst (device or host memory, at
  * least the output's size, stream-ordered): what = 0 col_p (n doubles),

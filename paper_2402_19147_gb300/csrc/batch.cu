@@ -479,6 +479,8 @@ std::vector<GTile> make_tiles(const std::vector<BatchProblem>& ps, int which, in
 }  // namespace
 
 // ----------------------------------------------------------------- plan ----
+constexpr int kBatchStages = 7;   // norms, sampler, gathers, core, T = U R, Z = C T, fold
+
 struct BatchPlan {
   int count = 0;
   std::vector<BatchProblem> host;
@@ -511,17 +513,28 @@ struct BatchPlan {
   TcGroupProb* dgprobs = nullptr;
   TcGroupTile* dgtiles = nullptr;
   int ngtiles = 0, tc_bn = 128;
+  // stage boundaries, recorded by the captured graph (qmcur_batch_stage_ms)
+  cudaEvent_t ev[kBatchStages + 1] = {};
 };
 
-static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st) {
+// With timed, the stage boundaries are recorded into p->ev (inside the
+// captured graph: one event-record node per boundary).
+static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st, bool timed = false) {
+  auto mark = [&](int i) {   // an external record: a node of the captured graph
+    if (timed) cudaEventRecordWithFlags(p->ev[i], st, cudaEventRecordExternal);
+  };
   const int norm = p->opts.sampler == QMCUR_SAMPLER_NORM;
+  mark(0);
   k_batch_norm_chunk<<<dim3(p->max_chunks, p->count), 256, 0, st>>>(p->dprobs, p->colpart);
   k_batch_norm_fold<<<p->count, 256, 0, st>>>(p->dprobs, p->colpart, norm, p->status);
+  mark(1);
   SampleArgs base{};
   base.seed = p->opts.seed;
   base.norm = norm;
   k_batch_sample<<<2 * p->count, kSampleThreads, p->samp_smem, st>>>(p->dprobs, base, p->status);
+  mark(2);
   k_batch_gather<<<dim3(64, p->count), 256, 0, st>>>(p->dprobs);
+  mark(3);
   if (p->subspace) {
     const qmcur_status s = pinv_each_launch(p->progs, p->order, p->count, p->kmax, st);
     if (s != QMCUR_OK) return s;
@@ -529,7 +542,9 @@ static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st) {
     k_batch_jacobi<<<p->count, 1024, p->jac_smem, st>>>(
         p->dprobs, p->opts.rcond, p->opts.max_sweeps > 0 ? p->opts.max_sweeps : 30);
   }
+  mark(4);
   launch_batch_gemm(p->cfg1, p->dprobs, p->dtiles1, p->ntiles1, 0, nullptr, st);
+  mark(5);
   if (p->tc) {
     qmcur_status s = tc_group_split(p->opts.prec, p->djobs, p->njobs, p->split_tiles, st);
     if (s != QMCUR_OK) return s;
@@ -539,7 +554,9 @@ static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st) {
   } else {
     launch_batch_gemm(p->cfg2, p->dprobs, p->dtiles2, p->ntiles2, 1, p->partial, st);
   }
+  mark(6);
   k_batch_fold<<<p->count, 32, 0, st>>>(p->dprobs, p->partial);
+  mark(7);
   return cuda_ok(cudaGetLastError());
 }
 
@@ -656,6 +673,8 @@ static int autotune(BatchPlan* p, int which, cudaStream_t st) {
 
 static void free_plan(BatchPlan* p) {
   if (p == nullptr) return;
+  for (cudaEvent_t& e : p->ev)
+    if (e) cudaEventDestroy(e);
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
   cudaFree(p->dprobs);
@@ -956,12 +975,14 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
   if (cudaStreamSynchronize(stream) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
   cudaStream_t cap = nullptr;
   if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
+  for (cudaEvent_t& e : p->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaStreamDestroy(cap); free_plan(p); return QMCUR_ERR_CUDA; }
   if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaStreamDestroy(cap);
     free_plan(p);
     return QMCUR_ERR_CUDA;
   }
-  qmcur_status s = enqueue_batch(p, cap);
+  qmcur_status s = enqueue_batch(p, cap, true);
   cudaGraph_t g = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(cap, &g);
   cudaStreamDestroy(cap);
@@ -976,6 +997,19 @@ qmcur_status qmcur_batch_run(void* plan, cudaStream_t stream) {
   NvtxRange nvtx_range("qmcur_batch_run");
   if (plan == nullptr) return QMCUR_ERR_INVALID_ARG;
   return cuda_ok(cudaGraphLaunch(static_cast<BatchPlan*>(plan)->exec, stream));
+}
+
+qmcur_status qmcur_batch_stage_ms(void* plan, float* ms, int32_t n) {
+  BatchPlan* p = static_cast<BatchPlan*>(plan);
+  if (p == nullptr || ms == nullptr || n < 0 || n > kBatchStages) return QMCUR_ERR_INVALID_ARG;
+  if (p->ev[kBatchStages] == nullptr) return QMCUR_ERR_INVALID_ARG;
+  bool ok = cudaEventSynchronize(p->ev[kBatchStages]) == cudaSuccess;
+  for (int i = 0; ok && i < n; ++i) ok = cudaEventElapsedTime(ms + i, p->ev[i], p->ev[i + 1]) == cudaSuccess;
+  if (!ok) {
+    (void)cudaGetLastError();   // leave no error behind for the next call
+    return QMCUR_ERR_CUDA;
+  }
+  return QMCUR_OK;
 }
 
 qmcur_status qmcur_batch_view(const void* plan, int32_t index, qmcur_batch_item* out) {

@@ -76,6 +76,7 @@ SIGNATURES = {
                                           _SZ, _P, _P]),
     "qmcur_batch_plan": (_I32, [_I32, _QP, _P, _P, _P, ctypes.POINTER(Opts), _P, _P, _P]),
     "qmcur_batch_run": (_I32, [_P, _P]),
+    "qmcur_batch_stage_ms": (_I32, [_P, _P, _I32]),
     "qmcur_batch_view": (_I32, [_P, _I32, _P]),
     "qmcur_batch_copy": (_I32, [_P, _I32, _I32, _P, _SZ, _P]),
     "qmcur_batch_destroy": (None, [_P]),
@@ -286,6 +287,15 @@ class Batch:
 
     def run(self, stream=None):
         _check(lib().qmcur_batch_run(self.handle, _stream(stream)), "qmcur_batch_run")
+
+    STAGES = ("norms", "sample", "gather", "core", "t_gemm", "z_gemm_residual", "fold")
+
+    def stage_ms(self):
+        """Durations (ms) of the stages of the last replay, by name; waits for it."""
+        out = (ctypes.c_float * len(self.STAGES))()
+        _check(lib().qmcur_batch_stage_ms(self.handle, out, len(self.STAGES)),
+               "qmcur_batch_stage_ms")
+        return dict(zip(self.STAGES, [float(x) for x in out]))
 
     def get(self, b, what, stream=None):
         code, dt = self.WHAT[what]

@@ -109,3 +109,24 @@ def test_batch_tensor_core_residual(prec):
         assert np.array_equal(again[b], host(T.get(b, "out3")))   # fixed-order folds
     F.close()
     T.close()
+
+
+def test_batch_stage_times():
+    # the graph records its stage boundaries: seven non-negative durations
+    # whose sum is the replay, timed around it on the stream
+    probs = synth.batch_problems(count=16, seed=5)
+    As = [dev(p["X"]) for p in probs]
+    B = Q.Batch(As, [p["c"] for p in probs], [p["r"] for p in probs], [p["rank"] for p in probs],
+                sampler=Q.SAMPLER_NORM, seed=2, pinv_method=Q.PINV_SUBSPACE_FP32,
+                prec=Q.PREC_BF16_MIXED)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    B.run()
+    e1.record()
+    st = B.stage_ms()
+    total = e0.elapsed_time(e1)
+    assert list(st) == list(Q.Batch.STAGES)
+    assert all(v >= 0.0 for v in st.values()), st
+    assert sum(st.values()) <= total * 1.05 + 0.01, (st, total)
+    assert st["core"] > 0.0 and st["z_gemm_residual"] > 0.0
+    B.close()

@@ -2,8 +2,9 @@
 W^+ (Sec. 2.2, Algorithm 1's core), at the intersections the decomposition
 workloads produce and on spectra built to a recipe.
 
-* QMCUR_PINV_REFINED_FP64 (subspace iteration with FP64 products and FP32
-  Cholesky preconditioners): U within max(1e-12, 64 u64 kappa sigma_1 / gap)
+* QMCUR_PINV_REFINED_FP64 (subspace iteration with float-float products on
+  the FP32 pipe, about 2^-46 relative, and FP32 Cholesky preconditioners): U
+  within max(1e-12, 64 u64 kappa sigma_1 / gap)
   relative Frobenius of the oracle, kappa = sigma_1 / sigma_k and gap =
   sigma_k - sigma_{k+1} (the first-order sensitivity of the truncated inverse
   to an FP64 backward error); 1e-12 on the 2048 x 2048 rank-50 workload's
