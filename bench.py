@@ -40,10 +40,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16mixed",
                     choices=["fp32", "tf32x3", "bf16x3", "bf16x6", "bf16mixed"])
-    ap.add_argument("--pinv", default="refined", choices=["refined", "subspace", "jacobi"],
+    ap.add_argument("--pinv", default=None, choices=["refined", "subspace", "jacobi"],
                     help="core of the decomposition workloads: the FP64-accurate refined "
-                         "subspace method (default), the FP64 Jacobi QSVD, or the FP32 "
-                         "subspace method (not FP64-accurate)")
+                         "subspace method, the FP64 Jacobi QSVD, or the FP32 subspace method "
+                         "(not FP64-accurate).  Default: the FP64-accurate core that applies, "
+                         "refined where the spectrum has a gap at the rank cap, the Jacobi on "
+                         "the colour field (sigma_101 / sigma_100 = 0.98)")
     ap.add_argument("--min-seconds", type=float, default=1.0,
                     help="the K-step timed loop is repeated until the repeats cover this "
                          "long; the median repeat is reported")
@@ -62,7 +64,10 @@ def parse():
                     help="decomposition workload: U = W^+ (default) or the paper's C^+ X R^+")
     ap.add_argument("--sampler", default=None, choices=["uniform", "norm"],
                     help="completion workload only (default: the workload's)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.pinv is None:
+        args.pinv = "jacobi" if args.workload == "color4096_smooth100" else "refined"
+    return args
 
 
 DECOMP_WORKLOADS = (WORKLOAD, "color4096_smooth100")
