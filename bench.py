@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "color4096_smooth100", "batch512_uneven",
-                             "color512x768_rank31_mr70",
+                             "color512x768_rank31_mr70", "color1024x1536_rank60_masked",
                              "qsvd_vs_qmcur"])
     ap.add_argument("--core", default="intersection", choices=["intersection", "paper"],
                     help="decomposition workload: U = W^+ (default) or the paper's C^+ X R^+")
@@ -886,6 +886,32 @@ def backward_extra(Q, synth, dev, steps=20, warmup=3):
                                 "peak_source": pk_kind + " BF16 burst"}}
 
 
+def run_backward(args):
+    """The differentiable workload on its own: backward passes per second of
+    the masked CUR loss (backward_extra), with the clocks of the timed calls."""
+    import torch
+    from paper_2402_19147_gb300 import qmcur as Q
+    from paper_2402_19147_gb300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    clocks = Clocks(0)
+    clocks.start()
+    b = backward_extra(Q, synth, dev, steps=args.steps, warmup=max(3, args.warmup))
+    clk = clocks.stop()
+    ms = b["backward_ms"]
+    line = {"metric": METRIC, "value": 1e3 / ms, "unit": "backward passes/s", "n_gpus": 1,
+            "steps": b["steps"], "warmup": b["warmup"], "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x6",
+            "data": "synthetic",
+            "config": {"workload": "color1024x1536_rank60_masked", "m": b["m"], "n": b["n"],
+                       "c": b["c"], "r": b["r"], "rank_cap": b["rank_cap"], "mask": "Bernoulli(0.5)",
+                       "l2": "inputs (25 MB) stay in L2 between calls"},
+            "loss": b["loss"], "roofline": b["tensor_roofline"],
+            "quaternion_tflops_large_products": b["quaternion_tflops_large_products"],
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def color_field_extra(args, Q, synth, dev, steps=3, warmup=1):
     """The 4096 x 4096 colour field (c = r = 500, rank cap 100, uniform
     sampling) decomposed with the FP64 Jacobi core, its FP64-accurate option:
@@ -1314,6 +1340,8 @@ def main():
         run_batch(args)
     elif args.workload == "color512x768_rank31_mr70":
         run_complete(args)
+    elif args.workload == "color1024x1536_rank60_masked":
+        run_backward(args)
     elif args.workload == "qsvd_vs_qmcur":
         run_qsvd_vs_qmcur(args)
     elif args.core == "paper":
