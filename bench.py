@@ -808,7 +808,7 @@ def run_ours(args):
         bl = batch_measure(args, Q, synth, dev, 10, 3)
         line["extra"]["batch512_uneven"] = {k: bl[k] for k in (
             "value", "unit", "ms_per_step", "steps", "warmup", "config", "fp32_gemms",
-            "speedup_over_fp32", "residual_max_abs_diff_vs_fp32", "z_product")}
+            "speedup_over_fp32", "residual_max_abs_diff_vs_fp32", "z_product", "fp32_subspace_core")}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -962,12 +962,14 @@ def color_field_extra(args, Q, synth, dev, steps=3, warmup=1):
 
 def run_batch(args):
     """512 uneven problems decomposed per step by one replay of the batched
-    plan's CUDA graph (one launch per stage; the core per --pinv: the FP32
-    subspace program, one CTA per problem, or the FP32 Jacobi).  Two plans of
-    the same batch are timed side by side: Z = C T with the fused residual as
-    the grouped FP32 CUDA-core GEMM, and as one grouped tcgen05 launch in the
-    split of --prec (BF16X3 for this product under bf16mixed); value is the
-    split plan's.  Their residuals are compared problem by problem."""
+    plan's CUDA graph (one launch per stage; the core per --pinv: by default
+    the FP64-accurate refined program, one CTA per problem; else the FP32
+    subspace program or the FP32 Jacobi).  Two plans of the same batch are
+    timed side by side: Z = C T with the fused residual as the grouped FP32
+    CUDA-core GEMM, and as one grouped tcgen05 launch in the split of --prec
+    (BF16X3 for this product under bf16mixed); value is the split plan's.
+    Their residuals are compared problem by problem.  With the refined core,
+    a third plan (split GEMMs, FP32 subspace core) is timed beside them."""
     import torch
     from paper_2402_19147_gb300 import qmcur as Q
     from paper_2402_19147_gb300 import synth
@@ -981,13 +983,20 @@ def batch_measure(args, Q, synth, dev, steps, warmup):
     probs = synth.batch_problems(count=512, seed=3)
     As = [torch.from_numpy(p["X"]).to(dev) for p in probs]
     stream = torch.cuda.current_stream()
-    pinv_method = Q.PINV_JACOBI_FP64 if args.pinv == "jacobi" else Q.PINV_SUBSPACE_FP32
+    core = args.pinv or "refined"
+    pinv_method = {"jacobi": Q.PINV_JACOBI_FP64, "subspace": Q.PINV_SUBSPACE_FP32,
+                   "refined": Q.PINV_REFINED_FP64}[core]
+    core_name = {"jacobi": "fp32-jacobi-per-cta", "subspace": "fp32-subspace-per-cta",
+                 "refined": "fp64-refined-subspace-per-cta"}
     split = args.prec if args.prec != "fp32" else "bf16mixed"
     plans = {}
-    for name, pc in (("fp32", Q.PREC_FP32), (split, Q.PREC_NAMES[split])):
+    legs = [("fp32", Q.PREC_FP32, pinv_method), (split, Q.PREC_NAMES[split], pinv_method)]
+    if core == "refined":
+        legs.append(("fp32_core", Q.PREC_NAMES[split], Q.PINV_SUBSPACE_FP32))
+    for name, pc, pm in legs:
         plans[name] = Q.Batch(As, [p["c"] for p in probs], [p["r"] for p in probs],
                               [p["rank"] for p in probs], sampler=Q.SAMPLER_NORM, seed=0,
-                              stream=stream, pinv_method=pinv_method, prec=pc)
+                              stream=stream, pinv_method=pm, prec=pc)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     res, stages = {}, {}
     clocks = Clocks(torch.cuda.current_device())
@@ -1038,13 +1047,17 @@ def batch_measure(args, Q, synth, dev, steps, warmup):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": split,
             "data": "synthetic",
             "config": {"workload": "batch512_uneven", "problems": 512, "gemm_prec": split,
-                       "pinv": ("fp32-jacobi-per-cta" if args.pinv == "jacobi"
-                                else "fp32-subspace-per-cta"), "graph": True,
+                       "pinv": core_name[core], "graph": True,
                        "gemm_tiles": {"t_simt": tiles[0], "z_tcgen05_bn": tiles[1]},
                        "l2": "flushed between steps (256 MiB write)"},
             "fp32_gemms": {"value": 512 / (ms32 / 1e3), "unit": "decompositions/s",
                            "ms_per_step": ms32},
             "speedup_over_fp32": ms32 / ms,
+            "fp32_subspace_core": ({"value": 512 / (res["fp32_core"] / 1e3),
+                                    "unit": "decompositions/s", "ms_per_step": res["fp32_core"],
+                                    "stage_ms": stages["fp32_core"],
+                                    "note": "split GEMMs, the FP32 subspace core (not FP64-accurate)"}
+                                   if "fp32_core" in res else None),
             "stage_ms": stages[split], "stage_ms_fp32": stages["fp32"], "roofline": roof,
             "residual_max_abs_diff_vs_fp32": float(np.max(np.abs(rel[split] - rel["fp32"]))),
             "gemm_qtflops_per_step": fl / (ms / 1e3) / 1e12,

@@ -435,7 +435,12 @@ qmcur_status qmcur_complete_step(qmcur_qmat* X, const uint8_t* mask, int64_t c, 
  * truncated at opts->rcond and rank_cap[b] (limits above);
  * QMCUR_PINV_SUBSPACE_FP32 runs the FP32 subspace method of qmcur_pinv_core
  * with one CTA per problem (rank_cap required, k <= 100, no shared-memory
- * limit on the intersection; largest problems first).  opts->prec selects the
+ * limit on the intersection; largest problems first);
+ * QMCUR_PINV_REFINED_FP64 runs the FP64-accurate refined method of
+ * qmcur_pinv_core with one CTA per problem (same requirements; max_sweeps is
+ * its iteration limit, info[1] the iterations taken, NO_CONVERGENCE in
+ * info[2] when the spectrum has no usable gap at the cap) and keeps U in
+ * FP64 as well (qmcur_batch_copy what = 10).  opts->prec selects the
  * arithmetic of Z = C T with the fused residual: QMCUR_PREC_FP32 (or FP64) a
  * grouped FP32 CUDA-core GEMM; QMCUR_PREC_BF16X3, BF16X6, TF32X3 or
  * BF16_MIXED (= BF16X3 for this product) one grouped tcgen05 launch over the
@@ -476,7 +481,9 @@ qmcur_status qmcur_batch_view(const void* plan, int32_t index, qmcur_batch_item*
 /* Copy one output of problem `index` into dst (device or host memory, at
  * least the output's size, stream-ordered): what = 0 col_p (n doubles),
  * 1 row_p (m doubles), 2 J (c int32), 3 I (r int32), 4 C, 5 R, 6 W, 7 U
- * (four contiguous F32 planes each), 8 out3 (3 doubles), 9 info (3 int32). */
+ * (four contiguous F32 planes each), 8 out3 (3 doubles), 9 info (3 int32),
+ * 10 U in FP64 (four contiguous F64 planes; plans with the refined core
+ * only, INVALID_ARG otherwise). */
 qmcur_status qmcur_batch_copy(const void* plan, int32_t index, int32_t what, void* dst,
                               size_t dst_bytes, cudaStream_t stream);
 void qmcur_batch_destroy(void* plan);

@@ -18,6 +18,10 @@
 //                    one CTA per problem runs the FP32 subspace program of
 //                    the single-problem path (pinv_fast.cu) on its own
 //                    intersection, largest problems first;
+//   or k_pinv_refine_each (opts->pinv_method = QMCUR_PINV_REFINED_FP64):
+//                    one CTA per problem runs the FP64-accurate refined
+//                    program of the single-problem path (pinv_refine.cu),
+//                    writing U in FP64 and its FP32 copy for the GEMMs;
 //   k_batch_gemm     grouped quaternion GEMMs over a flattened tile list
 //                    (T = U R, then Z = C T with the residual fused), tile
 //                    shape chosen per GEMM by timing the candidates at plan
@@ -42,6 +46,15 @@ qmcur_status pinv_each_build(const qmcur_qmat* W, int32_t rank_cap, qmcur_qmat* 
                              int32_t* dev_status, void* prog_out, int* k_out);
 qmcur_status pinv_each_launch(const void* dprogs, const int* dorder, int count, int kmax,
                               cudaStream_t st);
+// The FP64-accurate refined core, one problem per CTA (pinv_refine.cu).
+size_t refine_each_ws_bytes(int64_t r, int64_t c, int64_t k);
+size_t refine_each_args_bytes();
+qmcur_status refine_each_build(const qmcur_qmat* W, int32_t rank_cap, int32_t max_iter,
+                               qmcur_qmat* U, qmcur_qmat* U2, int32_t* rank_out, int32_t* status,
+                               uint64_t seed, void* ws, size_t ws_bytes, void* args_out,
+                               int* k_out);
+qmcur_status refine_each_launch(const void* dargs, const int* dorder, int count, int kmax,
+                                int32_t* batch_status, cudaStream_t st);
 
 constexpr int kBatchMaxCore = 80;      // largest min(r, c) held by k_batch_jacobi
 constexpr int64_t kBatchCoreSmem = 200 * 1024;   // bytes of G and V in shared memory
@@ -54,6 +67,7 @@ struct BatchProblem {
   int32_t* J;              // c
   int32_t* I;              // r
   QView C, R, W, U, T;     // F32: m x c, r x n, r x c, c x r, c x n
+  QView U64;               // F64 c x r (the refined core only; else unset)
   double* out3;            // {rel, num, den}
   int32_t* info;           // {rank, sweeps, status}
   int tile_base2;          // first tile of this problem in the second GEMM's list
@@ -493,7 +507,8 @@ struct BatchPlan {
   int32_t* status = nullptr;
   size_t jac_smem = 0, samp_smem = 0;
   bool subspace = false;      // the core: subspace programs instead of the Jacobi
-  void* progs = nullptr;      // device: one subspace program per problem
+  bool refined = false;       // the core: FP64-accurate refined programs
+  void* progs = nullptr;      // device: one subspace program (or refined arguments) per problem
   int* order = nullptr;       // device: problems, largest first
   void* pinv_arena = nullptr;
   int kmax = 0;
@@ -535,7 +550,11 @@ static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st, bool timed = fa
   mark(2);
   k_batch_gather<<<dim3(64, p->count), 256, 0, st>>>(p->dprobs);
   mark(3);
-  if (p->subspace) {
+  if (p->refined) {
+    const qmcur_status s =
+        refine_each_launch(p->progs, p->order, p->count, p->kmax, p->status, st);
+    if (s != QMCUR_OK) return s;
+  } else if (p->subspace) {
     const qmcur_status s = pinv_each_launch(p->progs, p->order, p->count, p->kmax, st);
     if (s != QMCUR_OK) return s;
   } else {
@@ -707,8 +726,9 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
   if (count < 1 || A == nullptr || c == nullptr || r == nullptr || opts == nullptr || plan_out == nullptr)
     return QMCUR_ERR_INVALID_ARG;
   if (opts->sampler != QMCUR_SAMPLER_NORM && opts->sampler != QMCUR_SAMPLER_UNIFORM) return QMCUR_ERR_INVALID_ARG;
-  const bool subspace = opts->pinv_method == QMCUR_PINV_SUBSPACE_FP32;
-  if (subspace && rank_cap == nullptr) return QMCUR_ERR_UNSUPPORTED;   // the method needs caps
+  const bool refined = opts->pinv_method == QMCUR_PINV_REFINED_FP64;
+  const bool subspace = opts->pinv_method == QMCUR_PINV_SUBSPACE_FP32 || refined;
+  if (subspace && rank_cap == nullptr) return QMCUR_ERR_UNSUPPORTED;   // the methods need caps
   for (int b = 0; b < count; ++b) {
     if (!valid_qmat(&A[b], true, false)) return QMCUR_ERR_INVALID_ARG;
     if (c[b] < 1 || c[b] > A[b].cols || r[b] < 1 || r[b] > A[b].rows) return QMCUR_ERR_INVALID_ARG;
@@ -735,7 +755,7 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
   std::vector<size_t> off;
   size_t total = 0;
   auto take = [&](size_t bytes) { size_t o = total; total += align_up(bytes, 256); return o; };
-  struct Offs { size_t cp, rp, J, I, C, R, W, U, T, o3, info; };
+  struct Offs { size_t cp, rp, J, I, C, R, W, U, T, o3, info, U64; };
   std::vector<Offs> os(count);
   size_t max_rc = 0, max_nm = 0;
   for (int b = 0; b < count; ++b) {
@@ -744,6 +764,7 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     o.cp = take(8 * n); o.rp = take(8 * m); o.J = take(4 * c[b]); o.I = take(4 * r[b]);
     o.C = take(16 * m * c[b]); o.R = take(16 * r[b] * n); o.W = take(16 * r[b] * c[b]);
     o.U = take(16 * c[b] * r[b]); o.T = take(16 * c[b] * n); o.o3 = take(24); o.info = take(12);
+    o.U64 = refined ? take(32 * c[b] * r[b]) : 0;
     const int64_t nr = c[b] > r[b] ? c[b] : r[b], nc = c[b] < r[b] ? c[b] : r[b];
     max_rc = std::max(max_rc, (size_t)(nr * nc + nc * nc));
     max_nm = std::max(max_nm, (size_t)(n > m ? n : m));
@@ -770,22 +791,29 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     P.I = reinterpret_cast<int32_t*>(base + o.I);
     P.C = q(o.C, P.m, P.c); P.R = q(o.R, P.r, P.n); P.W = q(o.W, P.r, P.c);
     P.U = q(o.U, P.c, P.r); P.T = q(o.T, P.c, P.n);
+    if (refined) {
+      for (int t = 0; t < 4; ++t) P.U64.p[t] = base + o.U64 + (size_t)t * P.c * P.r * 8;
+      P.U64.rows = P.c; P.U64.cols = P.r; P.U64.ld = P.r; P.U64.dtype = QMCUR_F64;
+    }
     P.out3 = reinterpret_cast<double*>(base + o.o3);
     P.info = reinterpret_cast<int32_t*>(base + o.info);
   }
   if (subspace) {
-    // one subspace program per problem over its own carve of one arena;
-    // CTA order: the most work (r c k + max(r, c) k^2) first
-    p->subspace = true;
+    // one subspace program (or refined program's arguments) per problem over
+    // its own carve of one arena; CTA order: the most work
+    // (r c k + max(r, c) k^2) first
+    p->subspace = !refined;
+    p->refined = refined;
     std::vector<size_t> woff(count);
     size_t wtotal = 0;
     for (int b = 0; b < count; ++b) {
       const int64_t nmin = c[b] < r[b] ? c[b] : r[b];
       const int64_t k = rank_cap[b] < nmin ? rank_cap[b] : nmin;
       woff[b] = wtotal;
-      wtotal += align_up(pinv_each_ws_bytes(r[b], c[b], k), 256);
+      wtotal += align_up(refined ? refine_each_ws_bytes(r[b], c[b], k)
+                                 : pinv_each_ws_bytes(r[b], c[b], k), 256);
     }
-    const size_t pb = pinv_each_prog_bytes();
+    const size_t pb = refined ? refine_each_args_bytes() : pinv_each_prog_bytes();
     std::vector<char> hprogs((size_t)count * pb);
     std::vector<double> work(count);
     if (cudaMalloc(&p->pinv_arena, wtotal) != cudaSuccess ||
@@ -804,10 +832,17 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
       };
       qmcur_qmat Wq = toq(P.W), Uq = toq(P.U);
       int k = 0;
-      const qmcur_status s = pinv_each_build(
-          &Wq, P.rank_cap, &Uq, P.info, opts->seed ^ (0x9e3779b97f4a7c15ull + (uint64_t)b),
-          static_cast<char*>(p->pinv_arena) + woff[b], wtotal - woff[b], dev_status,
-          hprogs.data() + (size_t)b * pb, &k);
+      const uint64_t seed_b = opts->seed ^ (0x9e3779b97f4a7c15ull + (uint64_t)b);
+      char* ws_b = static_cast<char*>(p->pinv_arena) + woff[b];
+      qmcur_status s;
+      if (refined) {
+        qmcur_qmat U64q = toq(P.U64);
+        s = refine_each_build(&Wq, P.rank_cap, opts->max_sweeps, &U64q, &Uq, P.info, P.info + 2,
+                              seed_b, ws_b, wtotal - woff[b], hprogs.data() + (size_t)b * pb, &k);
+      } else {
+        s = pinv_each_build(&Wq, P.rank_cap, &Uq, P.info, seed_b, ws_b, wtotal - woff[b],
+                            dev_status, hprogs.data() + (size_t)b * pb, &k);
+      }
       if (s != QMCUR_OK) { free_plan(p); return s; }
       p->kmax = std::max(p->kmax, k);
       const double rr = (double)P.r, cc = (double)P.c;
@@ -1048,6 +1083,9 @@ qmcur_status qmcur_batch_copy(const void* plan, int32_t index, int32_t what, voi
     case 7: src = P.U.p[0]; bytes = 16 * (size_t)P.c * P.r; break;
     case 8: src = P.out3; bytes = 24; break;
     case 9: src = P.info; bytes = 12; break;
+    case 10:   // U in FP64: the refined core only
+      if (!p->refined) return QMCUR_ERR_INVALID_ARG;
+      src = P.U64.p[0]; bytes = 32 * (size_t)P.c * P.r; break;
     default: return QMCUR_ERR_INVALID_ARG;
   }
   if (dst_bytes < bytes) return QMCUR_ERR_INVALID_ARG;

@@ -202,6 +202,7 @@ struct RfJob {
   int norm;
   int upper;
   float scale;          // exact power of two applied to the stored result (0: none)
+  QPtr Zout2;           // a second copy of the stored result (p[0] null: none)
   // filled by rf_plan
   int tm, tn;           // tile rows, tile columns
   int slices;           // k-slices of a full-depth tile
@@ -217,6 +218,7 @@ struct RfArgs {
   // float-float workspaces
   QPtr P[2], Y, Z, Zp, X, M, E, Mp, Gp, G1, G2, E2, Q1, Q2, T1, T2, V;
   QPtr U;              // c x r output
+  QPtr U2;             // optional second copy of U (p[0] null: none), e.g. F32 beside F64
   QFF* part;           // 2 x kRfMaxWorkers x kRfTileThreads partials of split tiles
   unsigned* cnt;       // kRfMaxWorkers split-tile arrival counts, then the norm fold's
   double* normpart;    // kRfMaxTiles x 2 tile norm partials
@@ -226,7 +228,7 @@ struct RfArgs {
   unsigned* wmax;      // bits of max |W_ij| over the planes (atomicMax, zeroed)
   int32_t* status;
   int32_t* rank_out;
-  int workers;         // gridDim.x * kRfWorkers
+  int workers;         // tile workers of the (virtual) grid: CTAs x kRfWorkers
 };
 
 // Shared memory: the tile workers' double-buffered operand slices, or the
@@ -404,6 +406,7 @@ __device__ void rf_epilogue(const RfJob& j, int tm, int tn, int tid, const QFF& 
     v.l = make_float4(v.l.x * j.scale, v.l.y * j.scale, v.l.z * j.scale, v.l.w * j.scale);
   }
   stff(j.Zout, (int64_t)i * j.Zout.ld + c, v);
+  if (j.Zout2.p[0] != nullptr) stff(j.Zout2, (int64_t)i * j.Zout2.ld + c, v);
 }
 
 // Sum of a worker's 256 values in a fixed order (warp shuffles, then warps).
@@ -468,14 +471,14 @@ __device__ __forceinline__ int rf_owner(int x, int nw, int total) {
 }
 
 // One step of up to three independent products (at most one with `norm`).
-// The workers of CTA b are workers kRfWorkers b .. kRfWorkers (b + 1) - 1,
-// so that small steps spread over the SMs.  A run that covers a tile only in part leaves its
+// The workers of CTA vb of the virtual grid are workers kRfWorkers vb ..
+// kRfWorkers (vb + 1) - 1, so that small steps spread over the SMs.  A run that covers a tile only in part leaves its
 // partial in the slot of its first tile (2w) or of its last (2w + 1); the
 // tile's counter is that of the worker holding its first unit (no other
 // split tile starts in that worker's run), and the last run to arrive sums
 // the partials in run order.
 __device__ __noinline__ void rf_gemm_step(const RfArgs& a, RfJob* jobs, int njobs, double* norm_out,
-                             unsigned char* smem) {
+                                          unsigned char* smem, int vb) {
   __shared__ int last_sh[kRfWorkers];
   __shared__ double red_sh[kRfWorkers][kRfTileThreads / 32];
   const int worker = threadIdx.x / kRfTileThreads, wtid = threadIdx.x % kRfTileThreads;
@@ -483,7 +486,7 @@ __device__ __noinline__ void rf_gemm_step(const RfArgs& a, RfJob* jobs, int njob
   const int bar_id = 1 + worker;
   const int total = rf_plan(jobs, njobs);
   const int nw = a.workers;
-  const int w = kRfWorkers * blockIdx.x + worker;
+  const int w = kRfWorkers * vb + worker;
   const int u_begin = rf_start(w, nw, total), u_end = rf_start(w + 1, nw, total);
   for (int u = u_begin; u < u_end;) {
     int q = 0;
@@ -533,7 +536,7 @@ __device__ __noinline__ void rf_gemm_step(const RfArgs& a, RfJob* jobs, int njob
         a.normpart[2 * tile] = sd;
         a.normpart[2 * tile + 1] = sz;
         __threadfence();
-        last_sh[worker] = atomicAdd(a.cnt + kRfMaxWorkers, 1u) == (unsigned)(j.tm * j.tn - 1);
+        last_sh[worker] = atomicAdd(a.cnt + nw, 1u) == (unsigned)(j.tm * j.tn - 1);
       }
       worker_bar(bar_id);
       if (last_sh[worker]) {   // the last tile folds them all: strided, then in thread order
@@ -548,7 +551,7 @@ __device__ __noinline__ void rf_gemm_step(const RfArgs& a, RfJob* jobs, int njob
         if (wtid == 0) {
           norm_out[0] = fd;
           norm_out[1] = fz;
-          a.cnt[kRfMaxWorkers] = 0u;
+          a.cnt[nw] = 0u;
         }
       }
     }
@@ -709,7 +712,13 @@ __device__ __forceinline__ RfJob job(const QPtr& X, int xh, const QPtr& Y, int y
   return j;
 }
 
-__device__ __forceinline__ bool rf_sync(const RfArgs& a, unsigned& target) {
+// The barrier between steps: the grid's, or the CTA's own when the virtual
+// grid is one CTA (vg == 1: one problem per CTA).
+__device__ __forceinline__ bool rf_sync(const RfArgs& a, int vg, unsigned& target) {
+  if (vg == 1) {
+    __syncthreads();   // the CTA's own global writes, then its reads
+    return true;
+  }
   return grid_sync(a.bar, a.status, target);
 }
 
@@ -740,8 +749,9 @@ struct StopState {
 // (about 2^-46 sqrt(k) relative): values above 32 times it are reliable.
 // Below it, rho is extrapolated from the last reliable value at the
 // contraction seen between two reliable values; with only one reliable value,
-// the fall from it onto the floor bounds the contraction.  Iteration 1 starts
-// from the random block, whose rho means nothing.
+// the fall from it onto the floor bounds the contraction, applied once per
+// iteration since that value.  Iteration 1 starts from the random block, whose
+// rho means nothing.
 __device__ __forceinline__ bool stop_now(StopState& st, int s, double nd, double nz, double kap2,
                                          int k) {
   if (s < 2 || !(nz > 0.0)) return false;
@@ -759,8 +769,10 @@ __device__ __forceinline__ bool stop_now(StopState& st, int s, double nd, double
     est = st.prev_rho * pow(st.contr, (double)(s - st.prev_s));
     contr = st.contr;
   } else if (st.prev_s > 0) {
-    est = rho;
-    contr = fmin(reliable / st.prev_rho, 0.999);   // at most the fall onto the floor
+    // one reliable value, then the floor: the fall onto the floor bounds the
+    // contraction, and every further iteration at the floor applies it again
+    contr = fmin(reliable / st.prev_rho, 0.999);
+    est = fmin(rho, st.prev_rho * pow(contr, (double)(s - st.prev_s)));
   } else {
     // at the floor with no history: W^H W leaves span(P) invariant to the
     // products' accuracy; twice in a row settles it
@@ -771,12 +783,18 @@ __device__ __forceinline__ bool stop_now(StopState& st, int s, double nd, double
   return contr > 0.0 && angle * contr <= kAngleTol;
 }
 
-__global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_constant__ RfArgs a) {
-  extern __shared__ __align__(16) unsigned char smr[];
+// The whole program over a virtual grid of vg CTAs, this one vb: the
+// single-problem kernel passes (blockIdx.x, gridDim.x) and grid barriers;
+// the batched kernel passes (0, 1) and CTA barriers.
+__device__ __forceinline__ void rf_program(const RfArgs& a, int vb, int vg, unsigned char* smr) {
   __shared__ int stop_sh;
-  const int vb = blockIdx.x, vg = gridDim.x;
   const int r = a.r, c = a.c, k = a.k;
   unsigned target = 0;
+  if (vg == 1) {   // one CTA owns the counters: clear them itself
+    for (int i = threadIdx.x; i <= a.workers; i += blockDim.x) a.cnt[i] = 0u;
+    if (threadIdx.x == 0) *a.wmax = 0u;
+    __syncthreads();
+  }
   // The pairs keep FP32's exponent range and Z = W^H W P scales as |W|^2, so
   // W is scaled by an exact power of two 2^-e to max |W_ij| in [1, 2); U is
   // scaled back by 2^-e in its store ((2^-e W)^+ = 2^e W^+).
@@ -792,7 +810,7 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(a.wmax, __float_as_uint(mx));
   }
-  if (!rf_sync(a, target)) return;
+  if (!rf_sync(a, vg, target)) return;
   const float wm = __uint_as_float(__ldcg(a.wmax));
   if (!isfinite(wm)) {
     if (vb == 0 && threadIdx.x == 0) set_status(a.status, QMCUR_ERR_NONFINITE);
@@ -821,11 +839,11 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
       stff(a.P[0], (f / k) * a.P[0].ld + f % k, v);
     }
   }
-  if (!rf_sync(a, target)) return;
+  if (!rf_sync(a, vg, target)) return;
   RfJob jb[3];
   jb[0] = job(a.Wf, 0, a.P[0], 0, a.Y, r, k, c);   // Y = W P0
-  rf_gemm_step(a, jb, 1, nullptr, smr);
-  if (!rf_sync(a, target)) return;
+  rf_gemm_step(a, jb, 1, nullptr, smr, vb);
+  if (!rf_sync(a, vg, target)) return;
   StopState st{0.0, 0, 0.0, 0};
   int cur = 0, s = 1;
   bool converged = false;
@@ -836,23 +854,23 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
     jb[1] = job(a.Y, 1, a.Y, 0, a.M, k, k, r);    // M = Y^H Y
     jb[2] = job(P, 1, P, 0, a.E, k, k, c);        // E = P^H P - I
     jb[2].minus_eye = 1;
-    rf_gemm_step(a, jb, 3, nullptr, smr);
-    if (!rf_sync(a, target)) return;
+    rf_gemm_step(a, jb, 3, nullptr, smr, vb);
+    if (!rf_sync(a, vg, target)) return;
     // Z' = Z R_Y^-1 with R_Y = chol32(M); then M' = M - E M on the tile workers
     rf_solve_step(a, a.M, a.Z, a.Zp, c, nullptr, nullptr, 0, a.kap2 + s, vb, vg, smr);
     jb[0] = job(a.E, 0, a.M, 0, a.Mp, k, k, k);
     jb[0].Zin = a.M;
     jb[0].neg = 1;
     jb[0].add_in = 1;
-    rf_gemm_step(a, jb, 1, nullptr, smr);
-    if (!rf_sync(a, target)) return;
+    rf_gemm_step(a, jb, 1, nullptr, smr, vb);
+    if (!rf_sync(a, vg, target)) return;
     jb[0] = job(a.Zp, 1, a.Zp, 0, a.Gp, k, k, c);   // G' = Z'^H Z'
     jb[0].upper = 1;
     jb[1] = job(a.Wf, 0, a.Zp, 0, a.X, r, k, c);    // X = W Z'
     jb[2] = job(P, 0, a.Mp, 0, a.Z, c, k, k);       // ||Z - P M'||, ||Z||
     jb[2].norm = 1;
-    rf_gemm_step(a, jb, 3, a.norms + 2 * s, smr);
-    if (!rf_sync(a, target)) return;
+    rf_gemm_step(a, jb, 3, a.norms + 2 * s, smr, vb);
+    if (!rf_sync(a, vg, target)) return;
     if (threadIdx.x == 0)
       stop_sh = stop_now(st, s, __ldcg(a.norms + 2 * s), __ldcg(a.norms + 2 * s + 1),
                          __ldcg(a.kap2 + s), k);
@@ -860,7 +878,7 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
     converged = stop_sh != 0;
     // R' = chol32(G'):  P <- Z' R'^-1,  Y <- X R'^-1 (= W P)
     rf_solve_step(a, a.Gp, a.Zp, Pn, c, &a.X, &a.Y, r, nullptr, vb, vg, smr);
-    if (!rf_sync(a, target)) return;
+    if (!rf_sync(a, vg, target)) return;
     cur ^= 1;
     if (converged) break;
   }
@@ -868,33 +886,61 @@ __global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_cons
   // U = P (W P)^+ by CholeskyQR2 with FP32 factors and the E2 correction
   jb[0] = job(a.Y, 1, a.Y, 0, a.G1, k, k, r);
   jb[0].upper = 1;
-  rf_gemm_step(a, jb, 1, nullptr, smr);
-  if (!rf_sync(a, target)) return;
+  rf_gemm_step(a, jb, 1, nullptr, smr, vb);
+  if (!rf_sync(a, vg, target)) return;
   rf_solve_step(a, a.G1, a.Y, a.Q1, r, &P, &a.T1, c, nullptr, vb, vg, smr);
-  if (!rf_sync(a, target)) return;
+  if (!rf_sync(a, vg, target)) return;
   jb[0] = job(a.Q1, 1, a.Q1, 0, a.G2, k, k, r);
   jb[0].upper = 1;
-  rf_gemm_step(a, jb, 1, nullptr, smr);
-  if (!rf_sync(a, target)) return;
+  rf_gemm_step(a, jb, 1, nullptr, smr, vb);
+  if (!rf_sync(a, vg, target)) return;
   rf_solve_step(a, a.G2, a.Q1, a.Q2, r, &a.T1, &a.T2, c, nullptr, vb, vg, smr);
-  if (!rf_sync(a, target)) return;
+  if (!rf_sync(a, vg, target)) return;
   jb[0] = job(a.Q2, 1, a.Q2, 0, a.E2, k, k, r);
   jb[0].minus_eye = 1;
-  rf_gemm_step(a, jb, 1, nullptr, smr);
-  if (!rf_sync(a, target)) return;
+  rf_gemm_step(a, jb, 1, nullptr, smr, vb);
+  if (!rf_sync(a, vg, target)) return;
   jb[0] = job(a.T2, 0, a.E2, 0, a.V, c, k, k);   // V = T2 - T2 E2
   jb[0].Zin = a.T2;
   jb[0].neg = 1;
   jb[0].add_in = 1;
-  rf_gemm_step(a, jb, 1, nullptr, smr);
-  if (!rf_sync(a, target)) return;
+  rf_gemm_step(a, jb, 1, nullptr, smr, vb);
+  if (!rf_sync(a, vg, target)) return;
   jb[0] = job(a.V, 0, a.Q2, 1, a.U, c, r, k);    // U = V Q2^H, back to W's scale
   jb[0].scale = wsc;
-  rf_gemm_step(a, jb, 1, nullptr, smr);
+  jb[0].Zout2 = a.U2;
+  rf_gemm_step(a, jb, 1, nullptr, smr, vb);
   if (vb == 0 && threadIdx.x == 0) {
     const int iters = s <= a.max_iter ? s : a.max_iter;
     if (a.rank_out != nullptr) { a.rank_out[0] = k; a.rank_out[1] = iters; }
     if (!converged) set_status(a.status, QMCUR_ERR_NO_CONVERGENCE);
+  }
+}
+
+__global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine(const __grid_constant__ RfArgs a) {
+  extern __shared__ __align__(16) unsigned char smr[];
+  rf_program(a, (int)blockIdx.x, (int)gridDim.x, smr);
+}
+
+// One problem per CTA: CTA b runs the program args[order[b]] alone, its
+// arguments copied to shared memory (the order puts the largest problems
+// first, so that the small ones fill in behind them).  Its status goes to
+// the problem's own word, cleared here, and from there to the batch's.
+__global__ void __launch_bounds__(kRfThreads, 1) k_pinv_refine_each(const RfArgs* __restrict__ args,
+                                                                    const int* __restrict__ order,
+                                                                    int32_t* batch_status) {
+  extern __shared__ __align__(16) unsigned char smr[];
+  __shared__ RfArgs sa;
+  if (threadIdx.x == 0) {
+    sa = args[order[blockIdx.x]];
+    *sa.status = 0;
+  }
+  __syncthreads();
+  rf_program(sa, 0, 1, smr);
+  __syncthreads();
+  if (threadIdx.x == 0 && batch_status != nullptr) {
+    const int32_t e = *(volatile int32_t*)sa.status;
+    if (e != 0) set_status(batch_status, e);
   }
 }
 
@@ -915,7 +961,10 @@ struct RfWs {
   size_t zero_bytes;
 };
 
-RfWs carve_refine(Carve& cv, int64_t r, int64_t c, int64_t k) {
+// Workspace of one program: the float-float matrices, the split-tile
+// partials and counters of `workers` tile workers, and the tile partials of
+// the norm product (c x k).
+RfWs carve_refine(Carve& cv, int64_t r, int64_t c, int64_t k, int workers = kRfMaxWorkers) {
   RfWs w{};
   RfArgs& a = w.a;
   a.Wf = carve_ff(cv, r, c);
@@ -937,16 +986,27 @@ RfWs carve_refine(Carve& cv, int64_t r, int64_t c, int64_t k) {
   a.T1 = carve_ff(cv, c, k);
   a.T2 = carve_ff(cv, c, k);
   a.V = carve_ff(cv, c, k);
-  a.part = cv.take<QFF>((size_t)2 * kRfMaxWorkers * kRfTileThreads);
-  a.normpart = cv.take<double>((size_t)2 * kRfMaxTiles);
+  const int64_t norm_tiles = ((c + kRfTS - 1) / kRfTS) * ((k + kRfTS - 1) / kRfTS);
+  a.part = cv.take<QFF>((size_t)2 * workers * kRfTileThreads);
+  a.normpart = cv.take<double>((size_t)2 * norm_tiles);
   a.norms = cv.take<double>((size_t)2 * (kRfMaxIter + 1));
   a.kap2 = cv.take<double>((size_t)(kRfMaxIter + 1));
-  w.zero_base = cv.take<unsigned>((size_t)(kRfMaxWorkers + 8));
-  w.zero_bytes = (size_t)(kRfMaxWorkers + 8) * sizeof(unsigned);
-  a.cnt = w.zero_base;                     // kRfMaxWorkers + 1 counters
-  a.wmax = w.zero_base + kRfMaxWorkers + 2;
-  a.bar = w.zero_base + kRfMaxWorkers + 4;
+  w.zero_base = cv.take<unsigned>((size_t)(workers + 8));
+  w.zero_bytes = (size_t)(workers + 8) * sizeof(unsigned);
+  a.cnt = w.zero_base;                     // workers + 1 counters
+  a.wmax = w.zero_base + workers + 2;
+  a.bar = w.zero_base + workers + 4;
   return w;
+}
+
+// The caller's W and U as the program reads and writes them.
+void rf_bind(RfArgs& a, const qmcur_qmat* W, const qmcur_qmat* U) {
+  for (int t = 0; t < 4; ++t) a.W.p[t] = W->plane[t];
+  a.W.ld = W->ld;
+  a.W.dtype = W->dtype;
+  for (int t = 0; t < 4; ++t) a.U.p[t] = U->plane[t];
+  a.U.ld = U->ld;
+  a.U.dtype = U->dtype;
 }
 
 }  // namespace
@@ -997,12 +1057,7 @@ qmcur_status launch_pinv_refine(const qmcur_qmat* W, double rcond, int32_t rank_
   int grid = cta_cap(sms);
   if (grid > kRfMaxGrid) grid = kRfMaxGrid;
   RfArgs& a = w.a;
-  for (int t = 0; t < 4; ++t) a.W.p[t] = W->plane[t];
-  a.W.ld = W->ld;
-  a.W.dtype = W->dtype;
-  for (int t = 0; t < 4; ++t) a.U.p[t] = U->plane[t];
-  a.U.ld = U->ld;
-  a.U.dtype = U->dtype;
+  rf_bind(a, W, U);
   a.r = (int)r;
   a.c = (int)c;
   a.k = k;
@@ -1015,6 +1070,71 @@ qmcur_status launch_pinv_refine(const qmcur_qmat* W, double rcond, int32_t rank_
   void* args[] = {(void*)&a};
   return cuda_ok(cudaLaunchCooperativeKernel((const void*)k_pinv_refine, dim3(grid),
                                              dim3(kRfThreads), args, smem, st));
+}
+
+// ---------------------------------------------------------------------------
+// One problem per CTA (the batched path): each problem's arguments, built on
+// the host over its own carve of the batch's arena with the tile workers of
+// one CTA; CTA b runs the problem order[b].
+
+size_t refine_each_ws_bytes(int64_t r, int64_t c, int64_t k) {
+  Carve cv(nullptr, 0);
+  carve_refine(cv, r, c, k, kRfWorkers);
+  return cv.off;
+}
+
+size_t refine_each_args_bytes() { return sizeof(RfArgs); }
+
+// W r x c (F32 or F64), U c x r (F64), U2 (c x r F32, or NULL); status is the
+// problem's own status word, rank_out its {k, iterations}.
+qmcur_status refine_each_build(const qmcur_qmat* W, int32_t rank_cap, int32_t max_iter,
+                               qmcur_qmat* U, qmcur_qmat* U2, int32_t* rank_out, int32_t* status,
+                               uint64_t seed, void* ws, size_t ws_bytes, void* args_out,
+                               int* k_out) {
+  if (!valid_qmat(W) || !valid_qmat(U) || (U2 != nullptr && !valid_qmat(U2)) || status == nullptr)
+    return QMCUR_ERR_INVALID_ARG;
+  const int64_t r = W->rows, c = W->cols;
+  if (U->rows != c || U->cols != r || (U2 != nullptr && (U2->rows != c || U2->cols != r)))
+    return QMCUR_ERR_INVALID_ARG;
+  const int64_t nmin = r < c ? r : c;
+  if (rank_cap < 1) return QMCUR_ERR_UNSUPPORTED;
+  const int k = (int)(rank_cap < nmin ? rank_cap : nmin);
+  if (k > kSmallCholMax || r > kRfMaxDim || c > kRfMaxDim) return QMCUR_ERR_UNSUPPORTED;
+  if (max_iter <= 0) max_iter = 30;
+  if (max_iter > kRfMaxIter) max_iter = kRfMaxIter;
+  Carve cv(ws, ws_bytes);
+  RfWs w = carve_refine(cv, r, c, k, kRfWorkers);
+  if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
+  RfArgs& a = w.a;
+  rf_bind(a, W, U);
+  if (U2 != nullptr) {
+    for (int t = 0; t < 4; ++t) a.U2.p[t] = U2->plane[t];
+    a.U2.ld = U2->ld;
+    a.U2.dtype = U2->dtype;
+  }
+  a.r = (int)r;
+  a.c = (int)c;
+  a.k = k;
+  a.max_iter = max_iter;
+  a.seed = seed;
+  a.status = status;
+  a.rank_out = rank_out;
+  a.workers = kRfWorkers;
+  *static_cast<RfArgs*>(args_out) = a;
+  *k_out = k;
+  return QMCUR_OK;
+}
+
+qmcur_status refine_each_launch(const void* dargs, const int* dorder, int count, int kmax,
+                                int32_t* batch_status, cudaStream_t st) {
+  if (count < 1 || kmax < 1 || kmax > kSmallCholMax) return QMCUR_ERR_INVALID_ARG;
+  const size_t smem = rf_smem(kmax);
+  if (cudaFuncSetAttribute(k_pinv_refine_each, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  k_pinv_refine_each<<<count, kRfThreads, smem, st>>>(static_cast<const RfArgs*>(dargs), dorder,
+                                                       batch_status);
+  return cuda_ok(cudaGetLastError());
 }
 
 }  // namespace qmcur

@@ -267,7 +267,7 @@ class Batch:
     WHAT = {"col_p": (0, torch.float64), "row_p": (1, torch.float64), "J": (2, torch.int32),
             "I": (3, torch.int32), "C": (4, torch.float32), "R": (5, torch.float32),
             "W": (6, torch.float32), "U": (7, torch.float32), "out3": (8, torch.float64),
-            "info": (9, torch.int32)}
+            "info": (9, torch.int32), "U64": (10, torch.float64)}
 
     def __init__(self, As, cs, rs, rank_caps=None, sampler=SAMPLER_NORM, seed=0, rcond=1e-10,
                  max_sweeps=0, stream=None, pinv_method=PINV_JACOBI_FP64, prec=PREC_FP32):
@@ -301,7 +301,8 @@ class Batch:
         code, dt = self.WHAT[what]
         m, n, c, r = self.shapes[b]
         shape = {"col_p": (n,), "row_p": (m,), "J": (c,), "I": (r,), "C": (4, m, c),
-                 "R": (4, r, n), "W": (4, r, c), "U": (4, c, r), "out3": (3,), "info": (3,)}[what]
+                 "R": (4, r, n), "W": (4, r, c), "U": (4, c, r), "out3": (3,), "info": (3,),
+                 "U64": (4, c, r)}[what]
         out = torch.empty(shape, dtype=dt, device=self.As[0].device)
         _check(lib().qmcur_batch_copy(self.handle, b, code, _ptr(out),
                                       out.numel() * out.element_size(), _stream(stream)),

@@ -6,8 +6,11 @@ FP64); index sets and gathers bit-exact (the oracle sampler is fed the
 library's probabilities, stream_id = problem index); U from the FP32
 one-sided Jacobi, a backward-stable QSVD, within 8 c u32 kappa(W_k) of the
 FP64 oracle, or from the FP32 subspace core (one CTA per problem) within its
-own bound 64 u32 kappa^2; ranks equal; the relative residual within 1e-5 of
-the oracle's evaluated on the same U.
+own bound 64 u32 kappa^2, or from the FP64-accurate refined core (one CTA per
+problem) in FP64 within 1e-12 kappa(W_k) (the FP64 path's 1e-12, scaled by
+the condition of the kept part), its FP32 copy being that FP64 U rounded;
+ranks equal; the relative residual within 1e-5 of the oracle's evaluated on
+the same U.
 """
 import numpy as np
 import pytest
@@ -21,8 +24,9 @@ from gpu_util import U32, dev, host, rel_fro
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module", params=[Q.PINV_JACOBI_FP64, Q.PINV_SUBSPACE_FP32],
-                ids=["jacobi", "subspace"])
+@pytest.fixture(scope="module",
+                params=[Q.PINV_JACOBI_FP64, Q.PINV_SUBSPACE_FP32, Q.PINV_REFINED_FP64],
+                ids=["jacobi", "subspace", "refined"])
 def batch(request):
     probs = synth.batch_problems(count=24, seed=3)
     As = [dev(p["X"]) for p in probs]
@@ -55,6 +59,11 @@ def test_batch_matches_oracle(batch):
         info = host(B.get(b, "info"))
         assert info[0] == ko and info[2] == 0
         kap = so[0] / so[ko - 1]
+        if method == Q.PINV_REFINED_FP64:
+            U64 = host(B.get(b, "U64"))
+            assert np.array_equal(host(B.get(b, "U")), U64.astype(np.float32))
+            assert 1 <= info[1] <= 30
+            assert rel_fro(U64, Uo) < 1e-12 * max(1.0, kap), (b, rel_fro(U64, Uo), kap)
         tol = 8 * p["c"] * U32 * kap if method == Q.PINV_JACOBI_FP64 else 64 * U32 * kap ** 2
         assert rel_fro(U, Uo) < tol, (b, rel_fro(U, Uo), kap)
         rel = host(B.get(b, "out3"))[0]

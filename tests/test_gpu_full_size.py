@@ -10,6 +10,8 @@ Z = C (U R), and, for the batch, every 32nd problem.  Checked in full:
   4096 x 4096 colour field, whose spectrum has no gap at the rank cap
   (sigma_101 / sigma_100 ~ 0.97), the FP64 Jacobi core within the gap-scaled
   bound 64 c u64 sigma_1 / (sigma_100 - sigma_101);
+* the batch's U (every 32nd problem): the refined core's FP64 U within
+  1e-12 kappa(W_k), the FP32 cores within their own bounds;
 * the fused relative residual against the oracle's own decomposition
   C W^+ R in FP64 (the oracle's U, not the library's), within 1e-5;
 * the same residual against the oracle's C U R with the library's U rounded
@@ -152,11 +154,14 @@ def test_color4096_full_size():
 
 @pytest.mark.parametrize("method,prec", [(Q.PINV_SUBSPACE_FP32, Q.PREC_FP32),
                                          (Q.PINV_JACOBI_FP64, Q.PREC_FP32),
-                                         (Q.PINV_SUBSPACE_FP32, Q.PREC_BF16_MIXED)],
-                         ids=["subspace", "jacobi", "subspace-bf16"])
+                                         (Q.PINV_SUBSPACE_FP32, Q.PREC_BF16_MIXED),
+                                         (Q.PINV_REFINED_FP64, Q.PREC_BF16_MIXED),
+                                         (Q.PINV_REFINED_FP64, Q.PREC_FP32)],
+                         ids=["subspace", "jacobi", "subspace-bf16", "refined-bf16",
+                              "refined"])
 def test_batch512_full_size(method, prec):
-    # the subspace core is the benchmarked one, with the FP32 and the split
-    # (grouped tcgen05) Z = C T
+    # the refined core with the split (grouped tcgen05) Z = C T is the
+    # benchmarked plan; the FP32 plans time beside it
     probs = synth.batch_problems(count=512, seed=3)
     As = [dev(p["X"]) for p in probs]
     B = Q.Batch(As, [p["c"] for p in probs], [p["r"] for p in probs],
@@ -164,7 +169,9 @@ def test_batch512_full_size(method, prec):
                 pinv_method=method, prec=prec)
     B.run()
     torch.cuda.synchronize()
-    assert int(B.status.item()) == 0
+    bad = [(b, host(B.get(b, "info")).tolist()) for b in range(len(probs))
+           if host(B.get(b, "info"))[2] != 0]
+    assert int(B.status.item()) == 0 and not bad, (int(B.status.item()), bad[:8])
     for b, p in enumerate(probs):
         info = host(B.get(b, "info"))
         assert info[2] == 0 and info[0] == p["rank"], (b, info)
@@ -182,6 +189,9 @@ def test_batch512_full_size(method, prec):
         U = host(B.get(b, "U")).astype(np.float64)
         Uo, ko, so = O.pinv_truncated(Wo, 1e-10, p["rank"])
         kap = so[0] / so[ko - 1]
+        if method == Q.PINV_REFINED_FP64:
+            U64 = host(B.get(b, "U64"))
+            assert rel_fro(U64, Uo) < 1e-12 * max(1.0, kap), (b, rel_fro(U64, Uo), kap)
         tol = 8 * p["c"] * U32 * kap if method == Q.PINV_JACOBI_FP64 else 64 * U32 * kap ** 2
         assert rel_fro(U, Uo) < tol, (b, kap)
         rel_o = O.residual(A64, O.reconstruct(Co, U, Ro))[0]
