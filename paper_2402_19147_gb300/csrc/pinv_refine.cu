@@ -201,6 +201,7 @@ struct RfJob {
   int minus_eye;
   int norm;
   int upper;
+  int fp32;             // plain FP32 products of the leading parts (stored with l = 0)
   float scale;          // exact power of two applied to the stored result (0: none)
   QPtr Zout2;           // a second copy of the stored result (p[0] null: none)
   // filled by rf_plan
@@ -306,12 +307,27 @@ __device__ __forceinline__ void ff_qmac(float S[4], float C[4], const QFF& x, co
                            bl.y, a.w, al.w, b.x, bl.x);
 }
 
+// S += x y in plain FP32 on the leading parts (the Hamilton product, Sec. 2.2)
+__device__ __forceinline__ void f32_qmac(float S[4], const QFF& x, const QFF& y) {
+  const float4 a = x.h, b = y.h;
+  S[0] = __fmaf_rn(a.x, b.x, S[0]); S[0] = __fmaf_rn(-a.y, b.y, S[0]);
+  S[0] = __fmaf_rn(-a.z, b.z, S[0]); S[0] = __fmaf_rn(-a.w, b.w, S[0]);
+  S[1] = __fmaf_rn(a.x, b.y, S[1]); S[1] = __fmaf_rn(a.y, b.x, S[1]);
+  S[1] = __fmaf_rn(a.z, b.w, S[1]); S[1] = __fmaf_rn(-a.w, b.z, S[1]);
+  S[2] = __fmaf_rn(a.x, b.z, S[2]); S[2] = __fmaf_rn(-a.y, b.w, S[2]);
+  S[2] = __fmaf_rn(a.z, b.x, S[2]); S[2] = __fmaf_rn(a.w, b.y, S[2]);
+  S[3] = __fmaf_rn(a.x, b.w, S[3]); S[3] = __fmaf_rn(a.y, b.z, S[3]);
+  S[3] = __fmaf_rn(-a.z, b.y, S[3]); S[3] = __fmaf_rn(a.w, b.x, S[3]);
+}
+
 // Entry (ty, tx) = (tid / 8, tid % 8) of tile (tm, tn), accumulated over
 // [kb, ke) by one worker; the thread carries the four components (four
 // independent dependency chains).  Slices are double-buffered (one barrier
 // per slice); each thread loads two entries of the X slice and two of the Y
 // slice, laid out so that consecutive threads read consecutive addresses of
 // the operand's storage.
+// With FF false the products are plain FP32 on the leading parts.
+template <bool FF>
 __device__ __noinline__ QFF rf_tile_acc(const RfOp op, int tm, int tn, int kb, int ke, QFF* sm,
                                         int tid, int bar_id) {
   QFF (*xs)[kRfTS][kRfBK + 1] = reinterpret_cast<QFF (*)[kRfTS][kRfBK + 1]>(sm);
@@ -360,7 +376,10 @@ __device__ __noinline__ QFF rf_tile_acc(const RfOp op, int tm, int tn, int kb, i
     const QFF* xr = xs[b][ty];
     const QFF (*yr)[kRfTS + 1] = ys[b];
     const int lend = ke - k0 < kRfBK ? ke - k0 : kRfBK;
-    if (lend == kRfBK) {
+    if (!FF) {
+#pragma unroll 4
+      for (int l = 0; l < lend; ++l) f32_qmac(S, xr[l], yr[l][tx]);
+    } else if (lend == kRfBK) {
 #pragma unroll 2
       for (int l = 0; l < kRfBK; ++l) ff_qmac(S, C, xr[l], yr[l][tx]);
     } else {
@@ -499,7 +518,8 @@ __device__ __noinline__ void rf_gemm_step(const RfArgs& a, RfJob* jobs, int njob
     const int s_end = ns < s + (u_end - u) ? ns : s + (u_end - u);
     const int ke = s_end * kRfBK < j.K ? s_end * kRfBK : j.K;
     const RfOp op{j.X, j.Y, j.M, j.N, j.xh, j.yh};
-    QFF acc = rf_tile_acc(op, tm, tn, s * kRfBK, ke, wsm, wtid, bar_id);
+    QFF acc = j.fp32 ? rf_tile_acc<false>(op, tm, tn, s * kRfBK, ke, wsm, wtid, bar_id)
+                     : rf_tile_acc<true>(op, tm, tn, s * kRfBK, ke, wsm, wtid, bar_id);
     u += s_end - s;
     if (s > 0 || s_end < ns) {   // a tile split over several runs
       // the runs holding the tile's units, in k order: from the owner of a
@@ -842,6 +862,7 @@ __device__ __forceinline__ void rf_program(const RfArgs& a, int vb, int vg, unsi
   if (!rf_sync(a, vg, target)) return;
   RfJob jb[3];
   jb[0] = job(a.Wf, 0, a.P[0], 0, a.Y, r, k, c);   // Y = W P0
+  jb[0].fp32 = 1;
   rf_gemm_step(a, jb, 1, nullptr, smr, vb);
   if (!rf_sync(a, vg, target)) return;
   StopState st{0.0, 0, 0.0, 0};
@@ -850,30 +871,40 @@ __device__ __forceinline__ void rf_program(const RfArgs& a, int vb, int vg, unsi
   for (; s <= a.max_iter; ++s) {
     const QPtr& P = a.P[cur];
     const QPtr& Pn = a.P[cur ^ 1];
+    // Iteration 1 starts from the random block: its rho means nothing, so it
+    // forms neither E, M' nor the norms, and its Z, M and G' (which only feed
+    // the FP32 factors and the next basis, whose span the later iterations
+    // correct) are plain FP32 products; X = W Z' stays float-float, so that
+    // the Y it gives is W P to working accuracy.
+    const bool first = s == 1;
     jb[0] = job(a.Wf, 1, a.Y, 0, a.Z, c, k, r);   // Z = W^H Y
     jb[1] = job(a.Y, 1, a.Y, 0, a.M, k, k, r);    // M = Y^H Y
     jb[2] = job(P, 1, P, 0, a.E, k, k, c);        // E = P^H P - I
     jb[2].minus_eye = 1;
-    rf_gemm_step(a, jb, 3, nullptr, smr, vb);
+    jb[0].fp32 = jb[1].fp32 = first;
+    rf_gemm_step(a, jb, first ? 2 : 3, nullptr, smr, vb);
     if (!rf_sync(a, vg, target)) return;
     // Z' = Z R_Y^-1 with R_Y = chol32(M); then M' = M - E M on the tile workers
     rf_solve_step(a, a.M, a.Z, a.Zp, c, nullptr, nullptr, 0, a.kap2 + s, vb, vg, smr);
-    jb[0] = job(a.E, 0, a.M, 0, a.Mp, k, k, k);
-    jb[0].Zin = a.M;
-    jb[0].neg = 1;
-    jb[0].add_in = 1;
-    rf_gemm_step(a, jb, 1, nullptr, smr, vb);
+    if (!first) {
+      jb[0] = job(a.E, 0, a.M, 0, a.Mp, k, k, k);
+      jb[0].Zin = a.M;
+      jb[0].neg = 1;
+      jb[0].add_in = 1;
+      rf_gemm_step(a, jb, 1, nullptr, smr, vb);
+    }
     if (!rf_sync(a, vg, target)) return;
     jb[0] = job(a.Zp, 1, a.Zp, 0, a.Gp, k, k, c);   // G' = Z'^H Z'
     jb[0].upper = 1;
+    jb[0].fp32 = first;
     jb[1] = job(a.Wf, 0, a.Zp, 0, a.X, r, k, c);    // X = W Z'
     jb[2] = job(P, 0, a.Mp, 0, a.Z, c, k, k);       // ||Z - P M'||, ||Z||
     jb[2].norm = 1;
-    rf_gemm_step(a, jb, 3, a.norms + 2 * s, smr, vb);
+    rf_gemm_step(a, jb, first ? 2 : 3, a.norms + 2 * s, smr, vb);
     if (!rf_sync(a, vg, target)) return;
     if (threadIdx.x == 0)
-      stop_sh = stop_now(st, s, __ldcg(a.norms + 2 * s), __ldcg(a.norms + 2 * s + 1),
-                         __ldcg(a.kap2 + s), k);
+      stop_sh = !first && stop_now(st, s, __ldcg(a.norms + 2 * s), __ldcg(a.norms + 2 * s + 1),
+                                   __ldcg(a.kap2 + s), k);
     __syncthreads();
     converged = stop_sh != 0;
     // R' = chol32(G'):  P <- Z' R'^-1,  Y <- X R'^-1 (= W P)
