@@ -243,7 +243,7 @@ def replica_value(world, steps, t_max_ms):
 def pinv_flops(w, method, sweeps):
     """Real flops of one pseudo-inverse of the r x c intersection, counted from
     the shapes of the method's steps (32 real flops per quaternion
-    multiply-add).  Refined: the FP64 products and FP64 triangular solves
+    multiply-add).  Refined: the float-float products and triangular solves
     (its FP32 Cholesky factors run on the FP32 pipe and are not counted)."""
     c, r = w["c"], w["r"]
     nr, nc = max(r, c), min(r, c)
@@ -255,10 +255,17 @@ def pinv_flops(w, method, sweeps):
         # rotation of both columns of G and V (q*w 32 flops, two combinations 16).
         return sweeps * pairs * (nr * 48 + (nr + nc) * 48)
     if method == "refined":
+        # float-float quaternion multiply-adds; the FP32 products of the
+        # first iteration (Y0 = W P0, Z, M, G') count at their instruction
+        # cost, 16 FP32 FMAs against FF_OPS_PER_QMAC for a float-float one
         it = max(1, sweeps)
-        per_iter = 2 * r * c * k + 4 * c * k * k + k ** 3 + 2 * (c * k * k // 2)
-        final = 3 * r * k * k + 2 * ((r + c) * k * k // 2) + c * k * k + c * r * k
-        return 32 * (r * c * k + it * per_iter + final)
+        solves = (2 * c + r) * k * k / 2
+        per_iter = 2 * r * c * k + r * k * k + c * k * k + k ** 3 + c * k * k / 2 + c * k * k + solves
+        first_ff = r * c * k + solves
+        first_fp32 = 2 * r * c * k + r * k * k + c * k * k / 2
+        final = (r * k * k + (r + c) * k * k + r * k * k + c * k * k + c * r * k)
+        ff = first_ff + (it - 1) * per_iter + final
+        return 32 * (ff + first_fp32 * 16.0 / FF_OPS_PER_QMAC)
     # subspace iteration: W Omega, W^H Q0, W P1, W^H Q1, W T (5 r c k); seven
     # Hermitian Grams (rows k^2 / 2) and Cholesky factorisations (k^3 / 6);
     # ten triangular solves (rows k^2 / 2); U = (P R1^-1 R2^-1) Q^H (c r k).
@@ -398,7 +405,7 @@ def fp64_check(Q, A, D, w, prec, sampler, stream, steps=10, warmup=3, rows=256):
 # ncu capture of the current code, per kernel (profiles/), on the 2048 x 2048
 # workload: the tensor-core Z = C T with the fused residual (mixed split) and
 # the refined pseudo-inverse of its 200 x 200 intersection.
-NCU_TRAFFIC = {"gemm_z": 81.89e6 + 2.36e6, "pinv_refine": 8.95e6 + 270.02e6}
+NCU_TRAFFIC = {"gemm_z": 81.91e6 + 2.24e6, "pinv_refine": 30.99e6 + 429.53e6}
 
 
 def peaks():
@@ -727,9 +734,10 @@ def run_ours(args):
                 amount, "bytes" if unit == "GB/s" else "flops")}
     if dom == "pinv" and args.pinv == "refined" and workload_name(args) == WORKLOAD:
         roof["traffic"] = NCU_TRAFFIC["pinv_refine"]
-        roof["traffic_note"] = ("almost all writes: L2 write-backs of the split-tile "
-                                "partials and float-float intermediates of its 27 steps "
-                                "(325 GB/s); the kernel reads W once (1.3 MB)")
+        roof["traffic_note"] = ("almost all writes: write-backs of the split-tile partials "
+                                "and float-float intermediates of its 27 steps (460 MB in "
+                                "the 0.93 ms capture, 490 GB/s); the kernel reads W once "
+                                "(1.3 MB)")
 
     # the GEMM stage: tensor work of the split (products x quaternion flops)
     # against the measured BF16 burst (TF32 at the nominal half of it)

@@ -476,9 +476,20 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
         row = mt * BM + sp * 32 + lane;
         n0 = nt * BN;
       }
-      // the residual's first A chunk is fetched while the MMAs still run
+      // the residual's first A chunk is fetched while the MMAs still run,
+      // and this thread's later chunks of the tile are prefetched into L2, so
+      // that the epilogue, which holds the only accumulator, reads A from L2
       float4 anext[4][4];
-      if constexpr (sums_mode) load_a(anext, row, n0 + 16 * half);
+      if constexpr (sums_mode) {
+        load_a(anext, row, n0 + 16 * half);
+        if (row < EM()) {
+#pragma unroll 1
+          for (int ch = half + 2; ch < BN / 16 && n0 + ch * 16 < EN(); ch += 2)
+#pragma unroll
+            for (int pl = 0; pl < 4; ++pl)
+              asm volatile("prefetch.global.L2 [%0];" ::"l"(EAP(pl) + (int64_t)row * ELD() + n0 + ch * 16));
+        }
+      }
       if (!mbar_wait(&tfull[a], aph, abort_flag)) break;
       tc_fence_after();
       const uint32_t tb = tmem_base + (uint32_t)(a * ACC_COLS) + ((uint32_t)(sp * 32) << 16);
