@@ -139,3 +139,34 @@ def test_batch_stage_times():
     assert sum(st.values()) <= total * 1.05 + 0.01, (st, total)
     assert st["core"] > 0.0 and st["z_gemm_residual"] > 0.0
     B.close()
+
+
+def test_batch_refined_reports_a_problem_without_gap():
+    # one Gaussian 64 x 64 problem (no gap at its rank cap 20: c = r = 64
+    # takes the whole matrix as W) among low-rank ones: the refined core
+    # runs out of its 5 iterations on it alone, reports NO_CONVERGENCE in
+    # that problem's info[2] and in the batch status, and still gives every
+    # other problem its FP64-accurate U
+    probs = synth.batch_problems(count=5, seed=7)
+    flat = np.random.default_rng(8).standard_normal((4, 64, 64)).astype(np.float32)
+    probs.insert(2, dict(X=flat, m=64, n=64, rank=20, c=64, r=64))
+    As = [dev(p["X"]) for p in probs]
+    B = Q.Batch(As, [p["c"] for p in probs], [p["r"] for p in probs],
+                [p["rank"] for p in probs], sampler=Q.SAMPLER_NORM, seed=3, max_sweeps=5,
+                pinv_method=Q.PINV_REFINED_FP64, prec=Q.PREC_BF16_MIXED)
+    B.run()
+    torch.cuda.synchronize()
+    assert int(B.status.item()) == 6   # QMCUR_ERR_NO_CONVERGENCE
+    for b, p in enumerate(probs):
+        info = host(B.get(b, "info"))
+        if b == 2:
+            assert info[2] == 6 and info[1] == 5, info
+            continue
+        assert info[2] == 0 and info[0] == p["rank"] and info[1] <= 5, (b, info)
+        A64 = p["X"].astype(np.float64)
+        J, I = host(B.get(b, "J")), host(B.get(b, "I"))
+        Wo = O.gather(A64, I, J)[2]
+        Uo, ko, so = O.pinv_truncated(Wo, 1e-10, p["rank"])
+        kap = so[0] / so[ko - 1]
+        assert rel_fro(host(B.get(b, "U64")), Uo) < 1e-12 * max(1.0, kap), b
+    B.close()
