@@ -195,27 +195,77 @@ k_qgemm_simt(QView X, QView Y, QView Z, QView A, const uint8_t* __restrict__ mas
   }
 }
 
-// Standalone residual over materialised A and Z: one CTA per 32 x 256 tile.
+// Standalone residual over materialised A and Z: one CTA per kResRows x 256
+// tile, one column per thread.  FP32 inputs are summed in float-float on the
+// FP32 pipe (a - z split exactly by TwoSum, squares by TwoProd, Knuth's
+// TwoSum into the pair), about 2^-44 of the sum over the tile's rows, and the
+// tile's partials are carried in FP64: FP64-level sums without FP64 work per
+// entry.  FP64 inputs are summed in FP64.
+constexpr int kResRows = 8;
+
+__device__ __forceinline__ void res_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+// (S, C) += x^2 (x = xh + xl exactly), in float-float
+__device__ __forceinline__ void res_add_sq(float& S, float& C, float xh, float xl) {
+  const float p = __fmul_rn(xh, xh);
+  const float e = __fmaf_rn(xh, xh, -p);
+  float s, t;
+  res_two_sum(S, p, s, t);
+  S = s;
+  C = __fadd_rn(C, __fadd_rn(t, __fmaf_rn(__fmul_rn(2.f, xh), xl, e)));
+}
+
 template <typename TA, typename TZ>
 __global__ void __launch_bounds__(256)
 k_residual(QView A, QView Z, const uint8_t* __restrict__ mask, double* __restrict__ partial) {
   const int64_t m = A.rows, n = A.cols;
   const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  const int64_t i0 = (int64_t)blockIdx.y * 32;
+  const int64_t i0 = (int64_t)blockIdx.y * kResRows;
+  constexpr bool ff = sizeof(TA) == 4 && sizeof(TZ) == 4;
   double num = 0.0, den = 0.0;
   if (j < n) {
-    for (int rr = 0; rr < 32; ++rr) {
+    // every load of the tile's column first (rows past m read as zero), then
+    // the sums; masked entries are selected away, so that whatever they hold
+    // (even a NaN) does not count
+    TA av[kResRows][4];
+    TZ zv[kResRows][4];
+    bool on[kResRows];
+#pragma unroll
+    for (int rr = 0; rr < kResRows; ++rr) {
       const int64_t i = i0 + rr;
-      if (i >= m) break;
-      if (mask != nullptr && mask[i * n + j] == 0) continue;
+      const bool in = i < m;
+      on[rr] = in && (mask == nullptr || mask[i * n + j] != 0);
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const double av = (double)reinterpret_cast<const TA*>(A.p[t])[i * A.ld + j];
-        const double zv = (double)reinterpret_cast<const TZ*>(Z.p[t])[i * Z.ld + j];
-        const double d = av - zv;
-        num = fma(d, d, num);
-        den = fma(av, av, den);
+        av[rr][t] = in ? reinterpret_cast<const TA*>(A.p[t])[i * A.ld + j] : TA(0);
+        zv[rr][t] = in ? reinterpret_cast<const TZ*>(Z.p[t])[i * Z.ld + j] : TZ(0);
       }
+    }
+    float Sn = 0.f, Cn = 0.f, Sd = 0.f, Cd = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < kResRows; ++rr) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if constexpr (ff) {
+          float dh, dl;
+          res_two_sum((float)av[rr][t], -(float)zv[rr][t], dh, dl);
+          res_add_sq(Sn, Cn, on[rr] ? dh : 0.f, on[rr] ? dl : 0.f);
+          res_add_sq(Sd, Cd, on[rr] ? (float)av[rr][t] : 0.f, 0.f);
+        } else {
+          const double d = on[rr] ? (double)av[rr][t] - (double)zv[rr][t] : 0.0;
+          const double a = on[rr] ? (double)av[rr][t] : 0.0;
+          num = fma(d, d, num);
+          den = fma(a, a, den);
+        }
+      }
+    }
+    if constexpr (ff) {
+      num = (double)Sn + (double)Cn;
+      den = (double)Sd + (double)Cd;
     }
   }
   __shared__ double red[2][256];
@@ -274,7 +324,7 @@ size_t simt_partials(int64_t m, int64_t n) {
 }
 
 size_t residual_partials(int64_t m, int64_t n) {
-  return (size_t)(((m + 31) / 32) * ((n + 255) / 256));
+  return (size_t)(((m + kResRows - 1) / kResRows) * ((n + 255) / 256));
 }
 
 // X (M x K) times Y (K x N) -> Z, or the fused residual against A, or (complete)
@@ -329,7 +379,7 @@ qmcur_status launch_residual_standalone(const qmcur_qmat* A, const qmcur_qmat* Z
   Carve cv(ws, ws_bytes);
   double* partial = cv.take<double>((size_t)(2 * cnt));
   if (!cv.ok) return QMCUR_ERR_INVALID_ARG;
-  dim3 grid((unsigned)((n + 255) / 256), (unsigned)((m + 31) / 32));
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)((m + kResRows - 1) / kResRows));
   if (grid.y > 65535) return QMCUR_ERR_UNSUPPORTED;
   QView a = view(A), z = view(Z);
   const bool ad = A->dtype == QMCUR_F64, zd = Z->dtype == QMCUR_F64;

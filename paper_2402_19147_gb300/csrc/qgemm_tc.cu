@@ -1273,6 +1273,48 @@ qmcur_status launch_reconstruct_tc(const qmcur_qmat* C, const qmcur_qmat* U, con
 
 namespace {
 
+// Tile width and K splits of a general product.  An output whose 128- or
+// 112-wide tiles fill the SMs keeps the stored product's rule (z_bn,
+// z_splits).  A smaller one takes, among the widths 128, 64 and 32 and the K
+// splits (each at least 4 k-iterations) that keep the items within one wave
+// over the SMs, the pair with the least modelled time: the tile's work per
+// split / the width's efficiency.  The efficiencies (1, 0.6, 0.35) are the
+// shared-memory bound of M = 128 MMAs at N = 128, 64 and 32: a narrow tile
+// reads A's slice for fewer outputs.  So a small output with a long K (the
+// backward's G_C = -2 E T^H, 1024 x 120 x 1536) keeps its wide tiles and
+// splits K instead of halving the width.
+struct GemmShape {
+  int bn, nsplit;
+};
+
+GemmShape gemm_shape(int64_t M, int64_t N, const TcPlan& pl, int64_t kp) {
+  const int bz = z_bn(M, N);
+  if (bz >= 112) return GemmShape{bz, z_splits(M, N, pl, kp)};
+  const int kiters = pl.nterms * (int)(kp / pl.epr);
+  const int64_t mt = (M + BM - 1) / BM;
+  const int widths[3] = {kBn2, 64, 32};
+  const double eff[3] = {1.0, 0.6, 0.35};
+  int max_ns = kiters / 4;
+  if (max_ns > kMaxZSplits) max_ns = kMaxZSplits;
+  if (max_ns < 1) max_ns = 1;
+  GemmShape best{bz, 1};
+  double best_cost = -1.0;
+  for (int w = 0; w < 3; ++w) {
+    const int64_t tiles = mt * ((N + widths[w] - 1) / widths[w]);
+    for (int ns = 1; ns <= max_ns; ++ns) {
+      const int per = (kiters + ns - 1) / ns;
+      const int nsz = (kiters + per - 1) / per;   // every split non-empty
+      if (nsz != ns || (ns > 1 && tiles * nsz > kWaveSms)) continue;
+      const double cost = (double)((tiles + kWaveSms - 1) / kWaveSms) * widths[w] * per / eff[w];
+      if (best_cost < 0.0 || cost < best_cost) {
+        best_cost = cost;
+        best = GemmShape{widths[w], nsz};
+      }
+    }
+  }
+  return best;
+}
+
 struct TcGemmWs {
   void *A, *B;
   float* Pz;
@@ -1284,7 +1326,7 @@ TcGemmWs carve_tc_gemm(Carve& cv, const TcPlan& pl, int64_t M, int64_t N, int64_
   TcGemmWs w;
   w.A = cv.take<char>((size_t)(pl.npieces * 4 * M * kp * es));
   w.B = cv.take<char>((size_t)(pl.npieces * 4 * N * kp * es));
-  const int nsz = z_splits(M, N, pl, kp);
+  const int nsz = gemm_shape(M, N, pl, kp).nsplit;
   w.Pz = nsz > 1 ? cv.take<float>((size_t)(nsz * 4 * M * rup(N, 4))) : nullptr;
   return w;
 }
@@ -1319,7 +1361,8 @@ qmcur_status tc_gemm(const QView& X, bool xh, const QView& Y, bool yh, int64_t M
     return QMCUR_ERR_UNSUPPORTED;
   qmcur_status s = pl.bf16 ? launch_splits<true>(js, tiles, st) : launch_splits<false>(js, tiles, st);
   if (s != QMCUR_OK) return s;
-  const int bn = z_bn(M, N);
+  const GemmShape shape = gemm_shape(M, N, pl, kp);
+  const int bn = shape.bn;
   CUtensorMap mA, mB;
   if (!make_map(&mA, w.A, pl.bf16, M, kp, pl.npieces, BM) ||
       !make_map(&mB, w.B, pl.bf16, N, kp, pl.npieces, bn))
@@ -1333,7 +1376,7 @@ qmcur_status tc_gemm(const QView& X, bool xh, const QView& Y, bool yh, int64_t M
   for (int i = 0; i < 6; ++i) { p.ta[i] = pl.ta[i]; p.tb[i] = pl.tb[i]; }
   p.mode = MODE_STORE_Z;
   p.status = dev_status;
-  const int nsz = z_splits(M, N, pl, kp);
+  const int nsz = shape.nsplit;
   const int64_t ldpz = rup(N, 4);
   if (nsz > 1 && M > 65535) return QMCUR_ERR_UNSUPPORTED;   // k_z_reduce's grid
   if (nsz > 1) {
