@@ -76,16 +76,26 @@ __global__ void k_scatter_add(QView dA, QPtr G, int64_t rows, int64_t cols, cons
   }
 }
 
-// Y += X (same shape)
-__global__ void k_qadd(QPtr X, QPtr Y, int64_t rows, int64_t cols) {
-  const int64_t total = rows * cols;
+// X = I (r x r) and Y = I (c x c), the starting values of I - W U and I - U W
+__global__ void k_two_eyes(QPtr X, int64_t r, QPtr Y, int64_t c) {
+  const int64_t total = r * r + c * c;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / cols, j = e % cols;
+    const bool first = e < r * r;
+    const int64_t f = first ? e : e - r * r, n = first ? r : c;
+    const int64_t i = f / n, j = f % n;
+    const QPtr& Q = first ? X : Y;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      reinterpret_cast<float*>(Y.p[t])[i * Y.ld + j] += reinterpret_cast<const float*>(X.p[t])[i * X.ld + j];
+      reinterpret_cast<float*>(Q.p[t])[i * Q.ld + j] = (t == 0 && i == j) ? 1.f : 0.f;
   }
+}
+
+// Rows r0.. and columns c0.. of q, as a matrix of its own
+QPtr sub_q(const QPtr& q, int64_t r0, int64_t c0) {
+  QPtr v = q;
+  for (int t = 0; t < 4; ++t) v.p[t] = reinterpret_cast<float*>(q.p[t]) + r0 * q.ld + c0;
+  return v;
 }
 
 QPtr take_q(Carve& cv, int64_t rows, int64_t cols) {
@@ -99,7 +109,9 @@ QPtr take_q(Carve& cv, int64_t rows, int64_t cols) {
 }
 
 struct BwdWs {
-  QPtr U32, W32, T, E, GC, GT, GU, GR, X1, WU, UW, UUh, UhU, M2, M3, GW;
+  // XL = [I - W U | M3] (r x (r + c)) and YL = [M2; I - U W] ((r + c) x c), so
+  // that (I - W U) M2 + M3 (I - U W) is one product XL YL
+  QPtr U32, W32, T, E, GC, GT, GU, GR, X1, UUh, UhU, XL, YL, GW;
   double* partial;
   double* out3;
   void* tc;          // operand pieces and K-split partials of the tensor-core products
@@ -140,12 +152,10 @@ BwdWs carve_bwd(Carve& cv, int64_t m, int64_t n, int64_t c, int64_t r) {
   w.GU = take_q(cv, c, r);
   w.GR = take_q(cv, r, n);
   w.X1 = take_q(cv, r, r);
-  w.WU = take_q(cv, r, r);
-  w.UW = take_q(cv, c, c);
   w.UUh = take_q(cv, c, c);
   w.UhU = take_q(cv, r, r);
-  w.M2 = take_q(cv, r, c);
-  w.M3 = take_q(cv, r, c);
+  w.XL = take_q(cv, r, r + c);
+  w.YL = take_q(cv, r + c, c);
   w.GW = take_q(cv, r, c);
   w.partial = cv.take<double>(2 * residual_partials(m, n));
   w.out3 = cv.take<double>(4);
@@ -222,19 +232,28 @@ qmcur_status launch_backward(const qmcur_qmat* A, const uint8_t* mask, const int
   if ((e = tc(vC, true, vE, false, c, n, m, -2.f * s, w.GT)) != QMCUR_OK) return e;
   if ((e = tc(vGT, false, vR, true, c, r, n, 1.f, w.GU)) != QMCUR_OK) return e;
   if ((e = tc(vU, true, vGT, false, r, n, c, 1.f, w.GR)) != QMCUR_OK) return e;
-  // G_W = -U^H G_U U^H + (I - W U) G_U^H U U^H + U^H U G_U^H (I - U W)
-  if ((e = small_qgemm(true, false, ri, ri, ci, 1.f, w.U32, w.GU, 0.f, w.X1, st)) != QMCUR_OK) return e;
-  if ((e = small_qgemm(false, true, ri, ci, ri, -1.f, w.X1, w.U32, 0.f, w.GW, st)) != QMCUR_OK) return e;
-  if ((e = small_qgemm(false, true, ci, ci, ri, 1.f, w.U32, w.U32, 0.f, w.UUh, st)) != QMCUR_OK) return e;
-  if ((e = small_qgemm(true, false, ri, ci, ci, 1.f, w.GU, w.UUh, 0.f, w.M2, st)) != QMCUR_OK) return e;
-  if ((e = small_qgemm(false, false, ri, ri, ci, 1.f, w.W32, w.U32, 0.f, w.WU, st)) != QMCUR_OK) return e;
-  k_qadd<<<blocks_for(r * c), 256, 0, st>>>(w.M2, w.GW, r, c);
-  if ((e = small_qgemm(false, false, ri, ci, ri, -1.f, w.WU, w.M2, 1.f, w.GW, st)) != QMCUR_OK) return e;
-  if ((e = small_qgemm(true, false, ri, ri, ci, 1.f, w.U32, w.U32, 0.f, w.UhU, st)) != QMCUR_OK) return e;
-  if ((e = small_qgemm(false, true, ri, ci, ri, 1.f, w.UhU, w.GU, 0.f, w.M3, st)) != QMCUR_OK) return e;
-  if ((e = small_qgemm(false, false, ci, ci, ri, 1.f, w.U32, w.W32, 0.f, w.UW, st)) != QMCUR_OK) return e;
-  k_qadd<<<blocks_for(r * c), 256, 0, st>>>(w.M3, w.GW, r, c);
-  if ((e = small_qgemm(false, false, ri, ci, ci, -1.f, w.M3, w.UW, 1.f, w.GW, st)) != QMCUR_OK) return e;
+  // G_W = -U^H G_U U^H + (I - W U) G_U^H U U^H + U^H U G_U^H (I - U W),
+  // by dependency level, one launch each:
+  //   X1 = U^H G_U, U U^H, U^H U, I - W U, I - U W;
+  //   G_W = -X1 U^H, M2 = G_U^H (U U^H), M3 = (U^H U) G_U^H;
+  //   G_W += [I - W U | M3] [M2; I - U W]
+  const QPtr IWU = sub_q(w.XL, 0, 0), M3 = sub_q(w.XL, 0, r);
+  const QPtr M2 = sub_q(w.YL, 0, 0), IUW = sub_q(w.YL, r, 0);
+  k_two_eyes<<<blocks_for(r * r + c * c), 256, 0, st>>>(IWU, r, IUW, c);
+  {
+    const SmallGemmArgs l1[5] = {{w.U32, w.GU, w.X1, ri, ri, ci, 1.f, 0.f, 1, 0},
+                                 {w.U32, w.U32, w.UUh, ci, ci, ri, 1.f, 0.f, 0, 1},
+                                 {w.U32, w.U32, w.UhU, ri, ri, ci, 1.f, 0.f, 1, 0},
+                                 {w.W32, w.U32, IWU, ri, ri, ci, -1.f, 1.f, 0, 0},
+                                 {w.U32, w.W32, IUW, ci, ci, ri, -1.f, 1.f, 0, 0}};
+    if ((e = small_qgemm_batch(l1, 5, st)) != QMCUR_OK) return e;
+    const SmallGemmArgs l2[3] = {{w.X1, w.U32, w.GW, ri, ci, ri, -1.f, 0.f, 0, 1},
+                                 {w.GU, w.UUh, M2, ri, ci, ci, 1.f, 0.f, 1, 0},
+                                 {w.UhU, w.GU, M3, ri, ci, ri, 1.f, 0.f, 0, 1}};
+    if ((e = small_qgemm_batch(l2, 3, st)) != QMCUR_OK) return e;
+    if ((e = small_qgemm(false, false, ri, ci, ri + ci, 1.f, w.XL, w.YL, 1.f, w.GW, st)) != QMCUR_OK)
+      return e;
+  }
   // scatters
   QView vdA = view(dA);
   k_scatter_add<<<blocks_for(m * c), 256, 0, st>>>(vdA, w.GC, m, c, I, J, 0);

@@ -25,10 +25,22 @@ struct QPtr {
 // triangular-solve row in 4 registers per lane.
 constexpr int kSmallCholMax = 100;
 
-// Z = alpha op(X) op(Y) + beta Z, op(X) M x K, op(Y) K x N.  With xh, X is
-// stored K x M and op(X) = X^H (conjugate transpose, Sec. 2.2); likewise yh.
-// X, Y are FP32; Z may be FP32 or FP64.  beta == 0 never reads Z.
+// One small product Z = alpha op(X) op(Y) + beta Z, op(X) M x K, op(Y) K x N.
+// With xh, X is stored K x M and op(X) = X^H (conjugate transpose, Sec. 2.2);
+// likewise yh.  X, Y are FP32; Z may be FP32 or FP64.  beta == 0 never reads Z.
+struct SmallGemmArgs {
+  QPtr X, Y, Z;
+  int M, N, K;
+  float alpha, beta;
+  int xh, yh;
+};
+
 qmcur_status small_qgemm(bool xh, bool yh, int M, int N, int K, float alpha, const QPtr& X,
                          const QPtr& Y, float beta, const QPtr& Z, cudaStream_t st);
+
+// Up to kSmallBatchMax independent small products in one launch (their tiles
+// side by side in the grid).  No product may read another's output.
+constexpr int kSmallBatchMax = 6;
+qmcur_status small_qgemm_batch(const SmallGemmArgs* jobs, int count, cudaStream_t st);
 
 }  // namespace qmcur

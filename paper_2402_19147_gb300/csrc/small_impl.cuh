@@ -16,13 +16,6 @@ constexpr int kSmTileThreads = 256;
 // keeps the transposed stores free of bank conflicts.
 constexpr int kSmGemmQuats = kSmTS * (kSmBK + 1) + kSmBK * (kSmTS + 1);
 
-struct SmallGemmArgs {
-  QPtr X, Y, Z;
-  int M, N, K;
-  float alpha, beta;
-  int xh, yh;
-};
-
 // Named barrier over the 256 threads of one tile worker.
 __device__ __forceinline__ void worker_sync(int bar_id) {
   asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(kSmTileThreads) : "memory");
