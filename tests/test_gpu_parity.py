@@ -267,6 +267,33 @@ def test_residual_fused_and_standalone():
         assert abs(o2[0] - rel_o) < 1e-5 and abs(o2[2] - den_o) < 1e-12 * den_o
 
 
+def test_residual_standalone_masked_nan_and_fp64():
+    # the standalone pass selects masked-out entries away: a NaN in A or Z
+    # where the mask is 0 does not reach the sums; FP64 inputs are summed in
+    # FP64, FP32 ones in float-float, both to FP64 level (1e-12 on the two sums)
+    m, n = 45, 300   # 45 rows: five 8-row tiles and a ragged one
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((4, m, n))
+    Z = A + 1e-3 * rng.standard_normal((4, m, n))
+    mask = synth.bernoulli_mask(m, n, seed=13, p_observed=0.6)
+    A[1, 3, 7] = np.nan
+    Z[2, 40, 299] = np.nan
+    mask[3, 7] = 0
+    mask[40, 299] = 0
+    for dt, tol in ((np.float64, 1e-12), (np.float32, 1e-12)):
+        Ad, Zd = A.astype(dt), Z.astype(dt)
+        rel_o, num_o, den_o = O.residual(np.nan_to_num(Ad.astype(np.float64)),
+                                         np.nan_to_num(Zd.astype(np.float64)), mask)
+        out3 = torch.empty(3, dtype=torch.float64, device="cuda")
+        ws = Q.workspace(m, n, 4, 4, Q.PREC_FP32)
+        st = Q.status_tensor()
+        Q.residual(dev(Ad), out3, mask=dev(mask), Z=dev(Zd), ws=ws, status=st)
+        assert run_status(st) == 0
+        o = host(out3)
+        assert np.all(np.isfinite(o)), o
+        assert abs(o[1] - num_o) < tol * num_o and abs(o[2] - den_o) < tol * den_o, (dt, o, num_o, den_o)
+
+
 # ---------------------------------------------------------------- whole path -
 def test_decompose_gauss256_fp64():
     w = synth.WORKLOADS["gauss256_rank10_fp64"]
