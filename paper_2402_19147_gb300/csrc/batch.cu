@@ -25,7 +25,9 @@
 //   k_batch_gemm     grouped quaternion GEMMs over a flattened tile list
 //                    (T = U R, then Z = C T with the residual fused), tile
 //                    shape chosen per GEMM by timing the candidates at plan
-//                    time (the autotuner);
+//                    time (the autotuner); in a split precision both are
+//                    instead one grouped tcgen05 launch each over stacked
+//                    operand pieces (k_split_table, then k_qgemm_tc);
 //   k_batch_fold     per problem, the tile partials of the residual in order.
 #include <algorithm>
 #include <map>
@@ -57,6 +59,7 @@ qmcur_status refine_each_launch(const void* dargs, const int* dorder, int count,
                                 int32_t* batch_status, cudaStream_t st);
 
 constexpr int kBatchMaxCore = 80;      // largest min(r, c) held by k_batch_jacobi
+constexpr int kBatchTBn = 64;          // tile width of the grouped tensor-core T = U R
 constexpr int64_t kBatchCoreSmem = 200 * 1024;   // bytes of G and V in shared memory
 
 struct BatchProblem {
@@ -528,6 +531,17 @@ struct BatchPlan {
   TcGroupProb* dgprobs = nullptr;
   TcGroupTile* dgtiles = nullptr;
   int ngtiles = 0, tc_bn = 128;
+  // T = U R on the tensor cores (the split of T in the precision, e.g. BF16X6
+  // under the mixed split): every problem's U (c x r) as rows of A1_all, its
+  // R^T (n x r) as rows of B1_all, K padded to the largest r
+  void* A1_all = nullptr;
+  void* B1_all = nullptr;
+  int64_t rows_a1 = 0, rows_b1 = 0, kpad1 = 0;
+  TcSplitJob* djobs1 = nullptr;
+  int njobs1 = 0, split_tiles1 = 0;
+  TcGroupProb* dgprobs1 = nullptr;
+  TcGroupTile* dgtiles1 = nullptr;
+  int ngtiles1 = 0;
   // stage boundaries, recorded by the captured graph (qmcur_batch_stage_ms)
   cudaEvent_t ev[kBatchStages + 1] = {};
 };
@@ -562,7 +576,15 @@ static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st, bool timed = fa
         p->dprobs, p->opts.rcond, p->opts.max_sweeps > 0 ? p->opts.max_sweeps : 30);
   }
   mark(4);
-  launch_batch_gemm(p->cfg1, p->dprobs, p->dtiles1, p->ntiles1, 0, nullptr, st);
+  if (p->tc) {
+    qmcur_status s = tc_group_split(p->opts.prec, p->djobs1, p->njobs1, p->split_tiles1, st, 0);
+    if (s != QMCUR_OK) return s;
+    s = tc_group_store(p->opts.prec, kBatchTBn, p->A1_all, p->rows_a1, p->B1_all, p->rows_b1,
+                       p->kpad1, p->dgtiles1, p->ngtiles1, p->dgprobs1, p->status, st);
+    if (s != QMCUR_OK) return s;
+  } else {
+    launch_batch_gemm(p->cfg1, p->dprobs, p->dtiles1, p->ntiles1, 0, nullptr, st);
+  }
   mark(5);
   if (p->tc) {
     qmcur_status s = tc_group_split(p->opts.prec, p->djobs, p->njobs, p->split_tiles, st);
@@ -710,12 +732,101 @@ static void free_plan(BatchPlan* p) {
   cudaFree(p->djobs);
   cudaFree(p->dgprobs);
   cudaFree(p->dgtiles);
+  cudaFree(p->A1_all);
+  cudaFree(p->B1_all);
+  cudaFree(p->djobs1);
+  cudaFree(p->dgprobs1);
+  cudaFree(p->dgtiles1);
   delete p;
 }
 
 }  // namespace qmcur
 
 using namespace qmcur;
+
+// T = U R on the tensor cores for a split precision: the stacked pieces of
+// every problem's U (A operand, rows c) and R^T (B operand, rows n), the
+// split jobs that cut them, the problem table (output T, K = r) and the tile
+// list (the c rows of a problem in one 128-row tile, its n columns in
+// kBatchTBn-wide tiles).
+static qmcur_status build_t_stage(BatchPlan* p, cudaStream_t stream) {
+  const int32_t pr = p->opts.prec;
+  const int64_t epr = tc_group_epr(pr, 0);
+  const int count = p->count;
+  std::vector<int64_t> arow(count), brow(count);
+  int64_t rmax = 1;
+  for (int b = 0; b < count; ++b) {
+    arow[b] = p->rows_a1;
+    brow[b] = p->rows_b1;
+    p->rows_a1 += p->host[b].c;
+    p->rows_b1 += p->host[b].n;
+    rmax = std::max<int64_t>(rmax, p->host[b].r);
+  }
+  p->kpad1 = (rmax + epr - 1) / epr * epr;
+  if (p->rows_a1 > INT32_MAX / 2 || p->rows_b1 > INT32_MAX / 2) return QMCUR_ERR_UNSUPPORTED;
+  const size_t ba = tc_group_piece_bytes(pr, p->rows_a1, p->kpad1, 0);
+  const size_t bb = tc_group_piece_bytes(pr, p->rows_b1, p->kpad1, 0);
+  if (cudaMalloc(&p->A1_all, ba) != cudaSuccess || cudaMalloc(&p->B1_all, bb) != cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  cudaMemsetAsync(p->A1_all, 0, ba, stream);
+  cudaMemsetAsync(p->B1_all, 0, bb, stream);
+  std::vector<TcSplitJob> jobs;
+  std::vector<TcGroupProb> gp(count);
+  std::vector<TcGroupTile> tiles;
+  int stiles = 0;
+  auto add_job = [&](const QView& S, bool trans, void* dst, int64_t rows, int64_t K, int64_t row0,
+                     int64_t rows_total) {
+    TcSplitJob j{};
+    j.S = S;
+    j.dst = dst;
+    j.rows = rows;
+    j.K = K;
+    j.kp_job = (K + epr - 1) / epr * epr;
+    j.kpad = p->kpad1;
+    j.row0 = row0;
+    j.plane_stride = rows_total * p->kpad1;
+    j.trans = trans ? 1 : 0;
+    j.tiles_k = (int)((j.kp_job + 63) / 64);
+    j.first_tile = stiles;
+    stiles += j.tiles_k * (int)((rows + 31) / 32);
+    jobs.push_back(j);
+  };
+  for (int b = 0; b < count; ++b) {
+    const BatchProblem& P = p->host[b];
+    add_job(P.U, false, p->A1_all, P.c, P.r, arow[b], p->rows_a1);   // A[i][k] = U[i][k]
+    add_job(P.R, true, p->B1_all, P.n, P.r, brow[b], p->rows_b1);    // B[j][k] = R[k][j]
+    TcGroupProb& g = gp[b];
+    g = TcGroupProb{};
+    g.m = P.c;
+    g.n = P.n;
+    g.K = P.r;
+    g.kblocks = (int)(((P.r + epr - 1) / epr * epr) / epr);
+    g.arow = (int)arow[b];
+    g.brow = (int)brow[b];
+    bool zv = P.T.ld % 4 == 0;
+    for (int t = 0; t < 4; ++t) {
+      g.z[t] = reinterpret_cast<float*>(P.T.p[t]);
+      zv = zv && reinterpret_cast<uintptr_t>(P.T.p[t]) % 16 == 0;
+    }
+    g.ldz = P.T.ld;
+    g.z_vec = zv ? 1 : 0;
+    for (int m0 = 0; m0 < P.c; m0 += 128)
+      for (int n0 = 0; n0 < P.n; n0 += kBatchTBn) tiles.push_back(TcGroupTile{b, m0, n0});
+  }
+  p->njobs1 = (int)jobs.size();
+  p->split_tiles1 = stiles;
+  p->ngtiles1 = (int)tiles.size();
+  if (cudaMalloc(&p->djobs1, jobs.size() * sizeof(TcSplitJob)) != cudaSuccess ||
+      cudaMalloc(&p->dgprobs1, gp.size() * sizeof(TcGroupProb)) != cudaSuccess ||
+      cudaMalloc(&p->dgtiles1, tiles.size() * sizeof(TcGroupTile)) != cudaSuccess)
+    return QMCUR_ERR_CUDA;
+  cudaMemcpyAsync(p->djobs1, jobs.data(), jobs.size() * sizeof(TcSplitJob), cudaMemcpyHostToDevice, stream);
+  cudaMemcpyAsync(p->dgprobs1, gp.data(), gp.size() * sizeof(TcGroupProb), cudaMemcpyHostToDevice, stream);
+  cudaMemcpyAsync(p->dgtiles1, tiles.data(), tiles.size() * sizeof(TcGroupTile), cudaMemcpyHostToDevice,
+                  stream);
+  // the host vectors must outlive their copies
+  return cudaStreamSynchronize(stream) == cudaSuccess ? QMCUR_OK : QMCUR_ERR_CUDA;
+}
 
 extern "C" {
 
@@ -952,6 +1063,8 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     cudaMemcpyAsync(p->djobs, jobs.data(), jobs.size() * sizeof(TcSplitJob), cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(p->dgprobs, gp.data(), gp.size() * sizeof(TcGroupProb), cudaMemcpyHostToDevice, stream);
     if (cudaStreamSynchronize(stream) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
+    const qmcur_status st1 = build_t_stage(p, stream);
+    if (st1 != QMCUR_OK) { free_plan(p); return st1; }
   }
   // first pass (un-captured): fills T and the operands so that the GEMM
   // candidates can be timed on real data
@@ -977,7 +1090,7 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     if (s != QMCUR_OK) { free_plan(p); return s; }
   }
   // autotune the two grouped GEMMs, rebuild their tile lists
-  p->cfg1 = autotune(p, 0, stream);
+  p->cfg1 = tc ? 0 : autotune(p, 0, stream);   // a split plan runs T on the tensor cores
   if (!tc) p->cfg2 = autotune(p, 1, stream);
   {
     cudaFree(p->dtiles1); cudaFree(p->dtiles2);
@@ -1060,7 +1173,7 @@ qmcur_status qmcur_batch_view(const void* plan, int32_t index, qmcur_batch_item*
   out->col_p = P.col_p; out->row_p = P.row_p; out->J = P.J; out->I = P.I;
   out->C = toq(P.C); out->R = toq(P.R); out->W = toq(P.W); out->U = toq(P.U);
   out->out3 = P.out3; out->info = P.info;
-  out->gemm_tiles[0] = kCfgs[p->cfg1].bm;
+  out->gemm_tiles[0] = p->tc ? kBatchTBn : kCfgs[p->cfg1].bm;
   out->gemm_tiles[1] = p->tc ? p->tc_bn : kCfgs[p->cfg2].bm;
   return QMCUR_OK;
 }

@@ -92,7 +92,11 @@ constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 // MODE_GROUPED is MODE_RESIDUAL over the tiles of many problems (tc_group.cuh):
 // each tile's coordinates, inner dimension and A come from the group tables,
 // and its partials go to partial[2 tile], with no fold in the kernel.
-enum { MODE_STORE_Z = 0, MODE_RESIDUAL = 1, MODE_STORE_ZT = 2, MODE_COMPLETE = 3, MODE_GROUPED = 4 };
+// MODE_GROUPED_STORE is MODE_STORE_Z over the tiles of many problems: each
+// tile stores into its problem's own output (group tables), masked by that
+// problem's m and n.
+enum { MODE_STORE_Z = 0, MODE_RESIDUAL = 1, MODE_STORE_ZT = 2, MODE_COMPLETE = 3, MODE_GROUPED = 4,
+       MODE_GROUPED_STORE = 5 };
 
 struct TcParams {
   int M, N;
@@ -296,8 +300,8 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
   constexpr uint32_t kIdPos = make_idesc(BF16, false, BN), kIdNeg = make_idesc(BF16, true, BN);
   constexpr int kElemsPerRow = ROWB / (BF16 ? 2 : 4);
   constexpr int kStepElems = 32 / (BF16 ? 2 : 4);          // K of one MMA (32 bytes)
-  constexpr bool grouped = MODE == MODE_GROUPED;
-  constexpr bool sums_mode = MODE == MODE_RESIDUAL || MODE == MODE_COMPLETE || grouped;
+  constexpr bool grouped = MODE == MODE_GROUPED || MODE == MODE_GROUPED_STORE;
+  constexpr bool sums_mode = MODE == MODE_RESIDUAL || MODE == MODE_COMPLETE || MODE == MODE_GROUPED;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int mtiles = (p.M + BM - 1) / BM, ntiles = (p.N + BN - 1) / BN;
@@ -427,6 +431,9 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     // the current tile's problem (the group tables, or p itself)
     // (grouped only; otherwise the accessors below read p directly)
     int Mv = 0, Nv = 0, avec = 0;
+    float* zg[4] = {nullptr, nullptr, nullptr, nullptr};   // MODE_GROUPED_STORE: the problem's output
+    int64_t ldzg = 0;
+    int zgvec = 0;
     int64_t ldav = 0;
     const float* ap[4] = {nullptr, nullptr, nullptr, nullptr};
     auto EM = [&]() -> int { if constexpr (grouped) return Mv; else return p.M; };
@@ -469,6 +476,12 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
         ldav = gp.lda;
 #pragma unroll
         for (int pl = 0; pl < 4; ++pl) ap[pl] = gp.a[pl];
+        if constexpr (MODE == MODE_GROUPED_STORE) {
+#pragma unroll
+          for (int pl = 0; pl < 4; ++pl) zg[pl] = gp.z[pl];
+          ldzg = gp.ldz;
+          zgvec = gp.z_vec;
+        }
         row = tl.m0 + sp * 32 + lane;
         n0 = tl.n0;
       } else {
@@ -585,7 +598,21 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
             float z[16];
             tmem_ld16(tb + pl * BN + ch * 16, z);
             const int c0 = n0 + ch * 16;
-            if constexpr (MODE == MODE_STORE_ZT) {
+            if constexpr (MODE == MODE_GROUPED_STORE) {
+              if (row < Mv) {
+                float* zr = zg[pl] + (int64_t)row * ldzg + c0;
+                if (c0 + 16 <= Nv && zgvec) {
+#pragma unroll
+                  for (int q = 0; q < 4; ++q)
+                    reinterpret_cast<float4*>(zr)[q] =
+                        make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+                } else {
+#pragma unroll
+                  for (int j = 0; j < 16; ++j)
+                    if (c0 + j < Nv) zr[j] = z[j];
+                }
+              }
+            } else if constexpr (MODE == MODE_STORE_ZT) {
               if (row < p.M) {
                 float* zc = p.z[pl] + split * p.zsplit + (int64_t)c0 * p.ldz + row;
 #pragma unroll
@@ -1098,7 +1125,7 @@ qmcur_status launch_gemm_mode(const CUtensorMap& ma, const CUtensorMap& mb, cons
   }
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return QMCUR_ERR_CUDA;
-  const int items = MODE == MODE_GROUPED ? p.gcount
+  const int items = (MODE == MODE_GROUPED || MODE == MODE_GROUPED_STORE) ? p.gcount
                                          : ((p.M + BM - 1) / BM) * ((p.N + BNT - 1) / BNT) * p.nsplit;
   const int cap = cta_cap(sms);
   const int grid = items < cap ? items : cap;
@@ -1483,26 +1510,27 @@ __global__ void __launch_bounds__(256) k_split_table(const TcSplitJob* __restric
 }
 
 // The plan of Z = C T for a batch precision (the second product's split).
-TcPlan group_plan(int32_t prec) {
+// The split of a precision for Z = C T (product 1) or for T = U R (product 0).
+TcPlan group_plan(int32_t prec, int product = 1) {
   TcPlan a, b;
   plans_for(prec, a, b);
-  return b;
+  return product == 0 ? a : b;
 }
 
 }  // namespace
 
-int tc_group_epr(int32_t prec) { return (int)group_plan(prec).epr; }
-int tc_group_npieces(int32_t prec) { return group_plan(prec).npieces; }
+int tc_group_epr(int32_t prec, int product) { return (int)group_plan(prec, product).epr; }
+int tc_group_npieces(int32_t prec, int product) { return group_plan(prec, product).npieces; }
 
-size_t tc_group_piece_bytes(int32_t prec, int64_t rows, int64_t kpad) {
-  const TcPlan pl = group_plan(prec);
+size_t tc_group_piece_bytes(int32_t prec, int64_t rows, int64_t kpad, int product) {
+  const TcPlan pl = group_plan(prec, product);
   return (size_t)pl.npieces * 4 * rows * kpad * (pl.bf16 ? 2 : 4);
 }
 
 qmcur_status tc_group_split(int32_t prec, const TcSplitJob* jobs, int njobs, int tiles,
-                            cudaStream_t st) {
+                            cudaStream_t st, int product) {
   if (njobs < 1 || tiles < 1) return QMCUR_ERR_INVALID_ARG;
-  const TcPlan pl = group_plan(prec);
+  const TcPlan pl = group_plan(prec, product);
   if (pl.bf16) k_split_table<true><<<tiles, 256, 0, st>>>(jobs, njobs, pl.npieces);
   else k_split_table<false><<<tiles, 256, 0, st>>>(jobs, njobs, pl.npieces);
   return cuda_ok(cudaGetLastError());
@@ -1536,6 +1564,34 @@ qmcur_status tc_group_residual(int32_t prec, int bn, const void* A_all, int64_t 
                     : launch_gemm_mode<true, 128, false, MODE_GROUPED>(mA, mB, p, st);
   return bn == 64 ? launch_gemm_mode<false, 64, false, MODE_GROUPED>(mA, mB, p, st)
                   : launch_gemm_mode<false, 128, false, MODE_GROUPED>(mA, mB, p, st);
+}
+
+qmcur_status tc_group_store(int32_t prec, int bn, const void* A_all, int64_t rows_a,
+                            const void* B_all, int64_t rows_b, int64_t kpad,
+                            const TcGroupTile* tiles, int ntiles, const TcGroupProb* probs,
+                            int32_t* dev_status, cudaStream_t st) {
+  if (ntiles < 1 || (bn != 64 && bn != 128)) return QMCUR_ERR_INVALID_ARG;
+  const TcPlan pl = group_plan(prec, 0);
+  CUtensorMap mA, mB;
+  if (!make_map(&mA, const_cast<void*>(A_all), pl.bf16, rows_a, kpad, pl.npieces, BM) ||
+      !make_map(&mB, const_cast<void*>(B_all), pl.bf16, rows_b, kpad, pl.npieces, bn))
+    return QMCUR_ERR_CUDA;
+  TcParams p{};
+  p.M = 1;
+  p.N = 1;
+  p.nterms = pl.nterms;
+  for (int i = 0; i < 6; ++i) { p.ta[i] = pl.ta[i]; p.tb[i] = pl.tb[i]; }
+  p.mode = MODE_GROUPED_STORE;
+  p.nsplit = 1;
+  p.status = dev_status;
+  p.gtiles = tiles;
+  p.gprobs = probs;
+  p.gcount = ntiles;
+  if (pl.bf16)
+    return bn == 64 ? launch_gemm_mode<true, 64, false, MODE_GROUPED_STORE>(mA, mB, p, st)
+                    : launch_gemm_mode<true, 128, false, MODE_GROUPED_STORE>(mA, mB, p, st);
+  return bn == 64 ? launch_gemm_mode<false, 64, false, MODE_GROUPED_STORE>(mA, mB, p, st)
+                  : launch_gemm_mode<false, 128, false, MODE_GROUPED_STORE>(mA, mB, p, st);
 }
 
 }  // namespace qmcur
