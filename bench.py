@@ -1056,7 +1056,7 @@ def batch_measure(args, Q, synth, dev, steps, warmup):
             "data": "synthetic",
             "config": {"workload": "batch512_uneven", "problems": 512, "gemm_prec": split,
                        "pinv": core_name[core], "graph": True,
-                       "gemm_tiles": {"t_simt": tiles[0], "z_tcgen05_bn": tiles[1]},
+                       "gemm_tiles": {"t_tcgen05_bn": tiles[0], "z_tcgen05_bn": tiles[1]},
                        "l2": "flushed between steps (256 MiB write)"},
             "fp32_gemms": {"value": 512 / (ms32 / 1e3), "unit": "decompositions/s",
                            "ms_per_step": ms32},
