@@ -871,11 +871,13 @@ __device__ __forceinline__ void rf_program(const RfArgs& a, int vb, int vg, unsi
   for (; s <= a.max_iter; ++s) {
     const QPtr& P = a.P[cur];
     const QPtr& Pn = a.P[cur ^ 1];
-    // Iteration 1 starts from the random block: its rho means nothing, so it
-    // forms neither E, M' nor the norms, and its Z, M and G' (which only feed
-    // the FP32 factors and the next basis, whose span the later iterations
-    // correct) are plain FP32 products; X = W Z' stays float-float, so that
-    // the Y it gives is W P to working accuracy.
+    // The Gram products G' (here) and G1, G2 (the ending) only feed FP32
+    // Cholesky factors, right preconditioners, so they are plain FP32
+    // products.  Iteration 1 starts from the random block: its rho means
+    // nothing, so it forms neither E, M' nor the norms, and its Z and M
+    // (which only feed the FP32 factors and the next basis, whose span the
+    // later iterations correct) are plain FP32 products too; X = W Z' stays
+    // float-float, so that the Y it gives is W P to working accuracy.
     const bool first = s == 1;
     jb[0] = job(a.Wf, 1, a.Y, 0, a.Z, c, k, r);   // Z = W^H Y
     jb[1] = job(a.Y, 1, a.Y, 0, a.M, k, k, r);    // M = Y^H Y
@@ -894,9 +896,9 @@ __device__ __forceinline__ void rf_program(const RfArgs& a, int vb, int vg, unsi
       rf_gemm_step(a, jb, 1, nullptr, smr, vb);
     }
     if (!rf_sync(a, vg, target)) return;
-    jb[0] = job(a.Zp, 1, a.Zp, 0, a.Gp, k, k, c);   // G' = Z'^H Z'
+    jb[0] = job(a.Zp, 1, a.Zp, 0, a.Gp, k, k, c);   // G' = Z'^H Z' (feeds chol32 only)
     jb[0].upper = 1;
-    jb[0].fp32 = first;
+    jb[0].fp32 = 1;
     jb[1] = job(a.Wf, 0, a.Zp, 0, a.X, r, k, c);    // X = W Z'
     jb[2] = job(P, 0, a.Mp, 0, a.Z, c, k, k);       // ||Z - P M'||, ||Z||
     jb[2].norm = 1;
@@ -915,14 +917,16 @@ __device__ __forceinline__ void rf_program(const RfArgs& a, int vb, int vg, unsi
   }
   const QPtr& P = a.P[cur];
   // U = P (W P)^+ by CholeskyQR2 with FP32 factors and the E2 correction
-  jb[0] = job(a.Y, 1, a.Y, 0, a.G1, k, k, r);
+  jb[0] = job(a.Y, 1, a.Y, 0, a.G1, k, k, r);   // feeds chol32 only
   jb[0].upper = 1;
+  jb[0].fp32 = 1;
   rf_gemm_step(a, jb, 1, nullptr, smr, vb);
   if (!rf_sync(a, vg, target)) return;
   rf_solve_step(a, a.G1, a.Y, a.Q1, r, &P, &a.T1, c, nullptr, vb, vg, smr);
   if (!rf_sync(a, vg, target)) return;
-  jb[0] = job(a.Q1, 1, a.Q1, 0, a.G2, k, k, r);
+  jb[0] = job(a.Q1, 1, a.Q1, 0, a.G2, k, k, r);   // feeds chol32 only
   jb[0].upper = 1;
+  jb[0].fp32 = 1;
   rf_gemm_step(a, jb, 1, nullptr, smr, vb);
   if (!rf_sync(a, vg, target)) return;
   rf_solve_step(a, a.G2, a.Q1, a.Q2, r, &a.T1, &a.T2, c, nullptr, vb, vg, smr);
