@@ -255,17 +255,20 @@ def pinv_flops(w, method, sweeps):
         # rotation of both columns of G and V (q*w 32 flops, two combinations 16).
         return sweeps * pairs * (nr * 48 + (nr + nc) * 48)
     if method == "refined":
-        # float-float quaternion multiply-adds; the FP32 products of the
-        # first iteration (Y0 = W P0, Z, M, G') count at their instruction
-        # cost, 16 FP32 FMAs against FF_OPS_PER_QMAC for a float-float one
+        # float-float quaternion multiply-adds; the FP32 products (the first
+        # iteration's Y0 = W P0, Z and M, every G', G1 and G2) count at their
+        # instruction cost, 16 FP32 FMAs against FF_OPS_PER_QMAC for a
+        # float-float one
+        # (the Gram products G', G1, G2 that only feed FP32 Cholesky factors
+        # are FP32 too)
         it = max(1, sweeps)
         solves = (2 * c + r) * k * k / 2
-        per_iter = 2 * r * c * k + r * k * k + c * k * k + k ** 3 + c * k * k / 2 + c * k * k + solves
+        per_iter = 2 * r * c * k + r * k * k + c * k * k + k ** 3 + c * k * k + solves
         first_ff = r * c * k + solves
-        first_fp32 = 2 * r * c * k + r * k * k + c * k * k / 2
-        final = (r * k * k + (r + c) * k * k + r * k * k + c * k * k + c * r * k)
+        fp32 = 2 * r * c * k + r * k * k + it * c * k * k / 2 + 2 * (r * k * k / 2)
+        final = (r + c) * k * k + r * k * k + c * k * k + c * r * k
         ff = first_ff + (it - 1) * per_iter + final
-        return 32 * (ff + first_fp32 * 16.0 / FF_OPS_PER_QMAC)
+        return 32 * (ff + fp32 * 16.0 / FF_OPS_PER_QMAC)
     # subspace iteration: W Omega, W^H Q0, W P1, W^H Q1, W T (5 r c k); seven
     # Hermitian Grams (rows k^2 / 2) and Cholesky factorisations (k^3 / 6);
     # ten triangular solves (rows k^2 / 2); U = (P R1^-1 R2^-1) Q^H (c r k).
