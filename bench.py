@@ -408,7 +408,7 @@ def fp64_check(Q, A, D, w, prec, sampler, stream, steps=10, warmup=3, rows=256):
 # ncu capture of the current code, per kernel (profiles/), on the 2048 x 2048
 # workload: the tensor-core Z = C T with the fused residual (mixed split) and
 # the refined pseudo-inverse of its 200 x 200 intersection.
-NCU_TRAFFIC = {"gemm_z": 81.91e6 + 2.24e6, "pinv_refine": 30.99e6 + 429.53e6}
+NCU_TRAFFIC = {"gemm_z": 81.91e6 + 2.24e6, "pinv_refine": 30.31e6 + 430.36e6}
 
 
 def peaks():
@@ -738,8 +738,8 @@ def run_ours(args):
     if dom == "pinv" and args.pinv == "refined" and workload_name(args) == WORKLOAD:
         roof["traffic"] = NCU_TRAFFIC["pinv_refine"]
         roof["traffic_note"] = ("almost all writes: write-backs of the split-tile partials "
-                                "and float-float intermediates of its 27 steps (460 MB in "
-                                "the 0.93 ms capture, 490 GB/s); the kernel reads W once "
+                                "and float-float intermediates of its 27 steps (461 MB in "
+                                "the 0.92 ms capture, 500 GB/s); the kernel reads W once "
                                 "(1.3 MB)")
 
     # the GEMM stage: tensor work of the split (products x quaternion flops)
