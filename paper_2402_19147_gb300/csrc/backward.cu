@@ -16,7 +16,7 @@
 
 namespace qmcur {
 
-size_t residual_partials(int64_t m, int64_t n);
+__global__ void k_residual_fold(const double* partial, int64_t count, double* out3);
 size_t tc_gemm_ws_bytes(int64_t M, int64_t N, int64_t K, int32_t prec);
 qmcur_status tc_gemm(const QView& X, bool xh, const QView& Y, bool yh, int64_t M, int64_t N,
                      int64_t K, float alpha, const QView& Z, int32_t prec, void* ws,
@@ -40,21 +40,64 @@ __global__ void k_to_qptr_f32(QView in, QPtr out) {
   }
 }
 
-// E = mask * (A - Z), in place over Z; dA = 2 s E.
-__global__ void k_residual_matrix(QView A, const uint8_t* __restrict__ mask, QPtr Z, QView dA,
-                                  float two_s) {
-  const int64_t m = A.rows, n = A.cols, total = m * n;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / n, j = e % n;
-    const bool on = mask == nullptr || mask[e] != 0;
+// E = mask * (A - Z), in place over Z; dA = 2 s E; and the loss's sums.
+// One CTA per kLossRows x 256 tile (the standalone residual's tiling, so
+// that its partial count and k_residual_fold apply), one column per thread:
+// partial[2 cta] = sum |e|^2, partial[2 cta + 1] = sum over Omega of |a|^2,
+// FP32 over the thread's at most 4 kLossRows terms, FP64 from there on.
+constexpr int kLossRows = 8;
+
+__global__ void __launch_bounds__(256)
+k_residual_matrix(QView A, const uint8_t* __restrict__ mask, QPtr Z, QView dA, float two_s,
+                  double* __restrict__ partial) {
+  const int64_t m = A.rows, n = A.cols;
+  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.y * kLossRows;
+  float num = 0.f, den = 0.f;
+  if (j < n) {
+    // every load of the tile's column first, then the sums and stores
+    float av[kLossRows][4], zv[kLossRows][4];
+    bool on[kLossRows];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      float* z = reinterpret_cast<float*>(Z.p[t]) + i * Z.ld + j;
-      const float ev = on ? (float)ld_as_double(A, t, i, j) - *z : 0.f;
-      *z = ev;
-      st_from_double(dA, t, i, j, (double)(two_s * ev));
+    for (int rr = 0; rr < kLossRows; ++rr) {
+      const int64_t i = i0 + rr;
+      const bool in = i < m;
+      on[rr] = in && (mask == nullptr || mask[i * n + j] != 0);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        av[rr][t] = in ? (float)ld_as_double(A, t, i, j) : 0.f;
+        zv[rr][t] = in ? reinterpret_cast<const float*>(Z.p[t])[i * Z.ld + j] : 0.f;
+      }
     }
+#pragma unroll
+    for (int rr = 0; rr < kLossRows; ++rr) {
+      const int64_t i = i0 + rr;
+      if (i >= m) break;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float ev = on[rr] ? av[rr][t] - zv[rr][t] : 0.f;
+        reinterpret_cast<float*>(Z.p[t])[i * Z.ld + j] = ev;
+        st_from_double(dA, t, i, j, (double)(two_s * ev));
+        num = fmaf(ev, ev, num);
+        den = on[rr] ? fmaf(av[rr][t], av[rr][t], den) : den;
+      }
+    }
+  }
+  __shared__ double red[2][256];
+  red[0][threadIdx.x] = (double)num;
+  red[1][threadIdx.x] = (double)den;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int64_t cta = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    partial[2 * cta] = red[0][0];
+    partial[2 * cta + 1] = red[1][0];
   }
 }
 
@@ -96,6 +139,10 @@ QPtr sub_q(const QPtr& q, int64_t r0, int64_t c0) {
   QPtr v = q;
   for (int t = 0; t < 4; ++t) v.p[t] = reinterpret_cast<float*>(q.p[t]) + r0 * q.ld + c0;
   return v;
+}
+
+int64_t loss_partials(int64_t m, int64_t n) {
+  return ((m + kLossRows - 1) / kLossRows) * ((n + 255) / 256);
 }
 
 QPtr take_q(Carve& cv, int64_t rows, int64_t cols) {
@@ -157,7 +204,7 @@ BwdWs carve_bwd(Carve& cv, int64_t m, int64_t n, int64_t c, int64_t r) {
   w.XL = take_q(cv, r, r + c);
   w.YL = take_q(cv, r + c, c);
   w.GW = take_q(cv, r, c);
-  w.partial = cv.take<double>(2 * residual_partials(m, n));
+  w.partial = cv.take<double>(2 * loss_partials(m, n));
   w.out3 = cv.take<double>(4);
   w.tc_bytes = bwd_tc_bytes(m, n, c, r);
   w.tc = cv.take<char>(w.tc_bytes);
@@ -211,21 +258,18 @@ qmcur_status launch_backward(const qmcur_qmat* A, const uint8_t* mask, const int
     return tc_gemm(X, xh, Y, yh, M, N, K, alpha, qv(Z, M, N), kBwdTcPrec, w.tc, w.tc_bytes,
                    dev_status, st);
   };
-  // forward pieces: T = U R, Z = C T (into E), loss, E = P_Omega(A - Z), dA = 2 s E
+  // forward pieces: T = U R, Z = C T (into E); then in one pass
+  // E = P_Omega(A - Z), dA = 2 s E and the loss's sums, folded in order
   if ((e = tc(vU, false, vR, false, c, n, r, 1.f, w.T)) != QMCUR_OK) return e;
   if ((e = tc(vC, false, vT, false, m, n, c, 1.f, w.E)) != QMCUR_OK) return e;
   {
-    qmcur_qmat Zq;
-    for (int t = 0; t < 4; ++t) Zq.plane[t] = w.E.p[t];
-    Zq.rows = m; Zq.cols = n; Zq.ld = w.E.ld; Zq.dtype = QMCUR_F32; Zq.reserved = 0;
-    if ((e = launch_residual_standalone(A, &Zq, mask, w.out3, w.partial,
-                                        (size_t)(2 * residual_partials(m, n)) * 8 + 256, dev_status,
-                                        st)) != QMCUR_OK)
-      return e;
+    const dim3 lgrid((unsigned)((n + 255) / 256), (unsigned)((m + kLossRows - 1) / kLossRows));
+    if (lgrid.y > 65535) return QMCUR_ERR_UNSUPPORTED;
+    k_residual_matrix<<<lgrid, 256, 0, st>>>(view(A), mask, w.E, view(dA), 2.f * s, w.partial);
+    k_residual_fold<<<1, 1024, 0, st>>>(w.partial, loss_partials(m, n), w.out3);
     if (loss_out != nullptr)
       cudaMemcpyAsync(loss_out, w.out3 + 1, sizeof(double), cudaMemcpyDeviceToDevice, st);
   }
-  k_residual_matrix<<<blocks_for(m * n), 256, 0, st>>>(view(A), mask, w.E, view(dA), 2.f * s);
   // adjoints of the two GEMMs (the conjugate transposes of Sec. 2.2: X^H Y
   // and X Y^H, never plain transposes, which do not reverse quaternion products)
   if ((e = tc(vE, false, vT, true, m, c, n, -2.f * s, w.GC)) != QMCUR_OK) return e;
