@@ -170,3 +170,37 @@ def test_batch_refined_reports_a_problem_without_gap():
         kap = so[0] / so[ko - 1]
         assert rel_fro(host(B.get(b, "U64")), Uo) < 1e-12 * max(1.0, kap), b
     B.close()
+
+
+def test_batch_tensor_core_ragged_shapes():
+    # shapes that fill no tile exactly (n and m off the 64- and 128-wide
+    # tiles, c and r odd): the grouped T = U R stores and the grouped
+    # Z = C T residuals mask every edge; against the oracle's residual of the
+    # same U and the FP32 plan's, within 1e-5, for both cores
+    shapes = [(70, 100, 7), (131, 250, 13), (64, 65, 5), (257, 63, 20), (90, 333, 31), (45, 77, 9)]
+    probs = []
+    for s_, (m, n, k) in enumerate(shapes):
+        X, _ = synth.lowrank_gaussian(m, n, k, seed=40 + s_, noise_rel=1e-4)
+        probs.append(dict(X=X, m=m, n=n, rank=k, c=min(2 * k + 1, n), r=min(2 * k + 1, m)))
+    As = [dev(p["X"]) for p in probs]
+    args = ([p["c"] for p in probs], [p["r"] for p in probs], [p["rank"] for p in probs])
+    for method in (Q.PINV_REFINED_FP64, Q.PINV_SUBSPACE_FP32):
+        kw = dict(sampler=Q.SAMPLER_NORM, seed=21, pinv_method=method)
+        F = Q.Batch(As, *args, prec=Q.PREC_FP32, **kw)
+        T = Q.Batch(As, *args, prec=Q.PREC_BF16_MIXED, **kw)
+        F.run()
+        T.run()
+        torch.cuda.synchronize()
+        assert int(F.status.item()) == 0 and int(T.status.item()) == 0
+        for b, p in enumerate(probs):
+            U = host(T.get(b, "U"))
+            assert np.array_equal(U, host(F.get(b, "U")))
+            A64 = p["X"].astype(np.float64)
+            Co = host(T.get(b, "C")).astype(np.float64)
+            Ro = A64[:, host(T.get(b, "I")), :]
+            rel_o = O.residual(A64, O.reconstruct(Co, U.astype(np.float64), Ro))[0]
+            rel, rel_f = host(T.get(b, "out3"))[0], host(F.get(b, "out3"))[0]
+            assert abs(rel - rel_o) < 1e-5, (method, b, rel, rel_o)
+            assert abs(rel - rel_f) < 1e-5, (method, b, rel, rel_f)
+        F.close()
+        T.close()
