@@ -59,7 +59,6 @@ qmcur_status refine_each_launch(const void* dargs, const int* dorder, int count,
                                 int32_t* batch_status, cudaStream_t st);
 
 constexpr int kBatchMaxCore = 80;      // largest min(r, c) held by k_batch_jacobi
-constexpr int kBatchTBn = 64;          // tile width of the grouped tensor-core T = U R
 constexpr int64_t kBatchCoreSmem = 200 * 1024;   // bytes of G and V in shared memory
 
 struct BatchProblem {
@@ -531,9 +530,10 @@ struct BatchPlan {
   TcGroupProb* dgprobs = nullptr;
   TcGroupTile* dgtiles = nullptr;
   int ngtiles = 0, tc_bn = 128;
-  // T = U R on the tensor cores (the split of T in the precision, e.g. BF16X6
-  // under the mixed split): every problem's U (c x r) as rows of A1_all, its
-  // R^T (n x r) as rows of B1_all, K padded to the largest r
+  // T = U R on the tensor cores, as T^T = R^T U in the split of T (BF16X6
+  // under the mixed split) with its epilogue writing Z = C T's B pieces:
+  // every problem's R^T (n x r) as rows of A1_all, its U (c x r) as rows of
+  // B1_all, K padded to the largest r
   void* A1_all = nullptr;
   void* B1_all = nullptr;
   int64_t rows_a1 = 0, rows_b1 = 0, kpad1 = 0;
@@ -579,8 +579,9 @@ static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st, bool timed = fa
   if (p->tc) {
     qmcur_status s = tc_group_split(p->opts.prec, p->djobs1, p->njobs1, p->split_tiles1, st, 0);
     if (s != QMCUR_OK) return s;
-    s = tc_group_store(p->opts.prec, kBatchTBn, p->A1_all, p->rows_a1, p->B1_all, p->rows_b1,
-                       p->kpad1, p->dgtiles1, p->ngtiles1, p->dgprobs1, p->status, st);
+    s = tc_group_t_pieces(p->opts.prec, p->A1_all, p->rows_a1, p->B1_all, p->rows_b1, p->kpad1,
+                          p->dgtiles1, p->ngtiles1, p->dgprobs1, p->B_all, p->kpad, p->rows_b,
+                          p->status, st);
     if (s != QMCUR_OK) return s;
   } else {
     launch_batch_gemm(p->cfg1, p->dprobs, p->dtiles1, p->ntiles1, 0, nullptr, st);
@@ -744,22 +745,24 @@ static void free_plan(BatchPlan* p) {
 
 using namespace qmcur;
 
-// T = U R on the tensor cores for a split precision: the stacked pieces of
-// every problem's U (A operand, rows c) and R^T (B operand, rows n), the
-// split jobs that cut them, the problem table (output T, K = r) and the tile
-// list (the c rows of a problem in one 128-row tile, its n columns in
-// kBatchTBn-wide tiles).
-static qmcur_status build_t_stage(BatchPlan* p, cudaStream_t stream) {
+// T = U R on the tensor cores for a split precision, as T^T = R^T U: the
+// stacked pieces of every problem's R^T (A operand, rows n) and U (B
+// operand, rows c), the split jobs that cut them, the problem table (K = r;
+// zrow = the problem's first row zrow[b] of Z = C T's B operand, which the
+// epilogue fills with T's pieces) and the tile list (n in 128-row tiles, c
+// in kGroupTBn-wide ones).
+static qmcur_status build_t_stage(BatchPlan* p, const std::vector<int64_t>& zrow,
+                                  cudaStream_t stream) {
   const int32_t pr = p->opts.prec;
   const int64_t epr = tc_group_epr(pr, 0);
   const int count = p->count;
-  std::vector<int64_t> arow(count), brow(count);
+  std::vector<int64_t> rrow(count), urow(count);
   int64_t rmax = 1;
   for (int b = 0; b < count; ++b) {
-    arow[b] = p->rows_a1;
-    brow[b] = p->rows_b1;
-    p->rows_a1 += p->host[b].c;
-    p->rows_b1 += p->host[b].n;
+    rrow[b] = p->rows_a1;
+    urow[b] = p->rows_b1;
+    p->rows_a1 += p->host[b].n;
+    p->rows_b1 += p->host[b].c;
     rmax = std::max<int64_t>(rmax, p->host[b].r);
   }
   p->kpad1 = (rmax + epr - 1) / epr * epr;
@@ -793,25 +796,19 @@ static qmcur_status build_t_stage(BatchPlan* p, cudaStream_t stream) {
   };
   for (int b = 0; b < count; ++b) {
     const BatchProblem& P = p->host[b];
-    add_job(P.U, false, p->A1_all, P.c, P.r, arow[b], p->rows_a1);   // A[i][k] = U[i][k]
-    add_job(P.R, true, p->B1_all, P.n, P.r, brow[b], p->rows_b1);    // B[j][k] = R[k][j]
+    add_job(P.R, true, p->A1_all, P.n, P.r, rrow[b], p->rows_a1);    // A[j][k] = R[k][j]
+    add_job(P.U, false, p->B1_all, P.c, P.r, urow[b], p->rows_b1);   // B[i][k] = U[i][k]
     TcGroupProb& g = gp[b];
     g = TcGroupProb{};
-    g.m = P.c;
-    g.n = P.n;
+    g.m = P.n;
+    g.n = P.c;
     g.K = P.r;
     g.kblocks = (int)(((P.r + epr - 1) / epr * epr) / epr);
-    g.arow = (int)arow[b];
-    g.brow = (int)brow[b];
-    bool zv = P.T.ld % 4 == 0;
-    for (int t = 0; t < 4; ++t) {
-      g.z[t] = reinterpret_cast<float*>(P.T.p[t]);
-      zv = zv && reinterpret_cast<uintptr_t>(P.T.p[t]) % 16 == 0;
-    }
-    g.ldz = P.T.ld;
-    g.z_vec = zv ? 1 : 0;
-    for (int m0 = 0; m0 < P.c; m0 += 128)
-      for (int n0 = 0; n0 < P.n; n0 += kBatchTBn) tiles.push_back(TcGroupTile{b, m0, n0});
+    g.arow = (int)rrow[b];
+    g.brow = (int)urow[b];
+    g.zrow = zrow[b];
+    for (int m0 = 0; m0 < P.n; m0 += 128)
+      for (int n0 = 0; n0 < P.c; n0 += kGroupTBn) tiles.push_back(TcGroupTile{b, m0, n0});
   }
   p->njobs1 = (int)jobs.size();
   p->split_tiles1 = stiles;
@@ -1037,7 +1034,7 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     for (int b = 0; b < count; ++b) {
       const BatchProblem& P = p->host[b];
       add_job(P.C, false, p->A_all, P.m, P.c, arow[b], p->rows_a);   // A[i][k] = C[i][k]
-      add_job(P.T, true, p->B_all, P.n, P.c, brow[b], p->rows_b);    // B[j][k] = T[k][j]
+      // (B[j][k] = T[k][j] is written by the T stage's epilogue)
       TcGroupProb& g = gp[b];
       bool av = P.A.ld % 4 == 0;
       for (int t = 0; t < 4; ++t) {
@@ -1063,7 +1060,7 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     cudaMemcpyAsync(p->djobs, jobs.data(), jobs.size() * sizeof(TcSplitJob), cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(p->dgprobs, gp.data(), gp.size() * sizeof(TcGroupProb), cudaMemcpyHostToDevice, stream);
     if (cudaStreamSynchronize(stream) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
-    const qmcur_status st1 = build_t_stage(p, stream);
+    const qmcur_status st1 = build_t_stage(p, brow, stream);
     if (st1 != QMCUR_OK) { free_plan(p); return st1; }
   }
   // first pass (un-captured): fills T and the operands so that the GEMM
@@ -1173,7 +1170,7 @@ qmcur_status qmcur_batch_view(const void* plan, int32_t index, qmcur_batch_item*
   out->col_p = P.col_p; out->row_p = P.row_p; out->J = P.J; out->I = P.I;
   out->C = toq(P.C); out->R = toq(P.R); out->W = toq(P.W); out->U = toq(P.U);
   out->out3 = P.out3; out->info = P.info;
-  out->gemm_tiles[0] = p->tc ? kBatchTBn : kCfgs[p->cfg1].bm;
+  out->gemm_tiles[0] = p->tc ? kGroupTBn : kCfgs[p->cfg1].bm;
   out->gemm_tiles[1] = p->tc ? p->tc_bn : kCfgs[p->cfg2].bm;
   return QMCUR_OK;
 }

@@ -92,11 +92,12 @@ constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 // MODE_GROUPED is MODE_RESIDUAL over the tiles of many problems (tc_group.cuh):
 // each tile's coordinates, inner dimension and A come from the group tables,
 // and its partials go to partial[2 tile], with no fold in the kernel.
-// MODE_GROUPED_STORE is MODE_STORE_Z over the tiles of many problems: each
-// tile stores into its problem's own output (group tables), masked by that
-// problem's m and n.
+// MODE_GROUPED_PIECES (with REV: the tiles of T^T = R^T U of many problems)
+// cuts each output value into the pieces of the next product's split and
+// stores them K-major at the problem's rows of that product's stacked B
+// operand: row = the tile row (a column of T), k = the tile column.
 enum { MODE_STORE_Z = 0, MODE_RESIDUAL = 1, MODE_STORE_ZT = 2, MODE_COMPLETE = 3, MODE_GROUPED = 4,
-       MODE_GROUPED_STORE = 5 };
+       MODE_GROUPED_PIECES = 5 };
 
 struct TcParams {
   int M, N;
@@ -123,6 +124,11 @@ struct TcParams {
   const TcGroupTile* gtiles;
   const TcGroupProb* gprobs;
   int gcount;
+  // MODE_GROUPED_PIECES: the stacked piece buffer, its row width (elements),
+  // plane stride (elements) and pieces per value
+  void* pieces;
+  int64_t pk_kpad, pk_plane;
+  int pk_npieces;
 };
 
 // ------------------------------------------------------------- PTX helpers -
@@ -300,7 +306,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
   constexpr uint32_t kIdPos = make_idesc(BF16, false, BN), kIdNeg = make_idesc(BF16, true, BN);
   constexpr int kElemsPerRow = ROWB / (BF16 ? 2 : 4);
   constexpr int kStepElems = 32 / (BF16 ? 2 : 4);          // K of one MMA (32 bytes)
-  constexpr bool grouped = MODE == MODE_GROUPED || MODE == MODE_GROUPED_STORE;
+  constexpr bool grouped = MODE == MODE_GROUPED || MODE == MODE_GROUPED_PIECES;
   constexpr bool sums_mode = MODE == MODE_RESIDUAL || MODE == MODE_COMPLETE || MODE == MODE_GROUPED;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -431,9 +437,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
     // the current tile's problem (the group tables, or p itself)
     // (grouped only; otherwise the accessors below read p directly)
     int Mv = 0, Nv = 0, avec = 0;
-    float* zg[4] = {nullptr, nullptr, nullptr, nullptr};   // MODE_GROUPED_STORE: the problem's output
-    int64_t ldzg = 0;
-    int zgvec = 0;
+    int64_t zrowg = 0;   // MODE_GROUPED_PIECES: the problem's first row in the piece buffer
     int64_t ldav = 0;
     const float* ap[4] = {nullptr, nullptr, nullptr, nullptr};
     auto EM = [&]() -> int { if constexpr (grouped) return Mv; else return p.M; };
@@ -476,12 +480,7 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
         ldav = gp.lda;
 #pragma unroll
         for (int pl = 0; pl < 4; ++pl) ap[pl] = gp.a[pl];
-        if constexpr (MODE == MODE_GROUPED_STORE) {
-#pragma unroll
-          for (int pl = 0; pl < 4; ++pl) zg[pl] = gp.z[pl];
-          ldzg = gp.ldz;
-          zgvec = gp.z_vec;
-        }
+        if constexpr (MODE == MODE_GROUPED_PIECES) zrowg = gp.zrow;
         row = tl.m0 + sp * 32 + lane;
         n0 = tl.n0;
       } else {
@@ -598,18 +597,45 @@ k_qgemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUt
             float z[16];
             tmem_ld16(tb + pl * BN + ch * 16, z);
             const int c0 = n0 + ch * 16;
-            if constexpr (MODE == MODE_GROUPED_STORE) {
+            if constexpr (MODE == MODE_GROUPED_PIECES) {
               if (row < Mv) {
-                float* zr = zg[pl] + (int64_t)row * ldzg + c0;
-                if (c0 + 16 <= Nv && zgvec) {
+                const int64_t rowoff = (zrowg + row) * p.pk_kpad + c0;
+                const int nv = Nv - c0 < 16 ? Nv - c0 : 16;   // valid columns (k) of the chunk
+                float pc[3][16];
 #pragma unroll
-                  for (int q = 0; q < 4; ++q)
-                    reinterpret_cast<float4*>(zr)[q] =
-                        make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
-                } else {
+                for (int j = 0; j < 16; ++j) {
+                  float q3[3];
+                  split_value<BF16, float>(z[j], p.pk_npieces, q3);
+                  pc[0][j] = q3[0];
+                  pc[1][j] = q3[1];
+                  pc[2][j] = q3[2];
+                }
 #pragma unroll
-                  for (int j = 0; j < 16; ++j)
-                    if (c0 + j < Nv) zr[j] = z[j];
+                for (int q = 0; q < 3; ++q) {
+                  if (q >= p.pk_npieces) break;
+                  const int64_t base = (int64_t)(q * 4 + pl) * p.pk_plane + rowoff;
+                  if constexpr (BF16) {
+                    __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(p.pieces) + base;
+                    if (nv == 16) {
+                      uint32_t w[8];
+#pragma unroll
+                      for (int h = 0; h < 8; ++h) {
+                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(pc[q][2 * h], pc[q][2 * h + 1]);
+                        w[h] = *reinterpret_cast<const uint32_t*>(&b2);
+                      }
+                      reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                      reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                    } else {
+#pragma unroll
+                      for (int j = 0; j < 16; ++j)
+                        if (j < nv) dst[j] = __float2bfloat16_rn(pc[q][j]);
+                    }
+                  } else {
+                    float* dst = reinterpret_cast<float*>(p.pieces) + base;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                      if (j < nv) dst[j] = pc[q][j];
+                  }
                 }
               }
             } else if constexpr (MODE == MODE_STORE_ZT) {
@@ -1125,7 +1151,7 @@ qmcur_status launch_gemm_mode(const CUtensorMap& ma, const CUtensorMap& mb, cons
   }
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return QMCUR_ERR_CUDA;
-  const int items = (MODE == MODE_GROUPED || MODE == MODE_GROUPED_STORE) ? p.gcount
+  const int items = (MODE == MODE_GROUPED || MODE == MODE_GROUPED_PIECES) ? p.gcount
                                          : ((p.M + BM - 1) / BM) * ((p.N + BNT - 1) / BNT) * p.nsplit;
   const int cap = cta_cap(sms);
   const int grid = items < cap ? items : cap;
@@ -1566,32 +1592,34 @@ qmcur_status tc_group_residual(int32_t prec, int bn, const void* A_all, int64_t 
                   : launch_gemm_mode<false, 128, false, MODE_GROUPED>(mA, mB, p, st);
 }
 
-qmcur_status tc_group_store(int32_t prec, int bn, const void* A_all, int64_t rows_a,
-                            const void* B_all, int64_t rows_b, int64_t kpad,
-                            const TcGroupTile* tiles, int ntiles, const TcGroupProb* probs,
-                            int32_t* dev_status, cudaStream_t st) {
-  if (ntiles < 1 || (bn != 64 && bn != 128)) return QMCUR_ERR_INVALID_ARG;
-  const TcPlan pl = group_plan(prec, 0);
+qmcur_status tc_group_t_pieces(int32_t prec, const void* R_all, int64_t rows_r, const void* U_all,
+                               int64_t rows_u, int64_t kpad, const TcGroupTile* tiles, int ntiles,
+                               const TcGroupProb* probs, void* pieces, int64_t pieces_kpad,
+                               int64_t pieces_rows, int32_t* dev_status, cudaStream_t st) {
+  if (ntiles < 1 || pieces == nullptr) return QMCUR_ERR_INVALID_ARG;
+  const TcPlan pl = group_plan(prec, 0), pz = group_plan(prec, 1);
+  if (pl.bf16 != pz.bf16) return QMCUR_ERR_UNSUPPORTED;   // the pieces take the MMA's type
   CUtensorMap mA, mB;
-  if (!make_map(&mA, const_cast<void*>(A_all), pl.bf16, rows_a, kpad, pl.npieces, BM) ||
-      !make_map(&mB, const_cast<void*>(B_all), pl.bf16, rows_b, kpad, pl.npieces, bn))
+  if (!make_map(&mA, const_cast<void*>(R_all), pl.bf16, rows_r, kpad, pl.npieces, BM) ||
+      !make_map(&mB, const_cast<void*>(U_all), pl.bf16, rows_u, kpad, pl.npieces, kGroupTBn))
     return QMCUR_ERR_CUDA;
   TcParams p{};
   p.M = 1;
   p.N = 1;
   p.nterms = pl.nterms;
-  for (int i = 0; i < 6; ++i) { p.ta[i] = pl.ta[i]; p.tb[i] = pl.tb[i]; }
-  p.mode = MODE_GROUPED_STORE;
+  for (int i = 0; i < 6; ++i) { p.ta[i] = pl.tb[i]; p.tb[i] = pl.ta[i]; }   // R's piece, U's piece
+  p.mode = MODE_GROUPED_PIECES;
   p.nsplit = 1;
   p.status = dev_status;
   p.gtiles = tiles;
   p.gprobs = probs;
   p.gcount = ntiles;
-  if (pl.bf16)
-    return bn == 64 ? launch_gemm_mode<true, 64, false, MODE_GROUPED_STORE>(mA, mB, p, st)
-                    : launch_gemm_mode<true, 128, false, MODE_GROUPED_STORE>(mA, mB, p, st);
-  return bn == 64 ? launch_gemm_mode<false, 64, false, MODE_GROUPED_STORE>(mA, mB, p, st)
-                  : launch_gemm_mode<false, 128, false, MODE_GROUPED_STORE>(mA, mB, p, st);
+  p.pieces = pieces;
+  p.pk_kpad = pieces_kpad;
+  p.pk_plane = pieces_rows * pieces_kpad;
+  p.pk_npieces = pz.npieces;
+  if (pl.bf16) return launch_gemm_mode<true, kGroupTBn, true, MODE_GROUPED_PIECES>(mA, mB, p, st);
+  return launch_gemm_mode<false, kGroupTBn, true, MODE_GROUPED_PIECES>(mA, mB, p, st);
 }
 
 }  // namespace qmcur

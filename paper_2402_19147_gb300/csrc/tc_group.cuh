@@ -14,17 +14,19 @@ struct TcGroupTile {
   int prob, m0, n0;
 };
 
-// What the grouped kernel needs of one problem: its input A (residual) or
-// its output Z (store), shape, inner dimension K and its pieces' k-blocks,
-// and the first rows of its operands in the stacked buffers.
+// What the grouped kernel needs of one problem: its input A (residual),
+// shape, inner dimension K and its pieces' k-blocks, the first rows of its
+// operands in the stacked buffers, and (pieces' store) its first row in the
+// output piece buffer.
 struct TcGroupProb {
   const float* a[4];
   int64_t lda;
   int m, n, K, kblocks, arow, brow, a_vec;
-  float* z[4];          // the store's output planes (row stride ldz)
-  int64_t ldz;
-  int z_vec;            // planes 16-byte aligned and ldz % 4 == 0
+  int64_t zrow;
 };
+
+// Tile width (columns of T^T, i.e. rows of T) of the grouped T^T = R^T U.
+constexpr int kGroupTBn = 64;
 
 // One operand of one problem for the batched split: S (rows x K as stored,
 // or K x rows when trans) into rows row0 .. row0 + rows of a stacked piece
@@ -49,12 +51,16 @@ size_t tc_group_piece_bytes(int32_t prec, int64_t rows, int64_t kpad, int produc
 // The batched split of the jobs (device table, tiles in all) into pieces.
 qmcur_status tc_group_split(int32_t prec, const TcSplitJob* jobs, int njobs, int tiles,
                             cudaStream_t st, int product = 1);
-// The grouped T = U R (T = A_all B_all^T per problem, the split of product
-// 0), each tile stored into its problem's z planes, masked by its m and n.
-qmcur_status tc_group_store(int32_t prec, int bn, const void* A_all, int64_t rows_a,
-                            const void* B_all, int64_t rows_b, int64_t kpad,
-                            const TcGroupTile* tiles, int ntiles, const TcGroupProb* probs,
-                            int32_t* dev_status, cudaStream_t st);
+// The grouped T^T = R^T U (the split of product 0; R_all holds every
+// problem's R^T pieces, rows n, U_all its U pieces, rows c, K = r), each
+// tile cut into the pieces of product 1's split and stored K-major at rows
+// zrow + (0 .. n) of `pieces` (pieces_rows rows of pieces_kpad elements per
+// plane and piece): Z = C T's B operand, with T never stored.
+qmcur_status tc_group_t_pieces(int32_t prec, const void* R_all, int64_t rows_r, const void* U_all,
+                               int64_t rows_u, int64_t kpad, const TcGroupTile* tiles, int ntiles,
+                               const TcGroupProb* probs, void* pieces, int64_t pieces_kpad,
+                               int64_t pieces_rows, int32_t* dev_status, cudaStream_t st);
+
 // The grouped Z = C T with the residual: partial[2 t], partial[2 t + 1] =
 // sum |a - z|^2, sum |a|^2 over tile t of the device tile list.
 qmcur_status tc_group_residual(int32_t prec, int bn, const void* A_all, int64_t rows_a,
