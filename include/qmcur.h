@@ -447,8 +447,9 @@ qmcur_status qmcur_complete_step(qmcur_qmat* X, const uint8_t* mask, int64_t c, 
  * split operands of all problems, stacked along rows (the plan allocates
  * them), with its tile width (128 or 64 columns) chosen by timing both.
  * T = U R runs in FP32 on the CUDA cores under QMCUR_PREC_FP32 (or FP64);
- * under a split precision it is one grouped tcgen05 launch too, in the
- * split of T (BF16X6 under BF16_MIXED), 64-column tiles.  dev_status
+ * under a split precision it is one grouped tcgen05 launch too, as
+ * T^T = R^T U in the split of T (BF16X6 under BF16_MIXED), whose epilogue
+ * writes Z's operand pieces directly (T itself is not stored).  dev_status
  * (device int32, may be NULL) receives the first error; per-problem errors
  * also land in info[2] of the problem.  The plan keeps the pointers it was
  * given: A[b] and dev_status must stay valid until qmcur_batch_destroy.
