@@ -408,7 +408,8 @@ def fp64_check(Q, A, D, w, prec, sampler, stream, steps=10, warmup=3, rows=256):
 # ncu capture of the current code, per kernel (profiles/), on the 2048 x 2048
 # workload: the tensor-core Z = C T with the fused residual (mixed split) and
 # the refined pseudo-inverse of its 200 x 200 intersection.
-NCU_TRAFFIC = {"gemm_z": 81.91e6 + 2.24e6, "pinv_refine": 30.31e6 + 430.36e6}
+NCU_TRAFFIC = {"gemm_z": 81.91e6 + 2.24e6, "pinv_refine": 30.31e6 + 430.36e6,
+               "refine_each": 468.51e6 + 2106.71e6}
 
 
 def peaks():
@@ -819,7 +820,8 @@ def run_ours(args):
         bl = batch_measure(args, Q, synth, dev, 10, 3)
         line["extra"]["batch512_uneven"] = {k: bl[k] for k in (
             "value", "unit", "ms_per_step", "steps", "warmup", "config", "fp32_gemms",
-            "speedup_over_fp32", "residual_max_abs_diff_vs_fp32", "z_product", "fp32_subspace_core")}
+            "speedup_over_fp32", "residual_max_abs_diff_vs_fp32", "z_product", "fp32_subspace_core",
+            "roofline")}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -1046,13 +1048,32 @@ def batch_measure(args, Q, synth, dev, steps, warmup):
     tpk = pk["bf16_tflops"] * (0.5 if split == "tf32x3" else 1.0)
     hpk = pk["hbm_gbs"] * (nprod * flz / zbytes) / 1e3
     zach = nprod * flz / (zms / 1e3) / 1e12
-    roof = {"kernel": "k_split_table + k_qgemm_tc (grouped, residual epilogue)",
-            "bound": "tensor" if tpk <= hpk else "hbm", "achieved": zach, "peak": min(tpk, hpk),
-            "unit": "TFLOP/s", "frac": zach / min(tpk, hpk), "traffic": None,
-            "work": "%d BF16 products x 32 m c n per problem; bytes 16 (m n + m c + c n)" % nprod,
-            "intensity_flop_per_byte": nprod * flz / zbytes, "stage_ms": zms,
-            "tensor_peak": tpk, "hbm_bound_tflops": hpk,
-            "peak_source": "measured BF16 burst and HBM copy (" + pk_kind + ")"}
+    zroof = {"kernel": "k_split_table + k_qgemm_tc (grouped, residual epilogue)",
+             "bound": "tensor" if tpk <= hpk else "hbm", "achieved": zach, "peak": min(tpk, hpk),
+             "unit": "TFLOP/s", "frac": zach / min(tpk, hpk), "traffic": None,
+             "work": "%d BF16 products x 32 m c n per problem; bytes 16 (m n + m c + c n)" % nprod,
+             "intensity_flop_per_byte": nprod * flz / zbytes, "stage_ms": zms,
+             "tensor_peak": tpk, "hbm_bound_tflops": hpk,
+             "peak_source": "measured BF16 burst and HBM copy (" + pk_kind + ")"}
+    roof = zroof
+    if core == "refined":
+        # the dominant stage: the FP64-accurate core, one problem per CTA, its
+        # work counted per problem from the step shapes at the iterations
+        # that problem took (info[1]), against the float-float peak
+        its = [int(plans[split].get(b, "info")[1].item()) for b in range(len(probs))]
+        cwork = sum(pinv_flops(dict(c=p["c"], r=p["r"], rank_cap=p["rank"]), "refined", it)
+                    for p, it in zip(probs, its))
+        cms = stages[split]["core"]
+        cach = cwork / (cms / 1e3) / 1e12
+        roof = {"kernel": "k_pinv_refine_each", "bound": "alu", "achieved": cach,
+                "peak": alu_peak_tflops("ff"), "unit": "TFLOP/s",
+                "frac": cach / alu_peak_tflops("ff"), "traffic": NCU_TRAFFIC["refine_each"],
+                "work": "%.4g flops per launch: the refined core's step shapes per problem at "
+                        "its iterations (%d to %d)" % (cwork, min(its), max(its)),
+                "stage_ms": cms,
+                "peak_source": "float-float on the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz / "
+                               "%d instructions per quaternion multiply-add (32 flops)"
+                               % FF_OPS_PER_QMAC}
     line = {"metric": METRIC, "value": 512 / (ms / 1e3), "unit": "decompositions/s",
             "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": split,
@@ -1070,6 +1091,7 @@ def batch_measure(args, Q, synth, dev, steps, warmup):
                                     "note": "split GEMMs, the FP32 subspace core (not FP64-accurate)"}
                                    if "fp32_core" in res else None),
             "stage_ms": stages[split], "stage_ms_fp32": stages["fp32"], "roofline": roof,
+            "z_roofline": zroof,
             "residual_max_abs_diff_vs_fp32": float(np.max(np.abs(rel[split] - rel["fp32"]))),
             "gemm_qtflops_per_step": fl / (ms / 1e3) / 1e12,
             "input_gbs_per_step": byts / (ms / 1e3) / 1e9,
