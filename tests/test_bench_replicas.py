@@ -114,8 +114,17 @@ def test_refined_pinv_flop_count_follows_the_shapes():
     sys.path.insert(0, ROOT)
     import bench
     w = {"c": 200, "r": 200, "rank_cap": 50}
-    # three iterations: the first product, three of the per-iteration set, the final set
-    per_iter = 2 * 200 * 200 * 50 + 4 * 200 * 50 * 50 + 50 ** 3 + 2 * (200 * 50 * 50 // 2)
-    final = 3 * 200 * 2500 + 2 * (400 * 2500 // 2) + 200 * 2500 + 200 * 200 * 50
-    assert bench.pinv_flops(w, "refined", 3) == 32 * (200 * 200 * 50 + 3 * per_iter + final)
+    r = c = 200
+    k = 50
+    # float-float quaternion multiply-adds at three iterations: the first
+    # iteration's X = W Z' and solves, two full iterations (Z, X, M, E, M',
+    # the norm product, the solves), the ending (solves, E2, V, U); the FP32
+    # products (Y0, the first Z and M, every G', G1 and G2) at 16/188 of one
+    solves = (2 * c + r) * k * k / 2
+    first = r * c * k + solves
+    per_iter = 2 * r * c * k + r * k * k + c * k * k + k ** 3 + c * k * k + solves
+    final = (r + c) * k * k + r * k * k + c * k * k + c * r * k
+    fp32 = 2 * r * c * k + r * k * k + 3 * c * k * k / 2 + r * k * k
+    expect = 32 * (first + 2 * per_iter + final + fp32 * 16.0 / 188)
+    assert abs(bench.pinv_flops(w, "refined", 3) - expect) < 1e-6 * expect
     assert bench.pinv_flops(w, "refined", 4) > bench.pinv_flops(w, "refined", 3)
