@@ -75,6 +75,17 @@ struct BatchProblem {
   int tile_base2;          // first tile of this problem in the second GEMM's list
   int tiles2;              // its number of tiles
   int64_t colpart_off;     // its column partials in the norms' scratch (doubles)
+  int64_t zarow;           // first row of its C pieces in Z's stacked A operand (split plans)
+};
+
+// Z = C T's stacked A operand, which the gather fills with C's pieces as it
+// gathers C (split plans; base null otherwise): pieces [(q 4 + t)][row][k],
+// rows of kpad elements, plane stride `plane` elements.
+struct CPieces {
+  void* base;
+  int64_t kpad, plane;
+  int npieces;
+  int bf16;
 };
 
 struct GTile {
@@ -197,7 +208,7 @@ k_batch_sample(const BatchProblem* probs, SampleArgs base, int32_t* status) {
 }
 
 // ---------------------------------------------------------------- gather -
-__global__ void k_batch_gather(const BatchProblem* probs) {
+__global__ void k_batch_gather(const BatchProblem* probs, CPieces cp) {
   const BatchProblem& P = probs[blockIdx.y];
   const int64_t nc = (int64_t)P.m * P.c, nr = (int64_t)P.r * P.n, nw = (int64_t)P.r * P.c;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nc + nr + nw;
@@ -208,7 +219,23 @@ __global__ void k_batch_gather(const BatchProblem* probs) {
     else if (e < nc + nr) { const int64_t f = e - nc; i = f / P.n; j = f % P.n; si = P.I[i]; sj = j; out = &P.R; }
     else { const int64_t f = e - nc - nr; i = f / P.c; j = f % P.c; si = P.I[i]; sj = P.J[j]; out = &P.W; }
     const bool in = si >= 0 && si < P.m && sj >= 0 && sj < P.n;
-    stf4(*out, i, j, in ? ldf4(P.A, si, sj) : make_float4(0.f, 0.f, 0.f, 0.f));
+    const float4 v = in ? ldf4(P.A, si, sj) : make_float4(0.f, 0.f, 0.f, 0.f);
+    stf4(*out, i, j, v);
+    if (e < nc && cp.base != nullptr && P.zarow >= 0) {   // C's pieces: row i, k = j
+      const float pl4[4] = {v.x, v.y, v.z, v.w};
+      const int64_t rowoff = (P.zarow + i) * cp.kpad + j;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float pc[3];
+        if (cp.bf16) split_value<true, float>(pl4[t], cp.npieces, pc);
+        else split_value<false, float>(pl4[t], cp.npieces, pc);
+        for (int q = 0; q < cp.npieces; ++q) {
+          const int64_t idx = (int64_t)(q * 4 + t) * cp.plane + rowoff;
+          if (cp.bf16) reinterpret_cast<__nv_bfloat16*>(cp.base)[idx] = __float2bfloat16_rn(pc[q]);
+          else reinterpret_cast<float*>(cp.base)[idx] = pc[q];
+        }
+      }
+    }
   }
 }
 
@@ -520,13 +547,12 @@ struct BatchPlan {
   cudaGraphExec_t exec = nullptr;
   qmcur_opts opts{};
   // Z = C T on the tensor cores (opts.prec a split precision): the stacked
-  // operand pieces, the split jobs, the group tables and the tile width
+  // operand pieces (C's written by the gather, T's by the T stage), the
+  // group tables and the tile width
   bool tc = false;
   void* A_all = nullptr;
   void* B_all = nullptr;
   int64_t rows_a = 0, rows_b = 0, kpad = 0;
-  TcSplitJob* djobs = nullptr;
-  int njobs = 0, split_tiles = 0;
   TcGroupProb* dgprobs = nullptr;
   TcGroupTile* dgtiles = nullptr;
   int ngtiles = 0, tc_bn = 128;
@@ -562,7 +588,15 @@ static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st, bool timed = fa
   base.norm = norm;
   k_batch_sample<<<2 * p->count, kSampleThreads, p->samp_smem, st>>>(p->dprobs, base, p->status);
   mark(2);
-  k_batch_gather<<<dim3(64, p->count), 256, 0, st>>>(p->dprobs);
+  CPieces cp{};
+  if (p->tc) {
+    cp.base = p->A_all;
+    cp.kpad = p->kpad;
+    cp.plane = p->rows_a * p->kpad;
+    cp.npieces = tc_group_npieces(p->opts.prec);
+    cp.bf16 = tc_group_epr(p->opts.prec) == 32;   // 32 BF16 or 16 TF32 per 64-byte row
+  }
+  k_batch_gather<<<dim3(64, p->count), 256, 0, st>>>(p->dprobs, cp);
   mark(3);
   if (p->refined) {
     const qmcur_status s =
@@ -588,9 +622,8 @@ static qmcur_status enqueue_batch(BatchPlan* p, cudaStream_t st, bool timed = fa
   }
   mark(5);
   if (p->tc) {
-    qmcur_status s = tc_group_split(p->opts.prec, p->djobs, p->njobs, p->split_tiles, st);
-    if (s != QMCUR_OK) return s;
-    s = tc_group_residual(p->opts.prec, p->tc_bn, p->A_all, p->rows_a, p->B_all, p->rows_b,
+    // (C's pieces come from the gather, T's from the T stage)
+    qmcur_status s = tc_group_residual(p->opts.prec, p->tc_bn, p->A_all, p->rows_a, p->B_all, p->rows_b,
                           p->kpad, p->dgtiles, p->ngtiles, p->dgprobs, p->partial, p->status, st);
     if (s != QMCUR_OK) return s;
   } else {
@@ -730,7 +763,6 @@ static void free_plan(BatchPlan* p) {
   cudaFree(p->colpart);
   cudaFree(p->A_all);
   cudaFree(p->B_all);
-  cudaFree(p->djobs);
   cudaFree(p->dgprobs);
   cudaFree(p->dgtiles);
   cudaFree(p->A1_all);
@@ -1005,26 +1037,7 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     if (p->rows_a > INT32_MAX / 2 || p->rows_b > INT32_MAX / 2) { free_plan(p); return QMCUR_ERR_UNSUPPORTED; }
     const size_t ba = tc_group_piece_bytes(pr, p->rows_a, p->kpad);
     const size_t bb = tc_group_piece_bytes(pr, p->rows_b, p->kpad);
-    std::vector<TcSplitJob> jobs;
     std::vector<TcGroupProb> gp(count);
-    int tiles = 0;
-    auto add_job = [&](const QView& S, bool trans, void* dst, int64_t rows, int64_t K, int64_t row0,
-                       int64_t rows_total) {
-      TcSplitJob j{};
-      j.S = S;
-      j.dst = dst;
-      j.rows = rows;
-      j.K = K;
-      j.kp_job = (K + epr - 1) / epr * epr;
-      j.kpad = p->kpad;
-      j.row0 = row0;
-      j.plane_stride = rows_total * p->kpad;
-      j.trans = trans ? 1 : 0;
-      j.tiles_k = (int)((j.kp_job + 63) / 64);
-      j.first_tile = tiles;
-      tiles += j.tiles_k * (int)((rows + 31) / 32);
-      jobs.push_back(j);
-    };
     if (cudaMalloc(&p->A_all, ba) != cudaSuccess || cudaMalloc(&p->B_all, bb) != cudaSuccess) {
       free_plan(p);
       return QMCUR_ERR_CUDA;
@@ -1033,8 +1046,9 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
     cudaMemsetAsync(p->B_all, 0, bb, stream);
     for (int b = 0; b < count; ++b) {
       const BatchProblem& P = p->host[b];
-      add_job(P.C, false, p->A_all, P.m, P.c, arow[b], p->rows_a);   // A[i][k] = C[i][k]
-      // (B[j][k] = T[k][j] is written by the T stage's epilogue)
+      // A[i][k] = C[i][k] is written by the gather, B[j][k] = T[k][j] by the
+      // T stage's epilogue
+      p->host[b].zarow = arow[b];
       TcGroupProb& g = gp[b];
       bool av = P.A.ld % 4 == 0;
       for (int t = 0; t < 4; ++t) {
@@ -1050,14 +1064,10 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
       g.brow = (int)brow[b];
       g.a_vec = av ? 1 : 0;
     }
-    p->njobs = (int)jobs.size();
-    p->split_tiles = tiles;
-    if (cudaMalloc(&p->djobs, jobs.size() * sizeof(TcSplitJob)) != cudaSuccess ||
-        cudaMalloc(&p->dgprobs, gp.size() * sizeof(TcGroupProb)) != cudaSuccess) {
+    if (cudaMalloc(&p->dgprobs, gp.size() * sizeof(TcGroupProb)) != cudaSuccess) {
       free_plan(p);
       return QMCUR_ERR_CUDA;
     }
-    cudaMemcpyAsync(p->djobs, jobs.data(), jobs.size() * sizeof(TcSplitJob), cudaMemcpyHostToDevice, stream);
     cudaMemcpyAsync(p->dgprobs, gp.data(), gp.size() * sizeof(TcGroupProb), cudaMemcpyHostToDevice, stream);
     if (cudaStreamSynchronize(stream) != cudaSuccess) { free_plan(p); return QMCUR_ERR_CUDA; }
     const qmcur_status st1 = build_t_stage(p, brow, stream);

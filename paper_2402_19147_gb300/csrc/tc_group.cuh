@@ -5,9 +5,41 @@
 // residual against each problem's A fused into the epilogue.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace qmcur {
+
+// An FP32 value rounded to TF32 (nearest, ties away from zero).
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Pieces of one value for the split products: BF16 (npieces 2 or 3) or
+// TF32 (npieces 2).
+template <bool BF16, typename T>
+__device__ __forceinline__ void split_value(T x, int npieces, float out[3]) {
+  // The pieces carry at most ~24 significant bits, so the split runs in FP32
+  // (GB300's FP64 rate is 1/64 of FP32); each residual below is exact in FP32.
+  const float xf = (float)x;
+  if constexpr (BF16) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(xf);
+    const float r1 = xf - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    out[0] = __bfloat162float(h);
+    out[1] = __bfloat162float(m);
+    out[2] = npieces > 2 ? __bfloat162float(__float2bfloat16_rn(r2)) : 0.f;
+  } else {
+    const float b = tf32_rna(xf);
+    out[0] = b;
+    out[1] = xf - b;
+    out[2] = 0.f;
+  }
+}
 
 // One 128-row output tile of problem `prob` at (m0, n0) of its Z = C T.
 struct TcGroupTile {
