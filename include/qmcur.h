@@ -437,7 +437,8 @@ qmcur_status qmcur_complete_step(qmcur_qmat* X, const uint8_t* mask, int64_t c, 
  * with one CTA per problem (rank_cap required, k <= 100, no shared-memory
  * limit on the intersection; largest problems first);
  * QMCUR_PINV_REFINED_FP64 runs the FP64-accurate refined method of
- * qmcur_pinv_core with one CTA per problem (same requirements; max_sweeps is
+ * qmcur_pinv_core with one CTA per problem (same requirements, and
+ * opts->rcond <= 1e-6 as for that method, else UNSUPPORTED; max_sweeps is
  * its iteration limit, info[1] the iterations taken, NO_CONVERGENCE in
  * info[2] when the spectrum has no usable gap at the cap) and keeps U in
  * FP64 as well (qmcur_batch_copy what = 10).  opts->prec selects the

@@ -869,6 +869,9 @@ qmcur_status qmcur_batch_plan(int32_t count, const qmcur_qmat* A, const int64_t*
   const bool refined = opts->pinv_method == QMCUR_PINV_REFINED_FP64;
   const bool subspace = opts->pinv_method == QMCUR_PINV_SUBSPACE_FP32 || refined;
   if (subspace && rank_cap == nullptr) return QMCUR_ERR_UNSUPPORTED;   // the methods need caps
+  // the refined core keeps exactly k values and certifies sigma_k / sigma_1
+  // only down to ~1e-4 (its FP32 factors): as in qmcur_pinv_core, no larger rcond
+  if (refined && !(opts->rcond >= 0.0 && opts->rcond <= 1e-6)) return QMCUR_ERR_UNSUPPORTED;
   for (int b = 0; b < count; ++b) {
     if (!valid_qmat(&A[b], true, false)) return QMCUR_ERR_INVALID_ARG;
     if (c[b] < 1 || c[b] > A[b].cols || r[b] < 1 || r[b] > A[b].rows) return QMCUR_ERR_INVALID_ARG;

@@ -204,3 +204,15 @@ def test_batch_tensor_core_ragged_shapes():
             assert abs(rel - rel_f) < 1e-5, (method, b, rel, rel_f)
         F.close()
         T.close()
+
+
+def test_batch_refined_host_refusals():
+    # the refined core needs rank caps and rcond <= 1e-6 (it keeps exactly k
+    # values): the plan refuses otherwise, before any launch
+    probs = synth.batch_problems(count=3, seed=9)
+    As = [dev(p["X"]) for p in probs]
+    cs, rs = [p["c"] for p in probs], [p["r"] for p in probs]
+    for kw in (dict(rank_caps=None), dict(rank_caps=[p["rank"] for p in probs], rcond=1e-3)):
+        with pytest.raises(Q.QmcurError) as e:
+            Q.Batch(As, cs, rs, pinv_method=Q.PINV_REFINED_FP64, **kw)
+        assert e.value.code == 7   # QMCUR_ERR_UNSUPPORTED
