@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kPinvThreads) k_pinv_colnorm(const double* G, 
 
 __global__ void __launch_bounds__(kPinvThreads) k_pinv_jacobi(PinvArgs a) {
   __shared__ double red[6 * 4];
+  __shared__ double rot_sh[6];
   __shared__ int rotated_sh;
   __shared__ double floor_sh;
   const int64_t nc = a.nc, nr = a.nr;
@@ -195,25 +196,42 @@ __global__ void __launch_bounds__(kPinvThreads) k_pinv_jacobi(PinvArgs a) {
         block_sum128(g2, red, 4);
         block_sum128(g3, red, 5);
         __syncthreads();
-        double s6[6];
+        // the rotation, once per pair: FP64 square roots and divisions are
+        // long sequences on GB300's FP64 pipe, so thread 0 forms it and the
+        // others read it (rot_sh[0] < 0: skip the pair)
+        if (threadIdx.x == 0) {
+          double s6[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) s6[q] = (red[q * 4 + 0] + red[q * 4 + 1]) + (red[q * 4 + 2] + red[q * 4 + 3]);
+          for (int q = 0; q < 6; ++q)
+            s6[q] = (red[q * 4 + 0] + red[q * 4 + 1]) + (red[q * 4 + 2] + red[q * 4 + 3]);
+          const double a2 = s6[0], b2 = s6[1];
+          const double gam = sqrt(s6[2] * s6[2] + s6[3] * s6[3] + s6[4] * s6[4] + s6[5] * s6[5]);
+          // Skip pairs already orthogonal to working accuracy, and pairs whose
+          // smaller column is below tol relative to the larger one (numerically
+          // zero next to it: rotating it only stirs rounding noise).
+          if (!(a2 > 0.0) || !(b2 > 0.0) || !(gam > a.tol * sqrt(a2) * sqrt(b2)) ||
+              fmin(a2, b2) < a.tol * a.tol * fmax(a2, b2) || fmax(a2, b2) < zero_floor) {
+            rot_sh[0] = -1.0;
+          } else {
+            rotated_sh = 1;
+            const double zeta = (b2 - a2) / (2.0 * gam);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double cs = 1.0 / sqrt(1.0 + t * t);
+            const double ig = 1.0 / gam;
+            rot_sh[0] = cs;
+            rot_sh[1] = cs * t;
+            // w = conj(u), u = gamma / g
+            rot_sh[2] = s6[2] * ig;
+            rot_sh[3] = -s6[3] * ig;
+            rot_sh[4] = -s6[4] * ig;
+            rot_sh[5] = -s6[5] * ig;
+          }
+        }
         __syncthreads();
-        al = s6[0]; be = s6[1];
-        const double gam = sqrt(s6[2] * s6[2] + s6[3] * s6[3] + s6[4] * s6[4] + s6[5] * s6[5]);
-        // Skip pairs already orthogonal to working accuracy, and pairs whose
-        // smaller column is below tol relative to the larger one (numerically
-        // zero next to it: rotating it only stirs rounding noise).
-        if (!(al > 0.0) || !(be > 0.0) || !(gam > a.tol * sqrt(al) * sqrt(be)) ||
-            fmin(al, be) < a.tol * a.tol * fmax(al, be) || fmax(al, be) < zero_floor)
-          continue;
-        if (threadIdx.x == 0) rotated_sh = 1;
-        const double zeta = (be - al) / (2.0 * gam);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t);
-        const double sn = cs * t;
-        // w = conj(u), u = gamma / g
-        const double w0 = s6[2] / gam, w1 = -s6[3] / gam, w2 = -s6[4] / gam, w3 = -s6[5] / gam;
+        const double cs = rot_sh[0], sn = rot_sh[1];
+        const double w0 = rot_sh[2], w1 = rot_sh[3], w2 = rot_sh[4], w3 = rot_sh[5];
+        __syncthreads();   // rot_sh and red are rewritten by the next pair
+        if (cs < 0.0) continue;
         for (int mat = 0; mat < 2; ++mat) {
           double* base = mat == 0 ? a.G : a.V;
           const int64_t len = mat == 0 ? nr : nc;
