@@ -147,6 +147,30 @@ __global__ void __launch_bounds__(kPinvThreads) k_pinv_colnorm(const double* G, 
   if (threadIdx.x == 0) colnorm2[blockIdx.x] = (red[0] + red[1]) + (red[2] + red[3]);
 }
 
+constexpr int kJacRegRows = 4;
+
+// |x|^2, |y|^2 and conj(x) * y, accumulated
+__device__ __forceinline__ void pair_dots(const Q4 x, const Q4 y, double& al, double& be, double& g0,
+                                          double& g1, double& g2, double& g3) {
+  al += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+  be += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
+  g0 += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+  g1 += x.x * y.y - x.y * y.x - x.z * y.w + x.w * y.z;
+  g2 += x.x * y.z + x.y * y.w - x.z * y.x - x.w * y.y;
+  g3 += x.x * y.w - x.y * y.z + x.z * y.y - x.w * y.x;
+}
+
+// row i of the pair (x, q) -> (cs x - sn q w, sn x + cs q w)
+__device__ __forceinline__ void rotate_rows(double* xa, double* xb, int64_t i, const Q4 x, const Q4 q,
+                                            double cs, double sn, const Q4 w) {
+  const Q4 y = {q.x * w.x - q.y * w.y - q.z * w.z - q.w * w.w,
+                q.x * w.y + q.y * w.x + q.z * w.w - q.w * w.z,
+                q.x * w.z - q.y * w.w + q.z * w.x + q.w * w.y,
+                q.x * w.w + q.y * w.z - q.z * w.y + q.w * w.x};
+  stq(xa, i, Q4{cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z, cs * x.w - sn * y.w});
+  stq(xb, i, Q4{sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z, sn * x.w + cs * y.w});
+}
+
 __global__ void __launch_bounds__(kPinvThreads) k_pinv_jacobi(PinvArgs a) {
   __shared__ double red[6 * 4];
   __shared__ double rot_sh[6];
@@ -168,6 +192,7 @@ __global__ void __launch_bounds__(kPinvThreads) k_pinv_jacobi(PinvArgs a) {
   const int64_t N = (nc % 2 == 0) ? nc : nc + 1;
   const int64_t npairs = N / 2;
   const int64_t steps = N - 1;
+  const bool in_regs = nr <= (int64_t)kJacRegRows * kPinvThreads;   // nc <= nr
   int sweep = 0;
   for (; sweep < a.max_sweeps; ++sweep) {
     if (threadIdx.x == 0) rotated_sh = 0;
@@ -178,16 +203,32 @@ __global__ void __launch_bounds__(kPinvThreads) k_pinv_jacobi(PinvArgs a) {
         if (ca >= nc || cb >= nc) continue;   // the dummy player of an odd count
         double* ga = a.G + ca * nr * 4;
         double* gb = a.G + cb * nr * 4;
+        double* va = a.V + ca * nc * 4;
+        double* vb = a.V + cb * nc * 4;
         double al = 0, be = 0, g0 = 0, g1 = 0, g2 = 0, g3 = 0;
-        for (int64_t i = threadIdx.x; i < nr; i += kPinvThreads) {
-          const Q4 x = ldq(ga, i), y = ldq(gb, i);
-          al += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
-          be += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
-          // conj(x) * y
-          g0 += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
-          g1 += x.x * y.y - x.y * y.x - x.z * y.w + x.w * y.z;
-          g2 += x.x * y.z + x.y * y.w - x.z * y.x - x.w * y.y;
-          g3 += x.x * y.w - x.y * y.z + x.z * y.y - x.w * y.x;
+        // Up to kJacRegRows rows per thread: both columns of G and of V are
+        // loaded into registers before the reduction (the loads of V overlap
+        // it) and rotated there; longer columns stream through the loops.
+        Q4 xg[kJacRegRows], yg[kJacRegRows], xv[kJacRegRows], yv[kJacRegRows];
+        if (in_regs) {
+#pragma unroll
+          for (int u = 0; u < kJacRegRows; ++u) {
+            const int64_t i = threadIdx.x + (int64_t)u * kPinvThreads;
+            xg[u] = i < nr ? ldq(ga, i) : Q4{0.0, 0.0, 0.0, 0.0};
+            yg[u] = i < nr ? ldq(gb, i) : Q4{0.0, 0.0, 0.0, 0.0};
+          }
+#pragma unroll
+          for (int u = 0; u < kJacRegRows; ++u) {
+            const int64_t i = threadIdx.x + (int64_t)u * kPinvThreads;
+            xv[u] = i < nc ? ldq(va, i) : Q4{0.0, 0.0, 0.0, 0.0};
+            yv[u] = i < nc ? ldq(vb, i) : Q4{0.0, 0.0, 0.0, 0.0};
+          }
+#pragma unroll
+          for (int u = 0; u < kJacRegRows; ++u)
+            pair_dots(xg[u], yg[u], al, be, g0, g1, g2, g3);
+        } else {
+          for (int64_t i = threadIdx.x; i < nr; i += kPinvThreads)
+            pair_dots(ldq(ga, i), ldq(gb, i), al, be, g0, g1, g2, g3);
         }
         block_sum128(al, red, 0);
         block_sum128(be, red, 1);
@@ -232,21 +273,19 @@ __global__ void __launch_bounds__(kPinvThreads) k_pinv_jacobi(PinvArgs a) {
         const double w0 = rot_sh[2], w1 = rot_sh[3], w2 = rot_sh[4], w3 = rot_sh[5];
         __syncthreads();   // rot_sh and red are rewritten by the next pair
         if (cs < 0.0) continue;
-        for (int mat = 0; mat < 2; ++mat) {
-          double* base = mat == 0 ? a.G : a.V;
-          const int64_t len = mat == 0 ? nr : nc;
-          double* xa = base + ca * len * 4;
-          double* xb = base + cb * len * 4;
-          for (int64_t i = threadIdx.x; i < len; i += kPinvThreads) {
-            const Q4 x = ldq(xa, i), q = ldq(xb, i);
-            // y = q * w
-            const Q4 y = {q.x * w0 - q.y * w1 - q.z * w2 - q.w * w3,
-                          q.x * w1 + q.y * w0 + q.z * w3 - q.w * w2,
-                          q.x * w2 - q.y * w3 + q.z * w0 + q.w * w1,
-                          q.x * w3 + q.y * w2 - q.z * w1 + q.w * w0};
-            stq(xa, i, Q4{cs * x.x - sn * y.x, cs * x.y - sn * y.y, cs * x.z - sn * y.z, cs * x.w - sn * y.w});
-            stq(xb, i, Q4{sn * x.x + cs * y.x, sn * x.y + cs * y.y, sn * x.z + cs * y.z, sn * x.w + cs * y.w});
+        const Q4 w = {w0, w1, w2, w3};
+        if (in_regs) {
+#pragma unroll
+          for (int u = 0; u < kJacRegRows; ++u) {
+            const int64_t i = threadIdx.x + (int64_t)u * kPinvThreads;
+            if (i < nr) rotate_rows(ga, gb, i, xg[u], yg[u], cs, sn, w);
+            if (i < nc) rotate_rows(va, vb, i, xv[u], yv[u], cs, sn, w);
           }
+        } else {
+          for (int64_t i = threadIdx.x; i < nr; i += kPinvThreads)
+            rotate_rows(ga, gb, i, ldq(ga, i), ldq(gb, i), cs, sn, w);
+          for (int64_t i = threadIdx.x; i < nc; i += kPinvThreads)
+            rotate_rows(va, vb, i, ldq(va, i), ldq(vb, i), cs, sn, w);
         }
       }
       if (!grid_barrier(a.bar, a.status)) return;
