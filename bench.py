@@ -51,9 +51,10 @@ def parse():
                          "long; the median repeat is reported")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the 4096 x 4096 colour-field decompositions of the default run")
-    ap.add_argument("--streams", type=int, default=8,
-                    help="decompositions in flight, each stream's persistent kernels on "
-                         "SMs / streams CTAs")
+    ap.add_argument("--streams", type=int, default=None,
+                    help="decompositions in flight (at most --steps), each stream's "
+                         "persistent kernels on SMs / streams CTAs.  Default: 8, or 1 with "
+                         "the FP64 Jacobi core, whose own grid already covers every SM")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default=WORKLOAD,
@@ -67,6 +68,8 @@ def parse():
     args = ap.parse_args()
     if args.pinv is None:
         args.pinv = "jacobi" if args.workload == "color4096_smooth100" else "refined"
+    if args.streams is None:
+        args.streams = 1 if args.pinv == "jacobi" else 8
     return args
 
 
@@ -528,7 +531,9 @@ def run_ours(args):
     # budgets sum to at most the SM count, so all the cooperative grids can
     # be resident at once.  Inputs larger than L2 stand in for a flush: four
     # row-rotated copies of A (the same spectrum), cycled.
-    NS = max(1, args.streams)
+    # (no more streams than the K decompositions of one timed loop: a stream
+    # left idle would still take its share of the SMs from the others)
+    NS = max(1, min(args.streams, K))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     budget = sms // NS if NS > 1 else 0
     Dp = [Q.Decomposition(m, n, c, r, prec, device=dev) for _ in range(NS)]
