@@ -128,3 +128,17 @@ def test_refined_pinv_flop_count_follows_the_shapes():
     expect = 32 * (first + 2 * per_iter + final + fp32 * 16.0 / 188)
     assert abs(bench.pinv_flops(w, "refined", 3) - expect) < 1e-6 * expect
     assert bench.pinv_flops(w, "refined", 4) > bench.pinv_flops(w, "refined", 3)
+
+
+def test_stream_defaults(monkeypatch):
+    # one stream with the FP64 Jacobi core (its own grid covers every SM),
+    # eight otherwise; never more streams than the timed steps
+    sys.path.insert(0, ROOT)
+    import bench
+    for argv, pinv, streams in ((["--workload", "color4096_smooth100"], "jacobi", 1),
+                                ([], "refined", 8),
+                                (["--pinv", "jacobi"], "jacobi", 1),
+                                (["--streams", "4"], "refined", 4)):
+        monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
+        a = bench.parse()
+        assert (a.pinv, a.streams) == (pinv, streams)

@@ -15,7 +15,10 @@ from gpu_util import dev, host, rel_fro, run_status
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("m,n,k", [(120, 90, 5), (70, 130, 6), (500, 500, 10)])
+# columns of up to 512 rows are rotated in registers, longer ones streamed:
+# 512 and 513 rows sit on either side, 700 and the wide 40 x 640 stream
+@pytest.mark.parametrize("m,n,k", [(120, 90, 5), (70, 130, 6), (500, 500, 10), (512, 40, 4),
+                                   (513, 40, 4), (700, 60, 5), (40, 640, 4)])
 def test_qsvd_truncated_matches_oracle(m, n, k):
     X, _ = synth.lowrank_gaussian(m, n, k, seed=m + n, noise_rel=1e-3, dtype=np.float64)
     B = torch.empty(4, m, n, dtype=torch.float64, device="cuda")
