@@ -586,12 +586,11 @@ def run_ours(args):
         Q.check_status(Db.status, "timed steps")
     t_med = statistics.median(reps)
     value = replica_value(world, K, t_med)
-    stage_ms = {k: 0.0 for k in stages}
-    for ev in evs:
-        for e in ev:
-            for i, k in enumerate(stages):
-                stage_ms[k] += e[i].elapsed_time(e[i + 1])
-    stage_ms = {k: v / (K * len(evs)) for k, v in stage_ms.items()}
+    # per-stage mean over the K steps of each repeat, then the median over
+    # the repeats (like the value: one slow repeat does not move it)
+    stage_ms = {k: statistics.median(sum(e[i].elapsed_time(e[i + 1]) for e in ev) / K
+                                     for ev in evs)
+                for i, k in enumerate(stages)}
     sweeps = int(D.rank[1].item())
     rel = float(D.out3[0].item())
 
