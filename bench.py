@@ -68,9 +68,23 @@ def parse():
     args = ap.parse_args()
     if args.pinv is None:
         args.pinv = "jacobi" if args.workload == "color4096_smooth100" else "refined"
+    args.streams_default = args.streams is None
     if args.streams is None:
         args.streams = 1 if args.pinv == "jacobi" else 8
     return args
+
+
+def stream_count(streams, K, adapt):
+    """Decompositions in flight for a K-step loop: at most K.  With the
+    default count, the number n in [min(4, N), N] whose waves cover the K
+    steps with the fewest idle stream slots (ceil(K / n) n smallest, the
+    larger n on ties): each stream holds SMs / n of the GPU for the whole
+    loop, so a last wave that fills only some streams leaves the others'
+    SMs idle."""
+    n0 = max(1, min(streams, K))
+    if not adapt:
+        return n0
+    return min(range(min(4, n0), n0 + 1), key=lambda n: (-(-K // n) * n, -n))
 
 
 DECOMP_WORKLOADS = (WORKLOAD, "color4096_smooth100")
@@ -412,7 +426,10 @@ def fp64_check(Q, A, D, w, prec, sampler, stream, steps=10, warmup=3, rows=256):
 # workload: the tensor-core Z = C T with the fused residual (mixed split) and
 # the refined pseudo-inverse of its 200 x 200 intersection.
 NCU_TRAFFIC = {"gemm_z": 81.91e6 + 2.24e6, "pinv_refine": 30.31e6 + 430.36e6,
-               "refine_each": 468.51e6 + 2106.71e6}
+               "refine_each": 468.51e6 + 2106.71e6,
+               # k_pinv_jacobi, per workload (G and V stay in L2 at both sizes)
+               "jacobi_" + WORKLOAD: 2.638e6 + 0.660e6,
+               "jacobi_color4096_smooth100": 16.746e6 + 16.661e6}
 
 
 def peaks():
@@ -531,9 +548,10 @@ def run_ours(args):
     # budgets sum to at most the SM count, so all the cooperative grids can
     # be resident at once.  Inputs larger than L2 stand in for a flush: four
     # row-rotated copies of A (the same spectrum), cycled.
-    # (no more streams than the K decompositions of one timed loop: a stream
-    # left idle would still take its share of the SMs from the others)
-    NS = max(1, min(args.streams, K))
+    # (no more streams than the K decompositions of one timed loop, and by
+    # default a count that divides them into full waves: a stream left idle
+    # would still take its share of the SMs from the others)
+    NS = stream_count(args.streams, K, args.streams_default)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     budget = sms // NS if NS > 1 else 0
     Dp = [Q.Decomposition(m, n, c, r, prec, device=dev) for _ in range(NS)]
@@ -733,7 +751,8 @@ def run_ours(args):
         achieved, peak, src = amount / per_launch_s / 1e12, pk["bf16_tflops"], pk_kind + " BF16"
     if not one_stream:
         src += "; timed in the one-stream leg (every SM)"
-    roof = {"kernel": {"pinv": "k_pinv_refine" if args.pinv == "refined" else dom,
+    roof = {"kernel": {"pinv": {"refined": "k_pinv_refine",
+                                "jacobi": "k_pinv_jacobi"}.get(args.pinv, dom),
                        "gemm": "reconstruction GEMMs"}.get(dom, dom),
             "bound": "alu" if bound == "alu" else bound, "achieved": achieved, "peak": peak,
             "unit": unit, "frac": achieved / peak,
@@ -746,6 +765,10 @@ def run_ours(args):
                                 "and float-float intermediates of its 27 steps (461 MB in "
                                 "the 0.92 ms capture, 500 GB/s); the kernel reads W once "
                                 "(1.3 MB)")
+    if dom == "pinv" and args.pinv == "jacobi" and "jacobi_" + workload_name(args) in NCU_TRAFFIC:
+        roof["traffic"] = NCU_TRAFFIC["jacobi_" + workload_name(args)]
+        roof["traffic_note"] = ("G and V (2.6 MB at 200 x 200, 16 MB at 500 x 500) stay in L2 "
+                                "across the sweeps: DRAM sees about one pass over them")
 
     # the GEMM stage: tensor work of the split (products x quaternion flops)
     # against the measured BF16 burst (TF32 at the nominal half of it)

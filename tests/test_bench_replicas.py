@@ -142,3 +142,21 @@ def test_stream_defaults(monkeypatch):
         monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
         a = bench.parse()
         assert (a.pinv, a.streams) == (pinv, streams)
+
+
+def test_stream_count_fills_whole_waves():
+    sys.path.insert(0, ROOT)
+    import bench
+    # the default count divides the K steps into full waves where it can
+    assert bench.stream_count(8, 200, True) == 8
+    assert bench.stream_count(8, 20, True) == 5
+    assert bench.stream_count(8, 11, True) == 6
+    assert bench.stream_count(8, 3, True) == 3
+    assert bench.stream_count(1, 20, True) == 1
+    # an explicit count is kept, capped at K
+    assert bench.stream_count(8, 20, False) == 8
+    assert bench.stream_count(8, 3, False) == 3
+    for K in range(1, 64):
+        n = bench.stream_count(8, K, True)
+        assert 1 <= n <= min(8, K)
+        assert -(-K // n) * n <= -(-K // min(8, K)) * min(8, K)
