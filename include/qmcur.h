@@ -19,7 +19,12 @@
  *   without synchronising.  No call copies between host and device, and no
  *   call allocates device memory: scratch space comes from the caller through
  *   (workspace, ws_bytes), sized by qmcur_workspace_size().  The workspace of
- *   one call may be reused by the next call on the same stream.
+ *   one call may be reused by the next call on the same stream.  So the
+ *   single-matrix calls (qmcur_decompose and the per-step calls, the
+ *   cooperative pseudo-inverse kernels included) may be captured into a CUDA
+ *   graph on the caller's stream; a replay reads the buffers' contents at
+ *   replay time.  Launch parameters (shapes, seed, CTA budget) are fixed at
+ *   capture.  The batched path captures its own graph (qmcur_batch_plan).
  * Errors.  Argument and shape errors are returned synchronously (nothing is
  *   enqueued).  Errors that depend on the data (non-finite input, zero norm,
  *   too few columns with positive probability, sampling attempt limit, Jacobi
