@@ -160,3 +160,60 @@ def test_stream_count_fills_whole_waves():
         n = bench.stream_count(8, K, True)
         assert 1 <= n <= min(8, K)
         assert -(-K // n) * n <= -(-K // min(8, K)) * min(8, K)
+
+
+def test_timed_repeats_releases_the_streams_together():
+    # with several streams, every repeat puts a device sleep before its start
+    # event on the launching stream (sized from the previous repeat's enqueue
+    # time, outside the timed region) and the streams wait for that event;
+    # with one stream there is no sleep
+    sys.path.insert(0, ROOT)
+    import bench
+    calls = []
+
+    class Ev:
+        def __init__(self, enable_timing=False):
+            pass
+
+        def record(self, st=None):
+            calls.append(("record", st))
+
+        def elapsed_time(self, other):
+            return 400.0
+
+    class St:
+        def wait_event(self, e):
+            calls.append(("wait", self))
+
+    class Cuda:
+        Event = Ev
+
+        def synchronize(self):
+            calls.append(("sync",))
+
+        def current_stream(self):
+            return "cur"
+
+        def _sleep(self, cycles):
+            calls.append(("sleep", cycles))
+
+    class FakeTorch:
+        cuda = Cuda()
+
+    def run_once():
+        calls.append(("run",))
+
+    streams = [St(), St()]
+    times = bench.timed_repeats(FakeTorch, run_once, streams, 1.0, sm_mhz=2000.0)
+    assert times == [400.0] * 3
+    sleeps = [c for c in calls if c[0] == "sleep"]
+    assert len(sleeps) == 3
+    assert sleeps[0][1] == int(5.0 * 1e3 * 2000.0)          # the first repeat's guess
+    assert all(s[1] < sleeps[0][1] for s in sleeps[1:])      # then the measured enqueue time
+    for i, c in enumerate(calls):
+        if c[0] == "sleep":   # sleep, start event, both streams wait, then the steps
+            assert calls[i + 1] == ("record", "cur")
+            assert [x[0] for x in calls[i + 2:i + 5]] == ["wait", "wait", "run"]
+    calls.clear()
+    assert bench.timed_repeats(FakeTorch, run_once, [], 1.0) == [400.0] * 3
+    assert not [c for c in calls if c[0] == "sleep"]
