@@ -185,6 +185,12 @@ def test_timed_repeats_releases_the_streams_together():
         def wait_event(self, e):
             calls.append(("wait", self))
 
+    class Cur:
+        def wait_event(self, e):
+            calls.append(("join",))
+
+    cur = Cur()
+
     class Cuda:
         Event = Ev
 
@@ -192,7 +198,7 @@ def test_timed_repeats_releases_the_streams_together():
             calls.append(("sync",))
 
         def current_stream(self):
-            return "cur"
+            return cur
 
         def _sleep(self, cycles):
             calls.append(("sleep", cycles))
@@ -212,7 +218,7 @@ def test_timed_repeats_releases_the_streams_together():
     assert all(s[1] < sleeps[0][1] for s in sleeps[1:])      # then the measured enqueue time
     for i, c in enumerate(calls):
         if c[0] == "sleep":   # sleep, start event, both streams wait, then the steps
-            assert calls[i + 1] == ("record", "cur")
+            assert calls[i + 1] == ("record", cur)
             assert [x[0] for x in calls[i + 2:i + 5]] == ["wait", "wait", "run"]
     calls.clear()
     assert bench.timed_repeats(FakeTorch, run_once, [], 1.0) == [400.0] * 3
