@@ -566,7 +566,7 @@ def run_ours(args):
     # (no more streams than the K decompositions of one timed loop, and by
     # default a count that divides them into full waves: a stream left idle
     # would still take its share of the SMs from the others)
-    NS = stream_count(args.streams, K, args.streams_default)
+    NS = stream_count(args.streams, K, getattr(args, "streams_default", False))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     budget = sms // NS if NS > 1 else 0
     Dp = [Q.Decomposition(m, n, c, r, prec, device=dev) for _ in range(NS)]
