@@ -152,14 +152,6 @@ __device__ __forceinline__ float4 q_sub_mul(float4 acc, const float4 a, const fl
   return acc;
 }
 
-// a b (quaternion product)
-__device__ __forceinline__ float4 q_mul(const float4 a, const float4 b) {
-  return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w,
-                     a.x * b.y + a.y * b.x + a.z * b.w - a.w * b.z,
-                     a.x * b.z - a.y * b.w + a.z * b.x + a.w * b.y,
-                     a.x * b.w + a.y * b.z - a.z * b.y + a.w * b.x);
-}
-
 __device__ __forceinline__ float4 q_add(float4 a, const float4 b) {
   a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
   return a;
