@@ -223,3 +223,22 @@ def test_timed_repeats_releases_the_streams_together():
     calls.clear()
     assert bench.timed_repeats(FakeTorch, run_once, [], 1.0) == [400.0] * 3
     assert not [c for c in calls if c[0] == "sleep"]
+
+
+def test_jacobi_pinv_flop_count_follows_the_shapes():
+    # per column pair of the round-robin order (n_c/2 pairs in each of n_c - 1
+    # steps for even n_c): the two squared norms (8 flops per entry each) and
+    # conj(x) y (32) over the n_r rows of G, then q w (32) and the two
+    # combinations (16) over the rows of G and of V (n_r + n_c)
+    sys.path.insert(0, ROOT)
+    import bench
+    for r, c, sweeps in ((200, 200, 16), (500, 500, 30), (120, 90, 9), (91, 91, 5)):
+        nr, nc = max(r, c), min(r, c)
+        N = nc + nc % 2
+        pairs = N // 2 * (N - 1)
+        expect = sweeps * pairs * (48 * nr + 48 * (nr + nc))
+        got = bench.pinv_flops({"c": c, "r": r, "rank_cap": 10}, "jacobi", sweeps)
+        assert got == expect, (r, c, got, expect)
+    # the colour field's 500 x 500 at 30 sweeps: 2.69e11
+    assert abs(bench.pinv_flops({"c": 500, "r": 500, "rank_cap": 100}, "jacobi", 30)
+               - 2.694e11) < 1e9
